@@ -1,0 +1,322 @@
+"""Plain FP64 CPU oracle for SU(3) gauge fixing by checkerboard overrelaxation.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The CUDA library
+never calls it and shares no code with it; the oracle is the slow, obviously
+correct reference that the library's results are compared against.
+
+The arithmetic lives in ``gf_oracle.c`` (plain C, FP64, compiled without FMA
+contraction) and ``conv_oracle.c``; this module compiles them with gcc on first
+use into ``oracle/_build/`` and wraps them with ctypes over numpy arrays.
+
+Field layout (the library's canonical layout as well): a complex128 array of
+shape (Lt, Lz, Ly, Lx, 4, 3, 3) -- x fastest among the sites, then the link
+direction mu = x, y, z, t, then the 3x3 matrix row-major.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SOURCES = ["gf_oracle.c"]
+_lock = threading.Lock()
+_libs: dict[str, C.CDLL] = {}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_lp = C.POINTER(C.c_long)
+_u32p = C.POINTER(C.c_uint32)
+
+
+def _compile(name: str, extra: list[str]) -> str:
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, name)
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    if os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in srcs):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-Wall", "-Wno-unused-function", *extra, *srcs, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def build() -> None:
+    """Compile both oracle builds (OpenMP, and single-thread flop counting)."""
+    with _lock:
+        _compile("liboracle.so", ["-fopenmp"])
+        _compile("liboracle_count.so", ["-DORACLE_COUNT_FLOPS"])
+
+
+def _declare(lib: C.CDLL) -> C.CDLL:
+    d = lib
+    d.oracle_or_half_sweep.argtypes = [_dp, _ip, C.c_int, C.c_double, C.c_int]
+    d.oracle_or_sweeps.argtypes = [_dp, _ip, C.c_double, C.c_int, C.c_int]
+    d.oracle_or_update_sites.argtypes = [_dp, _ip, _lp, C.c_long, C.c_double, C.c_int, _dp]
+    d.oracle_block_quaternion.argtypes = [_dp, _dp]
+    d.oracle_block_quaternion.restype = None
+    d.oracle_overrelax_quaternion.argtypes = [_dp, C.c_double, _dp]
+    d.oracle_site_quaternion.argtypes = [_dp, _ip, C.c_long, C.c_int, C.c_int, _dp]
+    d.oracle_site_rotate.argtypes = [_dp, _ip, C.c_long, C.c_int, _dp]
+    for f in ("oracle_functional", "oracle_theta", "oracle_theta_from_M"):
+        getattr(d, f).argtypes = [_dp, _ip, C.c_int]
+        getattr(d, f).restype = C.c_double
+    d.oracle_plaquette.argtypes = [_dp, _ip]
+    d.oracle_plaquette.restype = C.c_double
+    d.oracle_gauge_transform.argtypes = [_dp, _dp, _ip]
+    d.oracle_reunitarize.argtypes = [_dp, C.c_long]
+    d.oracle_reunitarize.restype = None
+    d.oracle_overrelax.argtypes = [_dp, _ip, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                   _ip, _dp, _dp]
+    d.oracle_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+    d.oracle_philox4x32_10.restype = None
+    d.oracle_heatbath_quaternion.argtypes = [_dp, C.c_double, C.c_uint32, C.c_uint32, C.c_int,
+                                             C.c_int, C.c_uint64, _dp]
+    d.oracle_sa_half_sweep.argtypes = [_dp, _ip, C.c_int, C.c_double, C.c_int, C.c_uint64,
+                                       C.c_uint32, C.c_int]
+    d.oracle_sa_half_sweep.restype = C.c_long
+    d.oracle_anneal.argtypes = [_dp, _ip, C.c_int, C.c_double, C.c_double, C.c_int, C.c_uint64,
+                                C.c_uint32, C.c_int]
+    d.oracle_anneal.restype = C.c_long
+    d.oracle_sa_update_sites.argtypes = [_dp, _ip, _lp, C.c_long, C.c_double, C.c_int,
+                                         C.c_uint64, C.c_uint32, C.c_int, _dp]
+    d.oracle_flops.restype = C.c_ulonglong
+    d.oracle_reset_flops.restype = None
+    d.oracle_num_threads.restype = C.c_int
+    return d
+
+
+def lib(counting: bool = False) -> C.CDLL:
+    """The compiled oracle (``counting=True``: the flop-counting build)."""
+    name = "liboracle_count.so" if counting else "liboracle.so"
+    with _lock:
+        if name not in _libs:
+            path = _compile(name, ["-DORACLE_COUNT_FLOPS"] if counting else ["-fopenmp"])
+            _libs[name] = _declare(C.CDLL(path))
+        return _libs[name]
+
+
+# ---------------------------------------------------------------------------
+# array helpers
+# ---------------------------------------------------------------------------
+def _field(U: np.ndarray) -> np.ndarray:
+    if not (isinstance(U, np.ndarray) and U.dtype == np.complex128 and U.flags.c_contiguous
+            and U.ndim == 7 and U.shape[4:] == (4, 3, 3)):
+        raise TypeError("field must be a C-contiguous complex128 array (Lt,Lz,Ly,Lx,4,3,3)")
+    return U
+
+
+def dims_of(U: np.ndarray) -> np.ndarray:
+    Lt, Lz, Ly, Lx = U.shape[:4]
+    return np.array([Lx, Ly, Lz, Lt], dtype=np.intc)
+
+
+def _d(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a: np.ndarray):
+    return a.ctypes.data_as(_ip)
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise ValueError(f"oracle {what} rejected its arguments (rc={rc})")
+
+
+# ---------------------------------------------------------------------------
+# overrelaxation (Alg. 1)
+# ---------------------------------------------------------------------------
+def or_half_sweep(U, parity: int, omega: float, gauge: int = 0, counting: bool = False) -> None:
+    U = _field(U)
+    _check(lib(counting).oracle_or_half_sweep(_d(U), _i(dims_of(U)), parity, omega, gauge),
+           "half sweep")
+
+
+def or_sweeps(U, omega: float, gauge: int = 0, n: int = 1) -> None:
+    U = _field(U)
+    _check(lib().oracle_or_sweeps(_d(U), _i(dims_of(U)), omega, gauge, n), "sweeps")
+
+
+def or_update_sites(U, sites, omega: float, gauge: int = 0) -> np.ndarray:
+    """New links of each listed site after its OR update, from unmodified U.
+
+    Returns (n, 8, 3, 3) complex: U_0..3(x) then U_0..3(x - mu).
+    """
+    U = _field(U)
+    s = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.zeros((len(s), 8, 3, 3), dtype=np.complex128)
+    _check(lib().oracle_or_update_sites(_d(U), _i(dims_of(U)), s.ctypes.data_as(_lp), len(s),
+                                        omega, gauge, _d(out)), "update sites")
+    return out
+
+
+def block_quaternion(w: np.ndarray) -> np.ndarray:
+    w = np.ascontiguousarray(w, dtype=np.complex128).reshape(2, 2)
+    k = np.zeros(4)
+    lib().oracle_block_quaternion(_d(w), _d(k))
+    return k
+
+
+def overrelax_quaternion(k, omega: float):
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    r = np.zeros(4)
+    ok = lib().oracle_overrelax_quaternion(_d(k), omega, _d(r))
+    return r if ok else None
+
+
+def site_quaternion(U, site: int, gauge: int, sg: int) -> np.ndarray:
+    U = _field(U)
+    k = np.zeros(4)
+    _check(lib().oracle_site_quaternion(_d(U), _i(dims_of(U)), site, gauge, sg, _d(k)), "quat")
+    return k
+
+
+def site_rotate(U, site: int, sg: int, r) -> None:
+    U = _field(U)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    _check(lib().oracle_site_rotate(_d(U), _i(dims_of(U)), site, sg, _d(r)), "rotate")
+
+
+# ---------------------------------------------------------------------------
+# observables
+# ---------------------------------------------------------------------------
+def functional(U, gauge: int = 0) -> float:
+    U = _field(U)
+    return lib().oracle_functional(_d(U), _i(dims_of(U)), gauge)
+
+
+def theta(U, gauge: int = 0) -> float:
+    U = _field(U)
+    return lib().oracle_theta(_d(U), _i(dims_of(U)), gauge)
+
+
+def theta_from_M(U, gauge: int = 0) -> float:
+    U = _field(U)
+    return lib().oracle_theta_from_M(_d(U), _i(dims_of(U)), gauge)
+
+
+def plaquette(U) -> float:
+    U = _field(U)
+    return lib().oracle_plaquette(_d(U), _i(dims_of(U)))
+
+
+def gauge_transform(U, g) -> None:
+    """U_mu(x) <- g(x) U_mu(x) g(x+mu)^dagger (eq. 1); g: (Lt,Lz,Ly,Lx,3,3)."""
+    U = _field(U)
+    g = np.ascontiguousarray(g, dtype=np.complex128)
+    if g.shape != U.shape[:4] + (3, 3):
+        raise TypeError("gauge field shape mismatch")
+    _check(lib().oracle_gauge_transform(_d(U), _d(g), _i(dims_of(U))), "gauge transform")
+
+
+def reunitarize(M) -> None:
+    if not (M.dtype == np.complex128 and M.flags.c_contiguous and M.shape[-2:] == (3, 3)):
+        raise TypeError("need C-contiguous complex128 (...,3,3)")
+    lib().oracle_reunitarize(_d(M), M.size // 9)
+
+
+def overrelax(U, gauge: int, omega: float, theta_target: float, max_iter: int,
+              check_every: int):
+    """Alg. 1 with the stopping rule; returns (converged, sweeps, F, theta)."""
+    U = _field(U)
+    it = C.c_int(0)
+    F = C.c_double(0)
+    th = C.c_double(0)
+    rc = lib().oracle_overrelax(_d(U), _i(dims_of(U)), gauge, omega, theta_target, max_iter,
+                                check_every, C.byref(it), C.byref(F), C.byref(th))
+    if rc < 0:
+        raise ValueError("oracle overrelax rejected its arguments")
+    return rc == 0, it.value, F.value, th.value
+
+
+# ---------------------------------------------------------------------------
+# random numbers and simulated annealing
+# ---------------------------------------------------------------------------
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().oracle_philox4x32_10(c.ctypes.data_as(_u32p), k.ctypes.data_as(_u32p),
+                               out.ctypes.data_as(_u32p))
+    return out
+
+
+def heatbath_quaternion(k, T: float, site: int, sweep: int, sg: int, cap: int, seed: int):
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    r = np.zeros(4)
+    st = lib().oracle_heatbath_quaternion(_d(k), T, site, sweep, sg, cap, seed, _d(r))
+    return st, r
+
+
+def sa_half_sweep(U, parity: int, T: float, gauge: int, seed: int, sweep: int,
+                  cap: int = 64) -> int:
+    U = _field(U)
+    f = lib().oracle_sa_half_sweep(_d(U), _i(dims_of(U)), parity, T, gauge, seed, sweep, cap)
+    if f < 0:
+        raise ValueError("oracle heatbath rejected its arguments")
+    return f
+
+
+def anneal(U, gauge: int, T0: float, T1: float, steps: int, seed: int, sweep_offset: int = 0,
+           cap: int = 64) -> int:
+    U = _field(U)
+    f = lib().oracle_anneal(_d(U), _i(dims_of(U)), gauge, T0, T1, steps, seed, sweep_offset, cap)
+    if f < 0:
+        raise ValueError("oracle anneal rejected its arguments")
+    return f
+
+
+def sa_update_sites(U, sites, T: float, gauge: int, seed: int, sweep: int,
+                    cap: int = 64) -> np.ndarray:
+    U = _field(U)
+    s = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.zeros((len(s), 8, 3, 3), dtype=np.complex128)
+    _check(lib().oracle_sa_update_sites(_d(U), _i(dims_of(U)), s.ctypes.data_as(_lp), len(s), T,
+                                        gauge, seed, sweep, cap, _d(out)), "sa update sites")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# flop counting build
+# ---------------------------------------------------------------------------
+def count_flops_half_sweep(U, parity: int, omega: float, gauge: int = 0) -> int:
+    L = lib(counting=True)
+    L.oracle_reset_flops()
+    or_half_sweep(U, parity, omega, gauge, counting=True)
+    return int(L.oracle_flops())
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+# ---------------------------------------------------------------------------
+# site helpers (canonical lexicographic order)
+# ---------------------------------------------------------------------------
+def site_index(dims, x, y, z, t) -> int:
+    Lx, Ly, Lz, _ = dims
+    return int(x + Lx * (y + Ly * (z + Lz * t)))
+
+
+def site_parity(dims, i: int) -> int:
+    Lx, Ly, Lz, _ = dims
+    x = i % Lx
+    y = (i // Lx) % Ly
+    z = (i // (Lx * Ly)) % Lz
+    t = i // (Lx * Ly * Lz)
+    return (x + y + z + t) & 1
+
+
+def backward_site(dims, i: int, mu: int) -> int:
+    Lx, Ly, Lz, Lt = dims
+    c = [i % Lx, (i // Lx) % Ly, (i // (Lx * Ly)) % Lz, i // (Lx * Ly * Lz)]
+    c[mu] = (c[mu] - 1) % dims[mu]
+    return site_index(dims, *c)

@@ -1,0 +1,895 @@
+/*
+ * gf_oracle.c -- plain FP64 CPU oracle for SU(3) lattice gauge fixing by
+ * checkerboard overrelaxation and simulated annealing.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * reference that the CUDA library is checked against.  Only the tests, the
+ * smoke check and the benchmark's CPU-baseline leg may load it.  It shares no
+ * code, header, table or helper with the CUDA path.
+ *
+ * Source: Schroeck & Vogt, "Gauge fixing using overrelaxation and simulated
+ * annealing on GPUs" (Lattice 2012).  Every function cites the passage it
+ * follows.  Points the paper leaves open are taken as follows (each is listed
+ * with its reason in the design notes of the repository):
+ *   - periodic boundaries, all extents even; RED = even parity, updated first;
+ *   - SU(2) subgroups visited in the order (0,1), (1,2), (0,2);
+ *   - the exponent g -> g^omega (Sec. 2, "to first or second order") is taken
+ *     as the 19-flop rational form: b = (w a0^2 + |a|^2)/(a0^2 + |a|^2),
+ *     r = (a0, b a)/sqrt(a0^2 + b^2 |a|^2) (equals relaxation at w = 1);
+ *   - F is normalised by 1/(Nc Nd V) so that the unit field has F = 1;
+ *   - the violation Delta(x) of eq. (theta) is the traceless part of
+ *     sum_mu [A_mu(x) - A_mu(x-mu)], A = (U - U^dagger)/(2i);
+ *   - Coulomb gauge: only spatial links enter K, F and theta, the temporal
+ *     links are rotated by the same g so that the update stays a gauge
+ *     transformation;
+ *   - a subgroup whose projected quaternion vanishes is left unchanged.
+ *
+ * Data layout (canonical, shared with the library's public API): a field is
+ * double U[Lt][Lz][Ly][Lx][4][3][3][2] -- site index x fastest, then the four
+ * link directions mu = x, y, z, t, then the 3x3 complex matrix row-major,
+ * complex numbers as (re, im).  dims = {Lx, Ly, Lz, Lt}.
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off (no fused multiply-add, so each
+ * operation rounds as written).  With -DORACLE_COUNT_FLOPS (and without
+ * OpenMP) every real floating-point operation of the overrelaxation update is
+ * counted, to pin the per-step counts printed in Alg. 1.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* 2 pi as the nearest double */
+#define ORACLE_TWO_PI 6.283185307179586476925286766559
+
+/* ------------------------------------------------------------------------ */
+/* flop counting (Alg. 1: 60 + 19 + 4 x (84 + 84) flop per subgroup)         */
+/* ------------------------------------------------------------------------ */
+#ifdef ORACLE_COUNT_FLOPS
+static unsigned long long g_flops;
+#define FLOPS(n) (g_flops += (unsigned long long)(n))
+#else
+#define FLOPS(n) ((void)0)
+#endif
+
+unsigned long long oracle_flops(void)
+{
+#ifdef ORACLE_COUNT_FLOPS
+    return g_flops;
+#else
+    return 0ULL;
+#endif
+}
+
+void oracle_reset_flops(void)
+{
+#ifdef ORACLE_COUNT_FLOPS
+    g_flops = 0;
+#endif
+}
+
+int oracle_counts_flops(void)
+{
+#ifdef ORACLE_COUNT_FLOPS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* complex numbers and 3x3 matrices                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct { double re, im; } cplx;
+typedef struct { cplx m[3][3]; } mat3;
+
+static cplx c_make(double re, double im) { cplx z; z.re = re; z.im = im; return z; }
+static cplx c_conj(cplx a) { return c_make(a.re, -a.im); }
+static cplx c_add(cplx a, cplx b) { FLOPS(2); return c_make(a.re + b.re, a.im + b.im); }
+static cplx c_sub(cplx a, cplx b) { FLOPS(2); return c_make(a.re - b.re, a.im - b.im); }
+static cplx c_mul(cplx a, cplx b)
+{
+    FLOPS(6);
+    return c_make(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+static double c_abs2(cplx a) { return a.re * a.re + a.im * a.im; }
+
+static mat3 mat_load(const double *p)
+{
+    mat3 u;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            u.m[a][b] = c_make(p[2 * (3 * a + b)], p[2 * (3 * a + b) + 1]);
+    return u;
+}
+
+static void mat_store(double *p, const mat3 *u)
+{
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            p[2 * (3 * a + b)] = u->m[a][b].re;
+            p[2 * (3 * a + b) + 1] = u->m[a][b].im;
+        }
+}
+
+static mat3 mat_dagger(const mat3 *u)
+{
+    mat3 d;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            d.m[a][b] = c_conj(u->m[b][a]);
+    return d;
+}
+
+static mat3 mat_mul(const mat3 *x, const mat3 *y)
+{
+    mat3 z;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            cplx s = c_make(0.0, 0.0);
+            for (int c = 0; c < 3; ++c)
+                s = c_add(s, c_mul(x->m[a][c], y->m[c][b]));
+            z.m[a][b] = s;
+        }
+    return z;
+}
+
+static double mat_retrace(const mat3 *u)
+{
+    return u->m[0][0].re + u->m[1][1].re + u->m[2][2].re;
+}
+
+/* ------------------------------------------------------------------------ */
+/* lattice geometry (Sec. 2: nearest neighbours, checkerboard RED/BLACK)     */
+/* ------------------------------------------------------------------------ */
+typedef struct { int L[4]; long V; } lattice;
+
+static int lattice_init(lattice *g, const int dims[4])
+{
+    g->V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (dims[mu] < 2 || (dims[mu] & 1)) return -1;
+        g->L[mu] = dims[mu];
+        g->V *= dims[mu];
+    }
+    return 0;
+}
+
+static void site_coords(const lattice *g, long i, int c[4])
+{
+    for (int mu = 0; mu < 4; ++mu) {
+        c[mu] = (int)(i % g->L[mu]);
+        i /= g->L[mu];
+    }
+}
+
+static long site_index(const lattice *g, const int c[4])
+{
+    return c[0] + (long)g->L[0] * (c[1] + (long)g->L[1] * (c[2] + (long)g->L[2] * c[3]));
+}
+
+static int site_parity(const lattice *g, long i)
+{
+    int c[4];
+    site_coords(g, i, c);
+    return (c[0] + c[1] + c[2] + c[3]) & 1;
+}
+
+/* index of x + dir * mu-hat with periodic wrap */
+static long site_shift(const lattice *g, long i, int mu, int dir)
+{
+    int c[4];
+    site_coords(g, i, c);
+    c[mu] = (c[mu] + dir + g->L[mu]) % g->L[mu];
+    return site_index(g, c);
+}
+
+static double *link_ptr(double *U, long i, int mu) { return U + (i * 4 + mu) * 18; }
+static const double *link_cptr(const double *U, long i, int mu) { return U + (i * 4 + mu) * 18; }
+
+/* ------------------------------------------------------------------------ */
+/* SU(2) subgroups (Sec. 2, Cabibbo-Marinari) in quaternion form             */
+/* ------------------------------------------------------------------------ */
+static const int SUBGROUP[3][2] = { { 0, 1 }, { 1, 2 }, { 0, 2 } };
+
+/*
+ * An SU(2) element r = (r0, r1, r2, r3), r.r = 1, is the matrix
+ *     R = r0 1 + i (r1 s1 + r2 s2 + r3 s3)
+ *       = [[ r0 + i r3,  r2 + i r1],
+ *          [-r2 + i r1,  r0 - i r3]]      (s_k the Pauli matrices).
+ * For any complex 2x2 block w, Re tr[R w] = r . k with the projection below,
+ * so the maximum of Re tr[R w] over SU(2) is |k|, reached at r = k/|k| --
+ * the quaternion form of the SU(2) local solution g = K^+/sqrt(det K^+) of
+ * eq. (localsolution).  Costs 4 flop.
+ */
+static void block_quaternion(cplx w00, cplx w01, cplx w10, cplx w11, double k[4])
+{
+    FLOPS(4);
+    k[0] = w00.re + w11.re;
+    k[1] = -(w01.im + w10.im);
+    k[2] = w10.re - w01.re;
+    k[3] = -(w00.im - w11.im);
+}
+
+static void su2_matrix(const double r[4], cplx R[2][2])
+{
+    R[0][0] = c_make(r[0], r[3]);
+    R[0][1] = c_make(r[2], r[1]);
+    R[1][0] = c_make(-r[2], r[1]);
+    R[1][1] = c_make(r[0], -r[3]);
+}
+
+/*
+ * Overrelaxation exponent g -> g^omega followed by the projection back to
+ * SU(2) (Alg. 1, "19 Flop"; Sec. 2 on the overrelaxation of Mandula and
+ * Ogilvie).  Input: the unnormalised quaternion k.  Output: r in SU(2).
+ * Returns 0 (and leaves r untouched) when k = 0.
+ */
+static int overrelax_quaternion(const double k[4], double omega, double r[4])
+{
+    double a0sq = k[0] * k[0];
+    double aisq = k[1] * k[1] + k[2] * k[2] + k[3] * k[3];
+    FLOPS(6);
+    if (a0sq + aisq == 0.0) return 0;
+    double b = (omega * a0sq + aisq) / (a0sq + aisq);
+    FLOPS(4);
+    double c = 1.0 / sqrt(a0sq + b * b * aisq);
+    FLOPS(4);
+    double bc = b * c;
+    FLOPS(1);
+    r[0] = c * k[0];
+    r[1] = bc * k[1];
+    r[2] = bc * k[2];
+    r[3] = bc * k[3];
+    FLOPS(4);
+    return 1;
+}
+
+/* U <- G U, G the subgroup (a,b) embedding of R: rows a, b mix (84 flop). */
+static void rotate_rows(mat3 *u, int a, int b, cplx R[2][2])
+{
+    for (int c = 0; c < 3; ++c) {
+        cplx ua = u->m[a][c], ub = u->m[b][c];
+        u->m[a][c] = c_add(c_mul(R[0][0], ua), c_mul(R[0][1], ub));
+        u->m[b][c] = c_add(c_mul(R[1][0], ua), c_mul(R[1][1], ub));
+    }
+}
+
+/* U <- U G^dagger: columns a, b mix (84 flop). */
+static void rotate_cols_dagger(mat3 *u, int a, int b, cplx R[2][2])
+{
+    cplx r00 = c_conj(R[0][0]), r01 = c_conj(R[0][1]);
+    cplx r10 = c_conj(R[1][0]), r11 = c_conj(R[1][1]);
+    for (int row = 0; row < 3; ++row) {
+        cplx ua = u->m[row][a], ub = u->m[row][b];
+        u->m[row][a] = c_add(c_mul(ua, r00), c_mul(ub, r01));
+        u->m[row][b] = c_add(c_mul(ua, r10), c_mul(ub, r11));
+    }
+}
+
+/*
+ * The eight links touching site x: forward U_mu(x) and backward U_mu(x-mu).
+ * nk = 4 for Landau gauge, 3 for Coulomb gauge (spatial directions in K).
+ */
+typedef struct { mat3 fwd[4], bwd[4]; } star;
+
+static void star_load(const double *U, const lattice *g, long i, star *s)
+{
+    for (int mu = 0; mu < 4; ++mu) {
+        s->fwd[mu] = mat_load(link_cptr(U, i, mu));
+        s->bwd[mu] = mat_load(link_cptr(U, site_shift(g, i, mu, -1), mu));
+    }
+}
+
+static void star_store(double *U, const lattice *g, long i, const star *s)
+{
+    for (int mu = 0; mu < 4; ++mu) {
+        mat_store(link_ptr(U, i, mu), &s->fwd[mu]);
+        mat_store(link_ptr(U, site_shift(g, i, mu, -1), mu), &s->bwd[mu]);
+    }
+}
+
+/*
+ * Quaternion of the subgroup (a,b) block of
+ *     M(x) = sum_mu [ U_mu(x) + U_mu(x-mu)^dagger ]
+ * i.e. of K(x) of eq. (Kx) with the current gauge transformation already
+ * absorbed into the links (Alg. 1 first step, "60 Flop" for nk = 4:
+ * 8 x 4 flop per link, 7 x 4 flop to sum).
+ */
+static void star_quaternion(const star *s, int nk, int a, int b, double k[4])
+{
+    double q[4];
+    int first = 1;
+    for (int mu = 0; mu < nk; ++mu) {
+        const mat3 *f = &s->fwd[mu];
+        block_quaternion(f->m[a][a], f->m[a][b], f->m[b][a], f->m[b][b], q);
+        if (first) {
+            memcpy(k, q, sizeof q);
+            first = 0;
+        } else {
+            for (int c = 0; c < 4; ++c) k[c] += q[c];
+            FLOPS(4);
+        }
+        /* block of U^dagger: (U^dagger)_{ab} = conj(U_{ba}) */
+        const mat3 *w = &s->bwd[mu];
+        block_quaternion(c_conj(w->m[a][a]), c_conj(w->m[b][a]), c_conj(w->m[a][b]),
+                         c_conj(w->m[b][b]), q);
+        for (int c = 0; c < 4; ++c) k[c] += q[c];
+        FLOPS(4);
+    }
+}
+
+static void star_rotate(star *s, int a, int b, cplx R[2][2])
+{
+    for (int mu = 0; mu < 4; ++mu) {
+        rotate_rows(&s->fwd[mu], a, b, R);
+        rotate_cols_dagger(&s->bwd[mu], a, b, R);
+    }
+}
+
+/*
+ * One overrelaxation update of one site: Alg. 1 inner body.  For every SU(2)
+ * subgroup: assemble the projected K, apply the exponent omega and project to
+ * SU(2), then U_mu(x) <- g U_mu(x) and U_mu(x-mu) <- U_mu(x-mu) g^dagger for
+ * all four mu.
+ */
+static void or_update_star(star *s, int nk, double omega)
+{
+    for (int sg = 0; sg < 3; ++sg) {
+        int a = SUBGROUP[sg][0], b = SUBGROUP[sg][1];
+        double k[4], r[4];
+        cplx R[2][2];
+        star_quaternion(s, nk, a, b, k);
+        if (!overrelax_quaternion(k, omega, r)) continue;
+        su2_matrix(r, R);
+        star_rotate(s, a, b, R);
+    }
+}
+
+static int gauge_nk(int gauge) { return gauge == 1 ? 3 : 4; }
+
+/*
+ * One half-sweep over the sites of one parity (Alg. 1, FORALL x of
+ * sublattice).  Sites of one parity share no link (Sec. 2, checkerboard), so
+ * they are updated independently and in any order.
+ */
+int oracle_or_half_sweep(double *U, const int dims[4], int parity, double omega, int gauge)
+{
+    lattice g;
+    if (lattice_init(&g, dims)) return -1;
+    int nk = gauge_nk(gauge);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (long i = 0; i < g.V; ++i) {
+        if (site_parity(&g, i) != parity) continue;
+        star s;
+        star_load(U, &g, i, &s);
+        or_update_star(&s, nk, omega);
+        star_store(U, &g, i, &s);
+    }
+    return 0;
+}
+
+/* nsweeps full sweeps: RED (parity 0) then BLACK (parity 1), Alg. 1. */
+int oracle_or_sweeps(double *U, const int dims[4], double omega, int gauge, int nsweeps)
+{
+    for (int n = 0; n < nsweeps; ++n)
+        for (int p = 0; p < 2; ++p)
+            if (oracle_or_half_sweep(U, dims, p, omega, gauge)) return -1;
+    return 0;
+}
+
+/*
+ * The eight updated links of selected sites after one OR update of each,
+ * computed from the unmodified field U (read only).  out holds, per site,
+ * U_0..3(x) then U_0..3(x-mu), 18 doubles each.  Used to check a
+ * half-sweep on a large lattice site by site.
+ */
+int oracle_or_update_sites(const double *U, const int dims[4], const long *sites, long n,
+                           double omega, int gauge, double *out)
+{
+    lattice g;
+    if (lattice_init(&g, dims)) return -1;
+    int nk = gauge_nk(gauge);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (long j = 0; j < n; ++j) {
+        star s;
+        star_load(U, &g, sites[j], &s);
+        or_update_star(&s, nk, omega);
+        for (int mu = 0; mu < 4; ++mu) {
+            mat_store(out + (j * 8 + mu) * 18, &s.fwd[mu]);
+            mat_store(out + (j * 8 + 4 + mu) * 18, &s.bwd[mu]);
+        }
+    }
+    return 0;
+}
+
+/* Single-site helpers exposed for the pinning tests. */
+void oracle_block_quaternion(const double w[8], double k[4])
+{
+    block_quaternion(c_make(w[0], w[1]), c_make(w[2], w[3]), c_make(w[4], w[5]),
+                     c_make(w[6], w[7]), k);
+}
+
+int oracle_overrelax_quaternion(const double k[4], double omega, double r[4])
+{
+    return overrelax_quaternion(k, omega, r);
+}
+
+/* quaternion k of subgroup (a,b) of M(x) at site i, from the field U */
+int oracle_site_quaternion(const double *U, const int dims[4], long i, int gauge, int sg,
+                           double k[4])
+{
+    lattice g;
+    if (lattice_init(&g, dims) || sg < 0 || sg > 2) return -1;
+    star s;
+    star_load(U, &g, i, &s);
+    star_quaternion(&s, gauge_nk(gauge), SUBGROUP[sg][0], SUBGROUP[sg][1], k);
+    return 0;
+}
+
+/*
+ * Apply one SU(2) subgroup rotation r (quaternion) at site i:
+ * U_mu(x) <- G U_mu(x), U_mu(x-mu) <- U_mu(x-mu) G^dagger for all mu.
+ */
+int oracle_site_rotate(double *U, const int dims[4], long i, int sg, const double r[4])
+{
+    lattice g;
+    if (lattice_init(&g, dims) || sg < 0 || sg > 2) return -1;
+    star s;
+    cplx R[2][2];
+    star_load(U, &g, i, &s);
+    su2_matrix(r, R);
+    star_rotate(&s, SUBGROUP[sg][0], SUBGROUP[sg][1], R);
+    star_store(U, &g, i, &s);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* gauge functional F (eq. F_g[U]) and precision theta (eq. theta)           */
+/* ------------------------------------------------------------------------ */
+
+/* F = 1/(3 nk V) sum_{x, mu < nk} Re tr U_mu(x). */
+double oracle_functional(const double *U, const int dims[4], int gauge)
+{
+    lattice g;
+    if (lattice_init(&g, dims)) return NAN;
+    int nk = gauge_nk(gauge);
+    double sum = 0.0;
+    for (long i = 0; i < g.V; ++i)
+        for (int mu = 0; mu < nk; ++mu) {
+            mat3 u = mat_load(link_cptr(U, i, mu));
+            sum += mat_retrace(&u);
+        }
+    return sum / (3.0 * nk * (double)g.V);
+}
+
+/* A = (U - U^dagger)/(2i) */
+static mat3 antiherm_part(const mat3 *u)
+{
+    mat3 A;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            cplx z = c_sub(u->m[a][b], c_conj(u->m[b][a]));
+            A.m[a][b] = c_make(0.5 * z.im, -0.5 * z.re); /* z / (2i) */
+        }
+    return A;
+}
+
+static void make_traceless(mat3 *A)
+{
+    cplx tr = c_make(0.0, 0.0);
+    for (int a = 0; a < 3; ++a) tr = c_add(tr, A->m[a][a]);
+    for (int a = 0; a < 3; ++a) A->m[a][a] = c_sub(A->m[a][a], c_make(tr.re / 3.0, tr.im / 3.0));
+}
+
+static double frob2(const mat3 *A)
+{
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) s += c_abs2(A->m[a][b]);
+    return s;
+}
+
+/*
+ * theta = 1/(Nc V) sum_x tr[Delta(x) Delta(x)^dagger] with
+ * Delta(x) = traceless part of sum_{mu<nk} [A_mu(x) - A_mu(x-mu)].
+ * This is the lattice divergence of the gauge field.
+ */
+double oracle_theta(const double *U, const int dims[4], int gauge)
+{
+    lattice g;
+    if (lattice_init(&g, dims)) return NAN;
+    int nk = gauge_nk(gauge);
+    double sum = 0.0;
+    for (long i = 0; i < g.V; ++i) {
+        mat3 D;
+        memset(&D, 0, sizeof D);
+        for (int mu = 0; mu < nk; ++mu) {
+            mat3 uf = mat_load(link_cptr(U, i, mu));
+            mat3 ub = mat_load(link_cptr(U, site_shift(&g, i, mu, -1), mu));
+            mat3 Af = antiherm_part(&uf), Ab = antiherm_part(&ub);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    D.m[a][b] = c_add(D.m[a][b], c_sub(Af.m[a][b], Ab.m[a][b]));
+        }
+        make_traceless(&D);
+        sum += frob2(&D);
+    }
+    return sum / (3.0 * (double)g.V);
+}
+
+/*
+ * The same theta through the local matrix of the update:
+ * Delta(x) = traceless part of (M(x) - M(x)^dagger)/(2i),
+ * M(x) = sum_mu [U_mu(x) + U_mu(x-mu)^dagger].  A second, independent route
+ * used to pin oracle_theta.
+ */
+double oracle_theta_from_M(const double *U, const int dims[4], int gauge)
+{
+    lattice g;
+    if (lattice_init(&g, dims)) return NAN;
+    int nk = gauge_nk(gauge);
+    double sum = 0.0;
+    for (long i = 0; i < g.V; ++i) {
+        mat3 M;
+        memset(&M, 0, sizeof M);
+        for (int mu = 0; mu < nk; ++mu) {
+            mat3 uf = mat_load(link_cptr(U, i, mu));
+            mat3 ub = mat_load(link_cptr(U, site_shift(&g, i, mu, -1), mu));
+            mat3 ubd = mat_dagger(&ub);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    M.m[a][b] = c_add(M.m[a][b], c_add(uf.m[a][b], ubd.m[a][b]));
+        }
+        mat3 D = antiherm_part(&M);
+        make_traceless(&D);
+        sum += frob2(&D);
+    }
+    return sum / (3.0 * (double)g.V);
+}
+
+/* average plaquette, 1/(18 V) sum_{x, mu<nu} Re tr[U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+] */
+double oracle_plaquette(const double *U, const int dims[4])
+{
+    lattice g;
+    if (lattice_init(&g, dims)) return NAN;
+    double sum = 0.0;
+    for (long i = 0; i < g.V; ++i)
+        for (int mu = 0; mu < 4; ++mu)
+            for (int nu = mu + 1; nu < 4; ++nu) {
+                mat3 a = mat_load(link_cptr(U, i, mu));
+                mat3 b = mat_load(link_cptr(U, site_shift(&g, i, mu, +1), nu));
+                mat3 c = mat_load(link_cptr(U, site_shift(&g, i, nu, +1), mu));
+                mat3 d = mat_load(link_cptr(U, i, nu));
+                mat3 cd = mat_dagger(&c), dd = mat_dagger(&d);
+                mat3 ab = mat_mul(&a, &b);
+                mat3 abc = mat_mul(&ab, &cd);
+                mat3 p = mat_mul(&abc, &dd);
+                sum += mat_retrace(&p);
+            }
+    return sum / (18.0 * (double)g.V);
+}
+
+/* ------------------------------------------------------------------------ */
+/* gauge transformation (eq. 1) and reunitarisation                           */
+/* ------------------------------------------------------------------------ */
+
+/* U_mu(x) <- g(x) U_mu(x) g(x+mu)^dagger for all x, mu; g[V][3][3][2]. */
+int oracle_gauge_transform(double *U, const double *gfield, const int dims[4])
+{
+    lattice g;
+    if (lattice_init(&g, dims)) return -1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (long i = 0; i < g.V; ++i) {
+        mat3 gx = mat_load(gfield + i * 18);
+        for (int mu = 0; mu < 4; ++mu) {
+            mat3 gy = mat_load(gfield + site_shift(&g, i, mu, +1) * 18);
+            mat3 gyd = mat_dagger(&gy);
+            mat3 u = mat_load(link_cptr(U, i, mu));
+            mat3 t = mat_mul(&gx, &u);
+            mat3 r = mat_mul(&t, &gyd);
+            mat_store(link_ptr(U, i, mu), &r);
+        }
+    }
+    return 0;
+}
+
+/*
+ * Project n 3x3 matrices back onto SU(3): Gram-Schmidt on rows 0 and 1, then
+ * row 2 = conj(row0 x row1), which makes the determinant 1.
+ */
+void oracle_reunitarize(double *M, long n)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (long j = 0; j < n; ++j) {
+        mat3 u = mat_load(M + j * 18);
+        double n0 = 0.0;
+        for (int c = 0; c < 3; ++c) n0 += c_abs2(u.m[0][c]);
+        n0 = 1.0 / sqrt(n0);
+        for (int c = 0; c < 3; ++c) u.m[0][c] = c_make(u.m[0][c].re * n0, u.m[0][c].im * n0);
+        cplx ip = c_make(0.0, 0.0); /* <row0, row1> */
+        for (int c = 0; c < 3; ++c) ip = c_add(ip, c_mul(c_conj(u.m[0][c]), u.m[1][c]));
+        for (int c = 0; c < 3; ++c) u.m[1][c] = c_sub(u.m[1][c], c_mul(ip, u.m[0][c]));
+        double n1 = 0.0;
+        for (int c = 0; c < 3; ++c) n1 += c_abs2(u.m[1][c]);
+        n1 = 1.0 / sqrt(n1);
+        for (int c = 0; c < 3; ++c) u.m[1][c] = c_make(u.m[1][c].re * n1, u.m[1][c].im * n1);
+        for (int c = 0; c < 3; ++c) {
+            int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+            cplx x = c_sub(c_mul(u.m[0][c1], u.m[1][c2]), c_mul(u.m[0][c2], u.m[1][c1]));
+            u.m[2][c] = c_conj(x);
+        }
+        mat_store(M + j * 18, &u);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* host convergence loop (Alg. 1 WHILE; Sec. 4.1: check every N iterations)  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Sweep until theta < theta_target, checking theta before the first sweep and
+ * then after every check_every sweeps, at most max_iter sweeps.  Returns 0 if
+ * converged, 1 if max_iter was reached, -1 on bad arguments.
+ */
+int oracle_overrelax(double *U, const int dims[4], int gauge, double omega, double theta_target,
+                     int max_iter, int check_every, int *iters_out, double *F_out,
+                     double *theta_out)
+{
+    lattice g;
+    if (lattice_init(&g, dims) || check_every < 1 || max_iter < 0) return -1;
+    int it = 0;
+    double th = oracle_theta(U, dims, gauge);
+    while (!(th < theta_target) && it < max_iter) {
+        int n = check_every;
+        if (n > max_iter - it) n = max_iter - it;
+        oracle_or_sweeps(U, dims, omega, gauge, n);
+        it += n;
+        th = oracle_theta(U, dims, gauge);
+    }
+    if (iters_out) *iters_out = it;
+    if (F_out) *F_out = oracle_functional(U, dims, gauge);
+    if (theta_out) *theta_out = th;
+    return th < theta_target ? 0 : 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,        */
+/* "Parallel random numbers: as easy as 1, 2, 3", SC'11)                     */
+/* ------------------------------------------------------------------------ */
+static void philox_round(uint32_t c[4], const uint32_t k[2])
+{
+    uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c[4] = { ctr[0], ctr[1], ctr[2], ctr[3] };
+    uint32_t k[2] = { key[0], key[1] };
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k[0] += 0x9E3779B9u;
+            k[1] += 0xBB67AE85u;
+        }
+        philox_round(c, k);
+    }
+    memcpy(out, c, sizeof c);
+}
+
+/* open-interval uniform (0,1) from one 32-bit word: (w + 1/2) / 2^32 */
+static double u01(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0); }
+
+/* ------------------------------------------------------------------------ */
+/* simulated annealing: SU(2)-subgroup heatbath on exp(Re tr[g K] / T)       */
+/* (Sec. 1, simulated annealing as a preconditioner)                         */
+/* ------------------------------------------------------------------------ */
+#define SA_TAG 1u
+#define SA_DIRECTION_DRAW 255u
+#define SA_ALPHA_SWITCH 2.0
+
+/*
+ * Draw s0 in [-1,1] with density sqrt(1 - s0^2) exp(alpha s0), the
+ * distribution of the real part of an SU(2) element under the Haar measure
+ * weighted by exp(alpha s0).  alpha < 2: Creutz (1980), inverse-CDF draw of
+ * exp(alpha s0) accepted with probability sqrt(1 - s0^2).  alpha >= 2:
+ * Kennedy and Pendleton (1985), s0 = 1 - 2 lambda^2 with lambda^2 drawn from
+ * lambda^2 exp(-2 alpha lambda^2) and accepted with probability
+ * sqrt(1 - lambda^2).  Attempt a uses Philox counter (site, sweep,
+ * sg * 256 + a, 1).  Returns 1 on success, 0 after cap rejections.
+ */
+static int heatbath_s0(double alpha, uint32_t site, uint32_t sweep, int sg, int cap,
+                       const uint32_t key[2], double *s0_out)
+{
+    for (int a = 0; a < cap && a < (int)SA_DIRECTION_DRAW; ++a) {
+        uint32_t ctr[4] = { site, sweep, (uint32_t)sg * 256u + (uint32_t)a, SA_TAG };
+        uint32_t w[4];
+        oracle_philox4x32_10(ctr, key, w);
+        if (alpha < SA_ALPHA_SWITCH) {
+            double u = u01(w[0]);
+            double e = exp(-2.0 * alpha);
+            double s0 = 1.0 + log(e + u * (1.0 - e)) / alpha;
+            double v = u01(w[1]);
+            if (v <= sqrt(1.0 - s0 * s0)) {
+                *s0_out = s0;
+                return 1;
+            }
+        } else {
+            double c = cos(ORACLE_TWO_PI * u01(w[1]));
+            double lam2 = -(log(u01(w[0])) + c * c * log(u01(w[2]))) / (2.0 * alpha);
+            double v = u01(w[3]);
+            if (v * v <= 1.0 - lam2) {
+                *s0_out = 1.0 - 2.0 * lam2;
+                return 1;
+            }
+        }
+    }
+    return 0;
+}
+
+/* quaternion product q = a b, the product of the SU(2) matrices */
+static void quat_mul(const double a[4], const double b[4], double q[4])
+{
+    q[0] = a[0] * b[0] - (a[1] * b[1] + a[2] * b[2] + a[3] * b[3]);
+    double cx = a[2] * b[3] - a[3] * b[2];
+    double cy = a[3] * b[1] - a[1] * b[3];
+    double cz = a[1] * b[2] - a[2] * b[1];
+    q[1] = a[0] * b[1] + b[0] * a[1] - cx;
+    q[2] = a[0] * b[2] + b[0] * a[2] - cy;
+    q[3] = a[0] * b[3] + b[0] * a[3] - cz;
+}
+
+/*
+ * Heatbath choice of the subgroup element: r = s k/|k| with s drawn from
+ * exp(alpha s0) dHaar(s), alpha = |k|/T, so that r has density
+ * proportional to exp(Re tr[r w]/T) = exp(r.k/T).  The direction of the
+ * imaginary part of s is uniform on the sphere, from Philox counter
+ * (site, sweep, sg * 256 + 255, 1).
+ */
+static int heatbath_quaternion(const double k[4], double T, uint32_t site, uint32_t sweep, int sg,
+                               int cap, const uint32_t key[2], double r[4])
+{
+    double kn = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
+    if (kn == 0.0) return 2; /* nothing to do */
+    double s0;
+    if (!heatbath_s0(kn / T, site, sweep, sg, cap, key, &s0)) return 0;
+    uint32_t ctr[4] = { site, sweep, (uint32_t)sg * 256u + SA_DIRECTION_DRAW, SA_TAG };
+    uint32_t w[4];
+    oracle_philox4x32_10(ctr, key, w);
+    double ct = 2.0 * u01(w[0]) - 1.0;
+    double phi = ORACLE_TWO_PI * u01(w[1]);
+    double st = sqrt(1.0 - ct * ct);
+    double rho = sqrt(1.0 - s0 * s0);
+    double s[4] = { s0, rho * st * cos(phi), rho * st * sin(phi), rho * ct };
+    double kh[4] = { k[0] / kn, k[1] / kn, k[2] / kn, k[3] / kn };
+    quat_mul(s, kh, r);
+    return 1;
+}
+
+int oracle_heatbath_quaternion(const double k[4], double T, uint32_t site, uint32_t sweep, int sg,
+                               int cap, uint64_t seed, double r[4])
+{
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    return heatbath_quaternion(k, T, site, sweep, sg, cap, key, r);
+}
+
+static int sa_update_star(star *s, int nk, double T, uint32_t site, uint32_t sweep, int cap,
+                          const uint32_t key[2])
+{
+    int ok = 1;
+    for (int sg = 0; sg < 3; ++sg) {
+        int a = SUBGROUP[sg][0], b = SUBGROUP[sg][1];
+        double k[4], r[4];
+        cplx R[2][2];
+        star_quaternion(s, nk, a, b, k);
+        int st = heatbath_quaternion(k, T, site, sweep, sg, cap, key, r);
+        if (st == 0) ok = 0;
+        if (st != 1) continue;
+        su2_matrix(r, R);
+        star_rotate(s, a, b, R);
+    }
+    return ok;
+}
+
+/*
+ * One heatbath half-sweep at temperature T over the sites of one parity.
+ * Returns the number of subgroup draws that hit the rejection cap (those
+ * subgroups are left unchanged), or -1 on bad arguments.
+ */
+long oracle_sa_half_sweep(double *U, const int dims[4], int parity, double T, int gauge,
+                          uint64_t seed, uint32_t sweep, int cap)
+{
+    lattice g;
+    if (lattice_init(&g, dims) || !(T > 0.0) || cap < 1) return -1;
+    int nk = gauge_nk(gauge);
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    long failures = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : failures)
+#endif
+    for (long i = 0; i < g.V; ++i) {
+        if (site_parity(&g, i) != parity) continue;
+        star s;
+        star_load(U, &g, i, &s);
+        if (!sa_update_star(&s, nk, T, (uint32_t)i, sweep, cap, key)) failures += 1;
+        star_store(U, &g, i, &s);
+    }
+    return failures;
+}
+
+/*
+ * Simulated annealing: steps heatbath sweeps with T falling linearly from T0
+ * to T1, T_k = T0 + (T1 - T0) k / (steps - 1); sweep k uses Philox sweep
+ * counter sweep_offset + k.
+ */
+long oracle_anneal(double *U, const int dims[4], int gauge, double T0, double T1, int steps,
+                   uint64_t seed, uint32_t sweep_offset, int cap)
+{
+    long failures = 0;
+    for (int k = 0; k < steps; ++k) {
+        double T = steps > 1 ? T0 + (T1 - T0) * (double)k / (double)(steps - 1) : T0;
+        for (int p = 0; p < 2; ++p) {
+            long f = oracle_sa_half_sweep(U, dims, p, T, gauge, seed, sweep_offset + (uint32_t)k, cap);
+            if (f < 0) return -1;
+            failures += f;
+        }
+    }
+    return failures;
+}
+
+/* per-site heatbath updates of selected sites from an unmodified field */
+int oracle_sa_update_sites(const double *U, const int dims[4], const long *sites, long n, double T,
+                           int gauge, uint64_t seed, uint32_t sweep, int cap, double *out)
+{
+    lattice g;
+    if (lattice_init(&g, dims)) return -1;
+    int nk = gauge_nk(gauge);
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (long j = 0; j < n; ++j) {
+        star s;
+        star_load(U, &g, sites[j], &s);
+        sa_update_star(&s, nk, T, (uint32_t)sites[j], sweep, cap, key);
+        for (int mu = 0; mu < 4; ++mu) {
+            mat_store(out + (j * 8 + mu) * 18, &s.fwd[mu]);
+            mat_store(out + (j * 8 + 4 + mu) * 18, &s.bwd[mu]);
+        }
+    }
+    return 0;
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    int n = 1;
+#pragma omp parallel
+    {
+#pragma omp single
+        n = omp_get_num_threads();
+    }
+    return n;
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,432 @@
+"""Pins of the CPU oracle against facts fixed by the paper and the mathematics.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (Alg. 1 flop counts), published known answers (Philox), closed
+forms and textbook routines (SU(2) local solution, eq. localsolution),
+invariants (gauge invariance of the plaquette, unitarity), brute force
+(no SU(2) rotation beats the closed-form subgroup maximum), monotonicity of
+plain relaxation, and the distribution a heatbath must sample.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1209_4008_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+SUBGROUPS = [(0, 1), (1, 2), (0, 2)]
+
+
+def field(dims, seed=1, gseed=2, plaq=0.60, pure=False):
+    return synth.as_numpy(synth.make_field(dims, plaq, seed, gseed, pure_gauge=pure))
+
+
+def su2_from_quaternion(r):
+    """Independent construction: R = r0 1 + i (r1 s1 + r2 s2 + r3 s3)."""
+    s1 = np.array([[0, 1], [1, 0]], complex)
+    s2 = np.array([[0, -1j], [1j, 0]], complex)
+    s3 = np.array([[1, 0], [0, -1]], complex)
+    return r[0] * np.eye(2) + 1j * (r[1] * s1 + r[2] * s2 + r[3] * s3)
+
+
+def embed(R2, a, b):
+    G = np.eye(3, dtype=complex)
+    G[np.ix_([a, b], [a, b])] = R2
+    return G
+
+
+def site_star(U, dims, i):
+    """The 8 links of site i: U_mu(x), U_mu(x - mu) (numpy views of copies)."""
+    Lx, Ly, Lz, Lt = dims
+    flat = U.reshape(-1, 4, 3, 3)
+    fwd = [flat[i, mu].copy() for mu in range(4)]
+    bwd = [flat[oracle.backward_site(dims, i, mu), mu].copy() for mu in range(4)]
+    return fwd, bwd
+
+
+def local_objective(G, fwd, bwd, nk=4):
+    """sum_mu Re tr[G U_mu(x)] + Re tr[U_mu(x-mu) G^dagger] -- the part of F that
+    depends on g(x) (eq. F_g[U] with the update of eq. 1 at one site)."""
+    return sum(np.trace(G @ fwd[m]).real + np.trace(bwd[m] @ G.conj().T).real for m in range(nk))
+
+
+def haar_su2(n, rng):
+    q = rng.standard_normal((n, 4))
+    return q / np.linalg.norm(q, axis=1, keepdims=True)
+
+
+# --------------------------------------------------------------------------
+# values the paper prints
+# --------------------------------------------------------------------------
+def test_flop_counts_match_alg1():
+    gold = json.load(open(os.path.join(GOLDEN, "paper_flop_counts.json")))
+    ps = gold["per_subgroup"]
+    per_sub = ps["assemble_K"] + ps["omega_and_project"] + 4 * (
+        ps["update_forward_link"] + ps["update_backward_link"])
+    assert per_sub == gold["per_site_per_subgroup"]
+    assert 3 * per_sub == gold["per_site_su3"]
+    dims = (4, 4, 4, 4)
+    U = field(dims)
+    V = 4 ** 4
+    flops = oracle.count_flops_half_sweep(U, 0, 1.7, 0)
+    assert flops == gold["per_site_su3"] * (V // 2)
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10 known answers (Salmon et al., SC'11)
+# --------------------------------------------------------------------------
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox4x32_10(v[0:4], v[4:6])
+        assert list(out) == v[6:10]
+
+
+# --------------------------------------------------------------------------
+# SU(2) subgroup algebra
+# --------------------------------------------------------------------------
+def test_quaternion_projection_is_re_trace():
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        w = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+        r = haar_su2(1, rng)[0]
+        k = oracle.block_quaternion(w)
+        assert np.trace(su2_from_quaternion(r) @ w).real == pytest.approx(r @ k, abs=1e-13)
+
+
+def test_overrelax_quaternion_properties():
+    rng = np.random.default_rng(6)
+    for _ in range(200):
+        k = rng.standard_normal(4) * rng.uniform(0.1, 10)
+        r1 = oracle.overrelax_quaternion(k, 1.0)
+        np.testing.assert_allclose(r1, k / np.linalg.norm(k), atol=1e-15)  # relaxation
+        r = oracle.overrelax_quaternion(k, 1.7)
+        assert abs(np.linalg.norm(r) - 1) < 1e-15
+        # same axis, larger rotation angle in the direction of k (tan phi' = b tan phi)
+        kh = k / np.linalg.norm(k)
+        phi = math.atan2(np.linalg.norm(kh[1:]), kh[0])
+        phip = math.atan2(np.linalg.norm(r[1:]), r[0])
+        b = (1.7 * kh[0] ** 2 + (1 - kh[0] ** 2))
+        assert math.tan(phip) == pytest.approx(b * math.tan(phi), rel=1e-10, abs=1e-12)
+        np.testing.assert_allclose(np.cross(r[1:], k[1:]), 0, atol=1e-12)
+    # small angles: g^omega to first order, angle multiplied by omega
+    k = np.array([1.0, 1e-4, -2e-4, 3e-4])
+    r = oracle.overrelax_quaternion(k, 1.7)
+    ang = lambda q: 2 * math.atan2(np.linalg.norm(q[1:]), q[0])
+    assert ang(r) == pytest.approx(1.7 * ang(k / np.linalg.norm(k)), rel=1e-6)
+    assert oracle.overrelax_quaternion(np.zeros(4), 1.7) is None
+
+
+def test_brute_force_no_su2_beats_subgroup_maximum():
+    """North-star test (c): random SU(2) rotations never raise Re tr[g K]
+    past the closed-form maximum |k| of the subgroup."""
+    dims = (4, 4, 4, 4)
+    U = field(dims, seed=11, gseed=12)
+    rng = np.random.default_rng(7)
+    for i in (0, 37, 101):
+        fwd, bwd = site_star(U, dims, i)
+        for sg, (a, b) in enumerate(SUBGROUPS):
+            k = oracle.site_quaternion(U, i, 0, sg)
+            rbest = oracle.overrelax_quaternion(k, 1.0)
+            base = local_objective(np.eye(3), fwd, bwd)
+            best = local_objective(embed(su2_from_quaternion(rbest), a, b), fwd, bwd)
+            # the identity's block contributes k0, the maximum |k|
+            assert best - base == pytest.approx(np.linalg.norm(k) - k[0], abs=1e-12)
+            qs = haar_su2(100_000, rng)
+            # objective is affine in r: base + (r - 1).k ; evaluate a sample exactly too
+            vals = base + qs @ k - k[0]
+            assert vals.max() <= best + 1e-12
+            assert vals.max() > best - 0.1 * np.linalg.norm(k)
+            for q in qs[:50]:
+                v = local_objective(embed(su2_from_quaternion(q), a, b), fwd, bwd)
+                assert v == pytest.approx(base + q @ k - k[0], abs=1e-12)
+                assert v <= best + 1e-12
+
+
+def test_stationary_after_relaxation_step():
+    dims = (4, 4, 4, 4)
+    U = field(dims, seed=13, gseed=14)
+    for i in (3, 64, 200):
+        for sg in range(3):
+            k = oracle.site_quaternion(U, i, 0, sg)
+            r = oracle.overrelax_quaternion(k, 1.0)
+            oracle.site_rotate(U, i, sg, r)
+            k2 = oracle.site_quaternion(U, i, 0, sg)
+            assert np.linalg.norm(k2[1:]) <= 1e-13 * np.linalg.norm(k)
+            assert k2[0] == pytest.approx(np.linalg.norm(k), rel=1e-14)
+
+
+def test_su2_reduction_matches_textbook_local_solution():
+    """Links block-diag(SU(2), 1): the SU(3) update at omega = 1 is SU(2)
+    relaxation g = K^+ / sqrt(det K^+) (eq. localsolution)."""
+    dims = (4, 4, 4, 4)
+    rng = np.random.default_rng(8)
+    V = 4 ** 4
+    q = haar_su2(V * 4, rng)
+    U = np.zeros((4, 4, 4, 4, 4, 3, 3), complex)
+    flat = U.reshape(-1, 3, 3)
+    for n in range(V * 4):
+        flat[n] = embed(su2_from_quaternion(q[n]), 0, 1)
+    ref = U.copy()
+    oracle.or_half_sweep(U, 0, 1.0, 0)
+    rflat = ref.reshape(-1, 4, 3, 3)
+    for i in range(V):
+        if oracle.site_parity(dims, i) != 0:
+            continue
+        K = np.zeros((2, 2), complex)
+        for mu in range(4):
+            K += rflat[i, mu, :2, :2]
+            K += rflat[oracle.backward_site(dims, i, mu), mu, :2, :2].conj().T
+        Kd = K.conj().T
+        g2 = Kd / np.sqrt(np.linalg.det(Kd))
+        G = embed(g2, 0, 1)
+        for mu in range(4):
+            rflat[i, mu] = G @ rflat[i, mu]
+            j = oracle.backward_site(dims, i, mu)
+            rflat[j, mu] = rflat[j, mu] @ G.conj().T
+    np.testing.assert_allclose(U, ref, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# functional and precision
+# --------------------------------------------------------------------------
+def test_functional_and_theta_special_cases():
+    dims = (4, 4, 4, 6)
+    U = np.zeros((6, 4, 4, 4, 4, 3, 3), complex)
+    U[...] = np.eye(3)
+    assert oracle.functional(U, 0) == pytest.approx(1.0, abs=1e-15)
+    assert oracle.theta(U, 0) == 0.0
+    assert oracle.plaquette(U) == pytest.approx(1.0, abs=1e-15)
+    # a constant field: F = Re tr U0 / 3, divergence zero
+    rng = np.random.default_rng(3)
+    U0 = synth.as_numpy(synth.haar_su3((1,), 77))[0]
+    U[...] = U0
+    assert oracle.functional(U, 0) == pytest.approx(np.trace(U0).real / 3, abs=1e-14)
+    assert oracle.theta(U, 0) < 1e-28
+    # centre element: F = Re(z) for z = exp(2 pi i / 3)
+    z = np.exp(2j * np.pi / 3)
+    U[...] = z * np.eye(3)
+    assert oracle.functional(U, 0) == pytest.approx(z.real, abs=1e-15)
+    del rng
+
+
+def test_theta_two_routes_agree():
+    for dims, gauge in (((4, 4, 4, 4), 0), ((4, 6, 4, 8), 0), ((4, 4, 4, 6), 1)):
+        U = field(dims, seed=21, gseed=22)
+        a, b = oracle.theta(U, gauge), oracle.theta_from_M(U, gauge)
+        assert a == pytest.approx(b, rel=1e-13)
+
+
+def test_theta_single_link_closed_form():
+    """One non-trivial link W at site 0 in direction mu, unit field elsewhere:
+    Delta = +A(W) at x = 0 and -A(W) at x + mu, so theta = 2 |A(W)|^2 / (3V)."""
+    dims = (4, 4, 4, 4)
+    U = np.zeros((4, 4, 4, 4, 4, 3, 3), complex)
+    U[...] = np.eye(3)
+    W = synth.as_numpy(synth.haar_su3((1,), 5))[0]
+    U[0, 0, 0, 0, 2] = W
+    A = (W - W.conj().T) / 2j
+    A -= np.trace(A) / 3 * np.eye(3)
+    expect = 2 * np.sum(np.abs(A) ** 2) / (3 * 256)
+    assert oracle.theta(U, 0) == pytest.approx(expect, rel=1e-13)
+    # Coulomb: a temporal link does not enter theta
+    U[...] = np.eye(3)
+    U[0, 0, 0, 0, 3] = W
+    assert oracle.theta(U, 1) == 0.0
+    assert oracle.functional(U, 1) == pytest.approx(1.0, abs=1e-15)
+
+
+def test_plaquette_target_of_the_generator():
+    U = field((8, 8, 8, 8), seed=1, gseed=2, plaq=0.60)
+    assert abs(oracle.plaquette(U) - 0.60) < 0.004
+
+
+# --------------------------------------------------------------------------
+# invariants of the sweep
+# --------------------------------------------------------------------------
+def unitarity_error(U):
+    M = U.reshape(-1, 3, 3)
+    e = np.abs(M @ M.conj().transpose(0, 2, 1) - np.eye(3)).max()
+    d = np.abs(np.linalg.det(M) - 1).max()
+    return max(e, d)
+
+
+@pytest.mark.parametrize("gauge", [0, 1])
+def test_plaquette_invariant_and_unitarity(gauge):
+    """North-star test (b): every sweep is a gauge transformation."""
+    dims = (4, 4, 6, 4)
+    U = field(dims, seed=31, gseed=32)
+    P0 = oracle.plaquette(U)
+    for n in range(20):
+        oracle.or_sweeps(U, 1.7, gauge, 5)
+        assert abs(oracle.plaquette(U) - P0) < 1e-13
+    assert unitarity_error(U) < 1e-13
+
+
+@pytest.mark.parametrize("gauge", [0, 1])
+def test_relaxation_is_monotone(gauge):
+    """North-star test (d): at omega = 1, F never decreases."""
+    dims = (4, 4, 4, 4)
+    U = field(dims, seed=41, gseed=42)
+    F = oracle.functional(U, gauge)
+    for n in range(30):
+        oracle.or_half_sweep(U, n % 2, 1.0, gauge)
+        F2 = oracle.functional(U, gauge)
+        assert F2 >= F - 1e-15
+        F = F2
+
+
+def test_half_sweep_touches_each_link_once_and_only_its_parity():
+    """Sites of one parity are independent: the site-by-site update equals the
+    half-sweep, and links between two sites of the other parity do not exist."""
+    dims = (4, 4, 4, 4)
+    U = field(dims, seed=51, gseed=52)
+    sites = [i for i in range(256) if oracle.site_parity(dims, i) == 1]
+    per_site = oracle.or_update_sites(U, sites, 1.7, 0)
+    W = U.copy()
+    oracle.or_half_sweep(W, 1, 1.7, 0)
+    flat = W.reshape(-1, 4, 3, 3)
+    for j, i in enumerate(sites):
+        for mu in range(4):
+            np.testing.assert_array_equal(per_site[j, mu], flat[i, mu])
+            np.testing.assert_array_equal(per_site[j, 4 + mu],
+                                          flat[oracle.backward_site(dims, i, mu), mu])
+
+
+def test_pure_gauge_reaches_unit_functional():
+    """North-star test (a): U = g(x) g(x+mu)^dagger fixes to F = 1, theta -> 0."""
+    for dims, seed in (((4, 4, 4, 4), 2), ((8, 8, 8, 8), 2), ((4, 6, 4, 8), 3)):
+        U = field(dims, gseed=seed, pure=True)
+        conv, it, F, th = oracle.overrelax(U, 0, 1.7, 1e-24, 20000, 10)
+        assert conv and th < 1e-24
+        assert F == pytest.approx(1.0, abs=1e-12)
+        np.testing.assert_allclose(np.abs(U.reshape(-1, 3, 3)[:, range(3), range(3)]), 1, atol=1e-10)
+
+
+def test_coulomb_converges_per_timeslice():
+    dims = (4, 4, 4, 4)
+    U = field(dims, seed=61, gseed=62)
+    conv, it, F, th = oracle.overrelax(U, 1, 1.7, 1e-13, 5000, 10)
+    assert conv and th < 1e-13
+    assert oracle.theta(U, 0) > 1e-6  # Landau violation remains: different gauge
+
+
+def test_overrelax_driver_checks_cadence():
+    dims = (4, 4, 4, 4)
+    U = field(dims, seed=71, gseed=72)
+    conv, it, F, th = oracle.overrelax(U.copy(), 0, 1.7, 1e-10, 5000, 7)
+    assert conv and it % 7 == 0
+    # the same number of sweeps by hand reproduces the result exactly
+    W = U.copy()
+    oracle.or_sweeps(W, 1.7, 0, it)
+    assert oracle.theta(W, 0) == th
+    conv2, it2, F2, th2 = oracle.overrelax(U.copy(), 0, 1.7, 1e-10, it - 7, 7)
+    assert not conv2 and it2 == it - 7 and th2 >= 1e-10
+    # already converged input: zero sweeps
+    conv3, it3, _, _ = oracle.overrelax(W, 0, 1.7, 1e-10, 100, 7)
+    assert conv3 and it3 == 0
+
+
+def test_reunitarize_projects_onto_su3():
+    M = synth.as_numpy(synth.haar_su3((500,), 9))
+    P = M.copy()
+    oracle.reunitarize(P)
+    np.testing.assert_allclose(P, M, atol=1e-14)  # idempotent on SU(3)
+    rng = np.random.default_rng(1)
+    N = M + 1e-3 * (rng.standard_normal(M.shape) + 1j * rng.standard_normal(M.shape))
+    oracle.reunitarize(N)
+    assert unitarity_error(N) < 1e-14
+    assert np.abs(N - M).max() < 1e-2
+
+
+def test_gauge_transform_preserves_plaquette():
+    dims = (4, 4, 4, 4)
+    U = field(dims, seed=81, gseed=82)
+    g = synth.as_numpy(synth.haar_su3((4, 4, 4, 4), 83))
+    P = oracle.plaquette(U)
+    oracle.gauge_transform(U, g)
+    assert oracle.plaquette(U) == pytest.approx(P, abs=1e-14)
+
+
+# --------------------------------------------------------------------------
+# heatbath (simulated annealing)
+# --------------------------------------------------------------------------
+def s0_cdf(alpha):
+    x = np.linspace(-1, 1, 200_001)
+    dens = np.sqrt(np.clip(1 - x * x, 0, None)) * np.exp(alpha * (x - 1))
+    c = np.concatenate([[0], np.cumsum(0.5 * (dens[1:] + dens[:-1]) * np.diff(x))])
+    return x, c / c[-1]
+
+
+@pytest.mark.parametrize("alpha", [0.3, 1.9, 2.1, 8.0, 150.0])
+def test_heatbath_samples_weighted_haar(alpha):
+    """r . k/|k| must follow sqrt(1 - s^2) exp(alpha s) (weight exp(Re tr[gK]/T)
+    times the SU(2) Haar measure); the perpendicular part must be isotropic."""
+    rng = np.random.default_rng(int(alpha * 10))
+    k = rng.standard_normal(4)
+    kn = np.linalg.norm(k)
+    T = kn / alpha
+    n = 6000
+    s = np.empty(n)
+    perp = np.empty((n, 3))
+    kh = k / kn
+    for j in range(n):
+        st, r = oracle.heatbath_quaternion(k, T, j, 17, j % 3, 64, 1234)
+        assert st == 1
+        assert abs(np.linalg.norm(r) - 1) < 1e-14
+        s[j] = r @ kh
+        # s = r kbar-hat (quaternion product) carries the isotropic direction
+        q0 = r[0] * kh[0] + r[1:] @ kh[1:]
+        qv = -r[0] * kh[1:] + kh[0] * r[1:] - np.cross(r[1:], -kh[1:])
+        assert q0 == pytest.approx(s[j], abs=1e-13)
+        perp[j] = qv / max(np.linalg.norm(qv), 1e-300)
+    x, cdf = s0_cdf(alpha)
+    emp = np.sort(s)
+    model = np.interp(emp, x, cdf)
+    ks = np.abs(model - (np.arange(1, n + 1) / n)).max()
+    assert ks < 1.63 / math.sqrt(n)  # 1% KS critical value
+    assert np.abs(perp.mean(axis=0)).max() < 0.06
+    np.testing.assert_allclose(np.diag(perp.T @ perp / n), 1 / 3, atol=0.04)
+
+
+def test_heatbath_zero_temperature_is_relaxation():
+    rng = np.random.default_rng(3)
+    for j in range(20):
+        k = rng.standard_normal(4)
+        st, r = oracle.heatbath_quaternion(k, 1e-9 * np.linalg.norm(k), j, 0, 0, 64, 9)
+        np.testing.assert_allclose(r, k / np.linalg.norm(k), atol=1e-3)
+
+
+def test_heatbath_rejection_cap_reported():
+    dims = (4, 4, 4, 4)
+    U = field(dims, seed=91, gseed=92)
+    W = U.copy()
+    fails = oracle.sa_half_sweep(W, 0, 0.05, 0, 5, 0, cap=1)
+    assert fails > 0
+    fails = oracle.sa_half_sweep(U, 0, 0.05, 0, 5, 0, cap=64)
+    assert fails == 0
+
+
+def test_anneal_is_gauge_transformation():
+    dims = (4, 4, 4, 4)
+    for gauge in (0, 1):
+        U = field(dims, seed=93, gseed=94)
+        P = oracle.plaquette(U)
+        assert oracle.anneal(U, gauge, 1.45, 0.01, 30, 77) == 0
+        assert oracle.plaquette(U) == pytest.approx(P, abs=1e-13)
+        assert unitarity_error(U) < 1e-13
+
+
+def test_haar_generator_moments():
+    M = synth.haar_su3((40_000,), 3)
+    tr = torch.diagonal(M, dim1=-2, dim2=-1).sum(-1)
+    assert abs(tr.mean().item()) < 0.02
+    assert (tr.abs() ** 2).mean().item() == pytest.approx(1.0, abs=0.03)
