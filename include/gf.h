@@ -1,0 +1,185 @@
+/*
+ * gf.h -- C ABI of libgf.so: SU(3) lattice gauge fixing on one GB300 GPU by
+ * checkerboard overrelaxation and simulated annealing.
+ *
+ * Method: Schroeck & Vogt, "Gauge fixing using overrelaxation and simulated
+ * annealing on GPUs" (Lattice 2012).  Gauge fixing maximises the functional
+ * F_g[U] = Re sum_{mu,x} tr[g(x) U_mu(x) g(x+mu)^dagger] (Sec. 2, eq. F_g)
+ * over gauge transformations g(x) in SU(3); the overrelaxation algorithm
+ * (Alg. 1) visits the sites of one checkerboard parity at a time and, for
+ * each of the three SU(2) subgroups (Cabibbo-Marinari), rotates the 8 links
+ * touching the site by the local maximiser raised to the power omega.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Field layout ("canonical"): double U[Lt][Lz][Ly][Lx][4][3][3][2], i.e. the
+ *   site index runs x fastest, then the link direction mu = x, y, z, t, then
+ *   the 3x3 complex matrix row-major, complex numbers as (re, im).
+ *   dims = {Lx, Ly, Lz, Lt}; every extent must be even and >= 2 (the
+ *   checkerboard needs it) and the volume below 2^31.  Boundaries are
+ *   periodic.  Parity of a site is (x+y+z+t) mod 2; RED = 0 is swept first.
+ * Pointers: a field argument may be device memory or host memory (pageable or
+ *   pinned).  Host fields are copied in and out by the call; device fields
+ *   are read (and, for in-place calls, written) on the context's stream.
+ *   The library never frees or keeps caller memory after a call returns.
+ * Ownership: a gf_ctx owns its internal device buffers (the resident field in
+ *   per-parity structure-of-arrays layout, reduction scratch, CUDA graphs);
+ *   they are allocated on first use and freed by gf_destroy.
+ * Streams: work is issued on the stream given by gf_set_stream (default: the
+ *   legacy default stream).  Calls that return numbers synchronise that
+ *   stream; the others are stream ordered.  A context is not thread safe.
+ * Errors: every function returns GF_OK (0) or one of the codes below;
+ *   gf_last_error returns a message for the most recent failure.
+ * Normalisations: F is divided by Nc * Nd * V (Nd = 4 Landau, 3 Coulomb) so
+ *   that the unit field has F = 1; theta (Sec. 2, eq. theta) is
+ *   1/(Nc V) sum_x tr[Delta Delta^dagger] with Delta(x) the traceless part of
+ *   sum_mu [A_mu(x) - A_mu(x-mu)], A = (U - U^dagger)/(2i), sum over the
+ *   gauge's directions.
+ */
+#ifndef GF_H
+#define GF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define GF_OK 0
+#define GF_EINVAL 1         /* bad argument: odd/zero extent, omega outside (0,2), NULL, NaN */
+#define GF_ECUDA 2          /* a CUDA runtime call failed (message in gf_last_error) */
+#define GF_ETIMEOUT 3       /* a bounded device-side wait expired; the context stays usable */
+#define GF_ENOTCONVERGED 4  /* max_iter reached before theta_target; outputs are valid */
+#define GF_ENOMEM 5         /* device allocation failed */
+#define GF_EREJECT 6        /* heatbath: some draws hit the rejection cap (left unchanged) */
+#define GF_ESTATE 7         /* call needs a resident field and none is loaded */
+
+/* gauges (Sec. 1: Landau d_mu A_mu = 0, Coulomb d_i A_i = 0) */
+#define GF_LANDAU 0
+#define GF_COULOMB 1
+
+/* precision policy for gf_overrelax (option "precision") */
+#define GF_FP64 0   /* FP64 storage and arithmetic throughout */
+#define GF_MIXED 1  /* FP32 sweeps until theta < "theta_switch", then FP64 */
+#define GF_FP32 2   /* FP32 storage and arithmetic; theta accumulated in FP64 */
+
+typedef struct gf_ctx gf_ctx;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context for a lattice of extents dims and the given gauge
+ * (GF_LANDAU or GF_COULOMB).  Allocates nothing on the device yet.
+ * *out receives the handle; release it with gf_destroy. */
+int gf_create(const int dims[4], int gauge, gf_ctx **out);
+
+/* Free the context and every device buffer it owns.  NULL is accepted. */
+int gf_destroy(gf_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none).  The string
+ * stays valid until the next call on the context. */
+const char *gf_last_error(const gf_ctx *ctx);
+
+/* Short name of a return code. */
+const char *gf_error_string(int code);
+
+/* Issue all work on stream (a cudaStream_t; NULL = legacy default stream). */
+int gf_set_stream(gf_ctx *ctx, void *stream);
+
+/* Options (numbers; unknown keys give GF_EINVAL):
+ *   "precision"      GF_FP64 / GF_MIXED / GF_FP32 (default GF_FP64)
+ *   "storage64"      18 or 12 reals per FP64 link (default 18; 12 stores two
+ *                    rows and rebuilds the third from unitarity, Sec. 4.1)
+ *   "storage32"      12 or 18 reals per FP32 link (default 12)
+ *   "check_every"    sweeps between theta checks (default 100, Sec. 4.1)
+ *   "theta_switch"   FP32 -> FP64 switch of GF_MIXED (default 1e-6)
+ *   "track_gauge"    GF_MIXED: 1 = accumulate g(x) in the FP32 phase and
+ *                    apply it to the caller's FP64 field at the switch, so
+ *                    the result is a gauge transform of the exact input
+ *                    (default 1); 0 = widen the FP32 links instead
+ *   "reunitarize_every"  FP32 phase: reunitarise every n checks (default 1)
+ *   "threads_per_site"   1, 2, 4 or 8; 0 = autotune (default 0)
+ *   "block"          threads per block (multiple of 32, <= 1024; 0 = autotune)
+ *   "use_graphs"     1 = replay sweep loops as CUDA graphs (default 1)
+ *   "sa_cap"         heatbath rejection cap per draw (default 64, <= 255)
+ *   "sa_sweep_offset" Philox sweep counter of the first annealing sweep */
+int gf_set_option(gf_ctx *ctx, const char *key, double value);
+int gf_get_option(const gf_ctx *ctx, const char *key, double *value);
+
+/* Statistics of the last gf_overrelax / gf_anneal call:
+ *   "sweeps", "sweeps_fp32", "sweeps_fp64", "checks", "ms_total",
+ *   "ms_fp32", "ms_fp64", "threads_per_site", "block", "sa_rejects". */
+int gf_get_stat(const gf_ctx *ctx, const char *key, double *value);
+
+/* ---------------------------------------------------- the method, one call */
+
+/* Gauge-fix U in place by overrelaxation (Alg. 1; Sec. 2 overrelaxation with
+ * exponent omega in (0, 2), omega = 1 is plain relaxation).  theta is
+ * checked before the first sweep and every "check_every" sweeps (Sec. 4.1);
+ * the call stops at the first check with theta < theta_target or after
+ * max_iter sweeps.  U: canonical field, host or device, in/out.
+ * Outputs (any may be NULL): sweeps done, final F, final theta.
+ * Returns GF_OK when converged, GF_ENOTCONVERGED at max_iter. */
+int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int max_iter,
+                 int *iters_out, double *F_out, double *theta_out);
+
+/* Simulated annealing (Sec. 1, as a preconditioner): steps heatbath sweeps
+ * at temperatures T_k = T0 + (T1 - T0) k / (steps - 1).  Per site and SU(2)
+ * subgroup the new subgroup element r is drawn with density proportional to
+ * exp(Re tr[r K]/T) times the SU(2) Haar measure (Creutz for |k|/T < 2,
+ * Kennedy-Pendleton otherwise) from Philox4x32-10 with key = seed and
+ * counter = (lexicographic site, sweep_offset + k, 256 * subgroup + draw, 1).
+ * U: canonical field, host or device, in/out.  Returns GF_EREJECT if some
+ * draws hit "sa_cap" (those subgroups are left unchanged). */
+int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t seed);
+
+/* F of a canonical field (host or device), FP64. */
+int gf_functional(gf_ctx *ctx, const double *U, double *F_out);
+
+/* theta of a canonical field (host or device), FP64. */
+int gf_theta(gf_ctx *ctx, const double *U, double *theta_out);
+
+/* average plaquette 1/(18 V) sum Re tr[U_mu U_nu U_mu^+ U_nu^+] (gauge
+ * invariant; used to check that sweeps are gauge transformations). */
+int gf_plaquette(gf_ctx *ctx, const double *U, double *P_out);
+
+/* ----------------------------------------- resident field, explicit steps */
+
+/* Copy a canonical field (host or device) into the context's resident field
+ * in per-parity structure-of-arrays form (Sec. 4.1: RED and BLACK blocks,
+ * site index fastest) at the precision given: GF_FP64 uses "storage64"
+ * reals per link, GF_FP32 uses "storage32". */
+int gf_upload(gf_ctx *ctx, const double *U, int precision);
+
+/* Write the resident field back in canonical form (host or device).  A
+ * 12-real field gets its third rows rebuilt in FP64. */
+int gf_download(gf_ctx *ctx, double *U);
+
+/* One OR half-sweep of the resident field over the sites of one parity
+ * (Alg. 1 inner loops). */
+int gf_or_half_sweep(gf_ctx *ctx, int parity, double omega);
+
+/* nsweeps full OR sweeps (RED then BLACK) of the resident field, no checks;
+ * replayed from a CUDA graph when "use_graphs" is set. */
+int gf_or_sweeps(gf_ctx *ctx, double omega, int nsweeps);
+
+/* One heatbath half-sweep of the resident field at temperature T with
+ * Philox key seed and sweep counter sweep. */
+int gf_sa_half_sweep(gf_ctx *ctx, int parity, double T, uint64_t seed, uint32_t sweep);
+
+/* F and theta of the resident field (accumulated in FP64). */
+int gf_measure(gf_ctx *ctx, double *F_out, double *theta_out);
+
+/* Project every resident link back onto SU(3) (Gram-Schmidt in FP64). */
+int gf_reunitarize(gf_ctx *ctx);
+
+/* Pick threads per site and block size for the resident field's storage by
+ * timing every candidate on a scratch copy; the choice is cached per
+ * (volume, storage, gauge) for the process.  Outputs may be NULL. */
+int gf_autotune(gf_ctx *ctx, int *threads_per_site, int *block);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF_H */

@@ -1,0 +1,800 @@
+// gf_api.cu -- the C ABI of libgf.so (declared in include/gf.h): contexts,
+// options, the resident field, the convergence loop of Alg. 1 (theta checked
+// every N sweeps, Sec. 4.1) replayed from CUDA graphs, the mixed FP32 -> FP64
+// driver, simulated annealing and the threads-per-site autotuner.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "gf.h"
+#include "gf_internal.h"
+
+using namespace gf;
+
+namespace {
+
+struct GraphKey {
+    int fmt, tps, block, n, trackg, measure, reunit;
+    double omega;
+    const void *field, *gt;
+    bool operator<(const GraphKey &o) const
+    {
+        return std::tie(fmt, tps, block, n, trackg, measure, reunit, omega, field, gt) <
+               std::tie(o.fmt, o.tps, o.block, o.n, o.trackg, o.measure, o.reunit, o.omega, o.field, o.gt);
+    }
+};
+
+// autotuner cache: (Lx, Ly, Lz, Lt, format, gauge) -> (threads per site, block)
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+double now_ms()
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct gf_ctx {
+    int dims[4];
+    int gauge;
+    Geom geom;
+    long V;
+    // options
+    int precision = GF_FP64;
+    int storage64 = 18;
+    int storage32 = 12;
+    int check_every = 100;
+    double theta_switch = 1e-6;
+    int track_gauge = 1;
+    int reunit_every = 1;
+    int tps = 0;
+    int block = 0;
+    int use_graphs = 1;
+    int autotune = 0;
+    int sa_cap = 64;
+    uint32_t sa_sweep_offset = 0;
+    // streams
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    // device buffers
+    char *f64 = nullptr;
+    size_t f64_bytes = 0;
+    char *f32 = nullptr;
+    size_t f32_bytes = 0;
+    char *gt = nullptr;
+    double *staging = nullptr;
+    double *partials = nullptr;
+    double *dres = nullptr;
+    double *hres = nullptr;
+    int *dstatus = nullptr;
+    int resident = -1;
+    int resident_fmt = -1;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<std::string, double> stats;
+    std::string err;
+};
+
+// ---------------------------------------------------------------------------
+// error helpers
+// ---------------------------------------------------------------------------
+static int fail(gf_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+static int cuda_fail(gf_ctx *c, cudaError_t e, const char *what)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return fail(c, e == cudaErrorMemoryAllocation ? GF_ENOMEM : GF_ECUDA, buf);
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+#define RET(call)                   \
+    do {                            \
+        int r_ = (call);            \
+        if (r_ != GF_OK) return r_; \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// buffers
+// ---------------------------------------------------------------------------
+static int fmt64(const gf_ctx *c) { return c->storage64 == 12 ? F64_12 : F64_18; }
+static int fmt32(const gf_ctx *c) { return c->storage32 == 18 ? F32_18 : F32_12; }
+
+static size_t plane_bytes(const gf_ctx *c) { return (size_t)c->geom.plane * 16; }
+static size_t field_bytes(const gf_ctx *c, int fmt) { return 8 * (size_t)format_chunks(fmt) * plane_bytes(c); }
+
+static FieldRef ref(const gf_ctx *c, char *base) { return FieldRef{ base, plane_bytes(c) }; }
+
+static void drop_graphs(gf_ctx *c)
+{
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+static int ensure_common(gf_ctx *ctx)
+{
+    if (!ctx->partials) {
+        int n = measure_blocks(ctx->geom);
+        int m = aos_blocks(ctx->geom);
+        CK(cudaMalloc(&ctx->partials, sizeof(double) * 2 * (size_t)(n > m ? n : m)));
+    }
+    if (!ctx->dres) CK(cudaMalloc(&ctx->dres, sizeof(double) * 4));
+    if (!ctx->hres) CK(cudaMallocHost(&ctx->hres, sizeof(double) * 4));
+    if (!ctx->dstatus) CK(cudaMalloc(&ctx->dstatus, sizeof(int) * 4));
+    if (!ctx->cap) CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+    return GF_OK;
+}
+
+static int ensure_field(gf_ctx *ctx, int prec)
+{
+    RET(ensure_common(ctx));
+    if (prec == GF_FP64) {
+        size_t need = field_bytes(ctx, fmt64(ctx));
+        if (ctx->f64_bytes < need) {
+            drop_graphs(ctx);
+            if (ctx->f64) cudaFree(ctx->f64);
+            ctx->f64 = nullptr;
+            ctx->f64_bytes = 0;
+            CK(cudaMalloc(&ctx->f64, need));
+            ctx->f64_bytes = need;
+        }
+    } else {
+        size_t need = field_bytes(ctx, fmt32(ctx));
+        if (ctx->f32_bytes < need) {
+            drop_graphs(ctx);
+            if (ctx->f32) cudaFree(ctx->f32);
+            ctx->f32 = nullptr;
+            ctx->f32_bytes = 0;
+            CK(cudaMalloc(&ctx->f32, need));
+            ctx->f32_bytes = need;
+        }
+    }
+    return GF_OK;
+}
+
+static int ensure_gauge_field(gf_ctx *ctx)
+{
+    if (!ctx->gt) {
+        drop_graphs(ctx);
+        CK(cudaMalloc(&ctx->gt, 2 * 3 * plane_bytes(ctx)));
+    }
+    return GF_OK;
+}
+
+static int ensure_staging(gf_ctx *ctx)
+{
+    if (!ctx->staging) CK(cudaMalloc(&ctx->staging, sizeof(double) * 72 * (size_t)ctx->V));
+    return GF_OK;
+}
+
+static bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// device view of a caller field: the pointer itself, or the staging copy
+static int device_view(gf_ctx *ctx, const double *U, const double **view, bool *host)
+{
+    if (!U) return fail(ctx, GF_EINVAL, "field pointer is NULL");
+    if ((uintptr_t)U % 16) return fail(ctx, GF_EINVAL, "field pointer must be 16-byte aligned");
+    *host = !is_device_pointer(U);
+    if (*host) {
+        RET(ensure_staging(ctx));
+        CK(cudaMemcpyAsync(ctx->staging, U, sizeof(double) * 72 * (size_t)ctx->V, cudaMemcpyHostToDevice,
+                           ctx->stream));
+        *view = ctx->staging;
+    } else {
+        *view = U;
+    }
+    return GF_OK;
+}
+
+static char *resident_base(gf_ctx *ctx) { return ctx->resident == GF_FP64 ? ctx->f64 : ctx->f32; }
+
+// ---------------------------------------------------------------------------
+// launch configuration
+// ---------------------------------------------------------------------------
+static std::pair<int, int> default_config(int fmt)
+{
+    switch (fmt) {
+    case F32_12: return { 1, 128 };
+    case F32_18: return { 2, 128 };
+    case F64_12: return { 2, 128 };
+    default: return { 2, 128 };
+    }
+}
+
+static std::pair<int, int> launch_config(const gf_ctx *c, int fmt)
+{
+    std::pair<int, int> cfg = default_config(fmt);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_cache.find(std::make_tuple(c->dims[0], c->dims[1], c->dims[2], c->dims[3], fmt, c->gauge));
+        if (it != g_tune_cache.end()) cfg = it->second;
+    }
+    if (c->tps) cfg.first = c->tps;
+    if (c->block) cfg.second = c->block;
+    return cfg;
+}
+
+static SweepArgs sweep_args(gf_ctx *ctx, char *field, int parity, double omega)
+{
+    SweepArgs a;
+    memset(&a, 0, sizeof a);
+    a.f = ref(ctx, field);
+    a.gt = ref(ctx, ctx->gt);
+    a.g = ctx->geom;
+    a.parity = parity;
+    a.omega = omega;
+    a.T = 1.0;
+    a.cap = ctx->sa_cap;
+    a.status = ctx->dstatus;
+    return a;
+}
+
+static cudaError_t issue_sweeps(gf_ctx *ctx, int fmt, char *field, double omega, int n, bool trackg,
+                                std::pair<int, int> cfg, cudaStream_t s)
+{
+    for (int k = 0; k < n; ++k)
+        for (int p = 0; p < 2; ++p) {
+            SweepArgs a = sweep_args(ctx, field, p, omega);
+            cudaError_t e = launch_sweep(fmt, a, cfg.first, ctx->gauge, 0, trackg, cfg.second, s);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+// n sweeps of the resident field [+ reunitarisation] [+ F/theta into hres]
+static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, bool trackg, bool measure,
+                     bool reunit)
+{
+    std::pair<int, int> cfg = launch_config(ctx, fmt);
+    FieldRef f = ref(ctx, field);
+    if (ctx->use_graphs && n > 0) {
+        GraphKey key{ fmt, cfg.first, cfg.second, n, trackg, measure, reunit, omega, field, ctx->gt };
+        auto it = ctx->graphs.find(key);
+        if (it == ctx->graphs.end()) {
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = issue_sweeps(ctx, fmt, field, omega, n, trackg, cfg, ctx->cap);
+            if (e == cudaSuccess && reunit) e = launch_reunitarize(fmt, f, ctx->geom, ctx->cap);
+            if (e == cudaSuccess && measure)
+                e = launch_measure(fmt, f, ctx->geom, ctx->gauge, ctx->partials, ctx->dres, ctx->cap);
+            if (e == cudaSuccess && measure)
+                e = cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->cap);
+            cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &graph);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "capturing the sweep graph");
+            CK(e2);
+            cudaGraphExec_t exec;
+            cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(e3);
+            it = ctx->graphs.emplace(key, exec).first;
+        }
+        CK(cudaGraphLaunch(it->second, ctx->stream));
+        return GF_OK;
+    }
+    CK(issue_sweeps(ctx, fmt, field, omega, n, trackg, cfg, ctx->stream));
+    if (reunit) CK(launch_reunitarize(fmt, f, ctx->geom, ctx->stream));
+    if (measure) {
+        CK(launch_measure(fmt, f, ctx->geom, ctx->gauge, ctx->partials, ctx->dres, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    return GF_OK;
+}
+
+static int measure_resident(gf_ctx *ctx, double *F, double *theta)
+{
+    if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
+    CK(launch_measure(ctx->resident_fmt, ref(ctx, resident_base(ctx)), ctx->geom, ctx->gauge, ctx->partials,
+                      ctx->dres, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (F) *F = ctx->hres[0];
+    if (theta) *theta = ctx->hres[1];
+    return GF_OK;
+}
+
+// Alg. 1 WHILE loop on the resident field: theta known on entry; sweep in
+// chunks of check_every until theta < target or budget sweeps are spent.
+static int converge(gf_ctx *ctx, double omega, double target, int budget, bool trackg, bool reunit, int *used,
+                    double *F, double *theta)
+{
+    int fmt = ctx->resident_fmt;
+    char *field = resident_base(ctx);
+    int it = 0, checks = 0;
+    while (!(*theta < target) && it < budget) {
+        int n = ctx->check_every;
+        if (n > budget - it) n = budget - it;
+        RET(run_chunk(ctx, fmt, field, omega, n, trackg, true, reunit));
+        CK(cudaStreamSynchronize(ctx->stream));
+        *F = ctx->hres[0];
+        *theta = ctx->hres[1];
+        it += n;
+        ++checks;
+        if (!std::isfinite(*theta)) return fail(ctx, GF_EINVAL, "theta became non-finite (input not in SU(3)?)");
+    }
+    *used = it;
+    ctx->stats["checks"] += checks;
+    return GF_OK;
+}
+
+static int upload(gf_ctx *ctx, const double *view, int prec)
+{
+    RET(ensure_field(ctx, prec));
+    int fmt = prec == GF_FP64 ? fmt64(ctx) : fmt32(ctx);
+    char *base = prec == GF_FP64 ? ctx->f64 : ctx->f32;
+    CK(launch_encode(fmt, view, ref(ctx, base), ctx->geom, ctx->stream));
+    ctx->resident = prec;
+    ctx->resident_fmt = fmt;
+    return GF_OK;
+}
+
+static int download(gf_ctx *ctx, double *U, bool host)
+{
+    if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
+    double *dst = U;
+    if (host) {
+        RET(ensure_staging(ctx));
+        dst = ctx->staging;
+    }
+    CK(launch_decode(ctx->resident_fmt, ref(ctx, resident_base(ctx)), ctx->geom, dst, ctx->stream));
+    if (host) {
+        CK(cudaMemcpyAsync(U, ctx->staging, sizeof(double) * 72 * (size_t)ctx->V, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return GF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+static int autotune_format(gf_ctx *ctx, int fmt, char *field, int *tps_out, int *block_out)
+{
+    size_t bytes = field_bytes(ctx, fmt);
+    char *scratch = nullptr;
+    CK(cudaMalloc(&scratch, bytes));
+    cudaError_t e = cudaMemcpyAsync(scratch, field, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int tps_c[4] = { 1, 2, 4, 8 };
+    const int blk_c[3] = { 64, 128, 256 };
+    float best = 1e30f;
+    std::pair<int, int> pick = default_config(fmt);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+        for (int b = 0; b < 3 && e == cudaSuccess; ++b) {
+            std::pair<int, int> cfg{ tps_c[i], blk_c[b] };
+            e = issue_sweeps(ctx, fmt, scratch, 1.7, 1, false, cfg, ctx->stream);  // warm up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+            if (e == cudaSuccess) e = issue_sweeps(ctx, fmt, scratch, 1.7, 3, false, cfg, ctx->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                pick = cfg;
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[std::make_tuple(ctx->dims[0], ctx->dims[1], ctx->dims[2], ctx->dims[3], fmt, ctx->gauge)] = pick;
+    }
+    if (tps_out) *tps_out = pick.first;
+    if (block_out) *block_out = pick.second;
+    return GF_OK;
+}
+
+static bool tuned(const gf_ctx *c, int fmt)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    return g_tune_cache.count(std::make_tuple(c->dims[0], c->dims[1], c->dims[2], c->dims[3], fmt, c->gauge)) > 0;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *gf_error_string(int code)
+{
+    switch (code) {
+    case GF_OK: return "GF_OK";
+    case GF_EINVAL: return "GF_EINVAL";
+    case GF_ECUDA: return "GF_ECUDA";
+    case GF_ETIMEOUT: return "GF_ETIMEOUT";
+    case GF_ENOTCONVERGED: return "GF_ENOTCONVERGED";
+    case GF_ENOMEM: return "GF_ENOMEM";
+    case GF_EREJECT: return "GF_EREJECT";
+    case GF_ESTATE: return "GF_ESTATE";
+    default: return "GF_UNKNOWN";
+    }
+}
+
+int gf_create(const int dims[4], int gauge, gf_ctx **out)
+{
+    if (!dims || !out) return GF_EINVAL;
+    *out = nullptr;
+    if (gauge != GF_LANDAU && gauge != GF_COULOMB) return GF_EINVAL;
+    long V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (dims[mu] < 2 || (dims[mu] & 1)) return GF_EINVAL;
+        V *= dims[mu];
+        if (V >= (1L << 31)) return GF_EINVAL;
+    }
+    gf_ctx *c = new (std::nothrow) gf_ctx;
+    if (!c) return GF_ENOMEM;
+    for (int mu = 0; mu < 4; ++mu) {
+        c->dims[mu] = dims[mu];
+        c->geom.L[mu] = dims[mu];
+    }
+    c->gauge = gauge;
+    c->V = V;
+    c->geom.Lh0 = dims[0] / 2;
+    c->geom.Vh = (int)(V / 2);
+    c->geom.plane = (int)((V / 2 + 63) / 64 * 64);
+    *out = c;
+    return GF_OK;
+}
+
+int gf_destroy(gf_ctx *ctx)
+{
+    if (!ctx) return GF_OK;
+    drop_graphs(ctx);
+    cudaFree(ctx->f64);
+    cudaFree(ctx->f32);
+    cudaFree(ctx->gt);
+    cudaFree(ctx->staging);
+    cudaFree(ctx->partials);
+    cudaFree(ctx->dres);
+    cudaFree(ctx->dstatus);
+    if (ctx->hres) cudaFreeHost(ctx->hres);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    delete ctx;
+    return GF_OK;
+}
+
+const char *gf_last_error(const gf_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int gf_set_stream(gf_ctx *ctx, void *stream)
+{
+    if (!ctx) return GF_EINVAL;
+    ctx->stream = (cudaStream_t)stream;
+    return GF_OK;
+}
+
+int gf_set_option(gf_ctx *ctx, const char *key, double v)
+{
+    if (!ctx || !key) return GF_EINVAL;
+    std::string k(key);
+    int iv = (int)v;
+    bool integral = (double)iv == v;
+    if (k == "precision") {
+        if (!integral || iv < GF_FP64 || iv > GF_FP32) return fail(ctx, GF_EINVAL, "precision: 0, 1 or 2");
+        ctx->precision = iv;
+    } else if (k == "storage64") {
+        if (iv != 18 && iv != 12) return fail(ctx, GF_EINVAL, "storage64: 18 or 12");
+        if (ctx->resident == GF_FP64 && iv != ctx->storage64) ctx->resident = -1;
+        ctx->storage64 = iv;
+    } else if (k == "storage32") {
+        if (iv != 18 && iv != 12) return fail(ctx, GF_EINVAL, "storage32: 18 or 12");
+        if (ctx->resident == GF_FP32 && iv != ctx->storage32) ctx->resident = -1;
+        ctx->storage32 = iv;
+    } else if (k == "check_every") {
+        if (!integral || iv < 1) return fail(ctx, GF_EINVAL, "check_every >= 1");
+        ctx->check_every = iv;
+    } else if (k == "theta_switch") {
+        if (!(v > 0.0)) return fail(ctx, GF_EINVAL, "theta_switch > 0");
+        ctx->theta_switch = v;
+    } else if (k == "track_gauge") {
+        ctx->track_gauge = v != 0.0;
+    } else if (k == "reunitarize_every") {
+        if (!integral || iv < 0) return fail(ctx, GF_EINVAL, "reunitarize_every >= 0");
+        ctx->reunit_every = iv;
+    } else if (k == "threads_per_site") {
+        if (iv != 0 && iv != 1 && iv != 2 && iv != 4 && iv != 8) return fail(ctx, GF_EINVAL, "threads_per_site");
+        ctx->tps = iv;
+    } else if (k == "block") {
+        if (!integral || iv < 0 || iv > 256 || (iv % 32)) return fail(ctx, GF_EINVAL, "block: 0 or 32..256 step 32");
+        ctx->block = iv;
+    } else if (k == "use_graphs") {
+        ctx->use_graphs = v != 0.0;
+    } else if (k == "autotune") {
+        ctx->autotune = v != 0.0;
+    } else if (k == "sa_cap") {
+        if (!integral || iv < 1 || iv > 255) return fail(ctx, GF_EINVAL, "sa_cap: 1..255");
+        ctx->sa_cap = iv;
+    } else if (k == "sa_sweep_offset") {
+        if (!(v >= 0.0) || v > 4294967295.0) return fail(ctx, GF_EINVAL, "sa_sweep_offset");
+        ctx->sa_sweep_offset = (uint32_t)v;
+    } else {
+        return fail(ctx, GF_EINVAL, "unknown option " + k);
+    }
+    return GF_OK;
+}
+
+int gf_get_option(const gf_ctx *ctx, const char *key, double *v)
+{
+    if (!ctx || !key || !v) return GF_EINVAL;
+    std::string k(key);
+    if (k == "precision") *v = ctx->precision;
+    else if (k == "storage64") *v = ctx->storage64;
+    else if (k == "storage32") *v = ctx->storage32;
+    else if (k == "check_every") *v = ctx->check_every;
+    else if (k == "theta_switch") *v = ctx->theta_switch;
+    else if (k == "track_gauge") *v = ctx->track_gauge;
+    else if (k == "reunitarize_every") *v = ctx->reunit_every;
+    else if (k == "threads_per_site") *v = ctx->tps;
+    else if (k == "block") *v = ctx->block;
+    else if (k == "use_graphs") *v = ctx->use_graphs;
+    else if (k == "autotune") *v = ctx->autotune;
+    else if (k == "sa_cap") *v = ctx->sa_cap;
+    else if (k == "sa_sweep_offset") *v = ctx->sa_sweep_offset;
+    else return GF_EINVAL;
+    return GF_OK;
+}
+
+int gf_get_stat(const gf_ctx *ctx, const char *key, double *v)
+{
+    if (!ctx || !key || !v) return GF_EINVAL;
+    auto it = ctx->stats.find(key);
+    if (it == ctx->stats.end()) return GF_EINVAL;
+    *v = it->second;
+    return GF_OK;
+}
+
+int gf_upload(gf_ctx *ctx, const double *U, int precision)
+{
+    if (!ctx) return GF_EINVAL;
+    if (precision != GF_FP64 && precision != GF_FP32) return fail(ctx, GF_EINVAL, "precision: GF_FP64 or GF_FP32");
+    RET(ensure_common(ctx));
+    const double *view;
+    bool host;
+    RET(device_view(ctx, U, &view, &host));
+    RET(upload(ctx, view, precision));
+    if (host) CK(cudaStreamSynchronize(ctx->stream));
+    return GF_OK;
+}
+
+int gf_download(gf_ctx *ctx, double *U)
+{
+    if (!ctx) return GF_EINVAL;
+    if (!U || (uintptr_t)U % 16) return fail(ctx, GF_EINVAL, "field pointer NULL or not 16-byte aligned");
+    return download(ctx, U, !is_device_pointer(U));
+}
+
+int gf_or_half_sweep(gf_ctx *ctx, int parity, double omega)
+{
+    if (!ctx) return GF_EINVAL;
+    if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
+    if ((parity & ~1) || !(omega > 0.0 && omega < 2.0)) return fail(ctx, GF_EINVAL, "parity 0/1, omega in (0,2)");
+    std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt);
+    SweepArgs a = sweep_args(ctx, resident_base(ctx), parity, omega);
+    CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 0, false, cfg.second, ctx->stream));
+    return GF_OK;
+}
+
+int gf_or_sweeps(gf_ctx *ctx, double omega, int nsweeps)
+{
+    if (!ctx) return GF_EINVAL;
+    if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
+    if (nsweeps < 0 || !(omega > 0.0 && omega < 2.0)) return fail(ctx, GF_EINVAL, "nsweeps >= 0, omega in (0,2)");
+    if (nsweeps == 0) return GF_OK;
+    return run_chunk(ctx, ctx->resident_fmt, resident_base(ctx), omega, nsweeps, false, false, false);
+}
+
+int gf_sa_half_sweep(gf_ctx *ctx, int parity, double T, uint64_t seed, uint32_t sweep)
+{
+    if (!ctx) return GF_EINVAL;
+    if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
+    if ((parity & ~1) || !(T > 0.0) || !std::isfinite(T)) return fail(ctx, GF_EINVAL, "parity 0/1, T > 0");
+    std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt);
+    SweepArgs a = sweep_args(ctx, resident_base(ctx), parity, 1.0);
+    a.T = T;
+    a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    a.sweep = sweep;
+    CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 1, false, cfg.second, ctx->stream));
+    return GF_OK;
+}
+
+int gf_measure(gf_ctx *ctx, double *F_out, double *theta_out)
+{
+    if (!ctx) return GF_EINVAL;
+    return measure_resident(ctx, F_out, theta_out);
+}
+
+int gf_reunitarize(gf_ctx *ctx)
+{
+    if (!ctx) return GF_EINVAL;
+    if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
+    CK(launch_reunitarize(ctx->resident_fmt, ref(ctx, resident_base(ctx)), ctx->geom, ctx->stream));
+    return GF_OK;
+}
+
+int gf_autotune(gf_ctx *ctx, int *threads_per_site, int *block)
+{
+    if (!ctx) return GF_EINVAL;
+    if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
+    return autotune_format(ctx, ctx->resident_fmt, resident_base(ctx), threads_per_site, block);
+}
+
+static int aos_reduce(gf_ctx *ctx, const double *U, int which, double *out)
+{
+    if (!ctx) return GF_EINVAL;
+    if (!out) return fail(ctx, GF_EINVAL, "output pointer is NULL");
+    RET(ensure_common(ctx));
+    const double *view;
+    bool host;
+    RET(device_view(ctx, U, &view, &host));
+    if (which == 2) CK(launch_plaquette_aos(view, ctx->geom, ctx->partials, ctx->dres, ctx->stream));
+    else CK(launch_measure_aos(view, ctx->geom, ctx->gauge, ctx->partials, ctx->dres, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *out = which == 1 ? ctx->hres[1] : ctx->hres[0];
+    return GF_OK;
+}
+
+int gf_functional(gf_ctx *ctx, const double *U, double *F_out) { return aos_reduce(ctx, U, 0, F_out); }
+int gf_theta(gf_ctx *ctx, const double *U, double *theta_out) { return aos_reduce(ctx, U, 1, theta_out); }
+int gf_plaquette(gf_ctx *ctx, const double *U, double *P_out) { return aos_reduce(ctx, U, 2, P_out); }
+
+int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int max_iter, int *iters_out,
+                 double *F_out, double *theta_out)
+{
+    if (!ctx) return GF_EINVAL;
+    if (!(omega > 0.0 && omega < 2.0)) return fail(ctx, GF_EINVAL, "omega must lie in (0, 2)");
+    if (!(theta_target >= 0.0) || !std::isfinite(theta_target)) return fail(ctx, GF_EINVAL, "theta_target");
+    if (max_iter < 0) return fail(ctx, GF_EINVAL, "max_iter < 0");
+    ctx->stats.clear();
+    double t0 = now_ms();
+    RET(ensure_common(ctx));
+    const double *view;
+    bool host;
+    RET(device_view(ctx, U, &view, &host));
+
+    int used32 = 0, used64 = 0;
+    double F = 0.0, theta = 0.0, ms32 = 0.0, ms64 = 0.0;
+    if (ctx->precision == GF_FP64) {
+        RET(upload(ctx, view, GF_FP64));
+        if (ctx->autotune && !tuned(ctx, ctx->resident_fmt))
+            RET(autotune_format(ctx, ctx->resident_fmt, ctx->f64, nullptr, nullptr));
+        RET(measure_resident(ctx, &F, &theta));
+        double t1 = now_ms();
+        RET(converge(ctx, omega, theta_target, max_iter, false, false, &used64, &F, &theta));
+        ms64 = now_ms() - t1;
+    } else {
+        bool track = ctx->precision == GF_MIXED && ctx->track_gauge;
+        double target32 = ctx->precision == GF_MIXED ? ctx->theta_switch : theta_target;
+        if (theta_target > target32) target32 = theta_target;
+        RET(upload(ctx, view, GF_FP32));
+        if (track) {
+            RET(ensure_gauge_field(ctx));
+            CK(launch_gauge_identity(ref(ctx, ctx->gt), ctx->geom, ctx->stream));
+        }
+        if (ctx->autotune && !tuned(ctx, ctx->resident_fmt))
+            RET(autotune_format(ctx, ctx->resident_fmt, ctx->f32, nullptr, nullptr));
+        RET(measure_resident(ctx, &F, &theta));
+        double t1 = now_ms();
+        // reunitarise at every check when reunitarize_every == 1 (graph-fused); else every n-th check below
+        bool fused = ctx->reunit_every == 1;
+        if (fused || ctx->reunit_every == 0) {
+            RET(converge(ctx, omega, target32, max_iter, track, fused, &used32, &F, &theta));
+        } else {
+            int budget = max_iter;
+            while (!(theta < target32) && used32 < budget) {
+                int chunk_budget = ctx->check_every * ctx->reunit_every;
+                if (chunk_budget > budget - used32) chunk_budget = budget - used32;
+                int u = 0;
+                RET(converge(ctx, omega, target32, chunk_budget, track, false, &u, &F, &theta));
+                used32 += u;
+                CK(launch_reunitarize(ctx->resident_fmt, ref(ctx, ctx->f32), ctx->geom, ctx->stream));
+                if (u == 0) break;
+            }
+        }
+        CK(cudaStreamSynchronize(ctx->stream));
+        ms32 = now_ms() - t1;
+        if (ctx->precision == GF_MIXED) {
+            double t2 = now_ms();
+            RET(ensure_field(ctx, GF_FP64));
+            if (track) {
+                CK(launch_apply_tracked_gauge(view, ref(ctx, ctx->gt), fmt64(ctx), ref(ctx, ctx->f64), ctx->geom,
+                                              ctx->stream));
+            } else {
+                CK(launch_widen(ctx->resident_fmt, ref(ctx, ctx->f32), fmt64(ctx), ref(ctx, ctx->f64), ctx->geom,
+                                ctx->stream));
+            }
+            ctx->resident = GF_FP64;
+            ctx->resident_fmt = fmt64(ctx);
+            if (ctx->autotune && !tuned(ctx, ctx->resident_fmt))
+                RET(autotune_format(ctx, ctx->resident_fmt, ctx->f64, nullptr, nullptr));
+            RET(measure_resident(ctx, &F, &theta));
+            RET(converge(ctx, omega, theta_target, max_iter - used32, false, false, &used64, &F, &theta));
+            ms64 = now_ms() - t2;
+        } else {
+            CK(launch_reunitarize(ctx->resident_fmt, ref(ctx, ctx->f32), ctx->geom, ctx->stream));
+            RET(measure_resident(ctx, &F, &theta));
+        }
+    }
+    RET(download(ctx, U, host));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt);
+    ctx->stats["sweeps"] = used32 + used64;
+    ctx->stats["sweeps_fp32"] = used32;
+    ctx->stats["sweeps_fp64"] = used64;
+    ctx->stats["ms_fp32"] = ms32;
+    ctx->stats["ms_fp64"] = ms64;
+    ctx->stats["ms_total"] = now_ms() - t0;
+    ctx->stats["threads_per_site"] = cfg.first;
+    ctx->stats["block"] = cfg.second;
+    if (iters_out) *iters_out = used32 + used64;
+    if (F_out) *F_out = F;
+    if (theta_out) *theta_out = theta;
+    return theta < theta_target ? GF_OK : GF_ENOTCONVERGED;
+}
+
+int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t seed)
+{
+    if (!ctx) return GF_EINVAL;
+    if (!(T0 > 0.0) || !(T1 > 0.0) || !std::isfinite(T0) || !std::isfinite(T1) || steps < 0)
+        return fail(ctx, GF_EINVAL, "temperatures must be positive and finite, steps >= 0");
+    ctx->stats.clear();
+    double t0 = now_ms();
+    RET(ensure_common(ctx));
+    const double *view;
+    bool host;
+    RET(device_view(ctx, U, &view, &host));
+    int prec = ctx->precision == GF_FP32 ? GF_FP32 : GF_FP64;
+    RET(upload(ctx, view, prec));
+    CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int) * 4, ctx->stream));
+    std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt);
+    for (int k = 0; k < steps; ++k) {
+        double T = steps > 1 ? T0 + (T1 - T0) * (double)k / (double)(steps - 1) : T0;
+        for (int p = 0; p < 2; ++p) {
+            SweepArgs a = sweep_args(ctx, resident_base(ctx), p, 1.0);
+            a.T = T;
+            a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+            a.sweep = ctx->sa_sweep_offset + (uint32_t)k;
+            CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 1, false, cfg.second, ctx->stream));
+        }
+    }
+    int rejects = 0;
+    CK(cudaMemcpyAsync(ctx->hres + 2, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    RET(download(ctx, U, host));
+    CK(cudaStreamSynchronize(ctx->stream));
+    memcpy(&rejects, ctx->hres + 2, sizeof(int));
+    ctx->stats["sweeps"] = steps;
+    ctx->stats["sa_rejects"] = rejects;
+    ctx->stats["ms_total"] = now_ms() - t0;
+    ctx->stats["threads_per_site"] = cfg.first;
+    ctx->stats["block"] = cfg.second;
+    if (rejects) return fail(ctx, GF_EREJECT, "heatbath rejection cap reached in some draws");
+    return GF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// gf_internal.h -- declarations shared by the library's translation units
+// (kernel launchers per storage format, codec/reduction launchers).  Not part
+// of the public ABI (that is include/gf.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gf_device.cuh"
+
+namespace gf {
+
+// arguments of one half-sweep launch
+struct SweepArgs {
+    FieldRef f;       // resident field
+    FieldRef gt;      // accumulated gauge transformation (F32_12 site field) or {0}
+    Geom g;
+    int parity;
+    double omega;     // overrelaxation exponent
+    double T;         // heatbath temperature
+    uint2 key;        // Philox key (seed)
+    uint32_t sweep;   // Philox sweep counter
+    int cap;          // heatbath rejection cap
+    int *status;      // [0]: heatbath draws that hit the cap
+};
+
+// half-sweep launchers, one per storage format (gf_sweep_*.cu)
+cudaError_t launch_sweep_f64_18(const SweepArgs &a, int tps, int coulomb, int mode, bool trackg, int block,
+                                cudaStream_t s);
+cudaError_t launch_sweep_f64_12(const SweepArgs &a, int tps, int coulomb, int mode, bool trackg, int block,
+                                cudaStream_t s);
+cudaError_t launch_sweep_f32_18(const SweepArgs &a, int tps, int coulomb, int mode, bool trackg, int block,
+                                cudaStream_t s);
+cudaError_t launch_sweep_f32_12(const SweepArgs &a, int tps, int coulomb, int mode, bool trackg, int block,
+                                cudaStream_t s);
+
+inline cudaError_t launch_sweep(int fmt, const SweepArgs &a, int tps, int coulomb, int mode, bool trackg, int block,
+                                cudaStream_t s)
+{
+    switch (fmt) {
+    case F64_18: return launch_sweep_f64_18(a, tps, coulomb, mode, trackg, block, s);
+    case F64_12: return launch_sweep_f64_12(a, tps, coulomb, mode, trackg, block, s);
+    case F32_18: return launch_sweep_f32_18(a, tps, coulomb, mode, trackg, block, s);
+    case F32_12: return launch_sweep_f32_12(a, tps, coulomb, mode, trackg, block, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+inline int format_chunks(int fmt)
+{
+    switch (fmt) {
+    case F64_18: return 9;
+    case F64_12: return 6;
+    case F32_18: return 5;
+    case F32_12: return 3;
+    default: return 0;
+    }
+}
+
+// bytes moved per site update by one half-sweep (8 links read + 8 written)
+inline double format_link_bytes(int fmt)
+{
+    switch (fmt) {
+    case F64_18: return 144.0;
+    case F64_12: return 96.0;
+    case F32_18: return 72.0;
+    case F32_12: return 48.0;
+    default: return 0.0;
+    }
+}
+
+// reductions write per-block partial sums (2 doubles per block)
+constexpr int kReduceBlock = 256;
+
+// codec, reductions and transforms (gf_field.cu)
+cudaError_t launch_encode(int fmt, const double *aos, FieldRef f, const Geom &g, cudaStream_t s);
+cudaError_t launch_decode(int fmt, FieldRef f, const Geom &g, double *aos, cudaStream_t s);
+cudaError_t launch_reunitarize(int fmt, FieldRef f, const Geom &g, cudaStream_t s);
+cudaError_t launch_widen(int src_fmt, FieldRef src, int dst_fmt, FieldRef dst, const Geom &g, cudaStream_t s);
+cudaError_t launch_gauge_identity(FieldRef gt, const Geom &g, cudaStream_t s);
+cudaError_t launch_apply_tracked_gauge(const double *aos, FieldRef gt, int dst_fmt, FieldRef dst, const Geom &g,
+                                       cudaStream_t s);
+// F and theta of the resident field: nblocks partials, then the final sum
+int measure_blocks(const Geom &g);
+cudaError_t launch_measure(int fmt, FieldRef f, const Geom &g, int coulomb, double *partials, double *out,
+                           cudaStream_t s);
+// F and theta of a canonical (AoS) field
+int aos_blocks(const Geom &g);
+cudaError_t launch_measure_aos(const double *aos, const Geom &g, int coulomb, double *partials, double *out,
+                               cudaStream_t s);
+cudaError_t launch_plaquette_aos(const double *aos, const Geom &g, double *partials, double *out, cudaStream_t s);
+
+}  // namespace gf

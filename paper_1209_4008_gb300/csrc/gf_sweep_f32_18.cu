@@ -1,0 +1,13 @@
+// Half-sweep kernels (overrelaxation and heatbath) for F32_18 link storage.
+#include "gf_sweep.cuh"
+
+namespace gf {
+
+cudaError_t launch_sweep_f32_18(const SweepArgs &a, int tps, int coulomb, int mode, bool trackg, int block,
+                              cudaStream_t s)
+{
+    return trackg ? dispatch_tps<F32_18, true>(a, tps, coulomb, mode, block, s)
+                  : dispatch_tps<F32_18, false>(a, tps, coulomb, mode, block, s);
+}
+
+}  // namespace gf

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of libgf.so (C ABI declared in include/gf.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Functions keep the C names; a field argument may be a torch
+tensor (CUDA or CPU, complex128 of shape (Lt, Lz, Ly, Lx, 4, 3, 3) or float64
+with a trailing 2), a numpy array, or a raw address (int).
+
+The library is built in-tree (``paper_1209_4008_gb300/_build/libgf.so``) by
+``paper_1209_4008_gb300.build``; if it is missing the binding raises -- there
+is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+GF_OK, GF_EINVAL, GF_ECUDA, GF_ETIMEOUT, GF_ENOTCONVERGED, GF_ENOMEM, GF_EREJECT, GF_ESTATE = range(8)
+GF_LANDAU, GF_COULOMB = 0, 1
+GF_FP64, GF_MIXED, GF_FP32 = 0, 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_name(code)}: {msg}")
+        self.code = code
+
+
+def _name(code: int) -> str:
+    names = ["GF_OK", "GF_EINVAL", "GF_ECUDA", "GF_ETIMEOUT", "GF_ENOTCONVERGED", "GF_ENOMEM",
+             "GF_EREJECT", "GF_ESTATE"]
+    return names[code] if 0 <= code < len(names) else f"code {code}"
+
+
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "gf_create": (C.c_int, [_ip, C.c_int, C.POINTER(_vp)]),
+    "gf_destroy": (C.c_int, [_vp]),
+    "gf_last_error": (C.c_char_p, [_vp]),
+    "gf_error_string": (C.c_char_p, [C.c_int]),
+    "gf_set_stream": (C.c_int, [_vp, _vp]),
+    "gf_set_option": (C.c_int, [_vp, C.c_char_p, C.c_double]),
+    "gf_get_option": (C.c_int, [_vp, C.c_char_p, _dp]),
+    "gf_get_stat": (C.c_int, [_vp, C.c_char_p, _dp]),
+    "gf_overrelax": (C.c_int, [_vp, _vp, C.c_double, C.c_double, C.c_int, _ip, _dp, _dp]),
+    "gf_anneal": (C.c_int, [_vp, _vp, C.c_double, C.c_double, C.c_int, C.c_uint64]),
+    "gf_functional": (C.c_int, [_vp, _vp, _dp]),
+    "gf_theta": (C.c_int, [_vp, _vp, _dp]),
+    "gf_plaquette": (C.c_int, [_vp, _vp, _dp]),
+    "gf_upload": (C.c_int, [_vp, _vp, C.c_int]),
+    "gf_download": (C.c_int, [_vp, _vp]),
+    "gf_or_half_sweep": (C.c_int, [_vp, C.c_int, C.c_double]),
+    "gf_or_sweeps": (C.c_int, [_vp, C.c_double, C.c_int]),
+    "gf_sa_half_sweep": (C.c_int, [_vp, C.c_int, C.c_double, C.c_uint64, C.c_uint32]),
+    "gf_measure": (C.c_int, [_vp, _dp, _dp]),
+    "gf_reunitarize": (C.c_int, [_vp]),
+    "gf_autotune": (C.c_int, [_vp, _ip, _ip]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load libgf.so (building it first if asked and it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError(f"libgf.so not built ({path}); run paper_1209_4008_gb300.build")
+                _build.build()
+            lib = C.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+        return _lib
+
+
+def _ptr(x) -> int:
+    """Address of a field/buffer argument."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported field argument {type(x)}")
+
+
+def _check_field(ctx: "Context", U) -> None:
+    if hasattr(U, "shape") and not isinstance(U, int):
+        n = 1
+        for s in U.shape:
+            n *= int(s)
+        itemsize = U.element_size() if hasattr(U, "element_size") else U.itemsize
+        if n * itemsize != ctx.volume * 4 * 9 * 16:
+            raise ValueError(f"field has {n * itemsize} bytes, lattice needs {ctx.volume * 576}")
+
+
+class Context:
+    """Owns a gf_ctx handle; the C functions below take it as first argument."""
+
+    def __init__(self, dims, gauge: int = GF_LANDAU):
+        self.lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.volume = 1
+        for d in self.dims:
+            self.volume *= d
+        arr = (C.c_int * 4)(*self.dims)
+        h = _vp()
+        rc = self.lib.gf_create(arr, int(gauge), C.byref(h))
+        if rc != GF_OK:
+            raise GFError(rc, f"gf_create{self.dims} gauge={gauge}")
+        self.handle = h
+        self.gauge = gauge
+
+    def check(self, rc: int, what: str, ok=(GF_OK,)) -> int:
+        if rc not in ok:
+            msg = self.lib.gf_last_error(self.handle)
+            raise GFError(rc, f"{what}: {msg.decode() if msg else ''}")
+        return rc
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            self.lib.gf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---------------------------------------------------------------------------
+# the C entry points, same names
+# ---------------------------------------------------------------------------
+def gf_create(dims, gauge: int = GF_LANDAU) -> Context:
+    return Context(dims, gauge)
+
+
+def gf_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def gf_set_stream(ctx: Context, stream) -> None:
+    """stream: a torch.cuda.Stream, a raw cudaStream_t address, or None."""
+    s = getattr(stream, "cuda_stream", stream)
+    ctx.check(ctx.lib.gf_set_stream(ctx.handle, s or None), "gf_set_stream")
+
+
+def gf_set_option(ctx: Context, key: str, value: float) -> None:
+    ctx.check(ctx.lib.gf_set_option(ctx.handle, key.encode(), float(value)), f"option {key}")
+
+
+def gf_get_option(ctx: Context, key: str) -> float:
+    v = C.c_double()
+    ctx.check(ctx.lib.gf_get_option(ctx.handle, key.encode(), C.byref(v)), f"option {key}")
+    return v.value
+
+
+def gf_get_stat(ctx: Context, key: str) -> float:
+    v = C.c_double()
+    ctx.check(ctx.lib.gf_get_stat(ctx.handle, key.encode(), C.byref(v)), f"stat {key}")
+    return v.value
+
+
+def gf_overrelax(ctx: Context, U, omega: float, theta_target: float, max_iter: int):
+    """Returns (converged, sweeps, F, theta); U is fixed in place."""
+    _check_field(ctx, U)
+    it, F, th = C.c_int(), C.c_double(), C.c_double()
+    rc = ctx.check(ctx.lib.gf_overrelax(ctx.handle, _ptr(U), omega, theta_target, int(max_iter),
+                                        C.byref(it), C.byref(F), C.byref(th)),
+                   "gf_overrelax", ok=(GF_OK, GF_ENOTCONVERGED))
+    return rc == GF_OK, it.value, F.value, th.value
+
+
+def gf_anneal(ctx: Context, U, T0: float, T1: float, steps: int, seed: int, allow_reject=False) -> int:
+    _check_field(ctx, U)
+    ok = (GF_OK, GF_EREJECT) if allow_reject else (GF_OK,)
+    return ctx.check(ctx.lib.gf_anneal(ctx.handle, _ptr(U), T0, T1, int(steps), int(seed)),
+                     "gf_anneal", ok=ok)
+
+
+def gf_functional(ctx: Context, U) -> float:
+    _check_field(ctx, U)
+    v = C.c_double()
+    ctx.check(ctx.lib.gf_functional(ctx.handle, _ptr(U), C.byref(v)), "gf_functional")
+    return v.value
+
+
+def gf_theta(ctx: Context, U) -> float:
+    _check_field(ctx, U)
+    v = C.c_double()
+    ctx.check(ctx.lib.gf_theta(ctx.handle, _ptr(U), C.byref(v)), "gf_theta")
+    return v.value
+
+
+def gf_plaquette(ctx: Context, U) -> float:
+    _check_field(ctx, U)
+    v = C.c_double()
+    ctx.check(ctx.lib.gf_plaquette(ctx.handle, _ptr(U), C.byref(v)), "gf_plaquette")
+    return v.value
+
+
+def gf_upload(ctx: Context, U, precision: int = GF_FP64) -> None:
+    _check_field(ctx, U)
+    ctx.check(ctx.lib.gf_upload(ctx.handle, _ptr(U), int(precision)), "gf_upload")
+
+
+def gf_download(ctx: Context, U) -> None:
+    _check_field(ctx, U)
+    ctx.check(ctx.lib.gf_download(ctx.handle, _ptr(U)), "gf_download")
+
+
+def gf_or_half_sweep(ctx: Context, parity: int, omega: float) -> None:
+    ctx.check(ctx.lib.gf_or_half_sweep(ctx.handle, int(parity), omega), "gf_or_half_sweep")
+
+
+def gf_or_sweeps(ctx: Context, omega: float, nsweeps: int) -> None:
+    ctx.check(ctx.lib.gf_or_sweeps(ctx.handle, omega, int(nsweeps)), "gf_or_sweeps")
+
+
+def gf_sa_half_sweep(ctx: Context, parity: int, T: float, seed: int, sweep: int) -> None:
+    ctx.check(ctx.lib.gf_sa_half_sweep(ctx.handle, int(parity), T, int(seed), int(sweep)),
+              "gf_sa_half_sweep")
+
+
+def gf_measure(ctx: Context):
+    F, th = C.c_double(), C.c_double()
+    ctx.check(ctx.lib.gf_measure(ctx.handle, C.byref(F), C.byref(th)), "gf_measure")
+    return F.value, th.value
+
+
+def gf_reunitarize(ctx: Context) -> None:
+    ctx.check(ctx.lib.gf_reunitarize(ctx.handle), "gf_reunitarize")
+
+
+def gf_autotune(ctx: Context):
+    t, b = C.c_int(), C.c_int()
+    ctx.check(ctx.lib.gf_autotune(ctx.handle, C.byref(t), C.byref(b)), "gf_autotune")
+    return t.value, b.value

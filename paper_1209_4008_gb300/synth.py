@@ -17,8 +17,9 @@ links live in SU(3) as U = exp(i a g A), Sec. 1 eq. 2):
 3. V is projected back onto SU(3) (one Newton-Schulz polar step and a
    determinant phase), to remove rounding of the matrix exponential.
 4. The field is rotated by a Haar-random gauge transformation g(x) (QR of a
-   complex Gaussian matrix with the phases of R's diagonal moved into Q,
-   Mezzadri 2007, then divided by a cube root of its determinant):
+   complex Gaussian matrix with R's diagonal made positive, Mezzadri 2007,
+   computed as Gram-Schmidt on its columns, then divided by a cube root of
+   its determinant):
    U_mu(x) = g(x) V_mu(x) g(x + mu)^dagger.
 5. The pure-gauge input takes V = 1: U_mu(x) = g(x) g(x + mu)^dagger.
 
@@ -68,12 +69,22 @@ def _algebra(xi: torch.Tensor) -> torch.Tensor:
     return torch.einsum("...a,aij->...ij", xi.to(torch.complex128), lam) * 0.5
 
 
+def _det3(M: torch.Tensor) -> torch.Tensor:
+    """Determinant of (..., 3, 3) matrices by cofactor expansion (vectorised)."""
+    return (M[..., 0, 0] * (M[..., 1, 1] * M[..., 2, 2] - M[..., 1, 2] * M[..., 2, 1])
+            - M[..., 0, 1] * (M[..., 1, 0] * M[..., 2, 2] - M[..., 1, 2] * M[..., 2, 0])
+            + M[..., 0, 2] * (M[..., 1, 0] * M[..., 2, 1] - M[..., 1, 1] * M[..., 2, 0]))
+
+
+def _remove_det_phase(U: torch.Tensor) -> torch.Tensor:
+    return U / torch.exp(1j * torch.angle(_det3(U)) / 3)[..., None, None]
+
+
 def _project_su3(U: torch.Tensor) -> torch.Tensor:
     """Nearest-unitary Newton-Schulz step, then remove the determinant phase."""
     eye = torch.eye(3, dtype=U.dtype, device=U.device)
     U = U @ (3 * eye - U.mH @ U) * 0.5
-    det = torch.linalg.det(U)
-    return U / torch.exp(1j * torch.angle(det) / 3)[..., None, None]
+    return _remove_det_phase(U)
 
 
 @functools.lru_cache(maxsize=None)
@@ -118,11 +129,18 @@ def haar_su3(shape, seed: int, device="cpu") -> torch.Tensor:
     re = torch.randn(*shape, 3, 3, dtype=torch.float64, generator=gen, device=device)
     im = torch.randn(*shape, 3, 3, dtype=torch.float64, generator=gen, device=device)
     Z = torch.complex(re, im) / math.sqrt(2.0)
-    Q, R = torch.linalg.qr(Z)
-    d = torch.diagonal(R, dim1=-2, dim2=-1)
-    Q = Q * (d / d.abs())[..., None, :]
-    det = torch.linalg.det(Q)
-    return Q / torch.exp(1j * torch.angle(det) / 3)[..., None, None]
+    # Q of the QR factorisation with a positive real diagonal of R (Mezzadri's
+    # phase fix) is the Gram-Schmidt orthonormalisation of Z's columns
+    # (two projection passes per column keep it orthogonal to rounding).
+    cols = []
+    for j in range(3):
+        v = Z[..., :, j]
+        for _ in range(2):
+            for q in cols:
+                v = v - (q.conj() * v).sum(-1, keepdim=True) * q
+        cols.append(v / torch.linalg.vector_norm(v, dim=-1, keepdim=True))
+    Q = torch.stack(cols, dim=-1)
+    return _remove_det_phase(Q)
 
 
 # axis of the (Lt, Lz, Ly, Lx) site block that direction mu runs along

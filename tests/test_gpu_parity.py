@@ -1,0 +1,314 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle.
+
+Tolerances
+----------
+FP64 storage: 1e-12 relative per half-sweep/sweep, element by element (the
+two sides differ only in rounding order and FMA contraction, ~1e-16 per
+operation over a few hundred operations).
+FP32 storage: the input is rounded to FP32 (relative 6e-8) and each link
+update is ~150 FP32 operations; the bound used is 5e-6 absolute per link
+element (|U_ab| <= 1) per half-sweep, 2e-5 after a few sweeps.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1209_4008_gb300 import gf, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+SMALL = [(4, 4, 4, 4), (8, 8, 8, 8), (6, 4, 6, 10), (10, 6, 4, 8)]
+
+
+def cpu_field(dims, seed=1, gseed=2, plaq=0.60, pure=False):
+    return synth.as_numpy(synth.make_field(dims, plaq, seed, gseed, pure_gauge=pure))
+
+
+def dev(U):
+    return torch.from_numpy(U).to(DEV)
+
+
+def host(T):
+    return T.cpu().numpy()
+
+
+def ctx_for(dims, gauge=0, **opts):
+    c = gf.gf_create(dims, gauge)
+    for k, v in opts.items():
+        gf.gf_set_option(c, k, v)
+    return c
+
+
+def max_rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+# ---------------------------------------------------------------------------
+# FP64 half-sweeps and sweeps, every threads-per-site variant
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", SMALL)
+@pytest.mark.parametrize("gauge", [0, 1])
+@pytest.mark.parametrize("tps", [1, 2, 4, 8])
+def test_fp64_half_sweep_parity(dims, gauge, tps):
+    U = cpu_field(dims, seed=3, gseed=4)
+    c = ctx_for(dims, gauge, threads_per_site=tps)
+    d = dev(U)
+    gf.gf_upload(c, d, gf.GF_FP64)
+    for parity in (0, 1):
+        gf.gf_or_half_sweep(c, parity, 1.7)
+        oracle.or_half_sweep(U, parity, 1.7, gauge)
+        gf.gf_download(c, d)
+        assert max_rel(host(d), U) < 1e-12
+
+
+@pytest.mark.parametrize("storage", [18, 12])
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 4, 6, 10)])
+def test_fp64_sweeps_parity(storage, dims):
+    U = cpu_field(dims, seed=5, gseed=6)
+    c = ctx_for(dims, 0, storage64=storage)
+    d = dev(U)
+    gf.gf_upload(c, d, gf.GF_FP64)
+    gf.gf_or_sweeps(c, 1.7, 10)
+    oracle.or_sweeps(U, 1.7, 0, 10)
+    gf.gf_download(c, d)
+    assert max_rel(host(d), U) < 1e-12
+
+
+@pytest.mark.parametrize("block", [32, 64, 256])
+def test_fp64_block_shapes(block):
+    dims = (6, 4, 6, 10)
+    U = cpu_field(dims, seed=7, gseed=8)
+    c = ctx_for(dims, 0, block=block, threads_per_site=2)
+    d = dev(U)
+    gf.gf_upload(c, d, gf.GF_FP64)
+    gf.gf_or_sweeps(c, 1.3, 3)
+    oracle.or_sweeps(U, 1.3, 0, 3)
+    gf.gf_download(c, d)
+    assert max_rel(host(d), U) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# FP32 storage
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", [12, 18])
+@pytest.mark.parametrize("tps", [1, 2, 4, 8])
+@pytest.mark.parametrize("gauge", [0, 1])
+def test_fp32_half_sweep_parity(storage, tps, gauge):
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=9, gseed=10)
+    c = ctx_for(dims, gauge, storage32=storage, threads_per_site=tps)
+    d = dev(U)
+    gf.gf_upload(c, d, gf.GF_FP32)
+    gf.gf_or_half_sweep(c, 0, 1.7)
+    gf.gf_or_half_sweep(c, 1, 1.7)
+    oracle.or_sweeps(U, 1.7, gauge, 1)
+    gf.gf_download(c, d)
+    assert np.abs(host(d) - U).max() < 5e-6
+    gf.gf_or_sweeps(c, 1.7, 4)
+    oracle.or_sweeps(U, 1.7, gauge, 4)
+    gf.gf_download(c, d)
+    assert np.abs(host(d) - U).max() < 2e-5
+
+
+# ---------------------------------------------------------------------------
+# reductions
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", SMALL)
+@pytest.mark.parametrize("gauge", [0, 1])
+def test_functional_theta_plaquette(dims, gauge):
+    U = cpu_field(dims, seed=11, gseed=12)
+    oracle.or_sweeps(U, 1.7, gauge, 3)  # a field with smaller theta as well
+    c = ctx_for(dims, gauge)
+    d = dev(U)
+    assert gf.gf_functional(c, d) == pytest.approx(oracle.functional(U, gauge), rel=1e-13, abs=1e-15)
+    assert gf.gf_theta(c, d) == pytest.approx(oracle.theta(U, gauge), rel=1e-12)
+    assert gf.gf_plaquette(c, d) == pytest.approx(oracle.plaquette(U), rel=1e-13)
+    # resident-field measurement, FP64 storage 18 and 12
+    for st in (18, 12):
+        gf.gf_set_option(c, "storage64", st)
+        gf.gf_upload(c, d, gf.GF_FP64)
+        F, th = gf.gf_measure(c)
+        assert F == pytest.approx(oracle.functional(U, gauge), rel=1e-13, abs=1e-15)
+        assert th == pytest.approx(oracle.theta(U, gauge), rel=1e-11)
+    # host (numpy) input takes the same path through a staging copy
+    assert gf.gf_theta(c, U) == pytest.approx(oracle.theta(U, gauge), rel=1e-12)
+
+
+def test_measure_is_deterministic():
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=13, gseed=14)
+    c = ctx_for(dims, 0)
+    d = dev(U)
+    vals = {gf.gf_theta(c, d) for _ in range(5)}
+    assert len(vals) == 1
+
+
+# ---------------------------------------------------------------------------
+# the whole method
+# ---------------------------------------------------------------------------
+def test_overrelax_fp64_matches_oracle_sweep_count():
+    """Config: Landau, omega = 1.7, 8^4, theta < 1e-12, seeds 1/2."""
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=1, gseed=2)
+    c = ctx_for(dims, 0, check_every=10)
+    d = dev(U)
+    conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-12, 5000)
+    oconv, oit, oF, oth = oracle.overrelax(U, 0, 1.7, 1e-12, 5000, 10)
+    assert conv and oconv
+    assert it == oit
+    assert F == pytest.approx(oF, rel=1e-12)
+    assert th == pytest.approx(oth, rel=1e-6)
+    assert max_rel(host(d), U) < 1e-10
+
+
+def test_pure_gauge_reaches_unit_functional_on_gpu():
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, gseed=2, pure=True)
+    c = ctx_for(dims, 0, check_every=10)
+    d = dev(U)
+    conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-24, 20000)
+    assert conv and th < 1e-24
+    assert F == pytest.approx(1.0, abs=1e-12)
+
+
+def test_plaquette_invariant_under_gpu_sweeps():
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=15, gseed=16)
+    P = oracle.plaquette(U)
+    c = ctx_for(dims, 0)
+    d = dev(U)
+    gf.gf_upload(c, d, gf.GF_FP64)
+    gf.gf_or_sweeps(c, 1.7, 200)
+    gf.gf_download(c, d)
+    assert gf.gf_plaquette(c, d) == pytest.approx(P, abs=1e-13)
+
+
+def test_host_pointer_path_equals_device_path():
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=17, gseed=18)
+    c = ctx_for(dims, 0, check_every=10)
+    d = dev(U)
+    Uh = U.copy()
+    r1 = gf.gf_overrelax(c, d, 1.7, 1e-10, 2000)
+    r2 = gf.gf_overrelax(c, Uh, 1.7, 1e-10, 2000)
+    assert r1 == r2
+    np.testing.assert_array_equal(host(d), Uh)
+
+
+def test_not_converged_is_reported_with_valid_outputs():
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=19, gseed=20)
+    c = ctx_for(dims, 0, check_every=10)
+    d = dev(U)
+    conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-14, 25)
+    assert not conv and it == 25 and th > 1e-14
+    assert th == pytest.approx(gf.gf_theta(c, d), rel=1e-12)
+
+
+def test_mixed_precision_reaches_same_functional():
+    """FP32 (12-real) sweeps to theta < 1e-6, then FP64 to 1e-14 (config on 8^4)."""
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=3, gseed=4)
+    c64 = ctx_for(dims, 0, check_every=10)
+    d64 = dev(U)
+    conv, it64, F64, th64 = gf.gf_overrelax(c64, d64, 1.7, 1e-14, 20000)
+    assert conv
+    for track in (1, 0):
+        c = ctx_for(dims, 0, check_every=10, precision=gf.GF_MIXED, track_gauge=track)
+        d = dev(U)
+        conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-14, 20000)
+        assert conv and th < 1e-14
+        assert gf.gf_get_stat(c, "sweeps_fp32") > 0 and gf.gf_get_stat(c, "sweeps_fp64") > 0
+        if track:
+            # a gauge transform of the exact input: same F as all-FP64, plaquette exact
+            assert abs(F - F64) < 1e-10
+            assert gf.gf_plaquette(c, d) == pytest.approx(oracle.plaquette(U), abs=1e-13)
+        else:
+            assert abs(F - F64) < 1e-6
+
+
+def test_fp32_policy_converges_to_fp32_precision():
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=3, gseed=4)
+    c = ctx_for(dims, 0, check_every=10, precision=gf.GF_FP32)
+    d = dev(U)
+    conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-8, 20000)
+    assert conv and th < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# simulated annealing
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("gauge", [0, 1])
+@pytest.mark.parametrize("tps", [1, 2, 8])
+@pytest.mark.parametrize("T", [1.45, 0.3, 0.01])
+def test_sa_half_sweep_parity(gauge, tps, T):
+    dims = (6, 4, 6, 10)
+    U = cpu_field(dims, seed=21, gseed=22)
+    c = ctx_for(dims, gauge, threads_per_site=tps)
+    d = dev(U)
+    gf.gf_upload(c, d, gf.GF_FP64)
+    gf.gf_sa_half_sweep(c, 0, T, 1234, 7)
+    gf.gf_sa_half_sweep(c, 1, T, 1234, 7)
+    assert oracle.sa_half_sweep(U, 0, T, gauge, 1234, 7) == 0
+    assert oracle.sa_half_sweep(U, 1, T, gauge, 1234, 7) == 0
+    gf.gf_download(c, d)
+    assert max_rel(host(d), U) < 1e-11
+
+
+def test_anneal_schedule_parity():
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=23, gseed=24)
+    c = ctx_for(dims, 1, sa_sweep_offset=100)
+    d = dev(U)
+    gf.gf_anneal(c, d, 1.45, 0.01, 12, 99)
+    assert oracle.anneal(U, 1, 1.45, 0.01, 12, 99, 100) == 0
+    assert max_rel(host(d), U) < 1e-10
+
+
+def test_anneal_rejection_cap_reports_error():
+    dims = (4, 4, 4, 4)
+    U = cpu_field(dims, seed=25, gseed=26)
+    c = ctx_for(dims, 0, sa_cap=1)
+    d = dev(U)
+    rc = gf.gf_anneal(c, d, 0.05, 0.05, 1, 5, allow_reject=True)
+    assert rc == gf.GF_EREJECT
+    assert gf.gf_get_stat(c, "sa_rejects") > 0
+    P = oracle.plaquette(U)
+    assert gf.gf_plaquette(c, d) == pytest.approx(P, abs=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# argument errors surface as GFError, no device fault
+# ---------------------------------------------------------------------------
+def test_argument_errors():
+    dims = (4, 4, 4, 4)
+    U = cpu_field(dims)
+    c = ctx_for(dims, 0)
+    d = dev(U)
+    with pytest.raises(gf.GFError) as e:
+        gf.gf_overrelax(c, d, 2.5, 1e-12, 10)
+    assert e.value.code == gf.GF_EINVAL
+    with pytest.raises(gf.GFError):
+        gf.gf_overrelax(c, d, float("nan"), 1e-12, 10)
+    with pytest.raises(gf.GFError):
+        gf.gf_anneal(c, d, -1.0, 0.1, 3, 1)
+    with pytest.raises(ValueError):
+        gf.gf_theta(c, torch.zeros(10, dtype=torch.float64, device=DEV))
+
+
+def test_autotune_picks_a_valid_config_and_keeps_parity():
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=27, gseed=28)
+    c = ctx_for(dims, 0)
+    d = dev(U)
+    gf.gf_upload(c, d, gf.GF_FP64)
+    tps, block = gf.gf_autotune(c)
+    assert tps in (1, 2, 4, 8) and block in (64, 128, 256)
+    gf.gf_upload(c, d, gf.GF_FP64)
+    gf.gf_or_sweeps(c, 1.7, 3)
+    oracle.or_sweeps(U, 1.7, 0, 3)
+    gf.gf_download(c, d)
+    assert max_rel(host(d), U) < 1e-12
