@@ -149,7 +149,7 @@ def oracle_sample(U_np: np.ndarray, budget_s: float = 12.0):
     t0 = time.perf_counter()
     oracle.or_sweeps(W, OMEGA, 0, 1)
     one = time.perf_counter() - t0
-    n = max(1, min(50, int(budget_s / max(one, 1e-3)) - 1))
+    n = max(1, min(500, int(budget_s / max(one, 1e-3)) - 1))
     t0 = time.perf_counter()
     oracle.or_sweeps(W, OMEGA, 0, n)
     dt = time.perf_counter() - t0
@@ -363,6 +363,40 @@ def gpu_arm(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+FORMATS = {"fp32_12": (1, "storage32", 12, 768), "fp32_18": (1, "storage32", 18, 1152),
+           "fp64_12": (0, "storage64", 12, 1536), "fp64_18": (0, "storage64", 18, 2304)}
+
+
+def kernel_only(args):
+    """One storage format's OR half-sweep on the 32^4 field, for profiling:
+    warmup sweeps, then timed sweeps; prints the average half-sweep time."""
+    from paper_1209_4008_gb300 import gf, synth
+    prec_code, key, st, nbytes = FORMATS[args.kernel]
+    prec = gf.GF_FP64 if prec_code == 0 else gf.GF_FP32
+    dims = tuple(args.dims) if args.dims else DIMS
+    field = synth.make_field(dims, PLAQ, *SEEDS, device="cuda")
+    c = gf.gf_create(dims, gf.GF_LANDAU)
+    gf.gf_set_option(c, key, st)
+    gf.gf_set_option(c, "threads_per_site", args.tps)
+    gf.gf_set_option(c, "block", args.block)
+    gf.gf_set_option(c, "use_graphs", 0)
+    gf.gf_set_stream(c, torch.cuda.current_stream())
+    gf.gf_upload(c, field, prec)
+    gf.gf_or_sweeps(c, OMEGA, args.warmup)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    gf.gf_or_sweeps(c, OMEGA, args.steps)
+    e1.record(s)
+    torch.cuda.synchronize()
+    t_half = e0.elapsed_time(e1) / (2 * args.steps)
+    Vh = int(np.prod(dims)) // 2
+    print(json.dumps({"kernel": args.kernel, "dims": list(dims), "tps": args.tps, "block": args.block,
+                      "ms_per_half_sweep": t_half, "gsu_per_s": Vh / (t_half * 1e-3) / 1e9,
+                      "algorithmic_gbs": Vh * nbytes / (t_half * 1e-3) / 1e9}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,7 +404,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gf", choices=["gf", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--kernel", choices=sorted(FORMATS), help="time one storage format's sweep only")
+    ap.add_argument("--tps", type=int, default=1)
+    ap.add_argument("--block", type=int, default=64)
+    ap.add_argument("--dims", type=int, nargs=4)
     args = ap.parse_args()
+    if args.kernel:
+        torch.cuda.set_device(0)
+        kernel_only(args)
+        return
     rank, world, local = dist_setup(args.gpus)
     try:
         if args.impl == "reference":

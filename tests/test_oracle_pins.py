@@ -430,3 +430,17 @@ def test_haar_generator_moments():
     tr = torch.diagonal(M, dim1=-2, dim2=-1).sum(-1)
     assert abs(tr.mean().item()) < 0.02
     assert (tr.abs() ** 2).mean().item() == pytest.approx(1.0, abs=0.03)
+
+
+def test_plaquette_single_link_closed_form():
+    """Unit field with one link W: the 6 plaquettes through it give Re tr W,
+    the other 6V - 6 give 3, so P = (18 V - 18 + 6 Re tr W) / (18 V)."""
+    dims = (4, 4, 6, 4)
+    V = 4 * 4 * 6 * 4
+    U = np.zeros((4, 6, 4, 4, 4, 3, 3), complex)
+    U[...] = np.eye(3)
+    W = synth.as_numpy(synth.haar_su3((1,), 6))[0]
+    U[1, 2, 3, 0, 1] = W
+    expect = (18 * V - 18 + 6 * np.trace(W).real) / (18 * V)
+    assert oracle.plaquette(U) == pytest.approx(expect, abs=1e-15)
+    del dims
