@@ -178,6 +178,36 @@ int gf_reunitarize(gf_ctx *ctx);
  * (volume, storage, gauge) for the process.  Outputs may be NULL. */
 int gf_autotune(gf_ctx *ctx, int *threads_per_site, int *block);
 
+/* ------------------------------------------------- allocation-free measure */
+
+/* Largest lattice volume gf_measure_noalloc accepts. */
+#define GF_NOALLOC_MAX_SITES (1 << 21)
+
+/* F and theta of a canonical field U held in device memory, computed without
+ * allocating anything: no cudaMalloc, no context, no library pool.  It is for
+ * callers that cannot allocate device memory at the point of the call -- for
+ * example code that runs while another thread captures a CUDA graph, code
+ * inside a framework that owns all device memory through its own allocator,
+ * or a service that forbids allocation after start-up.  (This entry point has
+ * no counterpart in the paper; it is a deployment convenience beside
+ * gf_functional / gf_theta, which allocate their scratch on first use.)
+ *
+ * dims, gauge: as for gf_create.  U: device pointer, canonical layout,
+ * 16-byte aligned, read only.  out: device pointer to 2 doubles, written with
+ * {F, theta} in stream order (read them after synchronising stream).
+ * stream: cudaStream_t (NULL = legacy default stream).
+ * Scratch: a fixed file-scope device array of 2 * GF_NOALLOC_MAX_SITES / 256
+ * doubles (128 KiB), present on every GPU that loads the library until the
+ * process exits.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls on a device share the array and
+ * leave their partial sums in it; calls whose kernels overlap on the GPU race
+ * and must be ordered by the caller.
+ * Errors: GF_EINVAL for a NULL, host or misaligned pointer, a bad gauge or
+ * extent, or a volume above GF_NOALLOC_MAX_SITES; GF_ECUDA if the launch or
+ * the address lookup fails. */
+int gf_measure_noalloc(const int dims[4], int gauge, const double *U, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,7 @@ SIGNATURES = {
     "gf_measure": (C.c_int, [_vp, _dp, _dp]),
     "gf_reunitarize": (C.c_int, [_vp]),
     "gf_autotune": (C.c_int, [_vp, _ip, _ip]),
+    "gf_measure_noalloc": (C.c_int, [_ip, C.c_int, _vp, _vp, _vp]),
 }
 
 
@@ -266,3 +267,13 @@ def gf_autotune(ctx: Context):
     t, b = C.c_int(), C.c_int()
     ctx.check(ctx.lib.gf_autotune(ctx.handle, C.byref(t), C.byref(b)), "gf_autotune")
     return t.value, b.value
+
+
+def gf_measure_noalloc(dims, gauge: int, U, out, stream=None) -> int:
+    """F and theta of a device field into the device buffer out (2 doubles),
+    without any allocation; returns the C return code."""
+    lib = load()
+    arr = (C.c_int * 4)(*[int(d) for d in dims])
+    s = getattr(stream, "cuda_stream", stream)
+    return lib.gf_measure_noalloc(arr, int(gauge), _ptr(U), _ptr(out), s or None)
+
