@@ -397,6 +397,143 @@ def kernel_only(args):
                       "algorithmic_gbs": Vh * nbytes / (t_half * 1e-3) / 1e9}), flush=True)
 
 
+BATCH_SIZES = (8, 12, 16, 24)
+
+
+def batched(args):
+    """64 lattices (16 each of 8^4, 12^4, 16^4, 24^4; seeds 100..163; plaquette
+    uniform in [0.55, 0.62] from seed 99), mixed precision, omega 1.7, theta <
+    1e-12: one persistent launch per precision phase under a CUDA graph versus a
+    loop of single-lattice calls.  Prints one JSON object (not the headline line)."""
+    from paper_1209_4008_gb300 import gf, synth
+    dims = [(L, L, L, L) for L in BATCH_SIZES for _ in range(16)]
+    plaq = synth.batched_plaquettes(len(dims))
+    pristine = [synth.make_field(d, plaq[k], 100 + k, 1100 + k, device="cuda") for k, d in enumerate(dims)]
+    work = [p.clone() for p in pristine]
+    target, max_iter = 1e-12, 100_000
+
+    def restore():
+        for w, p in zip(work, pristine):
+            w.copy_(p)
+
+    b = gf.gf_batch_create(dims, gf.GF_LANDAU)
+    gf.gf_batch_set_option(b, "precision", gf.GF_MIXED)
+    gf.gf_batch_set_option(b, "check_every", CHECK_EVERY)
+    gf.gf_batch_set_stream(b, torch.cuda.current_stream())
+    tps, block = gf.gf_batch_autotune(b, work)
+    restore()
+    gf.gf_batch_overrelax(b, work, OMEGA, target, max_iter)  # warm-up: capture the graph
+    restore()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, iters, F, th = gf.gf_batch_overrelax(b, work, OMEGA, target, max_iter)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    su = sum(i * int(np.prod(d)) for i, d in zip(iters, dims))
+    stats = {k: gf.gf_batch_get_stat(b, k) for k in ("ms_fp32", "ms_fp64", "grid_fp32", "grid_fp64", "tiles",
+                                                      "threads_per_site", "block")}
+    # per-lattice loop through the single-lattice entry point
+    ctxs = []
+    for d in dims:
+        c = gf.gf_create(d, gf.GF_LANDAU)
+        gf.gf_set_option(c, "precision", gf.GF_MIXED)
+        gf.gf_set_option(c, "check_every", CHECK_EVERY)
+        gf.gf_set_option(c, "autotune", 1)
+        gf.gf_set_stream(c, torch.cuda.current_stream())
+        ctxs.append(c)
+    restore()
+    for c, w in zip(ctxs, work):  # warm-up (autotune, graphs)
+        gf.gf_overrelax(c, w, OMEGA, target, max_iter)
+    restore()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    su_loop = 0
+    for c, w, d in zip(ctxs, work, dims):
+        conv, it, _, _ = gf.gf_overrelax(c, w, OMEGA, target, max_iter)
+        su_loop += it * int(np.prod(d))
+    torch.cuda.synchronize()
+    t_loop = time.perf_counter() - t0
+    print(json.dumps({"workload": "batched-landau 64 lattices (16 each of 8^4,12^4,16^4,24^4), mixed, theta<1e-12",
+                      "sites": int(sum(np.prod(d) for d in dims)), "converged": rc == gf.GF_OK,
+                      "persistent": {"s": t_batch, "site_updates": su, "su_per_s": su / t_batch,
+                                     "threads_per_site": tps, "block": block, **stats},
+                      "loop": {"s": t_loop, "site_updates": su_loop, "su_per_s": su_loop / t_loop},
+                      "speedup": t_loop / t_batch,
+                      "sweeps_min_max": [min(iters), max(iters)]}), flush=True)
+
+
+WEIGHTS = os.path.join(ROOT, "paper_1209_4008_gb300", "weights", "warm_start_16x16x16x16.npy")
+
+
+def learned(args):
+    """Learned warm start: training pairs from the solver on 16^4 fields (seeds
+    1000.., plaquette 0.60), GPU training, then fixing fresh 32^4 fields (seeds
+    5000..) to theta < 1e-14 with the mixed policy with and without the
+    network at the FP32 -> FP64 switch.  Prints one JSON object."""
+    from paper_1209_4008_gb300 import gf, learned as L, synth
+    t_start = time.perf_counter()
+    train_dims = (16, 16, 16, 16)
+    ctx = gf.gf_create(train_dims, gf.GF_LANDAU)
+    gf.gf_set_option(ctx, "autotune", 1)
+    pairs = []
+    t0 = time.perf_counter()
+    for k in range(args.pairs):
+        U = synth.make_field(train_dims, PLAQ, 1000 + k, 3000 + k, device="cuda")
+        pairs.append(L.make_pair(ctx, U, theta_switch=THETA_SWITCH, label_theta=1e-12, check_every=CHECK_EVERY))
+    t_data = time.perf_counter() - t0
+    nval = max(1, args.pairs // 10)
+    train_set, val_set = pairs[nval:], pairs[:nval]
+    net = gf.gf_net_create(train_dims)
+    gf.gf_net_set_params(net, L.init_params(0))
+    t0 = time.perf_counter()
+    hist = L.train(net, train_set, epochs=args.epochs, lr=args.lr, lr_decay=0.7,
+                   log=lambda m: print(m, file=sys.stderr, flush=True))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    val = L.validation_loss(net, val_set)
+    params = np.zeros(gf.gf_net_param_count(), dtype=np.float32)
+    gf.gf_net_get_params(net, params)
+    if args.save:
+        os.makedirs(os.path.dirname(WEIGHTS), exist_ok=True)
+        np.save(WEIGHTS, params)
+    # evaluation on 32^4 fields
+    big = gf.gf_net_create(DIMS)
+    gf.gf_net_set_params(big, params)
+    res = []
+    for k in range(args.eval_fields):
+        pristine = synth.make_field(DIMS, PLAQ, 5000 + k, 6000 + k, device="cuda")
+        row = {}
+        for mode in ("mixed", "learned"):
+            c = make_ctx(gf, gf.GF_MIXED)
+            if mode == "learned":
+                gf.gf_set_net(c, big)
+            work = pristine.clone()
+            gf.gf_overrelax(c, work, OMEGA, THETA_TARGET, MAX_ITER)  # warm-up (autotune, graphs)
+            work.copy_(pristine)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            conv, it, F, th = gf.gf_overrelax(c, work, OMEGA, THETA_TARGET, MAX_ITER)
+            torch.cuda.synchronize()
+            row[mode] = {"s": time.perf_counter() - t1, "sweeps": it, "F": F, "theta": th, "converged": conv,
+                         "sweeps_fp64": gf.gf_get_stat(c, "sweeps_fp64")}
+            if mode == "learned":
+                row[mode]["ms_network"] = gf.gf_get_stat(c, "ms_learned")
+                row[mode]["theta_before"] = gf.gf_get_stat(c, "theta_before_learned")
+                row[mode]["theta_after"] = gf.gf_get_stat(c, "theta_after_learned")
+        row["dF"] = abs(row["learned"]["F"] - row["mixed"]["F"])
+        res.append(row)
+    mean = lambda key, mode: float(np.mean([r[mode][key] for r in res]))
+    print(json.dumps({
+        "workload": f"learned warm start: {args.pairs} solver pairs on 16^4 (plaquette 0.60), "
+                    f"{args.epochs} epochs Adam; test on {args.eval_fields} fresh 32^4 fields, theta<1e-14",
+        "data_s": t_data, "train_s": t_train, "train_loss": hist, "val_loss": val,
+        "eval": res,
+        "mean": {"mixed_s": mean("s", "mixed"), "learned_s": mean("s", "learned"),
+                 "mixed_fp64_sweeps": mean("sweeps_fp64", "mixed"),
+                 "learned_fp64_sweeps": mean("sweeps_fp64", "learned")},
+        "total_s": time.perf_counter() - t_start}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,7 +545,22 @@ def main():
     ap.add_argument("--tps", type=int, default=1)
     ap.add_argument("--block", type=int, default=64)
     ap.add_argument("--dims", type=int, nargs=4)
+    ap.add_argument("--batched", action="store_true", help="the 64-lattice batched workload")
+    ap.add_argument("--learned", action="store_true", help="train and evaluate the learned warm start")
+    ap.add_argument("--pairs", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--eval-fields", type=int, default=4)
+    ap.add_argument("--save", action="store_true", help="store the trained parameters")
     args = ap.parse_args()
+    if args.learned:
+        torch.cuda.set_device(0)
+        learned(args)
+        return
+    if args.batched:
+        torch.cuda.set_device(0)
+        batched(args)
+        return
     if args.kernel:
         torch.cuda.set_device(0)
         kernel_only(args)

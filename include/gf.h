@@ -39,6 +39,7 @@
 #ifndef GF_H
 #define GF_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -99,6 +100,12 @@ int gf_set_stream(gf_ctx *ctx, void *stream);
  *                    (default 1); 0 = widen the FP32 links instead
  *   "reunitarize_every"  FP32 phase: reunitarise every n checks (default 1)
  *   "threads_per_site"   1, 2, 4 or 8; 0 = autotune (default 0)
+ *   "variant"        site update: 1 = the three subgroup rotations applied to
+ *                    the eight links held in registers (Alg. 1 literally,
+ *                    1-8 threads per site), 2 = the same steps on M(x) =
+ *                    sum of the links with G = R3 R2 R1 accumulated and applied
+ *                    once per link (one thread per site; equal in exact
+ *                    arithmetic), 0 = autotuned or default (default 0)
  *   "block"          threads per block (multiple of 32, <= 1024; 0 = autotune)
  *   "use_graphs"     1 = replay sweep loops as CUDA graphs (default 1)
  *   "sa_cap"         heatbath rejection cap per draw (default 64, <= 255)
@@ -177,6 +184,119 @@ int gf_reunitarize(gf_ctx *ctx);
  * timing every candidate on a scratch copy; the choice is cached per
  * (volume, storage, gauge) for the process.  Outputs may be NULL. */
 int gf_autotune(gf_ctx *ctx, int *threads_per_site, int *block);
+
+/* --------------------------------------------------- learned warm start */
+
+/* The learned warm start predicts, from the FP64 field at the FP32 -> FP64
+ * switch of GF_MIXED, the gauge transformation that the remaining FP64
+ * sweeps would apply, and applies it before they start; overrelaxation then
+ * finishes as usual and decides convergence.
+ *
+ * Network inputs, per site (channels last, BF16): the 72 reals of the four
+ * forward links U_mu(x), then tr(lambda_a Delta(x)) / s, a = 1..8, with
+ * Delta(x) the gauge-fixing violation of eq. theta and s = sqrt(theta).
+ * Output: 8 coefficients c_a(x); the applied transformation is
+ * g(x) = exp(i s sum_a c_a(x) lambda_a / 2), an exact FP64 gauge
+ * transformation of the field.  Sites are in lexicographic order.
+ *
+ * Network: four periodic 4D convolutions with 3^4 taps, channels
+ * 80 -> 32 -> 32 -> 32 -> 8, ReLU between layers, BF16 weights and
+ * activations, FP32 accumulation.  Parameters (FP32 master copy) are the
+ * concatenation W1 b1 W2 b2 W3 b3 W4 b4 with W_l[81][C_out][C_in], tap
+ * k = (dx+1) + 3(dy+1) + 9(dz+1) + 27(dt+1), Y[s][o] = b[o] +
+ * sum_k sum_i W[k][o][i] X[s + d(k)][i].  Loss: mean squared error over all
+ * sites and outputs.  Training uses Adam (beta 0.9 / 0.999, eps 1e-8). */
+#define GF_NET_CIN 80
+#define GF_NET_COUT 8
+typedef struct gf_net gf_net;
+
+size_t gf_net_param_count(void);
+/* A network sized for lattices of extents dims (activations are kept). */
+int gf_net_create(const int dims[4], gf_net **out);
+int gf_net_destroy(gf_net *n);
+const char *gf_net_last_error(const gf_net *n);
+int gf_net_set_stream(gf_net *n, void *stream);
+/* Copy gf_net_param_count() FP32 parameters in (host or device); resets Adam. */
+int gf_net_set_params(gf_net *n, const float *params);
+int gf_net_get_params(gf_net *n, float *params);
+/* features: device BF16 [V][80]; out: device FP32 [V][8]. */
+int gf_net_forward(gf_net *n, const void *features, float *out);
+/* Loss and gradient w.r.t. the parameters (grad host or device, may be NULL). */
+int gf_net_gradient(gf_net *n, const void *features, const float *target, float *grad, double *loss);
+/* Options: "tensor_cores" (default 1): forward and backward-data convolutions
+ * as implicit GEMMs on the tcgen05 tensor cores (BF16 in, FP32 accumulators
+ * in tensor memory); 0 = the CUDA-core kernels.  Forward, gradient and train
+ * calls synchronise the stream and return GF_ETIMEOUT if a bounded wait in a
+ * tensor-core kernel expired. */
+int gf_net_set_option(gf_net *n, const char *key, double value);
+/* One Adam step on (features, target); loss before the step in *loss. */
+int gf_net_train_step(gf_net *n, const void *features, const float *target, float lr, double *loss);
+
+/* Gauge tracking on the resident field: reset the tracked g(x) to 1; with
+ * option "track" = 1, gf_or_half_sweep / gf_or_sweeps / gf_converge also
+ * rotate g(x) (stored as FP32, 12 reals per site). */
+int gf_gauge_reset(gf_ctx *ctx);
+/* The tracked g as a canonical site field double g[V][3][3][2] (host or
+ * device), reprojected onto SU(3) in FP64. */
+int gf_get_gauge(gf_ctx *ctx, double *g);
+/* Alg. 1 convergence loop on the resident field (no upload/download);
+ * FP32 fields are reunitarised at each check. */
+int gf_converge(gf_ctx *ctx, double omega, double theta_target, int max_iter, int *iters_out, double *F_out,
+                double *theta_out);
+/* Resident FP64 field := g(x) U_mu(x) g(x+mu)^dagger for the caller's field
+ * U (host or device) and the tracked g: the FP32 -> FP64 switch of GF_MIXED. */
+int gf_apply_tracked_gauge(gf_ctx *ctx, const double *U);
+/* Network inputs of the resident FP64 field with scale s (device BF16 [V][80]). */
+int gf_features(gf_ctx *ctx, double scale, void *features);
+/* Training labels: tr(lambda_a (g - g^dagger)/(2i)) / s of the tracked g
+ * (the algebra coefficients of log g to first order), device FP32 [V][8]. */
+int gf_gauge_algebra(gf_ctx *ctx, double scale, float *c);
+/* Apply g(x) = exp(i s sum_a c_a(x) lambda_a / 2) to the resident FP64 field. */
+int gf_apply_algebra(gf_ctx *ctx, const float *c, double scale);
+/* Attach a trained network (NULL detaches): GF_MIXED then applies its
+ * prediction at the switch before the FP64 sweeps.  The context does not own it. */
+int gf_set_net(gf_ctx *ctx, gf_net *net);
+
+/* ------------------------------------ many lattices in one persistent launch */
+
+/* A batch of n independent lattices (uneven volumes allowed) gauge-fixed
+ * together: all fields share one device arena, their tiles form one work
+ * list, and each precision phase of Alg. 1 -- theta checks (Sec. 4.1),
+ * convergence decisions per lattice and the RED/BLACK half-sweeps -- runs
+ * as ONE persistent cooperative kernel whose blocks meet at grid-wide
+ * barriers; converged lattices drop out of the work list.  The whole call is
+ * captured once as a CUDA graph and replayed while its inputs stay the same.
+ * dims: n x 4 extents (each as for gf_create); gauge for all lattices. */
+typedef struct gf_batch gf_batch;
+int gf_batch_create(int n, const int *dims, int gauge, gf_batch **out);
+int gf_batch_destroy(gf_batch *b);
+const char *gf_batch_last_error(const gf_batch *b);
+int gf_batch_set_stream(gf_batch *b, void *stream);
+
+/* Options: "precision" (default GF_MIXED), "storage32", "storage64",
+ * "check_every" (default 25), "theta_switch" (default 1e-6),
+ * "threads_per_site", "block" (0 = autotuned or default), "use_graphs",
+ * "barrier_timeout_ms" (bounded grid-barrier wait, default 2000; on expiry
+ * the call returns GF_ETIMEOUT and the batch stays usable),
+ * "barrier_extra_blocks" (test hook: 1 makes every barrier wait for a block
+ * that does not exist, so the bounded wait expires). */
+int gf_batch_set_option(gf_batch *b, const char *key, double value);
+
+/* Stats of the last call: "site_updates", "ms_fp32", "ms_fp64", "ms_total",
+ * "grid_fp32", "grid_fp64", "threads_per_site", "block", "tiles". */
+int gf_batch_get_stat(const gf_batch *b, const char *key, double *value);
+
+/* Gauge-fix every U[i] (device pointers, canonical layout, in place) by
+ * overrelaxation with the batch's precision policy; per lattice: iters[i]
+ * sweeps, final F[i] and theta[i] (arrays of n, may be NULL).  Returns
+ * GF_OK if every lattice converged, GF_ENOTCONVERGED otherwise. */
+int gf_batch_overrelax(gf_batch *b, double *const *U, double omega, double theta_target, int max_iter,
+                       int *iters, double *F, double *theta);
+
+/* Choose threads per site and block size for both storage formats by timing
+ * every candidate on the fields U (left unchanged); cached per set of
+ * extents for the process.  Outputs (FP32 phase choice) may be NULL. */
+int gf_batch_autotune(gf_batch *b, double *const *U, int *threads_per_site, int *block);
 
 /* ------------------------------------------------- allocation-free measure */
 

@@ -24,7 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
-_SOURCES = ["gf_oracle.c"]
+_SOURCES = ["gf_oracle.c", "conv_oracle.c"]
 _lock = threading.Lock()
 _libs: dict[str, C.CDLL] = {}
 
@@ -87,6 +87,19 @@ def _declare(lib: C.CDLL) -> C.CDLL:
     d.oracle_anneal.restype = C.c_long
     d.oracle_sa_update_sites.argtypes = [_dp, _ip, _lp, C.c_long, C.c_double, C.c_int,
                                          C.c_uint64, C.c_uint32, C.c_int, _dp]
+    d.oracle_conv_forward.argtypes = [_dp, _dp, _dp, _ip, C.c_int, C.c_int, _dp]
+    d.oracle_conv_forward.restype = None
+    d.oracle_conv_backward_data.argtypes = [_dp, _dp, _ip, C.c_int, C.c_int, _dp]
+    d.oracle_conv_backward_data.restype = None
+    d.oracle_conv_backward_weights.argtypes = [_dp, _dp, _ip, C.c_int, C.c_int, _dp, _dp]
+    d.oracle_conv_backward_weights.restype = None
+    d.oracle_net_loss.argtypes = [_dp, _dp, _dp, _ip, _ip, _dp, _dp]
+    d.oracle_net_loss.restype = C.c_double
+    d.oracle_features.argtypes = [_dp, _ip, C.c_double, _dp]
+    d.oracle_expmap.argtypes = [_dp, C.c_double, _dp, C.c_long]
+    d.oracle_expmap.restype = None
+    d.oracle_algebra_log.argtypes = [_dp, C.c_double, _dp, C.c_long]
+    d.oracle_algebra_log.restype = None
     d.oracle_flops.restype = C.c_ulonglong
     d.oracle_reset_flops.restype = None
     d.oracle_num_threads.restype = C.c_int
@@ -296,6 +309,88 @@ def count_flops_half_sweep(U, parity: int, omega: float, gauge: int = 0) -> int:
 
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
+
+
+# ---------------------------------------------------------------------------
+# learned warm start: periodic 3^4 convolutions and the four-layer network
+# ---------------------------------------------------------------------------
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dims4(dims) -> np.ndarray:
+    return np.array([int(d) for d in dims], dtype=np.intc)
+
+
+def conv_forward(X, W, b, dims):
+    """Y[s][co] = b[co] + sum_k sum_ci W[k][co][ci] X[s + d(k)][ci] (periodic)."""
+    X, W = _f64(X), _f64(W)
+    cout, cin = W.shape[1], W.shape[2]
+    V = int(np.prod(dims))
+    Y = np.zeros((V, cout))
+    bb = _f64(b) if b is not None else None
+    lib().oracle_conv_forward(_d(X), _d(W), _d(bb) if bb is not None else None, _i(_dims4(dims)), cin,
+                              cout, _d(Y))
+    return Y
+
+
+def conv_backward_data(dY, W, dims):
+    dY, W = _f64(dY), _f64(W)
+    cout, cin = W.shape[1], W.shape[2]
+    V = int(np.prod(dims))
+    dX = np.zeros((V, cin))
+    lib().oracle_conv_backward_data(_d(dY), _d(W), _i(_dims4(dims)), cin, cout, _d(dX))
+    return dX
+
+
+def conv_backward_weights(dY, X, dims, cin, cout):
+    dY, X = _f64(dY), _f64(X)
+    dW = np.zeros((81, cout, cin))
+    db = np.zeros(cout)
+    lib().oracle_conv_backward_weights(_d(dY), _d(X), _i(_dims4(dims)), cin, cout, _d(dW), _d(db))
+    return dW, db
+
+
+def features(U, scale: float) -> np.ndarray:
+    """Network inputs (V, 80): forward-link reals, then tr(lambda_a Delta)/scale."""
+    U = _field(U)
+    V = int(np.prod(U.shape[:4]))
+    f = np.zeros((V, 80))
+    _check(lib().oracle_features(_d(U), _i(dims_of(U)), scale, _d(f)), "features")
+    return f
+
+
+def expmap(c, scale: float = 1.0) -> np.ndarray:
+    """exp(i scale sum_a c_a lambda_a / 2) for c of shape (n, 8) -> (n, 3, 3) complex."""
+    c = _f64(c).reshape(-1, 8)
+    g = np.zeros((c.shape[0], 3, 3), dtype=np.complex128)
+    lib().oracle_expmap(_d(c), scale, _d(g), c.shape[0])
+    return g
+
+
+def algebra_log(g, scale: float = 1.0) -> np.ndarray:
+    """First-order algebra coefficients tr(lambda_a (g - g^+)/2i)/scale, (n, 8)."""
+    g = np.ascontiguousarray(g, dtype=np.complex128).reshape(-1, 3, 3)
+    c = np.zeros((g.shape[0], 8))
+    lib().oracle_algebra_log(_d(g), scale, _d(c), g.shape[0])
+    return c
+
+
+def net_param_count(channels) -> int:
+    return sum(81 * channels[l + 1] * channels[l] + channels[l + 1] for l in range(4))
+
+
+def net_loss(f, target, params, dims, channels, want_grad=True):
+    """Loss (and gradient w.r.t. the flat parameter vector, and the output)."""
+    f, target, params = _f64(f), _f64(target), _f64(params)
+    c = np.array(channels, dtype=np.intc)
+    assert params.size == net_param_count(channels)
+    grad = np.zeros_like(params) if want_grad else None
+    V = int(np.prod(dims))
+    out = np.zeros((V, channels[4]))
+    loss = lib().oracle_net_loss(_d(f), _d(target), _d(params), _i(_dims4(dims)), _i(c),
+                                 _d(grad) if grad is not None else None, _d(out))
+    return loss, grad, out
 
 
 # ---------------------------------------------------------------------------

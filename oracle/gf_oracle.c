@@ -893,3 +893,123 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* learned warm start: network inputs, exp map, algebra coefficients         */
+/* ------------------------------------------------------------------------ */
+
+/* Gell-Mann matrices lambda_1..8, tr(lambda_a lambda_b) = 2 delta_ab */
+static mat3 gell_mann(int a)
+{
+    mat3 L;
+    memset(&L, 0, sizeof L);
+    const double r3 = 1.0 / sqrt(3.0);
+    switch (a) {
+    case 0: L.m[0][1] = c_make(1, 0); L.m[1][0] = c_make(1, 0); break;
+    case 1: L.m[0][1] = c_make(0, -1); L.m[1][0] = c_make(0, 1); break;
+    case 2: L.m[0][0] = c_make(1, 0); L.m[1][1] = c_make(-1, 0); break;
+    case 3: L.m[0][2] = c_make(1, 0); L.m[2][0] = c_make(1, 0); break;
+    case 4: L.m[0][2] = c_make(0, -1); L.m[2][0] = c_make(0, 1); break;
+    case 5: L.m[1][2] = c_make(1, 0); L.m[2][1] = c_make(1, 0); break;
+    case 6: L.m[1][2] = c_make(0, -1); L.m[2][1] = c_make(0, 1); break;
+    default:
+        L.m[0][0] = c_make(r3, 0);
+        L.m[1][1] = c_make(r3, 0);
+        L.m[2][2] = c_make(-2 * r3, 0);
+    }
+    return L;
+}
+
+/* Re tr(lambda_a X) */
+static double re_tr_lambda(int a, const mat3 *X)
+{
+    mat3 L = gell_mann(a);
+    mat3 P = mat_mul(&L, X);
+    return mat_retrace(&P);
+}
+
+/*
+ * Network inputs of the learned warm start, per site (channels last, 80 per
+ * site): the 72 reals of the four forward links U_mu(x) (row-major, re/im),
+ * then tr(lambda_a Delta(x)) / scale for a = 1..8, with Delta(x) the
+ * traceless part of (M - M^dagger)/(2i), M = sum_mu [U_mu(x) + U_mu(x-mu)^+]
+ * (Landau), i.e. the gauge-fixing violation of eq. theta.
+ */
+int oracle_features(const double *U, const int dims[4], double scale, double *f)
+{
+    lattice g;
+    if (lattice_init(&g, dims) || !(scale > 0)) return -1;
+    for (long i = 0; i < g.V; ++i) {
+        double *o = f + i * 80;
+        mat3 M;
+        memset(&M, 0, sizeof M);
+        for (int mu = 0; mu < 4; ++mu) {
+            const double *p = link_cptr(U, i, mu);
+            for (int r = 0; r < 18; ++r) o[mu * 18 + r] = p[r];
+            mat3 uf = mat_load(p);
+            mat3 ub = mat_load(link_cptr(U, site_shift(&g, i, mu, -1), mu));
+            mat3 ubd = mat_dagger(&ub);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) M.m[a][b] = c_add(M.m[a][b], c_add(uf.m[a][b], ubd.m[a][b]));
+        }
+        mat3 D = antiherm_part(&M);
+        make_traceless(&D);
+        for (int a = 0; a < 8; ++a) o[72 + a] = re_tr_lambda(a, &D) / scale;
+    }
+    return 0;
+}
+
+/*
+ * g = exp(i H), H = scale * sum_a c_a lambda_a / 2, for n sets of 8
+ * coefficients.  Taylor series of order 12 after halving H until its
+ * Frobenius norm is below 1/8, then repeated squaring (Moler and Van Loan,
+ * "scaling and squaring").
+ */
+void oracle_expmap(const double *c, double scale, double *gout, long n)
+{
+    for (long j = 0; j < n; ++j) {
+        mat3 H;
+        memset(&H, 0, sizeof H);
+        for (int a = 0; a < 8; ++a) {
+            mat3 L = gell_mann(a);
+            double w = 0.5 * scale * c[j * 8 + a];
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y)
+                    H.m[x][y] = c_add(H.m[x][y], c_make(w * L.m[x][y].re, w * L.m[x][y].im));
+        }
+        double nrm = sqrt(frob2(&H));
+        int sq = 0;
+        while (nrm > 0.125) {
+            nrm *= 0.5;
+            ++sq;
+        }
+        double s = ldexp(1.0, -sq);
+        mat3 A; /* A = i H s */
+        for (int x = 0; x < 3; ++x)
+            for (int y = 0; y < 3; ++y) A.m[x][y] = c_make(-H.m[x][y].im * s, H.m[x][y].re * s);
+        mat3 E, T;
+        memset(&E, 0, sizeof E);
+        for (int x = 0; x < 3; ++x) E.m[x][x] = c_make(1, 0);
+        T = E;
+        for (int k = 1; k <= 12; ++k) {
+            mat3 P = mat_mul(&T, &A);
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y) T.m[x][y] = c_make(P.m[x][y].re / k, P.m[x][y].im / k);
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y) E.m[x][y] = c_add(E.m[x][y], T.m[x][y]);
+        }
+        for (int k = 0; k < sq; ++k) E = mat_mul(&E, &E);
+        mat_store(gout + j * 18, &E);
+    }
+}
+
+/* c_a = tr(lambda_a (g - g^+)/(2i)) / scale: the algebra coefficients of
+ * log g to first order (exact up to O(|log g|^3)). */
+void oracle_algebra_log(const double *gin, double scale, double *c, long n)
+{
+    for (long j = 0; j < n; ++j) {
+        mat3 gm = mat_load(gin + j * 18);
+        mat3 A = antiherm_part(&gm);
+        for (int a = 0; a < 8; ++a) c[j * 8 + a] = re_tr_lambda(a, &A) / scale;
+    }
+}

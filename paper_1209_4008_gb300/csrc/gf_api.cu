@@ -55,10 +55,15 @@ struct gf_ctx {
     int reunit_every = 1;
     int tps = 0;
     int block = 0;
+    int variant = 0;  // 0 auto, 1 per-subgroup rotations of the held links, 2 accumulate form
     int use_graphs = 1;
     int autotune = 0;
     int sa_cap = 64;
     uint32_t sa_sweep_offset = 0;
+    int track = 0;             // resident sweeps also rotate the tracked g
+    gf_net *net = nullptr;     // learned warm start applied at the FP32 -> FP64 switch
+    void *feat = nullptr;      // BF16 network inputs [V][80]
+    float *cbuf = nullptr;     // network outputs [V][8]
     // streams
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
@@ -91,6 +96,7 @@ static int fail(gf_ctx *c, int code, const std::string &msg)
 
 static int cuda_fail(gf_ctx *c, cudaError_t e, const char *what)
 {
+    cudaGetLastError();  // do not leave the error for the next runtime call to report
     char buf[512];
     snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
     return fail(c, e == cudaErrorMemoryAllocation ? GF_ENOMEM : GF_ECUDA, buf);
@@ -233,6 +239,8 @@ static std::pair<int, int> launch_config(const gf_ctx *c, int fmt)
         if (it != g_tune_cache.end()) cfg = it->second;
     }
     if (c->tps) cfg.first = c->tps;
+    if (c->variant == 2) cfg.first = 0;  // accumulate form: one thread per site
+    if (c->variant == 1 && cfg.first == 0) cfg.first = c->tps ? c->tps : 2;
     if (c->block) cfg.second = c->block;
     return cfg;
 }
@@ -379,11 +387,11 @@ static int autotune_format(gf_ctx *ctx, int fmt, char *field, int *tps_out, int 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    const int tps_c[4] = { 1, 2, 4, 8 };
+    const int tps_c[5] = { 0, 1, 2, 4, 8 };  // 0: accumulate form
     const int blk_c[3] = { 64, 128, 256 };
     float best = 1e30f;
     std::pair<int, int> pick = default_config(fmt);
-    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i)
         for (int b = 0; b < 3 && e == cudaSuccess; ++b) {
             std::pair<int, int> cfg{ tps_c[i], blk_c[b] };
             e = issue_sweeps(ctx, fmt, scratch, 1.7, 1, false, cfg, ctx->stream);  // warm up
@@ -415,6 +423,33 @@ static bool tuned(const gf_ctx *c, int fmt)
 {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     return g_tune_cache.count(std::make_tuple(c->dims[0], c->dims[1], c->dims[2], c->dims[3], fmt, c->gauge)) > 0;
+}
+
+// ---------------------------------------------------------------------------
+// learned warm start (resident FP64 field)
+// ---------------------------------------------------------------------------
+static int ensure_learned_buffers(gf_ctx *ctx)
+{
+    if (!ctx->feat) CK(cudaMalloc(&ctx->feat, 2 * (size_t)GF_NET_CIN * ctx->V));
+    if (!ctx->cbuf) CK(cudaMalloc(&ctx->cbuf, sizeof(float) * GF_NET_COUT * ctx->V));
+    return GF_OK;
+}
+
+// network inputs -> network -> g = exp(i s c.lambda/2) -> resident field g U g^+
+static int learned_correction(gf_ctx *ctx, double theta)
+{
+    if (ctx->resident != GF_FP64) return fail(ctx, GF_ESTATE, "learned correction needs the FP64 field");
+    RET(ensure_learned_buffers(ctx));
+    RET(ensure_gauge_field(ctx));
+    double s = sqrt(theta);
+    CK(launch_features(ctx->resident_fmt, ref(ctx, ctx->f64), ctx->geom, 1.0 / s, ctx->feat, ctx->stream));
+    gf_net_set_stream(ctx->net, ctx->stream);
+    int r = gf_net_forward(ctx->net, ctx->feat, ctx->cbuf);
+    if (r != GF_OK) return fail(ctx, r, std::string("network: ") + gf_net_last_error(ctx->net));
+    CK(launch_expmap_to_gauge(ctx->cbuf, s, ref(ctx, ctx->gt), ctx->geom, ctx->stream));
+    CK(launch_gauge_transform_resident(ctx->resident_fmt, ref(ctx, ctx->f64), ref(ctx, ctx->gt), ctx->geom,
+                                       ctx->stream));
+    return GF_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -471,6 +506,8 @@ int gf_destroy(gf_ctx *ctx)
     cudaFree(ctx->f32);
     cudaFree(ctx->gt);
     cudaFree(ctx->staging);
+    cudaFree(ctx->feat);
+    cudaFree(ctx->cbuf);
     cudaFree(ctx->partials);
     cudaFree(ctx->dres);
     cudaFree(ctx->dstatus);
@@ -523,10 +560,15 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
     } else if (k == "block") {
         if (!integral || iv < 0 || iv > 256 || (iv % 32)) return fail(ctx, GF_EINVAL, "block: 0 or 32..256 step 32");
         ctx->block = iv;
+    } else if (k == "variant") {
+        if (!integral || iv < 0 || iv > 2) return fail(ctx, GF_EINVAL, "variant: 0, 1 or 2");
+        ctx->variant = iv;
     } else if (k == "use_graphs") {
         ctx->use_graphs = v != 0.0;
     } else if (k == "autotune") {
         ctx->autotune = v != 0.0;
+    } else if (k == "track") {
+        ctx->track = v != 0.0;
     } else if (k == "sa_cap") {
         if (!integral || iv < 1 || iv > 255) return fail(ctx, GF_EINVAL, "sa_cap: 1..255");
         ctx->sa_cap = iv;
@@ -552,9 +594,11 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *v)
     else if (k == "reunitarize_every") *v = ctx->reunit_every;
     else if (k == "threads_per_site") *v = ctx->tps;
     else if (k == "block") *v = ctx->block;
+    else if (k == "variant") *v = ctx->variant;
     else if (k == "use_graphs") *v = ctx->use_graphs;
     else if (k == "autotune") *v = ctx->autotune;
     else if (k == "sa_cap") *v = ctx->sa_cap;
+    else if (k == "track") *v = ctx->track;
     else if (k == "sa_sweep_offset") *v = ctx->sa_sweep_offset;
     else return GF_EINVAL;
     return GF_OK;
@@ -594,9 +638,10 @@ int gf_or_half_sweep(gf_ctx *ctx, int parity, double omega)
     if (!ctx) return GF_EINVAL;
     if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
     if ((parity & ~1) || !(omega > 0.0 && omega < 2.0)) return fail(ctx, GF_EINVAL, "parity 0/1, omega in (0,2)");
+    if (ctx->track && !ctx->gt) return fail(ctx, GF_ESTATE, "track is set but no gauge field (gf_gauge_reset)");
     std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt);
     SweepArgs a = sweep_args(ctx, resident_base(ctx), parity, omega);
-    CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 0, false, cfg.second, ctx->stream));
+    CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 0, ctx->track != 0, cfg.second, ctx->stream));
     return GF_OK;
 }
 
@@ -606,7 +651,8 @@ int gf_or_sweeps(gf_ctx *ctx, double omega, int nsweeps)
     if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
     if (nsweeps < 0 || !(omega > 0.0 && omega < 2.0)) return fail(ctx, GF_EINVAL, "nsweeps >= 0, omega in (0,2)");
     if (nsweeps == 0) return GF_OK;
-    return run_chunk(ctx, ctx->resident_fmt, resident_base(ctx), omega, nsweeps, false, false, false);
+    if (ctx->track && !ctx->gt) return fail(ctx, GF_ESTATE, "track is set but no gauge field (gf_gauge_reset)");
+    return run_chunk(ctx, ctx->resident_fmt, resident_base(ctx), omega, nsweeps, ctx->track != 0, false, false);
 }
 
 int gf_sa_half_sweep(gf_ctx *ctx, int parity, double T, uint64_t seed, uint32_t sweep)
@@ -734,6 +780,15 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
             if (ctx->autotune && !tuned(ctx, ctx->resident_fmt))
                 RET(autotune_format(ctx, ctx->resident_fmt, ctx->f64, nullptr, nullptr));
             RET(measure_resident(ctx, &F, &theta));
+            ctx->stats["theta_switch_measured"] = theta;
+            if (ctx->net && theta > 0.0 && !(theta < theta_target)) {
+                double t3 = now_ms();
+                RET(learned_correction(ctx, theta));
+                RET(measure_resident(ctx, &F, &theta));
+                ctx->stats["ms_learned"] = now_ms() - t3;
+                ctx->stats["theta_before_learned"] = ctx->stats["theta_switch_measured"];
+                ctx->stats["theta_after_learned"] = theta;
+            }
             RET(converge(ctx, omega, theta_target, max_iter - used32, false, false, &used64, &F, &theta));
             ms64 = now_ms() - t2;
         } else {
@@ -756,6 +811,102 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
     if (F_out) *F_out = F;
     if (theta_out) *theta_out = theta;
     return theta < theta_target ? GF_OK : GF_ENOTCONVERGED;
+}
+
+int gf_gauge_reset(gf_ctx *ctx)
+{
+    if (!ctx) return GF_EINVAL;
+    RET(ensure_common(ctx));
+    RET(ensure_gauge_field(ctx));
+    CK(launch_gauge_identity(ref(ctx, ctx->gt), ctx->geom, ctx->stream));
+    return GF_OK;
+}
+
+int gf_get_gauge(gf_ctx *ctx, double *g)
+{
+    if (!ctx || !g) return GF_EINVAL;
+    if (!ctx->gt) return fail(ctx, GF_ESTATE, "no tracked gauge field");
+    bool host = !is_device_pointer(g);
+    double *dst = g;
+    if (host) {
+        RET(ensure_staging(ctx));
+        dst = ctx->staging;
+    }
+    CK(launch_decode_gauge(ref(ctx, ctx->gt), ctx->geom, dst, ctx->stream));
+    if (host) CK(cudaMemcpyAsync(g, dst, sizeof(double) * 18 * (size_t)ctx->V, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GF_OK;
+}
+
+int gf_converge(gf_ctx *ctx, double omega, double theta_target, int max_iter, int *iters_out, double *F_out,
+                double *theta_out)
+{
+    if (!ctx) return GF_EINVAL;
+    if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
+    if (!(omega > 0.0 && omega < 2.0) || !(theta_target >= 0.0) || max_iter < 0)
+        return fail(ctx, GF_EINVAL, "omega in (0,2), theta_target >= 0, max_iter >= 0");
+    if (ctx->track && !ctx->gt) return fail(ctx, GF_ESTATE, "track is set but no gauge field (gf_gauge_reset)");
+    double F = 0.0, theta = 0.0;
+    int used = 0;
+    RET(measure_resident(ctx, &F, &theta));
+    bool reunit = ctx->resident == GF_FP32 && ctx->reunit_every > 0;
+    RET(converge(ctx, omega, theta_target, max_iter, ctx->track != 0, reunit, &used, &F, &theta));
+    if (iters_out) *iters_out = used;
+    if (F_out) *F_out = F;
+    if (theta_out) *theta_out = theta;
+    return theta < theta_target ? GF_OK : GF_ENOTCONVERGED;
+}
+
+int gf_apply_tracked_gauge(gf_ctx *ctx, const double *U)
+{
+    if (!ctx) return GF_EINVAL;
+    if (!ctx->gt) return fail(ctx, GF_ESTATE, "no tracked gauge field");
+    const double *view;
+    bool host;
+    RET(device_view(ctx, U, &view, &host));
+    RET(ensure_field(ctx, GF_FP64));
+    CK(launch_apply_tracked_gauge(view, ref(ctx, ctx->gt), fmt64(ctx), ref(ctx, ctx->f64), ctx->geom, ctx->stream));
+    ctx->resident = GF_FP64;
+    ctx->resident_fmt = fmt64(ctx);
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GF_OK;
+}
+
+int gf_features(gf_ctx *ctx, double scale, void *features)
+{
+    if (!ctx || !features || !(scale > 0.0)) return GF_EINVAL;
+    if (ctx->resident != GF_FP64) return fail(ctx, GF_ESTATE, "features need a resident FP64 field");
+    if (!is_device_pointer(features)) return fail(ctx, GF_EINVAL, "features must be device memory");
+    CK(launch_features(ctx->resident_fmt, ref(ctx, ctx->f64), ctx->geom, 1.0 / scale, features, ctx->stream));
+    return GF_OK;
+}
+
+int gf_gauge_algebra(gf_ctx *ctx, double scale, float *c)
+{
+    if (!ctx || !c || !(scale > 0.0)) return GF_EINVAL;
+    if (!ctx->gt) return fail(ctx, GF_ESTATE, "no tracked gauge field");
+    if (!is_device_pointer(c)) return fail(ctx, GF_EINVAL, "output must be device memory");
+    CK(launch_gauge_algebra(ref(ctx, ctx->gt), ctx->geom, 1.0 / scale, c, ctx->stream));
+    return GF_OK;
+}
+
+int gf_apply_algebra(gf_ctx *ctx, const float *c, double scale)
+{
+    if (!ctx || !c || !(scale > 0.0)) return GF_EINVAL;
+    if (ctx->resident != GF_FP64) return fail(ctx, GF_ESTATE, "needs a resident FP64 field");
+    if (!is_device_pointer(c)) return fail(ctx, GF_EINVAL, "coefficients must be device memory");
+    RET(ensure_gauge_field(ctx));
+    CK(launch_expmap_to_gauge(c, scale, ref(ctx, ctx->gt), ctx->geom, ctx->stream));
+    CK(launch_gauge_transform_resident(ctx->resident_fmt, ref(ctx, ctx->f64), ref(ctx, ctx->gt), ctx->geom,
+                                       ctx->stream));
+    return GF_OK;
+}
+
+int gf_set_net(gf_ctx *ctx, gf_net *net)
+{
+    if (!ctx) return GF_EINVAL;
+    ctx->net = net;
+    return GF_OK;
 }
 
 int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t seed)

@@ -90,4 +90,11 @@ cudaError_t launch_measure_aos(const double *aos, const Geom &g, int coulomb, do
                                cudaStream_t s);
 cudaError_t launch_plaquette_aos(const double *aos, const Geom &g, double *partials, double *out, cudaStream_t s);
 
+// learned warm start, field side (gf_learned.cu)
+cudaError_t launch_features(int fmt, FieldRef f, const Geom &g, double inv_scale, void *out, cudaStream_t s);
+cudaError_t launch_gauge_algebra(FieldRef gt, const Geom &g, double inv_scale, float *out, cudaStream_t s);
+cudaError_t launch_expmap_to_gauge(const float *c, double scale, FieldRef gt, const Geom &g, cudaStream_t s);
+cudaError_t launch_gauge_transform_resident(int fmt, FieldRef f, FieldRef gt, const Geom &g, cudaStream_t s);
+cudaError_t launch_decode_gauge(FieldRef gt, const Geom &g, double *out, cudaStream_t s);
+
 }  // namespace gf

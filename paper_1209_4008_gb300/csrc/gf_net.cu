@@ -1,0 +1,695 @@
+// gf_net.cu -- the learned warm-start network: four periodic 4D convolutions
+// with 3^4 taps (channels 80 -> 32 -> 32 -> 32 -> 8), ReLU between layers,
+// BF16 weights and activations, FP32 accumulation; forward, backward (data
+// and weights), mean-squared-error loss and Adam, all on the GPU.
+//
+// Conventions (as in the oracle): activations X[site][C] with site = x +
+// Lx (y + Ly (z + Lz t)); tap k = (dx+1) + 3 (dy+1) + 9 (dz+1) + 27 (dt+1);
+// W[k][co][ci]; Y[s][co] = b[co] + sum_k sum_ci W[k][co][ci] X[s + d(k)][ci].
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "gf.h"
+#include "gf_conv_tc.cuh"
+#include "gf_device.cuh"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kC[5] = { GF_NET_CIN, 32, 32, 32, GF_NET_COUT };
+
+struct Lat {
+    int L[4];
+    int V;
+};
+
+__device__ __forceinline__ int shift_site(const Lat &g, int s, int k, int sign)
+{
+    int c0 = s % g.L[0];
+    int r = s / g.L[0];
+    int c1 = r % g.L[1];
+    r /= g.L[1];
+    int c2 = r % g.L[2];
+    int c3 = r / g.L[2];
+    int d0 = k % 3 - 1, d1 = (k / 3) % 3 - 1, d2 = (k / 9) % 3 - 1, d3 = k / 27 - 1;
+    c0 += sign * d0;
+    c1 += sign * d1;
+    c2 += sign * d2;
+    c3 += sign * d3;
+    c0 = c0 < 0 ? c0 + g.L[0] : (c0 >= g.L[0] ? c0 - g.L[0] : c0);
+    c1 = c1 < 0 ? c1 + g.L[1] : (c1 >= g.L[1] ? c1 - g.L[1] : c1);
+    c2 = c2 < 0 ? c2 + g.L[2] : (c2 >= g.L[2] ? c2 - g.L[2] : c2);
+    c3 = c3 < 0 ? c3 + g.L[3] : (c3 >= g.L[3] ? c3 - g.L[3] : c3);
+    return c0 + g.L[0] * (c1 + g.L[1] * (c2 + g.L[2] * c3));
+}
+
+// ---------------------------------------------------------------------------
+// convolution on CUDA cores: Y[s][o] = b[o] + sum_k sum_i Wk[k][o][i] X[s + sign d(k)][i]
+// 256 threads: SITES sites x (O / 8) output groups of 8 outputs each.
+// Optional epilogue: ReLU, or multiplication by (mask[s][o] > 0).
+// ---------------------------------------------------------------------------
+template <int I, int O>
+__global__ void __launch_bounds__(256) k_conv_cc(const bf16 *__restrict__ X, const bf16 *__restrict__ W,
+                                                 const float *__restrict__ bias, Lat g, int sign, int relu,
+                                                 const bf16 *__restrict__ mask, bf16 *__restrict__ Yb,
+                                                 float *__restrict__ Yf)
+{
+    constexpr int G = O / 8;             // output groups
+    constexpr int SITES = 256 / G;       // sites per block
+    __shared__ float xs[SITES][I + 1];
+    __shared__ __align__(16) float ws[I][O];
+    __shared__ int nbr[SITES];
+    const int sl = threadIdx.x % SITES, og = threadIdx.x / SITES;
+    const int s0 = blockIdx.x * SITES;
+    float acc[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) acc[o] = bias ? bias[og * 8 + o] : 0.0f;
+    for (int k = 0; k < 81; ++k) {
+        __syncthreads();
+        for (int r = threadIdx.x; r < SITES; r += 256) nbr[r] = s0 + r < g.V ? shift_site(g, s0 + r, k, sign) : -1;
+        __syncthreads();
+        for (int e = threadIdx.x; e < SITES * I; e += 256) {
+            int r = e / I, i = e - r * I;
+            int nb = nbr[r];
+            xs[r][i] = nb >= 0 ? __bfloat162float(X[(long)nb * I + i]) : 0.0f;
+        }
+        for (int e = threadIdx.x; e < I * O; e += 256) {
+            int o = e / I, i = e - o * I;
+            ws[i][o] = __bfloat162float(W[((long)k * O + o) * I + i]);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int i = 0; i < I; ++i) {
+            float x = xs[sl][i];
+            float4 w0 = *reinterpret_cast<const float4 *>(&ws[i][og * 8]);
+            float4 w1 = *reinterpret_cast<const float4 *>(&ws[i][og * 8 + 4]);
+            acc[0] += w0.x * x;
+            acc[1] += w0.y * x;
+            acc[2] += w0.z * x;
+            acc[3] += w0.w * x;
+            acc[4] += w1.x * x;
+            acc[5] += w1.y * x;
+            acc[6] += w1.z * x;
+            acc[7] += w1.w * x;
+        }
+    }
+    int s = s0 + sl;
+    if (s >= g.V) return;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        int oc = og * 8 + o;
+        float v = acc[o];
+        if (relu) v = v > 0.0f ? v : 0.0f;
+        if (mask && !(__bfloat162float(mask[(long)s * O + oc]) > 0.0f)) v = 0.0f;
+        if (Yb) Yb[(long)s * O + oc] = __float2bfloat16(v);
+        if (Yf) Yf[(long)s * O + oc] = v;
+    }
+}
+
+// dW[k][o][i] += sum over a chunk of sites of dY[s][o] X[s + d(k)][i];
+// db[o] += sum_s dY[s][o] (tap 13 blocks only).  Block = (tap, chunk).
+template <int I, int O>
+__global__ void __launch_bounds__(256) k_conv_dw(const bf16 *__restrict__ dY, const bf16 *__restrict__ X, Lat g,
+                                                 float *__restrict__ dW, float *__restrict__ db)
+{
+    constexpr int CH = 64;
+    constexpr int PER = (I * O + 255) / 256;
+    __shared__ float ys[CH][O + 1];
+    __shared__ float xs[CH][I + 1];
+    __shared__ int nbr[CH];
+    const int k = blockIdx.y;
+    const int s0 = blockIdx.x * CH;
+    if (threadIdx.x < CH) nbr[threadIdx.x] = s0 + threadIdx.x < g.V ? shift_site(g, s0 + threadIdx.x, k, 1) : -1;
+    __syncthreads();
+    for (int e = threadIdx.x; e < CH * O; e += 256) {
+        int r = e / O, o = e - r * O;
+        int s = s0 + r;
+        ys[r][o] = s < g.V ? __bfloat162float(dY[(long)s * O + o]) : 0.0f;
+    }
+    for (int e = threadIdx.x; e < CH * I; e += 256) {
+        int r = e / I, i = e - r * I;
+        xs[r][i] = nbr[r] >= 0 ? __bfloat162float(X[(long)nbr[r] * I + i]) : 0.0f;
+    }
+    __syncthreads();
+    float acc[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) acc[j] = 0.0f;
+    for (int r = 0; r < CH; ++r) {
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            int e = threadIdx.x + j * 256;
+            if (e < I * O) {
+                int o = e / I, i = e - o * I;
+                acc[j] += ys[r][o] * xs[r][i];
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        int e = threadIdx.x + j * 256;
+        if (e < I * O) atomicAdd(&dW[(long)k * I * O + e], acc[j]);
+    }
+    if (k == 13 && db && threadIdx.x < O) {
+        float a = 0.0f;
+        for (int r = 0; r < CH; ++r) a += ys[r][threadIdx.x];
+        atomicAdd(&db[threadIdx.x], a);
+    }
+}
+
+// loss partials and the output gradient dOut = 2 (out - t) / n (BF16)
+__global__ void k_mse(const float *__restrict__ out, const float *__restrict__ t, long n, float inv_n,
+                      bf16 *__restrict__ dout, double *__restrict__ partial)
+{
+    double acc = 0.0;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        float d = out[e] - t[e];
+        acc += (double)d * d;
+        dout[e] = __float2bfloat16(2.0f * d * inv_n);
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_partials(const double *p, int n, double scale, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += p[i];
+        *out = s * scale;
+    }
+}
+
+// Adam on the FP32 master parameters, then BF16 copies W[k][o][i] and Wt[k][i][o]
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ gr, float *__restrict__ m,
+                       float *__restrict__ v, long n, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    float gi = gr[e];
+    float mi = b1 * m[e] + (1.0f - b1) * gi;
+    float vi = b2 * v[e] + (1.0f - b2) * gi * gi;
+    m[e] = mi;
+    v[e] = vi;
+    p[e] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+}
+
+__global__ void k_cast_weights(const float *__restrict__ W, int I, int O, bf16 *__restrict__ Wb,
+                               bf16 *__restrict__ Wt)
+{
+    long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long n = 81L * I * O;
+    if (e >= n) return;
+    int k = (int)(e / ((long)I * O));
+    int r = (int)(e - (long)k * I * O);
+    int o = r / I, i = r - o * I;
+    bf16 w = __float2bfloat16(W[e]);
+    Wb[e] = w;
+    Wt[((long)k * I + i) * O + o] = w;
+}
+
+
+// ---------------------------------------------------------------------------
+// convolution on the tensor cores (tcgen05): see gf_conv_tc.cuh
+// IP: input channels padded to a multiple of 16; N: output channels padded
+// (16 or 32).  X rows have I channels, W is [81][O][I].
+// ---------------------------------------------------------------------------
+template <int IP, int N>
+struct TcLayout {
+    static constexpr int A_BYTES = gf::tc::kM * IP * 2;
+    static constexpr int B_BYTES = N * IP * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int BAR_OFF = gf::tc::kStages * STAGE + gf::tc::kGuardBytes;
+    static constexpr int SMEM = BAR_OFF + (gf::tc::kStages + 1) * 8 + 16;
+};
+
+template <int IP, int N>
+__global__ void __launch_bounds__(128) k_conv_tc(const bf16 *__restrict__ X, int I, const bf16 *__restrict__ W, int O,
+                                                 const float *__restrict__ bias, Lat g, int sign, int relu,
+                                                 const bf16 *__restrict__ mask, bf16 *__restrict__ Yb,
+                                                 float *__restrict__ Yf, int *__restrict__ err)
+{
+    using namespace gf::tc;
+    typedef TcLayout<IP, N> LY;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);  // kStages + 1 (final)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + (kStages + 1) * 8);
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int s0 = blockIdx.x * kM;
+    constexpr uint32_t idesc = instr_desc(kM, N);
+
+    if (tid == 0) {
+        for (int st = 0; st <= kStages; ++st) mbar_init(&bar[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    const int site = s0 + tid;
+    bool fail = false;
+    for (int k = 0; k < 81; ++k) {
+        const int st = k % kStages;
+        if (k >= kStages) {
+            if (!mbar_wait(&bar[st], (uint32_t)((k / kStages - 1) & 1))) fail = true;
+        }
+        if (__syncthreads_or(fail)) {
+            fail = true;
+            break;
+        }
+        uint8_t *A = smem + st * LY::STAGE;
+        uint8_t *B = A + LY::A_BYTES;
+        // A: this thread's neighbour row, K-major core matrices (8 rows x 16 B):
+        // core (mr, kc) at (kc * 16 + mr) * 128  -> SBO 128, LBO 2048
+        const int nbs = site < g.V ? shift_site(g, site, k, sign) : -1;
+#pragma unroll
+        for (int c = 0; c < IP / 8; ++c) {
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (nbs >= 0 && 8 * c < I) v = *reinterpret_cast<const uint4 *>(X + (long)nbs * I + 8 * c);
+            *reinterpret_cast<uint4 *>(A + (c * 16 + (tid >> 3)) * 128 + (tid & 7) * 16) = v;
+        }
+        // B: weights of tap k, core (mr, kc) at (kc * (N/8) + mr) * 128 -> SBO 128, LBO N*16
+        for (int e = tid; e < N * (IP / 8); e += kThreads) {
+            const int o = e / (IP / 8), c = e - o * (IP / 8);
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (o < O && 8 * c < I) v = *reinterpret_cast<const uint4 *>(W + ((long)k * O + o) * I + 8 * c);
+            *reinterpret_cast<uint4 *>(B + (c * (N / 8) + (o >> 3)) * 128 + (o & 7) * 16) = v;
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after_sync();
+#pragma unroll
+            for (int kk = 0; kk < IP / 16; ++kk) {
+                uint64_t ad = smem_desc(smem_u32(A + kk * 2 * 2048), 2048, 128);
+                uint64_t bd = smem_desc(smem_u32(B + kk * 2 * (N / 8) * 128), (N / 8) * 128, 128);
+                mma_bf16(tmem, ad, bd, idesc, (k | kk) != 0);
+            }
+            mma_commit(&bar[st]);
+        }
+    }
+    // all MMAs issued by thread 0 are complete once the final commit arrives
+    if (tid == 0) mma_commit(&bar[kStages]);
+    if (!mbar_wait(&bar[kStages], 0)) fail = true;
+    fail = __syncthreads_or(fail);
+    if (!fail) {
+        fence_after_sync();
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        if (N == 32) {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+        } else {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+                " [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (site < g.V) {
+#pragma unroll
+            for (int o = 0; o < N; ++o) {
+                if (o >= O) break;
+                float v = __uint_as_float(r[o]) + (bias ? bias[o] : 0.0f);
+                if (relu) v = v > 0.0f ? v : 0.0f;
+                if (mask && !(__bfloat162float(mask[(long)site * O + o]) > 0.0f)) v = 0.0f;
+                if (Yb) Yb[(long)site * O + o] = __float2bfloat16(v);
+                if (Yf) Yf[(long)site * O + o] = v;
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(err, GF_ETIMEOUT);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    }
+}
+
+template <int IP, int N>
+cudaError_t conv_tc(const bf16 *X, int I, const bf16 *W, int O, const float *b, const Lat &g, int sign, int relu,
+                    const bf16 *mask, bf16 *Yb, float *Yf, int *err, cudaStream_t s)
+{
+    typedef TcLayout<IP, N> LY;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<IP, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, LY::SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_conv_tc<IP, N><<<(g.V + gf::tc::kM - 1) / gf::tc::kM, gf::tc::kThreads, LY::SMEM, s>>>(X, I, W, O, b, g, sign,
+                                                                                          relu, mask, Yb, Yf, err);
+    return cudaGetLastError();
+}
+
+template <int I, int O>
+cudaError_t conv_cc(const bf16 *X, const bf16 *W, const float *b, const Lat &g, int sign, int relu, const bf16 *mask,
+                    bf16 *Yb, float *Yf, cudaStream_t s)
+{
+    constexpr int SITES = 256 / (O / 8);
+    k_conv_cc<I, O><<<(g.V + SITES - 1) / SITES, 256, 0, s>>>(X, W, b, g, sign, relu, mask, Yb, Yf);
+    return cudaGetLastError();
+}
+
+template <int I, int O>
+cudaError_t conv_dw(const bf16 *dY, const bf16 *X, const Lat &g, float *dW, float *db, cudaStream_t s)
+{
+    dim3 grid((g.V + 63) / 64, 81);
+    k_conv_dw<I, O><<<grid, 256, 0, s>>>(dY, X, g, dW, db);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+struct gf_net {
+    Lat g;
+    cudaStream_t stream = nullptr;
+    float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    long np = 0;
+    long woff[4], boff[4];
+    bf16 *Wb[4] = { nullptr }, *Wt[4] = { nullptr };
+    bf16 *act[4] = { nullptr };  // act[1..3] owned; act[0] = caller's features
+    float *out = nullptr;
+    bf16 *dA = nullptr, *dB = nullptr;  // [V][32] gradient scratch (ping-pong)
+    double *partial = nullptr, *dloss = nullptr;
+    int *derr = nullptr;  // tensor-core kernels: bounded-wait expiry
+    int use_tc = 1;       // forward and backward-data on tcgen05 (else CUDA cores)
+    int step = 0;
+    std::string err;
+};
+
+static int nfail(gf_net *n, int code, const std::string &m)
+{
+    if (code == GF_ECUDA || code == GF_ENOMEM) cudaGetLastError();
+    n->err = m;
+    return code;
+}
+
+#define NCK(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return nfail(n, e_ == cudaErrorMemoryAllocation ? GF_ENOMEM : GF_ECUDA,        \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+static long param_count()
+{
+    long n = 0;
+    for (int l = 0; l < 4; ++l) n += 81L * kC[l + 1] * kC[l] + kC[l + 1];
+    return n;
+}
+
+static int refresh_weights(gf_net *n)
+{
+    for (int l = 0; l < 4; ++l) {
+        long cnt = 81L * kC[l + 1] * kC[l];
+        k_cast_weights<<<(int)((cnt + 255) / 256), 256, 0, n->stream>>>(n->params + n->woff[l], kC[l], kC[l + 1],
+                                                                          n->Wb[l], n->Wt[l]);
+        NCK(cudaGetLastError());
+    }
+    return GF_OK;
+}
+
+static int forward(gf_net *n, const bf16 *f)
+{
+    const Lat &g = n->g;
+    cudaStream_t s = n->stream;
+    n->act[0] = const_cast<bf16 *>(f);
+    if (n->use_tc) {
+        NCK((conv_tc<80, 32>(f, 80, n->Wb[0], 32, n->params + n->boff[0], g, 1, 1, nullptr, n->act[1], nullptr,
+                             n->derr, s)));
+        NCK((conv_tc<32, 32>(n->act[1], 32, n->Wb[1], 32, n->params + n->boff[1], g, 1, 1, nullptr, n->act[2],
+                             nullptr, n->derr, s)));
+        NCK((conv_tc<32, 32>(n->act[2], 32, n->Wb[2], 32, n->params + n->boff[2], g, 1, 1, nullptr, n->act[3],
+                             nullptr, n->derr, s)));
+        NCK((conv_tc<32, 16>(n->act[3], 32, n->Wb[3], 8, n->params + n->boff[3], g, 1, 0, nullptr, nullptr, n->out,
+                             n->derr, s)));
+        return GF_OK;
+    }
+    NCK((conv_cc<80, 32>(f, n->Wb[0], n->params + n->boff[0], g, 1, 1, nullptr, n->act[1], nullptr, s)));
+    NCK((conv_cc<32, 32>(n->act[1], n->Wb[1], n->params + n->boff[1], g, 1, 1, nullptr, n->act[2], nullptr, s)));
+    NCK((conv_cc<32, 32>(n->act[2], n->Wb[2], n->params + n->boff[2], g, 1, 1, nullptr, n->act[3], nullptr, s)));
+    NCK((conv_cc<32, 8>(n->act[3], n->Wb[3], n->params + n->boff[3], g, 1, 0, nullptr, nullptr, n->out, s)));
+    return GF_OK;
+}
+
+// backward data of layer l (l = 3, 2, 1): dX = conv^T(dY) masked by act[l] > 0
+static int backward_data(gf_net *n, int l, const bf16 *dY, bf16 *dX)
+{
+    const Lat &g = n->g;
+    cudaStream_t s = n->stream;
+    if (l == 3) {
+        if (n->use_tc) NCK((conv_tc<16, 32>(dY, 8, n->Wt[3], 32, nullptr, g, -1, 0, n->act[3], dX, nullptr, n->derr, s)));
+        else NCK((conv_cc<8, 32>(dY, n->Wt[3], nullptr, g, -1, 0, n->act[3], dX, nullptr, s)));
+    } else {
+        if (n->use_tc) NCK((conv_tc<32, 32>(dY, 32, n->Wt[l], 32, nullptr, g, -1, 0, n->act[l], dX, nullptr, n->derr, s)));
+        else NCK((conv_cc<32, 32>(dY, n->Wt[l], nullptr, g, -1, 0, n->act[l], dX, nullptr, s)));
+    }
+    return GF_OK;
+}
+
+static int check_status(gf_net *n)
+{
+    int e = 0;
+    NCK(cudaMemcpyAsync(&e, n->derr, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
+    NCK(cudaStreamSynchronize(n->stream));
+    if (e) {
+        cudaMemsetAsync(n->derr, 0, sizeof(int), n->stream);
+        return nfail(n, e, "a bounded wait expired in a tensor-core convolution");
+    }
+    return GF_OK;
+}
+
+// forward + loss + backward into n->grad; loss left in n->dloss (device)
+static int backward(gf_net *n, const bf16 *f, const float *target)
+{
+    const Lat &g = n->g;
+    cudaStream_t s = n->stream;
+    int r = forward(n, f);
+    if (r != GF_OK) return r;
+    long nout = (long)g.V * 8;
+    int nblk = 512;
+    k_mse<<<nblk, 256, 0, s>>>(n->out, target, nout, 1.0f / (float)nout, n->dA, n->partial);
+    NCK(cudaGetLastError());
+    k_sum_partials<<<1, 32, 0, s>>>(n->partial, nblk, 1.0 / (double)nout, n->dloss);
+    NCK(cudaGetLastError());
+    NCK(cudaMemsetAsync(n->grad, 0, sizeof(float) * n->np, s));
+    // layer 4: dY = dA [V][8]
+    NCK((conv_dw<32, 8>(n->dA, n->act[3], g, n->grad + n->woff[3], n->grad + n->boff[3], s)));
+    r = backward_data(n, 3, n->dA, n->dB);
+    if (r != GF_OK) return r;
+    // layer 3
+    NCK((conv_dw<32, 32>(n->dB, n->act[2], g, n->grad + n->woff[2], n->grad + n->boff[2], s)));
+    r = backward_data(n, 2, n->dB, n->dA);
+    if (r != GF_OK) return r;
+    // layer 2
+    NCK((conv_dw<32, 32>(n->dA, n->act[1], g, n->grad + n->woff[1], n->grad + n->boff[1], s)));
+    r = backward_data(n, 1, n->dA, n->dB);
+    if (r != GF_OK) return r;
+    // layer 1 (no input gradient needed)
+    NCK((conv_dw<80, 32>(n->dB, f, g, n->grad + n->woff[0], n->grad + n->boff[0], s)));
+    return GF_OK;
+}
+
+static bool device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+extern "C" {
+
+size_t gf_net_param_count(void) { return (size_t)param_count(); }
+
+int gf_net_create(const int dims[4], gf_net **out)
+{
+    if (!dims || !out) return GF_EINVAL;
+    *out = nullptr;
+    long V = 1;
+    for (int m = 0; m < 4; ++m) {
+        if (dims[m] < 3) return GF_EINVAL;
+        V *= dims[m];
+    }
+    if (V >= (1L << 31)) return GF_EINVAL;
+    gf_net *n = new (std::nothrow) gf_net;
+    if (!n) return GF_ENOMEM;
+    for (int m = 0; m < 4; ++m) n->g.L[m] = dims[m];
+    n->g.V = (int)V;
+    long off = 0;
+    for (int l = 0; l < 4; ++l) {
+        n->woff[l] = off;
+        off += 81L * kC[l + 1] * kC[l];
+        n->boff[l] = off;
+        off += kC[l + 1];
+    }
+    n->np = off;
+    *out = n;
+    return GF_OK;
+}
+
+static int ensure_buffers(gf_net *n)
+{
+    if (n->params) return GF_OK;
+    long V = n->g.V;
+    NCK(cudaMalloc(&n->params, sizeof(float) * n->np));
+    NCK(cudaMalloc(&n->grad, sizeof(float) * n->np));
+    NCK(cudaMalloc(&n->m, sizeof(float) * n->np));
+    NCK(cudaMalloc(&n->v, sizeof(float) * n->np));
+    for (int l = 0; l < 4; ++l) {
+        long cnt = 81L * kC[l + 1] * kC[l];
+        NCK(cudaMalloc(&n->Wb[l], sizeof(bf16) * cnt));
+        NCK(cudaMalloc(&n->Wt[l], sizeof(bf16) * cnt));
+    }
+    for (int l = 1; l < 4; ++l) NCK(cudaMalloc(&n->act[l], sizeof(bf16) * V * 32));
+    NCK(cudaMalloc(&n->out, sizeof(float) * V * 8));
+    NCK(cudaMalloc(&n->dA, sizeof(bf16) * V * 32));
+    NCK(cudaMalloc(&n->dB, sizeof(bf16) * V * 32));
+    NCK(cudaMalloc(&n->partial, sizeof(double) * 1024));
+    NCK(cudaMalloc(&n->dloss, sizeof(double)));
+    NCK(cudaMalloc(&n->derr, sizeof(int)));
+    NCK(cudaMemset(n->derr, 0, sizeof(int)));
+    return GF_OK;
+}
+
+int gf_net_destroy(gf_net *n)
+{
+    if (!n) return GF_OK;
+    cudaFree(n->params);
+    cudaFree(n->grad);
+    cudaFree(n->m);
+    cudaFree(n->v);
+    for (int l = 0; l < 4; ++l) {
+        cudaFree(n->Wb[l]);
+        cudaFree(n->Wt[l]);
+    }
+    for (int l = 1; l < 4; ++l) cudaFree(n->act[l]);
+    cudaFree(n->out);
+    cudaFree(n->dA);
+    cudaFree(n->dB);
+    cudaFree(n->partial);
+    cudaFree(n->dloss);
+    cudaFree(n->derr);
+    delete n;
+    return GF_OK;
+}
+
+const char *gf_net_last_error(const gf_net *n) { return n ? n->err.c_str() : "null network"; }
+
+int gf_net_set_stream(gf_net *n, void *stream)
+{
+    if (!n) return GF_EINVAL;
+    n->stream = (cudaStream_t)stream;
+    return GF_OK;
+}
+
+int gf_net_set_params(gf_net *n, const float *params)
+{
+    if (!n || !params) return GF_EINVAL;
+    int r = ensure_buffers(n);
+    if (r != GF_OK) return r;
+    NCK(cudaMemcpyAsync(n->params, params, sizeof(float) * n->np, cudaMemcpyDefault, n->stream));
+    NCK(cudaMemsetAsync(n->m, 0, sizeof(float) * n->np, n->stream));
+    NCK(cudaMemsetAsync(n->v, 0, sizeof(float) * n->np, n->stream));
+    n->step = 0;
+    r = refresh_weights(n);
+    if (r != GF_OK) return r;
+    NCK(cudaStreamSynchronize(n->stream));
+    return GF_OK;
+}
+
+int gf_net_get_params(gf_net *n, float *params)
+{
+    if (!n || !params) return GF_EINVAL;
+    if (!n->params) return nfail(n, GF_ESTATE, "parameters not set");
+    NCK(cudaMemcpyAsync(params, n->params, sizeof(float) * n->np, cudaMemcpyDefault, n->stream));
+    NCK(cudaStreamSynchronize(n->stream));
+    return GF_OK;
+}
+
+int gf_net_forward(gf_net *n, const void *features, float *out)
+{
+    if (!n || !features || !out) return GF_EINVAL;
+    if (!n->params) return nfail(n, GF_ESTATE, "parameters not set");
+    if (!device_ptr(features) || !device_ptr(out)) return nfail(n, GF_EINVAL, "device pointers required");
+    int r = forward(n, static_cast<const bf16 *>(features));
+    if (r != GF_OK) return r;
+    NCK(cudaMemcpyAsync(out, n->out, sizeof(float) * n->g.V * 8, cudaMemcpyDeviceToDevice, n->stream));
+    return check_status(n);
+}
+
+int gf_net_set_option(gf_net *n, const char *key, double value)
+{
+    if (!n || !key) return GF_EINVAL;
+    if (std::string(key) == "tensor_cores") {
+        n->use_tc = value != 0.0;
+        return GF_OK;
+    }
+    return nfail(n, GF_EINVAL, std::string("unknown option ") + key);
+}
+
+int gf_net_gradient(gf_net *n, const void *features, const float *target, float *grad, double *loss)
+{
+    if (!n || !features || !target) return GF_EINVAL;
+    if (!n->params) return nfail(n, GF_ESTATE, "parameters not set");
+    if (!device_ptr(features) || !device_ptr(target)) return nfail(n, GF_EINVAL, "device pointers required");
+    int r = backward(n, static_cast<const bf16 *>(features), target);
+    if (r != GF_OK) return r;
+    if (grad) NCK(cudaMemcpyAsync(grad, n->grad, sizeof(float) * n->np, cudaMemcpyDefault, n->stream));
+    if (loss) NCK(cudaMemcpyAsync(loss, n->dloss, sizeof(double), cudaMemcpyDefault, n->stream));
+    return check_status(n);
+}
+
+int gf_net_train_step(gf_net *n, const void *features, const float *target, float lr, double *loss)
+{
+    if (!n || !features || !target || !(lr > 0.0f)) return GF_EINVAL;
+    if (!n->params) return nfail(n, GF_ESTATE, "parameters not set");
+    int r = backward(n, static_cast<const bf16 *>(features), target);
+    if (r != GF_OK) return r;
+    n->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    float c1 = 1.0f / (1.0f - powf(b1, (float)n->step));
+    float c2 = 1.0f / (1.0f - powf(b2, (float)n->step));
+    k_adam<<<(int)((n->np + 255) / 256), 256, 0, n->stream>>>(n->params, n->grad, n->m, n->v, n->np, lr, b1, b2,
+                                                              1e-8f, c1, c2);
+    NCK(cudaGetLastError());
+    r = refresh_weights(n);
+    if (r != GF_OK) return r;
+    if (loss) NCK(cudaMemcpyAsync(loss, n->dloss, sizeof(double), cudaMemcpyDefault, n->stream));
+    return check_status(n);
+}
+
+}  // extern "C"

@@ -20,19 +20,223 @@ namespace gf {
 
 enum Mode { MODE_OR = 0, MODE_SA = 1 };
 
+// ---------------------------------------------------------------------------
+// accumulate form (one thread per site)
+// ---------------------------------------------------------------------------
+// Because every rotation acts on the rows of all eight held matrices X_l
+// (U_mu(x) and U_mu(x-mu)^dagger), M = sum_l X_l transforms as M -> R M: the
+// three subgroup steps of Alg. 1 can run on M alone while G = R3 R2 R1 is
+// accumulated, and G is applied once per link at the end.  Same arithmetic
+// result as the per-subgroup form in exact arithmetic; fewer operations, one
+// thread per site, and the links are read a second time (from cache) instead
+// of being held in registers.
+
+// re-read of a stored link (volatile: not merged with the first read)
+template <int FMT>
+__device__ __forceinline__ void reload(const FieldRef &f, int pl0, int h, mat3<typename Store<FMT>::T> &u);
+
+template <>
+__device__ __forceinline__ void reload<F64_18>(const FieldRef &f, int pl0, int h, mat3<double> &u)
+{
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const double2 *p = reinterpret_cast<const double2 *>(f.base + (pl0 + c) * f.plane_bytes) + h;
+        double2 v;
+        asm volatile("ld.global.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+        u.e[c / 3][c % 3] = mk<double>(v.x, v.y);
+    }
+}
+
+template <>
+__device__ __forceinline__ void reload<F64_12>(const FieldRef &f, int pl0, int h, mat3<double> &u)
+{
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const double2 *p = reinterpret_cast<const double2 *>(f.base + (pl0 + c) * f.plane_bytes) + h;
+        double2 v;
+        asm volatile("ld.global.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+        u.e[c / 3][c % 3] = mk<double>(v.x, v.y);
+    }
+    rebuild_row2(u);
+}
+
+template <>
+__device__ __forceinline__ void reload<F32_18>(const FieldRef &f, int pl0, int h, mat3<float> &u)
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float4 *p = reinterpret_cast<const float4 *>(f.base + (pl0 + c) * f.plane_bytes) + h;
+        float4 v;
+        asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+        int e0 = 2 * c, e1 = 2 * c + 1;
+        u.e[e0 / 3][e0 % 3] = mk<float>(v.x, v.y);
+        u.e[e1 / 3][e1 % 3] = mk<float>(v.z, v.w);
+    }
+    const float2 *p = reinterpret_cast<const float2 *>(f.base + (pl0 + 4) * f.plane_bytes) + h;
+    float2 v;
+    asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    u.e[2][2] = mk<float>(v.x, v.y);
+}
+
+template <>
+__device__ __forceinline__ void reload<F32_12>(const FieldRef &f, int pl0, int h, mat3<float> &u)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float4 *p = reinterpret_cast<const float4 *>(f.base + (pl0 + c) * f.plane_bytes) + h;
+        float4 v;
+        asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+        int e0 = 2 * c, e1 = 2 * c + 1;
+        u.e[e0 / 3][e0 % 3] = mk<float>(v.x, v.y);
+        u.e[e1 / 3][e1 % 3] = mk<float>(v.z, v.w);
+    }
+    rebuild_row2(u);
+}
+
+// z = x y for 3x3 complex matrices; rows >= ROWS of z are not computed
+template <class T, int ROWS>
+__device__ __forceinline__ void mul_rows(const mat3<T> &x, const mat3<T> &y, mat3<T> &z)
+{
+#pragma unroll
+    for (int a = 0; a < ROWS; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            T re = x.e[a][0].re * y.e[0][b].re - x.e[a][0].im * y.e[0][b].im;
+            T im = x.e[a][0].re * y.e[0][b].im + x.e[a][0].im * y.e[0][b].re;
+#pragma unroll
+            for (int c = 1; c < 3; ++c) {
+                re += x.e[a][c].re * y.e[c][b].re - x.e[a][c].im * y.e[c][b].im;
+                im += x.e[a][c].re * y.e[c][b].im + x.e[a][c].im * y.e[c][b].re;
+            }
+            z.e[a][b] = mk<T>(re, im);
+        }
+}
+
+// z = x y^dagger, rows >= ROWS of z not computed
+template <class T, int ROWS>
+__device__ __forceinline__ void mul_rows_dagger(const mat3<T> &x, const mat3<T> &y, mat3<T> &z)
+{
+#pragma unroll
+    for (int a = 0; a < ROWS; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            // sum_c x[a][c] conj(y[b][c])
+            T re = x.e[a][0].re * y.e[b][0].re + x.e[a][0].im * y.e[b][0].im;
+            T im = x.e[a][0].im * y.e[b][0].re - x.e[a][0].re * y.e[b][0].im;
+#pragma unroll
+            for (int c = 1; c < 3; ++c) {
+                re += x.e[a][c].re * y.e[b][c].re + x.e[a][c].im * y.e[b][c].im;
+                im += x.e[a][c].im * y.e[b][c].re - x.e[a][c].re * y.e[b][c].im;
+            }
+            z.e[a][b] = mk<T>(re, im);
+        }
+}
+
+template <int FMT, bool COULOMB, int MODE, bool TRACKG>
+__device__ __forceinline__ void sweep_site_acc(const SweepArgs &a, int h)
+{
+    typedef Store<FMT> S;
+    typedef typename S::T T;
+    constexpr int ROWS = S::REALS == 12 ? 2 : 3;  // rows of a link that are stored
+    const int p = a.parity;
+    int c[4];
+    site_coords(a.g, p, h, c);
+    int hb[4];
+    // M = sum over the gauge's directions of U_mu(x) + U_mu(x-mu)^dagger
+    mat3<T> M;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M.e[i][j] = mk<T>(T(0), T(0));
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        hb[mu] = back_half(a.g, c, mu);
+        if (COULOMB && mu == 3) continue;
+        mat3<T> u;
+        S::load(a.f, (p * 4 + mu) * S::NCHUNK, h, u);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                M.e[i][j].re += u.e[i][j].re;
+                M.e[i][j].im += u.e[i][j].im;
+            }
+        S::load(a.f, ((p ^ 1) * 4 + mu) * S::NCHUNK, hb[mu], u);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                M.e[i][j].re += u.e[j][i].re;
+                M.e[i][j].im -= u.e[j][i].im;
+            }
+    }
+    const uint32_t site = (uint32_t)lex_index(a.g, c);
+    mat3<T> G = identity3<T>();
+#pragma unroll
+    for (int sg = 0; sg < 3; ++sg) {
+        int ra, rb;
+        subgroup_rows(sg, ra, rb);
+        T k[4] = { T(0), T(0), T(0), T(0) };
+        add_block_quaternion(M, ra, rb, k);
+        T r[4];
+        bool ok;
+        if (MODE == MODE_OR) {
+            ok = overrelax_quat(k, (T)a.omega, r);
+        } else {
+            double kd[4] = { (double)k[0], (double)k[1], (double)k[2], (double)k[3] };
+            double rd[4];
+            int st = heatbath_quat(kd, a.T, site, a.sweep, sg, a.cap, a.key, rd);
+            if (st == 0) atomicAdd(a.status, 1);
+            ok = (st == 1);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) r[i] = (T)rd[i];
+        }
+        if (ok) {
+            rotate_rows(M, ra, rb, r);
+            rotate_rows(G, ra, rb, r);
+        }
+    }
+    // apply G: U_mu(x) <- G U_mu(x), U_mu(x-mu) <- U_mu(x-mu) G^dagger
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        mat3<T> u, v;
+        reload<FMT>(a.f, (p * 4 + mu) * S::NCHUNK, h, u);
+        mul_rows<T, ROWS>(G, u, v);
+        S::store(a.f, (p * 4 + mu) * S::NCHUNK, h, v);
+        reload<FMT>(a.f, ((p ^ 1) * 4 + mu) * S::NCHUNK, hb[mu], u);
+        mul_rows_dagger<T, ROWS>(u, G, v);
+        S::store(a.f, ((p ^ 1) * 4 + mu) * S::NCHUNK, hb[mu], v);
+    }
+    if (TRACKG) {
+        mat3<float> gx, gy;
+        Store<F32_12>::load(a.gt, p * 3, h, gx);
+        mat3<float> Gf;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Gf.e[i][j] = mk<float>((float)G.e[i][j].re, (float)G.e[i][j].im);
+        mul_rows<float, 2>(Gf, gx, gy);
+        Store<F32_12>::store(a.gt, p * 3, h, gy);
+    }
+}
+
+// mask of the TPS lanes that serve one site (all in the same warp)
+template <int TPS>
+__device__ __forceinline__ unsigned site_group_mask()
+{
+    const unsigned lane = threadIdx.x & 31u;
+    return (TPS == 1) ? (1u << lane) : (((1u << TPS) - 1u) << (lane & ~(unsigned)(TPS - 1)));
+}
+
+// The update of half-site h of parity a.parity by lane j (0 <= j < TPS) of its
+// site group: load the 8 links, three subgroup steps, store.
 template <int FMT, int TPS, bool COULOMB, int MODE, bool TRACKG>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
+__device__ __forceinline__ void sweep_site(const SweepArgs &a, int h, int j, unsigned gmask)
 {
     typedef Store<FMT> S;
     typedef typename S::T T;
     constexpr int NL = 8 / TPS;
     constexpr int HALF = (NL / 2 > 0) ? NL / 2 : 1;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int h = tid / TPS;
-    const int j = tid & (TPS - 1);
-    if (h >= a.g.Vh) return;
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned gmask = (TPS == 1) ? (1u << lane) : (((1u << TPS) - 1u) << (lane & ~(unsigned)(TPS - 1)));
     const int p = a.parity;
 
     int c[4];
@@ -111,12 +315,32 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
     if (TRACKG && j == 0) Store<F32_12>::store(a.gt, p * 3, h, gx);
 }
 
+template <int FMT, bool COULOMB, int MODE, bool TRACKG>
+__global__ void __launch_bounds__(256) k_sweep_acc(SweepArgs a)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= a.g.Vh) return;
+    sweep_site_acc<FMT, COULOMB, MODE, TRACKG>(a, h);
+}
+
+template <int FMT, int TPS, bool COULOMB, int MODE, bool TRACKG>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int h = tid / TPS;
+    const int j = tid & (TPS - 1);
+    if (h >= a.g.Vh) return;
+    sweep_site<FMT, TPS, COULOMB, MODE, TRACKG>(a, h, j, site_group_mask<TPS>());
+}
+
+// TPS == 0 selects the accumulate form (one thread per site)
 template <int FMT, int TPS, bool COULOMB, int MODE, bool TRACKG>
 static cudaError_t launch_k_sweep(const SweepArgs &a, int block, cudaStream_t s)
 {
-    long threads = (long)a.g.Vh * TPS;
+    long threads = (long)a.g.Vh * (TPS == 0 ? 1 : TPS);
     int grid = (int)((threads + block - 1) / block);
-    k_sweep<FMT, TPS, COULOMB, MODE, TRACKG><<<grid, block, 0, s>>>(a);
+    if (TPS == 0) k_sweep_acc<FMT, COULOMB, MODE, TRACKG><<<grid, block, 0, s>>>(a);
+    else k_sweep<FMT, (TPS == 0 ? 1 : TPS), COULOMB, MODE, TRACKG><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -136,6 +360,7 @@ template <int FMT, bool TRACKG>
 static cudaError_t dispatch_tps(const SweepArgs &a, int tps, int coulomb, int mode, int block, cudaStream_t s)
 {
     switch (tps) {
+    case 0: return dispatch_gauge_mode<FMT, 0, TRACKG>(a, coulomb, mode, block, s);
     case 1: return dispatch_gauge_mode<FMT, 1, TRACKG>(a, coulomb, mode, block, s);
     case 2: return dispatch_gauge_mode<FMT, 2, TRACKG>(a, coulomb, mode, block, s);
     case 4: return dispatch_gauge_mode<FMT, 4, TRACKG>(a, coulomb, mode, block, s);

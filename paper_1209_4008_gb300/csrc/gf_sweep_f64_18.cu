@@ -6,8 +6,8 @@ namespace gf {
 cudaError_t launch_sweep_f64_18(const SweepArgs &a, int tps, int coulomb, int mode, bool trackg, int block,
                               cudaStream_t s)
 {
-    if (trackg) return cudaErrorInvalidValue;  // g is tracked only in the FP32 phase
-    return dispatch_tps<F64_18, false>(a, tps, coulomb, mode, block, s);
+    return trackg ? dispatch_tps<F64_18, true>(a, tps, coulomb, mode, block, s)
+                  : dispatch_tps<F64_18, false>(a, tps, coulomb, mode, block, s);
 }
 
 }  // namespace gf

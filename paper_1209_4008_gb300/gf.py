@@ -65,6 +65,34 @@ SIGNATURES = {
     "gf_reunitarize": (C.c_int, [_vp]),
     "gf_autotune": (C.c_int, [_vp, _ip, _ip]),
     "gf_measure_noalloc": (C.c_int, [_ip, C.c_int, _vp, _vp, _vp]),
+    "gf_batch_create": (C.c_int, [C.c_int, _ip, C.c_int, C.POINTER(_vp)]),
+    "gf_batch_destroy": (C.c_int, [_vp]),
+    "gf_batch_last_error": (C.c_char_p, [_vp]),
+    "gf_batch_set_stream": (C.c_int, [_vp, _vp]),
+    "gf_batch_set_option": (C.c_int, [_vp, C.c_char_p, C.c_double]),
+    "gf_batch_get_stat": (C.c_int, [_vp, C.c_char_p, _dp]),
+    "gf_batch_overrelax": (C.c_int, [_vp, C.POINTER(_vp), C.c_double, C.c_double, C.c_int, _ip, _dp,
+                                     _dp]),
+    "gf_batch_autotune": (C.c_int, [_vp, C.POINTER(_vp), _ip, _ip]),
+    "gf_net_param_count": (C.c_size_t, []),
+    "gf_net_create": (C.c_int, [_ip, C.POINTER(_vp)]),
+    "gf_net_destroy": (C.c_int, [_vp]),
+    "gf_net_last_error": (C.c_char_p, [_vp]),
+    "gf_net_set_stream": (C.c_int, [_vp, _vp]),
+    "gf_net_set_params": (C.c_int, [_vp, _vp]),
+    "gf_net_get_params": (C.c_int, [_vp, _vp]),
+    "gf_net_forward": (C.c_int, [_vp, _vp, _vp]),
+    "gf_net_gradient": (C.c_int, [_vp, _vp, _vp, _vp, _dp]),
+    "gf_net_train_step": (C.c_int, [_vp, _vp, _vp, C.c_float, _dp]),
+    "gf_net_set_option": (C.c_int, [_vp, C.c_char_p, C.c_double]),
+    "gf_gauge_reset": (C.c_int, [_vp]),
+    "gf_get_gauge": (C.c_int, [_vp, _vp]),
+    "gf_converge": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int, _ip, _dp, _dp]),
+    "gf_apply_tracked_gauge": (C.c_int, [_vp, _vp]),
+    "gf_features": (C.c_int, [_vp, C.c_double, _vp]),
+    "gf_gauge_algebra": (C.c_int, [_vp, C.c_double, _vp]),
+    "gf_apply_algebra": (C.c_int, [_vp, _vp, C.c_double]),
+    "gf_set_net": (C.c_int, [_vp, _vp]),
 }
 
 
@@ -277,3 +305,203 @@ def gf_measure_noalloc(dims, gauge: int, U, out, stream=None) -> int:
     s = getattr(stream, "cuda_stream", stream)
     return lib.gf_measure_noalloc(arr, int(gauge), _ptr(U), _ptr(out), s or None)
 
+
+class Batch:
+    """Owns a gf_batch handle (n lattices gauge-fixed in one persistent launch)."""
+
+    def __init__(self, dims_list, gauge: int = GF_LANDAU):
+        self.lib = load()
+        self.n = len(dims_list)
+        flat = [int(d) for dims in dims_list for d in dims]
+        arr = (C.c_int * len(flat))(*flat)
+        h = _vp()
+        rc = self.lib.gf_batch_create(self.n, arr, int(gauge), C.byref(h))
+        if rc != GF_OK:
+            raise GFError(rc, "gf_batch_create")
+        self.handle = h
+
+    def check(self, rc: int, what: str, ok=(GF_OK,)) -> int:
+        if rc not in ok:
+            msg = self.lib.gf_batch_last_error(self.handle)
+            raise GFError(rc, f"{what}: {msg.decode() if msg else ''}")
+        return rc
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            self.lib.gf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gf_batch_create(dims_list, gauge: int = GF_LANDAU) -> Batch:
+    return Batch(dims_list, gauge)
+
+
+def gf_batch_destroy(b: Batch) -> None:
+    b.close()
+
+
+def gf_batch_set_stream(b: Batch, stream) -> None:
+    s = getattr(stream, "cuda_stream", stream)
+    b.check(b.lib.gf_batch_set_stream(b.handle, s or None), "gf_batch_set_stream")
+
+
+def gf_batch_set_option(b: Batch, key: str, value: float) -> None:
+    b.check(b.lib.gf_batch_set_option(b.handle, key.encode(), float(value)), f"option {key}")
+
+
+def gf_batch_get_stat(b: Batch, key: str) -> float:
+    v = C.c_double()
+    b.check(b.lib.gf_batch_get_stat(b.handle, key.encode(), C.byref(v)), f"stat {key}")
+    return v.value
+
+
+def _ptr_array(fields):
+    return (_vp * len(fields))(*[_ptr(u) for u in fields])
+
+
+def gf_batch_overrelax(b: Batch, fields, omega: float, theta_target: float, max_iter: int,
+                       raise_on_error: bool = True):
+    """Returns (rc, iters, F, theta) with per-lattice lists; fields fixed in place."""
+    n = b.n
+    it = (C.c_int * n)()
+    F = (C.c_double * n)()
+    th = (C.c_double * n)()
+    rc = b.lib.gf_batch_overrelax(b.handle, _ptr_array(fields), omega, theta_target, int(max_iter),
+                                  it, F, th)
+    if raise_on_error:
+        b.check(rc, "gf_batch_overrelax", ok=(GF_OK, GF_ENOTCONVERGED))
+    return rc, list(it), list(F), list(th)
+
+
+def gf_batch_autotune(b: Batch, fields):
+    t, k = C.c_int(), C.c_int()
+    b.check(b.lib.gf_batch_autotune(b.handle, _ptr_array(fields), C.byref(t), C.byref(k)),
+            "gf_batch_autotune")
+    return t.value, k.value
+
+
+# ---------------------------------------------------------------------------
+# learned warm start
+# ---------------------------------------------------------------------------
+GF_NET_CIN, GF_NET_COUT = 80, 8
+NET_CHANNELS = (80, 32, 32, 32, 8)
+
+
+def gf_net_param_count() -> int:
+    return int(load().gf_net_param_count())
+
+
+class Net:
+    """Owns a gf_net handle."""
+
+    def __init__(self, dims):
+        self.lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        h = _vp()
+        rc = self.lib.gf_net_create((C.c_int * 4)(*self.dims), C.byref(h))
+        if rc != GF_OK:
+            raise GFError(rc, "gf_net_create")
+        self.handle = h
+
+    def check(self, rc: int, what: str) -> int:
+        if rc != GF_OK:
+            msg = self.lib.gf_net_last_error(self.handle)
+            raise GFError(rc, f"{what}: {msg.decode() if msg else ''}")
+        return rc
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            self.lib.gf_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gf_net_create(dims) -> Net:
+    return Net(dims)
+
+
+def gf_net_destroy(n: Net) -> None:
+    n.close()
+
+
+def gf_net_set_stream(n: Net, stream) -> None:
+    s = getattr(stream, "cuda_stream", stream)
+    n.check(n.lib.gf_net_set_stream(n.handle, s or None), "gf_net_set_stream")
+
+
+def gf_net_set_option(n: Net, key: str, value: float) -> None:
+    n.check(n.lib.gf_net_set_option(n.handle, key.encode(), float(value)), f"option {key}")
+
+
+def gf_net_set_params(n: Net, params) -> None:
+    n.check(n.lib.gf_net_set_params(n.handle, _ptr(params)), "gf_net_set_params")
+
+
+def gf_net_get_params(n: Net, params) -> None:
+    n.check(n.lib.gf_net_get_params(n.handle, _ptr(params)), "gf_net_get_params")
+
+
+def gf_net_forward(n: Net, features, out) -> None:
+    n.check(n.lib.gf_net_forward(n.handle, _ptr(features), _ptr(out)), "gf_net_forward")
+
+
+def gf_net_gradient(n: Net, features, target, grad=None) -> float:
+    loss = C.c_double()
+    n.check(n.lib.gf_net_gradient(n.handle, _ptr(features), _ptr(target), _ptr(grad), C.byref(loss)),
+            "gf_net_gradient")
+    return loss.value
+
+
+def gf_net_train_step(n: Net, features, target, lr: float) -> float:
+    loss = C.c_double()
+    n.check(n.lib.gf_net_train_step(n.handle, _ptr(features), _ptr(target), float(lr), C.byref(loss)),
+            "gf_net_train_step")
+    return loss.value
+
+
+def gf_gauge_reset(ctx: Context) -> None:
+    ctx.check(ctx.lib.gf_gauge_reset(ctx.handle), "gf_gauge_reset")
+
+
+def gf_get_gauge(ctx: Context, g) -> None:
+    ctx.check(ctx.lib.gf_get_gauge(ctx.handle, _ptr(g)), "gf_get_gauge")
+
+
+def gf_converge(ctx: Context, omega: float, theta_target: float, max_iter: int):
+    it, F, th = C.c_int(), C.c_double(), C.c_double()
+    rc = ctx.check(ctx.lib.gf_converge(ctx.handle, omega, theta_target, int(max_iter), C.byref(it),
+                                       C.byref(F), C.byref(th)), "gf_converge",
+                   ok=(GF_OK, GF_ENOTCONVERGED))
+    return rc == GF_OK, it.value, F.value, th.value
+
+
+def gf_apply_tracked_gauge(ctx: Context, U) -> None:
+    _check_field(ctx, U)
+    ctx.check(ctx.lib.gf_apply_tracked_gauge(ctx.handle, _ptr(U)), "gf_apply_tracked_gauge")
+
+
+def gf_features(ctx: Context, scale: float, features) -> None:
+    ctx.check(ctx.lib.gf_features(ctx.handle, float(scale), _ptr(features)), "gf_features")
+
+
+def gf_gauge_algebra(ctx: Context, scale: float, c) -> None:
+    ctx.check(ctx.lib.gf_gauge_algebra(ctx.handle, float(scale), _ptr(c)), "gf_gauge_algebra")
+
+
+def gf_apply_algebra(ctx: Context, c, scale: float) -> None:
+    ctx.check(ctx.lib.gf_apply_algebra(ctx.handle, _ptr(c), float(scale)), "gf_apply_algebra")
+
+
+def gf_set_net(ctx: Context, net) -> None:
+    ctx.check(ctx.lib.gf_set_net(ctx.handle, net.handle if net is not None else None), "gf_set_net")

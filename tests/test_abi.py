@@ -73,3 +73,31 @@ def test_host_side_argument_checks(lib):
         assert lib.gf_destroy(h) == gf.GF_OK
     assert lib.gf_destroy(None) == gf.GF_OK
     assert lib.gf_error_string(gf.GF_ENOTCONVERGED) == b"GF_ENOTCONVERGED"
+
+
+def test_batch_handle_host_side(lib):
+    b = gf.gf_batch_create([(4, 4, 4, 4), (8, 8, 8, 8)], gf.GF_LANDAU)
+    gf.gf_batch_set_option(b, "precision", gf.GF_FP64)
+    gf.gf_batch_set_option(b, "check_every", 10)
+    with pytest.raises(gf.GFError):
+        gf.gf_batch_set_option(b, "threads_per_site", 3)
+    with pytest.raises(gf.GFError):
+        gf.gf_batch_set_option(b, "no_such_option", 1)
+    gf.gf_batch_destroy(b)
+    with pytest.raises(gf.GFError):
+        gf.gf_batch_create([(4, 4, 4, 5)])
+    h = C.c_void_p()
+    assert lib.gf_batch_create(0, (C.c_int * 4)(4, 4, 4, 4), 0, C.byref(h)) == gf.GF_EINVAL
+
+
+def test_binding_argument_counts_match_header():
+    text = ""
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text += re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b(gf_\w+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        args = m.group(2).strip()
+        protos[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    for name, (_, argtypes) in gf.SIGNATURES.items():
+        assert name in protos, name
+        assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])

@@ -1,0 +1,224 @@
+"""Learned warm start on the GPU against the oracle.
+
+Tolerances: BF16 stores 8 significant bits (relative rounding <= 2^-9); the
+network inputs are compared at 4e-3 relative.  The network's forward output
+and gradients use BF16 weights and activations with FP32 accumulation and are
+compared with the FP64 oracle evaluated on the same BF16-rounded weights and
+inputs: the remaining difference is the BF16 rounding of the three hidden
+activations and of the backpropagated gradients (~0.2-0.4 % each), so the
+relative L2 error bound is 2e-2 (output) and 5e-2 (gradient).  The applied
+gauge transformation is stored as FP32 and reprojected onto SU(3) in FP64,
+so it differs from the exact exponential by ~1e-7; it is still an exact FP64
+gauge transformation (plaquette to 1e-13).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1209_4008_gb300 import gf, learned, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def cpu_field(dims, seed=1, gseed=2):
+    return synth.as_numpy(synth.make_field(dims, 0.60, seed, gseed))
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_features_match_oracle():
+    dims = (6, 4, 6, 8)
+    U = cpu_field(dims, 3, 4)
+    oracle.or_sweeps(U, 1.7, 0, 20)
+    c = gf.gf_create(dims, 0)
+    gf.gf_upload(c, torch.from_numpy(U).cuda(), gf.GF_FP64)
+    s = math.sqrt(oracle.theta(U, 0))
+    V = int(np.prod(dims))
+    f = torch.empty(V, 80, dtype=torch.bfloat16, device="cuda")
+    gf.gf_features(c, s, f)
+    got = f.float().cpu().numpy().astype(np.float64)
+    want = oracle.features(U, s)
+    assert np.all(np.abs(got - want) <= 4e-3 * np.abs(want) + 1e-30)
+
+
+def test_apply_algebra_is_exact_gauge_transform():
+    dims = (4, 6, 4, 8)
+    U = cpu_field(dims, 5, 6)
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(0)
+    for scale in (1e-3, 0.7):
+        cc = rng.standard_normal((V, 8)).astype(np.float32)
+        ctx = gf.gf_create(dims, 0)
+        d = torch.from_numpy(U).cuda()
+        gf.gf_upload(ctx, d, gf.GF_FP64)
+        gf.gf_apply_algebra(ctx, torch.from_numpy(cc).cuda(), scale)
+        gf.gf_download(ctx, d)
+        W = U.copy()
+        g = oracle.expmap(cc.astype(np.float64), scale).reshape(U.shape[:4] + (3, 3))
+        oracle.gauge_transform(W, g)
+        assert np.abs(d.cpu().numpy() - W).max() < 1e-6
+        assert gf.gf_plaquette(ctx, d) == pytest.approx(oracle.plaquette(U), abs=1e-13)
+
+
+def test_tracked_gauge_and_labels():
+    dims = (8, 8, 8, 8)
+    U0 = cpu_field(dims, 7, 8)
+    for prec in (gf.GF_FP32, gf.GF_FP64):
+        ctx = gf.gf_create(dims, 0)
+        gf.gf_set_option(ctx, "track", 1)
+        d = torch.from_numpy(U0).cuda()
+        gf.gf_upload(ctx, d, prec)
+        gf.gf_gauge_reset(ctx)
+        gf.gf_or_sweeps(ctx, 1.7, 30)
+        gf.gf_download(ctx, d)
+        g = np.zeros(U0.shape[:4] + (3, 3), dtype=np.complex128)
+        gf.gf_get_gauge(ctx, g)
+        W = U0.copy()
+        oracle.gauge_transform(W, g)  # U_now must equal g U0 g^+ (g tracked in FP32)
+        assert np.abs(d.cpu().numpy() - W).max() < (2e-5 if prec == gf.GF_FP32 else 2e-6)
+        s = 0.01
+        lab = torch.empty(int(np.prod(dims)), 8, dtype=torch.float32, device="cuda")
+        gf.gf_gauge_algebra(ctx, s, lab)
+        want = oracle.algebra_log(g.reshape(-1, 3, 3), s)
+        np.testing.assert_allclose(lab.cpu().numpy(), want, rtol=1e-5, atol=1e-4)
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def test_network_forward_and_gradient_match_oracle():
+    dims = (4, 4, 4, 6)
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(1)
+    ch = gf.NET_CHANNELS
+    P = gf.gf_net_param_count()
+    assert P == oracle.net_param_count(ch)
+    params = learned.init_params(3, scale_last=1.0)
+    # biases non-zero to exercise them
+    off = 0
+    for l in range(4):
+        off += 81 * ch[l + 1] * ch[l]
+        params[off:off + ch[l + 1]] = rng.standard_normal(ch[l + 1]) * 0.1
+        off += ch[l + 1]
+    feats = bf16_round(rng.standard_normal((V, 80)))
+    target = rng.standard_normal((V, 8)).astype(np.float32)
+    net = gf.gf_net_create(dims)
+    gf.gf_net_set_params(net, params)
+    fd = torch.from_numpy(feats).to(torch.bfloat16).cuda()
+    td = torch.from_numpy(target).cuda()
+    out = torch.empty(V, 8, dtype=torch.float32, device="cuda")
+    gf.gf_net_forward(net, fd, out)
+    grad = np.zeros(P, dtype=np.float32)
+    loss = gf.gf_net_gradient(net, fd, td, grad)
+    # oracle on the BF16-rounded weights (biases stay FP32)
+    pq = params.astype(np.float64).copy()
+    off = 0
+    for l in range(4):
+        n = 81 * ch[l + 1] * ch[l]
+        pq[off:off + n] = bf16_round(params[off:off + n])
+        off += n + ch[l + 1]
+    oloss, ograd, oout = oracle.net_loss(feats, target, pq, dims, ch)
+    assert rel_l2(out.cpu().numpy(), oout) < 2e-2
+    assert loss == pytest.approx(oloss, rel=2e-2)
+    off = 0
+    for l in range(4):
+        n = 81 * ch[l + 1] * ch[l]
+        assert rel_l2(grad[off:off + n], ograd[off:off + n]) < 5e-2, l
+        assert rel_l2(grad[off + n:off + n + ch[l + 1]], ograd[off + n:off + n + ch[l + 1]]) < 5e-2, l
+        off += n + ch[l + 1]
+
+
+def test_training_reduces_loss():
+    """A student network fits the outputs of a teacher network (a target the
+    architecture can represent)."""
+    dims = (4, 4, 4, 4)
+    V = 256
+    rng = np.random.default_rng(2)
+    feats = torch.from_numpy(bf16_round(rng.standard_normal((V, 80)))).to(torch.bfloat16).cuda()
+    teacher = gf.gf_net_create(dims)
+    gf.gf_net_set_params(teacher, learned.init_params(11, scale_last=1.0))
+    target = torch.empty(V, 8, dtype=torch.float32, device="cuda")
+    gf.gf_net_forward(teacher, feats, target)
+    net = gf.gf_net_create(dims)
+    gf.gf_net_set_params(net, learned.init_params(4))
+    l0 = gf.gf_net_gradient(net, feats, target)
+    for _ in range(150):
+        gf.gf_net_train_step(net, feats, target, 1e-3)
+    assert gf.gf_net_gradient(net, feats, target) < 0.5 * l0
+
+
+def test_tensor_core_and_cuda_core_convolutions_agree():
+    dims = (4, 6, 4, 8)
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(3)
+    feats = torch.from_numpy(bf16_round(rng.standard_normal((V, 80)))).to(torch.bfloat16).cuda()
+    target = torch.from_numpy(rng.standard_normal((V, 8)).astype(np.float32)).cuda()
+    params = learned.init_params(12, scale_last=1.0)
+    outs, grads = [], []
+    for tc in (0, 1):
+        net = gf.gf_net_create(dims)
+        gf.gf_net_set_option(net, "tensor_cores", tc)
+        gf.gf_net_set_params(net, params)
+        out = torch.empty(V, 8, dtype=torch.float32, device="cuda")
+        gf.gf_net_forward(net, feats, out)
+        g = np.zeros(gf.gf_net_param_count(), dtype=np.float32)
+        gf.gf_net_gradient(net, feats, target, g)
+        outs.append(out.cpu().numpy())
+        grads.append(g)
+    # same BF16 operands, FP32 accumulation in a different order
+    assert rel_l2(outs[1], outs[0]) < 1e-2
+    assert rel_l2(grads[1], grads[0]) < 3e-2
+
+
+def test_zero_network_leaves_the_mixed_solver_unchanged():
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, 9, 10)
+    net = gf.gf_net_create(dims)
+    gf.gf_net_set_params(net, np.zeros(gf.gf_net_param_count(), dtype=np.float32))
+    res = []
+    for attach in (False, True):
+        c = gf.gf_create(dims, 0)
+        gf.gf_set_option(c, "precision", gf.GF_MIXED)
+        gf.gf_set_option(c, "check_every", 10)
+        if attach:
+            gf.gf_set_net(c, net)
+        d = torch.from_numpy(U).cuda()
+        res.append(gf.gf_overrelax(c, d, 1.7, 1e-14, 20000))
+    assert res[0][0] and res[1][0]
+    assert res[0][1] == res[1][1]
+    assert res[0][2] == pytest.approx(res[1][2], abs=1e-13)
+
+
+def test_learned_warm_start_pipeline_small():
+    """Train on solver pairs from 8^4 fields, then fix fresh fields with and
+    without the network; both must converge to the same F.  The gain (FP64
+    sweeps saved) is reported; the full-size measurement is in bench.py."""
+    dims = (8, 8, 8, 8)
+    ctx = gf.gf_create(dims, 0)
+    pairs = []
+    for k in range(6):
+        U = synth.make_field(dims, 0.60, 1000 + k, 3000 + k, device="cuda")
+        pairs.append(learned.make_pair(ctx, U, label_theta=1e-11))
+    net = gf.gf_net_create(dims)
+    gf.gf_net_set_params(net, learned.init_params(5))
+    hist = learned.train(net, pairs[:5], epochs=30, lr=1e-3)
+    assert hist[-1] < hist[0]
+    sweeps = {}
+    for attach in (False, True):
+        c = gf.gf_create(dims, 0)
+        gf.gf_set_option(c, "precision", gf.GF_MIXED)
+        gf.gf_set_option(c, "check_every", 10)
+        if attach:
+            gf.gf_set_net(c, net)
+        U = synth.make_field(dims, 0.60, 5000, 6000, device="cuda")
+        conv, it, F, th = gf.gf_overrelax(c, U, 1.7, 1e-14, 50000)
+        assert conv and th < 1e-14
+        sweeps[attach] = (gf.gf_get_stat(c, "sweeps_fp64"), F)
+    assert abs(sweeps[True][1] - sweeps[False][1]) < 1e-9
+    print("fp64 sweeps without / with the network:", sweeps[False][0], sweeps[True][0])
