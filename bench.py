@@ -377,7 +377,11 @@ def kernel_only(args):
     field = synth.make_field(dims, PLAQ, *SEEDS, device="cuda")
     c = gf.gf_create(dims, gf.GF_LANDAU)
     gf.gf_set_option(c, key, st)
-    gf.gf_set_option(c, "threads_per_site", args.tps)
+    if args.tps == 0:
+        gf.gf_set_option(c, "variant", 2)  # accumulate form, one thread per site
+    else:
+        gf.gf_set_option(c, "variant", 1)
+        gf.gf_set_option(c, "threads_per_site", args.tps)
     gf.gf_set_option(c, "block", args.block)
     gf.gf_set_option(c, "use_graphs", 0)
     gf.gf_set_stream(c, torch.cuda.current_stream())

@@ -28,10 +28,12 @@ def fields(dims_list, seed0=100):
 
 
 @pytest.mark.parametrize("gauge", [gf.GF_LANDAU, gf.GF_COULOMB])
-def test_batch_fp64_matches_oracle(gauge):
+@pytest.mark.parametrize("tps", [0, -1])
+def test_batch_fp64_matches_oracle(gauge, tps):
     host = fields(DIMS)
     dev = [torch.from_numpy(u).cuda() for u in host]
     b = gf.gf_batch_create(DIMS, gauge)
+    gf.gf_batch_set_option(b, "threads_per_site", tps)  # -1: accumulate form
     gf.gf_batch_set_option(b, "precision", gf.GF_FP64)
     gf.gf_batch_set_option(b, "check_every", 10)
     rc, iters, F, th = gf.gf_batch_overrelax(b, dev, 1.7, 1e-12, 3000)
@@ -102,7 +104,7 @@ def test_batch_autotune_keeps_results():
     dev = [torch.from_numpy(u).cuda() for u in host]
     b = gf.gf_batch_create(DIMS[:3], gf.GF_LANDAU)
     tps, block = gf.gf_batch_autotune(b, dev)
-    assert tps in (1, 2, 4, 8) and block in (64, 128, 256)
+    assert tps in (0, 1, 2, 4, 8) and block in (64, 128, 256)  # 0: accumulate form
     for d, u in zip(dev, host):
         assert torch.equal(d.cpu(), torch.from_numpy(u))  # autotuning leaves fields alone
     gf.gf_batch_set_option(b, "precision", gf.GF_FP64)

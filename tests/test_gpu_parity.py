@@ -36,6 +36,11 @@ def host(T):
 
 def ctx_for(dims, gauge=0, **opts):
     c = gf.gf_create(dims, gauge)
+    # threads_per_site = 0 in these tests selects the accumulate-form variant
+    if opts.get("threads_per_site", None) == 0:
+        opts = dict(opts)
+        del opts["threads_per_site"]
+        opts["variant"] = 2
     for k, v in opts.items():
         gf.gf_set_option(c, k, v)
     return c
@@ -50,7 +55,7 @@ def max_rel(a, b):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("dims", SMALL)
 @pytest.mark.parametrize("gauge", [0, 1])
-@pytest.mark.parametrize("tps", [1, 2, 4, 8])
+@pytest.mark.parametrize("tps", [0, 1, 2, 4, 8])
 def test_fp64_half_sweep_parity(dims, gauge, tps):
     U = cpu_field(dims, seed=3, gseed=4)
     c = ctx_for(dims, gauge, threads_per_site=tps)
@@ -65,9 +70,10 @@ def test_fp64_half_sweep_parity(dims, gauge, tps):
 
 @pytest.mark.parametrize("storage", [18, 12])
 @pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 4, 6, 10)])
-def test_fp64_sweeps_parity(storage, dims):
+@pytest.mark.parametrize("variant", [1, 2])
+def test_fp64_sweeps_parity(storage, dims, variant):
     U = cpu_field(dims, seed=5, gseed=6)
-    c = ctx_for(dims, 0, storage64=storage)
+    c = ctx_for(dims, 0, storage64=storage, variant=variant)
     d = dev(U)
     gf.gf_upload(c, d, gf.GF_FP64)
     gf.gf_or_sweeps(c, 1.7, 10)
@@ -93,7 +99,7 @@ def test_fp64_block_shapes(block):
 # FP32 storage
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("storage", [12, 18])
-@pytest.mark.parametrize("tps", [1, 2, 4, 8])
+@pytest.mark.parametrize("tps", [0, 1, 2, 4, 8])
 @pytest.mark.parametrize("gauge", [0, 1])
 def test_fp32_half_sweep_parity(storage, tps, gauge):
     dims = (8, 8, 8, 8)
@@ -207,7 +213,8 @@ def test_not_converged_is_reported_with_valid_outputs():
     assert th == pytest.approx(gf.gf_theta(c, d), rel=1e-12)
 
 
-def test_mixed_precision_reaches_same_functional():
+@pytest.mark.parametrize("variant", [1, 2])
+def test_mixed_precision_reaches_same_functional(variant):
     """FP32 (12-real) sweeps to theta < 1e-6, then FP64 to 1e-14 (config on 8^4)."""
     dims = (8, 8, 8, 8)
     U = cpu_field(dims, seed=3, gseed=4)
@@ -216,7 +223,7 @@ def test_mixed_precision_reaches_same_functional():
     conv, it64, F64, th64 = gf.gf_overrelax(c64, d64, 1.7, 1e-14, 20000)
     assert conv
     for track in (1, 0):
-        c = ctx_for(dims, 0, check_every=10, precision=gf.GF_MIXED, track_gauge=track)
+        c = ctx_for(dims, 0, check_every=10, precision=gf.GF_MIXED, track_gauge=track, variant=variant)
         d = dev(U)
         conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-14, 20000)
         assert conv and th < 1e-14
@@ -242,7 +249,7 @@ def test_fp32_policy_converges_to_fp32_precision():
 # simulated annealing
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("gauge", [0, 1])
-@pytest.mark.parametrize("tps", [1, 2, 8])
+@pytest.mark.parametrize("tps", [0, 1, 2, 8])
 @pytest.mark.parametrize("T", [1.45, 0.3, 0.01])
 def test_sa_half_sweep_parity(gauge, tps, T):
     dims = (6, 4, 6, 10)
@@ -306,7 +313,7 @@ def test_autotune_picks_a_valid_config_and_keeps_parity():
     d = dev(U)
     gf.gf_upload(c, d, gf.GF_FP64)
     tps, block = gf.gf_autotune(c)
-    assert tps in (1, 2, 4, 8) and block in (64, 128, 256)
+    assert tps in (0, 1, 2, 4, 8) and block in (64, 128, 256)  # 0: accumulate form
     gf.gf_upload(c, d, gf.GF_FP64)
     gf.gf_or_sweeps(c, 1.7, 3)
     oracle.or_sweeps(U, 1.7, 0, 3)
