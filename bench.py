@@ -290,15 +290,30 @@ def gpu_arm(args, rank, world, local):
     for name, prec, key, st, nbytes in (("fp32_12", gf.GF_FP32, "storage32", 12, 768),
                                         ("fp32_18", gf.GF_FP32, "storage32", 18, 1152),
                                         ("fp64_12", gf.GF_FP64, "storage64", 12, 1536),
-                                        ("fp64_18", gf.GF_FP64, "storage64", 18, 2304)):
+                                        ("fp64_18", gf.GF_FP64, "storage64", 18, 2304),
+                                        ("df64_18", gf.GF_FP64, "fp64_arith", 1, 2304)):
         n = 200 if prec == gf.GF_FP32 else 40
         t_half, tps, block = sweep_throughput(gf, ctx64, pristine, prec, key, st, nsweeps=n, warm=10)
         thr[name] = {"ms_per_half_sweep": t_half, "gsu_per_s": Vh / (t_half * 1e-3) / 1e9,
                      "algorithmic_gbs": Vh * nbytes / (t_half * 1e-3) / 1e9,
                      "bytes_per_site_update": nbytes,
                      "threads_per_site": tps, "block": block}
+        if key == "fp64_arith":
+            gf.gf_set_option(ctx64, "fp64_arith", 0)
     gf.gf_set_option(ctx64, "storage32", 12)
     gf.gf_set_option(ctx64, "storage64", 18)
+
+    # mixed policy with the FP64 phase in double-float arithmetic (FP32 pipe), once
+    ctxdf = make_ctx(gf, gf.GF_MIXED)
+    gf.gf_set_option(ctxdf, "fp64_arith", 1)
+    work.copy_(pristine)
+    gf.gf_overrelax(ctxdf, work, OMEGA, THETA_TARGET, MAX_ITER)  # warm-up: autotune, graphs
+    work.copy_(pristine)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    convdf, itdf, Fdf, thdf = gf.gf_overrelax(ctxdf, work, OMEGA, THETA_TARGET, MAX_ITER)
+    torch.cuda.synchronize()
+    t_df = time.perf_counter() - t0
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     host = torch.empty(pristine.shape, dtype=pristine.dtype, pin_memory=True)
@@ -349,6 +364,8 @@ def gpu_arm(args, rank, world, local):
                           "sweeps_fp64_phase": sw64 / args.steps, "sweeps_all_fp64": it64,
                           "F_mixed": F_mixed, "F_fp64": F64, "dF": abs(F_mixed - F64),
                           "theta_mixed": th_mixed, "theta_fp64": th64,
+                          "mixed_df64_s": t_df, "sweeps_mixed_df64": itdf, "F_mixed_df64": Fdf,
+                          "dF_mixed_df64": abs(Fdf - F64), "theta_mixed_df64": thdf,
                           "phase_ms": {"fp32": ms32 / args.steps, "fp64": ms64 / args.steps}},
         "sweep_throughput": thr,
         "roofline": roof,
@@ -364,7 +381,8 @@ def gpu_arm(args, rank, world, local):
 
 
 FORMATS = {"fp32_12": (1, "storage32", 12, 768), "fp32_18": (1, "storage32", 18, 1152),
-           "fp64_12": (0, "storage64", 12, 1536), "fp64_18": (0, "storage64", 18, 2304)}
+           "fp64_12": (0, "storage64", 12, 1536), "fp64_18": (0, "storage64", 18, 2304),
+           "df64_18": (0, "fp64_arith", 1, 2304)}
 
 
 def kernel_only(args):
@@ -538,6 +556,61 @@ def learned(args):
         "total_s": time.perf_counter() - t_start}), flush=True)
 
 
+COULOMB_DIMS = (48, 48, 48, 96)
+
+
+def coulomb(args):
+    """Coulomb gauge on 48^3 x 96 (FP64 links, 6.1 GB), plaquette 0.58, seeds
+    7000+k / 8000+k: simulated annealing (heatbath sweeps with T falling
+    linearly from 1.45 to 0.01, Philox key 9000+k) then FP64 overrelaxation at
+    omega 1.7 to theta < 1e-13; the same start fixed by overrelaxation alone
+    for comparison.  Reports the final F of every seed and their distribution.
+    Prints one JSON object."""
+    from paper_1209_4008_gb300 import gf, synth
+    t_start = time.perf_counter()
+    target = 1e-13
+    ctx = gf.gf_create(COULOMB_DIMS, gf.GF_COULOMB)
+    gf.gf_set_option(ctx, "precision", gf.GF_FP64)
+    gf.gf_set_option(ctx, "storage64", 18)
+    gf.gf_set_option(ctx, "check_every", CHECK_EVERY)
+    gf.gf_set_option(ctx, "autotune", 1)
+    gf.gf_set_stream(ctx, torch.cuda.current_stream())
+    V = int(np.prod(COULOMB_DIMS))
+    rows = []
+    for k in range(args.seeds):
+        pristine = synth.make_field(COULOMB_DIMS, 0.58, 7000 + k, 8000 + k, device="cuda")
+        row = {"seed": k, "plaquette": gf.gf_plaquette(ctx, pristine)}
+        for leg in ("sa+or", "or"):
+            U = pristine.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if leg == "sa+or":
+                rc = gf.gf_anneal(ctx, U, 1.45, 0.01, args.sa_sweeps, 9000 + k, allow_reject=True)
+                torch.cuda.synchronize()
+                row["sa_s"] = time.perf_counter() - t0
+                row["sa_rejects"] = gf.gf_get_stat(ctx, "sa_rejects")
+                row["F_after_sa"] = gf.gf_functional(ctx, U)
+                t0 = time.perf_counter()
+            conv, it, F, th = gf.gf_overrelax(ctx, U, OMEGA, target, MAX_ITER)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            row[leg] = {"or_s": dt, "sweeps": it, "F": F, "theta": th, "converged": conv,
+                        "su_per_s": V * it / dt, "dplaq": abs(gf.gf_plaquette(ctx, U) - row["plaquette"])}
+            del U
+        rows.append(row)
+        log(json.dumps(row))
+    F_sa = [r["sa+or"]["F"] for r in rows]
+    F_or = [r["or"]["F"] for r in rows]
+    stat = lambda v: {"mean": float(np.mean(v)), "std": float(np.std(v)), "min": float(min(v)), "max": float(max(v))}
+    print(json.dumps({
+        "workload": f"coulomb 48^3x96 FP64, plaquette 0.58, {args.sa_sweeps} heatbath sweeps T 1.45->0.01, "
+                    f"then OR omega 1.7 to theta<1e-13; {args.seeds} seeds",
+        "seeds": rows, "F_sa_or": stat(F_sa), "F_or": stat(F_or),
+        "sa_higher_F": int(sum(a > b for a, b in zip(F_sa, F_or))),
+        "sa_sweeps_per_s": float(np.mean([args.sa_sweeps / r["sa_s"] for r in rows])),
+        "total_s": time.perf_counter() - t_start}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -556,6 +629,9 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-fields", type=int, default=4)
     ap.add_argument("--save", action="store_true", help="store the trained parameters")
+    ap.add_argument("--coulomb", action="store_true", help="the 48^3x96 Coulomb workload with annealing")
+    ap.add_argument("--seeds", type=int, default=8)
+    ap.add_argument("--sa-sweeps", type=int, default=3000)
     args = ap.parse_args()
     if args.learned:
         torch.cuda.set_device(0)
@@ -564,6 +640,10 @@ def main():
     if args.batched:
         torch.cuda.set_device(0)
         batched(args)
+        return
+    if args.coulomb:
+        torch.cuda.set_device(0)
+        coulomb(args)
         return
     if args.kernel:
         torch.cuda.set_device(0)

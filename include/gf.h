@@ -109,7 +109,15 @@ int gf_set_stream(gf_ctx *ctx, void *stream);
  *   "block"          threads per block (multiple of 32, <= 1024; 0 = autotune)
  *   "use_graphs"     1 = replay sweep loops as CUDA graphs (default 1)
  *   "sa_cap"         heatbath rejection cap per draw (default 64, <= 255)
- *   "sa_sweep_offset" Philox sweep counter of the first annealing sweep */
+ *   "sa_sweep_offset" Philox sweep counter of the first annealing sweep
+ *   "stochastic_p"   > 0: gf_overrelax / gf_or_sweeps / gf_converge use
+ *                    stochastic relaxation with this probability instead of
+ *                    overrelaxation (omega unused; default 0)
+ *   "sr_seed"        Philox key of those draws (resets their sweep counter)
+ *   "fp64_arith"     FP64 phase and GF_FP64 policy: 0 = native FP64 (default),
+ *                    1 = double-float values (pairs of FP32, 48-bit
+ *                    significand, storage DF64_18) updated on the FP32 pipe;
+ *                    per sweep within 1e-12 of FP64 */
 int gf_set_option(gf_ctx *ctx, const char *key, double value);
 int gf_get_option(const gf_ctx *ctx, const char *key, double *value);
 
@@ -173,6 +181,14 @@ int gf_or_sweeps(gf_ctx *ctx, double omega, int nsweeps);
 /* One heatbath half-sweep of the resident field at temperature T with
  * Philox key seed and sweep counter sweep. */
 int gf_sa_half_sweep(gf_ctx *ctx, int parity, double T, uint64_t seed, uint32_t sweep);
+
+/* One stochastic-relaxation half-sweep (Sec. 1: relaxation against critical
+ * slowing down): per subgroup the maximiser r* = k/|k| is applied, or with
+ * probability p its square r*^2, which reflects the subgroup element through
+ * the maximum and leaves Re tr[g K] unchanged.  The draw for (site, subgroup)
+ * is the first word of Philox4x32-10 with key seed and counter
+ * (lexicographic site, sweep, 256 * subgroup, 2), compared with p in FP64. */
+int gf_sr_half_sweep(gf_ctx *ctx, int parity, double p, uint64_t seed, uint32_t sweep);
 
 /* F and theta of the resident field (accumulated in FP64). */
 int gf_measure(gf_ctx *ctx, double *F_out, double *theta_out);

@@ -95,6 +95,7 @@ def _declare(lib: C.CDLL) -> C.CDLL:
     d.oracle_conv_backward_weights.restype = None
     d.oracle_net_loss.argtypes = [_dp, _dp, _dp, _ip, _ip, _dp, _dp]
     d.oracle_net_loss.restype = C.c_double
+    d.oracle_sr_half_sweep.argtypes = [_dp, _ip, C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint32]
     d.oracle_features.argtypes = [_dp, _ip, C.c_double, _dp]
     d.oracle_expmap.argtypes = [_dp, C.c_double, _dp, C.c_long]
     d.oracle_expmap.restype = None
@@ -285,6 +286,12 @@ def anneal(U, gauge: int, T0: float, T1: float, steps: int, seed: int, sweep_off
     if f < 0:
         raise ValueError("oracle anneal rejected its arguments")
     return f
+
+
+def sr_half_sweep(U, parity: int, p: float, gauge: int, seed: int, sweep: int) -> None:
+    """Stochastic relaxation half-sweep: r* or, with probability p, r*^2."""
+    U = _field(U)
+    _check(lib().oracle_sr_half_sweep(_d(U), _i(dims_of(U)), parity, p, gauge, seed, sweep), "sr")
 
 
 def sa_update_sites(U, sites, T: float, gauge: int, seed: int, sweep: int,

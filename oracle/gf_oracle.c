@@ -1013,3 +1013,61 @@ void oracle_algebra_log(const double *gin, double scale, double *c, long n)
         for (int a = 0; a < 8; ++a) c[j * 8 + a] = re_tr_lambda(a, &A) / scale;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* stochastic relaxation (Sec. 1; de Forcrand's relaxation against critical  */
+/* slowing down): per subgroup the maximiser r* = k/|k| is used with         */
+/* probability 1 - p and its square r*^2 with probability p.  r*^2 reflects  */
+/* the current element through the maximum: it leaves Re tr[g K] of the      */
+/* subgroup unchanged ("microcanonical").  The draw per (site, subgroup) is  */
+/* the first word of Philox counter (site, sweep, 256 * subgroup, 2).        */
+/* ------------------------------------------------------------------------ */
+#define SR_TAG 2u
+
+static int sr_quaternion(const double k[4], double p, uint32_t site, uint32_t sweep, int sg, const uint32_t key[2],
+                         double r[4])
+{
+    double n2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + k[3] * k[3];
+    if (n2 == 0.0) return 0;
+    double inv = 1.0 / sqrt(n2);
+    for (int c = 0; c < 4; ++c) r[c] = k[c] * inv;
+    uint32_t ctr[4] = { site, sweep, (uint32_t)sg * 256u, SR_TAG };
+    uint32_t w[4];
+    oracle_philox4x32_10(ctr, key, w);
+    if (u01(w[0]) < p) { /* r <- r r (quaternion square) */
+        double r0 = r[0];
+        r[0] = 2.0 * r0 * r0 - 1.0;
+        r[1] = 2.0 * r0 * r[1];
+        r[2] = 2.0 * r0 * r[2];
+        r[3] = 2.0 * r0 * r[3];
+    }
+    return 1;
+}
+
+int oracle_sr_half_sweep(double *U, const int dims[4], int parity, double p, int gauge, uint64_t seed,
+                         uint32_t sweep)
+{
+    lattice g;
+    if (lattice_init(&g, dims) || !(p >= 0.0 && p <= 1.0)) return -1;
+    int nk = gauge_nk(gauge);
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (long i = 0; i < g.V; ++i) {
+        if (site_parity(&g, i) != parity) continue;
+        star s;
+        star_load(U, &g, i, &s);
+        for (int sg = 0; sg < 3; ++sg) {
+            int a = SUBGROUP[sg][0], b = SUBGROUP[sg][1];
+            double k[4], r[4];
+            cplx R[2][2];
+            star_quaternion(&s, nk, a, b, k);
+            if (!sr_quaternion(k, p, (uint32_t)i, sweep, sg, key, r)) continue;
+            su2_matrix(r, R);
+            star_rotate(&s, a, b, R);
+        }
+        star_store(U, &g, i, &s);
+    }
+    return 0;
+}

@@ -55,12 +55,16 @@ struct gf_ctx {
     int reunit_every = 1;
     int tps = 0;
     int block = 0;
+    int fp64_arith = 0;  // FP64 phase: 0 native FP64, 1 double-float on the FP32 pipe (DF64_18)
     int variant = 0;  // 0 auto, 1 per-subgroup rotations of the held links, 2 accumulate form
     int use_graphs = 1;
     int autotune = 0;
     int sa_cap = 64;
     uint32_t sa_sweep_offset = 0;
     int track = 0;             // resident sweeps also rotate the tracked g
+    double sr_p = 0.0;         // > 0: gf_overrelax uses stochastic relaxation with this probability
+    uint64_t sr_seed = 1;      // Philox key of the stochastic relaxation draws
+    uint32_t sr_sweep = 0;     // Philox sweep counter, advanced by every stochastic sweep
     gf_net *net = nullptr;     // learned warm start applied at the FP32 -> FP64 switch
     void *feat = nullptr;      // BF16 network inputs [V][80]
     float *cbuf = nullptr;     // network outputs [V][8]
@@ -117,7 +121,11 @@ static int cuda_fail(gf_ctx *c, cudaError_t e, const char *what)
 // ---------------------------------------------------------------------------
 // buffers
 // ---------------------------------------------------------------------------
-static int fmt64(const gf_ctx *c) { return c->storage64 == 12 ? F64_12 : F64_18; }
+static int fmt64(const gf_ctx *c)
+{
+    if (c->fp64_arith == 1) return DF64_18;
+    return c->storage64 == 12 ? F64_12 : F64_18;
+}
 static int fmt32(const gf_ctx *c) { return c->storage32 == 18 ? F32_18 : F32_12; }
 
 static size_t plane_bytes(const gf_ctx *c) { return (size_t)c->geom.plane * 16; }
@@ -226,6 +234,7 @@ static std::pair<int, int> default_config(int fmt)
     case F32_12: return { 1, 128 };
     case F32_18: return { 2, 128 };
     case F64_12: return { 2, 128 };
+    case DF64_18: return { 0, 128 };
     default: return { 2, 128 };
     }
 }
@@ -278,6 +287,22 @@ static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, boo
 {
     std::pair<int, int> cfg = launch_config(ctx, fmt);
     FieldRef f = ref(ctx, field);
+    if (ctx->sr_p > 0.0) {  // stochastic relaxation: fresh Philox counters every sweep, no graph replay
+        for (int k = 0; k < n; ++k, ++ctx->sr_sweep)
+            for (int p = 0; p < 2; ++p) {
+                SweepArgs a = sweep_args(ctx, field, p, omega);
+                a.prob = ctx->sr_p;
+                a.key = make_uint2((uint32_t)ctx->sr_seed, (uint32_t)(ctx->sr_seed >> 32));
+                a.sweep = ctx->sr_sweep;
+                CK(launch_sweep(fmt, a, cfg.first, ctx->gauge, 2, false, cfg.second, ctx->stream));
+            }
+        if (reunit) CK(launch_reunitarize(fmt, f, ctx->geom, ctx->stream));
+        if (measure) {
+            CK(launch_measure(fmt, f, ctx->geom, ctx->gauge, ctx->partials, ctx->dres, ctx->stream));
+            CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        return GF_OK;
+    }
     if (ctx->use_graphs && n > 0) {
         GraphKey key{ fmt, cfg.first, cfg.second, n, trackg, measure, reunit, omega, field, ctx->gt };
         auto it = ctx->graphs.find(key);
@@ -560,6 +585,10 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
     } else if (k == "block") {
         if (!integral || iv < 0 || iv > 256 || (iv % 32)) return fail(ctx, GF_EINVAL, "block: 0 or 32..256 step 32");
         ctx->block = iv;
+    } else if (k == "fp64_arith") {
+        if (iv != 0 && iv != 1) return fail(ctx, GF_EINVAL, "fp64_arith: 0 (native) or 1 (double-float)");
+        if (ctx->resident == GF_FP64 && iv != ctx->fp64_arith) ctx->resident = -1;
+        ctx->fp64_arith = iv;
     } else if (k == "variant") {
         if (!integral || iv < 0 || iv > 2) return fail(ctx, GF_EINVAL, "variant: 0, 1 or 2");
         ctx->variant = iv;
@@ -569,6 +598,13 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
         ctx->autotune = v != 0.0;
     } else if (k == "track") {
         ctx->track = v != 0.0;
+    } else if (k == "stochastic_p") {
+        if (!(v >= 0.0 && v <= 1.0)) return fail(ctx, GF_EINVAL, "stochastic_p in [0, 1]");
+        ctx->sr_p = v;
+    } else if (k == "sr_seed") {
+        if (!(v >= 0.0) || v > 18446744073709551615.0) return fail(ctx, GF_EINVAL, "sr_seed");
+        ctx->sr_seed = (uint64_t)v;
+        ctx->sr_sweep = 0;
     } else if (k == "sa_cap") {
         if (!integral || iv < 1 || iv > 255) return fail(ctx, GF_EINVAL, "sa_cap: 1..255");
         ctx->sa_cap = iv;
@@ -595,10 +631,13 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *v)
     else if (k == "threads_per_site") *v = ctx->tps;
     else if (k == "block") *v = ctx->block;
     else if (k == "variant") *v = ctx->variant;
+    else if (k == "fp64_arith") *v = ctx->fp64_arith;
     else if (k == "use_graphs") *v = ctx->use_graphs;
     else if (k == "autotune") *v = ctx->autotune;
     else if (k == "sa_cap") *v = ctx->sa_cap;
     else if (k == "track") *v = ctx->track;
+    else if (k == "stochastic_p") *v = ctx->sr_p;
+    else if (k == "sr_seed") *v = (double)ctx->sr_seed;
     else if (k == "sa_sweep_offset") *v = ctx->sa_sweep_offset;
     else return GF_EINVAL;
     return GF_OK;
@@ -666,6 +705,20 @@ int gf_sa_half_sweep(gf_ctx *ctx, int parity, double T, uint64_t seed, uint32_t 
     a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     a.sweep = sweep;
     CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 1, false, cfg.second, ctx->stream));
+    return GF_OK;
+}
+
+int gf_sr_half_sweep(gf_ctx *ctx, int parity, double p, uint64_t seed, uint32_t sweep)
+{
+    if (!ctx) return GF_EINVAL;
+    if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
+    if ((parity & ~1) || !(p >= 0.0 && p <= 1.0)) return fail(ctx, GF_EINVAL, "parity 0/1, p in [0, 1]");
+    std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt);
+    SweepArgs a = sweep_args(ctx, resident_base(ctx), parity, 1.0);
+    a.prob = p;
+    a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    a.sweep = sweep;
+    CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 2, false, cfg.second, ctx->stream));
     return GF_OK;
 }
 

@@ -31,7 +31,7 @@ constexpr int kThreads = 128;
 constexpr int kM = 128;
 constexpr int kStages = 4;
 constexpr long long kWaitNs = 1000000000LL;  // 1 s
-constexpr int kGuardBytes = 40 * 1024;       // slack after the operand stages
+constexpr int kGuardBytes = 0;  // no slack needed after the operand stages: operands stay inside their stage
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 

@@ -147,7 +147,9 @@ __device__ __forceinline__ int fwd_half(const Geom &g, const int c[4], int mu)
 //   F64_12: 6 double2 (rows 0, 1; row 2 rebuilt)
 //   F32_18: 4 float4 (two complex each, row-major) + 1 float2 (entry 2,2)
 //   F32_12: 3 float4 (rows 0, 1; row 2 rebuilt)
-enum Format { F64_18 = 0, F64_12 = 1, F32_18 = 2, F32_12 = 3 };
+//   DF64_18: 9 float4 (re.hi, re.lo, im.hi, im.lo): FP64-class values as pairs of
+//            FP32 (hi + lo), for the FP32-pipe kernels of gf_df64.cuh
+enum Format { F64_18 = 0, F64_12 = 1, F32_18 = 2, F32_12 = 3, DF64_18 = 4 };
 
 struct FieldRef {
     char *base;
@@ -264,6 +266,33 @@ struct Store<F32_12> {
             int e0 = 2 * c, e1 = 2 * c + 1;
             pl[h] = make_float4(u.e[e0 / 3][e0 % 3].re, u.e[e0 / 3][e0 % 3].im, u.e[e1 / 3][e1 % 3].re,
                                 u.e[e1 / 3][e1 % 3].im);
+        }
+    }
+};
+
+// FP64 view of DF64_18 (value = hi + lo), used by the whole-field kernels
+template <>
+struct Store<DF64_18> {
+    typedef double T;
+    static constexpr int NCHUNK = 9;
+    static constexpr int REALS = 18;
+    static __device__ __forceinline__ void load(const FieldRef &f, int pl0, int h, mat3<double> &u)
+    {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            const float4 *pl = reinterpret_cast<const float4 *>(f.base + (pl0 + c) * f.plane_bytes);
+            float4 v = pl[h];
+            u.e[c / 3][c % 3] = mk<double>((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+        }
+    }
+    static __device__ __forceinline__ void store(const FieldRef &f, int pl0, int h, const mat3<double> &u)
+    {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            float4 *pl = reinterpret_cast<float4 *>(f.base + (pl0 + c) * f.plane_bytes);
+            double re = u.e[c / 3][c % 3].re, im = u.e[c / 3][c % 3].im;
+            float rh = __double2float_rn(re), ih = __double2float_rn(im);
+            pl[h] = make_float4(rh, __double2float_rn(re - (double)rh), ih, __double2float_rn(im - (double)ih));
         }
     }
 };
@@ -421,6 +450,31 @@ __device__ __forceinline__ int heatbath_quat(const double k[4], double T, uint32
     r[2] = s[0] * kh[2] + kh[0] * s[2] - (s[3] * kh[1] - s[1] * kh[3]);
     r[3] = s[0] * kh[3] + kh[0] * s[3] - (s[1] * kh[2] - s[2] * kh[1]);
     return 1;
+}
+
+// Stochastic relaxation: the maximiser r* = k/|k|, replaced with probability
+// p by r*^2 (the microcanonical reflection through the maximum).  The draw is
+// the first word of Philox counter (site, sweep, 256 * subgroup, 2); the
+// decision u < p is taken in FP64.  Returns false when k = 0.
+#define GF_SR_TAG 2u
+template <class T>
+__device__ __forceinline__ bool sr_quat(const T k[4], double p, uint32_t site, uint32_t sweep, int sg, uint2 key,
+                                        T r[4])
+{
+    T n2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + k[3] * k[3];
+    if (n2 == T(0)) return false;
+    T inv = T(1) / sqrt(n2);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) r[c] = k[c] * inv;
+    uint4 w = philox4x32_10(make_uint4(site, sweep, (uint32_t)sg * 256u, GF_SR_TAG), key);
+    if (u01(w.x) < p) {
+        T r0 = r[0];
+        r[0] = T(2) * r0 * r0 - T(1);
+        r[1] = T(2) * r0 * r[1];
+        r[2] = T(2) * r0 * r[2];
+        r[3] = T(2) * r0 * r[3];
+    }
+    return true;
 }
 
 }  // namespace gf

@@ -174,6 +174,7 @@ static inline int nblocks(long n, int b) { return (int)((n + b - 1) / b); }
     case F64_12: CALL(F64_12); break;           \
     case F32_18: CALL(F32_18); break;           \
     case F32_12: CALL(F32_12); break;           \
+    case DF64_18: CALL(DF64_18); break;         \
     default: return cudaErrorInvalidValue;      \
     }
 
@@ -208,6 +209,8 @@ cudaError_t launch_widen(int src_fmt, FieldRef src, int dst_fmt, FieldRef dst, c
     else if (src_fmt == F32_12 && dst_fmt == F64_12) k_transcode<F32_12, F64_12><<<n, 256, 0, s>>>(src, dst, g);
     else if (src_fmt == F32_18 && dst_fmt == F64_18) k_transcode<F32_18, F64_18><<<n, 256, 0, s>>>(src, dst, g);
     else if (src_fmt == F32_18 && dst_fmt == F64_12) k_transcode<F32_18, F64_12><<<n, 256, 0, s>>>(src, dst, g);
+    else if (src_fmt == F32_12 && dst_fmt == DF64_18) k_transcode<F32_12, DF64_18><<<n, 256, 0, s>>>(src, dst, g);
+    else if (src_fmt == F32_18 && dst_fmt == DF64_18) k_transcode<F32_18, DF64_18><<<n, 256, 0, s>>>(src, dst, g);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -224,6 +227,7 @@ cudaError_t launch_apply_tracked_gauge(const double *aos, FieldRef gt, int dst_f
     int n = nblocks(8L * g.Vh, 128);
     if (dst_fmt == F64_18) k_apply_tracked_gauge<F64_18><<<n, 128, 0, s>>>(aos, gt, dst, g);
     else if (dst_fmt == F64_12) k_apply_tracked_gauge<F64_12><<<n, 128, 0, s>>>(aos, gt, dst, g);
+    else if (dst_fmt == DF64_18) k_apply_tracked_gauge<DF64_18><<<n, 128, 0, s>>>(aos, gt, dst, g);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

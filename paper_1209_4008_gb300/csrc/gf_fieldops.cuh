@@ -165,6 +165,38 @@ __device__ __forceinline__ void add_antiherm(const mat3<T> &u, double s, double 
     }
 }
 
+// the same accumulation in the storage precision A (FP32 fields: the FP32
+// phase only decides theta against thresholds >= 1e-12, far above FP32
+// rounding of the O(1) link entries, ~1e-7 in Delta)
+template <class T, class A>
+__device__ __forceinline__ void add_antiherm_p(const mat3<T> &u, A s, A dre[3][3], A dim[3][3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        dre[a][a] += s * (A)u.e[a][a].im;
+#pragma unroll
+        for (int b = a + 1; b < 3; ++b) {
+            dre[a][b] += s * A(0.5) * ((A)u.e[a][b].im + (A)u.e[b][a].im);
+            dim[a][b] -= s * A(0.5) * ((A)u.e[a][b].re - (A)u.e[b][a].re);
+        }
+    }
+}
+
+template <class A>
+__device__ __forceinline__ double traceless_norm2_p(A dre[3][3], A dim[3][3])
+{
+    A tr = (dre[0][0] + dre[1][1] + dre[2][2]) * A(1.0 / 3.0);
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        A d = dre[a][a] - tr;
+        s += (double)(d * d);
+#pragma unroll
+        for (int b = a + 1; b < 3; ++b) s += 2.0 * (double)(dre[a][b] * dre[a][b] + dim[a][b] * dim[a][b]);
+    }
+    return s;
+}
+
 // tr[D D^dagger] of the traceless part of the Hermitian D
 __device__ __forceinline__ double traceless_norm2(double dre[3][3], double dim[3][3])
 {
@@ -188,22 +220,23 @@ __device__ __forceinline__ void measure_site(const FieldRef &f, const Geom &g, i
                                              double &tsum)
 {
     typedef Store<FMT> S;
-    typedef typename S::T T;
+    typedef typename S::T T;  // per-site sums in the storage precision, totals in FP64
     constexpr int NK = COULOMB ? 3 : 4;
     int c[4];
     site_coords(g, p, h, c);
-    double dre[3][3] = { { 0 } }, dim[3][3] = { { 0 } };
-    fsum = 0.0;
+    T dre[3][3] = { { T(0) } }, dim[3][3] = { { T(0) } };
+    T fs = T(0);
 #pragma unroll
     for (int mu = 0; mu < NK; ++mu) {
         mat3<T> u;
         S::load(f, (p * 4 + mu) * S::NCHUNK, h, u);
-        fsum += (double)u.e[0][0].re + (double)u.e[1][1].re + (double)u.e[2][2].re;
-        add_antiherm(u, 1.0, dre, dim);
+        fs += u.e[0][0].re + u.e[1][1].re + u.e[2][2].re;
+        add_antiherm_p<T, T>(u, T(1), dre, dim);
         S::load(f, ((p ^ 1) * 4 + mu) * S::NCHUNK, back_half(g, c, mu), u);
-        add_antiherm(u, -1.0, dre, dim);
+        add_antiherm_p<T, T>(u, T(-1), dre, dim);
     }
-    tsum = traceless_norm2(dre, dim);
+    fsum = (double)fs;
+    tsum = traceless_norm2_p<T>(dre, dim);
 }
 
 }  // namespace gf

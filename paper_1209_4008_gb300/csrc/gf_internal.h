@@ -21,6 +21,7 @@ struct SweepArgs {
     uint2 key;        // Philox key (seed)
     uint32_t sweep;   // Philox sweep counter
     int cap;          // heatbath rejection cap
+    double prob;      // stochastic relaxation: probability of the microcanonical step
     int *status;      // [0]: heatbath draws that hit the cap
 };
 
@@ -33,6 +34,8 @@ cudaError_t launch_sweep_f32_18(const SweepArgs &a, int tps, int coulomb, int mo
                                 cudaStream_t s);
 cudaError_t launch_sweep_f32_12(const SweepArgs &a, int tps, int coulomb, int mode, bool trackg, int block,
                                 cudaStream_t s);
+cudaError_t launch_sweep_df64(const SweepArgs &a, int tps, int coulomb, int mode, bool trackg, int block,
+                              cudaStream_t s);
 
 inline cudaError_t launch_sweep(int fmt, const SweepArgs &a, int tps, int coulomb, int mode, bool trackg, int block,
                                 cudaStream_t s)
@@ -42,6 +45,7 @@ inline cudaError_t launch_sweep(int fmt, const SweepArgs &a, int tps, int coulom
     case F64_12: return launch_sweep_f64_12(a, tps, coulomb, mode, trackg, block, s);
     case F32_18: return launch_sweep_f32_18(a, tps, coulomb, mode, trackg, block, s);
     case F32_12: return launch_sweep_f32_12(a, tps, coulomb, mode, trackg, block, s);
+    case DF64_18: return launch_sweep_df64(a, tps, coulomb, mode, trackg, block, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -53,6 +57,7 @@ inline int format_chunks(int fmt)
     case F64_12: return 6;
     case F32_18: return 5;
     case F32_12: return 3;
+    case DF64_18: return 9;
     default: return 0;
     }
 }
@@ -65,6 +70,7 @@ inline double format_link_bytes(int fmt)
     case F64_12: return 96.0;
     case F32_18: return 72.0;
     case F32_12: return 48.0;
+    case DF64_18: return 144.0;
     default: return 0.0;
     }
 }

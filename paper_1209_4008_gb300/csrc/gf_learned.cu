@@ -177,6 +177,7 @@ cudaError_t launch_features(int fmt, FieldRef f, const Geom &g, double inv_scale
     __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out);
     if (fmt == F64_18) k_features<F64_18><<<nb(2L * g.Vh, 128), 128, 0, s>>>(f, g, inv_scale, o);
     else if (fmt == F64_12) k_features<F64_12><<<nb(2L * g.Vh, 128), 128, 0, s>>>(f, g, inv_scale, o);
+    else if (fmt == DF64_18) k_features<DF64_18><<<nb(2L * g.Vh, 128), 128, 0, s>>>(f, g, inv_scale, o);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -198,6 +199,7 @@ cudaError_t launch_gauge_transform_resident(int fmt, FieldRef f, FieldRef gt, co
     int n = nb(8L * g.Vh, 128);
     if (fmt == F64_18) k_gauge_transform_resident<F64_18><<<n, 128, 0, s>>>(f, gt, g);
     else if (fmt == F64_12) k_gauge_transform_resident<F64_12><<<n, 128, 0, s>>>(f, gt, g);
+    else if (fmt == DF64_18) k_gauge_transform_resident<DF64_18><<<n, 128, 0, s>>>(f, gt, g);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

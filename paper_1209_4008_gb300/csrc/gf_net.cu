@@ -371,6 +371,198 @@ cudaError_t conv_tc(const bf16 *X, int I, const bf16 *W, int O, const float *b, 
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// weight gradient on the tensor cores:
+//   dW[k][o][i] = sum_s dY[s][o] X[s + d(k)][i]
+// as D[(tap, i)][o] = sum_s A[(tap, i)][s] B[o][s] with M = 128 rows (TG taps x
+// IP input channels, padded), N = output channels (padded), K = sites.  A CTA
+// takes one tap group and a chunk of sites, in stages of 64 sites (4 MMAs of
+// K = 16); both operands are gathered transposed (site index along K) into the
+// K-major core layout; the FP32 result is added to dW with atomics.
+// ---------------------------------------------------------------------------
+constexpr int kDwStageSites = 64;
+constexpr int kDwChunk = 1024;  // sites per CTA
+
+template <int IP, int N>
+struct DwLayout {
+    static constexpr int TG = gf::tc::kM / IP;  // taps per group (IP = 32 -> 4, IP = 80 or 128 -> 1)
+    static constexpr int A_BYTES = gf::tc::kM * kDwStageSites * 2;
+    static constexpr int B_BYTES = N * kDwStageSites * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int BAR_OFF = 2 * STAGE;
+    static constexpr int SMEM = BAR_OFF + 3 * 8 + 16;
+};
+
+template <int IP, int N>
+__global__ void __launch_bounds__(128) k_conv_dw_tc(const bf16 *__restrict__ dY, int O, const bf16 *__restrict__ X,
+                                                    int I, Lat g, float *__restrict__ dW, int *__restrict__ err)
+{
+    using namespace gf::tc;
+    typedef DwLayout<IP, N> LY;
+    constexpr int TG = LY::TG;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);  // 2 stages + final
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + 3 * 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int k0 = blockIdx.y * TG;  // first tap of the group
+    const int s_begin = blockIdx.x * kDwChunk;
+    const int s_end = min(s_begin + kDwChunk, g.V);
+    constexpr uint32_t idesc = instr_desc(kM, N);
+
+    // operands start at zero (padding rows stay zero)
+    for (int e = tid; e < 2 * LY::STAGE / 16; e += kThreads)
+        reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (int st = 0; st < 3; ++st) mbar_init(&bar[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    bool fail = false;
+    const int nstage = (s_end - s_begin + kDwStageSites - 1) / kDwStageSites;
+    for (int t = 0; t < nstage; ++t) {
+        const int st = t & 1;
+        if (t >= 2) {
+            if (!mbar_wait(&bar[st], (uint32_t)((t / 2 - 1) & 1))) fail = true;
+        }
+        if (__syncthreads_or(fail)) {
+            fail = true;
+            break;
+        }
+        uint8_t *A = smem + st * LY::STAGE;
+        uint8_t *B = A + LY::A_BYTES;
+        const int s0 = s_begin + t * kDwStageSites;
+        // A[(kl, i)][s] = X[s + d(k0 + kl)][i]: core (r/8, s/8) at ((s/8) * 16 + r/8) * 128,
+        // row r%8 (16 B), element s%8 (2 B)
+        for (int it = tid; it < kDwStageSites * TG; it += kThreads) {
+            const int sl = it % kDwStageSites, kl = it / kDwStageSites;
+            const int s = s0 + sl, k = k0 + kl;
+            const bool ok = s < s_end && k < 81;
+            const int nb = ok ? shift_site(g, s, k, 1) : 0;
+            for (int c = 0; c < IP / 8; ++c) {
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (ok && 8 * c < I) v = *reinterpret_cast<const uint4 *>(X + (long)nb * I + 8 * c);
+                const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int r = kl * IP + 8 * c + q;
+                    *reinterpret_cast<bf16 *>(A + ((sl >> 3) * 16 + (r >> 3)) * 128 + (r & 7) * 16 + (sl & 7) * 2) = e[q];
+                }
+            }
+        }
+        // B[o][s] = dY[s][o]: core (o/8, s/8) at ((s/8) * (N/8) + o/8) * 128
+        for (int it = tid; it < kDwStageSites; it += kThreads) {
+            const int s = s0 + it;
+            for (int c = 0; c < (O + 7) / 8; ++c) {
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (s < s_end) v = *reinterpret_cast<const uint4 *>(dY + (long)s * O + 8 * c);
+                const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int o = 8 * c + q;
+                    *reinterpret_cast<bf16 *>(B + ((it >> 3) * (N / 8) + (o >> 3)) * 128 + (o & 7) * 16 + (it & 7) * 2) = e[q];
+                }
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after_sync();
+#pragma unroll
+            for (int kk = 0; kk < kDwStageSites / 16; ++kk) {
+                uint64_t ad = smem_desc(smem_u32(A + kk * 2 * 2048), 2048, 128);
+                uint64_t bd = smem_desc(smem_u32(B + kk * 2 * (N / 8) * 128), (N / 8) * 128, 128);
+                mma_bf16(tmem, ad, bd, idesc, (t | kk) != 0);
+            }
+            mma_commit(&bar[st]);
+        }
+    }
+    if (tid == 0) mma_commit(&bar[2]);
+    if (!mbar_wait(&bar[2], 0)) fail = true;
+    fail = __syncthreads_or(fail);
+    if (!fail && nstage > 0) {
+        fence_after_sync();
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        if (N == 32) {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+        } else {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+                " [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int row = tid, kl = row / IP, i = row - kl * IP, k = k0 + kl;
+        if (kl < TG && k < 81 && i < I) {
+#pragma unroll
+            for (int o = 0; o < N; ++o) {
+                if (o >= O) break;
+                atomicAdd(&dW[((long)k * O + o) * I + i], __uint_as_float(r[o]));
+            }
+        }
+    } else if (fail && tid == 0) {
+        atomicExch(err, GF_ETIMEOUT);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    }
+}
+
+// db[o] = sum_s dY[s][o]
+__global__ void k_bias_grad(const bf16 *__restrict__ dY, int O, int V, float *__restrict__ db)
+{
+    __shared__ float acc[32];
+    if (threadIdx.x < 32) acc[threadIdx.x] = 0.0f;
+    __syncthreads();
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)V * O; e += (long)gridDim.x * blockDim.x)
+        atomicAdd(&acc[e % O], __bfloat162float(dY[e]));
+    __syncthreads();
+    if (threadIdx.x < O) atomicAdd(&db[threadIdx.x], acc[threadIdx.x]);
+}
+
+template <int IP, int N>
+cudaError_t conv_dw_tc(const bf16 *dY, int O, const bf16 *X, int I, const Lat &g, float *dW, float *db, int *err,
+                       cudaStream_t s)
+{
+    typedef DwLayout<IP, N> LY;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_dw_tc<IP, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, LY::SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((g.V + kDwChunk - 1) / kDwChunk, (81 + LY::TG - 1) / LY::TG);
+    k_conv_dw_tc<IP, N><<<grid, gf::tc::kThreads, LY::SMEM, s>>>(dY, O, X, I, g, dW, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_bias_grad<<<256, 256, 0, s>>>(dY, O, g.V, db);
+    return cudaGetLastError();
+}
+
 template <int I, int O>
 cudaError_t conv_cc(const bf16 *X, const bf16 *W, const float *b, const Lat &g, int sign, int relu, const bf16 *mask,
                     bf16 *Yb, float *Yf, cudaStream_t s)
@@ -505,19 +697,23 @@ static int backward(gf_net *n, const bf16 *f, const float *target)
     NCK(cudaGetLastError());
     NCK(cudaMemsetAsync(n->grad, 0, sizeof(float) * n->np, s));
     // layer 4: dY = dA [V][8]
-    NCK((conv_dw<32, 8>(n->dA, n->act[3], g, n->grad + n->woff[3], n->grad + n->boff[3], s)));
+    if (n->use_tc) NCK((conv_dw_tc<32, 16>(n->dA, 8, n->act[3], 32, g, n->grad + n->woff[3], n->grad + n->boff[3], n->derr, s)));
+    else NCK((conv_dw<32, 8>(n->dA, n->act[3], g, n->grad + n->woff[3], n->grad + n->boff[3], s)));
     r = backward_data(n, 3, n->dA, n->dB);
     if (r != GF_OK) return r;
     // layer 3
-    NCK((conv_dw<32, 32>(n->dB, n->act[2], g, n->grad + n->woff[2], n->grad + n->boff[2], s)));
+    if (n->use_tc) NCK((conv_dw_tc<32, 32>(n->dB, 32, n->act[2], 32, g, n->grad + n->woff[2], n->grad + n->boff[2], n->derr, s)));
+    else NCK((conv_dw<32, 32>(n->dB, n->act[2], g, n->grad + n->woff[2], n->grad + n->boff[2], s)));
     r = backward_data(n, 2, n->dB, n->dA);
     if (r != GF_OK) return r;
     // layer 2
-    NCK((conv_dw<32, 32>(n->dA, n->act[1], g, n->grad + n->woff[1], n->grad + n->boff[1], s)));
+    if (n->use_tc) NCK((conv_dw_tc<32, 32>(n->dA, 32, n->act[1], 32, g, n->grad + n->woff[1], n->grad + n->boff[1], n->derr, s)));
+    else NCK((conv_dw<32, 32>(n->dA, n->act[1], g, n->grad + n->woff[1], n->grad + n->boff[1], s)));
     r = backward_data(n, 1, n->dA, n->dB);
     if (r != GF_OK) return r;
     // layer 1 (no input gradient needed)
-    NCK((conv_dw<80, 32>(n->dB, f, g, n->grad + n->woff[0], n->grad + n->boff[0], s)));
+    if (n->use_tc) NCK((conv_dw_tc<128, 32>(n->dB, 32, f, 80, g, n->grad + n->woff[0], n->grad + n->boff[0], n->derr, s)));
+    else NCK((conv_dw<80, 32>(n->dB, f, g, n->grad + n->woff[0], n->grad + n->boff[0], s)));
     return GF_OK;
 }
 

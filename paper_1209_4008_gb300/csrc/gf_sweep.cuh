@@ -18,7 +18,7 @@
 
 namespace gf {
 
-enum Mode { MODE_OR = 0, MODE_SA = 1 };
+enum Mode { MODE_OR = 0, MODE_SA = 1, MODE_SR = 2 };
 
 // ---------------------------------------------------------------------------
 // accumulate form (one thread per site)
@@ -91,6 +91,18 @@ __device__ __forceinline__ void reload<F32_12>(const FieldRef &f, int pl0, int h
         u.e[e1 / 3][e1 % 3] = mk<float>(v.z, v.w);
     }
     rebuild_row2(u);
+}
+
+template <>
+__device__ __forceinline__ void reload<DF64_18>(const FieldRef &f, int pl0, int h, mat3<double> &u)
+{
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const float4 *p = reinterpret_cast<const float4 *>(f.base + (pl0 + c) * f.plane_bytes) + h;
+        float4 v;
+        asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+        u.e[c / 3][c % 3] = mk<double>((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
 }
 
 // z = x y for 3x3 complex matrices; rows >= ROWS of z are not computed
@@ -182,6 +194,8 @@ __device__ __forceinline__ void sweep_site_acc(const SweepArgs &a, int h)
         bool ok;
         if (MODE == MODE_OR) {
             ok = overrelax_quat(k, (T)a.omega, r);
+        } else if (MODE == MODE_SR) {
+            ok = sr_quat(k, a.prob, site, a.sweep, sg, a.key, r);
         } else {
             double kd[4] = { (double)k[0], (double)k[1], (double)k[2], (double)k[3] };
             double rd[4];
@@ -284,6 +298,8 @@ __device__ __forceinline__ void sweep_site(const SweepArgs &a, int h, int j, uns
         bool ok;
         if (MODE == MODE_OR) {
             ok = overrelax_quat(k, (T)a.omega, r);
+        } else if (MODE == MODE_SR) {
+            ok = sr_quat(k, a.prob, site, a.sweep, sg, a.key, r);
         } else {
             double kd[4] = { (double)k[0], (double)k[1], (double)k[2], (double)k[3] };
             double rd[4];
@@ -351,7 +367,10 @@ static cudaError_t dispatch_gauge_mode(const SweepArgs &a, int coulomb, int mode
         return coulomb ? launch_k_sweep<FMT, TPS, true, MODE_OR, TRACKG>(a, block, s)
                        : launch_k_sweep<FMT, TPS, false, MODE_OR, TRACKG>(a, block, s);
     }
-    if (TRACKG) return cudaErrorInvalidValue;  // annealing never tracks g
+    if (TRACKG) return cudaErrorInvalidValue;  // annealing and stochastic relaxation never track g
+    if (mode == MODE_SR)
+        return coulomb ? launch_k_sweep<FMT, TPS, true, MODE_SR, false>(a, block, s)
+                       : launch_k_sweep<FMT, TPS, false, MODE_SR, false>(a, block, s);
     return coulomb ? launch_k_sweep<FMT, TPS, true, MODE_SA, false>(a, block, s)
                    : launch_k_sweep<FMT, TPS, false, MODE_SA, false>(a, block, s);
 }

@@ -62,6 +62,7 @@ SIGNATURES = {
     "gf_or_sweeps": (C.c_int, [_vp, C.c_double, C.c_int]),
     "gf_sa_half_sweep": (C.c_int, [_vp, C.c_int, C.c_double, C.c_uint64, C.c_uint32]),
     "gf_measure": (C.c_int, [_vp, _dp, _dp]),
+    "gf_sr_half_sweep": (C.c_int, [_vp, C.c_int, C.c_double, C.c_uint64, C.c_uint32]),
     "gf_reunitarize": (C.c_int, [_vp]),
     "gf_autotune": (C.c_int, [_vp, _ip, _ip]),
     "gf_measure_noalloc": (C.c_int, [_ip, C.c_int, _vp, _vp, _vp]),
@@ -279,6 +280,11 @@ def gf_or_sweeps(ctx: Context, omega: float, nsweeps: int) -> None:
 def gf_sa_half_sweep(ctx: Context, parity: int, T: float, seed: int, sweep: int) -> None:
     ctx.check(ctx.lib.gf_sa_half_sweep(ctx.handle, int(parity), T, int(seed), int(sweep)),
               "gf_sa_half_sweep")
+
+
+def gf_sr_half_sweep(ctx: Context, parity: int, p: float, seed: int, sweep: int) -> None:
+    ctx.check(ctx.lib.gf_sr_half_sweep(ctx.handle, int(parity), float(p), int(seed), int(sweep)),
+              "gf_sr_half_sweep")
 
 
 def gf_measure(ctx: Context):

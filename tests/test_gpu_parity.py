@@ -319,3 +319,110 @@ def test_autotune_picks_a_valid_config_and_keeps_parity():
     oracle.or_sweeps(U, 1.7, 0, 3)
     gf.gf_download(c, d)
     assert max_rel(host(d), U) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# FP64-class double-float storage and arithmetic (option fp64_arith = 1): each
+# double-float operation has relative error ~2^-47 (7e-15) and the input is
+# rounded to a 48-bit significand; a link update is ~100 operations, so the
+# bound is 1e-12 relative per half-sweep, growing linearly with the number of
+# half-sweeps compared (2e-12 per sweep).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 8, 8, 8), (6, 4, 6, 10)])
+@pytest.mark.parametrize("gauge", [0, 1])
+@pytest.mark.parametrize("variant", [2, 1])
+def test_df64_half_sweeps_parity(dims, gauge, variant):
+    U = cpu_field(dims, seed=31, gseed=32)
+    c = ctx_for(dims, gauge, fp64_arith=1, variant=variant)
+    d = dev(U)
+    gf.gf_upload(c, d, gf.GF_FP64)
+    gf.gf_download(c, d)
+    assert max_rel(host(d), U) < 1e-14  # 48-bit storage round trip
+    for parity in (0, 1):
+        gf.gf_or_half_sweep(c, parity, 1.7)
+        oracle.or_half_sweep(U, parity, 1.7, gauge)
+        gf.gf_download(c, d)
+        assert max_rel(host(d), U) < 1e-12
+    gf.gf_or_sweeps(c, 1.7, 10)
+    oracle.or_sweeps(U, 1.7, gauge, 10)
+    gf.gf_download(c, d)
+    assert max_rel(host(d), U) < 2e-12 * 11  # 11 sweeps in total
+
+
+@pytest.mark.parametrize("gauge", [0, 1])
+def test_df64_heatbath_parity(gauge):
+    dims = (6, 4, 6, 10)
+    U = cpu_field(dims, seed=33, gseed=34)
+    c = ctx_for(dims, gauge, fp64_arith=1)
+    d = dev(U)
+    gf.gf_upload(c, d, gf.GF_FP64)
+    for parity in (0, 1):
+        gf.gf_sa_half_sweep(c, parity, 0.7, 99, 4)
+        assert oracle.sa_half_sweep(U, parity, 0.7, gauge, 99, 4) == 0
+    gf.gf_download(c, d)
+    assert max_rel(host(d), U) < 1e-11
+
+
+def test_mixed_with_df64_phase_matches_native():
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=3, gseed=4)
+    res = {}
+    for arith in (0, 1):
+        c = ctx_for(dims, 0, check_every=10, precision=gf.GF_MIXED, fp64_arith=arith)
+        d = dev(U)
+        res[arith] = gf.gf_overrelax(c, d, 1.7, 1e-14, 20000)
+        assert res[arith][0] and res[arith][3] < 1e-14
+        assert gf.gf_plaquette(c, d) == pytest.approx(oracle.plaquette(U), abs=1e-13)
+    assert abs(res[0][2] - res[1][2]) < 1e-12
+    assert abs(res[0][1] - res[1][1]) <= 10
+
+
+# ---------------------------------------------------------------------------
+# stochastic relaxation (Sec. 1): same Philox draws on both sides
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("gauge", [0, 1])
+@pytest.mark.parametrize("tps", [0, 2, 8])
+@pytest.mark.parametrize("p", [0.0, 0.5, 1.0])
+def test_sr_half_sweep_parity(gauge, tps, p):
+    dims = (6, 4, 6, 10)
+    U = cpu_field(dims, seed=41, gseed=42)
+    c = ctx_for(dims, gauge, threads_per_site=tps)
+    d = dev(U)
+    gf.gf_upload(c, d, gf.GF_FP64)
+    for parity in (0, 1):
+        gf.gf_sr_half_sweep(c, parity, p, 77, 9)
+        oracle.sr_half_sweep(U, parity, p, gauge, 77, 9)
+    gf.gf_download(c, d)
+    assert max_rel(host(d), U) < 1e-12
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_sr_df64_parity(arith):
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=43, gseed=44)
+    c = ctx_for(dims, 0, fp64_arith=arith)
+    d = dev(U)
+    gf.gf_upload(c, d, gf.GF_FP64)
+    for n in range(3):
+        for parity in (0, 1):
+            gf.gf_sr_half_sweep(c, parity, 0.6, 5, n)
+            oracle.sr_half_sweep(U, parity, 0.6, 0, 5, n)
+    gf.gf_download(c, d)
+    # native FP64: 1e-12; double-float: 1e-12 per half-sweep (6 here)
+    assert max_rel(host(d), U) < (1e-12 if arith == 0 else 6e-12)
+
+
+def test_overrelax_with_stochastic_relaxation_converges():
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=1, gseed=2)
+    c = ctx_for(dims, 0, check_every=10, stochastic_p=0.85, sr_seed=3)
+    d = dev(U)
+    conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-12, 20000)
+    assert conv and th < 1e-12
+    assert gf.gf_plaquette(c, d) == pytest.approx(oracle.plaquette(U), abs=1e-13)
+    # the same number of stochastic sweeps in the oracle gives the same field
+    V = U.copy()
+    for n in range(it):
+        for parity in (0, 1):
+            oracle.sr_half_sweep(V, parity, 0.85, 0, 3, n)
+    assert max_rel(host(d), V) < 1e-9

@@ -444,3 +444,36 @@ def test_plaquette_single_link_closed_form():
     expect = (18 * V - 18 + 6 * np.trace(W).real) / (18 * V)
     assert oracle.plaquette(U) == pytest.approx(expect, abs=1e-15)
     del dims
+
+
+def test_stochastic_relaxation_limits():
+    """p = 0 is plain relaxation (the omega = 1 update); p = 1 applies the
+    microcanonical step at every subgroup, which leaves each subgroup's
+    Re tr[g K] and hence F unchanged; every step is a gauge transformation."""
+    dims = (4, 4, 4, 4)
+    U = field(dims, seed=95, gseed=96)
+    W = U.copy()
+    oracle.sr_half_sweep(U, 0, 0.0, 0, 7, 3)
+    oracle.or_half_sweep(W, 0, 1.0, 0)
+    np.testing.assert_allclose(U, W, atol=1e-14)
+    P = oracle.plaquette(U)
+    for gauge in (0, 1):
+        F = oracle.functional(U, gauge)
+        X = U.copy()
+        oracle.sr_half_sweep(X, 1, 1.0, gauge, 7, 4)
+        assert oracle.functional(X, gauge) == pytest.approx(F, abs=1e-13)
+        assert oracle.plaquette(X) == pytest.approx(P, abs=1e-13)
+        assert np.abs(X - U).max() > 1e-3  # it did move the links
+    # intermediate p: F between the two limits is not monotone but the draw is seeded
+    A, B = U.copy(), U.copy()
+    oracle.sr_half_sweep(A, 0, 0.5, 0, 11, 5)
+    oracle.sr_half_sweep(B, 0, 0.5, 0, 11, 5)
+    np.testing.assert_array_equal(A, B)
+
+
+def test_stochastic_relaxation_fixes_the_gauge():
+    dims = (4, 4, 4, 4)
+    U = field(dims, seed=97, gseed=98)
+    for n in range(400):
+        oracle.sr_half_sweep(U, n % 2, 0.8, 0, 3, n // 2)
+    assert oracle.theta(U, 0) < 1e-8
