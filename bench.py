@@ -165,11 +165,12 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     from paper_1209_4008_gb300 import synth
-    U = synth.as_numpy(synth.make_field(DIMS, PLAQ, *SEEDS))
+    dims = tuple(args.dims) if args.dims else DIMS
+    U = synth.as_numpy(synth.make_field(dims, PLAQ, *SEEDS))
     import oracle
     oracle.build()
     W = U.copy()
-    V = int(np.prod(DIMS))
+    V = int(np.prod(dims))
     for _ in range(args.warmup):
         oracle.or_sweeps(W, OMEGA, 0, 1)
     t0 = time.perf_counter()
@@ -182,11 +183,12 @@ def reference_arm(args, rank, world):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "landau-or-32^4 (one FP64 OR sweep per step, CPU oracle)",
-                   "lattice": list(DIMS), "omega": OMEGA, "plaquette": PLAQ, "seeds": list(SEEDS)},
+        "config": {"workload": f"landau-or-{'x'.join(map(str, dims))} (one FP64 OR sweep per step, CPU oracle)",
+                   "lattice": list(dims), "omega": OMEGA, "plaquette": PLAQ, "seeds": list(SEEDS)},
         "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": oracle.num_threads(),
                          "kind": "oracle",
-                         "sample": f"{args.steps} FP64 OR sweeps of the 32^4 field (one per step)"},
+                         "sample": f"{args.steps} FP64 OR sweeps of the {'x'.join(map(str, dims))} field "
+                                   f"(one per step)"},
         "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -236,6 +238,7 @@ def gpu_arm(args, rank, world, local):
     work = torch.empty_like(pristine)
 
     ctx = make_ctx(gf, gf.GF_MIXED)
+    gf.gf_set_option(ctx, "kernel_timing", 1)  # events around the sweep kernels, inside the graphs
 
     def step(c):
         work.copy_(pristine)
@@ -252,6 +255,8 @@ def gpu_arm(args, rank, world, local):
     checks = 0
     ms32 = ms64 = 0.0
     sw32 = sw64 = 0
+    kms = {"fp32": 0.0, "fp64": 0.0}
+    kn = {"fp32": 0, "fp64": 0}
     F_mixed = th_mixed = None
     barrier(world)
     torch.cuda.synchronize()
@@ -265,6 +270,9 @@ def gpu_arm(args, rank, world, local):
             ms64 += gf.gf_get_stat(ctx, "ms_fp64")
             sw32 += int(gf.gf_get_stat(ctx, "sweeps_fp32"))
             sw64 += int(gf.gf_get_stat(ctx, "sweeps_fp64"))
+            for ph in ("fp32", "fp64"):
+                kms[ph] += gf.gf_get_stat(ctx, f"ms_sweep_kernels_{ph}")
+                kn[ph] += int(gf.gf_get_stat(ctx, f"sweep_launches_{ph}"))
         e1.record(stream)
         torch.cuda.synchronize()
     barrier(world)
@@ -332,18 +340,23 @@ def gpu_arm(args, rank, world, local):
 
     pk = peaks()
     hbm = pk.get("hbm_gbs")
-    # dominant kernel of the step: the format whose phase took longer
-    dom = "fp64_18" if ms64 >= ms32 else "fp32_12"
-    roof = {"kernel": f"or_half_sweep[{dom}]", "bound": "hbm",
-            "achieved": thr[dom]["algorithmic_gbs"], "peak": hbm, "unit": "GB/s",
-            "frac": (thr[dom]["algorithmic_gbs"] / hbm) if hbm else None, "traffic": None,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6800"}
-    if dom.startswith("fp64"):
-        flops = Vh * 2253 / (thr[dom]["ms_per_half_sweep"] * 1e-3) / 1e12
+    # dominant kernel of the step: the half-sweep of the phase whose kernels took longer; its
+    # average launch duration comes from the events recorded around the sweep kernels of every
+    # check chunk of the timed steps (on the launching stream, inside the graphs)
+    ph = "fp64" if kms["fp64"] >= kms["fp32"] else "fp32"
+    dom = "fp64_18" if ph == "fp64" else "fp32_12"
+    t_launch = kms[ph] / max(1, kn[ph]) * 1e-3  # seconds per half-sweep launch
+    gbs = Vh * thr[dom]["bytes_per_site_update"] / t_launch / 1e9
+    roof = {"kernel": f"or_half_sweep[{dom}]", "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+            "frac": (gbs / hbm) if hbm else None, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6800",
+            "launch_ms": t_launch * 1e3, "launches_timed": kn[ph],
+            "isolated_launch_ms": thr[dom]["ms_per_half_sweep"]}
+    if ph == "fp64":
+        flops = Vh * 2253 / t_launch / 1e12
         roof.update({"bound": "alu", "achieved": flops, "peak": 1.25, "unit": "TFLOP/s",
                      "frac": flops / 1.25, "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)",
-                     "hbm_gbs": thr[dom]["algorithmic_gbs"], "hbm_frac": thr[dom]["algorithmic_gbs"] / hbm
-                     if hbm else None})
+                     "hbm_gbs": gbs, "hbm_frac": gbs / hbm if hbm else None})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -621,7 +634,7 @@ def main():
     ap.add_argument("--kernel", choices=sorted(FORMATS), help="time one storage format's sweep only")
     ap.add_argument("--tps", type=int, default=1)
     ap.add_argument("--block", type=int, default=64)
-    ap.add_argument("--dims", type=int, nargs=4)
+    ap.add_argument("--dims", type=int, nargs=4, help="lattice of --kernel and --impl reference (default 32^4)")
     ap.add_argument("--batched", action="store_true", help="the 64-lattice batched workload")
     ap.add_argument("--learned", action="store_true", help="train and evaluate the learned warm start")
     ap.add_argument("--pairs", type=int, default=2000)

@@ -108,6 +108,10 @@ int gf_set_stream(gf_ctx *ctx, void *stream);
  *                    arithmetic), 0 = autotuned or default (default 0)
  *   "block"          threads per block (multiple of 32, <= 1024; 0 = autotune)
  *   "use_graphs"     1 = replay sweep loops as CUDA graphs (default 1)
+ *   "kernel_timing"  1 = record CUDA events (inside the graphs) around the
+ *                    sweep kernels of every check chunk of gf_overrelax and
+ *                    report their time (default 0; creating the events may
+ *                    fail with GF_ECUDA)
  *   "sa_cap"         heatbath rejection cap per draw (default 64, <= 255)
  *   "sa_sweep_offset" Philox sweep counter of the first annealing sweep
  *   "stochastic_p"   > 0: gf_overrelax / gf_or_sweeps / gf_converge use
@@ -123,7 +127,10 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *value);
 
 /* Statistics of the last gf_overrelax / gf_anneal call:
  *   "sweeps", "sweeps_fp32", "sweeps_fp64", "checks", "ms_total",
- *   "ms_fp32", "ms_fp64", "threads_per_site", "block", "sa_rejects". */
+ *   "ms_fp32", "ms_fp64", "threads_per_site", "block", "sa_rejects";
+ *   with "kernel_timing": "ms_sweep_kernels_fp32", "sweep_launches_fp32",
+ *   "ms_sweep_kernels_fp64", "sweep_launches_fp64" (device time of the
+ *   half-sweep kernels of each phase and the number of launches it covers). */
 int gf_get_stat(const gf_ctx *ctx, const char *key, double *value);
 
 /* ---------------------------------------------------- the method, one call */

@@ -19,13 +19,14 @@ using namespace gf;
 namespace {
 
 struct GraphKey {
-    int fmt, tps, block, n, trackg, measure, reunit;
+    int fmt, tps, block, n, trackg, measure, reunit, ktime;
     double omega;
     const void *field, *gt;
     bool operator<(const GraphKey &o) const
     {
-        return std::tie(fmt, tps, block, n, trackg, measure, reunit, omega, field, gt) <
-               std::tie(o.fmt, o.tps, o.block, o.n, o.trackg, o.measure, o.reunit, o.omega, o.field, o.gt);
+        return std::tie(fmt, tps, block, n, trackg, measure, reunit, ktime, omega, field, gt) <
+               std::tie(o.fmt, o.tps, o.block, o.n, o.trackg, o.measure, o.reunit, o.ktime, o.omega, o.field,
+                        o.gt);
     }
 };
 
@@ -58,6 +59,10 @@ struct gf_ctx {
     int fp64_arith = 0;  // FP64 phase: 0 native FP64, 1 double-float on the FP32 pipe (DF64_18)
     int variant = 0;  // 0 auto, 1 per-subgroup rotations of the held links, 2 accumulate form
     int use_graphs = 1;
+    int kernel_timing = 0;     // events around the sweep kernels of every check chunk
+    cudaEvent_t kev[2] = { nullptr, nullptr };
+    double kms[2] = { 0.0, 0.0 };  // sweep-kernel milliseconds of the last call: [FP32 storage, FP64 class]
+    long kn[2] = { 0, 0 };         // half-sweep launches those milliseconds cover
     int autotune = 0;
     int sa_cap = 64;
     uint32_t sa_sweep_offset = 0;
@@ -287,7 +292,9 @@ static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, boo
 {
     std::pair<int, int> cfg = launch_config(ctx, fmt);
     FieldRef f = ref(ctx, field);
+    const bool kt = ctx->kernel_timing && n > 0;
     if (ctx->sr_p > 0.0) {  // stochastic relaxation: fresh Philox counters every sweep, no graph replay
+        if (kt) CK(cudaEventRecord(ctx->kev[0], ctx->stream));
         for (int k = 0; k < n; ++k, ++ctx->sr_sweep)
             for (int p = 0; p < 2; ++p) {
                 SweepArgs a = sweep_args(ctx, field, p, omega);
@@ -296,6 +303,7 @@ static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, boo
                 a.sweep = ctx->sr_sweep;
                 CK(launch_sweep(fmt, a, cfg.first, ctx->gauge, 2, false, cfg.second, ctx->stream));
             }
+        if (kt) CK(cudaEventRecord(ctx->kev[1], ctx->stream));
         if (reunit) CK(launch_reunitarize(fmt, f, ctx->geom, ctx->stream));
         if (measure) {
             CK(launch_measure(fmt, f, ctx->geom, ctx->gauge, ctx->partials, ctx->dres, ctx->stream));
@@ -304,12 +312,15 @@ static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, boo
         return GF_OK;
     }
     if (ctx->use_graphs && n > 0) {
-        GraphKey key{ fmt, cfg.first, cfg.second, n, trackg, measure, reunit, omega, field, ctx->gt };
+        GraphKey key{ fmt, cfg.first, cfg.second, n, trackg, measure, reunit, kt ? 1 : 0, omega, field, ctx->gt };
         auto it = ctx->graphs.find(key);
         if (it == ctx->graphs.end()) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = issue_sweeps(ctx, fmt, field, omega, n, trackg, cfg, ctx->cap);
+            cudaError_t e = cudaSuccess;
+            if (kt) e = cudaEventRecordWithFlags(ctx->kev[0], ctx->cap, cudaEventRecordExternal);
+            if (e == cudaSuccess) e = issue_sweeps(ctx, fmt, field, omega, n, trackg, cfg, ctx->cap);
+            if (e == cudaSuccess && kt) e = cudaEventRecordWithFlags(ctx->kev[1], ctx->cap, cudaEventRecordExternal);
             if (e == cudaSuccess && reunit) e = launch_reunitarize(fmt, f, ctx->geom, ctx->cap);
             if (e == cudaSuccess && measure)
                 e = launch_measure(fmt, f, ctx->geom, ctx->gauge, ctx->partials, ctx->dres, ctx->cap);
@@ -327,7 +338,9 @@ static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, boo
         CK(cudaGraphLaunch(it->second, ctx->stream));
         return GF_OK;
     }
+    if (kt) CK(cudaEventRecord(ctx->kev[0], ctx->stream));
     CK(issue_sweeps(ctx, fmt, field, omega, n, trackg, cfg, ctx->stream));
+    if (kt) CK(cudaEventRecord(ctx->kev[1], ctx->stream));
     if (reunit) CK(launch_reunitarize(fmt, f, ctx->geom, ctx->stream));
     if (measure) {
         CK(launch_measure(fmt, f, ctx->geom, ctx->gauge, ctx->partials, ctx->dres, ctx->stream));
@@ -361,6 +374,13 @@ static int converge(gf_ctx *ctx, double omega, double target, int budget, bool t
         if (n > budget - it) n = budget - it;
         RET(run_chunk(ctx, fmt, field, omega, n, trackg, true, reunit));
         CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->kernel_timing && n > 0) {
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, ctx->kev[0], ctx->kev[1]));
+            const int w = (fmt == F32_12 || fmt == F32_18) ? 0 : 1;
+            ctx->kms[w] += ms;
+            ctx->kn[w] += 2L * n;
+        }
         *F = ctx->hres[0];
         *theta = ctx->hres[1];
         it += n;
@@ -538,6 +558,8 @@ int gf_destroy(gf_ctx *ctx)
     cudaFree(ctx->dstatus);
     if (ctx->hres) cudaFreeHost(ctx->hres);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    for (int i = 0; i < 2; ++i)
+        if (ctx->kev[i]) cudaEventDestroy(ctx->kev[i]);
     delete ctx;
     return GF_OK;
 }
@@ -594,6 +616,12 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
         ctx->variant = iv;
     } else if (k == "use_graphs") {
         ctx->use_graphs = v != 0.0;
+    } else if (k == "kernel_timing") {
+        if (v != 0.0) {
+            for (int i = 0; i < 2; ++i)
+                if (!ctx->kev[i]) CK(cudaEventCreate(&ctx->kev[i]));
+        }
+        ctx->kernel_timing = v != 0.0;
     } else if (k == "autotune") {
         ctx->autotune = v != 0.0;
     } else if (k == "track") {
@@ -633,6 +661,7 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *v)
     else if (k == "variant") *v = ctx->variant;
     else if (k == "fp64_arith") *v = ctx->fp64_arith;
     else if (k == "use_graphs") *v = ctx->use_graphs;
+    else if (k == "kernel_timing") *v = ctx->kernel_timing;
     else if (k == "autotune") *v = ctx->autotune;
     else if (k == "sa_cap") *v = ctx->sa_cap;
     else if (k == "track") *v = ctx->track;
@@ -771,6 +800,8 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
     if (!(theta_target >= 0.0) || !std::isfinite(theta_target)) return fail(ctx, GF_EINVAL, "theta_target");
     if (max_iter < 0) return fail(ctx, GF_EINVAL, "max_iter < 0");
     ctx->stats.clear();
+    ctx->kms[0] = ctx->kms[1] = 0.0;
+    ctx->kn[0] = ctx->kn[1] = 0;
     double t0 = now_ms();
     RET(ensure_common(ctx));
     const double *view;
@@ -857,6 +888,12 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
     ctx->stats["sweeps_fp64"] = used64;
     ctx->stats["ms_fp32"] = ms32;
     ctx->stats["ms_fp64"] = ms64;
+    if (ctx->kernel_timing) {
+        ctx->stats["ms_sweep_kernels_fp32"] = ctx->kms[0];
+        ctx->stats["sweep_launches_fp32"] = (double)ctx->kn[0];
+        ctx->stats["ms_sweep_kernels_fp64"] = ctx->kms[1];
+        ctx->stats["sweep_launches_fp64"] = (double)ctx->kn[1];
+    }
     ctx->stats["ms_total"] = now_ms() - t0;
     ctx->stats["threads_per_site"] = cfg.first;
     ctx->stats["block"] = cfg.second;

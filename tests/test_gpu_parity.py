@@ -426,3 +426,24 @@ def test_overrelax_with_stochastic_relaxation_converges():
         for parity in (0, 1):
             oracle.sr_half_sweep(V, parity, 0.85, 0, 3, n)
     assert max_rel(host(d), V) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# in-graph kernel timing (used for the benchmark's roofline)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_kernel_timing_counts_every_sweep_launch(graphs):
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=3, gseed=4)
+    c = ctx_for(dims, 0, check_every=10, precision=gf.GF_MIXED, use_graphs=graphs, kernel_timing=1)
+    ref = ctx_for(dims, 0, check_every=10, precision=gf.GF_MIXED, use_graphs=graphs)
+    d, e = dev(U), dev(U)
+    r = gf.gf_overrelax(c, d, 1.7, 1e-14, 20000)
+    r0 = gf.gf_overrelax(ref, e, 1.7, 1e-14, 20000)
+    assert r[0] and r[1] == r0[1]
+    assert torch.equal(d, e)  # the events change nothing in the result
+    for ph in ("fp32", "fp64"):
+        n = gf.gf_get_stat(c, f"sweep_launches_{ph}")
+        assert n == 2 * gf.gf_get_stat(c, f"sweeps_{ph}")
+        ms = gf.gf_get_stat(c, f"ms_sweep_kernels_{ph}")
+        assert 0.0 < ms <= gf.gf_get_stat(c, f"ms_{ph}")
