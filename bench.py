@@ -417,17 +417,27 @@ def kernel_only(args):
     gf.gf_set_option(c, "use_graphs", 0)
     gf.gf_set_stream(c, torch.cuda.current_stream())
     gf.gf_upload(c, field, prec)
-    gf.gf_or_sweeps(c, OMEGA, args.warmup)
+
+    def sweeps(n, first):
+        if args.sa_temp is None:
+            gf.gf_or_sweeps(c, OMEGA, n)
+        else:  # heatbath half-sweeps at the fixed temperature
+            for k in range(first, first + n):
+                gf.gf_sa_half_sweep(c, 0, args.sa_temp, 9, k)
+                gf.gf_sa_half_sweep(c, 1, args.sa_temp, 9, k)
+
+    sweeps(args.warmup, 0)
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(s)
-    gf.gf_or_sweeps(c, OMEGA, args.steps)
+    sweeps(args.steps, args.warmup)
     e1.record(s)
     torch.cuda.synchronize()
     t_half = e0.elapsed_time(e1) / (2 * args.steps)
     Vh = int(np.prod(dims)) // 2
-    print(json.dumps({"kernel": args.kernel, "dims": list(dims), "tps": args.tps, "block": args.block,
+    print(json.dumps({"kernel": args.kernel + ("" if args.sa_temp is None else f" heatbath T={args.sa_temp}"),
+                      "dims": list(dims), "tps": args.tps, "block": args.block,
                       "ms_per_half_sweep": t_half, "gsu_per_s": Vh / (t_half * 1e-3) / 1e9,
                       "algorithmic_gbs": Vh * nbytes / (t_half * 1e-3) / 1e9}), flush=True)
 
@@ -508,29 +518,35 @@ def learned(args):
     from paper_1209_4008_gb300 import gf, learned as L, synth
     t_start = time.perf_counter()
     train_dims = (16, 16, 16, 16)
-    ctx = gf.gf_create(train_dims, gf.GF_LANDAU)
-    gf.gf_set_option(ctx, "autotune", 1)
-    pairs = []
-    t0 = time.perf_counter()
-    for k in range(args.pairs):
-        U = synth.make_field(train_dims, PLAQ, 1000 + k, 3000 + k, device="cuda")
-        pairs.append(L.make_pair(ctx, U, theta_switch=THETA_SWITCH, label_theta=1e-12, check_every=CHECK_EVERY))
-    t_data = time.perf_counter() - t0
-    nval = max(1, args.pairs // 10)
-    train_set, val_set = pairs[nval:], pairs[:nval]
-    net = gf.gf_net_create(train_dims)
-    gf.gf_net_set_params(net, L.init_params(0))
-    t0 = time.perf_counter()
-    hist = L.train(net, train_set, epochs=args.epochs, lr=args.lr, lr_decay=0.7,
-                   log=lambda m: print(m, file=sys.stderr, flush=True))
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    val = L.validation_loss(net, val_set)
-    params = np.zeros(gf.gf_net_param_count(), dtype=np.float32)
-    gf.gf_net_get_params(net, params)
+    t_data = t_train = 0.0
+    hist, val = [], None
+    if args.weights:
+        params = np.load(args.weights).astype(np.float32)
+    else:
+        ctx = gf.gf_create(train_dims, gf.GF_LANDAU)
+        gf.gf_set_option(ctx, "autotune", 1)
+        pairs = []
+        t0 = time.perf_counter()
+        for k in range(args.pairs):
+            U = synth.make_field(train_dims, PLAQ, 1000 + k, 3000 + k, device="cuda")
+            pairs.append(L.make_pair(ctx, U, theta_switch=THETA_SWITCH, label_theta=1e-12,
+                                     check_every=CHECK_EVERY))
+        t_data = time.perf_counter() - t0
+        nval = max(1, args.pairs // 10)
+        train_set, val_set = pairs[nval:], pairs[:nval]
+        net = gf.gf_net_create(train_dims)
+        gf.gf_net_set_params(net, L.init_params(0))
+        t0 = time.perf_counter()
+        hist = L.train(net, train_set, epochs=args.epochs, lr=args.lr, lr_decay=args.lr_decay,
+                       log=lambda m: print(m, file=sys.stderr, flush=True))
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        val = L.validation_loss(net, val_set)
+        params = np.zeros(gf.gf_net_param_count(), dtype=np.float32)
+        gf.gf_net_get_params(net, params)
     if args.save:
-        os.makedirs(os.path.dirname(WEIGHTS), exist_ok=True)
-        np.save(WEIGHTS, params)
+        os.makedirs(os.path.dirname(os.path.abspath(args.save)), exist_ok=True)
+        np.save(args.save, params)
     # evaluation on 32^4 fields
     big = gf.gf_net_create(DIMS)
     gf.gf_net_set_params(big, params)
@@ -559,8 +575,9 @@ def learned(args):
         res.append(row)
     mean = lambda key, mode: float(np.mean([r[mode][key] for r in res]))
     print(json.dumps({
-        "workload": f"learned warm start: {args.pairs} solver pairs on 16^4 (plaquette 0.60), "
-                    f"{args.epochs} epochs Adam; test on {args.eval_fields} fresh 32^4 fields, theta<1e-14",
+        "workload": (f"learned warm start: stored parameters {args.weights}" if args.weights else
+                     f"learned warm start: {args.pairs} solver pairs on 16^4 (plaquette 0.60), "
+                     f"{args.epochs} epochs Adam") + f"; test on {args.eval_fields} fresh 32^4 fields, theta<1e-14",
         "data_s": t_data, "train_s": t_train, "train_loss": hist, "val_loss": val,
         "eval": res,
         "mean": {"mixed_s": mean("s", "mixed"), "learned_s": mean("s", "learned"),
@@ -634,14 +651,19 @@ def main():
     ap.add_argument("--kernel", choices=sorted(FORMATS), help="time one storage format's sweep only")
     ap.add_argument("--tps", type=int, default=1)
     ap.add_argument("--block", type=int, default=64)
+    ap.add_argument("--sa-temp", type=float, help="--kernel: time heatbath half-sweeps at this temperature")
     ap.add_argument("--dims", type=int, nargs=4, help="lattice of --kernel and --impl reference (default 32^4)")
     ap.add_argument("--batched", action="store_true", help="the 64-lattice batched workload")
     ap.add_argument("--learned", action="store_true", help="train and evaluate the learned warm start")
     ap.add_argument("--pairs", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-decay", type=float, default=0.7, help="learning-rate factor per epoch")
     ap.add_argument("--eval-fields", type=int, default=4)
-    ap.add_argument("--save", action="store_true", help="store the trained parameters")
+    ap.add_argument("--save", nargs="?", const=WEIGHTS, default=None, metavar="PATH",
+                    help=f"store the trained parameters (.npy; default path {os.path.relpath(WEIGHTS, ROOT)})")
+    ap.add_argument("--weights", metavar="PATH",
+                    help="--learned: skip the pairs and training, evaluate these stored parameters")
     ap.add_argument("--coulomb", action="store_true", help="the 48^3x96 Coulomb workload with annealing")
     ap.add_argument("--seeds", type=int, default=8)
     ap.add_argument("--sa-sweeps", type=int, default=3000)

@@ -443,7 +443,8 @@ __device__ __forceinline__ int heatbath_quat(const double k[4], double T, uint32
     double sp, cp;
     sincos(phi, &sp, &cp);
     double s[4] = { s0, rho * st * cp, rho * st * sp, rho * ct };
-    double kh[4] = { k[0] / kn, k[1] / kn, k[2] / kn, k[3] / kn };
+    const double ikn = 1.0 / kn;  // one FP64 division instead of four
+    double kh[4] = { k[0] * ikn, k[1] * ikn, k[2] * ikn, k[3] * ikn };
     // r = s kh (product of the SU(2) matrices)
     r[0] = s[0] * kh[0] - (s[1] * kh[1] + s[2] * kh[2] + s[3] * kh[3]);
     r[1] = s[0] * kh[1] + kh[0] * s[1] - (s[2] * kh[3] - s[3] * kh[2]);

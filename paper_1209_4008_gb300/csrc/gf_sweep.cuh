@@ -105,6 +105,135 @@ __device__ __forceinline__ void reload<DF64_18>(const FieldRef &f, int pl0, int 
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// SU(2) subgroup element as R = [[alpha, beta], [-conj(beta), conj(alpha)]],
+// alpha = r0 + i r3, beta = r2 + i r1 (the quaternion convention of rotate_rows)
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ cpx<T> cconj(cpx<T> z) { return mk<T>(z.re, -z.im); }
+template <class T>
+__device__ __forceinline__ cpx<T> cneg(cpx<T> z) { return mk<T>(-z.re, -z.im); }
+template <class T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> x, cpx<T> y)
+{
+    return mk<T>(x.re * y.re - x.im * y.im, x.re * y.im + x.im * y.re);
+}
+// new row a: alpha x_a + beta x_b
+template <class T>
+__device__ __forceinline__ cpx<T> lin_a(cpx<T> al, cpx<T> be, cpx<T> xa, cpx<T> xb)
+{
+    return mk<T>(al.re * xa.re - al.im * xa.im + be.re * xb.re - be.im * xb.im,
+                 al.re * xa.im + al.im * xa.re + be.re * xb.im + be.im * xb.re);
+}
+// new row b: -conj(beta) x_a + conj(alpha) x_b
+template <class T>
+__device__ __forceinline__ cpx<T> lin_b(cpx<T> al, cpx<T> be, cpx<T> xa, cpx<T> xb)
+{
+    return mk<T>(al.re * xb.re + al.im * xb.im - be.re * xa.re - be.im * xa.im,
+                 al.re * xb.im - al.im * xb.re - be.re * xa.im + be.im * xa.re);
+}
+
+template <class T>
+struct quat {
+    T k[4];
+};
+
+// quaternion of the 2x2 block [[xaa, xab], [xba, xbb]] (see add_block_quaternion)
+template <class T>
+__device__ __forceinline__ quat<T> block_quaternion(cpx<T> xaa, cpx<T> xab, cpx<T> xba, cpx<T> xbb)
+{
+    quat<T> q;
+    q.k[0] = xaa.re + xbb.re;
+    q.k[1] = -(xab.im + xba.im);
+    q.k[2] = xba.re - xab.re;
+    q.k[3] = xbb.im - xaa.im;
+    return q;
+}
+
+// the subgroup's new element from its quaternion k (overrelaxation, heatbath
+// draw or stochastic relaxation); the identity when the step leaves it unchanged
+template <int MODE, class T>
+__device__ __forceinline__ void subgroup_element(const SweepArgs &a, quat<T> q, uint32_t site, int sg, cpx<T> &al,
+                                                 cpx<T> &be)
+{
+    T r[4];
+    bool ok;
+    if (MODE == MODE_OR) {
+        ok = overrelax_quat(q.k, (T)a.omega, r);
+    } else if (MODE == MODE_SR) {
+        ok = sr_quat(q.k, a.prob, site, a.sweep, sg, a.key, r);
+    } else {
+        double kd[4] = { (double)q.k[0], (double)q.k[1], (double)q.k[2], (double)q.k[3] };
+        double rd[4];
+        int st = heatbath_quat(kd, a.T, site, a.sweep, sg, a.cap, a.key, rd);
+        if (st == 0) atomicAdd(a.status, 1);
+        ok = (st == 1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) r[i] = (T)rd[i];
+    }
+    if (!ok) {
+        r[0] = T(1);
+        r[1] = r[2] = r[3] = T(0);
+    }
+    al = mk<T>(r[0], r[3]);
+    be = mk<T>(r[2], r[1]);
+}
+
+// rows 0 and 1 of a stored link, re-read (volatile); row 2 is left unset
+template <int FMT>
+__device__ __forceinline__ void reload_rows01(const FieldRef &f, int pl0, int h, mat3<typename Store<FMT>::T> &u);
+
+template <>
+__device__ __forceinline__ void reload_rows01<F64_18>(const FieldRef &f, int pl0, int h, mat3<double> &u)
+{
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const double2 *p = reinterpret_cast<const double2 *>(f.base + (pl0 + c) * f.plane_bytes) + h;
+        double2 v;
+        asm volatile("ld.global.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+        u.e[c / 3][c % 3] = mk<double>(v.x, v.y);
+    }
+}
+
+template <>
+__device__ __forceinline__ void reload_rows01<F64_12>(const FieldRef &f, int pl0, int h, mat3<double> &u)
+{
+    reload_rows01<F64_18>(f, pl0, h, u);  // the same first six chunks
+}
+
+template <>
+__device__ __forceinline__ void reload_rows01<F32_18>(const FieldRef &f, int pl0, int h, mat3<float> &u)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float4 *p = reinterpret_cast<const float4 *>(f.base + (pl0 + c) * f.plane_bytes) + h;
+        float4 v;
+        asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+        int e0 = 2 * c, e1 = 2 * c + 1;
+        u.e[e0 / 3][e0 % 3] = mk<float>(v.x, v.y);
+        u.e[e1 / 3][e1 % 3] = mk<float>(v.z, v.w);
+    }
+}
+
+template <>
+__device__ __forceinline__ void reload_rows01<F32_12>(const FieldRef &f, int pl0, int h, mat3<float> &u)
+{
+    reload_rows01<F32_18>(f, pl0, h, u);  // the same first three chunks
+}
+
+template <>
+__device__ __forceinline__ void reload_rows01<DF64_18>(const FieldRef &f, int pl0, int h, mat3<double> &u)
+{
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const float4 *p = reinterpret_cast<const float4 *>(f.base + (pl0 + c) * f.plane_bytes) + h;
+        float4 v;
+        asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+        u.e[c / 3][c % 3] = mk<double>((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
+}
+
 // z = x y for 3x3 complex matrices; rows >= ROWS of z are not computed
 template <class T, int ROWS>
 __device__ __forceinline__ void mul_rows(const mat3<T> &x, const mat3<T> &y, mat3<T> &z)
@@ -183,42 +312,51 @@ __device__ __forceinline__ void sweep_site_acc(const SweepArgs &a, int h)
             }
     }
     const uint32_t site = (uint32_t)lex_index(a.g, c);
-    mat3<T> G = identity3<T>();
-#pragma unroll
-    for (int sg = 0; sg < 3; ++sg) {
-        int ra, rb;
-        subgroup_rows(sg, ra, rb);
-        T k[4] = { T(0), T(0), T(0), T(0) };
-        add_block_quaternion(M, ra, rb, k);
-        T r[4];
-        bool ok;
-        if (MODE == MODE_OR) {
-            ok = overrelax_quat(k, (T)a.omega, r);
-        } else if (MODE == MODE_SR) {
-            ok = sr_quat(k, a.prob, site, a.sweep, sg, a.key, r);
-        } else {
-            double kd[4] = { (double)k[0], (double)k[1], (double)k[2], (double)k[3] };
-            double rd[4];
-            int st = heatbath_quat(kd, a.T, site, a.sweep, sg, a.cap, a.key, rd);
-            if (st == 0) atomicAdd(a.status, 1);
-            ok = (st == 1);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) r[i] = (T)rd[i];
-        }
-        if (ok) {
-            rotate_rows(M, ra, rb, r);
-            rotate_rows(G, ra, rb, r);
-        }
+    // The three subgroups in Alg. 1 order, (0,1), (1,2), (0,2).  Of each rotated
+    // M only the entries that the next subgroup's quaternion reads are formed:
+    // R1 M rows 0 (cols 0, 2) and 1 (cols 0..2), then R2 R1 M row 2 (cols 0, 2).
+    cpx<T> al[3], be[3];
+    subgroup_element<MODE>(a, block_quaternion(M.e[0][0], M.e[0][1], M.e[1][0], M.e[1][1]), site, 0, al[0],
+                           be[0]);
+    const cpx<T> m00 = lin_a(al[0], be[0], M.e[0][0], M.e[1][0]);
+    const cpx<T> m02 = lin_a(al[0], be[0], M.e[0][2], M.e[1][2]);
+    const cpx<T> m10 = lin_b(al[0], be[0], M.e[0][0], M.e[1][0]);
+    const cpx<T> m11 = lin_b(al[0], be[0], M.e[0][1], M.e[1][1]);
+    const cpx<T> m12 = lin_b(al[0], be[0], M.e[0][2], M.e[1][2]);
+    subgroup_element<MODE>(a, block_quaternion(m11, m12, M.e[2][1], M.e[2][2]), site, 1, al[1], be[1]);
+    const cpx<T> n20 = lin_b(al[1], be[1], m10, M.e[2][0]);
+    const cpx<T> n22 = lin_b(al[1], be[1], m12, M.e[2][2]);
+    subgroup_element<MODE>(a, block_quaternion(m00, m02, n20, n22), site, 2, al[2], be[2]);
+    // G = R3 R2 R1 in closed form (the zero pattern of the embedded factors
+    // saves most of the three full row rotations)
+    mat3<T> G;
+    {
+        const cpx<T> a1c = cconj(al[0]), b1c = cconj(be[0]), b2c = cconj(be[1]);
+        const cpx<T> g20 = cmul(b2c, b1c), g21 = cneg(cmul(b2c, a1c)), g22 = cconj(al[1]);
+        G.e[1][0] = cneg(cmul(al[1], b1c));
+        G.e[1][1] = cmul(al[1], a1c);
+        G.e[1][2] = be[1];
+        G.e[0][0] = lin_a(al[2], be[2], al[0], g20);
+        G.e[0][1] = lin_a(al[2], be[2], be[0], g21);
+        G.e[0][2] = cmul(be[2], g22);
+        G.e[2][0] = lin_b(al[2], be[2], al[0], g20);
+        G.e[2][1] = lin_b(al[2], be[2], be[0], g21);
+        G.e[2][2] = cmul(cconj(al[2]), g22);
     }
-    // apply G: U_mu(x) <- G U_mu(x), U_mu(x-mu) <- U_mu(x-mu) G^dagger
+    // apply G: U_mu(x) <- G U_mu(x), U_mu(x-mu) <- U_mu(x-mu) G^dagger.  Rows 0, 1
+    // are multiplied out; an 18-real link gets row 2 = conj(row0 x row1), which
+    // is the product's third row for SU(3) factors (Sec. 4.1) at 2/3 of the cost,
+    // and the backward link is re-read without its third row.
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
         mat3<T> u, v;
         reload<FMT>(a.f, (p * 4 + mu) * S::NCHUNK, h, u);
-        mul_rows<T, ROWS>(G, u, v);
+        mul_rows<T, 2>(G, u, v);
+        if (ROWS == 3) rebuild_row2(v);
         S::store(a.f, (p * 4 + mu) * S::NCHUNK, h, v);
-        reload<FMT>(a.f, ((p ^ 1) * 4 + mu) * S::NCHUNK, hb[mu], u);
-        mul_rows_dagger<T, ROWS>(u, G, v);
+        reload_rows01<FMT>(a.f, ((p ^ 1) * 4 + mu) * S::NCHUNK, hb[mu], u);
+        mul_rows_dagger<T, 2>(u, G, v);
+        if (ROWS == 3) rebuild_row2(v);
         S::store(a.f, ((p ^ 1) * 4 + mu) * S::NCHUNK, hb[mu], v);
     }
     if (TRACKG) {

@@ -12,21 +12,94 @@
 
 namespace gf {
 
-// rows a, b of x <- R (rows a, b), R the SU(2) element r (quaternion)
-__device__ __forceinline__ void rotate_rows_df(mat3df &x, int a, int b, const df r[4])
+__device__ __forceinline__ cdf cdf_conj(cdf z)
 {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        cdf xa = x.e[a][c], xb = x.e[b][c];
-        x.e[a][c].re = df_add(df_sub(df_mul(r[0], xa.re), df_mul(r[3], xa.im)),
-                              df_sub(df_mul(r[2], xb.re), df_mul(r[1], xb.im)));
-        x.e[a][c].im = df_add(df_add(df_mul(r[0], xa.im), df_mul(r[3], xa.re)),
-                              df_add(df_mul(r[2], xb.im), df_mul(r[1], xb.re)));
-        x.e[b][c].re = df_sub(df_add(df_mul(r[0], xb.re), df_mul(r[3], xb.im)),
-                              df_add(df_mul(r[2], xa.re), df_mul(r[1], xa.im)));
-        x.e[b][c].im = df_add(df_sub(df_mul(r[0], xb.im), df_mul(r[3], xb.re)),
-                              df_sub(df_mul(r[1], xa.re), df_mul(r[2], xa.im)));
+    z.im = df_neg(z.im);
+    return z;
+}
+
+__device__ __forceinline__ cdf cdf_neg(cdf z)
+{
+    z.re = df_neg(z.re);
+    z.im = df_neg(z.im);
+    return z;
+}
+
+__device__ __forceinline__ cdf cdf_mul(cdf x, cdf y)
+{
+    cdf r;
+    r.re = df_sub(df_mul(x.re, y.re), df_mul(x.im, y.im));
+    r.im = df_add(df_mul(x.re, y.im), df_mul(x.im, y.re));
+    return r;
+}
+
+// alpha x_a + beta x_b (new row a of an SU(2) rotation)
+__device__ __forceinline__ cdf lin_a_df(cdf al, cdf be, cdf xa, cdf xb)
+{
+    cdf p = cdf_mul(al, xa), q = cdf_mul(be, xb);
+    p.re = df_add(p.re, q.re);
+    p.im = df_add(p.im, q.im);
+    return p;
+}
+
+// -conj(beta) x_a + conj(alpha) x_b (new row b)
+__device__ __forceinline__ cdf lin_b_df(cdf al, cdf be, cdf xa, cdf xb)
+{
+    cdf p = cdf_mul(cdf_conj(al), xb), q = cdf_mul(cdf_conj(be), xa);
+    p.re = df_sub(p.re, q.re);
+    p.im = df_sub(p.im, q.im);
+    return p;
+}
+
+// conj(a d - b c)
+__device__ __forceinline__ cdf conj_cross_df(cdf a, cdf d, cdf b, cdf c)
+{
+    cdf p = cdf_mul(a, d), q = cdf_mul(b, c);
+    cdf r;
+    r.re = df_sub(p.re, q.re);
+    r.im = df_sub(q.im, p.im);
+    return r;
+}
+
+// third row of an SU(3) link from its first two rows, stored
+__device__ __forceinline__ void store_row2_df(const FieldRef &f, int pl0, int h, const cdf v[2][3])
+{
+    store_chunk_df(f, pl0 + 6, h, conj_cross_df(v[0][1], v[1][2], v[0][2], v[1][1]));
+    store_chunk_df(f, pl0 + 7, h, conj_cross_df(v[0][2], v[1][0], v[0][0], v[1][2]));
+    store_chunk_df(f, pl0 + 8, h, conj_cross_df(v[0][0], v[1][1], v[0][1], v[1][0]));
+}
+
+// subgroup element from the 2x2 block [[xaa, xab], [xba, xbb]]: the quaternion
+// in FP64, the scalar step in FP64 (overrelaxation, stochastic choice or
+// heatbath draw), the result as R = [[alpha, beta], [-conj(beta), conj(alpha)]]
+template <int MODE>
+__device__ __forceinline__ void subgroup_element_df(const SweepArgs &a, cdf xaa, cdf xab, cdf xba, cdf xbb,
+                                                    uint32_t site, int sg, cdf &al, cdf &be)
+{
+    double k[4];
+    k[0] = df_to_double(df_add(xaa.re, xbb.re));
+    k[1] = -df_to_double(df_add(xab.im, xba.im));
+    k[2] = df_to_double(df_sub(xba.re, xab.re));
+    k[3] = df_to_double(df_sub(xbb.im, xaa.im));
+    double rd[4];
+    bool ok;
+    if (MODE == MODE_OR) {
+        ok = overrelax_quat(k, a.omega, rd);
+    } else if (MODE == MODE_SR) {
+        ok = sr_quat(k, a.prob, site, a.sweep, sg, a.key, rd);
+    } else {
+        int st = heatbath_quat(k, a.T, site, a.sweep, sg, a.cap, a.key, rd);
+        if (st == 0) atomicAdd(a.status, 1);
+        ok = (st == 1);
     }
+    if (!ok) {
+        rd[0] = 1.0;
+        rd[1] = rd[2] = rd[3] = 0.0;
+    }
+    al.re = df_from_double(rd[0]);
+    al.im = df_from_double(rd[3]);
+    be.re = df_from_double(rd[2]);
+    be.im = df_from_double(rd[1]);
 }
 
 template <bool COULOMB, int MODE, bool TRACKG>
@@ -64,62 +137,58 @@ __device__ __forceinline__ void sweep_site_df(const SweepArgs &a, int h)
             }
     }
     const uint32_t site = (uint32_t)lex_index(a.g, c);
+    // subgroups (0,1), (1,2), (0,2) as in the FP64 accumulate form: only the
+    // entries of the rotated M that the next quaternion reads are formed
+    cdf al[3], be[3];
+    subgroup_element_df<MODE>(a, M.e[0][0], M.e[0][1], M.e[1][0], M.e[1][1], site, 0, al[0], be[0]);
+    const cdf m00 = lin_a_df(al[0], be[0], M.e[0][0], M.e[1][0]);
+    const cdf m02 = lin_a_df(al[0], be[0], M.e[0][2], M.e[1][2]);
+    const cdf m10 = lin_b_df(al[0], be[0], M.e[0][0], M.e[1][0]);
+    const cdf m11 = lin_b_df(al[0], be[0], M.e[0][1], M.e[1][1]);
+    const cdf m12 = lin_b_df(al[0], be[0], M.e[0][2], M.e[1][2]);
+    subgroup_element_df<MODE>(a, m11, m12, M.e[2][1], M.e[2][2], site, 1, al[1], be[1]);
+    const cdf n20 = lin_b_df(al[1], be[1], m10, M.e[2][0]);
+    const cdf n22 = lin_b_df(al[1], be[1], m12, M.e[2][2]);
+    subgroup_element_df<MODE>(a, m00, m02, n20, n22, site, 2, al[2], be[2]);
+    // G = R3 R2 R1 in closed form
     mat3df G;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            G.e[i][j] = cdf_zero();
-            if (i == j) G.e[i][j].re = df_make(1.f, 0.f);
-        }
-#pragma unroll
-    for (int sg = 0; sg < 3; ++sg) {
-        int ra, rb;
-        subgroup_rows(sg, ra, rb);
-        // quaternion of the (ra, rb) block of M (see add_block_quaternion)
-        double k[4];
-        k[0] = df_to_double(df_add(M.e[ra][ra].re, M.e[rb][rb].re));
-        k[1] = -df_to_double(df_add(M.e[ra][rb].im, M.e[rb][ra].im));
-        k[2] = df_to_double(df_sub(M.e[rb][ra].re, M.e[ra][rb].re));
-        k[3] = df_to_double(df_sub(M.e[rb][rb].im, M.e[ra][ra].im));
-        double rd[4];
-        bool ok;
-        if (MODE == MODE_OR) {
-            ok = overrelax_quat(k, a.omega, rd);
-        } else if (MODE == MODE_SR) {
-            ok = sr_quat(k, a.prob, site, a.sweep, sg, a.key, rd);
-        } else {
-            int st = heatbath_quat(k, a.T, site, a.sweep, sg, a.cap, a.key, rd);
-            if (st == 0) atomicAdd(a.status, 1);
-            ok = (st == 1);
-        }
-        if (ok) {
-            df r[4] = { df_from_double(rd[0]), df_from_double(rd[1]), df_from_double(rd[2]), df_from_double(rd[3]) };
-            rotate_rows_df(M, ra, rb, r);
-            rotate_rows_df(G, ra, rb, r);
-        }
+    {
+        const cdf a1c = cdf_conj(al[0]), b1c = cdf_conj(be[0]), b2c = cdf_conj(be[1]);
+        const cdf g20 = cdf_mul(b2c, b1c), g21 = cdf_neg(cdf_mul(b2c, a1c)), g22 = cdf_conj(al[1]);
+        G.e[1][0] = cdf_neg(cdf_mul(al[1], b1c));
+        G.e[1][1] = cdf_mul(al[1], a1c);
+        G.e[1][2] = be[1];
+        G.e[0][0] = lin_a_df(al[2], be[2], al[0], g20);
+        G.e[0][1] = lin_a_df(al[2], be[2], be[0], g21);
+        G.e[0][2] = cdf_mul(be[2], g22);
+        G.e[2][0] = lin_b_df(al[2], be[2], al[0], g20);
+        G.e[2][1] = lin_b_df(al[2], be[2], be[0], g21);
+        G.e[2][2] = cdf_mul(cdf_conj(al[2]), g22);
     }
-    // U_mu(x) <- G U_mu(x): one column of U at a time, each output chunk stored
-    // as soon as it is formed (few live registers);
-    // U_mu(x-mu) <- U_mu(x-mu) G^dagger: one row of U at a time
+    // U_mu(x) <- G U_mu(x) and U_mu(x-mu) <- U_mu(x-mu) G^dagger: rows 0, 1
+    // multiplied out (forward: one column of U at a time; backward: one row),
+    // row 2 = conj(row0 x row1)
 #pragma unroll 1
     for (int mu = 0; mu < 4; ++mu) {
         const int pf = (p * 4 + mu) * 9, pb = ((p ^ 1) * 4 + mu) * 9;
+        cdf v[2][3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             cdf col[3];
 #pragma unroll
             for (int l = 0; l < 3; ++l) col[l] = reload_chunk_df(a.f, pf + 3 * l + j, h);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
+            for (int i = 0; i < 2; ++i) {
                 cdf s = cdf_zero();
 #pragma unroll
                 for (int l = 0; l < 3; ++l) s = cdf_mac(s, G.e[i][l], col[l]);
+                v[i][j] = s;
                 store_chunk_df(a.f, pf + 3 * i + j, h, s);
             }
         }
+        store_row2_df(a.f, pf, h, v);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < 2; ++i) {
             cdf row[3];
 #pragma unroll
             for (int l = 0; l < 3; ++l) row[l] = reload_chunk_df(a.f, pb + 3 * i + l, hb[mu]);
@@ -128,9 +197,11 @@ __device__ __forceinline__ void sweep_site_df(const SweepArgs &a, int h)
                 cdf s = cdf_zero();
 #pragma unroll
                 for (int l = 0; l < 3; ++l) s = cdf_mac_conj(s, row[l], G.e[j][l]);
+                v[i][j] = s;
                 store_chunk_df(a.f, pb + 3 * i + j, hb[mu], s);
             }
         }
+        store_row2_df(a.f, pb, hb[mu], v);
     }
     if (TRACKG) {
         mat3<float> gx, gy, Gf;
