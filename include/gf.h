@@ -106,7 +106,9 @@ int gf_set_stream(gf_ctx *ctx, void *stream);
  *                    sum of the links with G = R3 R2 R1 accumulated and applied
  *                    once per link (one thread per site; equal in exact
  *                    arithmetic), 0 = autotuned or default (default 0)
- *   "block"          threads per block (multiple of 32, <= 1024; 0 = autotune)
+ *   "block"          threads per block (multiple of 32, <= 256; 0 = autotune)
+ *   "acc_registers"  accumulate form on FP64 storage: register budget per
+ *                    thread, 255, 168 or 128 (0 = autotuned or 255; default 0)
  *   "use_graphs"     1 = replay sweep loops as CUDA graphs (default 1)
  *   "kernel_timing"  1 = record CUDA events (inside the graphs) around the
  *                    sweep kernels of every check chunk of gf_overrelax and
@@ -127,7 +129,8 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *value);
 
 /* Statistics of the last gf_overrelax / gf_anneal call:
  *   "sweeps", "sweeps_fp32", "sweeps_fp64", "checks", "ms_total",
- *   "ms_fp32", "ms_fp64", "threads_per_site", "block", "sa_rejects";
+ *   "ms_fp32", "ms_fp64", "threads_per_site", "block", "accumulate_form",
+ *   "acc_registers", "sa_rejects";
  *   with "kernel_timing": "ms_sweep_kernels_fp32", "sweep_launches_fp32",
  *   "ms_sweep_kernels_fp64", "sweep_launches_fp64" (device time of the
  *   half-sweep kernels of each phase and the number of launches it covers). */
@@ -205,7 +208,11 @@ int gf_reunitarize(gf_ctx *ctx);
 
 /* Pick threads per site and block size for the resident field's storage by
  * timing every candidate on a scratch copy; the choice is cached per
- * (volume, storage, gauge) for the process.  Outputs may be NULL. */
+ * (volume, storage, gauge) for the process.  Outputs may be NULL.
+ * threads_per_site: 1, 2, 4, 8 = per-subgroup form with that many threads per
+ * site; 0, -1, -2 = accumulate form, one thread per site, with at most 255,
+ * 168 or 128 registers per thread (the budget of the last two is tried for
+ * FP64 storage only). */
 int gf_autotune(gf_ctx *ctx, int *threads_per_site, int *block);
 
 /* --------------------------------------------------- learned warm start */

@@ -58,6 +58,7 @@ struct gf_ctx {
     int block = 0;
     int fp64_arith = 0;  // FP64 phase: 0 native FP64, 1 double-float on the FP32 pipe (DF64_18)
     int variant = 0;  // 0 auto, 1 per-subgroup rotations of the held links, 2 accumulate form
+    int acc_regs = 0;  // accumulate form, FP64 storage: register budget 255, 168 or 128 (0 = autotuned)
     int use_graphs = 1;
     int kernel_timing = 0;     // events around the sweep kernels of every check chunk
     cudaEvent_t kev[2] = { nullptr, nullptr };
@@ -253,8 +254,13 @@ static std::pair<int, int> launch_config(const gf_ctx *c, int fmt)
         if (it != g_tune_cache.end()) cfg = it->second;
     }
     if (c->tps) cfg.first = c->tps;
-    if (c->variant == 2) cfg.first = 0;  // accumulate form: one thread per site
-    if (c->variant == 1 && cfg.first == 0) cfg.first = c->tps ? c->tps : 2;
+    if (c->variant == 2 && cfg.first > 0) cfg.first = GF_ACC;  // accumulate form: one thread per site
+    if (c->variant == 1 && cfg.first <= 0) cfg.first = c->tps ? c->tps : 2;
+    if (cfg.first <= 0 && c->acc_regs) {  // explicit register budget of the accumulate form
+        cfg.first = c->acc_regs == 168 ? GF_ACC_R168 : (c->acc_regs == 128 ? GF_ACC_R128 : GF_ACC);
+        if (fmt != F64_18 && fmt != F64_12) cfg.first = GF_ACC;
+    }
+    if (cfg.first == GF_ACC_R168 && cfg.second > 128) cfg.second = 128;
     if (c->block) cfg.second = c->block;
     return cfg;
 }
@@ -432,12 +438,15 @@ static int autotune_format(gf_ctx *ctx, int fmt, char *field, int *tps_out, int 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    const int tps_c[5] = { 0, 1, 2, 4, 8 };  // 0: accumulate form
+    // accumulate form (with the smaller register budgets for FP64 storage), then 1-8 threads per site
+    const int tps_c[7] = { GF_ACC, 1, 2, 4, 8, GF_ACC_R168, GF_ACC_R128 };
+    const int ntps = (fmt == F64_18 || fmt == F64_12) ? 7 : 5;
     const int blk_c[3] = { 64, 128, 256 };
     float best = 1e30f;
     std::pair<int, int> pick = default_config(fmt);
-    for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+    for (int i = 0; i < ntps && e == cudaSuccess; ++i)
         for (int b = 0; b < 3 && e == cudaSuccess; ++b) {
+            if (tps_c[i] == GF_ACC_R168 && blk_c[b] > 128) continue;
             std::pair<int, int> cfg{ tps_c[i], blk_c[b] };
             e = issue_sweeps(ctx, fmt, scratch, 1.7, 1, false, cfg, ctx->stream);  // warm up
             if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
@@ -614,6 +623,9 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
     } else if (k == "variant") {
         if (!integral || iv < 0 || iv > 2) return fail(ctx, GF_EINVAL, "variant: 0, 1 or 2");
         ctx->variant = iv;
+    } else if (k == "acc_registers") {
+        if (iv != 0 && iv != 255 && iv != 168 && iv != 128) return fail(ctx, GF_EINVAL, "acc_registers: 0, 255, 168 or 128");
+        ctx->acc_regs = iv;
     } else if (k == "use_graphs") {
         ctx->use_graphs = v != 0.0;
     } else if (k == "kernel_timing") {
@@ -661,6 +673,7 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *v)
     else if (k == "variant") *v = ctx->variant;
     else if (k == "fp64_arith") *v = ctx->fp64_arith;
     else if (k == "use_graphs") *v = ctx->use_graphs;
+    else if (k == "acc_registers") *v = ctx->acc_regs;
     else if (k == "kernel_timing") *v = ctx->kernel_timing;
     else if (k == "autotune") *v = ctx->autotune;
     else if (k == "sa_cap") *v = ctx->sa_cap;
@@ -895,7 +908,9 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
         ctx->stats["sweep_launches_fp64"] = (double)ctx->kn[1];
     }
     ctx->stats["ms_total"] = now_ms() - t0;
-    ctx->stats["threads_per_site"] = cfg.first;
+    ctx->stats["threads_per_site"] = cfg.first > 0 ? cfg.first : 1;
+    ctx->stats["accumulate_form"] = cfg.first <= 0;
+    ctx->stats["acc_registers"] = cfg.first == GF_ACC_R168 ? 168 : (cfg.first == GF_ACC_R128 ? 128 : 255);
     ctx->stats["block"] = cfg.second;
     if (iters_out) *iters_out = used32 + used64;
     if (F_out) *F_out = F;
@@ -1032,7 +1047,9 @@ int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t 
     ctx->stats["sweeps"] = steps;
     ctx->stats["sa_rejects"] = rejects;
     ctx->stats["ms_total"] = now_ms() - t0;
-    ctx->stats["threads_per_site"] = cfg.first;
+    ctx->stats["threads_per_site"] = cfg.first > 0 ? cfg.first : 1;
+    ctx->stats["accumulate_form"] = cfg.first <= 0;
+    ctx->stats["acc_registers"] = cfg.first == GF_ACC_R168 ? 168 : (cfg.first == GF_ACC_R128 ? 128 : 255);
     ctx->stats["block"] = cfg.second;
     if (rejects) return fail(ctx, GF_EREJECT, "heatbath rejection cap reached in some draws");
     return GF_OK;

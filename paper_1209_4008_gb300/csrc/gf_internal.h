@@ -10,6 +10,12 @@
 
 namespace gf {
 
+// launch-configuration codes of the site update ("threads per site"):
+// 1, 2, 4, 8 = per-subgroup form with that many threads per site; <= 0 =
+// accumulate form, one thread per site, with a register budget of 255, 168 or
+// 128 per thread (the last two for FP64 storage only)
+constexpr int GF_ACC = 0, GF_ACC_R168 = -1, GF_ACC_R128 = -2;
+
 // arguments of one half-sweep launch
 struct SweepArgs {
     FieldRef f;       // resident field

@@ -477,6 +477,17 @@ __global__ void __launch_bounds__(256) k_sweep_acc(SweepArgs a)
     sweep_site_acc<FMT, COULOMB, MODE, TRACKG>(a, h);
 }
 
+// the same with a register budget (the autotuner tries both for FP64
+// storage): RC = 1: 168 per thread (3 blocks of 128 threads per SM), RC = 2:
+// 128 (2 blocks of 256)
+template <int FMT, bool COULOMB, int MODE, bool TRACKG, int RC>
+__global__ void __launch_bounds__(RC == 1 ? 128 : 256, RC == 1 ? 3 : 2) k_sweep_acc_rc(SweepArgs a)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= a.g.Vh) return;
+    sweep_site_acc<FMT, COULOMB, MODE, TRACKG>(a, h);
+}
+
 template <int FMT, int TPS, bool COULOMB, int MODE, bool TRACKG>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
 {
@@ -487,14 +498,17 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
     sweep_site<FMT, TPS, COULOMB, MODE, TRACKG>(a, h, j, site_group_mask<TPS>());
 }
 
-// TPS == 0 selects the accumulate form (one thread per site)
+// TPS <= 0 selects the accumulate form (one thread per site) with register
+// budget RC = -TPS (GF_ACC, GF_ACC_R168, GF_ACC_R128)
 template <int FMT, int TPS, bool COULOMB, int MODE, bool TRACKG>
 static cudaError_t launch_k_sweep(const SweepArgs &a, int block, cudaStream_t s)
 {
-    long threads = (long)a.g.Vh * (TPS == 0 ? 1 : TPS);
+    long threads = (long)a.g.Vh * (TPS <= 0 ? 1 : TPS);
     int grid = (int)((threads + block - 1) / block);
+    if (TPS == GF_ACC_R168 && block > 128) return cudaErrorInvalidValue;
     if (TPS == 0) k_sweep_acc<FMT, COULOMB, MODE, TRACKG><<<grid, block, 0, s>>>(a);
-    else k_sweep<FMT, (TPS == 0 ? 1 : TPS), COULOMB, MODE, TRACKG><<<grid, block, 0, s>>>(a);
+    else if (TPS < 0) k_sweep_acc_rc<FMT, COULOMB, MODE, TRACKG, (TPS < 0 ? -TPS : 1)><<<grid, block, 0, s>>>(a);
+    else k_sweep<FMT, (TPS <= 0 ? 1 : TPS), COULOMB, MODE, TRACKG><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -517,6 +531,14 @@ template <int FMT, bool TRACKG>
 static cudaError_t dispatch_tps(const SweepArgs &a, int tps, int coulomb, int mode, int block, cudaStream_t s)
 {
     switch (tps) {
+    case GF_ACC_R168:
+        if constexpr (FMT == F64_18 || FMT == F64_12)
+            return dispatch_gauge_mode<FMT, GF_ACC_R168, TRACKG>(a, coulomb, mode, block, s);
+        return cudaErrorInvalidValue;
+    case GF_ACC_R128:
+        if constexpr (FMT == F64_18 || FMT == F64_12)
+            return dispatch_gauge_mode<FMT, GF_ACC_R128, TRACKG>(a, coulomb, mode, block, s);
+        return cudaErrorInvalidValue;
     case 0: return dispatch_gauge_mode<FMT, 0, TRACKG>(a, coulomb, mode, block, s);
     case 1: return dispatch_gauge_mode<FMT, 1, TRACKG>(a, coulomb, mode, block, s);
     case 2: return dispatch_gauge_mode<FMT, 2, TRACKG>(a, coulomb, mode, block, s);

@@ -447,3 +447,28 @@ def test_kernel_timing_counts_every_sweep_launch(graphs):
         assert n == 2 * gf.gf_get_stat(c, f"sweeps_{ph}")
         ms = gf.gf_get_stat(c, f"ms_sweep_kernels_{ph}")
         assert 0.0 < ms <= gf.gf_get_stat(c, f"ms_{ph}")
+
+
+# ---------------------------------------------------------------------------
+# accumulate form with a register budget (FP64 storage)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 4, 6, 10)])
+@pytest.mark.parametrize("gauge", [0, 1])
+@pytest.mark.parametrize("storage", [18, 12])
+@pytest.mark.parametrize("regs", [168, 128])
+def test_acc_register_budget_parity(dims, gauge, storage, regs):
+    U = cpu_field(dims, seed=3, gseed=4)
+    c = ctx_for(dims, gauge, variant=2, acc_registers=regs, storage64=storage, block=128)
+    gf.gf_upload(c, dev(U), gf.GF_FP64)
+    W = U.copy()
+    for p in (0, 1):
+        gf.gf_or_half_sweep(c, p, 1.7)
+        oracle.or_half_sweep(W, p, 1.7, gauge)
+    d = torch.empty_like(dev(U))
+    gf.gf_download(c, d)
+    assert max_rel(host(d), W) < 1e-12
+    # heatbath through the same kernels
+    gf.gf_sa_half_sweep(c, 0, 0.7, 5, 3)
+    oracle.sa_half_sweep(W, 0, 0.7, gauge, 5, 3)
+    gf.gf_download(c, d)
+    assert max_rel(host(d), W) < 1e-11
