@@ -237,11 +237,11 @@ static char *resident_base(gf_ctx *ctx) { return ctx->resident == GF_FP64 ? ctx-
 static std::pair<int, int> default_config(int fmt)
 {
     switch (fmt) {
-    case F32_12: return { 1, 128 };
+    case F32_12: return { GF_ACC, 64 };
     case F32_18: return { 2, 128 };
-    case F64_12: return { 2, 128 };
-    case DF64_18: return { 0, 128 };
-    default: return { 2, 128 };
+    case F64_12: return { GF_ACC, 64 };
+    case DF64_18: return { GF_ACC, 128 };
+    default: return { GF_ACC, 64 };  // F64_18
     }
 }
 
@@ -1027,6 +1027,8 @@ int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t 
     RET(device_view(ctx, U, &view, &host));
     int prec = ctx->precision == GF_FP32 ? GF_FP32 : GF_FP64;
     RET(upload(ctx, view, prec));
+    if (ctx->autotune && !tuned(ctx, ctx->resident_fmt))
+        RET(autotune_format(ctx, ctx->resident_fmt, resident_base(ctx), nullptr, nullptr));
     CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int) * 4, ctx->stream));
     std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt);
     for (int k = 0; k < steps; ++k) {
