@@ -644,6 +644,51 @@ def coulomb(args):
         "total_s": time.perf_counter() - t_start}), flush=True)
 
 
+def net_kernels(args):
+    """The warm-start network's convolutions on one lattice (default 32^4):
+    forward and one training step (forward, loss, backward data and weights,
+    Adam) on random BF16 inputs, CUDA events on the launch stream; the
+    tensor-core rate counts 2 x 81 x C_in x C_out flop per site and layer.
+    Prints one JSON object."""
+    from paper_1209_4008_gb300 import gf, learned as L
+    dims = tuple(args.dims) if args.dims else DIMS
+    V = int(np.prod(dims))
+    ch = gf.NET_CHANNELS
+    layer_flop = [2 * 81 * ch[l] * ch[l + 1] for l in range(4)]
+    fwd_flop = V * sum(layer_flop)
+    # training: forward, data gradients of layers 2-4, weight gradients of all layers
+    train_flop = V * (2 * sum(layer_flop) + sum(layer_flop[1:]))
+    net = gf.gf_net_create(dims)
+    gf.gf_net_set_stream(net, torch.cuda.current_stream())
+    gf.gf_net_set_params(net, L.init_params(0))
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    feats = torch.randn(V, ch[0], device="cuda", generator=gen).to(torch.bfloat16)
+    target = 0.1 * torch.randn(V, ch[4], device="cuda", generator=gen)
+    out = torch.empty(V, ch[4], device="cuda", dtype=torch.float32)
+    s = torch.cuda.current_stream()
+    res = {}
+    for name, fn, flop in (("forward", lambda: gf.gf_net_forward(net, feats, out), fwd_flop),
+                           ("train_step", lambda: gf.gf_net_train_step(net, feats, target, 1e-4), train_flop)):
+        for _ in range(args.warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(args.steps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = {"ms": ms, "tflops": flop / (ms * 1e-3) / 1e12}
+    pk = peaks()
+    bf16 = pk.get("bf16_tflops")
+    for r in res.values():
+        r["frac_of_bf16_peak"] = r["tflops"] / bf16 if bf16 else None
+    print(json.dumps({"workload": f"warm-start network {'x'.join(map(str, dims))}, channels {list(ch)}",
+                      "sites": V, "flop_forward": fwd_flop, "flop_train_step": train_flop,
+                      "bf16_peak_tflops": bf16, **res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -672,6 +717,7 @@ def main():
     ap.add_argument("--weights", metavar="PATH",
                     help="--learned: skip the pairs and training, evaluate these stored parameters")
     ap.add_argument("--coulomb", action="store_true", help="the 48^3x96 Coulomb workload with annealing")
+    ap.add_argument("--net", action="store_true", help="time the warm-start network's kernels")
     ap.add_argument("--seeds", type=int, default=8)
     ap.add_argument("--sa-sweeps", type=int, default=3000)
     args = ap.parse_args()
@@ -686,6 +732,10 @@ def main():
     if args.coulomb:
         torch.cuda.set_device(0)
         coulomb(args)
+        return
+    if args.net:
+        torch.cuda.set_device(0)
+        net_kernels(args)
         return
     if args.kernel:
         torch.cuda.set_device(0)

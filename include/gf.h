@@ -253,9 +253,9 @@ int gf_net_get_params(gf_net *n, float *params);
 int gf_net_forward(gf_net *n, const void *features, float *out);
 /* Loss and gradient w.r.t. the parameters (grad host or device, may be NULL). */
 int gf_net_gradient(gf_net *n, const void *features, const float *target, float *grad, double *loss);
-/* Options: "tensor_cores" (default 1): forward and backward-data convolutions
- * as implicit GEMMs on the tcgen05 tensor cores (BF16 in, FP32 accumulators
- * in tensor memory); 0 = the CUDA-core kernels.  Forward, gradient and train
+/* Options: "tensor_cores" (default 1): forward, backward-data and
+ * weight-gradient convolutions as implicit GEMMs on the tcgen05 tensor cores
+ * (BF16 in, FP32 accumulators in tensor memory); 0 = the CUDA-core kernels.  Forward, gradient and train
  * calls synchronise the stream and return GF_ETIMEOUT if a bounded wait in a
  * tensor-core kernel expired. */
 int gf_net_set_option(gf_net *n, const char *key, double value);
