@@ -63,6 +63,7 @@ def _declare(lib: C.CDLL) -> C.CDLL:
     d.oracle_block_quaternion.argtypes = [_dp, _dp]
     d.oracle_block_quaternion.restype = None
     d.oracle_overrelax_quaternion.argtypes = [_dp, C.c_double, _dp]
+    d.oracle_set_or_variant.argtypes = [C.c_int]
     d.oracle_site_quaternion.argtypes = [_dp, _ip, C.c_long, C.c_int, C.c_int, _dp]
     d.oracle_site_rotate.argtypes = [_dp, _ip, C.c_long, C.c_int, _dp]
     for f in ("oracle_functional", "oracle_theta", "oracle_theta_from_M"):
@@ -148,6 +149,17 @@ def _check(rc: int, what: str) -> None:
 # ---------------------------------------------------------------------------
 # overrelaxation (Alg. 1)
 # ---------------------------------------------------------------------------
+def set_or_variant(v: int) -> None:
+    """Reading of g -> g^omega for every later overrelaxation call of this
+    process: 0 = the 19-flop rational form (default), 1 = first order,
+    2 = the exact power (Sec. 2, "to first or second order")."""
+    _check(lib().oracle_set_or_variant(int(v)), "or variant")
+    with _lock:
+        counting = _libs.get("liboracle_count.so")
+    if counting is not None:
+        _check(counting.oracle_set_or_variant(int(v)), "or variant")
+
+
 def or_half_sweep(U, parity: int, omega: float, gauge: int = 0, counting: bool = False) -> None:
     U = _field(U)
     _check(lib(counting).oracle_or_half_sweep(_d(U), _i(dims_of(U)), parity, omega, gauge),

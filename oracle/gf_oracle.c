@@ -228,8 +228,61 @@ static void su2_matrix(const double r[4], cplx R[2][2])
  * Ogilvie).  Input: the unnormalised quaternion k.  Output: r in SU(2).
  * Returns 0 (and leaves r untouched) when k = 0.
  */
+/*
+ * The paper leaves open how g^omega is formed ("to first or second order",
+ * Sec. 2); three readings are selectable (one process-wide setting):
+ *   0: the 19-flop rational form above (default; matches Alg. 1's count);
+ *   1: first order, r = normalise((1 - omega) 1 + omega k/|k|);
+ *   2: the exact power: with k/|k| = (cos phi, sin phi n), r = (cos(omega phi),
+ *      sin(omega phi) n), phi in [0, pi]; the subgroup is left unchanged when
+ *      the direction n is undefined (k parallel to -1: phi = pi).
+ * All three give the relaxation step r = k/|k| at omega = 1.
+ */
+static int g_or_variant = 0;
+
+int oracle_set_or_variant(int v)
+{
+    if (v < 0 || v > 2) return -1;
+    g_or_variant = v;
+    return 0;
+}
+
+static int overrelax_first_order(const double k[4], double omega, double r[4])
+{
+    double n = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
+    if (n == 0.0) return 0;
+    double v[4] = { (1.0 - omega) + omega * (k[0] / n), omega * (k[1] / n), omega * (k[2] / n),
+                    omega * (k[3] / n) };
+    double m = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+    if (m == 0.0) return 0;
+    for (int c = 0; c < 4; ++c) r[c] = v[c] / m;
+    return 1;
+}
+
+static int overrelax_exact_power(const double k[4], double omega, double r[4])
+{
+    double a = sqrt(k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
+    if (a == 0.0) {
+        if (k[0] > 0.0) {  /* phi = 0: the relaxation step is the identity */
+            r[0] = 1.0;
+            r[1] = r[2] = r[3] = 0.0;
+            return 1;
+        }
+        return 0;  /* k = 0, or phi = pi with no direction */
+    }
+    double phi = atan2(a, k[0]);
+    double c = cos(omega * phi), sn = sin(omega * phi);
+    r[0] = c;
+    r[1] = sn * (k[1] / a);
+    r[2] = sn * (k[2] / a);
+    r[3] = sn * (k[3] / a);
+    return 1;
+}
+
 static int overrelax_quaternion(const double k[4], double omega, double r[4])
 {
+    if (g_or_variant == 1) return overrelax_first_order(k, omega, r);
+    if (g_or_variant == 2) return overrelax_exact_power(k, omega, r);
     double a0sq = k[0] * k[0];
     double aisq = k[1] * k[1] + k[2] * k[2] + k[3] * k[3];
     FLOPS(6);

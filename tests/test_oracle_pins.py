@@ -55,7 +55,7 @@ def local_objective(G, fwd, bwd, nk=4):
     return sum(np.trace(G @ fwd[m]).real + np.trace(bwd[m] @ G.conj().T).real for m in range(nk))
 
 
-def haar_su2(n, rng):
+def haarsu2_from_quaternion(n, rng):
     q = rng.standard_normal((n, 4))
     return q / np.linalg.norm(q, axis=1, keepdims=True)
 
@@ -97,7 +97,7 @@ def test_quaternion_projection_is_re_trace():
     rng = np.random.default_rng(5)
     for _ in range(200):
         w = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
-        r = haar_su2(1, rng)[0]
+        r = haarsu2_from_quaternion(1, rng)[0]
         k = oracle.block_quaternion(w)
         assert np.trace(su2_from_quaternion(r) @ w).real == pytest.approx(r @ k, abs=1e-13)
 
@@ -140,7 +140,7 @@ def test_brute_force_no_su2_beats_subgroup_maximum():
             best = local_objective(embed(su2_from_quaternion(rbest), a, b), fwd, bwd)
             # the identity's block contributes k0, the maximum |k|
             assert best - base == pytest.approx(np.linalg.norm(k) - k[0], abs=1e-12)
-            qs = haar_su2(100_000, rng)
+            qs = haarsu2_from_quaternion(100_000, rng)
             # objective is affine in r: base + (r - 1).k ; evaluate a sample exactly too
             vals = base + qs @ k - k[0]
             assert vals.max() <= best + 1e-12
@@ -170,7 +170,7 @@ def test_su2_reduction_matches_textbook_local_solution():
     dims = (4, 4, 4, 4)
     rng = np.random.default_rng(8)
     V = 4 ** 4
-    q = haar_su2(V * 4, rng)
+    q = haarsu2_from_quaternion(V * 4, rng)
     U = np.zeros((4, 4, 4, 4, 4, 3, 3), complex)
     flat = U.reshape(-1, 3, 3)
     for n in range(V * 4):
@@ -477,3 +477,85 @@ def test_stochastic_relaxation_fixes_the_gauge():
     for n in range(400):
         oracle.sr_half_sweep(U, n % 2, 0.8, 0, 3, n // 2)
     assert oracle.theta(U, 0) < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# readings of g -> g^omega (Sec. 2, "to first or second order")
+# ---------------------------------------------------------------------------
+@pytest.fixture
+def or_variant():
+    yield oracle.set_or_variant
+    oracle.set_or_variant(0)
+
+
+def test_or_variants_reduce_to_relaxation_at_omega_one(or_variant):
+    rng = np.random.default_rng(31)
+    for v in (0, 1, 2):
+        or_variant(v)
+        for _ in range(50):
+            k = rng.standard_normal(4) * rng.uniform(0.1, 5)
+            r = oracle.overrelax_quaternion(k, 1.0)
+            np.testing.assert_allclose(r, k / np.linalg.norm(k), atol=1e-15)
+
+
+def test_or_exact_power_is_the_matrix_power(or_variant):
+    """Reading 2 equals G^omega of the relaxation element G (principal
+    branch), computed by scipy's fractional matrix power."""
+    from scipy.linalg import fractional_matrix_power
+    or_variant(2)
+    rng = np.random.default_rng(32)
+    for _ in range(40):
+        k = rng.standard_normal(4)
+        k[0] = abs(k[0]) + 0.05  # rotation angle below pi/2 .. pi: principal branch well defined
+        omega = rng.uniform(0.2, 1.95)
+        G = su2_from_quaternion(k / np.linalg.norm(k))
+        want = fractional_matrix_power(G, omega)
+        got = su2_from_quaternion(oracle.overrelax_quaternion(k, omega))
+        np.testing.assert_allclose(got, want, atol=1e-12)
+
+
+def test_or_first_order_is_projected_linear_combination(or_variant):
+    """Reading 1 is (1 - omega) 1 + omega G projected back onto SU(2):
+    proportional to that matrix with a positive factor, and unitary."""
+    or_variant(1)
+    rng = np.random.default_rng(33)
+    for _ in range(40):
+        k = rng.standard_normal(4)
+        omega = rng.uniform(0.2, 1.95)
+        G = su2_from_quaternion(k / np.linalg.norm(k))
+        Mlin = (1 - omega) * np.eye(2) + omega * G
+        R = su2_from_quaternion(oracle.overrelax_quaternion(k, omega))
+        np.testing.assert_allclose(R @ R.conj().T, np.eye(2), atol=1e-14)
+        ratio = Mlin / R
+        np.testing.assert_allclose(ratio, ratio[0, 0] * np.ones((2, 2)), atol=1e-12)
+        assert ratio[0, 0].real > 0 and abs(ratio[0, 0].imag) < 1e-12
+
+
+def test_or_readings_agree_at_small_angles(or_variant):
+    """All readings rotate by omega * phi + O(phi^3) (first order in the
+    exponent's angle): the three agree to O(phi^3)."""
+    omega = 1.7
+    n = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+    for phi in (1e-2, 1e-3):
+        k = np.concatenate([[np.cos(phi)], np.sin(phi) * n])
+        rs = []
+        for v in (0, 1, 2):
+            or_variant(v)
+            rs.append(oracle.overrelax_quaternion(k, omega))
+        for r in rs:
+            ang = np.arctan2(np.linalg.norm(r[1:]), r[0])
+            assert abs(ang - omega * phi) < 2 * phi ** 3
+
+
+@pytest.mark.parametrize("v", [1, 2])
+def test_or_variants_fix_the_gauge_and_keep_the_plaquette(or_variant, v):
+    dims = (4, 4, 4, 4)
+    or_variant(v)
+    U = field(dims, seed=1, gseed=2, pure=True)
+    oracle.or_sweeps(U, 1.5, 0, 300)
+    assert oracle.theta(U, 0) < 1e-24
+    assert oracle.functional(U, 0) == pytest.approx(1.0, abs=1e-12)
+    W = field(dims, seed=5, gseed=6)
+    P = oracle.plaquette(W)
+    oracle.or_sweeps(W, 1.7, 0, 20)
+    assert oracle.plaquette(W) == pytest.approx(P, abs=1e-13)
