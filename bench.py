@@ -370,6 +370,9 @@ def gpu_arm(args, rank, world, local):
         "config": {"workload": "landau-or-32^4 mixed: fp32-12 sweeps to theta<1e-6, fp64-18 to theta<1e-14",
                    "lattice": list(DIMS), "omega": OMEGA, "plaquette": PLAQ, "seeds": list(SEEDS),
                    "check_every": CHECK_EVERY, "theta_switch": THETA_SWITCH,
+                   "or_variant": "rational 19-flop form of g^omega (Alg. 1)",
+                   "theta": "(1/3V) sum tr Delta Delta^dagger, Delta = traceless sum_mu [A_mu(x) - A_mu(x-mu)], "
+                            "A = (U - U^dagger)/2i",
                    "theta_target": THETA_TARGET, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (fp64 field 604 MB, fp32 field 201 MB)"},
         "time_to_theta": {"mixed_s": ms / args.steps / 1e3, "fp64_s": t_fp64,

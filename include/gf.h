@@ -107,6 +107,13 @@ int gf_set_stream(gf_ctx *ctx, void *stream);
  *                    once per link (one thread per site; equal in exact
  *                    arithmetic), 0 = autotuned or default (default 0)
  *   "block"          threads per block (multiple of 32, <= 256; 0 = autotune)
+ *   "or_variant"     reading of the exponent g -> g^omega (Sec. 2, "to first
+ *                    or second order"): 0 = the 19-flop rational form b =
+ *                    (omega a0^2 + |a|^2)/(a0^2 + |a|^2), r = (a0, b a)/norm
+ *                    (default; the count of Alg. 1), 1 = first order,
+ *                    normalise((1 - omega) 1 + omega k/|k|), 2 = the exact
+ *                    power (cos(omega phi), sin(omega phi) n); all equal
+ *                    relaxation at omega = 1.  Batches use 0.
  *   "acc_registers"  accumulate form on FP64 storage: register budget per
  *                    thread, 255, 168 or 128 (0 = autotuned or 255; default 0)
  *   "use_graphs"     1 = replay sweep loops as CUDA graphs (default 1)

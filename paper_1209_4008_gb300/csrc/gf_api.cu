@@ -19,14 +19,14 @@ using namespace gf;
 namespace {
 
 struct GraphKey {
-    int fmt, tps, block, n, trackg, measure, reunit, ktime;
+    int fmt, tps, block, n, trackg, measure, reunit, ktime, orv;
     double omega;
     const void *field, *gt;
     bool operator<(const GraphKey &o) const
     {
-        return std::tie(fmt, tps, block, n, trackg, measure, reunit, ktime, omega, field, gt) <
-               std::tie(o.fmt, o.tps, o.block, o.n, o.trackg, o.measure, o.reunit, o.ktime, o.omega, o.field,
-                        o.gt);
+        return std::tie(fmt, tps, block, n, trackg, measure, reunit, ktime, orv, omega, field, gt) <
+               std::tie(o.fmt, o.tps, o.block, o.n, o.trackg, o.measure, o.reunit, o.ktime, o.orv, o.omega,
+                        o.field, o.gt);
     }
 };
 
@@ -59,6 +59,7 @@ struct gf_ctx {
     int fp64_arith = 0;  // FP64 phase: 0 native FP64, 1 double-float on the FP32 pipe (DF64_18)
     int variant = 0;  // 0 auto, 1 per-subgroup rotations of the held links, 2 accumulate form
     int acc_regs = 0;  // accumulate form, FP64 storage: register budget 255, 168 or 128 (0 = autotuned)
+    int or_variant = 0;  // g -> g^omega: 0 rational 19-flop form, 1 first order, 2 exact power
     int use_graphs = 1;
     int kernel_timing = 0;     // events around the sweep kernels of every check chunk
     cudaEvent_t kev[2] = { nullptr, nullptr };
@@ -274,6 +275,7 @@ static SweepArgs sweep_args(gf_ctx *ctx, char *field, int parity, double omega)
     a.g = ctx->geom;
     a.parity = parity;
     a.omega = omega;
+    a.orv = ctx->or_variant;
     a.T = 1.0;
     a.cap = ctx->sa_cap;
     a.status = ctx->dstatus;
@@ -318,7 +320,8 @@ static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, boo
         return GF_OK;
     }
     if (ctx->use_graphs && n > 0) {
-        GraphKey key{ fmt, cfg.first, cfg.second, n, trackg, measure, reunit, kt ? 1 : 0, omega, field, ctx->gt };
+        GraphKey key{ fmt,        cfg.first,          cfg.second, n, trackg, measure, reunit, kt ? 1 : 0,
+                      ctx->or_variant, omega, field, ctx->gt };
         auto it = ctx->graphs.find(key);
         if (it == ctx->graphs.end()) {
             cudaGraph_t graph;
@@ -623,6 +626,9 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
     } else if (k == "variant") {
         if (!integral || iv < 0 || iv > 2) return fail(ctx, GF_EINVAL, "variant: 0, 1 or 2");
         ctx->variant = iv;
+    } else if (k == "or_variant") {
+        if (!integral || iv < 0 || iv > 2) return fail(ctx, GF_EINVAL, "or_variant: 0, 1 or 2");
+        ctx->or_variant = iv;
     } else if (k == "acc_registers") {
         if (iv != 0 && iv != 255 && iv != 168 && iv != 128) return fail(ctx, GF_EINVAL, "acc_registers: 0, 255, 168 or 128");
         ctx->acc_regs = iv;
@@ -674,6 +680,7 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *v)
     else if (k == "fp64_arith") *v = ctx->fp64_arith;
     else if (k == "use_graphs") *v = ctx->use_graphs;
     else if (k == "acc_registers") *v = ctx->acc_regs;
+    else if (k == "or_variant") *v = ctx->or_variant;
     else if (k == "kernel_timing") *v = ctx->kernel_timing;
     else if (k == "autotune") *v = ctx->autotune;
     else if (k == "sa_cap") *v = ctx->sa_cap;

@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(256) k_batch_persistent(BatchArgs b)
                     a.g = c.g;
                     a.parity = p;
                     a.omega = b.omega;
+                    a.orv = 0;  // the rational 19-flop form
                     a.T = 1.0;
                     a.key = make_uint2(0u, 0u);
                     a.sweep = 0;

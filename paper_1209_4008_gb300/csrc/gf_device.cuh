@@ -372,6 +372,50 @@ __device__ __forceinline__ bool overrelax_quat(const double k[4], double omega, 
     return true;
 }
 
+// Other readings of g -> g^omega (Sec. 2 leaves the form open), selected by
+// the context option "or_variant": 1 = first order, r = normalise((1 - omega)
+// 1 + omega k/|k|); 2 = the exact power, r = (cos(omega phi), sin(omega phi) n)
+// for k/|k| = (cos phi, sin phi n), left unchanged when n is undefined.
+template <class T>
+__device__ __forceinline__ bool overrelax_first_order(const T k[4], T omega, T r[4])
+{
+    T n = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
+    if (n == T(0)) return false;
+    T v[4] = { (T(1) - omega) + omega * (k[0] / n), omega * (k[1] / n), omega * (k[2] / n), omega * (k[3] / n) };
+    T m = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+    if (m == T(0)) return false;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) r[c] = v[c] / m;
+    return true;
+}
+
+template <class T>
+__device__ __forceinline__ bool overrelax_exact_power(const T k[4], T omega, T r[4])
+{
+    T a = sqrt(k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
+    if (a == T(0)) {
+        if (!(k[0] > T(0))) return false;
+        r[0] = T(1);
+        r[1] = r[2] = r[3] = T(0);
+        return true;
+    }
+    T phi = atan2(a, k[0]);
+    T c = cos(omega * phi), sn = sin(omega * phi);
+    r[0] = c;
+    r[1] = sn * (k[1] / a);
+    r[2] = sn * (k[2] / a);
+    r[3] = sn * (k[3] / a);
+    return true;
+}
+
+template <class T>
+__device__ __forceinline__ bool overrelax_step(const T k[4], T omega, int variant, T r[4])
+{
+    if (variant == 1) return overrelax_first_order(k, omega, r);
+    if (variant == 2) return overrelax_exact_power(k, omega, r);
+    return overrelax_quat(k, omega, r);
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
 // ---------------------------------------------------------------------------

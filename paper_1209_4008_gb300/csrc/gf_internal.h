@@ -23,6 +23,7 @@ struct SweepArgs {
     Geom g;
     int parity;
     double omega;     // overrelaxation exponent
+    int orv;          // reading of g -> g^omega: 0 rational 19-flop form, 1 first order, 2 exact power
     double T;         // heatbath temperature
     uint2 key;        // Philox key (seed)
     uint32_t sweep;   // Philox sweep counter

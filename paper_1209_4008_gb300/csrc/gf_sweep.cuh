@@ -160,7 +160,7 @@ __device__ __forceinline__ void subgroup_element(const SweepArgs &a, quat<T> q, 
     T r[4];
     bool ok;
     if (MODE == MODE_OR) {
-        ok = overrelax_quat(q.k, (T)a.omega, r);
+        ok = overrelax_step(q.k, (T)a.omega, a.orv, r);
     } else if (MODE == MODE_SR) {
         ok = sr_quat(q.k, a.prob, site, a.sweep, sg, a.key, r);
     } else {
@@ -435,7 +435,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs &a, int h, int j, uns
         T r[4];
         bool ok;
         if (MODE == MODE_OR) {
-            ok = overrelax_quat(k, (T)a.omega, r);
+            ok = overrelax_step(k, (T)a.omega, a.orv, r);
         } else if (MODE == MODE_SR) {
             ok = sr_quat(k, a.prob, site, a.sweep, sg, a.key, r);
         } else {

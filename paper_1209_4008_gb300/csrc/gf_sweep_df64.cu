@@ -84,7 +84,7 @@ __device__ __forceinline__ void subgroup_element_df(const SweepArgs &a, cdf xaa,
     double rd[4];
     bool ok;
     if (MODE == MODE_OR) {
-        ok = overrelax_quat(k, a.omega, rd);
+        ok = overrelax_step(k, a.omega, a.orv, rd);
     } else if (MODE == MODE_SR) {
         ok = sr_quat(k, a.prob, site, a.sweep, sg, a.key, rd);
     } else {

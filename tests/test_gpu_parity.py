@@ -472,3 +472,57 @@ def test_acc_register_budget_parity(dims, gauge, storage, regs):
     oracle.sa_half_sweep(W, 0, 0.7, gauge, 5, 3)
     gf.gf_download(c, d)
     assert max_rel(host(d), W) < 1e-11
+
+
+# ---------------------------------------------------------------------------
+# readings of g -> g^omega (option or_variant), same reading on both sides
+# ---------------------------------------------------------------------------
+@pytest.fixture
+def oracle_or_variant():
+    yield oracle.set_or_variant
+    oracle.set_or_variant(0)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("gauge", [0, 1])
+@pytest.mark.parametrize("form", ["acc", "tps2", "df64", "fp32"])
+def test_or_variant_parity(oracle_or_variant, variant, gauge, form):
+    dims = (6, 4, 6, 10)
+    U = cpu_field(dims, seed=3, gseed=4)
+    opts = {"or_variant": variant}
+    prec = gf.GF_FP64
+    if form == "acc":
+        opts["variant"] = 2
+    elif form == "tps2":
+        opts.update(variant=1, threads_per_site=2)
+    elif form == "df64":
+        opts["fp64_arith"] = 1
+    else:
+        prec = gf.GF_FP32
+    c = ctx_for(dims, gauge, **opts)
+    gf.gf_upload(c, dev(U), prec)
+    oracle_or_variant(variant)
+    W = U.copy()
+    for p in (0, 1):
+        gf.gf_or_half_sweep(c, p, 1.7)
+        oracle.or_half_sweep(W, p, 1.7, gauge)
+    d = torch.empty_like(dev(U))
+    gf.gf_download(c, d)
+    if prec == gf.GF_FP32:
+        assert np.abs(host(d) - W).max() < 5e-6 * 2
+    else:
+        assert max_rel(host(d), W) < 1e-12
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_or_variant_solver_converges_with_oracle_sweep_count(oracle_or_variant, variant):
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=3, gseed=4)
+    c = ctx_for(dims, 0, or_variant=variant, check_every=10)
+    d = dev(U)
+    conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-12, 20000)
+    oracle_or_variant(variant)
+    W = U.copy()
+    oconv, oit, oF, oth = oracle.overrelax(W, 0, 1.7, 1e-12, 20000, 10)
+    assert conv and oconv and it == oit
+    assert abs(F - oF) < 1e-12
