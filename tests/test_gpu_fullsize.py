@@ -6,7 +6,7 @@ the oracle instead recomputes the update of randomly sampled sites one by one
 from the same input field (sites of one parity are independent, Sec. 2), and
 the 8 links of each sampled site after the GPU half-sweep must match.  The GPU
 runs in the launch configuration the benchmark uses (autotuned).
-Tolerances as in test_gpu_parity.py: 1e-12 relative for FP64, 5e-6 absolute
+Tolerances as in test_gpu_parity.py: 1e-12 relative for FP64 and double-float, 5e-6 absolute
 per element for FP32-12 storage; SA 1e-11.
 """
 import numpy as np
@@ -41,13 +41,17 @@ def sites_of_parity(dims, parity, n, seed):
     return out
 
 
-@pytest.mark.parametrize("prec,storage,tol", [(gf.GF_FP64, 18, 1e-12), (gf.GF_FP32, 12, 5e-6)])
+@pytest.mark.parametrize("prec,storage,tol", [(gf.GF_FP64, 18, 1e-12), (gf.GF_FP32, 12, 5e-6),
+                                              (gf.GF_FP64, "df64", 1e-12)])
 def test_landau_32x32x32x32_half_sweep_sampled(prec, storage, tol):
     dims = (32, 32, 32, 32)
     U = synth.make_field(dims, 0.60, 3, 4, device="cuda")
     host = synth.as_numpy(U)
     c = gf.gf_create(dims, gf.GF_LANDAU)
-    gf.gf_set_option(c, "storage64" if prec == gf.GF_FP64 else "storage32", storage)
+    if storage == "df64":  # double-float storage, the mixed policy's alternative finish
+        gf.gf_set_option(c, "fp64_arith", 1)
+    else:
+        gf.gf_set_option(c, "storage64" if prec == gf.GF_FP64 else "storage32", storage)
     gf.gf_upload(c, U, prec)
     gf.gf_autotune(c)
     gf.gf_upload(c, U, prec)
