@@ -69,6 +69,7 @@ def _declare(lib: C.CDLL) -> C.CDLL:
     for f in ("oracle_functional", "oracle_theta", "oracle_theta_from_M"):
         getattr(d, f).argtypes = [_dp, _ip, C.c_int]
         getattr(d, f).restype = C.c_double
+    d.oracle_timeslices.argtypes = [_dp, _ip, C.c_int, _dp, _dp]
     d.oracle_plaquette.argtypes = [_dp, _ip]
     d.oracle_plaquette.restype = C.c_double
     d.oracle_gauge_transform.argtypes = [_dp, _dp, _ip]
@@ -222,6 +223,16 @@ def functional(U, gauge: int = 0) -> float:
 def theta(U, gauge: int = 0) -> float:
     U = _field(U)
     return lib().oracle_theta(_d(U), _i(dims_of(U)), gauge)
+
+
+def timeslices(U, gauge: int = 1):
+    """(F_t, theta_t) of every timeslice t (arrays of length Lt)."""
+    U = _field(U)
+    Lt = U.shape[0]
+    F = np.zeros(Lt)
+    th = np.zeros(Lt)
+    _check(lib().oracle_timeslices(_d(U), _i(dims_of(U)), gauge, _d(F), _d(th)), "timeslices")
+    return F, th
 
 
 def theta_from_M(U, gauge: int = 0) -> float:

@@ -579,6 +579,42 @@ double oracle_theta(const double *U, const int dims[4], int gauge)
 }
 
 /*
+ * F and theta of every timeslice t (the sites with time coordinate t; for
+ * Coulomb gauge each timeslice is gauge fixed on its own, Sec. 2):
+ * F_t = 1/(3 nk Ls) sum_{x in t, mu < nk} Re tr U_mu(x),
+ * theta_t = 1/(3 Ls) sum_{x in t} tr Delta(x) Delta(x)^dagger, Ls = Lx Ly Lz.
+ * The means over t are F and theta.
+ */
+int oracle_timeslices(const double *U, const int dims[4], int gauge, double *F_t, double *theta_t)
+{
+    lattice g;
+    if (lattice_init(&g, dims)) return -1;
+    int nk = gauge_nk(gauge);
+    long Ls = (long)g.L[0] * g.L[1] * g.L[2];
+    for (int t = 0; t < g.L[3]; ++t) {
+        double fs = 0.0, ts = 0.0;
+        for (long i = t * Ls; i < (t + 1) * Ls; ++i) {
+            mat3 D;
+            memset(&D, 0, sizeof D);
+            for (int mu = 0; mu < nk; ++mu) {
+                mat3 uf = mat_load(link_cptr(U, i, mu));
+                mat3 ub = mat_load(link_cptr(U, site_shift(&g, i, mu, -1), mu));
+                fs += mat_retrace(&uf);
+                mat3 Af = antiherm_part(&uf), Ab = antiherm_part(&ub);
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        D.m[a][b] = c_add(D.m[a][b], c_sub(Af.m[a][b], Ab.m[a][b]));
+            }
+            make_traceless(&D);
+            ts += frob2(&D);
+        }
+        F_t[t] = fs / (3.0 * nk * (double)Ls);
+        theta_t[t] = ts / (3.0 * (double)Ls);
+    }
+    return 0;
+}
+
+/*
  * The same theta through the local matrix of the update:
  * Delta(x) = traceless part of (M(x) - M(x)^dagger)/(2i),
  * M(x) = sum_mu [U_mu(x) + U_mu(x-mu)^dagger].  A second, independent route

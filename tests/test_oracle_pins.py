@@ -559,3 +559,35 @@ def test_or_variants_fix_the_gauge_and_keep_the_plaquette(or_variant, v):
     P = oracle.plaquette(W)
     oracle.or_sweeps(W, 1.7, 0, 20)
     assert oracle.plaquette(W) == pytest.approx(P, abs=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# per-timeslice F and theta (Coulomb gauge fixes each timeslice on its own)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("gauge", [0, 1])
+def test_timeslice_means_are_the_global_values(gauge):
+    U = field((4, 4, 6, 8), seed=41, gseed=42)
+    F_t, th_t = oracle.timeslices(U, gauge)
+    assert len(F_t) == 8
+    assert F_t.mean() == pytest.approx(oracle.functional(U, gauge), rel=1e-14)
+    assert th_t.mean() == pytest.approx(oracle.theta(U, gauge), rel=1e-13)
+
+
+def test_timeslice_values_are_local_in_time():
+    """A gauge rotation confined to timeslice t0 of the unit field leaves every
+    other timeslice at F_t = 1, theta_t = 0 in Coulomb gauge (spatial links of
+    t0 only are touched; temporal links do not enter F and theta)."""
+    import torch
+    dims = (4, 4, 4, 6)
+    Lx, Ly, Lz, Lt = dims
+    t0 = 2
+    one = torch.eye(3, dtype=torch.complex128).expand(Lt, Lz, Ly, Lx, 4, 3, 3).contiguous()
+    g = torch.eye(3, dtype=torch.complex128).expand(Lt, Lz, Ly, Lx, 3, 3).clone()
+    g[t0] = synth.haar_su3((Lz, Ly, Lx), 43)
+    U = synth.as_numpy(synth.rotate_field(one, g))
+    F_t, th_t = oracle.timeslices(U, 1)
+    for t in range(Lt):
+        if t == t0:
+            assert th_t[t] > 1e-3 and F_t[t] < 0.99
+        else:
+            assert th_t[t] < 1e-28 and F_t[t] == pytest.approx(1.0, abs=1e-14)
