@@ -629,7 +629,10 @@ def coulomb(args):
             conv, it, F, th = gf.gf_overrelax(ctx, U, OMEGA, target, MAX_ITER)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
+            F_t, th_t = gf.gf_measure_timeslices(ctx)
             row[leg] = {"or_s": dt, "sweeps": it, "F": F, "theta": th, "converged": conv,
+                        "theta_timeslice_max": float(th_t.max()), "F_timeslice_min_max": [float(F_t.min()),
+                                                                                          float(F_t.max())],
                         "su_per_s": V * it / dt, "dplaq": abs(gf.gf_plaquette(ctx, U) - row["plaquette"])}
             del U
         rows.append(row)

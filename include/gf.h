@@ -107,6 +107,10 @@ int gf_set_stream(gf_ctx *ctx, void *stream);
  *                    once per link (one thread per site; equal in exact
  *                    arithmetic), 0 = autotuned or default (default 0)
  *   "block"          threads per block (multiple of 32, <= 256; 0 = autotune)
+ *   "theta_per_timeslice"  1 = every theta the context reports or checks
+ *                    (stopping rule, gf_overrelax's output, gf_measure) is the
+ *                    largest timeslice value theta_t (gf_measure_timeslices),
+ *                    so that every timeslice reaches the target (default 0)
  *   "or_variant"     reading of the exponent g -> g^omega (Sec. 2, "to first
  *                    or second order"): 0 = the 19-flop rational form b =
  *                    (omega a0^2 + |a|^2)/(a0^2 + |a|^2), r = (a0, b a)/norm
@@ -207,8 +211,17 @@ int gf_sa_half_sweep(gf_ctx *ctx, int parity, double T, uint64_t seed, uint32_t 
  * (lexicographic site, sweep, 256 * subgroup, 2), compared with p in FP64. */
 int gf_sr_half_sweep(gf_ctx *ctx, int parity, double p, uint64_t seed, uint32_t sweep);
 
-/* F and theta of the resident field (accumulated in FP64). */
+/* F and theta of the resident field (accumulated in FP64).  With the option
+ * "theta_per_timeslice", theta_out is the largest theta_t (see below). */
 int gf_measure(gf_ctx *ctx, double *F_out, double *theta_out);
+
+/* F_t and theta_t of every timeslice t = 0..Lt-1 of the resident field
+ * (Coulomb gauge fixes each timeslice on its own, Sec. 2):
+ * F_t = 1/(3 nk Ls) sum_{x in t, mu < nk} Re tr U_mu(x), theta_t = 1/(3 Ls)
+ * sum_{x in t} tr Delta Delta^dagger, Ls = Lx Ly Lz, nk = 3 (Coulomb) or 4;
+ * their means over t are F and theta.  F_t, theta_t: Lt doubles each, host
+ * or device, either may be NULL.  Synchronises the context's stream. */
+int gf_measure_timeslices(gf_ctx *ctx, double *F_t, double *theta_t);
 
 /* Project every resident link back onto SU(3) (Gram-Schmidt in FP64). */
 int gf_reunitarize(gf_ctx *ctx);

@@ -6,10 +6,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "gf.h"
 #include "gf_internal.h"
@@ -19,14 +21,14 @@ using namespace gf;
 namespace {
 
 struct GraphKey {
-    int fmt, tps, block, n, trackg, measure, reunit, ktime, orv;
+    int fmt, tps, block, n, trackg, measure, reunit, ktime, orv, slices;
     double omega;
     const void *field, *gt;
     bool operator<(const GraphKey &o) const
     {
-        return std::tie(fmt, tps, block, n, trackg, measure, reunit, ktime, orv, omega, field, gt) <
-               std::tie(o.fmt, o.tps, o.block, o.n, o.trackg, o.measure, o.reunit, o.ktime, o.orv, o.omega,
-                        o.field, o.gt);
+        return std::tie(fmt, tps, block, n, trackg, measure, reunit, ktime, orv, slices, omega, field, gt) <
+               std::tie(o.fmt, o.tps, o.block, o.n, o.trackg, o.measure, o.reunit, o.ktime, o.orv, o.slices,
+                        o.omega, o.field, o.gt);
     }
 };
 
@@ -60,6 +62,8 @@ struct gf_ctx {
     int variant = 0;  // 0 auto, 1 per-subgroup rotations of the held links, 2 accumulate form
     int acc_regs = 0;  // accumulate form, FP64 storage: register budget 255, 168 or 128 (0 = autotuned)
     int or_variant = 0;  // g -> g^omega: 0 rational 19-flop form, 1 first order, 2 exact power
+    int slice_theta = 0;  // 1: convergence judged on the largest theta of the timeslices
+    double *dslices = nullptr;  // F_t, theta_t of the last per-timeslice measurement
     int use_graphs = 1;
     int kernel_timing = 0;     // events around the sweep kernels of every check chunk
     cudaEvent_t kev[2] = { nullptr, nullptr };
@@ -149,10 +153,12 @@ static void drop_graphs(gf_ctx *c)
 static int ensure_common(gf_ctx *ctx)
 {
     if (!ctx->partials) {
-        int n = measure_blocks(ctx->geom);
-        int m = aos_blocks(ctx->geom);
-        CK(cudaMalloc(&ctx->partials, sizeof(double) * 2 * (size_t)(n > m ? n : m)));
+        size_t n = (size_t)measure_blocks(ctx->geom);
+        size_t m = (size_t)aos_blocks(ctx->geom);
+        size_t k = (size_t)slice_blocks(ctx->geom) * (size_t)ctx->geom.L[3];
+        CK(cudaMalloc(&ctx->partials, sizeof(double) * 2 * std::max(n, std::max(m, k))));
     }
+    if (!ctx->dslices) CK(cudaMalloc(&ctx->dslices, sizeof(double) * 2 * (size_t)ctx->geom.L[3]));
     if (!ctx->dres) CK(cudaMalloc(&ctx->dres, sizeof(double) * 4));
     if (!ctx->hres) CK(cudaMallocHost(&ctx->hres, sizeof(double) * 4));
     if (!ctx->dstatus) CK(cudaMalloc(&ctx->dstatus, sizeof(int) * 4));
@@ -294,6 +300,14 @@ static cudaError_t issue_sweeps(gf_ctx *ctx, int fmt, char *field, double omega,
     return cudaSuccess;
 }
 
+// F and theta (or, per timeslice, mean F_t and max theta_t) of a resident field into dres
+static cudaError_t launch_check(gf_ctx *ctx, int fmt, FieldRef f, cudaStream_t s)
+{
+    if (ctx->slice_theta)
+        return launch_measure_slices(fmt, f, ctx->geom, ctx->gauge, ctx->partials, ctx->dslices, ctx->dres, s);
+    return launch_measure(fmt, f, ctx->geom, ctx->gauge, ctx->partials, ctx->dres, s);
+}
+
 // n sweeps of the resident field [+ reunitarisation] [+ F/theta into hres]
 static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, bool trackg, bool measure,
                      bool reunit)
@@ -314,14 +328,14 @@ static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, boo
         if (kt) CK(cudaEventRecord(ctx->kev[1], ctx->stream));
         if (reunit) CK(launch_reunitarize(fmt, f, ctx->geom, ctx->stream));
         if (measure) {
-            CK(launch_measure(fmt, f, ctx->geom, ctx->gauge, ctx->partials, ctx->dres, ctx->stream));
+            CK(launch_check(ctx, fmt, f, ctx->stream));
             CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         }
         return GF_OK;
     }
     if (ctx->use_graphs && n > 0) {
-        GraphKey key{ fmt,        cfg.first,          cfg.second, n, trackg, measure, reunit, kt ? 1 : 0,
-                      ctx->or_variant, omega, field, ctx->gt };
+        GraphKey key{ fmt,    cfg.first,       cfg.second,       n,     trackg, measure, reunit, kt ? 1 : 0,
+                      ctx->or_variant, ctx->slice_theta, omega, field, ctx->gt };
         auto it = ctx->graphs.find(key);
         if (it == ctx->graphs.end()) {
             cudaGraph_t graph;
@@ -332,7 +346,7 @@ static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, boo
             if (e == cudaSuccess && kt) e = cudaEventRecordWithFlags(ctx->kev[1], ctx->cap, cudaEventRecordExternal);
             if (e == cudaSuccess && reunit) e = launch_reunitarize(fmt, f, ctx->geom, ctx->cap);
             if (e == cudaSuccess && measure)
-                e = launch_measure(fmt, f, ctx->geom, ctx->gauge, ctx->partials, ctx->dres, ctx->cap);
+                e = launch_check(ctx, fmt, f, ctx->cap);
             if (e == cudaSuccess && measure)
                 e = cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->cap);
             cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &graph);
@@ -352,7 +366,7 @@ static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, boo
     if (kt) CK(cudaEventRecord(ctx->kev[1], ctx->stream));
     if (reunit) CK(launch_reunitarize(fmt, f, ctx->geom, ctx->stream));
     if (measure) {
-        CK(launch_measure(fmt, f, ctx->geom, ctx->gauge, ctx->partials, ctx->dres, ctx->stream));
+        CK(launch_check(ctx, fmt, f, ctx->stream));
         CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     }
     return GF_OK;
@@ -361,8 +375,7 @@ static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, boo
 static int measure_resident(gf_ctx *ctx, double *F, double *theta)
 {
     if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
-    CK(launch_measure(ctx->resident_fmt, ref(ctx, resident_base(ctx)), ctx->geom, ctx->gauge, ctx->partials,
-                      ctx->dres, ctx->stream));
+    CK(launch_check(ctx, ctx->resident_fmt, ref(ctx, resident_base(ctx)), ctx->stream));
     CK(cudaMemcpyAsync(ctx->hres, ctx->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (F) *F = ctx->hres[0];
@@ -566,6 +579,7 @@ int gf_destroy(gf_ctx *ctx)
     cudaFree(ctx->feat);
     cudaFree(ctx->cbuf);
     cudaFree(ctx->partials);
+    cudaFree(ctx->dslices);
     cudaFree(ctx->dres);
     cudaFree(ctx->dstatus);
     if (ctx->hres) cudaFreeHost(ctx->hres);
@@ -626,6 +640,8 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
     } else if (k == "variant") {
         if (!integral || iv < 0 || iv > 2) return fail(ctx, GF_EINVAL, "variant: 0, 1 or 2");
         ctx->variant = iv;
+    } else if (k == "theta_per_timeslice") {
+        ctx->slice_theta = v != 0.0;
     } else if (k == "or_variant") {
         if (!integral || iv < 0 || iv > 2) return fail(ctx, GF_EINVAL, "or_variant: 0, 1 or 2");
         ctx->or_variant = iv;
@@ -681,6 +697,7 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *v)
     else if (k == "use_graphs") *v = ctx->use_graphs;
     else if (k == "acc_registers") *v = ctx->acc_regs;
     else if (k == "or_variant") *v = ctx->or_variant;
+    else if (k == "theta_per_timeslice") *v = ctx->slice_theta;
     else if (k == "kernel_timing") *v = ctx->kernel_timing;
     else if (k == "autotune") *v = ctx->autotune;
     else if (k == "sa_cap") *v = ctx->sa_cap;
@@ -768,6 +785,27 @@ int gf_sr_half_sweep(gf_ctx *ctx, int parity, double p, uint64_t seed, uint32_t 
     a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     a.sweep = sweep;
     CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 2, false, cfg.second, ctx->stream));
+    return GF_OK;
+}
+
+int gf_measure_timeslices(gf_ctx *ctx, double *F_t, double *theta_t)
+{
+    if (!ctx) return GF_EINVAL;
+    if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
+    RET(ensure_common(ctx));
+    const int Lt = ctx->geom.L[3];
+    CK(launch_measure_slices(ctx->resident_fmt, ref(ctx, resident_base(ctx)), ctx->geom, ctx->gauge, ctx->partials,
+                             ctx->dslices, ctx->dres, ctx->stream));
+    std::vector<double> h(2 * (size_t)Lt);
+    CK(cudaMemcpyAsync(h.data(), ctx->dslices, sizeof(double) * 2 * Lt, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<double> a(Lt), b(Lt);
+    for (int t = 0; t < Lt; ++t) {
+        a[t] = h[2 * t];
+        b[t] = h[2 * t + 1];
+    }
+    if (F_t) CK(cudaMemcpy(F_t, a.data(), sizeof(double) * Lt, cudaMemcpyDefault));
+    if (theta_t) CK(cudaMemcpy(theta_t, b.data(), sizeof(double) * Lt, cudaMemcpyDefault));
     return GF_OK;
 }
 

@@ -105,6 +105,54 @@ __global__ void __launch_bounds__(kReduceBlock) k_measure(FieldRef f, Geom g, do
     block_sum2(fsum, tsum, partials + 2 * blockIdx.x);
 }
 
+// per timeslice: block (b, t) covers sites b*blockDim .. of timeslice t (both
+// parities; the half-sites of a timeslice are contiguous, Lx Ly Lz / 2 of each)
+template <int FMT, bool COULOMB>
+__global__ void __launch_bounds__(kReduceBlock) k_measure_slices(FieldRef f, Geom g, double *partials)
+{
+    const int hs = g.Vh / g.L[3];  // half-sites per timeslice and parity
+    const int t = blockIdx.y;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    double fsum = 0.0, tsum = 0.0;
+    if (j < 2 * hs) {
+        int p = j >= hs ? 1 : 0;
+        measure_site<FMT, COULOMB>(f, g, p, t * hs + (j - p * hs), fsum, tsum);
+    }
+    block_sum2(fsum, tsum, partials + 2 * ((long)t * gridDim.x + blockIdx.x));
+}
+
+// slices[2t], slices[2t+1] = F_t, theta_t (fixed-order sums of the block partials)
+__global__ void k_finalize_slices(const double *__restrict__ partials, int nb, double sa, double sb,
+                                  double *slices)
+{
+    const int t = blockIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a += partials[2 * ((long)t * nb + i)];
+        b += partials[2 * ((long)t * nb + i) + 1];
+    }
+    __shared__ double r[2];
+    block_sum2(a, b, r);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        slices[2 * t] = r[0] * sa;
+        slices[2 * t + 1] = r[1] * sb;
+    }
+}
+
+// out[0] = mean of F_t (the global F), out[1] = max of theta_t
+__global__ void k_slices_summary(const double *__restrict__ slices, int Lt, double *out)
+{
+    if (threadIdx.x != 0) return;
+    double f = 0.0, m = 0.0;
+    for (int t = 0; t < Lt; ++t) {
+        f += slices[2 * t];
+        m = fmax(m, slices[2 * t + 1]);
+    }
+    out[0] = f / (double)Lt;
+    out[1] = m;
+}
+
 template <bool COULOMB>
 __global__ void __launch_bounds__(kReduceBlock) k_measure_aos(const double *__restrict__ aos, Geom g,
                                                               double *partials)
@@ -248,6 +296,29 @@ cudaError_t launch_measure(int fmt, FieldRef f, const Geom &g, int coulomb, doub
     if (e != cudaSuccess) return e;
     double V = 2.0 * g.Vh;
     k_finalize<<<1, 256, 0, s>>>(partials, n, 1.0 / (3.0 * (coulomb ? 3 : 4) * V), 1.0 / (3.0 * V), out);
+    return cudaGetLastError();
+}
+
+int slice_blocks(const Geom &g) { return nblocks(2L * (g.Vh / g.L[3]), kReduceBlock); }
+
+cudaError_t launch_measure_slices(int fmt, FieldRef f, const Geom &g, int coulomb, double *partials,
+                                  double *slices, double *out, cudaStream_t s)
+{
+    int nb = slice_blocks(g);
+    dim3 grid(nb, g.L[3]);
+#define GF_CALL(F)                                                                   \
+    if (coulomb) k_measure_slices<F, true><<<grid, kReduceBlock, 0, s>>>(f, g, partials); \
+    else k_measure_slices<F, false><<<grid, kReduceBlock, 0, s>>>(f, g, partials)
+    GF_FMT_SWITCH(fmt, GF_CALL)
+#undef GF_CALL
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    double Ls = 2.0 * g.Vh / g.L[3];
+    k_finalize_slices<<<g.L[3], 256, 0, s>>>(partials, nb, 1.0 / (3.0 * (coulomb ? 3 : 4) * Ls), 1.0 / (3.0 * Ls),
+                                             slices);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_slices_summary<<<1, 32, 0, s>>>(slices, g.L[3], out);
     return cudaGetLastError();
 }
 

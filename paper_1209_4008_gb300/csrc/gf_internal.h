@@ -95,6 +95,10 @@ cudaError_t launch_apply_tracked_gauge(const double *aos, FieldRef gt, int dst_f
                                        cudaStream_t s);
 // F and theta of the resident field: nblocks partials, then the final sum
 int measure_blocks(const Geom &g);
+int slice_blocks(const Geom &g);  // blocks per timeslice of launch_measure_slices
+// F_t, theta_t of every timeslice into slices[2 Lt]; out[0] = mean F_t, out[1] = max theta_t
+cudaError_t launch_measure_slices(int fmt, FieldRef f, const Geom &g, int coulomb, double *partials,
+                                  double *slices, double *out, cudaStream_t s);
 cudaError_t launch_measure(int fmt, FieldRef f, const Geom &g, int coulomb, double *partials, double *out,
                            cudaStream_t s);
 // F and theta of a canonical (AoS) field

@@ -62,6 +62,7 @@ SIGNATURES = {
     "gf_or_sweeps": (C.c_int, [_vp, C.c_double, C.c_int]),
     "gf_sa_half_sweep": (C.c_int, [_vp, C.c_int, C.c_double, C.c_uint64, C.c_uint32]),
     "gf_measure": (C.c_int, [_vp, _dp, _dp]),
+    "gf_measure_timeslices": (C.c_int, [_vp, _dp, _dp]),
     "gf_sr_half_sweep": (C.c_int, [_vp, C.c_int, C.c_double, C.c_uint64, C.c_uint32]),
     "gf_reunitarize": (C.c_int, [_vp]),
     "gf_autotune": (C.c_int, [_vp, _ip, _ip]),
@@ -291,6 +292,17 @@ def gf_measure(ctx: Context):
     F, th = C.c_double(), C.c_double()
     ctx.check(ctx.lib.gf_measure(ctx.handle, C.byref(F), C.byref(th)), "gf_measure")
     return F.value, th.value
+
+
+def gf_measure_timeslices(ctx: Context):
+    """(F_t, theta_t) of every timeslice of the resident field (numpy arrays)."""
+    import numpy as np
+    Lt = int(ctx.dims[3])
+    F = np.zeros(Lt)
+    th = np.zeros(Lt)
+    ctx.check(ctx.lib.gf_measure_timeslices(ctx.handle, F.ctypes.data_as(_dp), th.ctypes.data_as(_dp)),
+              "gf_measure_timeslices")
+    return F, th
 
 
 def gf_reunitarize(ctx: Context) -> None:

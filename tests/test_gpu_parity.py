@@ -526,3 +526,42 @@ def test_or_variant_solver_converges_with_oracle_sweep_count(oracle_or_variant, 
     oconv, oit, oF, oth = oracle.overrelax(W, 0, 1.7, 1e-12, 20000, 10)
     assert conv and oconv and it == oit
     assert abs(F - oF) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# per-timeslice F and theta (Coulomb gauge fixes each timeslice on its own)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 6, 10), (10, 6, 4, 8)])
+@pytest.mark.parametrize("gauge", [0, 1])
+@pytest.mark.parametrize("prec", [gf.GF_FP64, gf.GF_FP32])
+def test_timeslice_measurement_matches_oracle(dims, gauge, prec):
+    U = cpu_field(dims, seed=21, gseed=22)
+    c = ctx_for(dims, gauge)
+    gf.gf_upload(c, dev(U), prec)
+    F_t, th_t = gf.gf_measure_timeslices(c)
+    oF, oth = oracle.timeslices(U, gauge)
+    if prec == gf.GF_FP64:
+        np.testing.assert_allclose(F_t, oF, rtol=1e-13)
+        np.testing.assert_allclose(th_t, oth, rtol=1e-12)
+    else:  # FP32 storage: the links are rounded to FP32 (6e-8)
+        np.testing.assert_allclose(F_t, oF, atol=1e-6)
+        np.testing.assert_allclose(th_t, oth, rtol=1e-5)
+    F, th = gf.gf_measure(c)
+    assert F == pytest.approx(F_t.mean(), rel=1e-12)
+
+
+def test_coulomb_converges_every_timeslice():
+    dims = (8, 8, 8, 6)
+    U = cpu_field(dims, seed=23, gseed=24)
+    c = ctx_for(dims, 1, check_every=10, theta_per_timeslice=1)
+    d = dev(U)
+    conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-12, 20000)
+    assert conv
+    W = host(d)
+    oF, oth = oracle.timeslices(W, 1)
+    assert oth.max() < 1e-12
+    assert th == pytest.approx(oth.max(), rel=1e-9)
+    # the global criterion stops no later (its theta is the mean)
+    c2 = ctx_for(dims, 1, check_every=10)
+    conv2, it2, F2, th2 = gf.gf_overrelax(c2, dev(U), 1.7, 1e-12, 20000)
+    assert conv2 and it2 <= it
