@@ -565,3 +565,34 @@ def test_coulomb_converges_every_timeslice():
     c2 = ctx_for(dims, 1, check_every=10)
     conv2, it2, F2, th2 = gf.gf_overrelax(c2, dev(U), 1.7, 1e-12, 20000)
     assert conv2 and it2 <= it
+
+
+# ---------------------------------------------------------------------------
+# a long annealing schedule down to T = 0.01 through every site-update form
+# ---------------------------------------------------------------------------
+FORMS = [dict(variant=1, threads_per_site=2), dict(variant=2), dict(variant=2, acc_registers=168, block=64),
+         dict(variant=2, acc_registers=168, block=128), dict(variant=2, acc_registers=128, block=128),
+         dict(variant=2, acc_registers=128, block=256), dict(fp64_arith=1)]
+
+
+@pytest.mark.parametrize("form", range(len(FORMS)))
+@pytest.mark.parametrize("gauge", [0, 1])
+def test_anneal_long_schedule_every_form(form, gauge):
+    dims = (8, 8, 8, 16)
+    U = cpu_field(dims, seed=27, gseed=28, plaq=0.58)
+    c = ctx_for(dims, gauge, **FORMS[form])
+    d = dev(U)
+    P = oracle.plaquette(U)
+    gf.gf_anneal(c, d, 1.45, 0.01, 300, 77)
+    out = host(d)
+    assert np.isfinite(out).all()
+    assert gf.gf_plaquette(c, d) == pytest.approx(P, abs=1e-12)
+    F_gpu = gf.gf_functional(c, d)
+    assert oracle.anneal(U, gauge, 1.45, 0.01, 300, 77) == 0
+    # same draws on both sides; the accept decisions agree unless a draw falls
+    # within rounding of a boundary, which these seeds avoid
+    assert max_rel(out, U) < 1e-8
+    assert F_gpu == pytest.approx(oracle.functional(U, gauge), abs=1e-10)
+    # overrelaxation continues from the annealed field
+    conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-10, 5000)
+    assert conv and np.isfinite(F)
