@@ -138,6 +138,7 @@ static int fmt64(const gf_ctx *c)
     return c->storage64 == 12 ? F64_12 : F64_18;
 }
 static int fmt32(const gf_ctx *c) { return c->storage32 == 18 ? F32_18 : F32_12; }
+static bool twelve_real(int fmt) { return fmt == F64_12 || fmt == F32_12; }
 
 static size_t plane_bytes(const gf_ctx *c) { return (size_t)c->geom.plane * 16; }
 static size_t field_bytes(const gf_ctx *c, int fmt) { return 8 * (size_t)format_chunks(fmt) * plane_bytes(c); }
@@ -874,7 +875,8 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
             RET(autotune_format(ctx, ctx->resident_fmt, ctx->f64, nullptr, nullptr));
         RET(measure_resident(ctx, &F, &theta));
         double t1 = now_ms();
-        RET(converge(ctx, omega, theta_target, max_iter, false, false, &used64, &F, &theta));
+        // 12-real storage: reunitarised at every check (row 2 is rebuilt on every load)
+        RET(converge(ctx, omega, theta_target, max_iter, false, twelve_real(ctx->resident_fmt), &used64, &F, &theta));
         ms64 = now_ms() - t1;
     } else {
         bool track = ctx->precision == GF_MIXED && ctx->track_gauge;
@@ -931,7 +933,8 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
                 ctx->stats["theta_before_learned"] = ctx->stats["theta_switch_measured"];
                 ctx->stats["theta_after_learned"] = theta;
             }
-            RET(converge(ctx, omega, theta_target, max_iter - used32, false, false, &used64, &F, &theta));
+            RET(converge(ctx, omega, theta_target, max_iter - used32, false, twelve_real(ctx->resident_fmt), &used64,
+                         &F, &theta));
             ms64 = now_ms() - t2;
         } else {
             CK(launch_reunitarize(ctx->resident_fmt, ref(ctx, ctx->f32), ctx->geom, ctx->stream));
@@ -1076,6 +1079,10 @@ int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t 
         RET(autotune_format(ctx, ctx->resident_fmt, resident_base(ctx), nullptr, nullptr));
     CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int) * 4, ctx->stream));
     std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt);
+    // 12-real storage rebuilds row 2 from rows 0, 1 on every load; under the
+    // large rotations of annealing that feeds unitarity errors back with gain
+    // up to 2 per update, so those fields are reunitarised every 4 sweeps
+    const bool reunit = twelve_real(ctx->resident_fmt);
     for (int k = 0; k < steps; ++k) {
         double T = steps > 1 ? T0 + (T1 - T0) * (double)k / (double)(steps - 1) : T0;
         for (int p = 0; p < 2; ++p) {
@@ -1085,6 +1092,8 @@ int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t 
             a.sweep = ctx->sa_sweep_offset + (uint32_t)k;
             CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 1, false, cfg.second, ctx->stream));
         }
+        if (reunit && (k % 4 == 3 || k == steps - 1))
+            CK(launch_reunitarize(ctx->resident_fmt, ref(ctx, resident_base(ctx)), ctx->geom, ctx->stream));
     }
     int rejects = 0;
     CK(cudaMemcpyAsync(ctx->hres + 2, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

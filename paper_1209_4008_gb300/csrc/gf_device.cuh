@@ -377,43 +377,62 @@ __device__ __forceinline__ bool overrelax_quat(const double k[4], double omega, 
 // 1 + omega k/|k|); 2 = the exact power, r = (cos(omega phi), sin(omega phi) n)
 // for k/|k| = (cos phi, sin phi n), left unchanged when n is undefined.
 template <class T>
-__device__ __forceinline__ bool overrelax_first_order(const T k[4], T omega, T r[4])
+struct quat_ok {
+    T r0, r1, r2, r3;
+    int ok;
+};
+
+// (out of line, arguments and result by value: the default reading pays no
+// registers or local memory for these paths)
+template <class T>
+__device__ __noinline__ quat_ok<T> overrelax_first_order(T k0, T k1, T k2, T k3, T omega)
 {
-    T n = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
-    if (n == T(0)) return false;
-    T v[4] = { (T(1) - omega) + omega * (k[0] / n), omega * (k[1] / n), omega * (k[2] / n), omega * (k[3] / n) };
-    T m = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
-    if (m == T(0)) return false;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) r[c] = v[c] / m;
-    return true;
+    quat_ok<T> q = { T(0), T(0), T(0), T(0), 0 };
+    T n = sqrt(k0 * k0 + k1 * k1 + k2 * k2 + k3 * k3);
+    if (n == T(0)) return q;
+    T v0 = (T(1) - omega) + omega * (k0 / n), v1 = omega * (k1 / n), v2 = omega * (k2 / n), v3 = omega * (k3 / n);
+    T m = sqrt(v0 * v0 + v1 * v1 + v2 * v2 + v3 * v3);
+    if (m == T(0)) return q;
+    q.r0 = v0 / m;
+    q.r1 = v1 / m;
+    q.r2 = v2 / m;
+    q.r3 = v3 / m;
+    q.ok = 1;
+    return q;
 }
 
 template <class T>
-__device__ __forceinline__ bool overrelax_exact_power(const T k[4], T omega, T r[4])
+__device__ __noinline__ quat_ok<T> overrelax_exact_power(T k0, T k1, T k2, T k3, T omega)
 {
-    T a = sqrt(k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
+    quat_ok<T> q = { T(0), T(0), T(0), T(0), 0 };
+    T a = sqrt(k1 * k1 + k2 * k2 + k3 * k3);
     if (a == T(0)) {
-        if (!(k[0] > T(0))) return false;
-        r[0] = T(1);
-        r[1] = r[2] = r[3] = T(0);
-        return true;
+        if (!(k0 > T(0))) return q;
+        q.r0 = T(1);
+        q.ok = 1;
+        return q;
     }
-    T phi = atan2(a, k[0]);
+    T phi = atan2(a, k0);
     T c = cos(omega * phi), sn = sin(omega * phi);
-    r[0] = c;
-    r[1] = sn * (k[1] / a);
-    r[2] = sn * (k[2] / a);
-    r[3] = sn * (k[3] / a);
-    return true;
+    q.r0 = c;
+    q.r1 = sn * (k1 / a);
+    q.r2 = sn * (k2 / a);
+    q.r3 = sn * (k3 / a);
+    q.ok = 1;
+    return q;
 }
 
 template <class T>
 __device__ __forceinline__ bool overrelax_step(const T k[4], T omega, int variant, T r[4])
 {
-    if (variant == 1) return overrelax_first_order(k, omega, r);
-    if (variant == 2) return overrelax_exact_power(k, omega, r);
-    return overrelax_quat(k, omega, r);
+    if (variant == 0) return overrelax_quat(k, omega, r);
+    quat_ok<T> q = variant == 1 ? overrelax_first_order(k[0], k[1], k[2], k[3], omega)
+                                : overrelax_exact_power(k[0], k[1], k[2], k[3], omega);
+    r[0] = q.r0;
+    r[1] = q.r1;
+    r[2] = q.r2;
+    r[3] = q.r3;
+    return q.ok != 0;
 }
 
 // ---------------------------------------------------------------------------

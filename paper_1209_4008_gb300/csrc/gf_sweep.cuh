@@ -273,6 +273,98 @@ __device__ __forceinline__ void mul_rows_dagger(const mat3<T> &x, const mat3<T> 
         }
 }
 
+
+// row 2 of z = x y
+template <class T>
+__device__ __forceinline__ void mul_row2(const mat3<T> &x, const mat3<T> &y, mat3<T> &z)
+{
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        T re = x.e[2][0].re * y.e[0][b].re - x.e[2][0].im * y.e[0][b].im;
+        T im = x.e[2][0].re * y.e[0][b].im + x.e[2][0].im * y.e[0][b].re;
+#pragma unroll
+        for (int c = 1; c < 3; ++c) {
+            re += x.e[2][c].re * y.e[c][b].re - x.e[2][c].im * y.e[c][b].im;
+            im += x.e[2][c].re * y.e[c][b].im + x.e[2][c].im * y.e[c][b].re;
+        }
+        z.e[2][b] = mk<T>(re, im);
+    }
+}
+
+// how strongly G mixes row 2 with rows 0, 1: |G20|^2 + |G21|^2
+template <class T>
+__device__ __forceinline__ T row2_mixing(const mat3<T> &G)
+{
+    return G.e[2][0].re * G.e[2][0].re + G.e[2][0].im * G.e[2][0].im + G.e[2][1].re * G.e[2][1].re +
+           G.e[2][1].im * G.e[2][1].im;
+}
+
+// below this mixing the third row of an 18-real link is rebuilt from rows 0, 1
+// (error growth at most 1 + 1e-4 per update); above it, multiplied out
+constexpr double kCrossRow2 = 1e-4;
+
+// Gram-Schmidt of rows 0 and 1 (row 2 is implied by them in 12-real storage)
+template <class T>
+__device__ __forceinline__ void normalize_rows01(mat3<T> &u)
+{
+    T n0 = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) n0 += u.e[0][c].re * u.e[0][c].re + u.e[0][c].im * u.e[0][c].im;
+    T i0 = rsqrt(n0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u.e[0][c] = mk<T>(u.e[0][c].re * i0, u.e[0][c].im * i0);
+    // row1 -= <row0, row1> row0
+    T pre = T(0), pim = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        pre += u.e[0][c].re * u.e[1][c].re + u.e[0][c].im * u.e[1][c].im;
+        pim += u.e[0][c].re * u.e[1][c].im - u.e[0][c].im * u.e[1][c].re;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        u.e[1][c] = mk<T>(u.e[1][c].re - (pre * u.e[0][c].re - pim * u.e[0][c].im),
+                          u.e[1][c].im - (pre * u.e[0][c].im + pim * u.e[0][c].re));
+    T n1 = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) n1 += u.e[1][c].re * u.e[1][c].re + u.e[1][c].im * u.e[1][c].im;
+    T i1 = rsqrt(n1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u.e[1][c] = mk<T>(u.e[1][c].re * i1, u.e[1][c].im * i1);
+}
+
+// U_mu(x) <- G U_mu(x), U_mu(x-mu) <- U_mu(x-mu) G^dagger for mu = 0..3, each
+// link re-read; CROSS: rows 0, 1 multiplied out and row 2 = conj(row0 x row1)
+// (the backward link re-read without its third row), else row 2 multiplied
+// out too (18-real storage only)
+template <int FMT, bool CROSS>
+__device__ __forceinline__ void apply_links(const SweepArgs &a, int p, int h, const int hb[4],
+                                            const mat3<typename Store<FMT>::T> &G)
+{
+    typedef Store<FMT> S;
+    typedef typename S::T T;
+    constexpr int ROWS = S::REALS == 12 ? 2 : 3;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        mat3<T> u, v;
+        reload<FMT>(a.f, (p * 4 + mu) * S::NCHUNK, h, u);
+        mul_rows<T, 2>(G, u, v);
+        if (ROWS == 3) {
+            if (CROSS) rebuild_row2(v);
+            else mul_row2(G, u, v);
+        }
+        S::store(a.f, (p * 4 + mu) * S::NCHUNK, h, v);
+        if (CROSS) {
+            reload_rows01<FMT>(a.f, ((p ^ 1) * 4 + mu) * S::NCHUNK, hb[mu], u);
+            mul_rows_dagger<T, 2>(u, G, v);
+            if (ROWS == 3) rebuild_row2(v);
+        } else {
+            reload<FMT>(a.f, ((p ^ 1) * 4 + mu) * S::NCHUNK, hb[mu], u);
+            mul_rows_dagger<T, ROWS>(u, G, v);
+        }
+        S::store(a.f, ((p ^ 1) * 4 + mu) * S::NCHUNK, hb[mu], v);
+    }
+}
+
 template <int FMT, bool COULOMB, int MODE, bool TRACKG>
 __device__ __forceinline__ void sweep_site_acc(const SweepArgs &a, int h)
 {
@@ -344,21 +436,15 @@ __device__ __forceinline__ void sweep_site_acc(const SweepArgs &a, int h)
         G.e[2][2] = cmul(cconj(al[2]), g22);
     }
     // apply G: U_mu(x) <- G U_mu(x), U_mu(x-mu) <- U_mu(x-mu) G^dagger.  Rows 0, 1
-    // are multiplied out; an 18-real link gets row 2 = conj(row0 x row1), which
-    // is the product's third row for SU(3) factors (Sec. 4.1) at 2/3 of the cost,
-    // and the backward link is re-read without its third row.
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-        mat3<T> u, v;
-        reload<FMT>(a.f, (p * 4 + mu) * S::NCHUNK, h, u);
-        mul_rows<T, 2>(G, u, v);
-        if (ROWS == 3) rebuild_row2(v);
-        S::store(a.f, (p * 4 + mu) * S::NCHUNK, h, v);
-        reload_rows01<FMT>(a.f, ((p ^ 1) * 4 + mu) * S::NCHUNK, hb[mu], u);
-        mul_rows_dagger<T, 2>(u, G, v);
-        if (ROWS == 3) rebuild_row2(v);
-        S::store(a.f, ((p ^ 1) * 4 + mu) * S::NCHUNK, hb[mu], v);
-    }
+    // are multiplied out.  Row 2 of an 18-real link: when G hardly mixes row 2
+    // with rows 0, 1 (w = |G20|^2 + |G21|^2 below kCrossRow2, as near
+    // convergence), conj(row0 x row1) -- the product's third row for SU(3)
+    // factors (Sec. 4.1) at 2/3 of the cost, the backward link re-read without
+    // its third row; otherwise the direct product, because the rebuilt row
+    // feeds the unitarity error of rows 0, 1 back with gain up to 1 + w per
+    // update (an unbounded growth under the large rotations of annealing).
+    if (ROWS == 2 || row2_mixing(G) < T(kCrossRow2)) apply_links<FMT, true>(a, p, h, hb, G);
+    else apply_links<FMT, false>(a, p, h, hb, G);
     if (TRACKG) {
         mat3<float> gx, gy;
         Store<F32_12>::load(a.gt, p * 3, h, gx);
@@ -368,6 +454,7 @@ __device__ __forceinline__ void sweep_site_acc(const SweepArgs &a, int h)
 #pragma unroll
             for (int j = 0; j < 3; ++j) Gf.e[i][j] = mk<float>((float)G.e[i][j].re, (float)G.e[i][j].im);
         mul_rows<float, 2>(Gf, gx, gy);
+        normalize_rows01(gy);  // 12-real storage: keep the rebuilt third row from amplifying errors
         Store<F32_12>::store(a.gt, p * 3, h, gy);
     }
 }
@@ -466,7 +553,10 @@ __device__ __forceinline__ void sweep_site(const SweepArgs &a, int h, int j, uns
         else
             S::store(a.f, ((p ^ 1) * 4 + mu) * S::NCHUNK, hb[l], dagger(x[l]));
     }
-    if (TRACKG && j == 0) Store<F32_12>::store(a.gt, p * 3, h, gx);
+    if (TRACKG && j == 0) {
+        normalize_rows01(gx);
+        Store<F32_12>::store(a.gt, p * 3, h, gx);
+    }
 }
 
 template <int FMT, bool COULOMB, int MODE, bool TRACKG>

@@ -102,6 +102,50 @@ __device__ __forceinline__ void subgroup_element_df(const SweepArgs &a, cdf xaa,
     be.im = df_from_double(rd[1]);
 }
 
+// U_mu(x) <- G U_mu(x) (one column of U at a time) and U_mu(x-mu) <- U_mu(x-mu)
+// G^dagger (one row at a time) for mu = 0..3; CROSS: rows 0, 1 multiplied out
+// and row 2 = conj(row0 x row1), else all three rows multiplied out
+template <bool CROSS>
+__device__ __forceinline__ void apply_links_df(const SweepArgs &a, int p, int h, const int hb[4], const mat3df &G)
+{
+    constexpr int NR = CROSS ? 2 : 3;
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+        const int pf = (p * 4 + mu) * 9, pb = ((p ^ 1) * 4 + mu) * 9;
+        cdf v[2][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cdf col[3];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) col[l] = reload_chunk_df(a.f, pf + 3 * l + j, h);
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                cdf s = cdf_zero();
+#pragma unroll
+                for (int l = 0; l < 3; ++l) s = cdf_mac(s, G.e[i][l], col[l]);
+                if (CROSS) v[i][j] = s;
+                store_chunk_df(a.f, pf + 3 * i + j, h, s);
+            }
+        }
+        if (CROSS) store_row2_df(a.f, pf, h, v);
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            cdf row[3];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) row[l] = reload_chunk_df(a.f, pb + 3 * i + l, hb[mu]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                cdf s = cdf_zero();
+#pragma unroll
+                for (int l = 0; l < 3; ++l) s = cdf_mac_conj(s, row[l], G.e[j][l]);
+                if (CROSS) v[i][j] = s;
+                store_chunk_df(a.f, pb + 3 * i + j, hb[mu], s);
+            }
+        }
+        if (CROSS) store_row2_df(a.f, pb, hb[mu], v);
+    }
+}
+
 template <bool COULOMB, int MODE, bool TRACKG>
 __device__ __forceinline__ void sweep_site_df(const SweepArgs &a, int h)
 {
@@ -166,43 +210,13 @@ __device__ __forceinline__ void sweep_site_df(const SweepArgs &a, int h)
         G.e[2][2] = cdf_mul(cdf_conj(al[2]), g22);
     }
     // U_mu(x) <- G U_mu(x) and U_mu(x-mu) <- U_mu(x-mu) G^dagger: rows 0, 1
-    // multiplied out (forward: one column of U at a time; backward: one row),
-    // row 2 = conj(row0 x row1)
-#pragma unroll 1
-    for (int mu = 0; mu < 4; ++mu) {
-        const int pf = (p * 4 + mu) * 9, pb = ((p ^ 1) * 4 + mu) * 9;
-        cdf v[2][3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            cdf col[3];
-#pragma unroll
-            for (int l = 0; l < 3; ++l) col[l] = reload_chunk_df(a.f, pf + 3 * l + j, h);
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                cdf s = cdf_zero();
-#pragma unroll
-                for (int l = 0; l < 3; ++l) s = cdf_mac(s, G.e[i][l], col[l]);
-                v[i][j] = s;
-                store_chunk_df(a.f, pf + 3 * i + j, h, s);
-            }
-        }
-        store_row2_df(a.f, pf, h, v);
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            cdf row[3];
-#pragma unroll
-            for (int l = 0; l < 3; ++l) row[l] = reload_chunk_df(a.f, pb + 3 * i + l, hb[mu]);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                cdf s = cdf_zero();
-#pragma unroll
-                for (int l = 0; l < 3; ++l) s = cdf_mac_conj(s, row[l], G.e[j][l]);
-                v[i][j] = s;
-                store_chunk_df(a.f, pb + 3 * i + j, hb[mu], s);
-            }
-        }
-        store_row2_df(a.f, pb, hb[mu], v);
-    }
+    // multiplied out (forward: one column of U at a time; backward: one row);
+    // row 2 = conj(row0 x row1) when G hardly mixes row 2 (as in the FP64
+    // accumulate form, kCrossRow2), else multiplied out as well
+    const float w = G.e[2][0].re.hi * G.e[2][0].re.hi + G.e[2][0].im.hi * G.e[2][0].im.hi +
+                    G.e[2][1].re.hi * G.e[2][1].re.hi + G.e[2][1].im.hi * G.e[2][1].im.hi;
+    if (w < (float)kCrossRow2) apply_links_df<true>(a, p, h, hb, G);
+    else apply_links_df<false>(a, p, h, hb, G);
     if (TRACKG) {
         mat3<float> gx, gy, Gf;
         Store<F32_12>::load(a.gt, p * 3, h, gx);
@@ -212,6 +226,7 @@ __device__ __forceinline__ void sweep_site_df(const SweepArgs &a, int h)
             for (int j = 0; j < 3; ++j)
                 Gf.e[i][j] = mk<float>(G.e[i][j].re.hi + G.e[i][j].re.lo, G.e[i][j].im.hi + G.e[i][j].im.lo);
         mul_rows<float, 2>(Gf, gx, gy);
+        normalize_rows01(gy);
         Store<F32_12>::store(a.gt, p * 3, h, gy);
     }
 }
