@@ -32,9 +32,10 @@ struct GraphKey {
     }
 };
 
-// autotuner cache: (Lx, Ly, Lz, Lt, format, gauge) -> (threads per site, block)
 std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+// autotuner cache: (Lx, Ly, Lz, Lt, format, gauge, mode) -> (threads per site, block);
+// mode 0: overrelaxation (and stochastic relaxation), 1: heatbath
+std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
 
 double now_ms()
 {
@@ -253,12 +254,18 @@ static std::pair<int, int> default_config(int fmt)
     }
 }
 
-static std::pair<int, int> launch_config(const gf_ctx *c, int fmt)
+static std::tuple<int, int, int, int, int, int, int> tune_key(const gf_ctx *c, int fmt, int mode)
+{
+    return std::make_tuple(c->dims[0], c->dims[1], c->dims[2], c->dims[3], fmt, c->gauge, mode == 1 ? 1 : 0);
+}
+
+static std::pair<int, int> launch_config(const gf_ctx *c, int fmt, int mode = 0)
 {
     std::pair<int, int> cfg = default_config(fmt);
     {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
-        auto it = g_tune_cache.find(std::make_tuple(c->dims[0], c->dims[1], c->dims[2], c->dims[3], fmt, c->gauge));
+        auto it = g_tune_cache.find(tune_key(c, fmt, mode));
+        if (it == g_tune_cache.end() && mode == 1) it = g_tune_cache.find(tune_key(c, fmt, 0));
         if (it != g_tune_cache.end()) cfg = it->second;
     }
     if (c->tps) cfg.first = c->tps;
@@ -446,7 +453,23 @@ static int download(gf_ctx *ctx, double *U, bool host)
 // ---------------------------------------------------------------------------
 // autotuner
 // ---------------------------------------------------------------------------
-static int autotune_format(gf_ctx *ctx, int fmt, char *field, int *tps_out, int *block_out)
+// heatbath half-sweeps of a scratch field for the autotuner (T = 1, fixed key)
+static cudaError_t issue_sa_sweeps(gf_ctx *ctx, int fmt, char *field, int n, std::pair<int, int> cfg, cudaStream_t s)
+{
+    for (int k = 0; k < n; ++k)
+        for (int p = 0; p < 2; ++p) {
+            SweepArgs a = sweep_args(ctx, field, p, 1.0);
+            a.T = 1.0;
+            a.key = make_uint2(0x9e3779b9u, 0u);
+            a.sweep = (uint32_t)k;
+            cudaError_t e = launch_sweep(fmt, a, cfg.first, ctx->gauge, 1, false, cfg.second, s);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+// mode 0: time overrelaxation sweeps; 1: heatbath sweeps
+static int autotune_format(gf_ctx *ctx, int fmt, char *field, int *tps_out, int *block_out, int mode = 0)
 {
     size_t bytes = field_bytes(ctx, fmt);
     char *scratch = nullptr;
@@ -465,9 +488,12 @@ static int autotune_format(gf_ctx *ctx, int fmt, char *field, int *tps_out, int 
         for (int b = 0; b < 3 && e == cudaSuccess; ++b) {
             if (tps_c[i] == GF_ACC_R168 && blk_c[b] > 128) continue;
             std::pair<int, int> cfg{ tps_c[i], blk_c[b] };
-            e = issue_sweeps(ctx, fmt, scratch, 1.7, 1, false, cfg, ctx->stream);  // warm up
+            e = mode == 1 ? issue_sa_sweeps(ctx, fmt, scratch, 1, cfg, ctx->stream)
+                          : issue_sweeps(ctx, fmt, scratch, 1.7, 1, false, cfg, ctx->stream);  // warm up
             if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
-            if (e == cudaSuccess) e = issue_sweeps(ctx, fmt, scratch, 1.7, 3, false, cfg, ctx->stream);
+            if (e == cudaSuccess)
+                e = mode == 1 ? issue_sa_sweeps(ctx, fmt, scratch, 2, cfg, ctx->stream)
+                              : issue_sweeps(ctx, fmt, scratch, 1.7, 3, false, cfg, ctx->stream);
             if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0;
@@ -483,17 +509,17 @@ static int autotune_format(gf_ctx *ctx, int fmt, char *field, int *tps_out, int 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
     {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
-        g_tune_cache[std::make_tuple(ctx->dims[0], ctx->dims[1], ctx->dims[2], ctx->dims[3], fmt, ctx->gauge)] = pick;
+        g_tune_cache[tune_key(ctx, fmt, mode)] = pick;
     }
     if (tps_out) *tps_out = pick.first;
     if (block_out) *block_out = pick.second;
     return GF_OK;
 }
 
-static bool tuned(const gf_ctx *c, int fmt)
+static bool tuned(const gf_ctx *c, int fmt, int mode = 0)
 {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
-    return g_tune_cache.count(std::make_tuple(c->dims[0], c->dims[1], c->dims[2], c->dims[3], fmt, c->gauge)) > 0;
+    return g_tune_cache.count(tune_key(c, fmt, mode)) > 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -766,7 +792,7 @@ int gf_sa_half_sweep(gf_ctx *ctx, int parity, double T, uint64_t seed, uint32_t 
     if (!ctx) return GF_EINVAL;
     if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
     if ((parity & ~1) || !(T > 0.0) || !std::isfinite(T)) return fail(ctx, GF_EINVAL, "parity 0/1, T > 0");
-    std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt);
+    std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt, 1);
     SweepArgs a = sweep_args(ctx, resident_base(ctx), parity, 1.0);
     a.T = T;
     a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -1075,10 +1101,10 @@ int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t 
     RET(device_view(ctx, U, &view, &host));
     int prec = ctx->precision == GF_FP32 ? GF_FP32 : GF_FP64;
     RET(upload(ctx, view, prec));
-    if (ctx->autotune && !tuned(ctx, ctx->resident_fmt))
-        RET(autotune_format(ctx, ctx->resident_fmt, resident_base(ctx), nullptr, nullptr));
+    if (ctx->autotune && !tuned(ctx, ctx->resident_fmt, 1))
+        RET(autotune_format(ctx, ctx->resident_fmt, resident_base(ctx), nullptr, nullptr, 1));
     CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int) * 4, ctx->stream));
-    std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt);
+    std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt, 1);
     // 12-real storage rebuilds row 2 from rows 0, 1 on every load; under the
     // large rotations of annealing that feeds unitarity errors back with gain
     // up to 2 per update, so those fields are reunitarised every 4 sweeps

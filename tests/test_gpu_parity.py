@@ -608,3 +608,17 @@ def test_anneal_long_schedule_every_form(form, gauge):
     assert gf.gf_functional(c, d) == pytest.approx(oracle.functional(W, gauge), abs=0.02)
     conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-10, 5000)  # overrelaxation continues from there
     assert conv and np.isfinite(F)
+
+
+def test_anneal_autotuned_heatbath_config():
+    """gf_anneal tunes its own launch configuration (heatbath timing); the
+    result is that of any fixed configuration up to rounding."""
+    dims = (8, 8, 8, 8)
+    U = cpu_field(dims, seed=29, gseed=30)
+    a = ctx_for(dims, 1, autotune=1)
+    b = ctx_for(dims, 1, variant=1, threads_per_site=4)
+    da, db = dev(U), dev(U)
+    gf.gf_anneal(a, da, 1.2, 0.1, 6, 5)
+    gf.gf_anneal(b, db, 1.2, 0.1, 6, 5)
+    assert max_rel(host(da), host(db)) < 1e-11
+    assert gf.gf_get_stat(a, "sweeps") == 6
