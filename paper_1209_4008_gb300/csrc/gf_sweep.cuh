@@ -443,7 +443,10 @@ __device__ __forceinline__ void sweep_site_acc(const SweepArgs &a, int h)
     // its third row; otherwise the direct product, because the rebuilt row
     // feeds the unitarity error of rows 0, 1 back with gain up to 1 + w per
     // update (an unbounded growth under the large rotations of annealing).
-    if (ROWS == 2 || row2_mixing(G) < T(kCrossRow2)) apply_links<FMT, true>(a, p, h, hb, G);
+    // the choice is made per warp (all its sites below the threshold), so that a
+    // warp never runs both paths
+    const bool cross = ROWS == 2 || __all_sync(__activemask(), row2_mixing(G) < T(kCrossRow2));
+    if (cross) apply_links<FMT, true>(a, p, h, hb, G);
     else apply_links<FMT, false>(a, p, h, hb, G);
     if (TRACKG) {
         mat3<float> gx, gy;

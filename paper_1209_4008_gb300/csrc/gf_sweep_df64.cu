@@ -215,7 +215,7 @@ __device__ __forceinline__ void sweep_site_df(const SweepArgs &a, int h)
     // accumulate form, kCrossRow2), else multiplied out as well
     const float w = G.e[2][0].re.hi * G.e[2][0].re.hi + G.e[2][0].im.hi * G.e[2][0].im.hi +
                     G.e[2][1].re.hi * G.e[2][1].re.hi + G.e[2][1].im.hi * G.e[2][1].im.hi;
-    if (w < (float)kCrossRow2) apply_links_df<true>(a, p, h, hb, G);
+    if (__all_sync(__activemask(), w < (float)kCrossRow2)) apply_links_df<true>(a, p, h, hb, G);  // per warp
     else apply_links_df<false>(a, p, h, hb, G);
     if (TRACKG) {
         mat3<float> gx, gy, Gf;
