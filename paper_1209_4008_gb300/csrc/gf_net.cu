@@ -223,6 +223,11 @@ __global__ void k_cast_weights(const float *__restrict__ W, int I, int O, bf16 *
 // IP: input channels padded to a multiple of 16; N: output channels padded
 // (16 or 32).  X rows have I channels, W is [81][O][I].
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrap_coord(int c, int L) { return c < 0 ? c + L : (c >= L ? c - L : c); }
+
+// v[j] for j in {0, 1, 2} without dynamic indexing (stays in registers)
+__device__ __forceinline__ int sel3(const int v[3], int j) { return j == 0 ? v[0] : (j == 1 ? v[1] : v[2]); }
+
 template <int IP, int N>
 struct TcLayout {
     static constexpr int A_BYTES = gf::tc::kM * IP * 2;
@@ -264,9 +269,56 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16 *__restrict__ X, int
     const uint32_t tmem = *tmem_slot;
 
     const int site = s0 + tid;
+    // neighbour of this row's site for tap k = (d0+1) + 3 (d1+1) + 9 (d2+1) +
+    // 27 (d3+1): the sum over dimensions of the wrapped coordinate c + sign d
+    // times its stride, the 12 terms formed once
+    int o0[3], o1[3], o2[3], o3[3];
+    {
+        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        if (site < g.V) {
+            c0 = site % g.L[0];
+            int r = site / g.L[0];
+            c1 = r % g.L[1];
+            r /= g.L[1];
+            c2 = r % g.L[2];
+            c3 = r / g.L[2];
+        }
+        const int st1 = g.L[0], st2 = g.L[0] * g.L[1], st3 = st2 * g.L[2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int d = sign * (j - 1);
+            o0[j] = wrap_coord(c0 + d, g.L[0]);
+            o1[j] = wrap_coord(c1 + d, g.L[1]) * st1;
+            o2[j] = wrap_coord(c2 + d, g.L[2]) * st2;
+            o3[j] = wrap_coord(c3 + d, g.L[3]) * st3;
+        }
+    }
+    constexpr int AC = IP / 8;                                  // 16-byte chunks of one A row
+    constexpr int WPT = (N * (IP / 8) + kThreads - 1) / kThreads;  // weight chunks per thread
+    uint4 cur[AC], nxt[AC], wcur[WPT], wnxt[WPT];
+    // global loads of tap k's A row and B chunks into registers
+    auto fetch = [&](int k, uint4 *a, uint4 *w) {
+        const int nbs = site < g.V ? sel3(o0, k % 3) + sel3(o1, (k / 3) % 3) + sel3(o2, (k / 9) % 3) + sel3(o3, k / 27)
+                                   : -1;
+#pragma unroll
+        for (int c = 0; c < AC; ++c) {
+            a[c] = make_uint4(0, 0, 0, 0);
+            if (nbs >= 0 && 8 * c < I) a[c] = *reinterpret_cast<const uint4 *>(X + (long)nbs * I + 8 * c);
+        }
+#pragma unroll
+        for (int q = 0; q < WPT; ++q) {
+            const int e = tid + q * kThreads;
+            const int o = e / (IP / 8), c = e - o * (IP / 8);
+            w[q] = make_uint4(0, 0, 0, 0);
+            if (e < N * (IP / 8) && o < O && 8 * c < I)
+                w[q] = *reinterpret_cast<const uint4 *>(W + ((long)k * O + o) * I + 8 * c);
+        }
+    };
+    fetch(0, cur, wcur);
     bool fail = false;
     for (int k = 0; k < 81; ++k) {
         const int st = k % kStages;
+        if (k + 1 < 81) fetch(k + 1, nxt, wnxt);  // in flight while tap k is staged
         if (k >= kStages) {
             if (!mbar_wait(&bar[st], (uint32_t)((k / kStages - 1) & 1))) fail = true;
         }
@@ -278,19 +330,16 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16 *__restrict__ X, int
         uint8_t *B = A + LY::A_BYTES;
         // A: this thread's neighbour row, K-major core matrices (8 rows x 16 B):
         // core (mr, kc) at (kc * 16 + mr) * 128  -> SBO 128, LBO 2048
-        const int nbs = site < g.V ? shift_site(g, site, k, sign) : -1;
 #pragma unroll
-        for (int c = 0; c < IP / 8; ++c) {
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (nbs >= 0 && 8 * c < I) v = *reinterpret_cast<const uint4 *>(X + (long)nbs * I + 8 * c);
-            *reinterpret_cast<uint4 *>(A + (c * 16 + (tid >> 3)) * 128 + (tid & 7) * 16) = v;
-        }
+        for (int c = 0; c < AC; ++c) *reinterpret_cast<uint4 *>(A + (c * 16 + (tid >> 3)) * 128 + (tid & 7) * 16) = cur[c];
         // B: weights of tap k, core (mr, kc) at (kc * (N/8) + mr) * 128 -> SBO 128, LBO N*16
-        for (int e = tid; e < N * (IP / 8); e += kThreads) {
-            const int o = e / (IP / 8), c = e - o * (IP / 8);
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (o < O && 8 * c < I) v = *reinterpret_cast<const uint4 *>(W + ((long)k * O + o) * I + 8 * c);
-            *reinterpret_cast<uint4 *>(B + (c * (N / 8) + (o >> 3)) * 128 + (o & 7) * 16) = v;
+#pragma unroll
+        for (int q = 0; q < WPT; ++q) {
+            const int e = tid + q * kThreads;
+            if (e < N * (IP / 8)) {
+                const int o = e / (IP / 8), c = e - o * (IP / 8);
+                *reinterpret_cast<uint4 *>(B + (c * (N / 8) + (o >> 3)) * 128 + (o & 7) * 16) = wcur[q];
+            }
         }
         fence_proxy_async();
         __syncthreads();
@@ -304,6 +353,10 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16 *__restrict__ X, int
             }
             mma_commit(&bar[st]);
         }
+#pragma unroll
+        for (int c = 0; c < AC; ++c) cur[c] = nxt[c];
+#pragma unroll
+        for (int q = 0; q < WPT; ++q) wcur[q] = wnxt[q];
     }
     // all MMAs issued by thread 0 are complete once the final commit arrives
     if (tid == 0) mma_commit(&bar[kStages]);
