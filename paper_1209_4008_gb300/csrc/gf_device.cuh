@@ -36,8 +36,15 @@ __device__ __forceinline__ cpx<T> mk(T re, T im)
 template <class T>
 __device__ __forceinline__ cpx<T> conj_cross(cpx<T> a, cpx<T> d, cpx<T> b, cpx<T> c)
 {
-    T re = a.re * d.re - a.im * d.im - (b.re * c.re - b.im * c.im);
-    T im = a.re * d.im + a.im * d.re - (b.re * c.im + b.im * c.re);
+    // one multiply and three FMAs per component
+    T re = a.re * d.re;
+    re = fma(-a.im, d.im, re);
+    re = fma(-b.re, c.re, re);
+    re = fma(b.im, c.im, re);
+    T im = a.re * d.im;
+    im = fma(a.im, d.re, im);
+    im = fma(-b.re, c.im, im);
+    im = fma(-b.im, c.re, im);
     return mk<T>(re, -im);
 }
 

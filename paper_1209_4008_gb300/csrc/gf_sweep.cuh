@@ -234,6 +234,10 @@ __device__ __forceinline__ void reload_rows01<DF64_18>(const FieldRef &f, int pl
     }
 }
 
+// Products of 3x3 complex matrices, written as explicit FMA chains: an
+// update "re += a*b - c*d" would round the difference first and cost an extra
+// add per term.
+
 // z = x y for 3x3 complex matrices; rows >= ROWS of z are not computed
 template <class T, int ROWS>
 __device__ __forceinline__ void mul_rows(const mat3<T> &x, const mat3<T> &y, mat3<T> &z)
@@ -242,12 +246,16 @@ __device__ __forceinline__ void mul_rows(const mat3<T> &x, const mat3<T> &y, mat
     for (int a = 0; a < ROWS; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            T re = x.e[a][0].re * y.e[0][b].re - x.e[a][0].im * y.e[0][b].im;
-            T im = x.e[a][0].re * y.e[0][b].im + x.e[a][0].im * y.e[0][b].re;
+            T re = x.e[a][0].re * y.e[0][b].re;
+            T im = x.e[a][0].re * y.e[0][b].im;
+            re = fma(-x.e[a][0].im, y.e[0][b].im, re);
+            im = fma(x.e[a][0].im, y.e[0][b].re, im);
 #pragma unroll
             for (int c = 1; c < 3; ++c) {
-                re += x.e[a][c].re * y.e[c][b].re - x.e[a][c].im * y.e[c][b].im;
-                im += x.e[a][c].re * y.e[c][b].im + x.e[a][c].im * y.e[c][b].re;
+                re = fma(x.e[a][c].re, y.e[c][b].re, re);
+                re = fma(-x.e[a][c].im, y.e[c][b].im, re);
+                im = fma(x.e[a][c].re, y.e[c][b].im, im);
+                im = fma(x.e[a][c].im, y.e[c][b].re, im);
             }
             z.e[a][b] = mk<T>(re, im);
         }
@@ -262,17 +270,20 @@ __device__ __forceinline__ void mul_rows_dagger(const mat3<T> &x, const mat3<T> 
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             // sum_c x[a][c] conj(y[b][c])
-            T re = x.e[a][0].re * y.e[b][0].re + x.e[a][0].im * y.e[b][0].im;
-            T im = x.e[a][0].im * y.e[b][0].re - x.e[a][0].re * y.e[b][0].im;
+            T re = x.e[a][0].re * y.e[b][0].re;
+            T im = x.e[a][0].im * y.e[b][0].re;
+            re = fma(x.e[a][0].im, y.e[b][0].im, re);
+            im = fma(-x.e[a][0].re, y.e[b][0].im, im);
 #pragma unroll
             for (int c = 1; c < 3; ++c) {
-                re += x.e[a][c].re * y.e[b][c].re + x.e[a][c].im * y.e[b][c].im;
-                im += x.e[a][c].im * y.e[b][c].re - x.e[a][c].re * y.e[b][c].im;
+                re = fma(x.e[a][c].re, y.e[b][c].re, re);
+                re = fma(x.e[a][c].im, y.e[b][c].im, re);
+                im = fma(x.e[a][c].im, y.e[b][c].re, im);
+                im = fma(-x.e[a][c].re, y.e[b][c].im, im);
             }
             z.e[a][b] = mk<T>(re, im);
         }
 }
-
 
 // row 2 of z = x y
 template <class T>
@@ -280,12 +291,16 @@ __device__ __forceinline__ void mul_row2(const mat3<T> &x, const mat3<T> &y, mat
 {
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        T re = x.e[2][0].re * y.e[0][b].re - x.e[2][0].im * y.e[0][b].im;
-        T im = x.e[2][0].re * y.e[0][b].im + x.e[2][0].im * y.e[0][b].re;
+        T re = x.e[2][0].re * y.e[0][b].re;
+        T im = x.e[2][0].re * y.e[0][b].im;
+        re = fma(-x.e[2][0].im, y.e[0][b].im, re);
+        im = fma(x.e[2][0].im, y.e[0][b].re, im);
 #pragma unroll
         for (int c = 1; c < 3; ++c) {
-            re += x.e[2][c].re * y.e[c][b].re - x.e[2][c].im * y.e[c][b].im;
-            im += x.e[2][c].re * y.e[c][b].im + x.e[2][c].im * y.e[c][b].re;
+            re = fma(x.e[2][c].re, y.e[c][b].re, re);
+            re = fma(-x.e[2][c].im, y.e[c][b].im, re);
+            im = fma(x.e[2][c].re, y.e[c][b].im, im);
+            im = fma(x.e[2][c].im, y.e[c][b].re, im);
         }
         z.e[2][b] = mk<T>(re, im);
     }
