@@ -51,13 +51,21 @@ __device__ __forceinline__ cdf lin_b_df(cdf al, cdf be, cdf xa, cdf xb)
     return p;
 }
 
-// conj(a d - b c)
+// conj(a d - b c), each component one double-float dot product of four terms
 __device__ __forceinline__ cdf conj_cross_df(cdf a, cdf d, cdf b, cdf c)
 {
-    cdf p = cdf_mul(a, d), q = cdf_mul(b, c);
+    dacc re = { 0.f, 0.f }, im = { 0.f, 0.f };
+    dacc_add_prod(re, a.re, d.re);
+    dacc_add_prod(re, df_neg(a.im), d.im);
+    dacc_add_prod(re, df_neg(b.re), c.re);
+    dacc_add_prod(re, b.im, c.im);
+    dacc_add_prod(im, df_neg(a.re), d.im);  // the imaginary part of a d - b c, negated
+    dacc_add_prod(im, df_neg(a.im), d.re);
+    dacc_add_prod(im, b.re, c.im);
+    dacc_add_prod(im, b.im, c.re);
     cdf r;
-    r.re = df_sub(p.re, q.re);
-    r.im = df_sub(q.im, p.im);
+    r.re = dacc_result(re);
+    r.im = dacc_result(im);
     return r;
 }
 
@@ -120,9 +128,7 @@ __device__ __forceinline__ void apply_links_df(const SweepArgs &a, int p, int h,
             for (int l = 0; l < 3; ++l) col[l] = reload_chunk_df(a.f, pf + 3 * l + j, h);
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
-                cdf s = cdf_zero();
-#pragma unroll
-                for (int l = 0; l < 3; ++l) s = cdf_mac(s, G.e[i][l], col[l]);
+                const cdf s = cdf_dot3<false>(G.e[i], col);
                 if (CROSS) v[i][j] = s;
                 store_chunk_df(a.f, pf + 3 * i + j, h, s);
             }
@@ -135,9 +141,7 @@ __device__ __forceinline__ void apply_links_df(const SweepArgs &a, int p, int h,
             for (int l = 0; l < 3; ++l) row[l] = reload_chunk_df(a.f, pb + 3 * i + l, hb[mu]);
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
-                cdf s = cdf_zero();
-#pragma unroll
-                for (int l = 0; l < 3; ++l) s = cdf_mac_conj(s, row[l], G.e[j][l]);
+                const cdf s = cdf_dot3<true>(row, G.e[j]);
                 if (CROSS) v[i][j] = s;
                 store_chunk_df(a.f, pb + 3 * i + j, hb[mu], s);
             }
