@@ -64,6 +64,13 @@ def _declare(lib: C.CDLL) -> C.CDLL:
     d.oracle_block_quaternion.restype = None
     d.oracle_overrelax_quaternion.argtypes = [_dp, C.c_double, _dp]
     d.oracle_set_or_variant.argtypes = [C.c_int]
+    d.oracle_mag_half_sweep.argtypes = [_dp, _ip, C.c_int, C.c_double]
+    d.oracle_mag_functional.argtypes = [_dp, _ip]
+    d.oracle_mag_functional.restype = C.c_double
+    d.oracle_mag_theta.argtypes = [_dp, _ip]
+    d.oracle_mag_theta.restype = C.c_double
+    d.oracle_mag_local_matrix.argtypes = [_dp, _ip, C.c_long, C.c_int, _dp]
+    d.oracle_mag_maximiser.argtypes = [_dp, _dp]
     d.oracle_site_quaternion.argtypes = [_dp, _ip, C.c_long, C.c_int, C.c_int, _dp]
     d.oracle_site_rotate.argtypes = [_dp, _ip, C.c_long, C.c_int, _dp]
     for f in ("oracle_functional", "oracle_theta", "oracle_theta_from_M"):
@@ -445,3 +452,41 @@ def backward_site(dims, i: int, mu: int) -> int:
     c = [i % Lx, (i // Lx) % Ly, (i // (Lx * Ly)) % Lz, i // (Lx * Ly * Lz)]
     c[mu] = (c[mu] - 1) % dims[mu]
     return site_index(dims, *c)
+
+
+# ---------------------------------------------------------------------------
+# maximally Abelian gauge (Sec. 6)
+# ---------------------------------------------------------------------------
+def mag_half_sweep(U, parity: int, omega: float) -> None:
+    U = _field(U)
+    _check(lib().oracle_mag_half_sweep(_d(U), _i(dims_of(U)), parity, omega), "mag half sweep")
+
+
+def mag_sweeps(U, omega: float, n: int = 1) -> None:
+    for _ in range(n):
+        mag_half_sweep(U, 0, omega)
+        mag_half_sweep(U, 1, omega)
+
+
+def mag_functional(U) -> float:
+    U = _field(U)
+    return lib().oracle_mag_functional(_d(U), _i(dims_of(U)))
+
+
+def mag_theta(U) -> float:
+    U = _field(U)
+    return lib().oracle_mag_theta(_d(U), _i(dims_of(U)))
+
+
+def mag_local_matrix(U, site: int, sg: int) -> np.ndarray:
+    U = _field(U)
+    A = np.zeros(16)
+    _check(lib().oracle_mag_local_matrix(_d(U), _i(dims_of(U)), site, sg, _d(A)), "mag local matrix")
+    return A.reshape(4, 4)
+
+
+def mag_maximiser(A) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.float64).reshape(16)
+    r = np.zeros(4)
+    lib().oracle_mag_maximiser(_d(A), _d(r))
+    return r

@@ -1160,3 +1160,207 @@ int oracle_sr_half_sweep(double *U, const int dims[4], int parity, double p, int
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Maximally Abelian gauge (named in Sec. 6 as the next application of the  */
+/* method; the functional is the one of the gauge-fixing literature)        */
+/* ------------------------------------------------------------------------ */
+/*
+ * F_MAG = 1/(3 Nd V) sum_{x, mu} sum_i |U_mu(x)_ii|^2   (Nd = 4; 1 for diagonal links)
+ *
+ * Local step at site x, subgroup (a,b), element R(r) = r0 + i r.sigma: the
+ * site's part of F_MAG after U_mu(x) <- R U_mu(x), U_mu(x-mu) <- U_mu(x-mu) R^+
+ * is a quadratic form q(r) = r^T A r in the quaternion r (R is linear in r).
+ * A is read off q by polarisation; the maximiser over unit r is an eigenvector
+ * of the largest eigenvalue (Jacobi rotations).  That eigenvalue is at least
+ * two-fold: F_MAG does not change under the diagonal U(1) of the subgroup,
+ * so among the maximisers the one closest to the identity (largest r0) is
+ * taken.  The overrelaxation exponent is then applied to it as for Landau
+ * gauge (overrelax_quaternion with k = r).
+ */
+static double diag_sq(const mat3 *u, int a, int b)
+{
+    return c_abs2(u->m[a][a]) + c_abs2(u->m[b][b]);
+}
+
+/* q(r): the (a,b) diagonal weight of the star after the (unnormalised) rotation R(r) */
+static double mag_local_value(const star *s, int a, int b, const double r[4])
+{
+    cplx R[2][2];
+    su2_matrix(r, R);
+    double q = 0.0;
+    for (int mu = 0; mu < 4; ++mu) {
+        mat3 f = s->fwd[mu], w = s->bwd[mu];
+        rotate_rows(&f, a, b, R);
+        rotate_cols_dagger(&w, a, b, R);
+        q += diag_sq(&f, a, b) + diag_sq(&w, a, b);
+    }
+    return q;
+}
+
+static void mag_local_matrix(const star *s, int a, int b, double A[4][4])
+{
+    for (int k = 0; k < 4; ++k)
+        for (int m = k; m < 4; ++m) {
+            double p[4] = { 0, 0, 0, 0 }, n[4] = { 0, 0, 0, 0 };
+            p[k] += 1.0;
+            p[m] += 1.0;
+            n[k] += 1.0;
+            n[m] -= 1.0;
+            /* polarisation: A_km = (q(e_k + e_m) - q(e_k - e_m)) / 4 */
+            A[k][m] = A[m][k] = 0.25 * (mag_local_value(s, a, b, p) - mag_local_value(s, a, b, n));
+        }
+}
+
+/* eigen-decomposition of a symmetric 4x4 matrix by cyclic Jacobi rotations:
+ * A <- V^T A V diagonal, columns of V the eigenvectors */
+static void jacobi4(double A[4][4], double V[4][4])
+{
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                tot += A[i][j] * A[i][j];
+                if (i != j) off += A[i][j] * A[i][j];
+            }
+        if (off <= 1e-32 * tot) break;
+        for (int p = 0; p < 3; ++p)
+            for (int q = p + 1; q < 4; ++q) {
+                if (A[p][q] == 0.0) continue;
+                double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < 4; ++k) { /* columns p, q */
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - sn * akq;
+                    A[k][q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < 4; ++k) { /* rows p, q */
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - sn * aqk;
+                    A[q][k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < 4; ++k) {
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+/* the maximiser closest to the identity; returns 0 (r = identity) when the
+ * top eigenspace contains no direction with r0 != 0 */
+static int mag_maximiser(double A[4][4], double r[4])
+{
+    double B[4][4], V[4][4];
+    memcpy(B, A, sizeof B);
+    jacobi4(B, V);
+    int i1 = 0, i2 = -1;
+    for (int i = 1; i < 4; ++i)
+        if (B[i][i] > B[i1][i1]) i1 = i;
+    for (int i = 0; i < 4; ++i)
+        if (i != i1 && (i2 < 0 || B[i][i] > B[i2][i2])) i2 = i;
+    /* project e0 onto the top eigenspace (two-fold by the U(1) symmetry) */
+    double scale = fabs(B[i1][i1]) > 1.0 ? fabs(B[i1][i1]) : 1.0;
+    int two = (B[i1][i1] - B[i2][i2]) <= 1e-10 * scale;
+    for (int c = 0; c < 4; ++c) r[c] = V[0][i1] * V[c][i1] + (two ? V[0][i2] * V[c][i2] : 0.0);
+    double n = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+    if (!(n > 1e-12)) {
+        r[0] = 1.0;
+        r[1] = r[2] = r[3] = 0.0;
+        return 0;
+    }
+    for (int c = 0; c < 4; ++c) r[c] /= n;
+    return 1;
+}
+
+static void mag_update_star(star *s, double omega)
+{
+    for (int sg = 0; sg < 3; ++sg) {
+        int a = SUBGROUP[sg][0], b = SUBGROUP[sg][1];
+        double A[4][4], r[4], ro[4];
+        cplx R[2][2];
+        mag_local_matrix(s, a, b, A);
+        if (!mag_maximiser(A, r)) continue;
+        if (!overrelax_quaternion(r, omega, ro)) continue;
+        su2_matrix(ro, R);
+        star_rotate(s, a, b, R);
+    }
+}
+
+int oracle_mag_half_sweep(double *U, const int dims[4], int parity, double omega)
+{
+    lattice g;
+    if (lattice_init(&g, dims)) return -1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (long i = 0; i < g.V; ++i) {
+        if (site_parity(&g, i) != parity) continue;
+        star s;
+        star_load(U, &g, i, &s);
+        mag_update_star(&s, omega);
+        star_store(U, &g, i, &s);
+    }
+    return 0;
+}
+
+double oracle_mag_functional(const double *U, const int dims[4])
+{
+    lattice g;
+    if (lattice_init(&g, dims)) return NAN;
+    double sum = 0.0;
+    for (long i = 0; i < g.V; ++i)
+        for (int mu = 0; mu < 4; ++mu) {
+            mat3 u = mat_load(link_cptr(U, i, mu));
+            for (int a = 0; a < 3; ++a) sum += c_abs2(u.m[a][a]);
+        }
+    return sum / (3.0 * 4.0 * (double)g.V);
+}
+
+/*
+ * theta_MAG = 1/(3V) sum_x sum_{subgroups} (A_10^2 + A_20^2): the squared
+ * gradient of the local functional at the identity along the two directions
+ * that are not the residual U(1) (which has zero gradient); zero exactly at a
+ * stationary point of every subgroup update.
+ */
+double oracle_mag_theta(const double *U, const int dims[4])
+{
+    lattice g;
+    if (lattice_init(&g, dims)) return NAN;
+    double sum = 0.0;
+    for (long i = 0; i < g.V; ++i) {
+        star s;
+        star_load(U, &g, i, &s);
+        for (int sg = 0; sg < 3; ++sg) {
+            double A[4][4];
+            mag_local_matrix(&s, SUBGROUP[sg][0], SUBGROUP[sg][1], A);
+            sum += A[1][0] * A[1][0] + A[2][0] * A[2][0];
+        }
+    }
+    return sum / (3.0 * (double)g.V);
+}
+
+/* the local matrix A of site i, subgroup sg (row-major 16 doubles), for the pins */
+int oracle_mag_local_matrix(const double *U, const int dims[4], long i, int sg, double *A16)
+{
+    lattice g;
+    if (lattice_init(&g, dims) || sg < 0 || sg > 2) return -1;
+    star s;
+    star_load(U, &g, i, &s);
+    double A[4][4];
+    mag_local_matrix(&s, SUBGROUP[sg][0], SUBGROUP[sg][1], A);
+    memcpy(A16, A, sizeof A);
+    return 0;
+}
+
+/* the maximiser of a given local matrix (closest to the identity) */
+int oracle_mag_maximiser(const double *A16, double *r)
+{
+    double A[4][4];
+    memcpy(A, A16, sizeof A);
+    return mag_maximiser(A, r);
+}

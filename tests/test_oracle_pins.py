@@ -591,3 +591,109 @@ def test_timeslice_values_are_local_in_time():
             assert th_t[t] > 1e-3 and F_t[t] < 0.99
         else:
             assert th_t[t] < 1e-28 and F_t[t] == pytest.approx(1.0, abs=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# maximally Abelian gauge (Sec. 6; functional sum |U_ii|^2 of the literature)
+# ---------------------------------------------------------------------------
+def _diag_weight_after(star_links, a, b, R):
+    """sum over the 8 links of |diag_a|^2 + |diag_b|^2 after the subgroup
+    rotation R (forward links R U, backward links U R^dagger), with numpy."""
+    G = np.eye(3, dtype=complex)
+    G[np.ix_([a, b], [a, b])] = R
+    q = 0.0
+    for f in star_links[0]:
+        V = G @ f
+        q += abs(V[a, a]) ** 2 + abs(V[b, b]) ** 2
+    for w in star_links[1]:
+        V = w @ G.conj().T
+        q += abs(V[a, a]) ** 2 + abs(V[b, b]) ** 2
+    return q
+
+
+def _star(U, site):
+    dims = oracle.dims_of(U)
+    flat = U.reshape(-1, 4, 3, 3)
+    fwd = [flat[site, mu] for mu in range(4)]
+    bwd = [flat[oracle.backward_site(tuple(int(d) for d in dims), site, mu), mu] for mu in range(4)]
+    return fwd, bwd
+
+
+def test_mag_local_matrix_is_the_quadratic_form_and_its_maximum():
+    """q(r) = r^T A r for unit and non-unit r (numpy evaluation of the diagonal
+    weight); no random SU(2) element beats the chosen maximiser, which reaches
+    the largest eigenvalue of A."""
+    U = field((4, 4, 4, 4), seed=51, gseed=52)
+    rng = np.random.default_rng(53)
+    for site, sg in ((0, 0), (37, 1), (101, 2)):
+        a, b = [(0, 1), (1, 2), (0, 2)][sg]
+        A = oracle.mag_local_matrix(U, site, sg)
+        st = _star(U, site)
+        for _ in range(5):
+            r = rng.standard_normal(4)
+            assert r @ A @ r == pytest.approx(_diag_weight_after(st, a, b, su2_from_quaternion(r)), rel=1e-12)
+        r = oracle.mag_maximiser(A)
+        best = _diag_weight_after(st, a, b, su2_from_quaternion(r))
+        assert best == pytest.approx(np.linalg.eigvalsh(A).max(), rel=1e-12)
+        trials = rng.standard_normal((20000, 4))
+        trials /= np.linalg.norm(trials, axis=1, keepdims=True)
+        vals = np.einsum("ni,ij,nj->n", trials, A, trials)
+        assert vals.max() <= best + 1e-12
+
+
+def test_mag_maximiser_is_the_su2_textbook_solution():
+    """For links block-diag(SU(2), 1) the subgroup-(0,1) MAG step is the SU(2)
+    one: g rotates X = sum_mu [U s3 U^+ + U_b^+ s3 U_b] onto +|X| s3 (numpy)."""
+    U = field((4, 4, 4, 4), seed=55, gseed=56)
+    flat = U.reshape(-1, 4, 3, 3)
+    for n in range(flat.shape[0]):  # keep the SU(2) block of every link
+        for mu in range(4):
+            m = flat[n, mu][:2, :2]
+            d = np.sqrt(np.linalg.det(m))
+            flat[n, mu] = np.eye(3)
+            flat[n, mu][:2, :2] = m / d
+    s3 = np.diag([1.0, -1.0])
+    for site in (0, 77):
+        fwd, bwd = _star(U, site)
+        X = sum(f[:2, :2] @ s3 @ f[:2, :2].conj().T for f in fwd) + \
+            sum(w[:2, :2].conj().T @ s3 @ w[:2, :2] for w in bwd)
+        R = su2_from_quaternion(oracle.mag_maximiser(oracle.mag_local_matrix(U, site, 0)))
+        Y = R @ X @ R.conj().T
+        assert abs(Y[0, 1]) < 1e-12 and Y[0, 0].real > 0
+        assert Y[0, 0].real == pytest.approx(np.sqrt(0.5 * np.trace(X @ X).real), rel=1e-12)
+
+
+def test_mag_relaxation_is_monotone_and_a_gauge_transformation():
+    U = field((4, 4, 4, 6), seed=57, gseed=58)
+    P = oracle.plaquette(U)
+    F = oracle.mag_functional(U)
+    for n in range(6):
+        oracle.mag_half_sweep(U, n % 2, 1.0)
+        F1 = oracle.mag_functional(U)
+        assert F1 >= F - 1e-14
+        F = F1
+    assert oracle.plaquette(U) == pytest.approx(P, abs=1e-13)
+
+
+def test_mag_fixed_points():
+    """Diagonal links are maximal (F = 1, theta = 0) and left unchanged; a
+    gauge-rotated diagonal field is brought back to F = 1, theta -> 0."""
+    import torch
+    dims = (4, 4, 4, 4)
+    rng = np.random.default_rng(59)
+    ph = rng.uniform(0, 2 * np.pi, (4, 4, 4, 4, 4, 2))
+    D = np.zeros((4, 4, 4, 4, 4, 3, 3), complex)
+    D[..., 0, 0] = np.exp(1j * ph[..., 0])
+    D[..., 1, 1] = np.exp(1j * ph[..., 1])
+    D[..., 2, 2] = np.exp(-1j * (ph[..., 0] + ph[..., 1]))
+    assert oracle.mag_functional(D) == pytest.approx(1.0, abs=1e-15)
+    assert oracle.mag_theta(D) < 1e-28
+    W = D.copy()
+    oracle.mag_sweeps(W, 1.7, 2)
+    np.testing.assert_allclose(W, D, atol=1e-14)
+    g = synth.haar_su3((4, 4, 4, 4), 60)
+    R = synth.as_numpy(synth.rotate_field(torch.from_numpy(D), g))
+    assert oracle.mag_functional(R) < 0.6
+    oracle.mag_sweeps(R, 1.7, 300)
+    assert oracle.mag_theta(R) < 1e-20
+    assert oracle.mag_functional(R) == pytest.approx(1.0, abs=1e-10)
