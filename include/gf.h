@@ -56,9 +56,13 @@ extern "C" {
 #define GF_EREJECT 6        /* heatbath: some draws hit the rejection cap (left unchanged) */
 #define GF_ESTATE 7         /* call needs a resident field and none is loaded */
 
-/* gauges (Sec. 1: Landau d_mu A_mu = 0, Coulomb d_i A_i = 0) */
+/* gauges (Sec. 1: Landau d_mu A_mu = 0, Coulomb d_i A_i = 0; Sec. 6: the
+ * maximally Abelian gauge, functional F = 1/(3 Nd V) sum_{x,mu} sum_i
+ * |U_mu(x)_ii|^2, theta = 1/(3V) sum_x sum_subgroups |h12|^2, the squared
+ * gradient of the local subgroup functional at the identity) */
 #define GF_LANDAU 0
 #define GF_COULOMB 1
+#define GF_MAG 2
 
 /* precision policy for gf_overrelax (option "precision") */
 #define GF_FP64 0   /* FP64 storage and arithmetic throughout */
@@ -70,7 +74,12 @@ typedef struct gf_ctx gf_ctx;
 /* ---------------------------------------------------------------- context */
 
 /* Create a context for a lattice of extents dims and the given gauge
- * (GF_LANDAU or GF_COULOMB).  Allocates nothing on the device yet.
+ * (GF_LANDAU, GF_COULOMB or GF_MAG).  Allocates nothing on the device yet.
+ * GF_MAG supports overrelaxation (gf_overrelax, gf_or_half_sweep,
+ * gf_or_sweeps, gf_converge, all precision policies, per-subgroup site
+ * update with 1-8 threads per site, native storage formats) and the
+ * measurements; annealing, stochastic relaxation, double-float storage,
+ * per-timeslice measurement and the learned warm start return GF_EINVAL.
  * *out receives the handle; release it with gf_destroy. */
 int gf_create(const int dims[4], int gauge, gf_ctx **out);
 

@@ -1251,30 +1251,35 @@ static void jacobi4(double A[4][4], double V[4][4])
     }
 }
 
-/* the maximiser closest to the identity; returns 0 (r = identity) when the
- * top eigenspace contains no direction with r0 != 0 */
+/* The maximiser closest to the identity: e0 = (1,0,0,0) projected onto the
+ * eigenspace of the largest eigenvalue (two-fold by the U(1) symmetry, four-
+ * fold when A is a multiple of the identity).  When that eigenspace is
+ * orthogonal to e0 (all maximisers have r0 = 0), e2 = (0,0,1,0) is projected
+ * instead (beta real and positive).  Returns 0 when the result is the identity. */
 static int mag_maximiser(double A[4][4], double r[4])
 {
     double B[4][4], V[4][4];
     memcpy(B, A, sizeof B);
     jacobi4(B, V);
-    int i1 = 0, i2 = -1;
+    double top = B[0][0];
     for (int i = 1; i < 4; ++i)
-        if (B[i][i] > B[i1][i1]) i1 = i;
-    for (int i = 0; i < 4; ++i)
-        if (i != i1 && (i2 < 0 || B[i][i] > B[i2][i2])) i2 = i;
-    /* project e0 onto the top eigenspace (two-fold by the U(1) symmetry) */
-    double scale = fabs(B[i1][i1]) > 1.0 ? fabs(B[i1][i1]) : 1.0;
-    int two = (B[i1][i1] - B[i2][i2]) <= 1e-10 * scale;
-    for (int c = 0; c < 4; ++c) r[c] = V[0][i1] * V[c][i1] + (two ? V[0][i2] * V[c][i2] : 0.0);
-    double n = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
-    if (!(n > 1e-12)) {
-        r[0] = 1.0;
-        r[1] = r[2] = r[3] = 0.0;
-        return 0;
+        if (B[i][i] > top) top = B[i][i];
+    double scale = fabs(top) > 1.0 ? fabs(top) : 1.0;
+    for (int target = 0; target < 2; ++target) {
+        const int e = target == 0 ? 0 : 2;
+        for (int c = 0; c < 4; ++c) r[c] = 0.0;
+        for (int i = 0; i < 4; ++i)
+            if (B[i][i] >= top - 1e-10 * scale)
+                for (int c = 0; c < 4; ++c) r[c] += V[e][i] * V[c][i];
+        double n = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+        if (n > 1e-12) {
+            for (int c = 0; c < 4; ++c) r[c] /= n;
+            return !(r[0] == 1.0 && r[1] == 0.0 && r[2] == 0.0 && r[3] == 0.0);
+        }
     }
-    for (int c = 0; c < 4; ++c) r[c] /= n;
-    return 1;
+    r[0] = 1.0;
+    r[1] = r[2] = r[3] = 0.0;
+    return 0;
 }
 
 static void mag_update_star(star *s, double omega)

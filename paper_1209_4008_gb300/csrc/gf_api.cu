@@ -139,6 +139,9 @@ static int fmt64(const gf_ctx *c)
     return c->storage64 == 12 ? F64_12 : F64_18;
 }
 static int fmt32(const gf_ctx *c) { return c->storage32 == 18 ? F32_18 : F32_12; }
+// the Coulomb flag and the overrelaxation mode of the sweep kernels for the context's gauge
+static int coulomb_of(const gf_ctx *c) { return c->gauge == GF_COULOMB ? 1 : 0; }
+static int or_mode(const gf_ctx *c) { return c->gauge == GF_MAG ? 3 : 0; }  // MODE_MAG : MODE_OR
 static bool twelve_real(int fmt) { return fmt == F64_12 || fmt == F32_12; }
 
 static size_t plane_bytes(const gf_ctx *c) { return (size_t)c->geom.plane * 16; }
@@ -276,6 +279,7 @@ static std::pair<int, int> launch_config(const gf_ctx *c, int fmt, int mode = 0)
         if (fmt != F64_18 && fmt != F64_12) cfg.first = GF_ACC;
     }
     if (cfg.first == GF_ACC_R168 && cfg.second > 128) cfg.second = 128;
+    if (c->gauge == GF_MAG && cfg.first <= 0) cfg.first = c->tps > 0 ? c->tps : 2;  // per-subgroup form only
     if (c->block) cfg.second = c->block;
     return cfg;
 }
@@ -302,7 +306,7 @@ static cudaError_t issue_sweeps(gf_ctx *ctx, int fmt, char *field, double omega,
     for (int k = 0; k < n; ++k)
         for (int p = 0; p < 2; ++p) {
             SweepArgs a = sweep_args(ctx, field, p, omega);
-            cudaError_t e = launch_sweep(fmt, a, cfg.first, ctx->gauge, 0, trackg, cfg.second, s);
+            cudaError_t e = launch_sweep(fmt, a, cfg.first, coulomb_of(ctx), or_mode(ctx), trackg, cfg.second, s);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
@@ -331,7 +335,7 @@ static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, boo
                 a.prob = ctx->sr_p;
                 a.key = make_uint2((uint32_t)ctx->sr_seed, (uint32_t)(ctx->sr_seed >> 32));
                 a.sweep = ctx->sr_sweep;
-                CK(launch_sweep(fmt, a, cfg.first, ctx->gauge, 2, false, cfg.second, ctx->stream));
+                CK(launch_sweep(fmt, a, cfg.first, coulomb_of(ctx), 2, false, cfg.second, ctx->stream));
             }
         if (kt) CK(cudaEventRecord(ctx->kev[1], ctx->stream));
         if (reunit) CK(launch_reunitarize(fmt, f, ctx->geom, ctx->stream));
@@ -462,7 +466,7 @@ static cudaError_t issue_sa_sweeps(gf_ctx *ctx, int fmt, char *field, int n, std
             a.T = 1.0;
             a.key = make_uint2(0x9e3779b9u, 0u);
             a.sweep = (uint32_t)k;
-            cudaError_t e = launch_sweep(fmt, a, cfg.first, ctx->gauge, 1, false, cfg.second, s);
+            cudaError_t e = launch_sweep(fmt, a, cfg.first, coulomb_of(ctx), 1, false, cfg.second, s);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
@@ -484,9 +488,11 @@ static int autotune_format(gf_ctx *ctx, int fmt, char *field, int *tps_out, int 
     const int blk_c[3] = { 64, 128, 256 };
     float best = 1e30f;
     std::pair<int, int> pick = default_config(fmt);
+    if (ctx->gauge == GF_MAG) pick.first = 2;
     for (int i = 0; i < ntps && e == cudaSuccess; ++i)
         for (int b = 0; b < 3 && e == cudaSuccess; ++b) {
             if (tps_c[i] == GF_ACC_R168 && blk_c[b] > 128) continue;
+            if (ctx->gauge == GF_MAG && tps_c[i] <= 0) continue;  // the MAG step uses the per-subgroup form
             std::pair<int, int> cfg{ tps_c[i], blk_c[b] };
             e = mode == 1 ? issue_sa_sweeps(ctx, fmt, scratch, 1, cfg, ctx->stream)
                           : issue_sweeps(ctx, fmt, scratch, 1.7, 1, false, cfg, ctx->stream);  // warm up
@@ -573,7 +579,7 @@ int gf_create(const int dims[4], int gauge, gf_ctx **out)
 {
     if (!dims || !out) return GF_EINVAL;
     *out = nullptr;
-    if (gauge != GF_LANDAU && gauge != GF_COULOMB) return GF_EINVAL;
+    if (gauge != GF_LANDAU && gauge != GF_COULOMB && gauge != GF_MAG) return GF_EINVAL;
     long V = 1;
     for (int mu = 0; mu < 4; ++mu) {
         if (dims[mu] < 2 || (dims[mu] & 1)) return GF_EINVAL;
@@ -662,12 +668,14 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
         ctx->block = iv;
     } else if (k == "fp64_arith") {
         if (iv != 0 && iv != 1) return fail(ctx, GF_EINVAL, "fp64_arith: 0 (native) or 1 (double-float)");
+        if (iv == 1 && ctx->gauge == GF_MAG) return fail(ctx, GF_EINVAL, "fp64_arith: not in the maximally Abelian gauge");
         if (ctx->resident == GF_FP64 && iv != ctx->fp64_arith) ctx->resident = -1;
         ctx->fp64_arith = iv;
     } else if (k == "variant") {
         if (!integral || iv < 0 || iv > 2) return fail(ctx, GF_EINVAL, "variant: 0, 1 or 2");
         ctx->variant = iv;
     } else if (k == "theta_per_timeslice") {
+        if (v != 0.0 && ctx->gauge == GF_MAG) return fail(ctx, GF_EINVAL, "theta_per_timeslice: not in the maximally Abelian gauge");
         ctx->slice_theta = v != 0.0;
     } else if (k == "or_variant") {
         if (!integral || iv < 0 || iv > 2) return fail(ctx, GF_EINVAL, "or_variant: 0, 1 or 2");
@@ -689,6 +697,7 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
         ctx->track = v != 0.0;
     } else if (k == "stochastic_p") {
         if (!(v >= 0.0 && v <= 1.0)) return fail(ctx, GF_EINVAL, "stochastic_p in [0, 1]");
+        if (v > 0.0 && ctx->gauge == GF_MAG) return fail(ctx, GF_EINVAL, "stochastic_p: not in the maximally Abelian gauge");
         ctx->sr_p = v;
     } else if (k == "sr_seed") {
         if (!(v >= 0.0) || v > 18446744073709551615.0) return fail(ctx, GF_EINVAL, "sr_seed");
@@ -773,7 +782,8 @@ int gf_or_half_sweep(gf_ctx *ctx, int parity, double omega)
     if (ctx->track && !ctx->gt) return fail(ctx, GF_ESTATE, "track is set but no gauge field (gf_gauge_reset)");
     std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt);
     SweepArgs a = sweep_args(ctx, resident_base(ctx), parity, omega);
-    CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 0, ctx->track != 0, cfg.second, ctx->stream));
+    CK(launch_sweep(ctx->resident_fmt, a, cfg.first, coulomb_of(ctx), or_mode(ctx), ctx->track != 0, cfg.second,
+                    ctx->stream));
     return GF_OK;
 }
 
@@ -787,9 +797,15 @@ int gf_or_sweeps(gf_ctx *ctx, double omega, int nsweeps)
     return run_chunk(ctx, ctx->resident_fmt, resident_base(ctx), omega, nsweeps, ctx->track != 0, false, false);
 }
 
+static int mag_unsupported(gf_ctx *ctx, const char *what)
+{
+    return fail(ctx, GF_EINVAL, std::string(what) + " is not available in the maximally Abelian gauge");
+}
+
 int gf_sa_half_sweep(gf_ctx *ctx, int parity, double T, uint64_t seed, uint32_t sweep)
 {
     if (!ctx) return GF_EINVAL;
+    if (ctx->gauge == GF_MAG) return mag_unsupported(ctx, "annealing");
     if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
     if ((parity & ~1) || !(T > 0.0) || !std::isfinite(T)) return fail(ctx, GF_EINVAL, "parity 0/1, T > 0");
     std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt, 1);
@@ -797,13 +813,14 @@ int gf_sa_half_sweep(gf_ctx *ctx, int parity, double T, uint64_t seed, uint32_t 
     a.T = T;
     a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     a.sweep = sweep;
-    CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 1, false, cfg.second, ctx->stream));
+    CK(launch_sweep(ctx->resident_fmt, a, cfg.first, coulomb_of(ctx), 1, false, cfg.second, ctx->stream));
     return GF_OK;
 }
 
 int gf_sr_half_sweep(gf_ctx *ctx, int parity, double p, uint64_t seed, uint32_t sweep)
 {
     if (!ctx) return GF_EINVAL;
+    if (ctx->gauge == GF_MAG) return mag_unsupported(ctx, "stochastic relaxation");
     if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
     if ((parity & ~1) || !(p >= 0.0 && p <= 1.0)) return fail(ctx, GF_EINVAL, "parity 0/1, p in [0, 1]");
     std::pair<int, int> cfg = launch_config(ctx, ctx->resident_fmt);
@@ -811,13 +828,14 @@ int gf_sr_half_sweep(gf_ctx *ctx, int parity, double p, uint64_t seed, uint32_t 
     a.prob = p;
     a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     a.sweep = sweep;
-    CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 2, false, cfg.second, ctx->stream));
+    CK(launch_sweep(ctx->resident_fmt, a, cfg.first, coulomb_of(ctx), 2, false, cfg.second, ctx->stream));
     return GF_OK;
 }
 
 int gf_measure_timeslices(gf_ctx *ctx, double *F_t, double *theta_t)
 {
     if (!ctx) return GF_EINVAL;
+    if (ctx->gauge == GF_MAG) return mag_unsupported(ctx, "per-timeslice measurement");
     if (ctx->resident < 0) return fail(ctx, GF_ESTATE, "no resident field");
     RET(ensure_common(ctx));
     const int Lt = ctx->geom.L[3];
@@ -1084,6 +1102,7 @@ int gf_apply_algebra(gf_ctx *ctx, const float *c, double scale)
 int gf_set_net(gf_ctx *ctx, gf_net *net)
 {
     if (!ctx) return GF_EINVAL;
+    if (ctx->gauge == GF_MAG && net) return mag_unsupported(ctx, "the learned warm start");
     ctx->net = net;
     return GF_OK;
 }
@@ -1091,6 +1110,7 @@ int gf_set_net(gf_ctx *ctx, gf_net *net)
 int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t seed)
 {
     if (!ctx) return GF_EINVAL;
+    if (ctx->gauge == GF_MAG) return mag_unsupported(ctx, "annealing");
     if (!(T0 > 0.0) || !(T1 > 0.0) || !std::isfinite(T0) || !std::isfinite(T1) || steps < 0)
         return fail(ctx, GF_EINVAL, "temperatures must be positive and finite, steps >= 0");
     ctx->stats.clear();
@@ -1116,7 +1136,7 @@ int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t 
             a.T = T;
             a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
             a.sweep = ctx->sa_sweep_offset + (uint32_t)k;
-            CK(launch_sweep(ctx->resident_fmt, a, cfg.first, ctx->gauge, 1, false, cfg.second, ctx->stream));
+            CK(launch_sweep(ctx->resident_fmt, a, cfg.first, coulomb_of(ctx), 1, false, cfg.second, ctx->stream));
         }
         if (reunit && (k % 4 == 3 || k == steps - 1))
             CK(launch_reunitarize(ctx->resident_fmt, ref(ctx, resident_base(ctx)), ctx->geom, ctx->stream));

@@ -443,6 +443,67 @@ __device__ __forceinline__ bool overrelax_step(const T k[4], T omega, int varian
 }
 
 // ---------------------------------------------------------------------------
+// Maximally Abelian gauge (Sec. 6): F = sum |U_ii|^2.  For subgroup (a,b) and
+// a held matrix X (forward link U, or U^dagger of a backward link), the
+// diagonal weight after X <- R X, R = [[alpha, beta], [-beta*, alpha*]], is
+// |alpha X_aa + beta X_ba|^2 + |alpha conj(X_bb) - beta conj(X_ab)|^2 =
+// z^dagger H z with z = (alpha, beta) and H the 2x2 Hermitian matrix summed
+// below.  Its maximiser over |z| = 1 is the top eigenvector of H, unique up to
+// the phase of the residual U(1); the phase is fixed by alpha >= 0 (the
+// maximiser closest to the identity).
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void add_mag_terms(const mat3<T> &x, int a, int b, T h[4])
+{
+    const cpx<T> xaa = x.e[a][a], xab = x.e[a][b], xba = x.e[b][a], xbb = x.e[b][b];
+    h[0] += xaa.re * xaa.re + xaa.im * xaa.im + xbb.re * xbb.re + xbb.im * xbb.im;  // h11
+    h[1] += xba.re * xba.re + xba.im * xba.im + xab.re * xab.re + xab.im * xab.im;  // h22
+    // h12 += conj(xaa) xba - xbb conj(xab)
+    h[2] += xaa.re * xba.re + xaa.im * xba.im - (xbb.re * xab.re + xbb.im * xab.im);
+    h[3] += xaa.re * xba.im - xaa.im * xba.re - (xbb.im * xab.re - xbb.re * xab.im);
+}
+
+// quaternion r of the maximiser (r0 = |alpha|, r3 = 0, r2 + i r1 = beta);
+// false (no change) when H is a multiple of the identity
+template <class T>
+__device__ __forceinline__ bool mag_element(const T h[4], T r[4])
+{
+    const T d = T(0.5) * (h[0] - h[1]);
+    const T n12 = h[2] * h[2] + h[3] * h[3];
+    if (n12 == T(0) && d >= T(0)) {  // already optimal (or degenerate): identity
+        return false;
+    }
+    const T rt = sqrt(d * d + n12);
+    // top eigenvector: (lambda - h22, conj(h12)) when h11 >= h22, else (h12, lambda - h11)
+    T v1re, v1im, v2re, v2im;
+    if (d >= T(0)) {
+        v1re = d + rt;
+        v1im = T(0);
+        v2re = h[2];
+        v2im = -h[3];
+    } else {
+        v1re = h[2];
+        v1im = h[3];
+        v2re = rt - d;
+        v2im = T(0);
+    }
+    const T n1 = sqrt(v1re * v1re + v1im * v1im);
+    const T nv = sqrt(v1re * v1re + v1im * v1im + v2re * v2re + v2im * v2im);
+    if (n1 > T(0)) {  // alpha = |v1|, beta = v2 conj(v1) / |v1|
+        r[0] = n1 / nv;
+        r[3] = T(0);
+        r[2] = (v2re * v1re + v2im * v1im) / (n1 * nv);
+        r[1] = (v2im * v1re - v2re * v1im) / (n1 * nv);
+    } else {  // no maximiser near the identity: alpha = 0, beta = |v2|
+        r[0] = T(0);
+        r[3] = T(0);
+        r[2] = T(1);
+        r[1] = T(0);
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)

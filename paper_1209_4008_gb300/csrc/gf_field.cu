@@ -4,6 +4,7 @@
 // gauge transformation accumulated during the FP32 phase, and the
 // deterministic FP64 reductions of F (eq. F_g), theta (eq. theta) and the
 // plaquette.
+#include "gf.h"
 #include "gf_fieldops.cuh"
 
 namespace gf {
@@ -153,6 +154,18 @@ __global__ void k_slices_summary(const double *__restrict__ slices, int Lt, doub
     out[1] = m;
 }
 
+template <int FMT>
+__global__ void __launch_bounds__(kReduceBlock) k_measure_mag(FieldRef f, Geom g, double *partials)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double fsum = 0.0, tsum = 0.0;
+    if (t < 2 * g.Vh) {
+        int p = t >= g.Vh ? 1 : 0;
+        measure_site_mag<FMT>(f, g, p, t - p * g.Vh, fsum, tsum);
+    }
+    block_sum2(fsum, tsum, partials + 2 * blockIdx.x);
+}
+
 template <bool COULOMB>
 __global__ void __launch_bounds__(kReduceBlock) k_measure_aos(const double *__restrict__ aos, Geom g,
                                                               double *partials)
@@ -287,6 +300,17 @@ cudaError_t launch_measure(int fmt, FieldRef f, const Geom &g, int coulomb, doub
                            cudaStream_t s)
 {
     int n = measure_blocks(g);
+    if (coulomb == GF_MAG) {  // maximally Abelian gauge: F_MAG and theta_MAG
+        if (fmt == DF64_18) return cudaErrorInvalidValue;
+#define GF_CALL(F) k_measure_mag<F><<<n, kReduceBlock, 0, s>>>(f, g, partials)
+        GF_FMT_SWITCH(fmt, GF_CALL)
+#undef GF_CALL
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        double V = 2.0 * g.Vh;
+        k_finalize<<<1, 256, 0, s>>>(partials, n, 1.0 / (3.0 * 4.0 * V), 1.0 / (3.0 * V), out);
+        return cudaGetLastError();
+    }
 #define GF_CALL(F)                                                               \
     if (coulomb) k_measure<F, true><<<n, kReduceBlock, 0, s>>>(f, g, partials);  \
     else k_measure<F, false><<<n, kReduceBlock, 0, s>>>(f, g, partials)
@@ -322,10 +346,50 @@ cudaError_t launch_measure_slices(int fmt, FieldRef f, const Geom &g, int coulom
     return cudaGetLastError();
 }
 
+// maximally Abelian gauge on a canonical field (see measure_site_mag)
+__global__ void __launch_bounds__(kReduceBlock) k_measure_aos_mag(const double *__restrict__ aos, Geom g,
+                                                                  double *partials)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double fsum = 0.0, tsum = 0.0;
+    if (i < 2 * g.Vh) {
+        int c[4];
+        coords_of_lex(g, i, c);
+        double hs[3][4] = { { 0 } };
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            mat3<double> u = load_aos(aos, 4L * i + mu);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) fsum += u.e[a][a].re * u.e[a][a].re + u.e[a][a].im * u.e[a][a].im;
+            int st = lex_stride(g, mu);
+            int j = coord_of(c, mu) == 0 ? i + (extent_of(g, mu) - 1) * st : i - st;
+            const mat3<double> x = dagger(load_aos(aos, 4L * j + mu));
+#pragma unroll
+            for (int sg = 0; sg < 3; ++sg) {
+                int a, b;
+                subgroup_rows(sg, a, b);
+                add_mag_terms(u, a, b, hs[sg]);
+                add_mag_terms(x, a, b, hs[sg]);
+            }
+        }
+#pragma unroll
+        for (int sg = 0; sg < 3; ++sg) tsum += hs[sg][2] * hs[sg][2] + hs[sg][3] * hs[sg][3];
+    }
+    block_sum2(fsum, tsum, partials + 2 * blockIdx.x);
+}
+
 cudaError_t launch_measure_aos(const double *aos, const Geom &g, int coulomb, double *partials, double *out,
                                cudaStream_t s)
 {
     int n = aos_blocks(g);
+    if (coulomb == GF_MAG) {
+        k_measure_aos_mag<<<n, kReduceBlock, 0, s>>>(aos, g, partials);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        double V = 2.0 * g.Vh;
+        k_finalize<<<1, 256, 0, s>>>(partials, n, 1.0 / (3.0 * 4.0 * V), 1.0 / (3.0 * V), out);
+        return cudaGetLastError();
+    }
     if (coulomb) k_measure_aos<true><<<n, kReduceBlock, 0, s>>>(aos, g, partials);
     else k_measure_aos<false><<<n, kReduceBlock, 0, s>>>(aos, g, partials);
     cudaError_t e = cudaGetLastError();

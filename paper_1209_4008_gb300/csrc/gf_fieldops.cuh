@@ -239,4 +239,46 @@ __device__ __forceinline__ void measure_site(const FieldRef &f, const Geom &g, i
     tsum = traceless_norm2_p<T>(dre, dim);
 }
 
+// Maximally Abelian gauge: F part sum_mu sum_i |U_mu(x)_ii|^2, theta part
+// sum over the three subgroups of |h12|^2, h12 the off-diagonal element of the
+// local matrix H of the subgroup step at the identity (the squared gradient of
+// the local functional along the directions that are not the residual U(1))
+template <int FMT>
+__device__ __forceinline__ void measure_site_mag(const FieldRef &f, const Geom &g, int p, int h, double &fsum,
+                                                 double &tsum)
+{
+    typedef Store<FMT> S;
+    typedef typename S::T T;
+    int c[4];
+    site_coords(g, p, h, c);
+    T hs[3][4] = { { T(0) } };
+    T fs = T(0);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        mat3<T> u;
+        S::load(f, (p * 4 + mu) * S::NCHUNK, h, u);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) fs += u.e[i][i].re * u.e[i][i].re + u.e[i][i].im * u.e[i][i].im;
+#pragma unroll
+        for (int sg = 0; sg < 3; ++sg) {
+            int a, b;
+            subgroup_rows(sg, a, b);
+            add_mag_terms(u, a, b, hs[sg]);
+        }
+        S::load(f, ((p ^ 1) * 4 + mu) * S::NCHUNK, back_half(g, c, mu), u);
+        const mat3<T> x = dagger(u);
+#pragma unroll
+        for (int sg = 0; sg < 3; ++sg) {
+            int a, b;
+            subgroup_rows(sg, a, b);
+            add_mag_terms(x, a, b, hs[sg]);
+        }
+    }
+    fsum = (double)fs;
+    double t = 0.0;
+#pragma unroll
+    for (int sg = 0; sg < 3; ++sg) t += (double)hs[sg][2] * (double)hs[sg][2] + (double)hs[sg][3] * (double)hs[sg][3];
+    tsum = t;
+}
+
 }  // namespace gf

@@ -18,7 +18,9 @@
 
 namespace gf {
 
-enum Mode { MODE_OR = 0, MODE_SA = 1, MODE_SR = 2 };
+// MODE_MAG: overrelaxation towards the maximally Abelian gauge (Sec. 6), the
+// subgroup element from the 2x2 matrix H of add_mag_terms (per-subgroup form only)
+enum Mode { MODE_OR = 0, MODE_SA = 1, MODE_SR = 2, MODE_MAG = 3 };
 
 // ---------------------------------------------------------------------------
 // accumulate form (one thread per site)
@@ -525,12 +527,13 @@ __device__ __forceinline__ void sweep_site(const SweepArgs &a, int h, int j, uns
     for (int sg = 0; sg < 3; ++sg) {
         int ra, rb;
         subgroup_rows(sg, ra, rb);
-        T k[4] = { T(0), T(0), T(0), T(0) };
+        T k[4] = { T(0), T(0), T(0), T(0) };  // quaternion of K, or H of the MAG step
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
             const int mu = (TPS == 8) ? (j & 3) : ((l % HALF) * TPS + j);
             if (COULOMB && mu == 3) continue;  // Coulomb: K from spatial links only
-            add_block_quaternion(x[l], ra, rb, k);
+            if (MODE == MODE_MAG) add_mag_terms(x[l], ra, rb, k);
+            else add_block_quaternion(x[l], ra, rb, k);
         }
 #pragma unroll
         for (int o = 1; o < TPS; o <<= 1)
@@ -539,7 +542,10 @@ __device__ __forceinline__ void sweep_site(const SweepArgs &a, int h, int j, uns
 
         T r[4];
         bool ok;
-        if (MODE == MODE_OR) {
+        if (MODE == MODE_MAG) {
+            T rm[4];
+            ok = mag_element(k, rm) && overrelax_step(rm, (T)a.omega, a.orv, r);
+        } else if (MODE == MODE_OR) {
             ok = overrelax_step(k, (T)a.omega, a.orv, r);
         } else if (MODE == MODE_SR) {
             ok = sr_quat(k, a.prob, site, a.sweep, sg, a.key, r);
@@ -614,10 +620,14 @@ static cudaError_t launch_k_sweep(const SweepArgs &a, int block, cudaStream_t s)
     long threads = (long)a.g.Vh * (TPS <= 0 ? 1 : TPS);
     int grid = (int)((threads + block - 1) / block);
     if (TPS == GF_ACC_R168 && block > 128) return cudaErrorInvalidValue;
-    if (TPS == 0) k_sweep_acc<FMT, COULOMB, MODE, TRACKG><<<grid, block, 0, s>>>(a);
-    else if (TPS < 0) k_sweep_acc_rc<FMT, COULOMB, MODE, TRACKG, (TPS < 0 ? -TPS : 1)><<<grid, block, 0, s>>>(a);
-    else k_sweep<FMT, (TPS <= 0 ? 1 : TPS), COULOMB, MODE, TRACKG><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    if constexpr (MODE == MODE_MAG && TPS <= 0) {
+        return cudaErrorInvalidValue;  // the MAG step needs the links: per-subgroup form only
+    } else {
+        if (TPS == 0) k_sweep_acc<FMT, COULOMB, MODE, TRACKG><<<grid, block, 0, s>>>(a);
+        else if (TPS < 0) k_sweep_acc_rc<FMT, COULOMB, MODE, TRACKG, (TPS < 0 ? -TPS : 1)><<<grid, block, 0, s>>>(a);
+        else k_sweep<FMT, (TPS <= 0 ? 1 : TPS), COULOMB, MODE, TRACKG><<<grid, block, 0, s>>>(a);
+        return cudaGetLastError();
+    }
 }
 
 template <int FMT, int TPS, bool TRACKG>
@@ -626,6 +636,14 @@ static cudaError_t dispatch_gauge_mode(const SweepArgs &a, int coulomb, int mode
     if (mode == MODE_OR) {
         return coulomb ? launch_k_sweep<FMT, TPS, true, MODE_OR, TRACKG>(a, block, s)
                        : launch_k_sweep<FMT, TPS, false, MODE_OR, TRACKG>(a, block, s);
+    }
+    if (mode == MODE_MAG) {
+        if constexpr (FMT == DF64_18) {
+            return cudaErrorInvalidValue;
+        } else {
+            if (coulomb) return cudaErrorInvalidValue;
+            return launch_k_sweep<FMT, TPS, false, MODE_MAG, TRACKG>(a, block, s);
+        }
     }
     if (TRACKG) return cudaErrorInvalidValue;  // annealing and stochastic relaxation never track g
     if (mode == MODE_SR)

@@ -269,6 +269,7 @@ static cudaError_t launch_df(const SweepArgs &a, int coulomb, int mode, int bloc
 cudaError_t launch_sweep_df64(const SweepArgs &a, int tps, int coulomb, int mode, bool trackg, int block,
                               cudaStream_t s)
 {
+    if (mode == MODE_MAG) return cudaErrorInvalidValue;  // maximally Abelian gauge: native storage only
     if (tps == 0) return trackg ? launch_df<true>(a, coulomb, mode, block, s) : launch_df<false>(a, coulomb, mode, block, s);
     switch (tps) {
     case 1: return trackg ? dispatch_gauge_mode<DF64_18, 1, true>(a, coulomb, mode, block, s)

@@ -18,7 +18,7 @@ import threading
 from . import build as _build
 
 GF_OK, GF_EINVAL, GF_ECUDA, GF_ETIMEOUT, GF_ENOTCONVERGED, GF_ENOMEM, GF_EREJECT, GF_ESTATE = range(8)
-GF_LANDAU, GF_COULOMB = 0, 1
+GF_LANDAU, GF_COULOMB, GF_MAG = 0, 1, 2
 GF_FP64, GF_MIXED, GF_FP32 = 0, 1, 2
 
 _lock = threading.Lock()

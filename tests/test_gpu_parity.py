@@ -622,3 +622,96 @@ def test_anneal_autotuned_heatbath_config():
     gf.gf_anneal(b, db, 1.2, 0.1, 6, 5)
     assert max_rel(host(da), host(db)) < 1e-11
     assert gf.gf_get_stat(a, "sweeps") == 6
+
+
+# ---------------------------------------------------------------------------
+# maximally Abelian gauge (Sec. 6): the same subgroup relaxation on both sides
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 6, 10)])
+@pytest.mark.parametrize("tps", [1, 2, 4, 8])
+@pytest.mark.parametrize("storage", [18, 12])
+def test_mag_half_sweep_parity(dims, tps, storage):
+    U = cpu_field(dims, seed=61, gseed=62)
+    c = ctx_for(dims, gf.GF_MAG, threads_per_site=tps, storage64=storage)
+    gf.gf_upload(c, dev(U), gf.GF_FP64)
+    W = U.copy()
+    for p, om in ((0, 1.0), (1, 1.7), (0, 1.7)):
+        gf.gf_or_half_sweep(c, p, om)
+        oracle.mag_half_sweep(W, p, om)
+        d = torch.empty_like(dev(U))
+        gf.gf_download(c, d)
+        assert max_rel(host(d), W) < 1e-12
+
+
+def test_mag_fp32_half_sweep():
+    dims = (6, 4, 6, 10)
+    U = cpu_field(dims, seed=63, gseed=64)
+    c = ctx_for(dims, gf.GF_MAG, threads_per_site=2)
+    gf.gf_upload(c, dev(U), gf.GF_FP32)
+    W = U.copy()
+    gf.gf_or_half_sweep(c, 0, 1.7)
+    oracle.mag_half_sweep(W, 0, 1.7)
+    d = torch.empty_like(dev(U))
+    gf.gf_download(c, d)
+    assert np.abs(host(d) - W).max() < 5e-6
+
+
+@pytest.mark.parametrize("prec", [gf.GF_FP64, gf.GF_FP32])
+def test_mag_measurement_matches_oracle(prec):
+    dims = (6, 4, 6, 10)
+    U = cpu_field(dims, seed=65, gseed=66)
+    c = ctx_for(dims, gf.GF_MAG)
+    F_aos, th_aos = gf.gf_functional(c, dev(U)), gf.gf_theta(c, dev(U))
+    assert F_aos == pytest.approx(oracle.mag_functional(U), rel=1e-13)
+    assert th_aos == pytest.approx(oracle.mag_theta(U), rel=1e-12)
+    gf.gf_upload(c, dev(U), prec)
+    F, th = gf.gf_measure(c)
+    tol = 1e-12 if prec == gf.GF_FP64 else 1e-5
+    assert F == pytest.approx(oracle.mag_functional(U), rel=tol)
+    assert th == pytest.approx(oracle.mag_theta(U), rel=tol)
+
+
+def test_mag_overrelax_matches_oracle_sweep_count():
+    dims = (4, 4, 4, 6)
+    U = cpu_field(dims, seed=67, gseed=68)
+    c = ctx_for(dims, gf.GF_MAG, check_every=10)
+    d = dev(U)
+    conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-10, 4000)
+    assert conv and th < 1e-10
+    W = U.copy()
+    n = 0
+    while not oracle.mag_theta(W) < 1e-10 and n < 4000:
+        oracle.mag_sweeps(W, 1.7, 10)
+        n += 10
+    assert n == it
+    assert F == pytest.approx(oracle.mag_functional(W), abs=1e-12)
+    assert gf.gf_plaquette(c, d) == pytest.approx(oracle.plaquette(U), abs=1e-13)
+
+
+def test_mag_mixed_precision_is_exact_gauge_transform():
+    dims = (6, 4, 6, 10)
+    U = cpu_field(dims, seed=69, gseed=70)
+    res = {}
+    for prec in (gf.GF_FP64, gf.GF_MIXED):
+        c = ctx_for(dims, gf.GF_MAG, check_every=10, precision=prec, theta_switch=1e-5)
+        d = dev(U)
+        res[prec] = gf.gf_overrelax(c, d, 1.7, 1e-11, 10000)
+        assert res[prec][0]
+        assert gf.gf_plaquette(c, d) == pytest.approx(oracle.plaquette(U), abs=1e-13)
+    assert abs(res[gf.GF_FP64][2] - res[gf.GF_MIXED][2]) < 1e-6  # same local maximum region
+
+
+def test_mag_unsupported_paths_raise():
+    dims = (4, 4, 4, 4)
+    U = cpu_field(dims)
+    c = ctx_for(dims, gf.GF_MAG)
+    with pytest.raises(gf.GFError):
+        gf.gf_anneal(c, dev(U), 1.0, 0.1, 2, 1)
+    with pytest.raises(gf.GFError):
+        gf.gf_set_option(c, "fp64_arith", 1)
+    with pytest.raises(gf.GFError):
+        gf.gf_set_option(c, "stochastic_p", 0.5)
+    gf.gf_upload(c, dev(U), gf.GF_FP64)
+    with pytest.raises(gf.GFError):
+        gf.gf_measure_timeslices(c)
+    gf.gf_or_half_sweep(c, 0, 1.5)  # still usable afterwards
