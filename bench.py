@@ -706,6 +706,40 @@ def net_kernels(args):
                       "bf16_peak_tflops": bf16, **res}), flush=True)
 
 
+def mag(args):
+    """Maximally Abelian gauge on the 32^4 field (seeds 3/4, plaquette 0.60):
+    overrelaxation omega 1.7 to theta_MAG < 1e-10 with the FP64 and the mixed
+    policy (FP32 to 1e-5), per-subgroup site update (autotuned threads per
+    site).  Prints one JSON object."""
+    from paper_1209_4008_gb300 import gf, synth
+    pristine = synth.make_field(DIMS, PLAQ, *SEEDS, device="cuda")
+    V = int(np.prod(DIMS))
+    out = {"workload": "maximally Abelian gauge 32^4, omega 1.7, theta_MAG < 1e-10"}
+    for name, prec in (("fp64", gf.GF_FP64), ("mixed", gf.GF_MIXED)):
+        c = gf.gf_create(DIMS, gf.GF_MAG)
+        gf.gf_set_option(c, "precision", prec)
+        gf.gf_set_option(c, "theta_switch", 1e-5)
+        gf.gf_set_option(c, "check_every", CHECK_EVERY)
+        gf.gf_set_option(c, "autotune", 1)
+        gf.gf_set_option(c, "kernel_timing", 1)
+        gf.gf_set_stream(c, torch.cuda.current_stream())
+        work = pristine.clone()
+        gf.gf_overrelax(c, work, OMEGA, 1e-10, MAX_ITER)  # warm-up: autotune, graphs
+        work.copy_(pristine)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        conv, it, F, th = gf.gf_overrelax(c, work, OMEGA, 1e-10, MAX_ITER)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        k64 = gf.gf_get_stat(c, "ms_sweep_kernels_fp64") / max(1.0, gf.gf_get_stat(c, "sweep_launches_fp64"))
+        out[name] = {"s": dt, "sweeps": it, "F": F, "theta": th, "converged": conv,
+                     "su_per_s": V * it / dt, "ms_fp64_half_sweep": k64,
+                     "threads_per_site": gf.gf_get_stat(c, "threads_per_site"),
+                     "dplaq": abs(gf.gf_plaquette(c, work) - gf.gf_plaquette(c, pristine))}
+    out["dF"] = abs(out["fp64"]["F"] - out["mixed"]["F"])
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -737,6 +771,7 @@ def main():
                     help="--learned: skip the pairs and training, evaluate these stored parameters")
     ap.add_argument("--coulomb", action="store_true", help="the 48^3x96 Coulomb workload with annealing")
     ap.add_argument("--net", action="store_true", help="time the warm-start network's kernels")
+    ap.add_argument("--mag", action="store_true", help="the maximally Abelian gauge on the 32^4 field")
     ap.add_argument("--seeds", type=int, default=8)
     ap.add_argument("--sa-sweeps", type=int, default=3000)
     args = ap.parse_args()
@@ -755,6 +790,10 @@ def main():
     if args.net:
         torch.cuda.set_device(0)
         net_kernels(args)
+        return
+    if args.mag:
+        torch.cuda.set_device(0)
+        mag(args)
         return
     if args.kernel:
         torch.cuda.set_device(0)
