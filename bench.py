@@ -7,7 +7,8 @@ theta < 1e-14 (omega = 1.7, theta checked every 25 sweeps).  The field is
 restored from a resident pristine copy at the start of each step.
 
 value = site updates per second over the timed steps (V x sweeps / time).
-Extra keys: time to theta for mixed vs all-FP64, |F_mixed - F_FP64|, sweep
+Extra keys: time to theta for mixed, mixed with the learned warm start (stored
+parameters), mixed with a double-float finish and all-FP64, |F - F_FP64|, sweep
 throughput and achieved HBM bandwidth per storage format, the roofline of the
 dominant kernel, the CPU oracle baseline, end-to-end throughput with host
 buffers.
@@ -323,6 +324,27 @@ def gpu_arm(args, rank, world, local):
     torch.cuda.synchronize()
     t_df = time.perf_counter() - t0
 
+    # the mixed policy with the learned warm start (stored parameters), once
+    learned_row = None
+    if os.path.exists(WEIGHTS):
+        net = gf.gf_net_create(DIMS)
+        gf.gf_net_set_stream(net, torch.cuda.current_stream())
+        gf.gf_net_set_params(net, np.load(WEIGHTS).astype(np.float32))
+        ctxl = make_ctx(gf, gf.GF_MIXED)
+        gf.gf_set_net(ctxl, net)
+        work.copy_(pristine)
+        gf.gf_overrelax(ctxl, work, OMEGA, THETA_TARGET, MAX_ITER)  # warm-up
+        work.copy_(pristine)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        convl, itl, Fl, thl = gf.gf_overrelax(ctxl, work, OMEGA, THETA_TARGET, MAX_ITER)
+        torch.cuda.synchronize()
+        learned_row = {"learned_s": time.perf_counter() - t0, "sweeps_learned": itl,
+                       "sweeps_fp64_phase_learned": gf.gf_get_stat(ctxl, "sweeps_fp64"),
+                       "F_learned": Fl, "dF_learned": abs(Fl - F64), "theta_learned": thl,
+                       "ms_network": gf.gf_get_stat(ctxl, "ms_learned"),
+                       "weights": os.path.relpath(WEIGHTS, ROOT)}
+
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     host = torch.empty(pristine.shape, dtype=pristine.dtype, pin_memory=True)
     e2e_ms = 0.0
@@ -382,7 +404,8 @@ def gpu_arm(args, rank, world, local):
                           "theta_mixed": th_mixed, "theta_fp64": th64,
                           "mixed_df64_s": t_df, "sweeps_mixed_df64": itdf, "F_mixed_df64": Fdf,
                           "dF_mixed_df64": abs(Fdf - F64), "theta_mixed_df64": thdf,
-                          "phase_ms": {"fp32": ms32 / args.steps, "fp64": ms64 / args.steps}},
+                          "phase_ms": {"fp32": ms32 / args.steps, "fp64": ms64 / args.steps},
+                          **(learned_row or {})},
         "sweep_throughput": thr,
         "roofline": roof,
         "cpu_baseline": cpu,
