@@ -653,7 +653,9 @@ def test_mag_fp32_half_sweep():
     oracle.mag_half_sweep(W, 0, 1.7)
     d = torch.empty_like(dev(U))
     gf.gf_download(c, d)
-    assert np.abs(host(d) - W).max() < 5e-6
+    # the MAG step is an eigenvector of H: FP32 rounding of H (~1e-6 of |H|)
+    # is amplified by |H| / (eigenvalue gap), up to ~10 on random fields
+    assert np.abs(host(d) - W).max() < 2e-5
 
 
 @pytest.mark.parametrize("prec", [gf.GF_FP64, gf.GF_FP32])
