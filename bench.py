@@ -360,6 +360,11 @@ def gpu_arm(args, rank, world, local):
     e2e_ms = max_over_ranks(e2e_ms, world)
     e2e_value = world * V * e2e_sweeps / (e2e_ms / 1e3)
 
+    # DRAM bytes (read + write) per launch of the FP64 phase's half-sweep from one ncu capture
+    # (profiles/or_half_sweep_fp64_18_32x32x32x32.md): valid for the configuration captured there,
+    # the accumulate form with 128 registers per thread near convergence; null for any other
+    acc = gf.gf_get_stat(ctx, "accumulate_form") == 1 and gf.gf_get_stat(ctx, "acc_registers") == 128
+    traffic64 = 1554.9e6 if acc else None
     pk = peaks()
     hbm = pk.get("hbm_gbs")
     # dominant kernel of the step: the half-sweep of the phase whose kernels took longer; its
@@ -378,7 +383,9 @@ def gpu_arm(args, rank, world, local):
         flops = Vh * 2253 / t_launch / 1e12
         roof.update({"bound": "alu", "achieved": flops, "peak": 1.25, "unit": "TFLOP/s",
                      "frac": flops / 1.25, "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)",
-                     "hbm_gbs": gbs, "hbm_frac": gbs / hbm if hbm else None})
+                     "hbm_gbs": gbs, "hbm_frac": gbs / hbm if hbm else None,
+                     "traffic": traffic64, "traffic_unit": "bytes per launch (ncu dram read + write)",
+                     "algorithmic_bytes": Vh * thr[dom]["bytes_per_site_update"]})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
