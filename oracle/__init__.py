@@ -71,6 +71,10 @@ def _declare(lib: C.CDLL) -> C.CDLL:
     d.oracle_mag_theta.restype = C.c_double
     d.oracle_mag_local_matrix.argtypes = [_dp, _ip, C.c_long, C.c_int, _dp]
     d.oracle_mag_maximiser.argtypes = [_dp, _dp]
+    d.oracle_wilson_update.argtypes = [_dp, _ip, C.c_int, C.c_int, C.c_double, C.c_int, C.c_uint64,
+                                       C.c_uint32, C.c_int]
+    d.oracle_wilson_update.restype = C.c_long
+    d.oracle_staple.argtypes = [_dp, _ip, C.c_long, C.c_int, _dp]
     d.oracle_site_quaternion.argtypes = [_dp, _ip, C.c_long, C.c_int, C.c_int, _dp]
     d.oracle_site_rotate.argtypes = [_dp, _ip, C.c_long, C.c_int, _dp]
     for f in ("oracle_functional", "oracle_theta", "oracle_theta_from_M"):
@@ -490,3 +494,33 @@ def mag_maximiser(A) -> np.ndarray:
     r = np.zeros(4)
     lib().oracle_mag_maximiser(_d(A), _d(r))
     return r
+
+
+# ---------------------------------------------------------------------------
+# Wilson-action gauge-field generation (thermalised inputs, Sec. 5)
+# ---------------------------------------------------------------------------
+def wilson_update(U, mu: int, parity: int, beta: float, mode: int, seed: int, sweep: int,
+                  cap: int = 64) -> int:
+    """mode 0 heatbath, 1 overrelaxation, for the links U_mu(x), x of one parity;
+    returns the number of heatbath draws that hit the rejection cap."""
+    U = _field(U)
+    f = lib().oracle_wilson_update(_d(U), _i(dims_of(U)), mu, parity, beta, mode, seed, sweep, cap)
+    if f < 0:
+        raise ValueError("oracle wilson update rejected its arguments")
+    return f
+
+
+def wilson_sweep(U, beta: float, mode: int, seed: int, sweep: int) -> int:
+    """All links once: directions 0..3, parities 0, 1."""
+    f = 0
+    for mu in range(4):
+        for p in (0, 1):
+            f += wilson_update(U, mu, p, beta, mode, seed, sweep)
+    return f
+
+
+def staple(U, site: int, mu: int) -> np.ndarray:
+    U = _field(U)
+    out = np.zeros((3, 3), dtype=np.complex128)
+    _check(lib().oracle_staple(_d(U), _i(dims_of(U)), site, mu, _d(out)), "staple")
+    return out

@@ -807,10 +807,10 @@ static double u01(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0);
  * sg * 256 + a, 1).  Returns 1 on success, 0 after cap rejections.
  */
 static int heatbath_s0(double alpha, uint32_t site, uint32_t sweep, int sg, int cap,
-                       const uint32_t key[2], double *s0_out)
+                       const uint32_t key[2], uint32_t tag, double *s0_out)
 {
     for (int a = 0; a < cap && a < (int)SA_DIRECTION_DRAW; ++a) {
-        uint32_t ctr[4] = { site, sweep, (uint32_t)sg * 256u + (uint32_t)a, SA_TAG };
+        uint32_t ctr[4] = { site, sweep, (uint32_t)sg * 256u + (uint32_t)a, tag };
         uint32_t w[4];
         oracle_philox4x32_10(ctr, key, w);
         if (alpha < SA_ALPHA_SWITCH) {
@@ -854,14 +854,14 @@ static void quat_mul(const double a[4], const double b[4], double q[4])
  * imaginary part of s is uniform on the sphere, from Philox counter
  * (site, sweep, sg * 256 + 255, 1).
  */
-static int heatbath_quaternion(const double k[4], double T, uint32_t site, uint32_t sweep, int sg,
-                               int cap, const uint32_t key[2], double r[4])
+static int heatbath_quaternion_tag(const double k[4], double T, uint32_t site, uint32_t sweep, int sg,
+                                   int cap, const uint32_t key[2], uint32_t tag, double r[4])
 {
     double kn = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
     if (kn == 0.0) return 2; /* nothing to do */
     double s0;
-    if (!heatbath_s0(kn / T, site, sweep, sg, cap, key, &s0)) return 0;
-    uint32_t ctr[4] = { site, sweep, (uint32_t)sg * 256u + SA_DIRECTION_DRAW, SA_TAG };
+    if (!heatbath_s0(kn / T, site, sweep, sg, cap, key, tag, &s0)) return 0;
+    uint32_t ctr[4] = { site, sweep, (uint32_t)sg * 256u + SA_DIRECTION_DRAW, tag };
     uint32_t w[4];
     oracle_philox4x32_10(ctr, key, w);
     double ct = 2.0 * u01(w[0]) - 1.0;
@@ -872,6 +872,12 @@ static int heatbath_quaternion(const double k[4], double T, uint32_t site, uint3
     double kh[4] = { k[0] / kn, k[1] / kn, k[2] / kn, k[3] / kn };
     quat_mul(s, kh, r);
     return 1;
+}
+
+static int heatbath_quaternion(const double k[4], double T, uint32_t site, uint32_t sweep, int sg,
+                               int cap, const uint32_t key[2], double r[4])
+{
+    return heatbath_quaternion_tag(k, T, site, sweep, sg, cap, key, SA_TAG, r);
 }
 
 int oracle_heatbath_quaternion(const double k[4], double T, uint32_t site, uint32_t sweep, int sg,
@@ -1368,4 +1374,116 @@ int oracle_mag_maximiser(const double *A16, double *r)
     double A[4][4];
     memcpy(A, A16, sizeof A);
     return mag_maximiser(A, r);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gauge-field generation with the Wilson action (to give the gauge fixing  */
+/* thermalised inputs like the paper's ensembles, Sec. 5)                   */
+/* ------------------------------------------------------------------------ */
+/*
+ * S = beta sum_P (1 - Re tr U_P / 3).  The part of S that depends on the link
+ * U = U_mu(x) is -(beta/3) Re tr(U A) with the staple sum
+ *   A = sum_{nu != mu} [ U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+ *                       + U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu) ].
+ * Cabibbo-Marinari: for each SU(2) subgroup the link is multiplied from the
+ * left by R, and Re tr(R U A) = r.k with k the quaternion of the subgroup
+ * block of W = U A; the heatbath draws r with weight exp((beta/3) r.k),
+ * i.e. the SU(2) draw of the annealing at T = 3/beta, with Philox counter
+ * (4 site + mu, sweep, 256 subgroup + draw, 3).  The overrelaxation step is
+ * the microcanonical r = (k/|k|)^2, which leaves Re tr(U A) unchanged.
+ * Links U_mu(x) of one direction and one parity share no staple, so they are
+ * updated together.
+ */
+#define WILSON_TAG 3u
+
+static mat3 staple_sum(const double *U, const lattice *g, long i, int mu)
+{
+    mat3 A;
+    memset(&A, 0, sizeof A);
+    long xp = site_shift(g, i, mu, +1);
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        long xn = site_shift(g, i, nu, +1), xm = site_shift(g, i, nu, -1);
+        long xpm = site_shift(g, xp, nu, -1);
+        /* upper staple U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ */
+        mat3 a = mat_load(link_cptr(U, xp, nu));
+        mat3 b = mat_load(link_cptr(U, xn, mu));
+        mat3 c = mat_load(link_cptr(U, i, nu));
+        mat3 bd = mat_dagger(&b), cd = mat_dagger(&c);
+        mat3 t = mat_mul(&a, &bd);
+        mat3 up = mat_mul(&t, &cd);
+        /* lower staple U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu) */
+        mat3 d = mat_load(link_cptr(U, xpm, nu));
+        mat3 e = mat_load(link_cptr(U, xm, mu));
+        mat3 f = mat_load(link_cptr(U, xm, nu));
+        mat3 dd = mat_dagger(&d), ed = mat_dagger(&e);
+        mat3 t2 = mat_mul(&dd, &ed);
+        mat3 lo = mat_mul(&t2, &f);
+        for (int r = 0; r < 3; ++r)
+            for (int c2 = 0; c2 < 3; ++c2) A.m[r][c2] = c_add(A.m[r][c2], c_add(up.m[r][c2], lo.m[r][c2]));
+    }
+    return A;
+}
+
+/* squared quaternion of the relaxation element: the microcanonical step */
+static int micro_quaternion(const double k[4], double r[4])
+{
+    double n = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
+    if (n == 0.0) return 0;
+    double h[4] = { k[0] / n, k[1] / n, k[2] / n, k[3] / n };
+    quat_mul(h, h, r);
+    return 1;
+}
+
+/*
+ * Update every link U_mu(x) with x of the given parity: mode 0 heatbath
+ * (counter sweep), mode 1 overrelaxation.  Returns the number of heatbath
+ * draws that hit the rejection cap (those subgroups are left unchanged), or
+ * -1 on bad arguments.
+ */
+long oracle_wilson_update(double *U, const int dims[4], int mu, int parity, double beta, int mode,
+                          uint64_t seed, uint32_t sweep, int cap)
+{
+    lattice g;
+    if (lattice_init(&g, dims) || mu < 0 || mu > 3 || !(beta > 0.0) || cap < 1) return -1;
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    long fails = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : fails)
+#endif
+    for (long i = 0; i < g.V; ++i) {
+        if (site_parity(&g, i) != parity) continue;
+        mat3 A = staple_sum(U, &g, i, mu);
+        mat3 u = mat_load(link_cptr(U, i, mu));
+        for (int sg = 0; sg < 3; ++sg) {
+            int a = SUBGROUP[sg][0], b = SUBGROUP[sg][1];
+            mat3 W = mat_mul(&u, &A);
+            double k[4], r[4];
+            block_quaternion(W.m[a][a], W.m[a][b], W.m[b][a], W.m[b][b], k);
+            int st;
+            if (mode == 0) {
+                st = heatbath_quaternion_tag(k, 3.0 / beta, (uint32_t)(4 * i + mu), sweep, sg, cap, key,
+                                             WILSON_TAG, r);
+            } else {
+                st = micro_quaternion(k, r);
+            }
+            if (mode == 0 && st == 0) ++fails;
+            if (st != 1) continue;
+            cplx R[2][2];
+            su2_matrix(r, R);
+            rotate_rows(&u, a, b, R);
+        }
+        mat_store(link_ptr(U, i, mu), &u);
+    }
+    return fails;
+}
+
+/* the staple sum A of link U_mu(x_i), for the pins (18 doubles) */
+int oracle_staple(const double *U, const int dims[4], long i, int mu, double *out)
+{
+    lattice g;
+    if (lattice_init(&g, dims) || mu < 0 || mu > 3) return -1;
+    mat3 A = staple_sum(U, &g, i, mu);
+    mat_store(out, &A);
+    return 0;
 }

@@ -697,3 +697,88 @@ def test_mag_fixed_points():
     oracle.mag_sweeps(R, 1.7, 300)
     assert oracle.mag_theta(R) < 1e-20
     assert oracle.mag_functional(R) == pytest.approx(1.0, abs=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Wilson-action generation (heatbath + microcanonical overrelaxation)
+# ---------------------------------------------------------------------------
+def _plaquettes_with_link(U, site, mu):
+    """sum over the 6 plaquettes containing U_mu(x) of Re tr U_P, with numpy."""
+    dims = tuple(int(d) for d in oracle.dims_of(U))
+    flat = U.reshape(-1, 4, 3, 3)
+
+    def shift(i, nu, d):
+        c = list(np.unravel_index(i, dims[::-1])[::-1])
+        c[nu] = (c[nu] + d) % dims[nu]
+        return int(np.ravel_multi_index(c[::-1], dims[::-1]))
+    tot = 0.0
+    for nu in range(4):
+        if nu == mu:
+            continue
+        xp, xn, xm = shift(site, mu, 1), shift(site, nu, 1), shift(site, nu, -1)
+        P = flat[site, mu] @ flat[xp, nu] @ flat[xn, mu].conj().T @ flat[site, nu].conj().T
+        Q = flat[xm, mu] @ flat[shift(xm, mu, 1), nu] @ flat[site, mu].conj().T @ flat[xm, nu].conj().T
+        tot += np.trace(P).real + np.trace(Q).real
+    return tot
+
+
+def test_staple_gives_the_plaquettes_of_the_link():
+    """Re tr(U A) equals the sum over the six plaquettes containing U (numpy)."""
+    U = field((4, 4, 4, 6), seed=71, gseed=72)
+    flat = U.reshape(-1, 4, 3, 3)
+    for site, mu in ((0, 0), (57, 2), (300, 3)):
+        A = oracle.staple(U, site, mu)
+        assert np.trace(flat[site, mu] @ A).real == pytest.approx(_plaquettes_with_link(U, site, mu), rel=1e-12)
+
+
+def test_wilson_overrelaxation_conserves_the_action():
+    U = field((4, 4, 4, 4), seed=73, gseed=74)
+    P = oracle.plaquette(U)
+    V = U.copy()
+    for mu in range(4):
+        for p in (0, 1):
+            oracle.wilson_update(V, mu, p, 6.0, 1, 1, 0)
+    assert oracle.plaquette(V) == pytest.approx(P, abs=1e-13)
+    assert np.abs(V - U).max() > 1e-2  # the links did move
+
+
+def test_wilson_heatbath_zero_temperature_is_relaxation():
+    """beta -> infinity: each subgroup is set to the maximiser of Re tr(R U A),
+    so the local action Re tr(U A) reaches its subgroup maxima and the
+    plaquette rises."""
+    U = field((4, 4, 4, 4), seed=75, gseed=76)
+    P0 = oracle.plaquette(U)
+    flat_before = U.reshape(-1, 4, 3, 3).copy()
+    oracle.wilson_update(U, 0, 0, 1e15, 0, 3, 0)  # heatbath spread ~ sqrt(3 / (beta |k|)) ~ 1e-8
+    assert oracle.plaquette(U) > P0
+    # the updated link maximises the last subgroup (0, 2): its quaternion is real
+    A = oracle.staple(U, 0, 0)
+    W = U.reshape(-1, 4, 3, 3)[0, 0] @ A
+    k = oracle.block_quaternion(np.array([[W[0, 0], W[0, 2]], [W[2, 0], W[2, 2]]]))
+    assert np.linalg.norm(k[1:]) < 1e-6 * np.linalg.norm(k) and k[0] > 0
+    assert not np.allclose(flat_before[0, 0], U.reshape(-1, 4, 3, 3)[0, 0])
+
+
+def test_wilson_strong_coupling_plaquette():
+    """beta = 0.3: <Re tr U_P / 3> = beta/18 + O(beta^2) for SU(3)."""
+    beta = 0.3
+    U = field((4, 4, 4, 4), seed=77, gseed=78, plaq=0.1)
+    vals = []
+    for n in range(60):
+        assert oracle.wilson_sweep(U, beta, 0, 5, n) == 0
+        if n >= 20:
+            vals.append(oracle.plaquette(U))
+    assert np.mean(vals) == pytest.approx(beta / 18, abs=3e-3)
+
+
+def test_wilson_beta6_plaquette():
+    """beta = 6.0 on 8^4: the average plaquette of the thermalised Wilson
+    theory, 0.5937 (a standard value of the literature), within 0.006."""
+    U = field((8, 8, 8, 8), seed=79, gseed=80, plaq=0.59)
+    vals = []
+    for n in range(40):
+        oracle.wilson_sweep(U, 6.0, 0, 7, n)
+        oracle.wilson_sweep(U, 6.0, 1, 7, n)
+        if n >= 15:
+            vals.append(oracle.plaquette(U))
+    assert np.mean(vals) == pytest.approx(0.5937, abs=6e-3)
