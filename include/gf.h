@@ -244,6 +244,26 @@ int gf_reunitarize(gf_ctx *ctx);
  * FP64 storage only). */
 int gf_autotune(gf_ctx *ctx, int *threads_per_site, int *block);
 
+/* ------------------------------------- Wilson-action gauge-field generation */
+
+/* Thermalised inputs like the paper's ensembles (Sec. 5), S = beta sum_P
+ * (1 - Re tr U_P / 3).  One update of every link U_mu(x), x of the given
+ * parity, of the resident FP64 field (storage 18 or 12): mode 0 heatbath
+ * (Cabibbo-Marinari on the SU(2) draw of gf_anneal at T = 3/beta, Philox
+ * key seed, counter (4 x + mu, sweep, 256 subgroup + draw, 3)), mode 1
+ * microcanonical overrelaxation (the squared relaxation element; the action
+ * is unchanged).  Heatbath draws that hit "sa_cap" leave their subgroup
+ * unchanged and are counted for the next gf_generate status. */
+int gf_wilson_update(gf_ctx *ctx, int mu, int parity, double beta, int mode, uint64_t seed, uint32_t sweep);
+
+/* n_sweeps compound sweeps on a canonical field U (host or device, in/out):
+ * each one heatbath sweep (directions 0..3, parities 0, 1; counter sweep0 +
+ * k) followed by n_or overrelaxation sweeps.  12-real storage is
+ * reunitarised every 4 compound sweeps.  Returns GF_EREJECT if some draws hit
+ * the rejection cap.  Stats: "sweeps", "or_sweeps", "sa_rejects",
+ * "ms_total". */
+int gf_generate(gf_ctx *ctx, double *U, double beta, int n_sweeps, int n_or, uint64_t seed, uint32_t sweep0);
+
 /* --------------------------------------------------- learned warm start */
 
 /* The learned warm start predicts, from the FP64 field at the FP32 -> FP64

@@ -1157,4 +1157,64 @@ int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t 
     return GF_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Wilson-action gauge-field generation (thermalised inputs)
+// ---------------------------------------------------------------------------
+int gf_wilson_update(gf_ctx *ctx, int mu, int parity, double beta, int mode, uint64_t seed, uint32_t sweep)
+{
+    if (!ctx) return GF_EINVAL;
+    if (ctx->resident != GF_FP64 || ctx->resident_fmt == DF64_18)
+        return fail(ctx, GF_ESTATE, "needs a resident FP64 field (storage 18 or 12)");
+    if (mu < 0 || mu > 3 || (parity & ~1) || !(beta > 0.0) || !std::isfinite(beta) || (mode != 0 && mode != 1))
+        return fail(ctx, GF_EINVAL, "mu 0..3, parity 0/1, beta > 0, mode 0 (heatbath) or 1 (overrelaxation)");
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    CK(launch_wilson(ctx->resident_fmt, ref(ctx, ctx->f64), ctx->geom, mu, parity, beta, mode, key, sweep, ctx->sa_cap,
+                     ctx->dstatus, ctx->stream));
+    return GF_OK;
+}
+
+int gf_generate(gf_ctx *ctx, double *U, double beta, int n_sweeps, int n_or, uint64_t seed, uint32_t sweep0)
+{
+    if (!ctx) return GF_EINVAL;
+    if (!(beta > 0.0) || !std::isfinite(beta) || n_sweeps < 0 || n_or < 0)
+        return fail(ctx, GF_EINVAL, "beta > 0, n_sweeps >= 0, n_or >= 0");
+    if (ctx->fp64_arith == 1) return fail(ctx, GF_EINVAL, "generation runs on FP64 storage (fp64_arith 0)");
+    ctx->stats.clear();
+    double t0 = now_ms();
+    RET(ensure_common(ctx));
+    const double *view;
+    bool host;
+    RET(device_view(ctx, U, &view, &host));
+    RET(upload(ctx, view, GF_FP64));
+    CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int) * 4, ctx->stream));
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    FieldRef f = ref(ctx, ctx->f64);
+    const bool reunit = twelve_real(ctx->resident_fmt);  // row 2 rebuilt on load: keep rows 0, 1 unitary
+    for (int k = 0; k < n_sweeps; ++k) {
+        for (int mu = 0; mu < 4; ++mu)
+            for (int p = 0; p < 2; ++p)
+                CK(launch_wilson(ctx->resident_fmt, f, ctx->geom, mu, p, beta, 0, key, sweep0 + (uint32_t)k,
+                                 ctx->sa_cap, ctx->dstatus, ctx->stream));
+        for (int o = 0; o < n_or; ++o)
+            for (int mu = 0; mu < 4; ++mu)
+                for (int p = 0; p < 2; ++p)
+                    CK(launch_wilson(ctx->resident_fmt, f, ctx->geom, mu, p, beta, 1, key, 0, ctx->sa_cap,
+                                     ctx->dstatus, ctx->stream));
+        if (reunit && (k % 4 == 3 || k == n_sweeps - 1))
+            CK(launch_reunitarize(ctx->resident_fmt, f, ctx->geom, ctx->stream));
+    }
+    int rejects = 0;
+    CK(cudaMemcpyAsync(ctx->hres + 2, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    RET(download(ctx, U, host));
+    CK(cudaStreamSynchronize(ctx->stream));
+    memcpy(&rejects, ctx->hres + 2, sizeof(int));
+    ctx->stats["sweeps"] = n_sweeps;
+    ctx->stats["or_sweeps"] = (double)n_sweeps * n_or;
+    ctx->stats["sa_rejects"] = rejects;
+    ctx->stats["ms_total"] = now_ms() - t0;
+    if (rejects) return fail(ctx, GF_EREJECT, "heatbath rejection cap reached in some draws");
+    return GF_OK;
+}
+
 }  // extern "C"

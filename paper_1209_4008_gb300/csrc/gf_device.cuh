@@ -536,7 +536,7 @@ __device__ __forceinline__ double u01(uint32_t w) { return ((double)w + 0.5) * (
 // accept/reject decisions follow the FP64 definition.  Returns 1 on success,
 // 0 when cap attempts were rejected, 2 when k = 0 (nothing to do).
 __device__ __forceinline__ int heatbath_quat(const double k[4], double T, uint32_t site, uint32_t sweep, int sg,
-                                             int cap, uint2 key, double r[4])
+                                             int cap, uint2 key, double r[4], uint32_t tag = GF_SA_TAG)
 {
     double kn = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
     if (kn == 0.0) return 2;
@@ -544,7 +544,7 @@ __device__ __forceinline__ int heatbath_quat(const double k[4], double T, uint32
     double s0 = 0.0;
     bool ok = false;
     for (int a = 0; a < cap && a < (int)GF_SA_DIRECTION; ++a) {
-        uint4 w = philox4x32_10(make_uint4(site, sweep, (uint32_t)sg * 256u + (uint32_t)a, GF_SA_TAG), key);
+        uint4 w = philox4x32_10(make_uint4(site, sweep, (uint32_t)sg * 256u + (uint32_t)a, tag), key);
         if (alpha < GF_SA_ALPHA_SWITCH) {
             double u = u01(w.x);
             double e = exp(-2.0 * alpha);
@@ -566,7 +566,7 @@ __device__ __forceinline__ int heatbath_quat(const double k[4], double T, uint32
         }
     }
     if (!ok) return 0;
-    uint4 w = philox4x32_10(make_uint4(site, sweep, (uint32_t)sg * 256u + GF_SA_DIRECTION, GF_SA_TAG), key);
+    uint4 w = philox4x32_10(make_uint4(site, sweep, (uint32_t)sg * 256u + GF_SA_DIRECTION, tag), key);
     double ct = 2.0 * u01(w.x) - 1.0;
     double phi = GF_TWO_PI * u01(w.y);
     double st = sqrt(1.0 - ct * ct);

@@ -94,6 +94,11 @@ cudaError_t launch_gauge_identity(FieldRef gt, const Geom &g, cudaStream_t s);
 cudaError_t launch_apply_tracked_gauge(const double *aos, FieldRef gt, int dst_fmt, FieldRef dst, const Geom &g,
                                        cudaStream_t s);
 // F and theta of the resident field: nblocks partials, then the final sum
+// Wilson-action update of the links U_mu(x), x of one parity (mode 0 heatbath, 1 overrelaxation;
+// FP64 storage); heatbath draws that hit the cap are counted in *status
+cudaError_t launch_wilson(int fmt, FieldRef f, const Geom &g, int mu, int parity, double beta, int mode, uint2 key,
+                          uint32_t sweep, int cap, int *status, cudaStream_t s);
+
 int measure_blocks(const Geom &g);
 int slice_blocks(const Geom &g);  // blocks per timeslice of launch_measure_slices
 // F_t, theta_t of every timeslice into slices[2 Lt]; out[0] = mean F_t, out[1] = max theta_t

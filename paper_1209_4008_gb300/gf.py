@@ -63,6 +63,8 @@ SIGNATURES = {
     "gf_sa_half_sweep": (C.c_int, [_vp, C.c_int, C.c_double, C.c_uint64, C.c_uint32]),
     "gf_measure": (C.c_int, [_vp, _dp, _dp]),
     "gf_measure_timeslices": (C.c_int, [_vp, _dp, _dp]),
+    "gf_wilson_update": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_uint32]),
+    "gf_generate": (C.c_int, [_vp, _vp, C.c_double, C.c_int, C.c_int, C.c_uint64, C.c_uint32]),
     "gf_sr_half_sweep": (C.c_int, [_vp, C.c_int, C.c_double, C.c_uint64, C.c_uint32]),
     "gf_reunitarize": (C.c_int, [_vp]),
     "gf_autotune": (C.c_int, [_vp, _ip, _ip]),
@@ -303,6 +305,20 @@ def gf_measure_timeslices(ctx: Context):
     ctx.check(ctx.lib.gf_measure_timeslices(ctx.handle, F.ctypes.data_as(_dp), th.ctypes.data_as(_dp)),
               "gf_measure_timeslices")
     return F, th
+
+
+def gf_wilson_update(ctx: Context, mu: int, parity: int, beta: float, mode: int, seed: int, sweep: int) -> None:
+    ctx.check(ctx.lib.gf_wilson_update(ctx.handle, int(mu), int(parity), float(beta), int(mode), int(seed),
+                                       int(sweep)), "gf_wilson_update")
+
+
+def gf_generate(ctx: Context, U, beta: float, n_sweeps: int, n_or: int, seed: int, sweep0: int = 0,
+                allow_reject=False) -> int:
+    """Wilson-action heatbath + overrelaxation sweeps on U in place."""
+    _check_field(ctx, U)
+    ok = (GF_OK, GF_EREJECT) if allow_reject else (GF_OK,)
+    return ctx.check(ctx.lib.gf_generate(ctx.handle, _ptr(U), float(beta), int(n_sweeps), int(n_or), int(seed),
+                                         int(sweep0)), "gf_generate", ok=ok)
 
 
 def gf_reunitarize(ctx: Context) -> None:

@@ -717,3 +717,48 @@ def test_mag_unsupported_paths_raise():
     with pytest.raises(gf.GFError):
         gf.gf_measure_timeslices(c)
     gf.gf_or_half_sweep(c, 0, 1.5)  # still usable afterwards
+
+
+# ---------------------------------------------------------------------------
+# Wilson-action generation: the same Cabibbo-Marinari updates on both sides
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 6, 10)])
+@pytest.mark.parametrize("storage", [18, 12])
+def test_wilson_update_parity(dims, storage):
+    U = cpu_field(dims, seed=81, gseed=82, plaq=0.59)
+    c = ctx_for(dims, 0, storage64=storage)
+    gf.gf_upload(c, dev(U), gf.GF_FP64)
+    W = U.copy()
+    for mu in range(4):
+        for p in (0, 1):
+            for mode in (0, 1):
+                gf.gf_wilson_update(c, mu, p, 6.1, mode, 11, 3)
+                assert oracle.wilson_update(W, mu, p, 6.1, mode, 11, 3) == 0
+    d = torch.empty_like(dev(U))
+    gf.gf_download(c, d)
+    assert max_rel(host(d), W) < 1e-11
+
+
+def test_generate_matches_oracle_and_thermalises():
+    dims = (6, 4, 6, 10)
+    U = cpu_field(dims, seed=83, gseed=84, plaq=0.5)
+    c = ctx_for(dims, 0)
+    d = dev(U)
+    gf.gf_generate(c, d, 6.0, 2, 2, 13, 0)
+    W = U.copy()
+    for k in range(2):
+        oracle.wilson_sweep(W, 6.0, 0, 13, k)
+        for _ in range(2):
+            oracle.wilson_sweep(W, 6.0, 1, 13, 0)
+    assert max_rel(host(d), W) < 1e-10
+    # thermalised plaquette at beta = 6.0 (0.5937 in the literature; 8^4)
+    d8 = dev(cpu_field((8, 8, 8, 8), seed=85, gseed=86, plaq=0.5))
+    c8 = ctx_for((8, 8, 8, 8), 0)
+    gf.gf_generate(c8, d8, 6.0, 30, 2, 17, 0)
+    vals = []
+    for k in range(20):
+        gf.gf_generate(c8, d8, 6.0, 1, 2, 17, 30 + k)
+        vals.append(gf.gf_plaquette(c8, d8))
+    assert np.mean(vals) == pytest.approx(0.5937, abs=6e-3)
+    M = host(d8).reshape(-1, 3, 3)
+    assert np.abs(M @ np.conj(np.swapaxes(M, -1, -2)) - np.eye(3)).max() < 1e-12
