@@ -770,6 +770,45 @@ def mag(args):
     print(json.dumps(out), flush=True)
 
 
+def thermal(args):
+    """Gauge fixing of a thermalised field: the 32^4 synthetic field (seeds 3/4)
+    evolved with the Wilson action at beta = 6.1 (the paper's ensembles, Sec. 5)
+    by --therm compound sweeps (one heatbath and 4 overrelaxation sweeps each),
+    then fixed to Landau gauge (omega 1.7, theta < 1e-14) with the mixed and the
+    all-FP64 policies.  Prints one JSON object."""
+    from paper_1209_4008_gb300 import gf, synth
+    beta, n_or = 6.1, 4
+    U = synth.make_field(DIMS, PLAQ, *SEEDS, device="cuda")
+    V = int(np.prod(DIMS))
+    g = gf.gf_create(DIMS, gf.GF_LANDAU)
+    gf.gf_set_stream(g, torch.cuda.current_stream())
+    gf.gf_generate(g, U, beta, 2, n_or, 21, 0)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gf.gf_generate(g, U, beta, args.therm, n_or, 21, 2)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    plaq = gf.gf_plaquette(g, U)
+    out = {"workload": f"32^4 Wilson beta={beta}, {args.therm} compound sweeps (1 heatbath + {n_or} OR), "
+                       f"then Landau OR omega 1.7 to theta<1e-14",
+           "generation": {"s": t_gen, "ms_per_compound_sweep": 1e3 * t_gen / max(1, args.therm),
+                          "link_updates_per_s": 4 * V * (1 + n_or) * args.therm / t_gen, "plaquette": plaq}}
+    pristine = U.clone()
+    for name, prec in (("mixed", gf.GF_MIXED), ("fp64", gf.GF_FP64)):
+        c = make_ctx(gf, prec)
+        work = pristine.clone()
+        gf.gf_overrelax(c, work, OMEGA, THETA_TARGET, MAX_ITER)  # warm-up
+        work.copy_(pristine)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        conv, it, F, th = gf.gf_overrelax(c, work, OMEGA, THETA_TARGET, MAX_ITER)
+        torch.cuda.synchronize()
+        out[name] = {"s": time.perf_counter() - t0, "sweeps": it, "F": F, "theta": th, "converged": conv,
+                     "sweeps_fp64": gf.gf_get_stat(c, "sweeps_fp64")}
+    out["dF"] = abs(out["mixed"]["F"] - out["fp64"]["F"])
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -802,6 +841,8 @@ def main():
     ap.add_argument("--coulomb", action="store_true", help="the 48^3x96 Coulomb workload with annealing")
     ap.add_argument("--net", action="store_true", help="time the warm-start network's kernels")
     ap.add_argument("--mag", action="store_true", help="the maximally Abelian gauge on the 32^4 field")
+    ap.add_argument("--thermal", action="store_true", help="gauge fixing of a field thermalised at beta 6.1")
+    ap.add_argument("--therm", type=int, default=100, help="--thermal: compound sweeps of generation")
     ap.add_argument("--seeds", type=int, default=8)
     ap.add_argument("--sa-sweeps", type=int, default=3000)
     args = ap.parse_args()
@@ -824,6 +865,10 @@ def main():
     if args.mag:
         torch.cuda.set_device(0)
         mag(args)
+        return
+    if args.thermal:
+        torch.cuda.set_device(0)
+        thermal(args)
         return
     if args.kernel:
         torch.cuda.set_device(0)
