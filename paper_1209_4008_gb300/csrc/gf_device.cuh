@@ -456,11 +456,12 @@ template <class T>
 __device__ __forceinline__ void add_mag_terms(const mat3<T> &x, int a, int b, T h[4])
 {
     const cpx<T> xaa = x.e[a][a], xab = x.e[a][b], xba = x.e[b][a], xbb = x.e[b][b];
-    h[0] += xaa.re * xaa.re + xaa.im * xaa.im + xbb.re * xbb.re + xbb.im * xbb.im;  // h11
-    h[1] += xba.re * xba.re + xba.im * xba.im + xab.re * xab.re + xab.im * xab.im;  // h22
+    // (accumulated as FMA chains)
+    h[0] = fma(xaa.re, xaa.re, fma(xaa.im, xaa.im, fma(xbb.re, xbb.re, fma(xbb.im, xbb.im, h[0]))));  // h11
+    h[1] = fma(xba.re, xba.re, fma(xba.im, xba.im, fma(xab.re, xab.re, fma(xab.im, xab.im, h[1]))));  // h22
     // h12 += conj(xaa) xba - xbb conj(xab)
-    h[2] += xaa.re * xba.re + xaa.im * xba.im - (xbb.re * xab.re + xbb.im * xab.im);
-    h[3] += xaa.re * xba.im - xaa.im * xba.re - (xbb.im * xab.re - xbb.re * xab.im);
+    h[2] = fma(xaa.re, xba.re, fma(xaa.im, xba.im, fma(-xbb.re, xab.re, fma(-xbb.im, xab.im, h[2]))));
+    h[3] = fma(xaa.re, xba.im, fma(-xaa.im, xba.re, fma(-xbb.im, xab.re, fma(xbb.re, xab.im, h[3]))));
 }
 
 // quaternion r of the maximiser (r0 = |alpha|, r3 = 0, r2 + i r1 = beta);

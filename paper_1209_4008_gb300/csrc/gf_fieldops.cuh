@@ -90,6 +90,7 @@ __device__ __forceinline__ void reunitarize3(mat3<double> &u)
     rebuild_row2(u);
 }
 
+// x y, accumulated as one multiply and FMAs per component (no separate adds)
 __device__ __forceinline__ mat3<double> mul3(const mat3<double> &x, const mat3<double> &y)
 {
     mat3<double> z;
@@ -97,11 +98,16 @@ __device__ __forceinline__ mat3<double> mul3(const mat3<double> &x, const mat3<d
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            double re = 0.0, im = 0.0;
+            double re = x.e[a][0].re * y.e[0][b].re;
+            double im = x.e[a][0].re * y.e[0][b].im;
+            re = fma(-x.e[a][0].im, y.e[0][b].im, re);
+            im = fma(x.e[a][0].im, y.e[0][b].re, im);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                re += x.e[a][c].re * y.e[c][b].re - x.e[a][c].im * y.e[c][b].im;
-                im += x.e[a][c].re * y.e[c][b].im + x.e[a][c].im * y.e[c][b].re;
+            for (int c = 1; c < 3; ++c) {
+                re = fma(x.e[a][c].re, y.e[c][b].re, re);
+                re = fma(-x.e[a][c].im, y.e[c][b].im, re);
+                im = fma(x.e[a][c].re, y.e[c][b].im, im);
+                im = fma(x.e[a][c].im, y.e[c][b].re, im);
             }
             z.e[a][b] = mk<double>(re, im);
         }
