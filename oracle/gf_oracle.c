@@ -22,7 +22,13 @@
  *   - Coulomb gauge: only spatial links enter K, F and theta, the temporal
  *     links are rotated by the same g so that the update stays a gauge
  *     transformation;
- *   - a subgroup whose projected quaternion vanishes is left unchanged.
+ *   - a subgroup whose projected quaternion vanishes is left unchanged;
+ *   - two further readings of g -> g^omega are selectable (first order, exact
+ *     power; oracle_set_or_variant);
+ *   - the maximally Abelian gauge (Sec. 6, named only) maximises the
+ *     literature's sum |U_ii|^2 by the same subgroup relaxation/overrelaxation;
+ *   - thermalised inputs (Sec. 5) come from the Wilson action by
+ *     Cabibbo-Marinari heatbath and microcanonical overrelaxation.
  *
  * Data layout (canonical, shared with the library's public API): a field is
  * double U[Lt][Lz][Ly][Lx][4][3][3][2] -- site index x fastest, then the four
