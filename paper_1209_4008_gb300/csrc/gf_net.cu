@@ -230,25 +230,12 @@ __device__ __forceinline__ int sel3(const int v[3], int j) { return j == 0 ? v[0
 
 template <int IP, int N>
 struct TcLayout {
-    static constexpr int S = IP <= 32 ? 6 : 4;  // shared-memory stages (one tap each)
-    static constexpr int LOOK = S - 2;          // taps in flight ahead of the one consumed
     static constexpr int A_BYTES = gf::tc::kM * IP * 2;
     static constexpr int B_BYTES = N * IP * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int BAR_OFF = S * STAGE + gf::tc::kGuardBytes;
-    static constexpr int SMEM = BAR_OFF + (S + 1) * 8 + 16;
+    static constexpr int BAR_OFF = gf::tc::kStages * STAGE + gf::tc::kGuardBytes;
+    static constexpr int SMEM = BAR_OFF + (gf::tc::kStages + 1) * 8 + 16;
 };
-
-// 16-byte asynchronous copy global -> shared (zero-filled when src_bytes = 0)
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, int src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(gf::tc::smem_u32(smem_dst)), "l"(gsrc),
-                 "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int IP, int N>
 __global__ void __launch_bounds__(128) k_conv_tc(const bf16 *__restrict__ X, int I, const bf16 *__restrict__ W, int O,
@@ -259,15 +246,15 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16 *__restrict__ X, int
     using namespace gf::tc;
     typedef TcLayout<IP, N> LY;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);  // S + 1 (final)
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + (LY::S + 1) * 8);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);  // kStages + 1 (final)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + (kStages + 1) * 8);
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int s0 = blockIdx.x * kM;
     constexpr uint32_t idesc = instr_desc(kM, N);
 
     if (tid == 0) {
-        for (int st = 0; st <= LY::S; ++st) mbar_init(&bar[st], 1);
+        for (int st = 0; st <= kStages; ++st) mbar_init(&bar[st], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
     }
@@ -306,59 +293,56 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16 *__restrict__ X, int
             o3[j] = wrap_coord(c3 + d, g.L[3]) * st3;
         }
     }
-    constexpr int S = LY::S, LOOK = LY::LOOK;
-    constexpr int AC = IP / 8;                                     // 16-byte chunks of one A row
+    constexpr int AC = IP / 8;                                  // 16-byte chunks of one A row
     constexpr int WPT = (N * (IP / 8) + kThreads - 1) / kThreads;  // weight chunks per thread
-    // asynchronous copies of tap k's A row (this thread's site) and B chunks into stage k % S:
-    // A core (mr, kc) at (kc * 16 + mr) * 128 (SBO 128, LBO 2048); B core (mr, kc) at
-    // (kc * (N/8) + mr) * 128 (SBO 128, LBO N*16); absent data is zero-filled
-    auto issue = [&](int k) {
-        uint8_t *A = smem + (k % S) * LY::STAGE;
-        uint8_t *B = A + LY::A_BYTES;
+    uint4 cur[AC], nxt[AC], wcur[WPT], wnxt[WPT];
+    // global loads of tap k's A row and B chunks into registers
+    auto fetch = [&](int k, uint4 *a, uint4 *w) {
         const int nbs = site < g.V ? sel3(o0, k % 3) + sel3(o1, (k / 3) % 3) + sel3(o2, (k / 9) % 3) + sel3(o3, k / 27)
                                    : -1;
 #pragma unroll
         for (int c = 0; c < AC; ++c) {
-            const bool ok = nbs >= 0 && 8 * c < I;
-            cp_async16(A + (c * 16 + (tid >> 3)) * 128 + (tid & 7) * 16, ok ? (const void *)(X + (long)nbs * I + 8 * c)
-                                                                           : (const void *)X,
-                       ok ? 16 : 0);
+            a[c] = make_uint4(0, 0, 0, 0);
+            if (nbs >= 0 && 8 * c < I) a[c] = *reinterpret_cast<const uint4 *>(X + (long)nbs * I + 8 * c);
         }
 #pragma unroll
         for (int q = 0; q < WPT; ++q) {
             const int e = tid + q * kThreads;
-            if (e < N * (IP / 8)) {
-                const int o = e / (IP / 8), c = e - o * (IP / 8);
-                const bool ok = o < O && 8 * c < I;
-                cp_async16(B + (c * (N / 8) + (o >> 3)) * 128 + (o & 7) * 16,
-                           ok ? (const void *)(W + ((long)k * O + o) * I + 8 * c) : (const void *)W, ok ? 16 : 0);
-            }
+            const int o = e / (IP / 8), c = e - o * (IP / 8);
+            w[q] = make_uint4(0, 0, 0, 0);
+            if (e < N * (IP / 8) && o < O && 8 * c < I)
+                w[q] = *reinterpret_cast<const uint4 *>(W + ((long)k * O + o) * I + 8 * c);
         }
     };
-#pragma unroll
-    for (int k = 0; k < LOOK; ++k) {
-        issue(k);
-        cp_async_commit();
-    }
+    fetch(0, cur, wcur);
     bool fail = false;
     for (int k = 0; k < 81; ++k) {
-        const int st = k % S;
-        // refill the stage of tap k + LOOK, last used by tap k + LOOK - S = k - 2 (its MMAs must be done)
-        const int kn = k + LOOK;
-        if (kn < 81) {
-            const int prev = kn - S;
-            if (prev >= 0 && !mbar_wait(&bar[kn % S], (uint32_t)((prev / S) & 1))) fail = true;
-            if (!fail) issue(kn);
+        const int st = k % kStages;
+        if (k + 1 < 81) fetch(k + 1, nxt, wnxt);  // in flight while tap k is staged
+        if (k >= kStages) {
+            if (!mbar_wait(&bar[st], (uint32_t)((k / kStages - 1) & 1))) fail = true;
         }
-        cp_async_commit();   // one group per iteration (possibly empty)
-        cp_async_wait<LOOK>();  // this thread's copies of tap k have landed
-        fence_proxy_async();
         if (__syncthreads_or(fail)) {
             fail = true;
             break;
         }
         uint8_t *A = smem + st * LY::STAGE;
         uint8_t *B = A + LY::A_BYTES;
+        // A: this thread's neighbour row, K-major core matrices (8 rows x 16 B):
+        // core (mr, kc) at (kc * 16 + mr) * 128  -> SBO 128, LBO 2048
+#pragma unroll
+        for (int c = 0; c < AC; ++c) *reinterpret_cast<uint4 *>(A + (c * 16 + (tid >> 3)) * 128 + (tid & 7) * 16) = cur[c];
+        // B: weights of tap k, core (mr, kc) at (kc * (N/8) + mr) * 128 -> SBO 128, LBO N*16
+#pragma unroll
+        for (int q = 0; q < WPT; ++q) {
+            const int e = tid + q * kThreads;
+            if (e < N * (IP / 8)) {
+                const int o = e / (IP / 8), c = e - o * (IP / 8);
+                *reinterpret_cast<uint4 *>(B + (c * (N / 8) + (o >> 3)) * 128 + (o & 7) * 16) = wcur[q];
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
         if (tid == 0) {
             fence_after_sync();
 #pragma unroll
@@ -369,11 +353,14 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16 *__restrict__ X, int
             }
             mma_commit(&bar[st]);
         }
+#pragma unroll
+        for (int c = 0; c < AC; ++c) cur[c] = nxt[c];
+#pragma unroll
+        for (int q = 0; q < WPT; ++q) wcur[q] = wnxt[q];
     }
-    cp_async_wait<0>();  // no copy may still be in flight when the CTA leaves
     // all MMAs issued by thread 0 are complete once the final commit arrives
-    if (tid == 0) mma_commit(&bar[LY::S]);
-    if (!mbar_wait(&bar[LY::S], 0)) fail = true;
+    if (tid == 0) mma_commit(&bar[kStages]);
+    if (!mbar_wait(&bar[kStages], 0)) fail = true;
     fail = __syncthreads_or(fail);
     if (!fail) {
         fence_after_sync();
