@@ -333,7 +333,9 @@ int gf_gauge_algebra(gf_ctx *ctx, double scale, float *c);
 /* Apply g(x) = exp(i s sum_a c_a(x) lambda_a / 2) to the resident FP64 field. */
 int gf_apply_algebra(gf_ctx *ctx, const float *c, double scale);
 /* Attach a trained network (NULL detaches): GF_MIXED then applies its
- * prediction at the switch before the FP64 sweeps.  The context does not own it. */
+ * prediction at the switch before the FP64 sweeps.  The context does not own it.
+ * Landau-gauge contexts only (the inputs carry the Landau violation); other
+ * gauges return GF_EINVAL. */
 int gf_set_net(gf_ctx *ctx, gf_net *net);
 
 /* ------------------------------------ many lattices in one persistent launch */

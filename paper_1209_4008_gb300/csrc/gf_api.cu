@@ -1102,7 +1102,8 @@ int gf_apply_algebra(gf_ctx *ctx, const float *c, double scale)
 int gf_set_net(gf_ctx *ctx, gf_net *net)
 {
     if (!ctx) return GF_EINVAL;
-    if (ctx->gauge == GF_MAG && net) return mag_unsupported(ctx, "the learned warm start");
+    if (ctx->gauge != GF_LANDAU && net)
+        return fail(ctx, GF_EINVAL, "the learned warm start is defined for Landau gauge (its inputs use the Landau violation)");
     ctx->net = net;
     return GF_OK;
 }

@@ -224,3 +224,16 @@ def test_learned_warm_start_pipeline_small():
     print("fp64 sweeps without / with the network:", sweeps[False][0], sweeps[True][0])
     # what the trained network gains: fewer FP64 sweeps to the same final F
     assert sweeps[True][0] < sweeps[False][0]
+
+
+
+def test_learned_warm_start_only_in_landau_gauge():
+    net = gf.gf_net_create((4, 4, 4, 4))
+    for gauge in (gf.GF_COULOMB, gf.GF_MAG):
+        c = gf.gf_create((4, 4, 4, 4), gauge)
+        with pytest.raises(gf.GFError) as e:
+            gf.gf_set_net(c, net)
+        assert e.value.code == gf.GF_EINVAL
+    c = gf.gf_create((4, 4, 4, 4), gf.GF_LANDAU)
+    gf.gf_set_net(c, net)
+    gf.gf_set_net(c, None)
