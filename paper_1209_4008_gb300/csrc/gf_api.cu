@@ -899,6 +899,7 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
                  double *F_out, double *theta_out)
 {
     if (!ctx) return GF_EINVAL;
+    if (!U) return fail(ctx, GF_EINVAL, "field pointer is NULL");
     if (!(omega > 0.0 && omega < 2.0)) return fail(ctx, GF_EINVAL, "omega must lie in (0, 2)");
     if (!(theta_target >= 0.0) || !std::isfinite(theta_target)) return fail(ctx, GF_EINVAL, "theta_target");
     if (max_iter < 0) return fail(ctx, GF_EINVAL, "max_iter < 0");
@@ -1111,6 +1112,7 @@ int gf_set_net(gf_ctx *ctx, gf_net *net)
 int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t seed)
 {
     if (!ctx) return GF_EINVAL;
+    if (!U) return fail(ctx, GF_EINVAL, "field pointer is NULL");
     if (ctx->gauge == GF_MAG) return mag_unsupported(ctx, "annealing");
     if (!(T0 > 0.0) || !(T1 > 0.0) || !std::isfinite(T0) || !std::isfinite(T1) || steps < 0)
         return fail(ctx, GF_EINVAL, "temperatures must be positive and finite, steps >= 0");
@@ -1178,6 +1180,7 @@ int gf_wilson_update(gf_ctx *ctx, int mu, int parity, double beta, int mode, uin
 int gf_generate(gf_ctx *ctx, double *U, double beta, int n_sweeps, int n_or, uint64_t seed, uint32_t sweep0)
 {
     if (!ctx) return GF_EINVAL;
+    if (!U) return fail(ctx, GF_EINVAL, "field pointer is NULL");
     if (!(beta > 0.0) || !std::isfinite(beta) || n_sweeps < 0 || n_or < 0)
         return fail(ctx, GF_EINVAL, "beta > 0, n_sweeps >= 0, n_or >= 0");
     if (ctx->fp64_arith == 1) return fail(ctx, GF_EINVAL, "generation runs on FP64 storage (fp64_arith 0)");

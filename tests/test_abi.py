@@ -75,6 +75,37 @@ def test_host_side_argument_checks(lib):
     assert lib.gf_error_string(gf.GF_ENOTCONVERGED) == b"GF_ENOTCONVERGED"
 
 
+def test_host_side_checks_of_the_added_paths(lib):
+    """Options and entry points of the OR readings, register budgets, per-
+    timeslice stopping, the maximally Abelian gauge and generation: argument
+    and state errors are reported without touching a GPU."""
+    h = C.c_void_p()
+    assert lib.gf_create((C.c_int * 4)(4, 4, 4, 4), gf.GF_MAG, C.byref(h)) == gf.GF_OK
+    try:
+        for key, bad, good in ((b"or_variant", 3.0, 2.0), (b"acc_registers", 200.0, 168.0)):
+            assert lib.gf_set_option(h, key, bad) == gf.GF_EINVAL
+            assert lib.gf_set_option(h, key, good) == gf.GF_OK
+        # not in the maximally Abelian gauge
+        assert lib.gf_set_option(h, b"theta_per_timeslice", 1.0) == gf.GF_EINVAL
+        assert lib.gf_set_option(h, b"fp64_arith", 1.0) == gf.GF_EINVAL
+        assert lib.gf_set_option(h, b"stochastic_p", 0.5) == gf.GF_EINVAL
+        assert b"maximally Abelian" in lib.gf_last_error(h)
+        F = (C.c_double * 4)()
+        assert lib.gf_measure_timeslices(h, F, F) == gf.GF_EINVAL  # not in this gauge
+        assert lib.gf_wilson_update(h, 0, 0, 6.0, 0, 1, 0) == gf.GF_ESTATE
+    finally:
+        lib.gf_destroy(h)
+    assert lib.gf_create((C.c_int * 4)(4, 4, 4, 4), gf.GF_COULOMB, C.byref(h)) == gf.GF_OK
+    try:
+        assert lib.gf_set_option(h, b"theta_per_timeslice", 1.0) == gf.GF_OK
+        F = (C.c_double * 4)()
+        assert lib.gf_measure_timeslices(h, F, F) == gf.GF_ESTATE  # no resident field
+        assert lib.gf_generate(h, None, 6.0, 1, 1, 1, 0) == gf.GF_EINVAL  # no field
+        assert lib.gf_generate(h, None, -1.0, 1, 1, 1, 0) == gf.GF_EINVAL
+    finally:
+        lib.gf_destroy(h)
+
+
 def test_batch_handle_host_side(lib):
     b = gf.gf_batch_create([(4, 4, 4, 4), (8, 8, 8, 8)], gf.GF_LANDAU)
     gf.gf_batch_set_option(b, "precision", gf.GF_FP64)
