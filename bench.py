@@ -604,6 +604,7 @@ def learned(args):
             c = make_ctx(gf, gf.GF_MIXED)
             if mode == "learned":
                 gf.gf_set_net(c, big)
+                gf.gf_set_option(c, "learned_repeat", args.learned_repeat)
             work = pristine.clone()
             gf.gf_overrelax(c, work, OMEGA, THETA_TARGET, MAX_ITER)  # warm-up (autotune, graphs)
             work.copy_(pristine)
@@ -617,6 +618,8 @@ def learned(args):
                 row[mode]["ms_network"] = gf.gf_get_stat(c, "ms_learned")
                 row[mode]["theta_before"] = gf.gf_get_stat(c, "theta_before_learned")
                 row[mode]["theta_after"] = gf.gf_get_stat(c, "theta_after_learned")
+                row[mode]["applications"] = 1 + (gf.gf_get_stat(c, "learned_applications")
+                                                 if args.learned_repeat else 0)
         row["dF"] = abs(row["learned"]["F"] - row["mixed"]["F"])
         res.append(row)
     mean = lambda key, mode: float(np.mean([r[mode][key] for r in res]))
@@ -833,6 +836,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--lr-decay", type=float, default=0.7, help="learning-rate factor per epoch")
+    ap.add_argument("--learned-repeat", type=int, default=0,
+                    help="--learned: further applications of the network in the FP64 phase")
     ap.add_argument("--eval-fields", type=int, default=4)
     ap.add_argument("--save", nargs="?", const=WEIGHTS, default=None, metavar="PATH",
                     help=f"store the trained parameters (.npy; default path {os.path.relpath(WEIGHTS, ROOT)})")

@@ -116,6 +116,10 @@ int gf_set_stream(gf_ctx *ctx, void *stream);
  *                    once per link (one thread per site; equal in exact
  *                    arithmetic), 0 = autotuned or default (default 0)
  *   "block"          threads per block (multiple of 32, <= 256; 0 = autotune)
+ *   "learned_repeat" with an attached network (gf_set_net): apply it again,
+ *                    up to this many times, each time theta has fallen by the
+ *                    factor "learned_factor" (default 1e-2) during the FP64
+ *                    phase (default 0: once, at the switch)
  *   "theta_per_timeslice"  1 = every theta the context reports or checks
  *                    (stopping rule, gf_overrelax's output, gf_measure) is the
  *                    largest timeslice value theta_t (gf_measure_timeslices),

@@ -63,6 +63,8 @@ struct gf_ctx {
     int variant = 0;  // 0 auto, 1 per-subgroup rotations of the held links, 2 accumulate form
     int acc_regs = 0;  // accumulate form, FP64 storage: register budget 255, 168 or 128 (0 = autotuned)
     int or_variant = 0;  // g -> g^omega: 0 rational 19-flop form, 1 first order, 2 exact power
+    int learned_repeat = 0;       // further applications of the learned warm start in the FP64 phase
+    double learned_factor = 1e-2;  // ... each after theta has fallen by this factor
     int slice_theta = 0;  // 1: convergence judged on the largest theta of the timeslices
     double *dslices = nullptr;  // F_t, theta_t of the last per-timeslice measurement
     int use_graphs = 1;
@@ -674,6 +676,12 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
     } else if (k == "variant") {
         if (!integral || iv < 0 || iv > 2) return fail(ctx, GF_EINVAL, "variant: 0, 1 or 2");
         ctx->variant = iv;
+    } else if (k == "learned_repeat") {
+        if (!integral || iv < 0 || iv > 16) return fail(ctx, GF_EINVAL, "learned_repeat: 0..16");
+        ctx->learned_repeat = iv;
+    } else if (k == "learned_factor") {
+        if (!(v > 0.0 && v < 1.0)) return fail(ctx, GF_EINVAL, "learned_factor in (0, 1)");
+        ctx->learned_factor = v;
     } else if (k == "theta_per_timeslice") {
         if (v != 0.0 && ctx->gauge == GF_MAG) return fail(ctx, GF_EINVAL, "theta_per_timeslice: not in the maximally Abelian gauge");
         ctx->slice_theta = v != 0.0;
@@ -733,6 +741,8 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *v)
     else if (k == "use_graphs") *v = ctx->use_graphs;
     else if (k == "acc_registers") *v = ctx->acc_regs;
     else if (k == "or_variant") *v = ctx->or_variant;
+    else if (k == "learned_repeat") *v = ctx->learned_repeat;
+    else if (k == "learned_factor") *v = ctx->learned_factor;
     else if (k == "theta_per_timeslice") *v = ctx->slice_theta;
     else if (k == "kernel_timing") *v = ctx->kernel_timing;
     else if (k == "autotune") *v = ctx->autotune;
@@ -978,8 +988,27 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
                 ctx->stats["theta_before_learned"] = ctx->stats["theta_switch_measured"];
                 ctx->stats["theta_after_learned"] = theta;
             }
-            RET(converge(ctx, omega, theta_target, max_iter - used32, false, twelve_real(ctx->resident_fmt), &used64,
+            // with "learned_repeat" n > 0 the prediction is applied again each time theta has
+            // fallen by a factor learned_factor (at most n more times) before the final stretch
+            int repeats = ctx->net ? ctx->learned_repeat : 0;
+            while (repeats > 0 && theta > 0.0 && !(theta < theta_target)) {
+                const double stage = std::max(theta_target, theta * ctx->learned_factor);
+                int u = 0;
+                RET(converge(ctx, omega, stage, max_iter - used32 - used64, false, twelve_real(ctx->resident_fmt), &u,
+                             &F, &theta));
+                used64 += u;
+                if (!(theta < stage) || theta < theta_target) break;  // budget spent, or done
+                double t3 = now_ms();
+                RET(learned_correction(ctx, theta));
+                RET(measure_resident(ctx, &F, &theta));
+                ctx->stats["ms_learned"] += now_ms() - t3;
+                ctx->stats["learned_applications"] += 1;
+                --repeats;
+            }
+            int u = 0;
+            RET(converge(ctx, omega, theta_target, max_iter - used32 - used64, false, twelve_real(ctx->resident_fmt), &u,
                          &F, &theta));
+            used64 += u;
             ms64 = now_ms() - t2;
         } else {
             CK(launch_reunitarize(ctx->resident_fmt, ref(ctx, ctx->f32), ctx->geom, ctx->stream));
