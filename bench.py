@@ -332,6 +332,7 @@ def gpu_arm(args, rank, world, local):
         gf.gf_net_set_params(net, np.load(WEIGHTS).astype(np.float32))
         ctxl = make_ctx(gf, gf.GF_MIXED)
         gf.gf_set_net(ctxl, net)
+        gf.gf_set_option(ctxl, "learned_repeat", args.learned_repeat)
         work.copy_(pristine)
         gf.gf_overrelax(ctxl, work, OMEGA, THETA_TARGET, MAX_ITER)  # warm-up
         work.copy_(pristine)
@@ -343,6 +344,8 @@ def gpu_arm(args, rank, world, local):
                        "sweeps_fp64_phase_learned": gf.gf_get_stat(ctxl, "sweeps_fp64"),
                        "F_learned": Fl, "dF_learned": abs(Fl - F64), "theta_learned": thl,
                        "ms_network": gf.gf_get_stat(ctxl, "ms_learned"),
+                       "network_applications": 1 + (gf.gf_get_stat(ctxl, "learned_applications")
+                                                    if args.learned_repeat else 0),
                        "weights": os.path.relpath(WEIGHTS, ROOT)}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -836,8 +839,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--lr-decay", type=float, default=0.7, help="learning-rate factor per epoch")
-    ap.add_argument("--learned-repeat", type=int, default=0,
-                    help="--learned: further applications of the network in the FP64 phase")
+    ap.add_argument("--learned-repeat", type=int, default=3,
+                    help="further applications of the network in the FP64 phase, each after theta fell 100x")
     ap.add_argument("--eval-fields", type=int, default=4)
     ap.add_argument("--save", nargs="?", const=WEIGHTS, default=None, metavar="PATH",
                     help=f"store the trained parameters (.npy; default path {os.path.relpath(WEIGHTS, ROOT)})")
