@@ -210,16 +210,21 @@ def test_learned_warm_start_pipeline_small():
     hist = learned.train(net, pairs[:5], epochs=30, lr=1e-3)
     assert hist[-1] < hist[0]
     sweeps = {}
-    for attach in (False, True):
+    for attach in (False, True, "repeat"):
         c = gf.gf_create(dims, 0)
         gf.gf_set_option(c, "precision", gf.GF_MIXED)
         gf.gf_set_option(c, "check_every", 10)
         if attach:
             gf.gf_set_net(c, net)
+        if attach == "repeat":  # applied again at every hundredfold drop of theta
+            gf.gf_set_option(c, "learned_repeat", 3)
         U = synth.make_field(dims, 0.60, 5000, 6000, device="cuda")
         conv, it, F, th = gf.gf_overrelax(c, U, 1.7, 1e-14, 50000)
         assert conv and th < 1e-14
         sweeps[attach] = (gf.gf_get_stat(c, "sweeps_fp64"), F)
+        if attach == "repeat":
+            assert gf.gf_get_stat(c, "learned_applications") >= 1
+    assert abs(sweeps["repeat"][1] - sweeps[False][1]) < 1e-9
     assert abs(sweeps[True][1] - sweeps[False][1]) < 1e-9
     print("fp64 sweeps without / with the network:", sweeps[False][0], sweeps[True][0])
     # what the trained network gains: fewer FP64 sweeps to the same final F
