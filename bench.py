@@ -333,6 +333,7 @@ def gpu_arm(args, rank, world, local):
         ctxl = make_ctx(gf, gf.GF_MIXED)
         gf.gf_set_net(ctxl, net)
         gf.gf_set_option(ctxl, "learned_repeat", args.learned_repeat)
+        gf.gf_set_option(ctxl, "learned_factor", args.learned_factor)
         work.copy_(pristine)
         gf.gf_overrelax(ctxl, work, OMEGA, THETA_TARGET, MAX_ITER)  # warm-up
         work.copy_(pristine)
@@ -608,6 +609,7 @@ def learned(args):
             if mode == "learned":
                 gf.gf_set_net(c, big)
                 gf.gf_set_option(c, "learned_repeat", args.learned_repeat)
+                gf.gf_set_option(c, "learned_factor", args.learned_factor)
             work = pristine.clone()
             gf.gf_overrelax(c, work, OMEGA, THETA_TARGET, MAX_ITER)  # warm-up (autotune, graphs)
             work.copy_(pristine)
@@ -840,7 +842,9 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--lr-decay", type=float, default=0.7, help="learning-rate factor per epoch")
     ap.add_argument("--learned-repeat", type=int, default=3,
-                    help="further applications of the network in the FP64 phase, each after theta fell 100x")
+                    help="further applications of the network in the FP64 phase")
+    ap.add_argument("--learned-factor", type=float, default=1e-2,
+                    help="theta falls by this factor between applications")
     ap.add_argument("--eval-fields", type=int, default=4)
     ap.add_argument("--save", nargs="?", const=WEIGHTS, default=None, metavar="PATH",
                     help=f"store the trained parameters (.npy; default path {os.path.relpath(WEIGHTS, ROOT)})")
