@@ -841,9 +841,9 @@ def main():
     ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--lr-decay", type=float, default=0.7, help="learning-rate factor per epoch")
-    ap.add_argument("--learned-repeat", type=int, default=3,
+    ap.add_argument("--learned-repeat", type=int, default=15,
                     help="further applications of the network in the FP64 phase")
-    ap.add_argument("--learned-factor", type=float, default=1e-2,
+    ap.add_argument("--learned-factor", type=float, default=0.316,
                     help="theta falls by this factor between applications")
     ap.add_argument("--eval-fields", type=int, default=4)
     ap.add_argument("--save", nargs="?", const=WEIGHTS, default=None, metavar="PATH",

@@ -677,7 +677,7 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
         if (!integral || iv < 0 || iv > 2) return fail(ctx, GF_EINVAL, "variant: 0, 1 or 2");
         ctx->variant = iv;
     } else if (k == "learned_repeat") {
-        if (!integral || iv < 0 || iv > 16) return fail(ctx, GF_EINVAL, "learned_repeat: 0..16");
+        if (!integral || iv < 0 || iv > 64) return fail(ctx, GF_EINVAL, "learned_repeat: 0..64");
         ctx->learned_repeat = iv;
     } else if (k == "learned_factor") {
         if (!(v > 0.0 && v < 1.0)) return fail(ctx, GF_EINVAL, "learned_factor in (0, 1)");
