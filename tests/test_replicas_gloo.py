@@ -82,3 +82,11 @@ def test_torchrun_two_ranks_reference_arm_single_line(tmp_path):
     assert d["impl"] == "reference" and d["n_gpus"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    # the reference arm reports on the GPU arm's metric, unit and workload
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["metric"] == bench.METRIC and d["unit"] == "site-updates/s" and d["higher_is_better"]
+    ref = bench.headline_config(2)
+    assert {k: v for k, v in d["config"].items() if k not in ("workload", "lattice")} == \
+        {k: v for k, v in ref.items() if k not in ("workload", "lattice")}
+    assert d["config"]["lattice"] == [4, 4, 4, 4]
