@@ -301,6 +301,26 @@ def test_half_sweep_touches_each_link_once_and_only_its_parity():
                                           flat[oracle.backward_site(dims, i, mu), mu])
 
 
+@pytest.mark.parametrize("gauge", [0, 1])
+def test_heatbath_site_by_site_equals_the_half_sweep(gauge):
+    """The sampled-site heatbath used at full sizes draws the same numbers as
+    the half-sweep (the Philox counter depends on the site, not on the order)."""
+    dims = (4, 4, 6, 4)
+    U = field(dims, seed=53, gseed=54)
+    V = int(np.prod(dims))
+    sites = [i for i in range(V) if oracle.site_parity(dims, i) == 0][::3]
+    per_site = oracle.sa_update_sites(U, sites, 0.7, gauge, 99, 5)
+    W = U.copy()
+    assert oracle.sa_half_sweep(W, 0, 0.7, gauge, 99, 5) == 0
+    flat = W.reshape(-1, 4, 3, 3)
+    assert np.abs(W - U).max() > 1e-2
+    for j, i in enumerate(sites):
+        for mu in range(4):
+            np.testing.assert_array_equal(per_site[j, mu], flat[i, mu])
+            np.testing.assert_array_equal(per_site[j, 4 + mu],
+                                          flat[oracle.backward_site(dims, i, mu), mu])
+
+
 def test_pure_gauge_reaches_unit_functional():
     """North-star test (a): U = g(x) g(x+mu)^dagger fixes to F = 1, theta -> 0."""
     for dims, seed in (((4, 4, 4, 4), 2), ((8, 8, 8, 8), 2), ((4, 6, 4, 8), 3)):
