@@ -133,6 +133,12 @@ int gf_set_stream(gf_ctx *ctx, void *stream);
  *                    relaxation at omega = 1.  Batches use 0.
  *   "acc_registers"  accumulate form on FP64 storage: register budget per
  *                    thread, 255, 168 or 128 (0 = autotuned or 255; default 0)
+ *   "autotune"       1 = time the candidate launch configurations (threads
+ *                    per site, accumulate form and register budget, block)
+ *                    of each storage format the first time a call sweeps it,
+ *                    and cache the fastest per (extents, format, gauge,
+ *                    overrelaxation or heatbath) for the process (default 0:
+ *                    the fixed defaults, or "threads_per_site"/"block")
  *   "use_graphs"     1 = replay sweep loops as CUDA graphs (default 1)
  *   "kernel_timing"  1 = record CUDA events (inside the graphs) around the
  *                    sweep kernels of every check chunk of gf_overrelax and
@@ -157,7 +163,11 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *value);
  *   "acc_registers", "sa_rejects";
  *   with "kernel_timing": "ms_sweep_kernels_fp32", "sweep_launches_fp32",
  *   "ms_sweep_kernels_fp64", "sweep_launches_fp64" (device time of the
- *   half-sweep kernels of each phase and the number of launches it covers). */
+ *   half-sweep kernels of each phase and the number of launches it covers);
+ *   GF_MIXED: "theta_switch_measured" (theta of the FP64 field at the switch);
+ *   with a network (gf_set_net): "theta_before_learned", "theta_after_learned"
+ *   (around the first application), "ms_learned" (wall time of all
+ *   applications), "learned_applications" (those after the first). */
 int gf_get_stat(const gf_ctx *ctx, const char *key, double *value);
 
 /* ---------------------------------------------------- the method, one call */
