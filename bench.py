@@ -367,6 +367,27 @@ def gpu_arm(args, rank, world, local):
                                                     if args.learned_repeat else 0),
                        "weights": os.path.relpath(WEIGHTS, ROOT)}
 
+    # optional: the mixed policy with FP32 restarts (option fp32_restarts), once
+    restart_row = None
+    if args.fp32_restarts > 0:
+        ctxr = make_ctx(gf, gf.GF_MIXED)
+        gf.gf_set_option(ctxr, "fp32_restarts", args.fp32_restarts)
+        gf.gf_set_option(ctxr, "theta_switch", args.restart_switch)
+        work.copy_(pristine)
+        gf.gf_overrelax(ctxr, work, OMEGA, THETA_TARGET, MAX_ITER)  # warm-up
+        work.copy_(pristine)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        convr, itr, Fr, thr_ = gf.gf_overrelax(ctxr, work, OMEGA, THETA_TARGET, MAX_ITER)
+        torch.cuda.synchronize()
+        restart_row = {"restarts_s": time.perf_counter() - t0, "restarts": args.fp32_restarts,
+                       "restart_theta_switch": args.restart_switch, "sweeps_restarts": itr,
+                       "sweeps_fp32_restarts": gf.gf_get_stat(ctxr, "sweeps_fp32"),
+                       "sweeps_fp64_phase_restarts": gf.gf_get_stat(ctxr, "sweeps_fp64"),
+                       "theta_after_restarts": gf.gf_get_stat(ctxr, "theta_after_restarts"),
+                       "F_restarts": Fr, "dF_restarts": abs(Fr - F64), "theta_restarts": thr_,
+                       "converged_restarts": convr}
+
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     host = torch.empty(pristine.shape, dtype=pristine.dtype, pin_memory=True)
     e2e_ms = 0.0
@@ -429,7 +450,7 @@ def gpu_arm(args, rank, world, local):
                           "mixed_df64_s": t_df, "sweeps_mixed_df64": itdf, "F_mixed_df64": Fdf,
                           "dF_mixed_df64": abs(Fdf - F64), "theta_mixed_df64": thdf,
                           "phase_ms": {"fp32": ms32 / args.steps, "fp64": ms64 / args.steps},
-                          **(learned_row or {})},
+                          **(learned_row or {}), **(restart_row or {})},
         "sweep_throughput": thr,
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -859,6 +880,11 @@ def main():
     ap.add_argument("--learned-factor", type=float, default=0.316,
                     help="theta falls by this factor between applications")
     ap.add_argument("--eval-fields", type=int, default=4)
+    ap.add_argument("--fp32-restarts", type=int, default=0,
+                    help="add a line for the mixed policy with this many FP32 restarts (0: none)")
+    ap.add_argument("--restart-switch", type=float, default=1e-30,
+                    help="theta_switch of the FP32-restart line (default 1e-30: the first FP32 phase "
+                         "runs to its rounding floor)")
     ap.add_argument("--save", nargs="?", const=WEIGHTS, default=None, metavar="PATH",
                     help=f"store the trained parameters (.npy; default path {os.path.relpath(WEIGHTS, ROOT)})")
     ap.add_argument("--weights", metavar="PATH",

@@ -120,6 +120,17 @@ int gf_set_stream(gf_ctx *ctx, void *stream);
  *                    up to this many times, each time theta has fallen by the
  *                    factor "learned_factor" (default 1e-2) during the FP64
  *                    phase (default 0: once, at the switch)
+ *   "fp32_restarts"  GF_MIXED (track_gauge 1, reunitarize_every 1, else
+ *                    gf_overrelax returns GF_EINVAL): after the switch, up to
+ *                    n times (0..16, default 0), the FP32 field is re-encoded
+ *                    from the FP64 field, g is reset to the identity, the FP32
+ *                    sweeps run until theta (below 1e-8) falls by less than
+ *                    10 % over 100 sweeps -- the FP32 rounding floor -- and g
+ *                    is applied to the FP64 field in FP64; FP64 sweeps then
+ *                    finish.  With n > 0 the first FP32 phase also stops at
+ *                    that floor (a tiny "theta_switch", e.g. 1e-30, sweeps
+ *                    it there).
+ *                    The result stays a gauge transform of the exact input.
  *   "theta_per_timeslice"  1 = every theta the context reports or checks
  *                    (stopping rule, gf_overrelax's output, gf_measure) is the
  *                    largest timeslice value theta_t (gf_measure_timeslices),
@@ -167,7 +178,9 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *value);
  *   GF_MIXED: "theta_switch_measured" (theta of the FP64 field at the switch);
  *   with a network (gf_set_net): "theta_before_learned", "theta_after_learned"
  *   (around the first application), "ms_learned" (wall time of all
- *   applications), "learned_applications" (those after the first). */
+ *   applications), "learned_applications" (those after the first); with
+ *   "fp32_restarts": "fp32_restarts_done", "theta_after_restarts" (theta of
+ *   the FP64 field after the last restart), "ms_restarts". */
 int gf_get_stat(const gf_ctx *ctx, const char *key, double *value);
 
 /* ---------------------------------------------------- the method, one call */

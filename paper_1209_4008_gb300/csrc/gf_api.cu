@@ -65,6 +65,7 @@ struct gf_ctx {
     int or_variant = 0;  // g -> g^omega: 0 rational 19-flop form, 1 first order, 2 exact power
     int learned_repeat = 0;       // further applications of the learned warm start in the FP64 phase
     double learned_factor = 1e-2;  // ... each after theta has fallen by this factor
+    int fp32_restarts = 0;  // GF_MIXED: FP32 stages after the first, each from the FP64 field with g reset
     int slice_theta = 0;  // 1: convergence judged on the largest theta of the timeslices
     double *dslices = nullptr;  // F_t, theta_t of the last per-timeslice measurement
     int use_graphs = 1;
@@ -397,14 +398,21 @@ static int measure_resident(gf_ctx *ctx, double *F, double *theta)
     return GF_OK;
 }
 
+// below this theta a check may declare the FP32 rounding floor reached (stall)
+constexpr double kStallTheta = 1e-8;
+
 // Alg. 1 WHILE loop on the resident field: theta known on entry; sweep in
 // chunks of check_every until theta < target or budget sweeps are spent.
+// stall: also stop once theta (below kStallTheta) has fallen by less than 10 %
+// over the last 100 sweeps -- the rounding floor of an FP32 field.
 static int converge(gf_ctx *ctx, double omega, double target, int budget, bool trackg, bool reunit, int *used,
-                    double *F, double *theta)
+                    double *F, double *theta, bool stall = false)
 {
     int fmt = ctx->resident_fmt;
     char *field = resident_base(ctx);
     int it = 0, checks = 0;
+    const int window = std::max(1, (100 + ctx->check_every - 1) / ctx->check_every);
+    std::vector<double> hist;
     while (!(*theta < target) && it < budget) {
         int n = ctx->check_every;
         if (n > budget - it) n = budget - it;
@@ -422,6 +430,11 @@ static int converge(gf_ctx *ctx, double omega, double target, int budget, bool t
         it += n;
         ++checks;
         if (!std::isfinite(*theta)) return fail(ctx, GF_EINVAL, "theta became non-finite (input not in SU(3)?)");
+        if (stall) {
+            hist.push_back(*theta);
+            const size_t m = hist.size();
+            if (*theta < kStallTheta && m > (size_t)window && *theta > 0.9 * hist[m - 1 - window]) break;
+        }
     }
     *used = it;
     ctx->stats["checks"] += checks;
@@ -682,6 +695,9 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
     } else if (k == "learned_factor") {
         if (!(v > 0.0 && v < 1.0)) return fail(ctx, GF_EINVAL, "learned_factor in (0, 1)");
         ctx->learned_factor = v;
+    } else if (k == "fp32_restarts") {
+        if (!integral || iv < 0 || iv > 16) return fail(ctx, GF_EINVAL, "fp32_restarts: 0..16");
+        ctx->fp32_restarts = iv;
     } else if (k == "theta_per_timeslice") {
         if (v != 0.0 && ctx->gauge == GF_MAG) return fail(ctx, GF_EINVAL, "theta_per_timeslice: not in the maximally Abelian gauge");
         ctx->slice_theta = v != 0.0;
@@ -743,6 +759,7 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *v)
     else if (k == "or_variant") *v = ctx->or_variant;
     else if (k == "learned_repeat") *v = ctx->learned_repeat;
     else if (k == "learned_factor") *v = ctx->learned_factor;
+    else if (k == "fp32_restarts") *v = ctx->fp32_restarts;
     else if (k == "theta_per_timeslice") *v = ctx->slice_theta;
     else if (k == "kernel_timing") *v = ctx->kernel_timing;
     else if (k == "autotune") *v = ctx->autotune;
@@ -913,6 +930,8 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
     if (!(omega > 0.0 && omega < 2.0)) return fail(ctx, GF_EINVAL, "omega must lie in (0, 2)");
     if (!(theta_target >= 0.0) || !std::isfinite(theta_target)) return fail(ctx, GF_EINVAL, "theta_target");
     if (max_iter < 0) return fail(ctx, GF_EINVAL, "max_iter < 0");
+    if (ctx->precision == GF_MIXED && ctx->fp32_restarts > 0 && !(ctx->track_gauge && ctx->reunit_every == 1))
+        return fail(ctx, GF_EINVAL, "fp32_restarts needs track_gauge 1 and reunitarize_every 1");
     ctx->stats.clear();
     ctx->kms[0] = ctx->kms[1] = 0.0;
     ctx->kn[0] = ctx->kn[1] = 0;
@@ -935,6 +954,8 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
         ms64 = now_ms() - t1;
     } else {
         bool track = ctx->precision == GF_MIXED && ctx->track_gauge;
+        // FP32 restarts: every FP32 stage, the first included, also ends at the FP32 rounding floor
+        const bool refine = ctx->precision == GF_MIXED && ctx->fp32_restarts > 0;
         double target32 = ctx->precision == GF_MIXED ? ctx->theta_switch : theta_target;
         if (theta_target > target32) target32 = theta_target;
         RET(upload(ctx, view, GF_FP32));
@@ -949,7 +970,7 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
         // reunitarise at every check when reunitarize_every == 1 (graph-fused); else every n-th check below
         bool fused = ctx->reunit_every == 1;
         if (fused || ctx->reunit_every == 0) {
-            RET(converge(ctx, omega, target32, max_iter, track, fused, &used32, &F, &theta));
+            RET(converge(ctx, omega, target32, max_iter, track, fused, &used32, &F, &theta, refine));
         } else {
             int budget = max_iter;
             while (!(theta < target32) && used32 < budget) {
@@ -980,6 +1001,33 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
                 RET(autotune_format(ctx, ctx->resident_fmt, ctx->f64, nullptr, nullptr));
             RET(measure_resident(ctx, &F, &theta));
             ctx->stats["theta_switch_measured"] = theta;
+            // "fp32_restarts" n > 0: n times, the FP32 field is re-encoded from the FP64 field, g is
+            // reset to the identity, the FP32 sweeps run to their rounding floor, and g is applied
+            // to the FP64 field in FP64.  Each stage starts g afresh, so the rounding g gathered in
+            // the stage before is not carried; the FP64 field stays a gauge transform of the input.
+            for (int r = 0; refine && r < ctx->fp32_restarts && theta > 0.0 && !(theta < theta_target); ++r) {
+                const double t3 = now_ms();
+                const int f32fmt = fmt32(ctx);
+                CK(launch_narrow(ctx->resident_fmt, ref(ctx, ctx->f64), f32fmt, ref(ctx, ctx->f32), ctx->geom,
+                                 ctx->stream));
+                CK(launch_gauge_identity(ref(ctx, ctx->gt), ctx->geom, ctx->stream));
+                ctx->resident = GF_FP32;
+                ctx->resident_fmt = f32fmt;
+                double F32 = 0.0, theta32 = 0.0;
+                RET(measure_resident(ctx, &F32, &theta32));
+                int u = 0;
+                RET(converge(ctx, omega, theta_target, max_iter - used32 - used64, true, true, &u, &F32, &theta32,
+                             true));
+                used32 += u;
+                ctx->resident = GF_FP64;
+                ctx->resident_fmt = fmt64(ctx);
+                CK(launch_gauge_transform_resident(ctx->resident_fmt, ref(ctx, ctx->f64), ref(ctx, ctx->gt),
+                                                   ctx->geom, ctx->stream));
+                RET(measure_resident(ctx, &F, &theta));
+                ctx->stats["fp32_restarts_done"] += 1;
+                ctx->stats["theta_after_restarts"] = theta;
+                ctx->stats["ms_restarts"] += now_ms() - t3;
+            }
             if (ctx->net && theta > 0.0 && !(theta < theta_target)) {
                 double t3 = now_ms();
                 RET(learned_correction(ctx, theta));

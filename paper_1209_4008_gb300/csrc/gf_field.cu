@@ -276,6 +276,19 @@ cudaError_t launch_widen(int src_fmt, FieldRef src, int dst_fmt, FieldRef dst, c
     return cudaGetLastError();
 }
 
+cudaError_t launch_narrow(int src_fmt, FieldRef src, int dst_fmt, FieldRef dst, const Geom &g, cudaStream_t s)
+{
+    int n = nblocks(8L * g.Vh, 256);
+    if (src_fmt == F64_18 && dst_fmt == F32_12) k_transcode<F64_18, F32_12><<<n, 256, 0, s>>>(src, dst, g);
+    else if (src_fmt == F64_18 && dst_fmt == F32_18) k_transcode<F64_18, F32_18><<<n, 256, 0, s>>>(src, dst, g);
+    else if (src_fmt == F64_12 && dst_fmt == F32_12) k_transcode<F64_12, F32_12><<<n, 256, 0, s>>>(src, dst, g);
+    else if (src_fmt == F64_12 && dst_fmt == F32_18) k_transcode<F64_12, F32_18><<<n, 256, 0, s>>>(src, dst, g);
+    else if (src_fmt == DF64_18 && dst_fmt == F32_12) k_transcode<DF64_18, F32_12><<<n, 256, 0, s>>>(src, dst, g);
+    else if (src_fmt == DF64_18 && dst_fmt == F32_18) k_transcode<DF64_18, F32_18><<<n, 256, 0, s>>>(src, dst, g);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gauge_identity(FieldRef gt, const Geom &g, cudaStream_t s)
 {
     k_gauge_identity<<<nblocks(2L * g.Vh, 256), 256, 0, s>>>(gt, g);

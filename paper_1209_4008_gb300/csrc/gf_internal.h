@@ -90,6 +90,8 @@ cudaError_t launch_encode(int fmt, const double *aos, FieldRef f, const Geom &g,
 cudaError_t launch_decode(int fmt, FieldRef f, const Geom &g, double *aos, cudaStream_t s);
 cudaError_t launch_reunitarize(int fmt, FieldRef f, const Geom &g, cudaStream_t s);
 cudaError_t launch_widen(int src_fmt, FieldRef src, int dst_fmt, FieldRef dst, const Geom &g, cudaStream_t s);
+// FP64-class field -> FP32 field (reunitarised in FP64, then rounded)
+cudaError_t launch_narrow(int src_fmt, FieldRef src, int dst_fmt, FieldRef dst, const Geom &g, cudaStream_t s);
 cudaError_t launch_gauge_identity(FieldRef gt, const Geom &g, cudaStream_t s);
 cudaError_t launch_apply_tracked_gauge(const double *aos, FieldRef gt, int dst_fmt, FieldRef dst, const Geom &g,
                                        cudaStream_t s);

@@ -106,6 +106,30 @@ def test_host_side_checks_of_the_added_paths(lib):
         lib.gf_destroy(h)
 
 
+def test_fp32_restarts_option_host_side(lib):
+    """The restart option's range, and the policy it needs (tracked gauge and
+    reunitarisation at every check), are checked before any device work."""
+    import numpy as np
+    h = C.c_void_p()
+    assert lib.gf_create((C.c_int * 4)(4, 4, 4, 4), gf.GF_LANDAU, C.byref(h)) == gf.GF_OK
+    try:
+        for bad in (-1.0, 17.0, 1.5):
+            assert lib.gf_set_option(h, b"fp32_restarts", bad) == gf.GF_EINVAL
+        assert lib.gf_set_option(h, b"fp32_restarts", 2.0) == gf.GF_OK
+        v = C.c_double()
+        assert lib.gf_get_option(h, b"fp32_restarts", C.byref(v)) == gf.GF_OK and v.value == 2
+        assert lib.gf_set_option(h, b"precision", float(gf.GF_MIXED)) == gf.GF_OK
+        U = np.zeros(4 ** 4 * 72)
+        it, F, th = C.c_int(), C.c_double(), C.c_double()
+        for key, val in ((b"track_gauge", 0.0), (b"reunitarize_every", 2.0)):
+            assert lib.gf_set_option(h, key, val) == gf.GF_OK
+            rc = lib.gf_overrelax(h, U.ctypes.data, 1.7, 1e-12, 10, C.byref(it), C.byref(F), C.byref(th))
+            assert rc == gf.GF_EINVAL and b"fp32_restarts" in lib.gf_last_error(h)
+            assert lib.gf_set_option(h, key, 1.0) == gf.GF_OK
+    finally:
+        lib.gf_destroy(h)
+
+
 def test_batch_handle_host_side(lib):
     b = gf.gf_batch_create([(4, 4, 4, 4), (8, 8, 8, 8)], gf.GF_LANDAU)
     gf.gf_batch_set_option(b, "precision", gf.GF_FP64)
