@@ -135,8 +135,8 @@ int gf_set_stream(gf_ctx *ctx, void *stream);
  *                    (stopping rule, gf_overrelax's output, gf_measure) is the
  *                    largest timeslice value theta_t (gf_measure_timeslices),
  *                    so that every timeslice reaches the target (default 0)
- *   "or_variant"     reading of the exponent g -> g^omega (Sec. 2, "to first
- *                    or second order"): 0 = the 19-flop rational form b =
+ *   "or_variant"     reading of the exponent g -> g^omega (Sec. 2 leaves its
+ *                    order open): 0 = the 19-flop rational form b =
  *                    (omega a0^2 + |a|^2)/(a0^2 + |a|^2), r = (a0, b a)/norm
  *                    (default; the count of Alg. 1), 1 = first order,
  *                    normalise((1 - omega) 1 + omega k/|k|), 2 = the exact

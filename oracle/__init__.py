@@ -164,7 +164,7 @@ def _check(rc: int, what: str) -> None:
 def set_or_variant(v: int) -> None:
     """Reading of g -> g^omega for every later overrelaxation call of this
     process: 0 = the 19-flop rational form (default), 1 = first order,
-    2 = the exact power (Sec. 2, "to first or second order")."""
+    2 = the exact power (Sec. 2 leaves the order of the exponent open)."""
     _check(lib().oracle_set_or_variant(int(v)), "or variant")
     with _lock:
         counting = _libs.get("liboracle_count.so")

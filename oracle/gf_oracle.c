@@ -13,7 +13,7 @@
  * with its reason in the design notes of the repository):
  *   - periodic boundaries, all extents even; RED = even parity, updated first;
  *   - SU(2) subgroups visited in the order (0,1), (1,2), (0,2);
- *   - the exponent g -> g^omega (Sec. 2, "to first or second order") is taken
+ *   - the exponent g -> g^omega (Sec. 2 leaves its order open) is taken
  *     as the 19-flop rational form: b = (w a0^2 + |a|^2)/(a0^2 + |a|^2),
  *     r = (a0, b a)/sqrt(a0^2 + b^2 |a|^2) (equals relaxation at w = 1);
  *   - F is normalised by 1/(Nc Nd V) so that the unit field has F = 1;
@@ -229,15 +229,10 @@ static void su2_matrix(const double r[4], cplx R[2][2])
 }
 
 /*
- * Overrelaxation exponent g -> g^omega followed by the projection back to
- * SU(2) (Alg. 1, "19 Flop"; Sec. 2 on the overrelaxation of Mandula and
- * Ogilvie).  Input: the unnormalised quaternion k.  Output: r in SU(2).
- * Returns 0 (and leaves r untouched) when k = 0.
- */
-/*
- * The paper leaves open how g^omega is formed ("to first or second order",
- * Sec. 2); three readings are selectable (one process-wide setting):
- *   0: the 19-flop rational form above (default; matches Alg. 1's count);
+ * The paper leaves open to which order g^omega is formed (Sec. 2); three
+ * readings are selectable (one process-wide setting):
+ *   0: the 19-flop rational form b = (w a0^2 + |a|^2)/(a0^2 + |a|^2),
+ *      r = (a0, b a)/sqrt(a0^2 + b^2 |a|^2) (default; Alg. 1's count);
  *   1: first order, r = normalise((1 - omega) 1 + omega k/|k|);
  *   2: the exact power: with k/|k| = (cos phi, sin phi n), r = (cos(omega phi),
  *      sin(omega phi) n), phi in [0, pi]; the subgroup is left unchanged when
@@ -285,6 +280,13 @@ static int overrelax_exact_power(const double k[4], double omega, double r[4])
     return 1;
 }
 
+/*
+ * Overrelaxation exponent g -> g^omega followed by the projection back to
+ * SU(2) (Alg. 1's 19-flop step; Sec. 2 on the overrelaxation of Mandula and
+ * Ogilvie), in the reading selected above.  Input: the unnormalised
+ * quaternion k.  Output: r in SU(2).  Returns 0 (and leaves r untouched)
+ * when k = 0.
+ */
 static int overrelax_quaternion(const double k[4], double omega, double r[4])
 {
     if (g_or_variant == 1) return overrelax_first_order(k, omega, r);
@@ -355,7 +357,7 @@ static void star_store(double *U, const lattice *g, long i, const star *s)
  * Quaternion of the subgroup (a,b) block of
  *     M(x) = sum_mu [ U_mu(x) + U_mu(x-mu)^dagger ]
  * i.e. of K(x) of eq. (Kx) with the current gauge transformation already
- * absorbed into the links (Alg. 1 first step, "60 Flop" for nk = 4:
+ * absorbed into the links (Alg. 1 first step, 60 flop for nk = 4:
  * 8 x 4 flop per link, 7 x 4 flop to sum).
  */
 static void star_quaternion(const star *s, int nk, int a, int b, double k[4])

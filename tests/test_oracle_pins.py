@@ -500,7 +500,7 @@ def test_stochastic_relaxation_fixes_the_gauge():
 
 
 # ---------------------------------------------------------------------------
-# readings of g -> g^omega (Sec. 2, "to first or second order")
+# readings of g -> g^omega (Sec. 2 leaves the order of the exponent open)
 # ---------------------------------------------------------------------------
 @pytest.fixture
 def or_variant():
