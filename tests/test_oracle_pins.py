@@ -321,6 +321,56 @@ def test_heatbath_site_by_site_equals_the_half_sweep(gauge):
                                           flat[oracle.backward_site(dims, i, mu), mu])
 
 
+def constant_field(dims, D):
+    Lx, Ly, Lz, Lt = dims
+    return np.broadcast_to(np.asarray(D, complex), (Lt, Lz, Ly, Lx, 4, 3, 3)).copy()
+
+
+@pytest.mark.parametrize("or_variant", [0, 1, 2])
+def test_unit_field_is_a_fixed_point(or_variant):
+    """Every subgroup quaternion of the unit field is (4, 0, 0, 0) > 0, whose
+    relaxation element is the identity: sweeps leave it exactly unchanged."""
+    U = constant_field((4, 4, 4, 6), np.eye(3))
+    assert oracle.functional(U, 0) == 1.0 and oracle.theta(U, 0) == 0.0
+    W = U.copy()
+    try:
+        oracle.set_or_variant(or_variant)
+        oracle.or_sweeps(W, 1.7, 0, 3)
+    finally:
+        oracle.set_or_variant(0)
+    np.testing.assert_array_equal(W, U)
+
+
+@pytest.mark.parametrize("or_variant", [0, 1, 2])
+def test_degenerate_subgroups_of_a_constant_diagonal_field(or_variant):
+    """All links D = diag(i, i, -1): M(x) = 4 D + 4 D^dagger = diag(0, 0, -8).
+    Subgroup (0,1): the block vanishes, k = 0, no change.  Subgroup (1,2):
+    k = (-8, 0, 0, 0), relaxation element -1 (a rotation by pi); the rational
+    and first-order readings give R = -1 (rows 1, 2 of forward links and
+    columns 1, 2 of backward links change sign), the exact power has no axis
+    there and changes nothing.  Every link touches one even site, so after the
+    even half-sweep every link is D' = diag(i, -i, 1) (readings 0, 1), whose
+    subgroup quaternions are all 0 or positive: a fixed point with theta = 0
+    but F = 1/3 -- theta vanishes at stationary points that are not maxima."""
+    dims = (4, 4, 4, 6)
+    D = np.diag([1j, 1j, -1.0])
+    Dp = np.diag([1j, -1j, 1.0])
+    U = constant_field(dims, D)
+    assert oracle.theta(U, 0) == 0.0 and oracle.functional(U, 0) == pytest.approx(-1 / 3, abs=1e-15)
+    W = U.copy()
+    try:
+        oracle.set_or_variant(or_variant)
+        oracle.or_half_sweep(W, 0, 1.7, 0)
+        expect = constant_field(dims, D if or_variant == 2 else Dp)
+        np.testing.assert_allclose(W, expect, atol=1e-15)
+        oracle.or_sweeps(W, 1.7, 0, 2)
+        np.testing.assert_allclose(W, expect, atol=1e-15)
+    finally:
+        oracle.set_or_variant(0)
+    assert oracle.theta(W, 0) == 0.0
+    assert oracle.functional(W, 0) == pytest.approx(-1 / 3 if or_variant == 2 else 1 / 3, abs=1e-15)
+
+
 def test_pure_gauge_reaches_unit_functional():
     """North-star test (a): U = g(x) g(x+mu)^dagger fixes to F = 1, theta -> 0."""
     for dims, seed in (((4, 4, 4, 4), 2), ((8, 8, 8, 8), 2), ((4, 6, 4, 8), 3)):
