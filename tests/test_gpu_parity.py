@@ -762,3 +762,45 @@ def test_generate_matches_oracle_and_thermalises():
     assert np.mean(vals) == pytest.approx(0.5937, abs=6e-3)
     M = host(d8).reshape(-1, 3, 3)
     assert np.abs(M @ np.conj(np.swapaxes(M, -1, -2)) - np.eye(3)).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# degenerate subgroups: k = 0 and k along -1 (a constant diagonal field)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("form", ["acc", "tps1", "tps8", "df64", "fp32"])
+def test_degenerate_subgroups_match_oracle(oracle_or_variant, variant, form):
+    """All links diag(i, i, -1): subgroup (0,1) has k = 0 (no change) and
+    subgroup (1,2) has k = (-8, 0, 0, 0) (rotation by pi, or no change for the
+    exact power); the oracle pins give the result, diag(i, -i, 1) everywhere
+    after one half-sweep for the rational and first-order readings."""
+    dims = (4, 4, 4, 6)
+    Lx, Ly, Lz, Lt = dims
+    D = np.diag([1j, 1j, -1.0])
+    U = np.broadcast_to(D, (Lt, Lz, Ly, Lx, 4, 3, 3)).copy()
+    opts = {"or_variant": variant}
+    prec = gf.GF_FP64
+    if form == "acc":
+        opts["variant"] = 2
+    elif form.startswith("tps"):
+        opts.update(variant=1, threads_per_site=int(form[3:]))
+    elif form == "df64":
+        opts["fp64_arith"] = 1
+    else:
+        prec = gf.GF_FP32
+    c = ctx_for(dims, 0, **opts)
+    gf.gf_upload(c, dev(U), prec)
+    oracle_or_variant(variant)
+    W = U.copy()
+    for p in (0, 1, 0, 1):
+        gf.gf_or_half_sweep(c, p, 1.7)
+        oracle.or_half_sweep(W, p, 1.7, 0)
+    d = torch.empty_like(dev(U))
+    gf.gf_download(c, d)
+    # FP32: the reciprocal square root of the rotation by pi rounds (6e-8 per step, a
+    # few dozen steps): the multi-sweep FP32 bound of this file
+    tol = 2e-5 if prec == gf.GF_FP32 else 1e-12
+    expect = np.broadcast_to(D if variant == 2 else np.diag([1j, -1j, 1.0]), U.shape)
+    assert np.abs(W - expect).max() < 1e-15
+    assert np.abs(host(d) - W).max() < tol
+    gf.gf_destroy(c)
