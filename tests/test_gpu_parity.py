@@ -804,3 +804,39 @@ def test_degenerate_subgroups_match_oracle(oracle_or_variant, variant, form):
     assert np.abs(W - expect).max() < 1e-15
     assert np.abs(host(d) - W).max() < tol
     gf.gf_destroy(c)
+
+
+# ---------------------------------------------------------------------------
+# the smallest extents: with L = 2, x + mu and x - mu are the same site
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 2, 6)])
+@pytest.mark.parametrize("gauge", [0, 1])
+@pytest.mark.parametrize("form", ["acc", "tps2", "tps8", "df64", "fp32"])
+def test_extent_two_half_sweeps_match_oracle(dims, gauge, form):
+    U = cpu_field(dims, seed=5, gseed=6)
+    opts = {}
+    prec = gf.GF_FP64
+    if form == "acc":
+        opts["variant"] = 2
+    elif form.startswith("tps"):
+        opts.update(variant=1, threads_per_site=int(form[3:]))
+    elif form == "df64":
+        opts["fp64_arith"] = 1
+    else:
+        prec = gf.GF_FP32
+    c = ctx_for(dims, gauge, **opts)
+    gf.gf_upload(c, dev(U), prec)
+    W = U.copy()
+    for p in (0, 1):
+        gf.gf_or_half_sweep(c, p, 1.7)
+        oracle.or_half_sweep(W, p, 1.7, gauge)
+    d = torch.empty_like(dev(U))
+    gf.gf_download(c, d)
+    if prec == gf.GF_FP32:
+        assert np.abs(host(d) - W).max() < 5e-6 * 2
+    else:
+        assert max_rel(host(d), W) < 1e-12
+    F, th = gf.gf_measure(c)
+    # FP32 storage is measured from its FP32 values (row 2 rebuilt in FP32)
+    assert F == pytest.approx(oracle.functional(host(d), gauge), abs=1e-6 if prec == gf.GF_FP32 else 1e-13)
+    gf.gf_destroy(c)

@@ -373,7 +373,9 @@ def test_degenerate_subgroups_of_a_constant_diagonal_field(or_variant):
 
 def test_pure_gauge_reaches_unit_functional():
     """North-star test (a): U = g(x) g(x+mu)^dagger fixes to F = 1, theta -> 0."""
-    for dims, seed in (((4, 4, 4, 4), 2), ((8, 8, 8, 8), 2), ((4, 6, 4, 8), 3)):
+    # (extent 2 is the smallest lattice: x + mu and x - mu are the same site)
+    for dims, seed in (((4, 4, 4, 4), 2), ((8, 8, 8, 8), 2), ((4, 6, 4, 8), 3), ((2, 2, 2, 2), 2),
+                       ((2, 4, 2, 6), 3)):
         U = field(dims, gseed=seed, pure=True)
         conv, it, F, th = oracle.overrelax(U, 0, 1.7, 1e-24, 20000, 10)
         assert conv and th < 1e-24
