@@ -426,6 +426,202 @@ cudaError_t conv_tc(const bf16 *X, int I, const bf16 *W, int O, const float *b, 
 
 
 // ---------------------------------------------------------------------------
+// halo-tile convolution on the tensor cores (net option "conv_halo"): a CTA
+// computes an 8 (x) x 16 (y) tile of one (z, t) plane, M = 128 rows with row
+// r = x + 8 y.  Per 16-channel chunk of the input it stages the tile's periodic
+// halo (10 x 18 x 3 x 3 sites) once in shared memory, K-major without swizzle:
+// the 8 consecutive x positions of a y line form one core matrix (8 rows x
+// 16 B), consecutive y lines are 160 B apart (SBO) and the two 8-channel core
+// columns HS * 16 B apart (LBO).  The A operand of tap d is then the same
+// array from a different start address, so nothing is gathered per tap; the
+// weights of one slab of 27 taps (fixed dt) are staged per phase.  Phases run
+// one after another (a CTA waits for its MMAs before restaging); two CTAs per
+// SM overlap one's staging with the other's MMAs.  Needs Lx % 8 == 0 and
+// Ly % 16 == 0; other lattices use k_conv_tc.
+// ---------------------------------------------------------------------------
+namespace halo {
+constexpr int TX = 8, TY = 16, HX = TX + 2, HY = TY + 2, HZ = 3, HT = 3;
+constexpr int HS = HX * HY * HZ * HT;  // 1620 halo sites
+constexpr int LBO_A = HS * 16;         // between the two 8-channel core columns
+constexpr int SBO_A = HX * 16;         // between consecutive y lines (8-row groups)
+constexpr int A_BYTES = 2 * LBO_A;
+}  // namespace halo
+
+template <int N>
+struct HaloLayout {
+    static constexpr int W_BYTES = 27 * N * 32;  // 27 taps x N outputs x 16 BF16 channels
+    static constexpr int BAR_OFF = halo::A_BYTES + W_BYTES;
+    static constexpr int SMEM = BAR_OFF + 2 * 8 + 16;
+};
+
+static bool halo_ok(const Lat &g) { return g.L[0] % halo::TX == 0 && g.L[1] % halo::TY == 0; }
+
+template <int IP, int N>
+__global__ void __launch_bounds__(128) k_conv_halo_tc(const bf16 *__restrict__ X, int I, const bf16 *__restrict__ W,
+                                                      int O, const float *__restrict__ bias, Lat g, int sign, int relu,
+                                                      const bf16 *__restrict__ mask, bf16 *__restrict__ Yb,
+                                                      float *__restrict__ Yf, int *__restrict__ err)
+{
+    using namespace gf::tc;
+    using namespace halo;
+    typedef HaloLayout<N> LY;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *A = smem;
+    uint8_t *B = smem + A_BYTES;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);  // [0] per phase, [1] final drain
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + 16);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    constexpr uint32_t idesc = instr_desc(kM, N);
+    constexpr int NPHASE = (IP / 16) * 3;  // (16-channel chunk, dt slab)
+
+    int b = blockIdx.x;
+    const int nbx = g.L[0] / TX, nby = g.L[1] / TY;
+    const int x0 = (b % nbx) * TX;
+    b /= nbx;
+    const int y0 = (b % nby) * TY;
+    b /= nby;
+    const int z0 = b % g.L[2];
+    const int t0 = b / g.L[2];
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    bool fail = false;
+    for (int ph = 0; ph < NPHASE; ++ph) {
+        const int cc = ph / 3, slab = ph % 3;
+        // the MMAs of the previous phase read A and B: wait for them before restaging
+        if (ph > 0 && !mbar_wait(&bar[0], (uint32_t)((ph - 1) & 1))) fail = true;
+        if (__syncthreads_or(fail)) {
+            fail = true;
+            break;
+        }
+        if (slab == 0) {
+            // halo of the tile, channels 16 cc .. 16 cc + 15; adjacent threads take the two
+            // 16-byte halves of one site's 32 bytes
+            for (int w = tid; w < 2 * HS; w += kThreads) {
+                const int kc = w & 1, hs = w >> 1;
+                const int hx = hs % HX;
+                int l = hs / HX;
+                const int hy = l % HY;
+                l /= HY;
+                const int hz = l % HZ, ht = l / HZ;
+                const long x = wrap_coord(x0 - 1 + hx, g.L[0]);
+                const long y = wrap_coord(y0 - 1 + hy, g.L[1]);
+                const long z = wrap_coord(z0 - 1 + hz, g.L[2]);
+                const long t = wrap_coord(t0 - 1 + ht, g.L[3]);
+                const long site = x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
+                const int ch = 16 * cc + 8 * kc;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (ch < I) v = *reinterpret_cast<const uint4 *>(X + site * I + ch);
+                *reinterpret_cast<uint4 *>(A + kc * LBO_A + hs * 16) = v;
+            }
+        }
+        // weights of the 27 taps of this slab, the same 16 channels: tap j's B at
+        // j * N * 32, core (mr, kc) at (kc * (N/8) + mr) * 128 -> SBO 128, LBO N * 16
+        for (int w = tid; w < 27 * N * 2; w += kThreads) {
+            const int kc = w & 1, r = w >> 1;
+            const int o = r % N, j = r / N;
+            const int ch = 16 * cc + 8 * kc;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (o < O && ch < I) v = *reinterpret_cast<const uint4 *>(W + ((long)(27 * slab + j) * O + o) * I + ch);
+            *reinterpret_cast<uint4 *>(B + j * N * 32 + (kc * (N / 8) + (o >> 3)) * 128 + (o & 7) * 16) = v;
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after_sync();
+            const int dt = sign * (slab - 1);
+            for (int j = 0; j < 27; ++j) {
+                const int dx = sign * (j % 3 - 1), dy = sign * ((j / 3) % 3 - 1), dz = sign * (j / 9 - 1);
+                // first halo line of the shifted tile; x offset dx + 1 within the line
+                const int l0 = (dy + 1) + HY * ((dz + 1) + HZ * (dt + 1));
+                const uint64_t ad = smem_desc(smem_u32(A + (l0 * HX + dx + 1) * 16), LBO_A, SBO_A);
+                const uint64_t bd = smem_desc(smem_u32(B + j * N * 32), (N / 8) * 128, 128);
+                mma_bf16(tmem, ad, bd, idesc, (ph | j) != 0);
+            }
+            mma_commit(&bar[0]);
+        }
+    }
+    // all MMAs issued by thread 0 are complete once the final commit arrives
+    if (tid == 0) mma_commit(&bar[1]);
+    if (!mbar_wait(&bar[1], 0)) fail = true;
+    fail = __syncthreads_or(fail);
+    if (!fail) {
+        fence_after_sync();
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        if (N == 32) {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+        } else {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+                " [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // accumulator row tid = x + 8 y of the tile
+        const long site = (x0 + (tid & 7)) + (long)g.L[0] * ((y0 + (tid >> 3)) + (long)g.L[1] * (z0 + (long)g.L[2] * t0));
+#pragma unroll
+        for (int o = 0; o < N; ++o) {
+            if (o >= O) break;
+            float v = __uint_as_float(r[o]) + (bias ? bias[o] : 0.0f);
+            if (relu) v = v > 0.0f ? v : 0.0f;
+            if (mask && !(__bfloat162float(mask[site * O + o]) > 0.0f)) v = 0.0f;
+            if (Yb) Yb[site * O + o] = __float2bfloat16(v);
+            if (Yf) Yf[site * O + o] = v;
+        }
+    } else if (tid == 0) {
+        atomicExch(err, GF_ETIMEOUT);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    }
+}
+
+template <int IP, int N>
+cudaError_t conv_halo_tc(const bf16 *X, int I, const bf16 *W, int O, const float *b, const Lat &g, int sign, int relu,
+                         const bf16 *mask, bf16 *Yb, float *Yf, int *err, cudaStream_t s)
+{
+    typedef HaloLayout<N> LY;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_conv_halo_tc<IP, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, LY::SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int blocks = (g.L[0] / halo::TX) * (g.L[1] / halo::TY) * g.L[2] * g.L[3];
+    k_conv_halo_tc<IP, N><<<blocks, gf::tc::kThreads, LY::SMEM, s>>>(X, I, W, O, b, g, sign, relu, mask, Yb, Yf, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // weight gradient on the tensor cores:
 //   dW[k][o][i] = sum_s dY[s][o] X[s + d(k)][i]
 // as D[(tap, i)][o] = sum_s A[(tap, i)][s] B[o][s] with M = 128 rows (TG taps x
@@ -648,6 +844,7 @@ struct gf_net {
     double *partial = nullptr, *dloss = nullptr;
     int *derr = nullptr;  // tensor-core kernels: bounded-wait expiry
     int use_tc = 1;       // forward and backward-data on tcgen05 (else CUDA cores)
+    int use_halo = 0;     // ... with the halo-tile kernel where the extents allow it
     int step = 0;
     std::string err;
 };
@@ -685,20 +882,30 @@ static int refresh_weights(gf_net *n)
     return GF_OK;
 }
 
+// forward / backward-data convolution on the tensor cores: the halo-tile kernel
+// when selected and the extents allow it, else the per-tap gather kernel
+template <int IP, int N>
+static cudaError_t conv_tensor(const gf_net *n, const bf16 *X, int I, const bf16 *W, int O, const float *b, int sign,
+                               int relu, const bf16 *mask, bf16 *Yb, float *Yf)
+{
+    if (n->use_halo && halo_ok(n->g))
+        return conv_halo_tc<IP, N>(X, I, W, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->stream);
+    return conv_tc<IP, N>(X, I, W, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->stream);
+}
+
 static int forward(gf_net *n, const bf16 *f)
 {
     const Lat &g = n->g;
     cudaStream_t s = n->stream;
     n->act[0] = const_cast<bf16 *>(f);
     if (n->use_tc) {
-        NCK((conv_tc<80, 32>(f, 80, n->Wb[0], 32, n->params + n->boff[0], g, 1, 1, nullptr, n->act[1], nullptr,
-                             n->derr, s)));
-        NCK((conv_tc<32, 32>(n->act[1], 32, n->Wb[1], 32, n->params + n->boff[1], g, 1, 1, nullptr, n->act[2],
-                             nullptr, n->derr, s)));
-        NCK((conv_tc<32, 32>(n->act[2], 32, n->Wb[2], 32, n->params + n->boff[2], g, 1, 1, nullptr, n->act[3],
-                             nullptr, n->derr, s)));
-        NCK((conv_tc<32, 16>(n->act[3], 32, n->Wb[3], 8, n->params + n->boff[3], g, 1, 0, nullptr, nullptr, n->out,
-                             n->derr, s)));
+        NCK((conv_tensor<80, 32>(n, f, 80, n->Wb[0], 32, n->params + n->boff[0], 1, 1, nullptr, n->act[1], nullptr)));
+        NCK((conv_tensor<32, 32>(n, n->act[1], 32, n->Wb[1], 32, n->params + n->boff[1], 1, 1, nullptr, n->act[2],
+                                 nullptr)));
+        NCK((conv_tensor<32, 32>(n, n->act[2], 32, n->Wb[2], 32, n->params + n->boff[2], 1, 1, nullptr, n->act[3],
+                                 nullptr)));
+        NCK((conv_tensor<32, 16>(n, n->act[3], 32, n->Wb[3], 8, n->params + n->boff[3], 1, 0, nullptr, nullptr,
+                                 n->out)));
         return GF_OK;
     }
     NCK((conv_cc<80, 32>(f, n->Wb[0], n->params + n->boff[0], g, 1, 1, nullptr, n->act[1], nullptr, s)));
@@ -714,10 +921,10 @@ static int backward_data(gf_net *n, int l, const bf16 *dY, bf16 *dX)
     const Lat &g = n->g;
     cudaStream_t s = n->stream;
     if (l == 3) {
-        if (n->use_tc) NCK((conv_tc<16, 32>(dY, 8, n->Wt[3], 32, nullptr, g, -1, 0, n->act[3], dX, nullptr, n->derr, s)));
+        if (n->use_tc) NCK((conv_tensor<16, 32>(n, dY, 8, n->Wt[3], 32, nullptr, -1, 0, n->act[3], dX, nullptr)));
         else NCK((conv_cc<8, 32>(dY, n->Wt[3], nullptr, g, -1, 0, n->act[3], dX, nullptr, s)));
     } else {
-        if (n->use_tc) NCK((conv_tc<32, 32>(dY, 32, n->Wt[l], 32, nullptr, g, -1, 0, n->act[l], dX, nullptr, n->derr, s)));
+        if (n->use_tc) NCK((conv_tensor<32, 32>(n, dY, 32, n->Wt[l], 32, nullptr, -1, 0, n->act[l], dX, nullptr)));
         else NCK((conv_cc<32, 32>(dY, n->Wt[l], nullptr, g, -1, 0, n->act[l], dX, nullptr, s)));
     }
     return GF_OK;
@@ -905,6 +1112,10 @@ int gf_net_set_option(gf_net *n, const char *key, double value)
     if (!n || !key) return GF_EINVAL;
     if (std::string(key) == "tensor_cores") {
         n->use_tc = value != 0.0;
+        return GF_OK;
+    }
+    if (std::string(key) == "conv_halo") {
+        n->use_halo = value != 0.0;
         return GF_OK;
     }
     return nfail(n, GF_EINVAL, std::string("unknown option ") + key);
