@@ -23,7 +23,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_BUILD = os.path.join(_HERE, "_build")
+# ORACLE_SOURCE_DIR (tests only): build from another copy of the C sources; the
+# mutation tests plant mistakes in such a copy and check that the pins fail
+_SRC_DIR = os.environ.get("ORACLE_SOURCE_DIR") or _HERE
+_BUILD = os.path.join(_SRC_DIR, "_build")
 _SOURCES = ["gf_oracle.c", "conv_oracle.c"]
 _lock = threading.Lock()
 _libs: dict[str, C.CDLL] = {}
@@ -37,7 +40,7 @@ _u32p = C.POINTER(C.c_uint32)
 def _compile(name: str, extra: list[str]) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     out = os.path.join(_BUILD, name)
-    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    srcs = [os.path.join(_SRC_DIR, s) for s in _SOURCES]
     if os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in srcs):
         return out
     tmp = out + f".tmp{os.getpid()}"

@@ -1,0 +1,114 @@
+"""The pins pin: plausible mistakes planted in a copy of the oracle make them fail.
+
+Each case copies the oracle's C sources to a temporary directory, replaces one
+line with a plausible mistake (a dropped term, a wrong sign or index, a
+transposed operand, a wrong constant), checks that the copy still compiles,
+and runs the oracle pin tests against it (environment ORACLE_SOURCE_DIR).
+The case passes when the pins fail.  All on the CPU; nothing here touches a
+GPU or the library.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+SOURCES = ("gf_oracle.c", "conv_oracle.c")
+
+# (name, file, original text, planted mistake)
+MUTATIONS = [
+    ("quaternion sign", "gf_oracle.c",
+     "k[1] = -(w01.im + w10.im);", "k[1] = (w01.im + w10.im);"),
+    ("quaternion transposed operands", "gf_oracle.c",
+     "k[2] = w10.re - w01.re;", "k[2] = w01.re - w10.re;"),
+    ("su2 matrix sign", "gf_oracle.c",
+     "R[1][0] = c_make(-r[2], r[1]);", "R[1][0] = c_make(r[2], r[1]);"),
+    ("omega on the wrong term", "gf_oracle.c",
+     "double b = (omega * a0sq + aisq) / (a0sq + aisq);", "double b = (a0sq + omega * aisq) / (a0sq + aisq);"),
+    ("backward rotation without dagger", "gf_oracle.c",
+     "cplx r00 = c_conj(R[0][0]), r01 = c_conj(R[0][1]);", "cplx r00 = R[0][0], r01 = R[0][1];"),
+    ("backward link at x + mu", "gf_oracle.c",
+     "s->bwd[mu] = mat_load(link_cptr(U, site_shift(g, i, mu, -1), mu));",
+     "s->bwd[mu] = mat_load(link_cptr(U, site_shift(g, i, mu, +1), mu));"),
+    ("backward block not transposed", "gf_oracle.c",
+     "block_quaternion(c_conj(w->m[a][a]), c_conj(w->m[b][a]), c_conj(w->m[a][b]),",
+     "block_quaternion(c_conj(w->m[a][a]), c_conj(w->m[a][b]), c_conj(w->m[b][a]),"),
+    ("Coulomb gauge with temporal links", "gf_oracle.c",
+     "static int gauge_nk(int gauge) { return gauge == 1 ? 3 : 4; }",
+     "static int gauge_nk(int gauge) { return gauge == 1 ? 4 : 4; }"),
+    ("functional normalisation", "gf_oracle.c",
+     "return sum / (3.0 * nk * (double)g.V);", "return sum / (3.0 * 4 * (double)g.V);"),
+    ("theta without the 1/2", "gf_oracle.c",
+     "A.m[a][b] = c_make(0.5 * z.im, -0.5 * z.re);", "A.m[a][b] = c_make(z.im, -z.re);"),
+    ("theta not traceless", "gf_oracle.c",
+     "c_sub(Af.m[a][b], Ab.m[a][b]));\n        }\n        make_traceless(&D);",
+     "c_sub(Af.m[a][b], Ab.m[a][b]));\n        }"),
+    ("gauge transform with g(x) on both ends", "gf_oracle.c",
+     "mat3 gy = mat_load(gfield + site_shift(&g, i, mu, +1) * 18);", "mat3 gy = mat_load(gfield + i * 18);"),
+    ("Philox key schedule constant", "gf_oracle.c",
+     "k[1] += 0xBB67AE85u;", "k[1] += 0xBB67AE87u;"),
+    ("Creutz draw support", "gf_oracle.c",
+     "double e = exp(-2.0 * alpha);", "double e = exp(-alpha);"),
+    ("Kennedy-Pendleton scale", "gf_oracle.c",
+     "double lam2 = -(log(u01(w[0])) + c * c * log(u01(w[2]))) / (2.0 * alpha);",
+     "double lam2 = -(log(u01(w[0])) + c * c * log(u01(w[2]))) / alpha;"),
+    ("heatbath direction not on the sphere", "gf_oracle.c",
+     "double s[4] = { s0, rho * st * cos(phi), rho * st * sin(phi), rho * ct };",
+     "double s[4] = { s0, rho * cos(phi), rho * sin(phi), rho * ct };"),
+    ("stochastic relaxation probability inverted", "gf_oracle.c",
+     "if (u01(w[0]) < p) {", "if (u01(w[0]) >= p) {"),
+    ("maximally Abelian weight of an off-diagonal entry", "gf_oracle.c",
+     "return c_abs2(u->m[a][a]) + c_abs2(u->m[b][b]);", "return c_abs2(u->m[a][a]) + c_abs2(u->m[a][b]);"),
+    ("maximally Abelian polarisation factor", "gf_oracle.c",
+     "A[k][m] = A[m][k] = 0.25 * (", "A[k][m] = A[m][k] = 0.5 * ("),
+    ("lower staple product order", "gf_oracle.c",
+     "mat3 t2 = mat_mul(&dd, &ed);", "mat3 t2 = mat_mul(&ed, &dd);"),
+    ("convolution taps transposed", "conv_oracle.c",
+     "int d[4] = { k % 3 - 1, (k / 3) % 3 - 1, (k / 9) % 3 - 1, (k / 27) % 3 - 1 };",
+     "int d[4] = { (k / 3) % 3 - 1, k % 3 - 1, (k / 9) % 3 - 1, (k / 27) % 3 - 1 };"),
+    ("convolution backward data with the forward shift", "conv_oracle.c",
+     "const double *dy = dY + shifted(&g, s, k, -1) * cout;", "const double *dy = dY + shifted(&g, s, k, +1) * cout;"),
+]
+
+
+def _pins_on_copy(tmp_path, mutation=None):
+    """Copy the sources (with the mutation applied), build them where the oracle
+    module looks for them, run the pins against the copy; the pytest exit code."""
+    for f in SOURCES:
+        shutil.copy(os.path.join(ORACLE, f), tmp_path / f)
+    if mutation is not None:
+        fname, old, new = mutation
+        path = tmp_path / fname
+        text = path.read_text()
+        assert text.count(old) == 1, f"mutation site not unique or missing: {old!r}"
+        path.write_text(text.replace(old, new))
+    # the copy must compile, so that a failing pin run means a caught mistake
+    srcs = [str(tmp_path / f) for f in SOURCES]
+    os.makedirs(tmp_path / "_build")
+    cc = subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-Wall",
+                         "-Wno-unused-function", "-fopenmp", *srcs, "-o", str(tmp_path / "_build" / "liboracle.so"),
+                         "-lm"], capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr[-2000:]
+    env = dict(os.environ, ORACLE_SOURCE_DIR=str(tmp_path), CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+           os.path.join(ROOT, "tests", "test_conv_oracle.py"), "-x", "-q", "-m", "not gpu",
+           "-p", "no:cacheprovider"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=str(tmp_path), env=env)
+    return r.returncode, r.stdout
+
+
+def test_unmodified_copy_passes_the_pins(tmp_path):
+    """Control: the same procedure on an unmodified copy passes, so a failure
+    below is the planted mistake's doing."""
+    rc, out = _pins_on_copy(tmp_path)
+    assert rc == 0, out[-3000:]
+
+
+@pytest.mark.parametrize("name,fname,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_the_pins(tmp_path, name, fname, old, new):
+    rc, out = _pins_on_copy(tmp_path, (fname, old, new))
+    # pytest exit code 1: tests ran and some failed (2+ would be an interrupted or broken run)
+    assert rc == 1, f"the pins did not catch '{name}':\n{out[-3000:]}"
