@@ -7,6 +7,7 @@ and runs the oracle pin tests against it (environment ORACLE_SOURCE_DIR).
 The case passes when the pins fail.  All on the CPU; nothing here touches a
 GPU or the library.
 """
+import concurrent.futures as cf
 import os
 import shutil
 import subprocess
@@ -66,6 +67,30 @@ MUTATIONS = [
      "A[k][m] = A[m][k] = 0.25 * (", "A[k][m] = A[m][k] = 0.5 * ("),
     ("lower staple product order", "gf_oracle.c",
      "mat3 t2 = mat_mul(&dd, &ed);", "mat3 t2 = mat_mul(&ed, &dd);"),
+    ("exact-power reading ignores omega", "gf_oracle.c",
+     "double c = cos(omega * phi), sn = sin(omega * phi);", "double c = cos(phi), sn = sin(phi);"),
+    ("first-order reading drops omega on k", "gf_oracle.c",
+     "double v[4] = { (1.0 - omega) + omega * (k[0] / n),", "double v[4] = { (1.0 - omega) + (k[0] / n),"),
+    ("timeslice functional normalisation", "gf_oracle.c",
+     "F_t[t] = fs / (3.0 * nk * (double)Ls);", "F_t[t] = fs / (3.0 * 4 * (double)Ls);"),
+    ("driver sweeps once per check", "gf_oracle.c",
+     "oracle_or_sweeps(U, dims, omega, gauge, n);", "oracle_or_sweeps(U, dims, omega, gauge, 1);"),
+    ("microcanonical step replaced by relaxation", "gf_oracle.c",
+     "    quat_mul(h, h, r);\n    return 1;", "    memcpy(r, h, sizeof h);\n    return 1;"),
+    ("network inputs without the backward dagger", "gf_oracle.c",
+     "for (int b = 0; b < 3; ++b) M.m[a][b] = c_add(M.m[a][b], c_add(uf.m[a][b], ubd.m[a][b]));",
+     "for (int b = 0; b < 3; ++b) M.m[a][b] = c_add(M.m[a][b], c_add(uf.m[a][b], ub.m[a][b]));"),
+    ("network inputs with the link reals out of order", "gf_oracle.c",
+     "for (int r = 0; r < 18; ++r) o[mu * 18 + r] = p[r];",
+     "for (int r = 0; r < 18; ++r) o[mu * 18 + r] = p[(r + 2) % 18];"),
+    ("exponential map without the 1/2 of lambda/2", "gf_oracle.c",
+     "double w = 0.5 * scale * c[j * 8 + a];", "double w = scale * c[j * 8 + a];"),
+    ("exponential map Taylor divisor", "gf_oracle.c",
+     "T.m[x][y] = c_make(P.m[x][y].re / k, P.m[x][y].im / k);",
+     "T.m[x][y] = c_make(P.m[x][y].re / (k + 1), P.m[x][y].im / (k + 1));"),
+    ("algebra coefficients multiplied by the scale", "gf_oracle.c",
+     "for (int a = 0; a < 8; ++a) c[j * 8 + a] = re_tr_lambda(a, &A) / scale;",
+     "for (int a = 0; a < 8; ++a) c[j * 8 + a] = re_tr_lambda(a, &A) * scale;"),
     ("convolution taps transposed", "conv_oracle.c",
      "int d[4] = { k % 3 - 1, (k / 3) % 3 - 1, (k / 9) % 3 - 1, (k / 27) % 3 - 1 };",
      "int d[4] = { (k / 3) % 3 - 1, k % 3 - 1, (k / 9) % 3 - 1, (k / 27) % 3 - 1 };"),
@@ -74,41 +99,56 @@ MUTATIONS = [
 ]
 
 
-def _pins_on_copy(tmp_path, mutation=None):
+def _pins_on_copy(workdir, mutation=None):
     """Copy the sources (with the mutation applied), build them where the oracle
-    module looks for them, run the pins against the copy; the pytest exit code."""
+    module looks for them, run the pins against the copy; (pytest exit code, output)."""
+    os.makedirs(workdir)
     for f in SOURCES:
-        shutil.copy(os.path.join(ORACLE, f), tmp_path / f)
+        shutil.copy(os.path.join(ORACLE, f), os.path.join(workdir, f))
     if mutation is not None:
         fname, old, new = mutation
-        path = tmp_path / fname
-        text = path.read_text()
-        assert text.count(old) == 1, f"mutation site not unique or missing: {old!r}"
-        path.write_text(text.replace(old, new))
+        path = os.path.join(workdir, fname)
+        text = open(path).read()
+        if text.count(old) != 1:
+            return None, f"mutation site not unique or missing: {old!r}"
+        open(path, "w").write(text.replace(old, new))
     # the copy must compile, so that a failing pin run means a caught mistake
-    srcs = [str(tmp_path / f) for f in SOURCES]
-    os.makedirs(tmp_path / "_build")
+    srcs = [os.path.join(workdir, f) for f in SOURCES]
+    os.makedirs(os.path.join(workdir, "_build"))
     cc = subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-Wall",
-                         "-Wno-unused-function", "-fopenmp", *srcs, "-o", str(tmp_path / "_build" / "liboracle.so"),
-                         "-lm"], capture_output=True, text=True)
-    assert cc.returncode == 0, cc.stderr[-2000:]
-    env = dict(os.environ, ORACLE_SOURCE_DIR=str(tmp_path), CUDA_VISIBLE_DEVICES="")
+                         "-Wno-unused-function", "-fopenmp", *srcs, "-o",
+                         os.path.join(workdir, "_build", "liboracle.so"), "-lm"], capture_output=True, text=True)
+    if cc.returncode != 0:
+        return None, "does not compile:\n" + cc.stderr[-2000:]
+    env = dict(os.environ, ORACLE_SOURCE_DIR=workdir, CUDA_VISIBLE_DEVICES="", OMP_NUM_THREADS="2")
     cmd = [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
            os.path.join(ROOT, "tests", "test_conv_oracle.py"), "-x", "-q", "-m", "not gpu",
            "-p", "no:cacheprovider"]
-    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=str(tmp_path), env=env)
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=workdir, env=env)
     return r.returncode, r.stdout
 
 
-def test_unmodified_copy_passes_the_pins(tmp_path):
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """Every case (and the unmodified control) run up front, four at a time."""
+    base = str(tmp_path_factory.mktemp("mutants"))
+    jobs = {"control": None, **{m[0]: m[1:] for m in MUTATIONS}}
+    with cf.ThreadPoolExecutor(max_workers=4) as ex:
+        futs = {name: ex.submit(_pins_on_copy, os.path.join(base, f"case{i}"), mut)
+                for i, (name, mut) in enumerate(jobs.items())}
+        return {name: f.result() for name, f in futs.items()}
+
+
+def test_unmodified_copy_passes_the_pins(outcomes):
     """Control: the same procedure on an unmodified copy passes, so a failure
     below is the planted mistake's doing."""
-    rc, out = _pins_on_copy(tmp_path)
+    rc, out = outcomes["control"]
     assert rc == 0, out[-3000:]
 
 
-@pytest.mark.parametrize("name,fname,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_planted_mistake_fails_the_pins(tmp_path, name, fname, old, new):
-    rc, out = _pins_on_copy(tmp_path, (fname, old, new))
+@pytest.mark.parametrize("name", [m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_the_pins(outcomes, name):
+    rc, out = outcomes[name]
+    assert rc is not None, out
     # pytest exit code 1: tests ran and some failed (2+ would be an interrupted or broken run)
     assert rc == 1, f"the pins did not catch '{name}':\n{out[-3000:]}"
