@@ -91,6 +91,36 @@ MUTATIONS = [
     ("algebra coefficients multiplied by the scale", "gf_oracle.c",
      "for (int a = 0; a < 8; ++a) c[j * 8 + a] = re_tr_lambda(a, &A) / scale;",
      "for (int a = 0; a < 8; ++a) c[j * 8 + a] = re_tr_lambda(a, &A) * scale;"),
+    ("plaquette second link at x", "gf_oracle.c",
+     "mat3 b = mat_load(link_cptr(U, site_shift(&g, i, mu, +1), nu));", "mat3 b = mat_load(link_cptr(U, i, nu));"),
+    ("reunitarised third row not conjugated", "gf_oracle.c",
+     "            u.m[2][c] = c_conj(x);\n        }\n        mat_store(M + j * 18, &u);",
+     "            u.m[2][c] = x;\n        }\n        mat_store(M + j * 18, &u);"),
+    ("Gram-Schmidt projection conjugated wrongly", "gf_oracle.c",
+     "ip = c_add(ip, c_mul(c_conj(u.m[0][c]), u.m[1][c]));", "ip = c_add(ip, c_mul(u.m[0][c], c_conj(u.m[1][c])));"),
+    ("annealing schedule misses T1", "gf_oracle.c",
+     "double T = steps > 1 ? T0 + (T1 - T0) * (double)k / (double)(steps - 1) : T0;",
+     "double T = steps > 1 ? T0 + (T1 - T0) * (double)k / (double)steps : T0;"),
+    ("heatbath alpha = |k| T", "gf_oracle.c",
+     "if (!heatbath_s0(kn / T, site, sweep, sg, cap, key, tag, &s0)) return 0;",
+     "if (!heatbath_s0(kn * T, site, sweep, sg, cap, key, tag, &s0)) return 0;"),
+    ("Wilson heatbath temperature 1/beta", "gf_oracle.c",
+     "st = heatbath_quaternion_tag(k, 3.0 / beta,", "st = heatbath_quaternion_tag(k, 1.0 / beta,"),
+    ("Wilson local matrix A U instead of U A", "gf_oracle.c",
+     "mat3 W = mat_mul(&u, &A);", "mat3 W = mat_mul(&A, &u);"),
+    ("maximally Abelian theta along the residual U(1)", "gf_oracle.c",
+     "sum += A[1][0] * A[1][0] + A[2][0] * A[2][0];", "sum += A[1][0] * A[1][0] + A[3][0] * A[3][0];"),
+    ("maximally Abelian maximiser projects e1", "gf_oracle.c",
+     "const int e = target == 0 ? 0 : 2;", "const int e = target == 0 ? 1 : 2;"),
+    ("microcanonical square without the -1", "gf_oracle.c",
+     "r[0] = 2.0 * r0 * r0 - 1.0;", "r[0] = 2.0 * r0 * r0;"),
+    ("loss gradient factor", "conv_oracle.c",
+     "dY[i] = 2.0 * (act[4][i] - target[i]) / (double)n;", "dY[i] = 1.0 * (act[4][i] - target[i]) / (double)n;"),
+    ("ReLU mask never applied", "conv_oracle.c",
+     "if (!(act[l][i] > 0.0)) dX[i] = 0.0;", "if (!(act[l][i] >= 0.0)) dX[i] = 0.0;"),
+    ("weight gradient with the backward shift", "conv_oracle.c",
+     "        for (long s = 0; s < g.V; ++s) {\n            const double *x = X + shifted(&g, s, k, +1) * cin;",
+     "        for (long s = 0; s < g.V; ++s) {\n            const double *x = X + shifted(&g, s, k, -1) * cin;"),
     ("convolution taps transposed", "conv_oracle.c",
      "int d[4] = { k % 3 - 1, (k / 3) % 3 - 1, (k / 9) % 3 - 1, (k / 27) % 3 - 1 };",
      "int d[4] = { (k / 3) % 3 - 1, k % 3 - 1, (k / 9) % 3 - 1, (k / 27) % 3 - 1 };"),

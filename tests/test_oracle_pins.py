@@ -497,6 +497,24 @@ def test_anneal_is_gauge_transformation():
         assert unitarity_error(U) < 1e-13
 
 
+def test_anneal_schedule_ends_at_t1():
+    """T falls linearly from T0 to T1 inclusive: with T1 -> 0 the last sweep is a
+    relaxation, so every site of the parity updated last ends at the maximum of
+    its last subgroup (quaternion real and positive); an end temperature above
+    T1 would leave a heatbath spread of order sqrt(T / |k|)."""
+    dims = (4, 4, 4, 4)
+    U = field(dims, seed=61, gseed=62)
+    assert oracle.anneal(U, 0, 1.0, 1e-12, 2, 5) == 0
+    worst = 0.0
+    for i in range(int(np.prod(dims))):
+        if oracle.site_parity(dims, i) != 1:
+            continue
+        k = oracle.site_quaternion(U, i, 0, 2)
+        assert k[0] > 0
+        worst = max(worst, np.linalg.norm(k[1:]) / np.linalg.norm(k))
+    assert worst < 1e-4
+
+
 def test_haar_generator_moments():
     M = synth.haar_su3((40_000,), 3)
     tr = torch.diagonal(M, dim1=-2, dim2=-1).sum(-1)
@@ -745,6 +763,46 @@ def test_mag_relaxation_is_monotone_and_a_gauge_transformation():
         assert F1 >= F - 1e-14
         F = F1
     assert oracle.plaquette(U) == pytest.approx(P, abs=1e-13)
+
+
+def test_mag_theta_is_the_squared_gradient_of_the_diagonal_weight():
+    """theta_MAG = 1/(3V) sum_x sum_subgroups |grad q|^2 / 4, q the star's
+    diagonal weight after R = exp(i eps sigma_j) (numpy, central differences):
+    dq/deps_j = 2 A_j0.  The third direction is the residual U(1), along which
+    q is flat."""
+    U = field((4, 4, 4, 4), seed=63, gseed=64)
+    V = 256
+    eps = 1e-5
+    sig = [np.array([[0, 1], [1, 0]], complex), np.array([[0, -1j], [1j, 0]], complex),
+           np.array([[1, 0], [0, -1]], complex)]
+    total = 0.0
+    for site in range(V):
+        st = _star(U, site)
+        for sg, (a, b) in enumerate([(0, 1), (1, 2), (0, 2)]):
+            g = []
+            for j in range(3):
+                Rp = np.cos(eps) * np.eye(2) + 1j * np.sin(eps) * sig[j]
+                Rm = np.cos(eps) * np.eye(2) - 1j * np.sin(eps) * sig[j]
+                g.append((_diag_weight_after(st, a, b, Rp) - _diag_weight_after(st, a, b, Rm)) / (2 * eps))
+            assert abs(g[2]) < 1e-6 * (1 + abs(g[0]) + abs(g[1]))
+            total += (g[0] ** 2 + g[1] ** 2) / 4
+    assert oracle.mag_theta(U) == pytest.approx(total / (3 * V), rel=1e-6)
+
+
+def test_mag_maximiser_is_the_one_closest_to_the_identity():
+    """The maximisers of the subgroup's diagonal weight form a circle (the
+    residual U(1)); the chosen one has alpha real and positive, i.e. r3 = 0,
+    r0 > 0, and r0 equal to the largest identity component on that circle: the
+    norm of the projection of e0 onto the top eigenspace (numpy eigh)."""
+    U = field((4, 4, 4, 4), seed=65, gseed=66)
+    for site, sg in ((3, 0), (77, 1), (150, 2), (201, 0)):
+        A = oracle.mag_local_matrix(U, site, sg)
+        w, Q = np.linalg.eigh(A)
+        top = Q[:, w > w.max() - 1e-10 * max(1.0, abs(w.max()))]
+        r = oracle.mag_maximiser(A)
+        assert abs(r[3]) < 1e-12 and r[0] > 0
+        assert r[0] == pytest.approx(np.linalg.norm(top.T @ np.eye(4)[0]), rel=1e-12)
+        assert r @ A @ r == pytest.approx(w.max(), rel=1e-12)
 
 
 def test_mag_fixed_points():
