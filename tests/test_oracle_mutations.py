@@ -121,6 +121,16 @@ MUTATIONS = [
     ("weight gradient with the backward shift", "conv_oracle.c",
      "        for (long s = 0; s < g.V; ++s) {\n            const double *x = X + shifted(&g, s, k, +1) * cin;",
      "        for (long s = 0; s < g.V; ++s) {\n            const double *x = X + shifted(&g, s, k, -1) * cin;"),
+    ("temporal links of the star not rotated", "gf_oracle.c",
+     "static void star_rotate(star *s, int a, int b, cplx R[2][2])\n{\n    for (int mu = 0; mu < 4; ++mu) {",
+     "static void star_rotate(star *s, int a, int b, cplx R[2][2])\n{\n    for (int mu = 0; mu < 3; ++mu) {"),
+    ("maximally Abelian step without the overrelaxation exponent", "gf_oracle.c",
+     "if (!overrelax_quaternion(r, omega, ro)) continue;", "if (!overrelax_quaternion(r, 1.0, ro)) continue;"),
+    ("network violation inputs not scaled", "gf_oracle.c",
+     "for (int a = 0; a < 8; ++a) o[72 + a] = re_tr_lambda(a, &D) / scale;",
+     "for (int a = 0; a < 8; ++a) o[72 + a] = re_tr_lambda(a, &D);"),
+    ("stochastic-relaxation square drops a factor 2", "gf_oracle.c",
+     "r[1] = 2.0 * r0 * r[1];", "r[1] = r0 * r[1];"),
     ("convolution taps transposed", "conv_oracle.c",
      "int d[4] = { k % 3 - 1, (k / 3) % 3 - 1, (k / 9) % 3 - 1, (k / 27) % 3 - 1 };",
      "int d[4] = { (k / 3) % 3 - 1, k % 3 - 1, (k / 9) % 3 - 1, (k / 27) % 3 - 1 };"),

@@ -709,6 +709,19 @@ def _star(U, site):
     return fwd, bwd
 
 
+def block_su2_field(dims, seed):
+    """Every link block-diag(R, 1), R Haar-random in SU(2)."""
+    rng = np.random.default_rng(seed)
+    V = int(np.prod(dims))
+    q = haarsu2_from_quaternion(V * 4, rng)
+    Lx, Ly, Lz, Lt = dims
+    U = np.zeros((Lt, Lz, Ly, Lx, 4, 3, 3), complex)
+    flat = U.reshape(-1, 3, 3)
+    for n in range(V * 4):
+        flat[n] = embed(su2_from_quaternion(q[n]), 0, 1)
+    return U
+
+
 def test_mag_local_matrix_is_the_quadratic_form_and_its_maximum():
     """q(r) = r^T A r for unit and non-unit r (numpy evaluation of the diagonal
     weight); no random SU(2) element beats the chosen maximiser, which reaches
@@ -734,14 +747,7 @@ def test_mag_local_matrix_is_the_quadratic_form_and_its_maximum():
 def test_mag_maximiser_is_the_su2_textbook_solution():
     """For links block-diag(SU(2), 1) the subgroup-(0,1) MAG step is the SU(2)
     one: g rotates X = sum_mu [U s3 U^+ + U_b^+ s3 U_b] onto +|X| s3 (numpy)."""
-    U = field((4, 4, 4, 4), seed=55, gseed=56)
-    flat = U.reshape(-1, 4, 3, 3)
-    for n in range(flat.shape[0]):  # keep the SU(2) block of every link
-        for mu in range(4):
-            m = flat[n, mu][:2, :2]
-            d = np.sqrt(np.linalg.det(m))
-            flat[n, mu] = np.eye(3)
-            flat[n, mu][:2, :2] = m / d
+    U = block_su2_field((4, 4, 4, 4), 55)
     s3 = np.diag([1.0, -1.0])
     for site in (0, 77):
         fwd, bwd = _star(U, site)
@@ -749,8 +755,46 @@ def test_mag_maximiser_is_the_su2_textbook_solution():
             sum(w[:2, :2].conj().T @ s3 @ w[:2, :2] for w in bwd)
         R = su2_from_quaternion(oracle.mag_maximiser(oracle.mag_local_matrix(U, site, 0)))
         Y = R @ X @ R.conj().T
+        assert abs(X[0, 1]) > 1e-3  # a non-trivial rotation
         assert abs(Y[0, 1]) < 1e-12 and Y[0, 0].real > 0
         assert Y[0, 0].real == pytest.approx(np.sqrt(0.5 * np.trace(X @ X).real), rel=1e-12)
+
+
+def test_mag_overrelaxation_applies_the_exponent_to_the_relaxation_step():
+    """Links block-diag(SU(2), 1): only subgroup (0,1) acts, and the step maps
+    X = sum_mu [U s3 U^+ + U_b^+ s3 U_b] (numpy) to R X R^+.  Relaxation turns X
+    onto +s3 (angle 2 phi -> 0); with omega the element is the rational map of
+    the relaxation element, tan phi' = b tan phi, b = omega cos^2 phi + sin^2 phi,
+    so the angle between R X R^+ and s3 becomes |2 phi' - 2 phi|."""
+    omega = 1.7
+    U = block_su2_field((4, 4, 4, 4), 67)
+    s3 = np.diag([1.0, -1.0])
+
+    def X_of(W, site):
+        fwd, bwd = _star(W, site)
+        return sum(f[:2, :2] @ s3 @ f[:2, :2].conj().T for f in fwd) + \
+            sum(w[:2, :2].conj().T @ s3 @ w[:2, :2] for w in bwd)
+
+    def angle(X):
+        n = np.sqrt(0.5 * np.trace(X @ X).real)
+        return np.arccos(np.clip(0.5 * np.trace(X @ s3).real / n, -1, 1)), n
+
+    W = U.copy()
+    oracle.mag_half_sweep(W, 0, omega)
+    checked = 0
+    for site in range(256):
+        if oracle.site_parity((4, 4, 4, 4), site) != 0:
+            continue
+        a0, n0 = angle(X_of(U, site))
+        a1, n1 = angle(X_of(W, site))
+        phi = a0 / 2
+        b = omega * np.cos(phi) ** 2 + np.sin(phi) ** 2
+        phi1 = np.arctan2(b * np.sin(phi), np.cos(phi))
+        assert a0 > 1e-3  # a non-trivial rotation
+        assert n1 == pytest.approx(n0, rel=1e-12)
+        assert a1 == pytest.approx(abs(2 * phi1 - 2 * phi), abs=1e-9)
+        checked += 1
+    assert checked == 128
 
 
 def test_mag_relaxation_is_monotone_and_a_gauge_transformation():
