@@ -73,7 +73,7 @@ MUTATIONS = [
      "double v[4] = { (1.0 - omega) + omega * (k[0] / n),", "double v[4] = { (1.0 - omega) + (k[0] / n),"),
     ("timeslice functional normalisation", "gf_oracle.c",
      "F_t[t] = fs / (3.0 * nk * (double)Ls);", "F_t[t] = fs / (3.0 * 4 * (double)Ls);"),
-    ("driver sweeps once per check", "gf_oracle.c",
+    ("convergence loop sweeps once per check", "gf_oracle.c",
      "oracle_or_sweeps(U, dims, omega, gauge, n);", "oracle_or_sweeps(U, dims, omega, gauge, 1);"),
     ("microcanonical step replaced by relaxation", "gf_oracle.c",
      "    quat_mul(h, h, r);\n    return 1;", "    memcpy(r, h, sizeof h);\n    return 1;"),
