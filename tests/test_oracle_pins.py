@@ -249,6 +249,20 @@ def test_plaquette_target_of_the_generator():
     assert abs(oracle.plaquette(U) - 0.60) < 0.004
 
 
+def test_generator_is_seeded_and_its_fields_are_su3():
+    """Same seeds, same field (bit for bit); another field seed or gauge seed
+    gives another field; every link is in SU(3); the gauge rotation leaves the
+    plaquette of the unrotated field unchanged."""
+    dims = (4, 4, 4, 6)
+    a = field(dims, seed=7, gseed=8)
+    np.testing.assert_array_equal(a, field(dims, seed=7, gseed=8))
+    assert np.abs(a - field(dims, seed=9, gseed=8)).max() > 0.1
+    assert np.abs(a - field(dims, seed=7, gseed=9)).max() > 0.1
+    assert unitarity_error(a) < 1e-13
+    # same field seed, different gauge seeds: gauge-equivalent fields
+    assert oracle.plaquette(a) == pytest.approx(oracle.plaquette(field(dims, seed=7, gseed=9)), abs=1e-13)
+
+
 # --------------------------------------------------------------------------
 # invariants of the sweep
 # --------------------------------------------------------------------------
