@@ -130,6 +130,29 @@ def test_fp32_restarts_option_host_side(lib):
         lib.gf_destroy(h)
 
 
+def documented_options():
+    """Option keys listed in the gf_set_option documentation of include/gf.h."""
+    text = open(os.path.join(ROOT, "include", "gf.h")).read()
+    block = text[text.index("int gf_create"):text.index("int gf_set_option")]
+    return re.findall(r'^\s*\*\s+"(\w+)"', block, flags=re.M)
+
+
+def test_every_documented_option_round_trips(lib):
+    """Each documented option is known to gf_get_option, and setting it to the
+    value read back is accepted (the documentation and the parser agree)."""
+    keys = documented_options()
+    assert len(keys) >= 20
+    h = C.c_void_p()
+    assert lib.gf_create((C.c_int * 4)(4, 4, 4, 4), gf.GF_LANDAU, C.byref(h)) == gf.GF_OK
+    try:
+        for key in keys:
+            v = C.c_double()
+            assert lib.gf_get_option(h, key.encode(), C.byref(v)) == gf.GF_OK, key
+            assert lib.gf_set_option(h, key.encode(), v.value) == gf.GF_OK, (key, v.value)
+    finally:
+        lib.gf_destroy(h)
+
+
 def test_batch_handle_host_side(lib):
     b = gf.gf_batch_create([(4, 4, 4, 4), (8, 8, 8, 8)], gf.GF_LANDAU)
     gf.gf_batch_set_option(b, "precision", gf.GF_FP64)
