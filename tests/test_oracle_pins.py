@@ -511,6 +511,21 @@ def test_anneal_is_gauge_transformation():
         assert unitarity_error(U) < 1e-13
 
 
+def test_anneal_resumes_from_a_sweep_offset():
+    """A schedule split in two calls -- the second starting at the next
+    temperature with the Philox sweep counter offset by the sweeps done --
+    equals the schedule run at once, bit for bit (counter-based draws)."""
+    dims = (4, 4, 4, 4)
+    T0, T1, n = 1.2, 0.3, 4
+    Tk = [T0 + (T1 - T0) * k / (n - 1) for k in range(n)]
+    A = field(dims, seed=69, gseed=70)
+    B = A.copy()
+    assert oracle.anneal(A, 0, T0, T1, n, 11) == 0
+    assert oracle.anneal(B, 0, Tk[0], Tk[1], 2, 11, 0) == 0
+    assert oracle.anneal(B, 0, Tk[2], Tk[3], 2, 11, 2) == 0
+    np.testing.assert_array_equal(A, B)
+
+
 def test_anneal_schedule_ends_at_t1():
     """T falls linearly from T0 to T1 inclusive: with T1 -> 0 the last sweep is a
     relaxation, so every site of the parity updated last ends at the maximum of
