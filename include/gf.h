@@ -18,9 +18,10 @@
  *   dims = {Lx, Ly, Lz, Lt}; every extent must be even and >= 2 (the
  *   checkerboard needs it) and the volume below 2^31.  Boundaries are
  *   periodic.  Parity of a site is (x+y+z+t) mod 2; RED = 0 is swept first.
- * Pointers: a field argument may be device memory or host memory (pageable or
- *   pinned).  Host fields are copied in and out by the call; device fields
- *   are read (and, for in-place calls, written) on the context's stream.
+ * Pointers: a field argument may be device memory of the current device or
+ *   host memory (pageable or pinned).  Host fields are copied in and out by
+ *   the call; device fields are read (and, for in-place calls, written) on the
+ *   context's stream.  Device memory of another device gives GF_EINVAL.
  *   The library never frees or keeps caller memory after a call returns.
  * Ownership: a gf_ctx owns its internal device buffers (the resident field in
  *   per-parity structure-of-arrays layout, reduction scratch, CUDA graphs);
@@ -435,9 +436,11 @@ int gf_batch_autotune(gf_batch *b, double *const *U, int *threads_per_site, int 
  * call before any stream capture.  All calls on a device share the array and
  * leave their partial sums in it; calls whose kernels overlap on the GPU race
  * and must be ordered by the caller.
- * Errors: GF_EINVAL for a NULL, host or misaligned pointer, a bad gauge or
- * extent, or a volume above GF_NOALLOC_MAX_SITES; GF_ECUDA if the launch or
- * the address lookup fails. */
+ * Errors: GF_EINVAL for a NULL, host or misaligned pointer, a pointer to
+ * memory of a device other than the current one, a bad gauge or extent, or a
+ * volume above GF_NOALLOC_MAX_SITES; GF_ECUDA if a CUDA error from earlier
+ * work of the calling thread is pending on entry (it is left in place for the
+ * caller, nothing is launched), or if the launch or the address lookup fails. */
 int gf_measure_noalloc(const int dims[4], int gauge, const double *U, double *out, void *stream);
 
 #ifdef __cplusplus

@@ -216,23 +216,14 @@ static int ensure_staging(gf_ctx *ctx)
     return GF_OK;
 }
 
-static bool is_device_pointer(const void *p)
-{
-    cudaPointerAttributes a;
-    cudaError_t e = cudaPointerGetAttributes(&a, p);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 // device view of a caller field: the pointer itself, or the staging copy
 static int device_view(gf_ctx *ctx, const double *U, const double **view, bool *host)
 {
     if (!U) return fail(ctx, GF_EINVAL, "field pointer is NULL");
     if ((uintptr_t)U % 16) return fail(ctx, GF_EINVAL, "field pointer must be 16-byte aligned");
-    *host = !is_device_pointer(U);
+    const PtrKind k = pointer_kind(U);
+    if (k == PTR_FOREIGN) return fail(ctx, GF_EINVAL, "field is device memory of another device");
+    *host = k == PTR_HOST;
     if (*host) {
         RET(ensure_staging(ctx));
         CK(cudaMemcpyAsync(ctx->staging, U, sizeof(double) * 72 * (size_t)ctx->V, cudaMemcpyHostToDevice,
@@ -798,7 +789,9 @@ int gf_download(gf_ctx *ctx, double *U)
 {
     if (!ctx) return GF_EINVAL;
     if (!U || (uintptr_t)U % 16) return fail(ctx, GF_EINVAL, "field pointer NULL or not 16-byte aligned");
-    return download(ctx, U, !is_device_pointer(U));
+    const PtrKind k = pointer_kind(U);
+    if (k == PTR_FOREIGN) return fail(ctx, GF_EINVAL, "field is device memory of another device");
+    return download(ctx, U, k == PTR_HOST);
 }
 
 int gf_or_half_sweep(gf_ctx *ctx, int parity, double omega)
@@ -1101,7 +1094,9 @@ int gf_get_gauge(gf_ctx *ctx, double *g)
 {
     if (!ctx || !g) return GF_EINVAL;
     if (!ctx->gt) return fail(ctx, GF_ESTATE, "no tracked gauge field");
-    bool host = !is_device_pointer(g);
+    const PtrKind k = pointer_kind(g);
+    if (k == PTR_FOREIGN) return fail(ctx, GF_EINVAL, "output is device memory of another device");
+    bool host = k == PTR_HOST;
     double *dst = g;
     if (host) {
         RET(ensure_staging(ctx));
@@ -1151,7 +1146,7 @@ int gf_features(gf_ctx *ctx, double scale, void *features)
 {
     if (!ctx || !features || !(scale > 0.0)) return GF_EINVAL;
     if (ctx->resident != GF_FP64) return fail(ctx, GF_ESTATE, "features need a resident FP64 field");
-    if (!is_device_pointer(features)) return fail(ctx, GF_EINVAL, "features must be device memory");
+    if (pointer_kind(features) != PTR_DEVICE) return fail(ctx, GF_EINVAL, "features must be device memory of the current device");
     CK(launch_features(ctx->resident_fmt, ref(ctx, ctx->f64), ctx->geom, 1.0 / scale, features, ctx->stream));
     return GF_OK;
 }
@@ -1160,7 +1155,7 @@ int gf_gauge_algebra(gf_ctx *ctx, double scale, float *c)
 {
     if (!ctx || !c || !(scale > 0.0)) return GF_EINVAL;
     if (!ctx->gt) return fail(ctx, GF_ESTATE, "no tracked gauge field");
-    if (!is_device_pointer(c)) return fail(ctx, GF_EINVAL, "output must be device memory");
+    if (pointer_kind(c) != PTR_DEVICE) return fail(ctx, GF_EINVAL, "output must be device memory of the current device");
     CK(launch_gauge_algebra(ref(ctx, ctx->gt), ctx->geom, 1.0 / scale, c, ctx->stream));
     return GF_OK;
 }
@@ -1169,7 +1164,7 @@ int gf_apply_algebra(gf_ctx *ctx, const float *c, double scale)
 {
     if (!ctx || !c || !(scale > 0.0)) return GF_EINVAL;
     if (ctx->resident != GF_FP64) return fail(ctx, GF_ESTATE, "needs a resident FP64 field");
-    if (!is_device_pointer(c)) return fail(ctx, GF_EINVAL, "coefficients must be device memory");
+    if (pointer_kind(c) != PTR_DEVICE) return fail(ctx, GF_EINVAL, "coefficients must be device memory of the current device");
     RET(ensure_gauge_field(ctx));
     CK(launch_expmap_to_gauge(c, scale, ref(ctx, ctx->gt), ctx->geom, ctx->stream));
     CK(launch_gauge_transform_resident(ctx->resident_fmt, ref(ctx, ctx->f64), ref(ctx, ctx->gt), ctx->geom,

@@ -733,12 +733,8 @@ int gf_batch_overrelax(gf_batch *b, double *const *U, double omega, double theta
     if (!(theta_target >= 0.0) || !std::isfinite(theta_target) || max_iter < 0)
         return bfail(b, GF_EINVAL, "theta_target >= 0, max_iter >= 0");
     for (int i = 0; i < b->n; ++i) {
-        cudaPointerAttributes at;
-        if (!U[i] || (uintptr_t)U[i] % 16 || cudaPointerGetAttributes(&at, U[i]) != cudaSuccess ||
-            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-            cudaGetLastError();
-            return bfail(b, GF_EINVAL, "every field must be a 16-byte aligned device pointer");
-        }
+        if (!U[i] || (uintptr_t)U[i] % 16 || pointer_kind(U[i]) != PTR_DEVICE)
+            return bfail(b, GF_EINVAL, "every field must be a 16-byte aligned pointer to memory of the current device");
     }
     BRET(ensure_small_buffers(b));
     const bool fp32_first = b->precision != GF_FP64;

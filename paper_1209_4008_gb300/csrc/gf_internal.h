@@ -82,6 +82,30 @@ inline double format_link_bytes(int fmt)
     }
 }
 
+// Where a caller's pointer lives, for entry points that take host or device
+// memory: PTR_HOST (pageable or pinned host memory, or memory CUDA does not
+// know), PTR_DEVICE (device memory of the current device, or managed memory),
+// PTR_FOREIGN (device memory of another device: kernels launched on the
+// current device must not dereference it).
+enum PtrKind { PTR_HOST = 0, PTR_DEVICE = 1, PTR_FOREIGN = 2 };
+
+inline PtrKind pointer_kind(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // this query's own error only
+        return PTR_HOST;
+    }
+    if (a.type == cudaMemoryTypeManaged) return PTR_DEVICE;
+    if (a.type != cudaMemoryTypeDevice) return PTR_HOST;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PTR_FOREIGN;
+    }
+    return a.device == dev ? PTR_DEVICE : PTR_FOREIGN;
+}
+
 // reductions write per-block partial sums (2 doubles per block)
 constexpr int kReduceBlock = 256;
 

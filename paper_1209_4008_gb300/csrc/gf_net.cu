@@ -15,6 +15,7 @@
 #include "gf.h"
 #include "gf_conv_tc.cuh"
 #include "gf_device.cuh"
+#include "gf_internal.h"
 
 namespace {
 
@@ -977,15 +978,7 @@ static int backward(gf_net *n, const bf16 *f, const float *target)
     return GF_OK;
 }
 
-static bool device_ptr(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+static bool device_ptr(const void *p) { return gf::pointer_kind(p) == gf::PTR_DEVICE; }
 
 extern "C" {
 
@@ -1100,7 +1093,7 @@ int gf_net_forward(gf_net *n, const void *features, float *out)
 {
     if (!n || !features || !out) return GF_EINVAL;
     if (!n->params) return nfail(n, GF_ESTATE, "parameters not set");
-    if (!device_ptr(features) || !device_ptr(out)) return nfail(n, GF_EINVAL, "device pointers required");
+    if (!device_ptr(features) || !device_ptr(out)) return nfail(n, GF_EINVAL, "device pointers of the current device required");
     int r = forward(n, static_cast<const bf16 *>(features));
     if (r != GF_OK) return r;
     NCK(cudaMemcpyAsync(out, n->out, sizeof(float) * n->g.V * 8, cudaMemcpyDeviceToDevice, n->stream));
@@ -1125,7 +1118,7 @@ int gf_net_gradient(gf_net *n, const void *features, const float *target, float 
 {
     if (!n || !features || !target) return GF_EINVAL;
     if (!n->params) return nfail(n, GF_ESTATE, "parameters not set");
-    if (!device_ptr(features) || !device_ptr(target)) return nfail(n, GF_EINVAL, "device pointers required");
+    if (!device_ptr(features) || !device_ptr(target)) return nfail(n, GF_EINVAL, "device pointers of the current device required");
     int r = backward(n, static_cast<const bf16 *>(features), target);
     if (r != GF_OK) return r;
     if (grad) NCK(cudaMemcpyAsync(grad, n->grad, sizeof(float) * n->np, cudaMemcpyDefault, n->stream));

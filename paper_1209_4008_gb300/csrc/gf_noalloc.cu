@@ -21,6 +21,7 @@
 
 #include "gf.h"
 #include "gf_device.cuh"
+#include "gf_internal.h"
 
 namespace {
 
@@ -140,16 +141,6 @@ __global__ void __launch_bounds__(kNoallocBlock) k_finish_noalloc(const double *
     }
 }
 
-bool on_device(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 // Device address of the scratch array on the current device, looked up once
 // per device (host code cannot use the array's name as a device pointer).
 int scratch_for_current_device(double **ptr)
@@ -180,7 +171,10 @@ extern "C" int gf_measure_noalloc(const int dims[4], int gauge, const double *U,
         V *= dims[mu];
         if (V > GF_NOALLOC_MAX_SITES) return GF_EINVAL;
     }
-    if (!on_device(U) || !on_device(out)) return GF_EINVAL;
+    // an error left pending by the caller's own earlier work stays theirs: report it, do not clear it
+    if (cudaPeekAtLastError() != cudaSuccess) return GF_ECUDA;
+    // both must be memory of the current device: the kernels below run there
+    if (pointer_kind(U) != PTR_DEVICE || pointer_kind(out) != PTR_DEVICE) return GF_EINVAL;
 
     double *scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
@@ -195,6 +189,7 @@ extern "C" int gf_measure_noalloc(const int dims[4], int gauge, const double *U,
     int nblocks = (int)((V + kNoallocBlock - 1) / kNoallocBlock);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     k_measure_noalloc<<<nblocks, kNoallocBlock, 0, s>>>(U, g, nk, scratch);
+    if (cudaGetLastError() != cudaSuccess) return GF_ECUDA;
     k_finish_noalloc<<<1, kNoallocBlock, 0, s>>>(scratch, nblocks, 1.0 / (3.0 * nk * (double)V),
                                                  1.0 / (3.0 * (double)V), out);
     return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;

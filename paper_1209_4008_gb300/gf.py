@@ -333,9 +333,25 @@ def gf_autotune(ctx: Context):
 
 def gf_measure_noalloc(dims, gauge: int, U, out, stream=None) -> int:
     """F and theta of a device field into the device buffer out (2 doubles),
-    without any allocation; returns the C return code."""
+    without any allocation; returns the C return code.  Tensors are checked
+    here first (the library sees only addresses): U must hold the lattice's
+    float64 links and out at least two float64 values."""
     lib = load()
-    arr = (C.c_int * 4)(*[int(d) for d in dims])
+    dims = [int(d) for d in dims]
+    if hasattr(U, "element_size") or hasattr(out, "element_size"):
+        import torch
+        vol = 1
+        for d in dims:
+            vol *= d
+        for name, t, need in (("U", U, vol * 72), ("out", out, 2)):
+            if not isinstance(t, torch.Tensor):
+                continue
+            if t.dtype not in (torch.float64, torch.complex128):
+                raise ValueError(f"{name} must be float64 (or complex128), got {t.dtype}")
+            n = t.numel() * (2 if t.dtype == torch.complex128 else 1)
+            if (n != need) if name == "U" else (n < need):
+                raise ValueError(f"{name} holds {n} float64 values, needs {'' if name == 'U' else 'at least '}{need}")
+    arr = (C.c_int * 4)(*dims)
     s = getattr(stream, "cuda_stream", stream)
     return lib.gf_measure_noalloc(arr, int(gauge), _ptr(U), _ptr(out), s or None)
 

@@ -179,3 +179,23 @@ def test_binding_argument_counts_match_header():
     for name, (_, argtypes) in gf.SIGNATURES.items():
         assert name in protos, name
         assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
+
+
+def test_noalloc_binding_refuses_mistyped_tensors(lib):
+    """The allocation-free measurement reads U and writes two doubles at raw
+    addresses; the binding refuses tensors of the wrong type or size before
+    the library sees them, and the library refuses what it cannot hold."""
+    import torch
+    U = torch.zeros(4 ** 4 * 72, dtype=torch.float64)
+    out = torch.zeros(2, dtype=torch.float64)
+    for bad_u, bad_out in ((U, torch.zeros(2, dtype=torch.float32)), (U, torch.zeros(1, dtype=torch.float64)),
+                           (U[:-2], out), (U.float(), out)):
+        with pytest.raises(ValueError):
+            gf.gf_measure_noalloc((4, 4, 4, 4), gf.GF_LANDAU, bad_u, bad_out)
+    dims = (C.c_int * 4)
+    assert lib.gf_measure_noalloc(dims(4, 4, 4, 4), gf.GF_LANDAU, None, None, None) == gf.GF_EINVAL
+    # host memory is never accepted (no staging copy without an allocation)
+    assert lib.gf_measure_noalloc(dims(4, 4, 4, 4), gf.GF_LANDAU, U.data_ptr(), out.data_ptr(), None) \
+        in (gf.GF_EINVAL, gf.GF_ECUDA)  # ECUDA where no driver is present
+    assert lib.gf_measure_noalloc(dims(4, 4, 4, 4), 7, U.data_ptr(), out.data_ptr(), None) == gf.GF_EINVAL
+    assert lib.gf_measure_noalloc(dims(64, 64, 64, 64), 0, U.data_ptr(), out.data_ptr(), None) == gf.GF_EINVAL
