@@ -89,3 +89,29 @@ def test_coulomb_48x48x48x96_or_and_sa_sampled():
     assert np.abs(sampled_links(after2, dims, sites) - want).max() < 1e-11
     # both steps are gauge transformations: spatial and temporal plaquettes unchanged
     assert gf.gf_plaquette(c, U) == pytest.approx(gf.gf_plaquette(c, torch.from_numpy(host).cuda()), abs=1e-12)
+
+
+def test_landau_32x32x32x32_fp32_restarts_equal_fp64_solve():
+    """The mixed policy with FP32 restarts on the benchmark field: the same F as
+    the all-FP64 solve (to 1e-13), theta < 1e-14, plaquette of the input kept
+    (an exact FP64 gauge transform)."""
+    dims = (32, 32, 32, 32)
+    U0 = synth.make_field(dims, 0.60, 3, 4, device="cuda")
+    res = {}
+    for name, opts in (("fp64", {"precision": gf.GF_FP64}),
+                       ("restarts", {"precision": gf.GF_MIXED, "fp32_restarts": 2, "theta_switch": 1e-30})):
+        c = gf.gf_create(dims, gf.GF_LANDAU)
+        gf.gf_set_option(c, "check_every", 25)
+        for k, v in opts.items():
+            gf.gf_set_option(c, k, v)
+        U = U0.clone()
+        conv, it, F, th = gf.gf_overrelax(c, U, 1.7, 1e-14, 20000)
+        assert conv and th < 1e-14, name
+        res[name] = (F, gf.gf_plaquette(c, U), gf.gf_theta(c, U), gf.gf_get_stat(c, "sweeps_fp64"))
+        if name == "restarts":
+            assert gf.gf_get_stat(c, "fp32_restarts_done") >= 1
+        P0 = gf.gf_plaquette(c, U0)
+    assert abs(res["restarts"][0] - res["fp64"][0]) <= 1e-13
+    assert res["restarts"][1] == pytest.approx(P0, abs=1e-13)
+    assert res["restarts"][2] < 1e-14
+    assert res["restarts"][3] < res["fp64"][3]

@@ -1,15 +1,29 @@
 """Learned warm start on the GPU against the oracle.
 
-Tolerances: BF16 stores 8 significant bits (relative rounding <= 2^-9); the
-network inputs are compared at 4e-3 relative.  The network's forward output
-and gradients use BF16 weights and activations with FP32 accumulation and are
-compared with the FP64 oracle evaluated on the same BF16-rounded weights and
-inputs: the remaining difference is the BF16 rounding of the three hidden
-activations and of the backpropagated gradients (~0.2-0.4 % each), so the
-relative L2 error bound is 2e-2 (output) and 5e-2 (gradient).  The applied
-gauge transformation is stored as FP32 and reprojected onto SU(3) in FP64,
-so it differs from the exact exponential by ~1e-7; it is still an exact FP64
-gauge transformation (plaquette to 1e-13).
+Tolerances: BF16 stores 8 significant bits (unit roundoff 2^-8); the network
+inputs are compared at 4e-3 relative.
+
+The network (forward output, loss, every weight and bias gradient) is
+compared with the FP64 oracle in two ways:
+- bit for bit, on integer-valued weights, biases and inputs chosen so that
+  every hidden activation and every back-propagated value is exactly
+  representable in BF16 and every sum exactly in FP32: the GPU's rounding
+  steps are then all exact, so any wrong tap, channel, site, wrap or mask
+  shows up as a difference.  The test asserts that precondition on the
+  oracle's own intermediate values before it compares.  Lattices: 8x16x4x4
+  and 16x32x4x4 (periodic wrap inside one halo tile, several tiles), and the
+  ragged 6x4x6x10 (1440 sites, not a multiple of the 128-site tile), each
+  with the per-tap gather kernels, the halo-tile kernels and the CUDA-core
+  kernels;
+- element by element on random weights, within 8 standard deviations of
+  the rounding error, which is propagated through the layers from the
+  arithmetic: the BF16 rounding of every stored activation and the FP32
+  accumulation of every sum, independent and zero mean, carried forward
+  through W^2 (a worst-case bound through |W| is vacuous for random signs).
+
+The applied gauge transformation is stored as FP32 and reprojected onto SU(3)
+in FP64, so it differs from the exact exponential by ~1e-7; it is still an
+exact FP64 gauge transformation (plaquette to 1e-13).
 """
 import math
 
@@ -132,6 +146,119 @@ def test_network_forward_and_gradient_match_oracle():
         assert rel_l2(grad[off:off + n], ograd[off:off + n]) < 5e-2, l
         assert rel_l2(grad[off + n:off + n + ch[l + 1]], ograd[off + n:off + n + ch[l + 1]]) < 5e-2, l
         off += n + ch[l + 1]
+
+
+CHANNELS = (80, 32, 32, 32, 8)
+
+
+def exact_network(dims, seed, nnz=(12, 6, 3, 6)):
+    """Integer weights (nnz entries of +-1 per output channel), integer biases
+    in {-1, 0, 1} and inputs in {-1, 0, 1}; the target differs from the
+    output by q * {-1, 0, 1}, q the odd part of the output count, so that the
+    loss gradient 2 (out - target) / (8 V) is a power of two times an integer."""
+    rng = np.random.default_rng(seed)
+    V = int(np.prod(dims))
+    Ws, bs, flat = [], [], []
+    for l in range(4):
+        ci, co = CHANNELS[l], CHANNELS[l + 1]
+        W = np.zeros((81, co, ci))
+        for o in range(co):
+            idx = rng.choice(81 * ci, nnz[l], replace=False)
+            W[idx // ci, o, idx % ci] = rng.choice([-1.0, 1.0], nnz[l])
+        b = rng.integers(-1, 2, co).astype(np.float64)
+        Ws.append(W)
+        bs.append(b)
+        flat += [W.ravel(), b]
+    X0 = rng.integers(-1, 2, (V, 80)).astype(np.float64)
+    acts = [X0]
+    for l in range(4):
+        Y = oracle.conv_forward(acts[-1], Ws[l], bs[l], dims)
+        acts.append(np.maximum(Y, 0.0) if l < 3 else Y)
+    nout = V * 8
+    q = nout >> ((nout & -nout).bit_length() - 1)
+    target = acts[4] - q * rng.integers(-1, 2, (V, 8)).astype(np.float64)
+    # precondition: every value the GPU rounds to BF16 is exactly representable
+    g = 2.0 * (acts[4] - target) / nout
+    rounded = [acts[1], acts[2], acts[3], g]
+    for l in (3, 2, 1):
+        g = oracle.conv_backward_data(g, Ws[l], dims) * (acts[l] > 0)
+        rounded.append(g)
+    for a in rounded:
+        assert np.array_equal(bf16_round(a).astype(np.float64), a), "design not exact in BF16"
+    return np.concatenate(flat).astype(np.float32), X0, target, acts[4]
+
+
+@pytest.mark.parametrize("dims", [(8, 16, 4, 4), (16, 32, 4, 4), (6, 4, 6, 10)])
+@pytest.mark.parametrize("path", ["gather", "halo", "cuda_cores"])
+def test_network_exact_arithmetic_matches_oracle_bit_for_bit(dims, path):
+    params, X0, target, out_exact = exact_network(dims, seed=sum(dims))
+    V = int(np.prod(dims))
+    loss_o, grad_o, out_o = oracle.net_loss(X0, target, params.astype(np.float64), dims, CHANNELS)
+    assert np.array_equal(out_o, out_exact)
+    assert np.array_equal(grad_o.astype(np.float32).astype(np.float64), grad_o)  # exact in FP32
+    net = gf.gf_net_create(dims)
+    gf.gf_net_set_option(net, "tensor_cores", 0 if path == "cuda_cores" else 1)
+    gf.gf_net_set_option(net, "conv_halo", 1 if path == "halo" else 0)
+    gf.gf_net_set_params(net, params)
+    fd = torch.from_numpy(X0.astype(np.float32)).to(torch.bfloat16).cuda()
+    td = torch.from_numpy(target.astype(np.float32)).cuda()
+    out = torch.empty(V, 8, dtype=torch.float32, device="cuda")
+    gf.gf_net_forward(net, fd, out)
+    np.testing.assert_array_equal(out.cpu().numpy().astype(np.float64), out_o)
+    grad = np.zeros(gf.gf_net_param_count(), dtype=np.float32)
+    loss = gf.gf_net_gradient(net, fd, td, grad)
+    assert loss == pytest.approx(loss_o, rel=1e-14)
+    bad = np.flatnonzero(grad.astype(np.float64) != grad_o)
+    assert bad.size == 0, (bad[:10], grad[bad[:10]], grad_o[bad[:10]])
+
+
+def forward_error_sigma(X0, Ws, bs, dims):
+    """Element-wise standard deviation of GPU output - FP64 output, from the
+    arithmetic: every stored activation is rounded to BF16 (an error uniform
+    within half a unit in the last place, at most 2^-8 of the value, variance
+    (2^-7 |x|)^2 / 12), every sum of K products accumulates in FP32 (variance
+    at most K (2^-24 sum |W||X|)^2 / 3); the errors are independent and zero
+    mean, so their variances propagate through the next layer as W^2, and
+    through ReLU only where the activation is positive."""
+    X, VarE = X0, np.zeros_like(X0)
+    for l in range(4):
+        K = 81 * X.shape[1]
+        Y = oracle.conv_forward(X, Ws[l], bs[l], dims)
+        mag = oracle.conv_forward(np.abs(X), np.abs(Ws[l]), np.abs(bs[l]), dims)
+        VarD = oracle.conv_forward(VarE, Ws[l] ** 2, None, dims) + K * (2.0 ** -24 * mag) ** 2 / 3.0
+        if l == 3:
+            return Y, np.sqrt(VarD)
+        X = np.maximum(Y, 0.0)
+        VarE = VarD * (Y > 0) + (2.0 ** -7 * X) ** 2 / 12.0
+
+
+@pytest.mark.parametrize("dims", [(8, 16, 4, 4), (6, 4, 6, 10)])
+@pytest.mark.parametrize("path", ["gather", "halo", "cuda_cores"])
+def test_network_forward_within_rounding_bound_elementwise(dims, path):
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(7)
+    params = learned.init_params(21, scale_last=1.0)
+    Ws, bs, off = [], [], 0
+    for l in range(4):
+        n = 81 * CHANNELS[l + 1] * CHANNELS[l]
+        params[off + n:off + n + CHANNELS[l + 1]] = rng.standard_normal(CHANNELS[l + 1]) * 0.1
+        Ws.append(bf16_round(params[off:off + n]).astype(np.float64).reshape(81, CHANNELS[l + 1], CHANNELS[l]))
+        bs.append(params[off + n:off + n + CHANNELS[l + 1]].astype(np.float64))
+        off += n + CHANNELS[l + 1]
+    X0 = bf16_round(rng.standard_normal((V, 80))).astype(np.float64)
+    Y, sigma = forward_error_sigma(X0, Ws, bs, dims)
+    D = 8.0 * sigma + 1e-7 * np.abs(Y)
+    net = gf.gf_net_create(dims)
+    gf.gf_net_set_option(net, "tensor_cores", 0 if path == "cuda_cores" else 1)
+    gf.gf_net_set_option(net, "conv_halo", 1 if path == "halo" else 0)
+    gf.gf_net_set_params(net, params)
+    out = torch.empty(V, 8, dtype=torch.float32, device="cuda")
+    gf.gf_net_forward(net, torch.from_numpy(X0.astype(np.float32)).to(torch.bfloat16).cuda(), out)
+    err = np.abs(out.cpu().numpy().astype(np.float64) - Y)
+    assert np.all(err <= D), (err.max(), D[err > D][:5])
+    # the bound is not vacuous: it is about 6 % of the output's scale, while a
+    # single wrong tap (one of 81) moves an output by about a ninth of it
+    assert np.median(D) < 0.1 * np.median(np.abs(Y))
 
 
 def test_training_reduces_loss():
