@@ -303,6 +303,11 @@ def gpu_arm(args, rank, world, local):
     fp32_checks = sw32 / CHECK_EVERY
     launches = int(2 * sweeps + 2 * checks + fp32_checks + args.steps * (4 + 4))
 
+    # plaquette of the input and of each leg's result: every sweep is a gauge transformation, so
+    # the change measures the rounding drift a leg leaves in the links
+    P_in = gf.gf_plaquette(ctx, pristine)
+    dP_mixed = abs(gf.gf_plaquette(ctx, work) - P_in)
+
     # all-FP64 reference solve (time to theta), once, outside the timed steps
     ctx64 = make_ctx(gf, gf.GF_FP64)
     work.copy_(pristine)
@@ -311,6 +316,7 @@ def gpu_arm(args, rank, world, local):
     conv64, it64, F64, th64 = gf.gf_overrelax(ctx64, work, OMEGA, THETA_TARGET, MAX_ITER)
     torch.cuda.synchronize()
     t_fp64 = time.perf_counter() - t0
+    dP_fp64 = abs(gf.gf_plaquette(ctx64, work) - P_in)
 
     # per-format half-sweep kernel times on the same field
     thr = {}
@@ -341,6 +347,7 @@ def gpu_arm(args, rank, world, local):
     convdf, itdf, Fdf, thdf = gf.gf_overrelax(ctxdf, work, OMEGA, THETA_TARGET, MAX_ITER)
     torch.cuda.synchronize()
     t_df = time.perf_counter() - t0
+    dP_df = abs(gf.gf_plaquette(ctxdf, work) - P_in)
 
     # the mixed policy with the learned warm start (stored parameters), once
     learned_row = None
@@ -367,12 +374,17 @@ def gpu_arm(args, rank, world, local):
                                                     if args.learned_repeat else 0),
                        "weights": os.path.relpath(WEIGHTS, ROOT)}
 
-    # optional: the mixed policy with FP32 restarts (option fp32_restarts), once
-    restart_row = None
-    if args.fp32_restarts > 0:
+    # the mixed policy with FP32 restarts (option fp32_restarts), once with a native FP64 finish
+    # and once with the double-float finish (fp64_arith 1: the transformation tracked as E = g - 1
+    # and applied to the FP64 field in FP64, so the result stays an exact FP64 gauge transform)
+    restart_row = {}
+    for tag, arith in (("restarts", 0), ("restarts_df64", 1)):
+        if args.fp32_restarts <= 0:
+            break
         ctxr = make_ctx(gf, gf.GF_MIXED)
         gf.gf_set_option(ctxr, "fp32_restarts", args.fp32_restarts)
         gf.gf_set_option(ctxr, "theta_switch", args.restart_switch)
+        gf.gf_set_option(ctxr, "fp64_arith", arith)
         work.copy_(pristine)
         gf.gf_overrelax(ctxr, work, OMEGA, THETA_TARGET, MAX_ITER)  # warm-up
         work.copy_(pristine)
@@ -380,13 +392,25 @@ def gpu_arm(args, rank, world, local):
         t0 = time.perf_counter()
         convr, itr, Fr, thr_ = gf.gf_overrelax(ctxr, work, OMEGA, THETA_TARGET, MAX_ITER)
         torch.cuda.synchronize()
-        restart_row = {"restarts_s": time.perf_counter() - t0, "restarts": args.fp32_restarts,
-                       "restart_theta_switch": args.restart_switch, "sweeps_restarts": itr,
-                       "sweeps_fp32_restarts": gf.gf_get_stat(ctxr, "sweeps_fp32"),
-                       "sweeps_fp64_phase_restarts": gf.gf_get_stat(ctxr, "sweeps_fp64"),
-                       "theta_after_restarts": gf.gf_get_stat(ctxr, "theta_after_restarts"),
-                       "F_restarts": Fr, "dF_restarts": abs(Fr - F64), "theta_restarts": thr_,
-                       "converged_restarts": convr}
+        restart_row.update({
+            f"{tag}_s": time.perf_counter() - t0, f"sweeps_{tag}": itr,
+            f"sweeps_fp32_{tag}": gf.gf_get_stat(ctxr, "sweeps_fp32"),
+            f"sweeps_fp64_phase_{tag}": gf.gf_get_stat(ctxr, "sweeps_fp64"),
+            f"theta_after_fp32_stages_{tag}": gf.gf_get_stat(ctxr, "theta_after_restarts"),
+            f"F_{tag}": Fr, f"dF_{tag}": abs(Fr - F64), f"dF_vs_exact_{tag}": abs(Fr - Fdf),
+            f"theta_{tag}": thr_, f"converged_{tag}": convr,
+            f"dP_{tag}": abs(gf.gf_plaquette(ctxr, work) - P_in)})
+        if arith:
+            restart_row[f"sweeps_df64_{tag}"] = gf.gf_get_stat(ctxr, "sweeps_df64")
+    if restart_row:
+        restart_row.update({"restarts": args.fp32_restarts, "restart_theta_switch": args.restart_switch})
+
+    # measured FMA peaks (own kernel, CUDA events), clocks sampled meanwhile: the FP64 one is the
+    # denominator of the FP64 sweep's roofline
+    with ClockSampler(local if world > 1 else 0) as clk_peak:
+        fp64_peak, _ = gf.gf_fma_peak(True, 4000)
+        fp32_peak, _ = gf.gf_fma_peak(False, 200000)
+    peak_clocks = clk_peak.summary()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     host = torch.empty(pristine.shape, dtype=pristine.dtype, pin_memory=True)
@@ -424,10 +448,14 @@ def gpu_arm(args, rank, world, local):
             "isolated_launch_ms": thr[dom]["ms_per_half_sweep"]}
     if ph == "fp64":
         flops = Vh * 2253 / t_launch / 1e12
-        roof.update({"bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": flops / FP64_PEAK_TFLOPS,
-                     "peak_source": "derived: 152 SMs x 2 FP64 instructions per clock (ncu pipe peak) x 2 flop "
-                                    "per FMA x 2.07 GHz maximum SM clock (no measured FP64 peak)",
+        roof.update({"bound": "alu", "achieved": flops, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": flops / fp64_peak,
+                     "peak_source": "measured: gf_fma_peak (FP64 FMA chains, 8 blocks per SM, CUDA events), "
+                                    f"median SM clock {peak_clocks.get('sm_mhz')} MHz while measured",
+                     "derived_peak": FP64_PEAK_TFLOPS,
+                     "derived_peak_source": "152 SMs x 2 FP64 instructions per clock (ncu pipe peak) x 2 flop "
+                                            "per FMA x 2.07 GHz maximum SM clock",
+                     "fp32_fma_peak": fp32_peak,
                      "hbm_gbs": gbs, "hbm_frac": gbs / hbm if hbm else None,
                      "traffic": traffic64, "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "algorithmic_bytes": Vh * thr[dom]["bytes_per_site_update"]})
@@ -447,8 +475,11 @@ def gpu_arm(args, rank, world, local):
                           "sweeps_fp64_phase": sw64 / args.steps, "sweeps_all_fp64": it64,
                           "F_mixed": F_mixed, "F_fp64": F64, "dF": abs(F_mixed - F64),
                           "theta_mixed": th_mixed, "theta_fp64": th64,
+                          "dP_mixed": dP_mixed, "dP_fp64": dP_fp64,
                           "mixed_df64_s": t_df, "sweeps_mixed_df64": itdf, "F_mixed_df64": Fdf,
-                          "dF_mixed_df64": abs(Fdf - F64), "theta_mixed_df64": thdf,
+                          "dF_mixed_df64": abs(Fdf - F64), "theta_mixed_df64": thdf, "dP_mixed_df64": dP_df,
+                          "exact_reference": "F_mixed_df64: the double-float finish applies the tracked "
+                                             "transformation to the FP64 field once, in FP64 (no drift)",
                           "phase_ms": {"fp32": ms32 / args.steps, "fp64": ms64 / args.steps},
                           **(learned_row or {}), **(restart_row or {})},
         "sweep_throughput": thr,
@@ -533,7 +564,9 @@ def batched(args):
     """64 lattices (16 each of 8^4, 12^4, 16^4, 24^4; seeds 100..163; plaquette
     uniform in [0.55, 0.62] from seed 99), mixed precision, omega 1.7, theta <
     1e-12: one persistent launch per precision phase under a CUDA graph versus a
-    loop of single-lattice calls.  Prints one JSON object (not the headline line)."""
+    loop of single-lattice calls, with the FP64 phase in native FP64 and in
+    double-float arithmetic (fp64_arith 1: E = g - 1 tracked, applied in FP64).
+    Prints one JSON object (not the headline line)."""
     from paper_1209_4008_gb300 import gf, synth
     dims = [(L, L, L, L) for L in BATCH_SIZES for _ in range(16)]
     plaq = synth.batched_plaquettes(len(dims))
@@ -545,50 +578,64 @@ def batched(args):
         for w, p in zip(work, pristine):
             w.copy_(p)
 
-    b = gf.gf_batch_create(dims, gf.GF_LANDAU)
-    gf.gf_batch_set_option(b, "precision", gf.GF_MIXED)
-    gf.gf_batch_set_option(b, "check_every", CHECK_EVERY)
-    gf.gf_batch_set_stream(b, torch.cuda.current_stream())
-    tps, block = gf.gf_batch_autotune(b, work)
-    restore()
-    gf.gf_batch_overrelax(b, work, OMEGA, target, max_iter)  # warm-up: capture the graph
-    restore()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rc, iters, F, th = gf.gf_batch_overrelax(b, work, OMEGA, target, max_iter)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    su = sum(i * int(np.prod(d)) for i, d in zip(iters, dims))
-    stats = {k: gf.gf_batch_get_stat(b, k) for k in ("ms_fp32", "ms_fp64", "grid_fp32", "grid_fp64", "tiles",
-                                                      "threads_per_site", "block")}
-    # per-lattice loop through the single-lattice entry point
-    ctxs = []
-    for d in dims:
-        c = gf.gf_create(d, gf.GF_LANDAU)
-        gf.gf_set_option(c, "precision", gf.GF_MIXED)
-        gf.gf_set_option(c, "check_every", CHECK_EVERY)
-        gf.gf_set_option(c, "autotune", 1)
-        gf.gf_set_stream(c, torch.cuda.current_stream())
-        ctxs.append(c)
-    restore()
-    for c, w in zip(ctxs, work):  # warm-up (autotune, graphs)
-        gf.gf_overrelax(c, w, OMEGA, target, max_iter)
-    restore()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    su_loop = 0
-    for c, w, d in zip(ctxs, work, dims):
-        conv, it, _, _ = gf.gf_overrelax(c, w, OMEGA, target, max_iter)
-        su_loop += it * int(np.prod(d))
-    torch.cuda.synchronize()
-    t_loop = time.perf_counter() - t0
-    print(json.dumps({"workload": "batched-landau 64 lattices (16 each of 8^4,12^4,16^4,24^4), mixed, theta<1e-12",
-                      "sites": int(sum(np.prod(d) for d in dims)), "converged": rc == gf.GF_OK,
-                      "persistent": {"s": t_batch, "site_updates": su, "su_per_s": su / t_batch,
-                                     "threads_per_site": tps, "block": block, **stats},
-                      "loop": {"s": t_loop, "site_updates": su_loop, "su_per_s": su_loop / t_loop},
-                      "speedup": t_loop / t_batch,
-                      "sweeps_min_max": [min(iters), max(iters)]}), flush=True)
+    out = {"workload": "batched-landau 64 lattices (16 each of 8^4,12^4,16^4,24^4), mixed, theta<1e-12",
+           "sites": int(sum(np.prod(d) for d in dims))}
+    F_native = None
+    for arith in (0, 1):
+        b = gf.gf_batch_create(dims, gf.GF_LANDAU)
+        gf.gf_batch_set_option(b, "precision", gf.GF_MIXED)
+        gf.gf_batch_set_option(b, "check_every", CHECK_EVERY)
+        gf.gf_batch_set_option(b, "fp64_arith", arith)
+        gf.gf_batch_set_stream(b, torch.cuda.current_stream())
+        tps, block = gf.gf_batch_autotune(b, work)
+        restore()
+        gf.gf_batch_overrelax(b, work, OMEGA, target, max_iter)  # warm-up: capture the graph
+        restore()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, iters, F, th = gf.gf_batch_overrelax(b, work, OMEGA, target, max_iter)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        su = sum(i * int(np.prod(d)) for i, d in zip(iters, dims))
+        stats = {k: gf.gf_batch_get_stat(b, k) for k in ("ms_fp32", "ms_fp64", "grid_fp32", "grid_fp64", "tiles",
+                                                          "threads_per_site", "block")}
+        if arith:
+            stats["grid_df64"] = gf.gf_batch_get_stat(b, "grid_df64")
+        gf.gf_batch_destroy(b)
+        # per-lattice loop through the single-lattice entry point
+        ctxs = []
+        for d in dims:
+            c = gf.gf_create(d, gf.GF_LANDAU)
+            gf.gf_set_option(c, "precision", gf.GF_MIXED)
+            gf.gf_set_option(c, "check_every", CHECK_EVERY)
+            gf.gf_set_option(c, "autotune", 1)
+            gf.gf_set_option(c, "fp64_arith", arith)
+            gf.gf_set_stream(c, torch.cuda.current_stream())
+            ctxs.append(c)
+        restore()
+        for c, w in zip(ctxs, work):  # warm-up (autotune, graphs)
+            gf.gf_overrelax(c, w, OMEGA, target, max_iter)
+        restore()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        su_loop = 0
+        for c, w, d in zip(ctxs, work, dims):
+            conv, it, _, _ = gf.gf_overrelax(c, w, OMEGA, target, max_iter)
+            su_loop += it * int(np.prod(d))
+        torch.cuda.synchronize()
+        t_loop = time.perf_counter() - t0
+        for c in ctxs:
+            gf.gf_destroy(c)
+        if F_native is None:
+            F_native = F
+        out["df64" if arith else "native"] = {
+            "converged": rc == gf.GF_OK,
+            "persistent": {"s": t_batch, "site_updates": su, "su_per_s": su / t_batch,
+                           "threads_per_site": tps, "block": block, **stats},
+            "loop": {"s": t_loop, "site_updates": su_loop, "su_per_s": su_loop / t_loop},
+            "speedup": t_loop / t_batch, "sweeps_min_max": [min(iters), max(iters)],
+            "max_dF_vs_native": max(abs(a - c) for a, c in zip(F, F_native))}
+    print(json.dumps(out), flush=True)
 
 
 WEIGHTS = os.path.join(ROOT, "paper_1209_4008_gb300", "weights", "warm_start_16x16x16x16.npy")
@@ -640,6 +687,7 @@ def learned(args):
         row = {}
         for mode in ("mixed", "learned"):
             c = make_ctx(gf, gf.GF_MIXED)
+            gf.gf_set_option(c, "fp64_arith", args.eval_arith)
             if mode == "learned":
                 gf.gf_set_net(c, big)
                 gf.gf_set_option(c, "learned_repeat", args.learned_repeat)
@@ -662,6 +710,11 @@ def learned(args):
         row["dF"] = abs(row["learned"]["F"] - row["mixed"]["F"])
         res.append(row)
     mean = lambda key, mode: float(np.mean([r[mode][key] for r in res]))
+
+    def mmm(vals):
+        return {"min": float(np.min(vals)), "median": float(np.median(vals)), "max": float(np.max(vals))}
+    saved_sweeps = [r["mixed"]["sweeps_fp64"] - r["learned"]["sweeps_fp64"] for r in res]
+    saved_s = [r["mixed"]["s"] - r["learned"]["s"] for r in res]
     print(json.dumps({
         "workload": (f"learned warm start: stored parameters {args.weights}" if args.weights else
                      f"learned warm start: {args.pairs} solver pairs on 16^4 (plaquette 0.60), "
@@ -671,6 +724,10 @@ def learned(args):
         "mean": {"mixed_s": mean("s", "mixed"), "learned_s": mean("s", "learned"),
                  "mixed_fp64_sweeps": mean("sweeps_fp64", "mixed"),
                  "learned_fp64_sweeps": mean("sweeps_fp64", "learned")},
+        "fp64_phase_sweeps_saved": mmm(saved_sweeps), "seconds_saved": mmm(saved_s),
+        "time_ratio": mmm([r["learned"]["s"] / r["mixed"]["s"] for r in res]),
+        "max_dF": float(max(r["dF"] for r in res)), "all_dF_below_1e-10": all(r["dF"] < 1e-10 for r in res),
+        "fp64_arith": args.eval_arith,
         "total_s": time.perf_counter() - t_start}), flush=True)
 
 
@@ -854,6 +911,83 @@ def thermal(args):
     print(json.dumps(out), flush=True)
 
 
+def sr_study(args):
+    """Overrelaxation against stochastic relaxation (Sec. 1 names both; Sec. 5
+    tunes their parameters by the iterations to theta < 1e-12): sweeps and
+    time to theta < 1e-12 for omega in --omegas (overrelaxation) and p in
+    --probs (stochastic relaxation: the relaxation element, or with
+    probability p its square), on the 32^4 synthetic field (seeds 3/4) and on
+    that field thermalised at beta = 6.1 (--therm compound sweeps).  FP64
+    storage with double-float arithmetic (fp64_arith 1), theta checked every
+    25 sweeps.  Prints one JSON object."""
+    from paper_1209_4008_gb300 import gf, synth
+    target, max_iter = 1e-12, args.sr_max_iter
+    base = synth.make_field(DIMS, PLAQ, *SEEDS, device="cuda")
+    fields = {"synthetic": base}
+    if args.therm > 0:
+        g = gf.gf_create(DIMS, gf.GF_LANDAU)
+        th = base.clone()
+        gf.gf_generate(g, th, 6.1, args.therm, 4, 21, 0)
+        fields["beta6.1"] = th
+        gf.gf_destroy(g)
+    out = {"workload": f"32^4 Landau, theta<{target:g}, FP64 storage, double-float arithmetic, check every 25",
+           "therm_sweeps": args.therm, "fields": {}}
+    for name, U0 in fields.items():
+        rows = []
+        runs = [("or", float(w)) for w in args.omegas] + [("sr", float(q)) for q in args.probs]
+        for kind, val in runs:
+            c = gf.gf_create(DIMS, gf.GF_LANDAU)
+            gf.gf_set_stream(c, torch.cuda.current_stream())
+            gf.gf_set_option(c, "check_every", CHECK_EVERY)
+            gf.gf_set_option(c, "fp64_arith", 1)
+            if kind == "sr":
+                gf.gf_set_option(c, "stochastic_p", val)
+                gf.gf_set_option(c, "sr_seed", 5)
+            U = U0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            conv, it, F, thv = gf.gf_overrelax(c, U, val if kind == "or" else 1.0, target, max_iter)
+            torch.cuda.synchronize()
+            rows.append({"method": kind, "omega" if kind == "or" else "p": val, "sweeps": it, "converged": conv,
+                         "s": time.perf_counter() - t0, "F": F, "theta": thv})
+            gf.gf_destroy(c)
+            log(name, rows[-1])
+        pc = gf.gf_create(DIMS, gf.GF_LANDAU)
+        out["fields"][name] = {"plaquette": gf.gf_plaquette(pc, U0), "runs": rows}
+        gf.gf_destroy(pc)
+    print(json.dumps(out), flush=True)
+
+
+def single_solve(args):
+    """One gauge fixing of the seeded synthetic field on --dims (default 32^4)
+    with the mixed policy and the given --fp64-arith / --fp32-restarts, twice
+    (the second timed); for profiling the kernels of one policy.  Prints one
+    JSON object."""
+    from paper_1209_4008_gb300 import gf, synth
+    dims = tuple(args.dims) if args.dims else DIMS
+    U0 = synth.make_field(dims, PLAQ, *SEEDS, device="cuda")
+    c = gf.gf_create(dims, gf.GF_LANDAU)
+    gf.gf_set_stream(c, torch.cuda.current_stream())
+    for k, v in (("precision", gf.GF_MIXED), ("check_every", CHECK_EVERY), ("fp64_arith", args.fp64_arith),
+                 ("fp32_restarts", args.fp32_restarts), ("kernel_timing", 1),
+                 ("theta_switch", args.restart_switch if args.fp32_restarts else THETA_SWITCH)):
+        gf.gf_set_option(c, k, v)
+    for rep in range(2):
+        U = U0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        conv, it, F, th = gf.gf_overrelax(c, U, OMEGA, THETA_TARGET, MAX_ITER)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    st = {k: gf.gf_get_stat(c, k) for k in ("sweeps_fp32", "sweeps_fp64", "ms_sweep_kernels_fp32",
+                                              "sweep_launches_fp32", "ms_sweep_kernels_fp64", "sweep_launches_fp64")}
+    print(json.dumps({"dims": dims, "fp64_arith": args.fp64_arith, "fp32_restarts": args.fp32_restarts, "s": t,
+                      "sweeps": it, "F": F, "theta": th, "converged": conv,
+                      "ms_per_fp64_class_launch": st["ms_sweep_kernels_fp64"] / max(1, st["sweep_launches_fp64"]),
+                      "ms_per_fp32_launch": st["ms_sweep_kernels_fp32"] / max(1, st["sweep_launches_fp32"]),
+                      **st}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -883,7 +1017,9 @@ def main():
     ap.add_argument("--learned-factor", type=float, default=0.316,
                     help="theta falls by this factor between applications")
     ap.add_argument("--eval-fields", type=int, default=4)
-    ap.add_argument("--fp32-restarts", type=int, default=0,
+    ap.add_argument("--eval-arith", type=int, default=0, choices=[0, 1],
+                    help="--learned evaluation: fp64_arith of both legs (1: the exact double-float finish)")
+    ap.add_argument("--fp32-restarts", type=int, default=2,
                     help="add a line for the mixed policy with this many FP32 restarts (0: none)")
     ap.add_argument("--restart-switch", type=float, default=1e-30,
                     help="theta_switch of the FP32-restart line (default 1e-30: the first FP32 phase "
@@ -898,6 +1034,14 @@ def main():
                     help="--net: forward and backward-data convolutions with the halo-tile kernel")
     ap.add_argument("--mag", action="store_true", help="the maximally Abelian gauge on the 32^4 field")
     ap.add_argument("--thermal", action="store_true", help="gauge fixing of a field thermalised at beta 6.1")
+    ap.add_argument("--solve", action="store_true",
+                    help="one mixed-policy solve on --dims with --fp64-arith / --fp32-restarts (profiling)")
+    ap.add_argument("--fp64-arith", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--sr", action="store_true",
+                    help="sweeps to theta<1e-12 against omega (overrelaxation) and p (stochastic relaxation)")
+    ap.add_argument("--omegas", type=float, nargs="+", default=[1.5, 1.6, 1.7, 1.8, 1.9])
+    ap.add_argument("--probs", type=float, nargs="+", default=[0.5, 0.7, 0.8, 0.9, 0.95])
+    ap.add_argument("--sr-max-iter", type=int, default=40000)
     ap.add_argument("--therm", type=int, default=100, help="--thermal: compound sweeps of generation")
     ap.add_argument("--seeds", type=int, default=8)
     ap.add_argument("--sa-sweeps", type=int, default=3000)
@@ -925,6 +1069,14 @@ def main():
     if args.thermal:
         torch.cuda.set_device(0)
         thermal(args)
+        return
+    if args.sr:
+        torch.cuda.set_device(0)
+        sr_study(args)
+        return
+    if args.solve:
+        torch.cuda.set_device(0)
+        single_solve(args)
         return
     if args.kernel:
         torch.cuda.set_device(0)

@@ -165,7 +165,16 @@ int gf_set_stream(gf_ctx *ctx, void *stream);
  *   "fp64_arith"     FP64 phase and GF_FP64 policy: 0 = native FP64 (default),
  *                    1 = double-float values (pairs of FP32, 48-bit
  *                    significand, storage DF64_18) updated on the FP32 pipe;
- *                    per sweep within 1e-12 of FP64 */
+ *                    per sweep within 1e-12 of FP64.  In gf_overrelax the
+ *                    double-float sweeps run on a working copy of the FP64
+ *                    field and track the gauge transformation they apply as
+ *                    E = g - 1 in double-float; g = 1 + E (reunitarised in
+ *                    FP64) is then applied to the FP64 field in FP64, so the
+ *                    result is a gauge transform of the input to FP64
+ *                    rounding; native FP64 sweeps finish if theta of that
+ *                    field is not yet below the target.  With "stochastic_p"
+ *                    > 0 the double-float field is used throughout instead
+ *                    (stochastic sweeps do not track the transformation). */
 int gf_set_option(gf_ctx *ctx, const char *key, double value);
 int gf_get_option(const gf_ctx *ctx, const char *key, double *value);
 
@@ -177,6 +186,7 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *value);
  *   "ms_sweep_kernels_fp64", "sweep_launches_fp64" (device time of the
  *   half-sweep kernels of each phase and the number of launches it covers);
  *   GF_MIXED: "theta_switch_measured" (theta of the FP64 field at the switch);
+ *   with "fp64_arith" 1: "sweeps_df64" (double-float sweeps among "sweeps_fp64");
  *   with a network (gf_set_net): "theta_before_learned", "theta_after_learned"
  *   (around the first application), "ms_learned" (wall time of all
  *   applications), "learned_applications" (those after the first); with
@@ -202,6 +212,11 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
  * exp(Re tr[r K]/T) times the SU(2) Haar measure (Creutz for |k|/T < 2,
  * Kennedy-Pendleton otherwise) from Philox4x32-10 with key = seed and
  * counter = (lexicographic site, sweep_offset + k, 256 * subgroup + draw, 1).
+ * With "fp64_arith" 1 (and a policy other than GF_FP32) the sweeps run in
+ * double-float arithmetic on a copy of the FP64 field while the
+ * transformation is tracked as E = g - 1, and g = 1 + E is applied to the
+ * FP64 field in FP64 at the end: the annealed field stays a gauge transform
+ * of the input to FP64 rounding.
  * U: canonical field, host or device, in/out.  Returns GF_EREJECT if some
  * draws hit "sa_cap" (those subgroups are left unchanged). */
 int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t seed);
@@ -392,11 +407,17 @@ int gf_batch_set_stream(gf_batch *b, void *stream);
  * "barrier_timeout_ms" (bounded grid-barrier wait, default 2000; on expiry
  * the call returns GF_ETIMEOUT and the batch stays usable),
  * "barrier_extra_blocks" (test hook: 1 makes every barrier wait for a block
- * that does not exist, so the bounded wait expires). */
+ * that does not exist, so the bounded wait expires), "fp64_arith" (default
+ * 0; 1 = the FP64 phase runs as double-float sweeps on copies of the FP64
+ * fields, one thread per site, with E = g - 1 tracked in double-float, then
+ * g = 1 + E is applied to each FP64 field in FP64 and native FP64 sweeps
+ * finish any lattice not yet below the target: the results stay gauge
+ * transforms of the inputs to FP64 rounding, as in gf_overrelax). */
 int gf_batch_set_option(gf_batch *b, const char *key, double value);
 
-/* Stats of the last call: "site_updates", "ms_fp32", "ms_fp64", "ms_total",
- * "grid_fp32", "grid_fp64", "threads_per_site", "block", "tiles". */
+/* Stats of the last call: "site_updates", "ms_fp32", "ms_fp64" (the whole
+ * FP64-class phase), "ms_total", "grid_fp32", "grid_fp64", "grid_df64",
+ * "threads_per_site", "block", "tiles". */
 int gf_batch_get_stat(const gf_batch *b, const char *key, double *value);
 
 /* Gauge-fix every U[i] (device pointers, canonical layout, in place) by
@@ -406,10 +427,39 @@ int gf_batch_get_stat(const gf_batch *b, const char *key, double *value);
 int gf_batch_overrelax(gf_batch *b, double *const *U, double omega, double theta_target, int max_iter,
                        int *iters, double *F, double *theta);
 
+/* The batched solve in one call (Alg. 1 for each of n Landau-gauge lattices,
+ * theta checked every 25 sweeps on the device, Sec. 4.1): a batch with the
+ * default options (GF_MIXED, FP32 12-real then FP64 18-real storage, switch
+ * at theta < 1e-6, threads per site and block from the autotuner's cache of
+ * this process or the defaults) is created, run once on the legacy default
+ * stream and destroyed.  dims: n rows of {Lx, Ly, Lz, Lt}; U: n device
+ * pointers (canonical layout, in place); iters, F, theta: arrays of n (may
+ * be NULL).  Returns GF_OK if every lattice converged, GF_ENOTCONVERGED
+ * otherwise, or the error of the first failing step (the message is not
+ * kept: callers that need it, other options, another gauge, a stream or
+ * repeated solves use gf_batch_create / gf_batch_overrelax, which also keep
+ * the device arena and replay the captured graph). */
+int gf_overrelax_batched(int n, const int (*dims)[4], double **U, double omega, double theta_target, int max_iter,
+                         int *iters, double *F, double *theta);
+
 /* Choose threads per site and block size for both storage formats by timing
  * every candidate on the fields U (left unchanged); cached per set of
  * extents for the process.  Outputs (FP32 phase choice) may be NULL. */
 int gf_batch_autotune(gf_batch *b, double *const *U, int *threads_per_site, int *block);
+
+/* ------------------------------------------------ measured arithmetic peak */
+
+/* The arithmetic rate this GPU sustains, for the roofline of the sweeps that
+ * are bound by an arithmetic unit rather than by HBM (the FP64 sweeps are
+ * bound by the FP64 unit).  Launches, on the legacy default stream of the
+ * current device, 8 blocks per SM of 256 threads, each thread running eight
+ * independent chains of iters fused multiply-adds (fp64 = 1: double, 0:
+ * float); one warm-up launch, then three timed with CUDA events.  The paper
+ * has no counterpart (it quotes Fermi's nominal figures); this is a
+ * measurement helper.  Outputs (may be NULL): *tflops = 2 x FMAs / time in
+ * 10^12 flop/s, *ms_per_launch.  Synchronises the device's default stream.
+ * GF_EINVAL for fp64 outside {0, 1} or iters < 1; GF_ECUDA on a CUDA error. */
+int gf_fma_peak(int fp64, int iters, double *tflops, double *ms_per_launch);
 
 /* ------------------------------------------------- allocation-free measure */
 

@@ -23,14 +23,18 @@ namespace {
 struct GraphKey {
     int fmt, tps, block, n, trackg, measure, reunit, ktime, orv, slices;
     double omega;
-    const void *field, *gt;
+    const void *field, *gt, *ge;
     bool operator<(const GraphKey &o) const
     {
-        return std::tie(fmt, tps, block, n, trackg, measure, reunit, ktime, orv, slices, omega, field, gt) <
+        return std::tie(fmt, tps, block, n, trackg, measure, reunit, ktime, orv, slices, omega, field, gt, ge) <
                std::tie(o.fmt, o.tps, o.block, o.n, o.trackg, o.measure, o.reunit, o.ktime, o.orv, o.slices,
-                        o.omega, o.field, o.gt);
+                        o.omega, o.field, o.gt, o.ge);
     }
 };
+
+// resident state of gf_overrelax's double-float stages: the working copy
+// (fdf, DF64_18) of the exact FP64 field (f64); never visible between calls
+constexpr int kResDfWork = 3;
 
 std::mutex g_tune_mutex;
 // autotuner cache: (Lx, Ly, Lz, Lt, format, gauge, mode) -> (threads per site, block);
@@ -60,6 +64,7 @@ struct gf_ctx {
     int tps = 0;
     int block = 0;
     int fp64_arith = 0;  // FP64 phase: 0 native FP64, 1 double-float on the FP32 pipe (DF64_18)
+    bool exact_run = false;  // inside gf_overrelax with double-float stages on a copy of an FP64 field
     int variant = 0;  // 0 auto, 1 per-subgroup rotations of the held links, 2 accumulate form
     int acc_regs = 0;  // accumulate form, FP64 storage: register budget 255, 168 or 128 (0 = autotuned)
     int or_variant = 0;  // g -> g^omega: 0 rational 19-flop form, 1 first order, 2 exact power
@@ -92,6 +97,8 @@ struct gf_ctx {
     char *f32 = nullptr;
     size_t f32_bytes = 0;
     char *gt = nullptr;
+    char *fdf = nullptr;  // double-float working copy of the FP64 field (gf_overrelax, fp64_arith 1)
+    char *ge = nullptr;   // E = g - 1 tracked by the double-float sweeps (DF64_18 site field)
     double *staging = nullptr;
     double *partials = nullptr;
     double *dres = nullptr;
@@ -138,7 +145,7 @@ static int cuda_fail(gf_ctx *c, cudaError_t e, const char *what)
 // ---------------------------------------------------------------------------
 static int fmt64(const gf_ctx *c)
 {
-    if (c->fp64_arith == 1) return DF64_18;
+    if (c->fp64_arith == 1 && !c->exact_run) return DF64_18;
     return c->storage64 == 12 ? F64_12 : F64_18;
 }
 static int fmt32(const gf_ctx *c) { return c->storage32 == 18 ? F32_18 : F32_12; }
@@ -210,6 +217,20 @@ static int ensure_gauge_field(gf_ctx *ctx)
     return GF_OK;
 }
 
+// the double-float working field and the E field of gf_overrelax's double-float stages
+static int ensure_df_work(gf_ctx *ctx)
+{
+    if (!ctx->fdf) {
+        drop_graphs(ctx);
+        CK(cudaMalloc(&ctx->fdf, field_bytes(ctx, DF64_18)));
+    }
+    if (!ctx->ge) {
+        drop_graphs(ctx);
+        CK(cudaMalloc(&ctx->ge, 2 * 9 * plane_bytes(ctx)));
+    }
+    return GF_OK;
+}
+
 static int ensure_staging(gf_ctx *ctx)
 {
     if (!ctx->staging) CK(cudaMalloc(&ctx->staging, sizeof(double) * 72 * (size_t)ctx->V));
@@ -235,7 +256,11 @@ static int device_view(gf_ctx *ctx, const double *U, const double **view, bool *
     return GF_OK;
 }
 
-static char *resident_base(gf_ctx *ctx) { return ctx->resident == GF_FP64 ? ctx->f64 : ctx->f32; }
+static char *resident_base(gf_ctx *ctx)
+{
+    if (ctx->resident == kResDfWork) return ctx->fdf;
+    return ctx->resident == GF_FP64 ? ctx->f64 : ctx->f32;
+}
 
 // ---------------------------------------------------------------------------
 // launch configuration
@@ -284,6 +309,7 @@ static SweepArgs sweep_args(gf_ctx *ctx, char *field, int parity, double omega)
     memset(&a, 0, sizeof a);
     a.f = ref(ctx, field);
     a.gt = ref(ctx, ctx->gt);
+    if (ctx->resident == kResDfWork && field == ctx->fdf) a.ge = ref(ctx, ctx->ge);
     a.g = ctx->geom;
     a.parity = parity;
     a.omega = omega;
@@ -341,7 +367,8 @@ static int run_chunk(gf_ctx *ctx, int fmt, char *field, double omega, int n, boo
     }
     if (ctx->use_graphs && n > 0) {
         GraphKey key{ fmt,    cfg.first,       cfg.second,       n,     trackg, measure, reunit, kt ? 1 : 0,
-                      ctx->or_variant, ctx->slice_theta, omega, field, ctx->gt };
+                      ctx->or_variant, ctx->slice_theta, omega, field, ctx->gt,
+                      ctx->resident == kResDfWork ? ctx->ge : nullptr };
         auto it = ctx->graphs.find(key);
         if (it == ctx->graphs.end()) {
             cudaGraph_t graph;
@@ -534,6 +561,61 @@ static bool tuned(const gf_ctx *c, int fmt, int mode = 0)
     return g_tune_cache.count(tune_key(c, fmt, mode)) > 0;
 }
 
+// One double-float stage of gf_overrelax's FP64 phase ("fp64_arith" 1).  The
+// resident FP64 field (the exact field) is copied into the double-float
+// working field, whose sweeps run on the FP32 pipe while the transformation
+// they apply is tracked as E = g - 1 in double-float; at the end g = 1 + E,
+// reunitarised in FP64, is applied to the exact field in FP64.  The exact
+// field therefore stays a gauge transform of the input to FP64 rounding,
+// whatever the double-float rounding of the working copy.  On entry F and
+// theta are those of the exact field; on return, too.
+static int df_stage(gf_ctx *ctx, double omega, double target, int budget, int *used, double *F, double *theta)
+{
+    *used = 0;
+    if (*theta < target || budget <= 0) return GF_OK;
+    const int xfmt = ctx->resident_fmt;
+    RET(ensure_df_work(ctx));
+    CK(launch_to_df(xfmt, ref(ctx, ctx->f64), ref(ctx, ctx->fdf), ctx->geom, ctx->stream));
+    CK(cudaMemsetAsync(ctx->ge, 0, 2 * 9 * plane_bytes(ctx), ctx->stream));
+    ctx->resident = kResDfWork;
+    ctx->resident_fmt = DF64_18;
+    if (ctx->autotune && !tuned(ctx, DF64_18)) {
+        const int rc = autotune_format(ctx, DF64_18, ctx->fdf, nullptr, nullptr);
+        if (rc != GF_OK) {
+            ctx->resident = GF_FP64;
+            ctx->resident_fmt = xfmt;
+            return rc;
+        }
+    }
+    double Fw = *F, thw = *theta;
+    int u = 0;
+    const int rc = converge(ctx, omega, target, budget, true, false, &u, &Fw, &thw);
+    ctx->resident = GF_FP64;  // back to the exact field, whatever happened
+    ctx->resident_fmt = xfmt;
+    RET(rc);
+    CK(launch_apply_gauge_e(xfmt, ref(ctx, ctx->f64), ref(ctx, ctx->ge), ctx->geom, ctx->stream));
+    RET(measure_resident(ctx, F, theta));
+    *used = u;
+    ctx->stats["sweeps_df64"] += u;
+    return GF_OK;
+}
+
+// FP64-class convergence of the resident FP64 field: double-float stages
+// (exact_run), then native FP64 sweeps for whatever target is left; else
+// native FP64 sweeps (12-real storage reunitarised at every check)
+static int converge64(gf_ctx *ctx, double omega, double target, int budget, int *used, double *F, double *theta)
+{
+    *used = 0;
+    if (ctx->exact_run) {
+        RET(df_stage(ctx, omega, target, budget, used, F, theta));
+        budget -= *used;
+    }
+    int u = 0;
+    RET(converge(ctx, omega, target, budget, false, twelve_real(ctx->resident_fmt), &u, F, theta));
+    *used += u;
+    return GF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // learned warm start (resident FP64 field)
 // ---------------------------------------------------------------------------
@@ -614,6 +696,8 @@ int gf_destroy(gf_ctx *ctx)
     cudaFree(ctx->f64);
     cudaFree(ctx->f32);
     cudaFree(ctx->gt);
+    cudaFree(ctx->fdf);
+    cudaFree(ctx->ge);
     cudaFree(ctx->staging);
     cudaFree(ctx->feat);
     cudaFree(ctx->cbuf);
@@ -933,6 +1017,13 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
     const double *view;
     bool host;
     RET(device_view(ctx, U, &view, &host));
+    // double-float FP64 phase: stages on a working copy of an FP64 field (not
+    // with stochastic relaxation, whose sweeps do not track the transformation)
+    struct ExactRun {
+        gf_ctx *c;
+        ~ExactRun() { c->exact_run = false; }
+    } exact_guard{ ctx };
+    ctx->exact_run = ctx->fp64_arith == 1 && ctx->sr_p == 0.0;
 
     int used32 = 0, used64 = 0;
     double F = 0.0, theta = 0.0, ms32 = 0.0, ms64 = 0.0;
@@ -943,7 +1034,7 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
         RET(measure_resident(ctx, &F, &theta));
         double t1 = now_ms();
         // 12-real storage: reunitarised at every check (row 2 is rebuilt on every load)
-        RET(converge(ctx, omega, theta_target, max_iter, false, twelve_real(ctx->resident_fmt), &used64, &F, &theta));
+        RET(converge64(ctx, omega, theta_target, max_iter, &used64, &F, &theta));
         ms64 = now_ms() - t1;
     } else {
         bool track = ctx->precision == GF_MIXED && ctx->track_gauge;
@@ -1035,8 +1126,7 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
             while (repeats > 0 && theta > 0.0 && !(theta < theta_target)) {
                 const double stage = std::max(theta_target, theta * ctx->learned_factor);
                 int u = 0;
-                RET(converge(ctx, omega, stage, max_iter - used32 - used64, false, twelve_real(ctx->resident_fmt), &u,
-                             &F, &theta));
+                RET(converge64(ctx, omega, stage, max_iter - used32 - used64, &u, &F, &theta));
                 used64 += u;
                 if (!(theta < stage) || theta < theta_target) break;  // budget spent, or done
                 double t3 = now_ms();
@@ -1047,8 +1137,7 @@ int gf_overrelax(gf_ctx *ctx, double *U, double omega, double theta_target, int 
                 --repeats;
             }
             int u = 0;
-            RET(converge(ctx, omega, theta_target, max_iter - used32 - used64, false, twelve_real(ctx->resident_fmt), &u,
-                         &F, &theta));
+            RET(converge64(ctx, omega, theta_target, max_iter - used32 - used64, &u, &F, &theta));
             used64 += u;
             ms64 = now_ms() - t2;
         } else {
@@ -1195,7 +1284,32 @@ int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t 
     bool host;
     RET(device_view(ctx, U, &view, &host));
     int prec = ctx->precision == GF_FP32 ? GF_FP32 : GF_FP64;
+    // fp64_arith 1: the heatbath sweeps run on a double-float copy of the FP64 field with the
+    // transformation tracked as E = g - 1 and applied to the FP64 field in FP64 at the end, so the
+    // annealed field stays a gauge transform of the input to FP64 rounding
+    const bool exact = ctx->fp64_arith == 1 && prec == GF_FP64;
+    struct ExactRun {
+        gf_ctx *c;
+        int xfmt;
+        ~ExactRun()
+        {
+            c->exact_run = false;
+            if (c->resident == kResDfWork) {  // an error left the working copy resident
+                c->resident = GF_FP64;
+                c->resident_fmt = xfmt;
+            }
+        }
+    } exact_guard{ ctx, F64_18 };
+    ctx->exact_run = exact;
     RET(upload(ctx, view, prec));
+    if (exact) {
+        exact_guard.xfmt = ctx->resident_fmt;
+        RET(ensure_df_work(ctx));
+        CK(launch_to_df(ctx->resident_fmt, ref(ctx, ctx->f64), ref(ctx, ctx->fdf), ctx->geom, ctx->stream));
+        CK(cudaMemsetAsync(ctx->ge, 0, 2 * 9 * plane_bytes(ctx), ctx->stream));
+        ctx->resident = kResDfWork;
+        ctx->resident_fmt = DF64_18;
+    }
     if (ctx->autotune && !tuned(ctx, ctx->resident_fmt, 1))
         RET(autotune_format(ctx, ctx->resident_fmt, resident_base(ctx), nullptr, nullptr, 1));
     CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int) * 4, ctx->stream));
@@ -1211,10 +1325,15 @@ int gf_anneal(gf_ctx *ctx, double *U, double T0, double T1, int steps, uint64_t 
             a.T = T;
             a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
             a.sweep = ctx->sa_sweep_offset + (uint32_t)k;
-            CK(launch_sweep(ctx->resident_fmt, a, cfg.first, coulomb_of(ctx), 1, false, cfg.second, ctx->stream));
+            CK(launch_sweep(ctx->resident_fmt, a, cfg.first, coulomb_of(ctx), 1, exact, cfg.second, ctx->stream));
         }
         if (reunit && (k % 4 == 3 || k == steps - 1))
             CK(launch_reunitarize(ctx->resident_fmt, ref(ctx, resident_base(ctx)), ctx->geom, ctx->stream));
+    }
+    if (exact) {
+        ctx->resident = GF_FP64;
+        ctx->resident_fmt = exact_guard.xfmt;
+        CK(launch_apply_gauge_e(ctx->resident_fmt, ref(ctx, ctx->f64), ref(ctx, ctx->ge), ctx->geom, ctx->stream));
     }
     int rejects = 0;
     CK(cudaMemcpyAsync(ctx->hres + 2, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

@@ -23,6 +23,7 @@
 #include "gf.h"
 #include "gf_fieldops.cuh"
 #include "gf_sweep.cuh"
+#include "gf_sweep_df64.cuh"
 
 using namespace gf;
 
@@ -31,6 +32,7 @@ namespace gf {
 struct BatchConfig {
     Geom g;
     size_t off32, off64, offg;  // byte offsets of this configuration's fields in the arenas
+    size_t offdf, offe;         // double-float working copy and its E = g - 1 site field
     int tile0;                  // first tile of this configuration (per parity)
     int ntiles;                 // tiles per parity
     int nk;                     // directions in F and theta
@@ -44,7 +46,8 @@ struct BatchArgs {
     int ntiles;           // tiles per parity (all configurations)
     char *arena;          // field arena of the phase's precision
     char *garena;         // gauge-tracking arena (FP32-12 site fields)
-    int fp64;             // 1: arena offsets are off64, else off32
+    char *earena;         // double-float phase: E = g - 1 arena (DF64_18 site fields)
+    int kind;             // arena offsets: 0 off32 (FP32), 1 off64 (FP64), 2 offdf (double-float copy)
     double omega;
     double target;
     int check_every;
@@ -103,7 +106,7 @@ __device__ bool grid_barrier(const BatchArgs &b)
 template <int FMT>
 __device__ __forceinline__ FieldRef field_of(const BatchArgs &b, const BatchConfig &c)
 {
-    return FieldRef{ b.arena + (b.fp64 ? c.off64 : c.off32), (size_t)c.g.plane * 16 };
+    return FieldRef{ b.arena + (b.kind == 2 ? c.offdf : (b.kind == 1 ? c.off64 : c.off32)), (size_t)c.g.plane * 16 };
 }
 
 __device__ __forceinline__ FieldRef gauge_of(const BatchArgs &b, const BatchConfig &c)
@@ -210,6 +213,7 @@ __global__ void __launch_bounds__(256) k_batch_persistent(BatchArgs b)
                     int h = (t - c.tile0) * spt + ls;
                     if (h >= c.g.Vh) continue;
                     SweepArgs a;
+                    memset(&a, 0, sizeof a);
                     a.f = field_of<FMT>(b, c);
                     a.gt = gauge_of(b, c);
                     a.g = c.g;
@@ -221,7 +225,15 @@ __global__ void __launch_bounds__(256) k_batch_persistent(BatchArgs b)
                     a.sweep = 0;
                     a.cap = 1;
                     a.status = b.status;
-                    if (TPS == 0) {
+                    if constexpr (FMT == DF64_18) {
+                        // double-float copy of an FP64 field: the transformation is tracked as E = g - 1,
+                        // prefetched into shared memory while the site update runs
+                        extern __shared__ float4 epre[];
+                        a.ge = FieldRef{ b.earena + c.offe, (size_t)c.g.plane * 16 };
+                        prefetch_e_df(a, p, h, epre, threadIdx.x, blockDim.x);
+                        if (c.nk == 3) sweep_site_df<true, MODE_OR, false, true>(a, h, epre, threadIdx.x, blockDim.x);
+                        else sweep_site_df<false, MODE_OR, false, true>(a, h, epre, threadIdx.x, blockDim.x);
+                    } else if (TPS == 0) {
                         if (c.nk == 3) sweep_site_acc<FMT, true, MODE_OR, TRACKG>(a, h);
                         else sweep_site_acc<FMT, false, MODE_OR, TRACKG>(a, h);
                     } else {
@@ -255,8 +267,21 @@ __global__ void k_batch_next_phase(int n, int max_iter, int *conv, int *sweeps, 
     conv[i] = 0;
 }
 
+// Between the double-float phase and the native FP64 one: remember the
+// double-float sweeps, give each configuration the rest of its budget and
+// clear the convergence flags.
+__global__ void k_batch_after_df(int n, int *conv, int *sweeps, int *maxit, int *sweepsdf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    sweepsdf[i] = sweeps[i];
+    maxit[i] -= sweeps[i];
+    sweeps[i] = 0;
+    conv[i] = 0;
+}
+
 __global__ void k_batch_first_phase(int n, int max_iter, int *conv, int *sweeps, int *maxit, int *sweeps32,
-                                    int *status, unsigned *bar)
+                                    int *sweepsdf, int *status, unsigned *bar)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
@@ -264,6 +289,7 @@ __global__ void k_batch_first_phase(int n, int max_iter, int *conv, int *sweeps,
         sweeps[i] = 0;
         sweeps32[i] = 0;
         conv[i] = 0;
+        sweepsdf[i] = 0;
     }
     if (i == 0) {
         *status = 0;
@@ -302,6 +328,7 @@ void *kernel_for(int fmt, int tps, bool trackg)
     GF_K(F32_12, 0) GF_K(F32_12, 1) GF_K(F32_12, 2) GF_K(F32_12, 4) GF_K(F32_12, 8)
     GF_K(F32_18, 0) GF_K(F32_18, 1) GF_K(F32_18, 2) GF_K(F32_18, 4) GF_K(F32_18, 8)
 #undef GF_K
+    if (fmt == DF64_18 && tps == 0 && !trackg) return persistent_kernel_ptr<DF64_18, 0, false>(false);
 #define GF_K64(F, T) \
     if (fmt == F && tps == T && !trackg) return persistent_kernel_ptr<F, T, false>(false);
     GF_K64(F64_18, 0) GF_K64(F64_18, 1) GF_K64(F64_18, 2) GF_K64(F64_18, 4) GF_K64(F64_18, 8)
@@ -327,18 +354,19 @@ struct gf_batch {
     int check_every = 25;
     double theta_switch = 1e-6;
     int tps = 0, block = 0;
+    int fp64_arith = 0;  // 1: FP64 phase as double-float sweeps on copies, E tracked, applied in FP64
     double timeout_ms = 2000.0;
     int extra_blocks = 0;  // test hook: a barrier that can never complete
     cudaStream_t stream = nullptr;
     // device memory
-    char *a32 = nullptr, *a64 = nullptr, *ag = nullptr;
-    size_t a32_bytes = 0, a64_bytes = 0, ag_bytes = 0;
+    char *a32 = nullptr, *a64 = nullptr, *ag = nullptr, *adf = nullptr, *ae = nullptr;
+    size_t a32_bytes = 0, a64_bytes = 0, ag_bytes = 0, adf_bytes = 0, ae_bytes = 0;
     BatchConfig *dcfg = nullptr;
     int *dtile = nullptr;
     int tiles_spt = 0;  // sites per tile the tile table was built for
     int ntiles = 0;
     double *partials = nullptr;
-    int *dint = nullptr;     // conv[n], sweeps[n], maxit[n], sweeps32[n], status, bar[2]
+    int *dint = nullptr;     // conv[n], sweeps[n], maxit[n], sweeps32[n], status, pad, bar[2], sweepsdf[n]
     double *ddbl = nullptr;  // F[n], theta[n]
     int *hint = nullptr;
     double *hdbl = nullptr;
@@ -406,7 +434,7 @@ static int build_tiles(gf_batch *b, int spt)
     if (b->tiles_spt == spt && b->dtile) return GF_OK;
     b->cfg.assign(b->n, BatchConfig{});
     std::vector<int> tiles;
-    size_t o32 = 0, o64 = 0, og = 0;
+    size_t o32 = 0, o64 = 0, og = 0, odf = 0, oe = 0;
     for (int i = 0; i < b->n; ++i) {
         BatchConfig &c = b->cfg[i];
         c.g = b->geom[i];
@@ -414,9 +442,13 @@ static int build_tiles(gf_batch *b, int spt)
         c.off32 = o32;
         c.off64 = o64;
         c.offg = og;
+        c.offdf = odf;
+        c.offe = oe;
         o32 += 8 * (size_t)format_chunks(bfmt32(b)) * pb;
         o64 += 8 * (size_t)format_chunks(bfmt64(b)) * pb;
         og += 6 * pb;
+        odf += 8 * (size_t)format_chunks(DF64_18) * pb;
+        oe += 2 * 9 * pb;
         c.tile0 = (int)tiles.size();
         c.ntiles = (c.g.Vh + spt - 1) / spt;
         c.nk = b->gauge == GF_COULOMB ? 3 : 4;
@@ -439,6 +471,18 @@ static int build_tiles(gf_batch *b, int spt)
         b->ag = nullptr;
         BCK(cudaMalloc(&b->ag, og));
         b->ag_bytes = og;
+    }
+    if (b->fp64_arith && b->adf_bytes < odf) {
+        cudaFree(b->adf);
+        b->adf = nullptr;
+        BCK(cudaMalloc(&b->adf, odf));
+        b->adf_bytes = odf;
+    }
+    if (b->fp64_arith && b->ae_bytes < oe) {
+        cudaFree(b->ae);
+        b->ae = nullptr;
+        BCK(cudaMalloc(&b->ae, oe));
+        b->ae_bytes = oe;
     }
     cudaFree(b->dcfg);
     cudaFree(b->dtile);
@@ -464,6 +508,8 @@ static int *maxit_of(gf_batch *b) { return b->dint + 2 * b->n; }
 static int *sweeps32_of(gf_batch *b) { return b->dint + 3 * b->n; }
 static int *status_of(gf_batch *b) { return b->dint + 4 * b->n; }
 static unsigned *bar_of(gf_batch *b) { return (unsigned *)(b->dint + 4 * b->n + 2); }
+static int *sweepsdf_of(gf_batch *b) { return b->dint + 4 * b->n + 4; }
+static size_t dint_count(const gf_batch *b) { return 5 * (size_t)b->n + 4; }
 
 // An event recorded inside a stream capture must be an external record node
 // to be recorded (and timeable) when the graph is replayed.
@@ -481,13 +527,18 @@ static int issue_phase(gf_batch *b, int fmt, bool trackg, double omega, double t
 {
     std::pair<int, int> lc = batch_config(b, fmt);
     int tps = lc.first, block = lc.second;
+    if (fmt == DF64_18) {  // the double-float site update: one thread per site
+        tps = 0;
+        block = b->tiles_spt;
+    }
     if (b->tiles_spt != block / (tps == 0 ? 1 : tps)) return bfail(b, GF_EINVAL, "both phases need the same sites per tile");
     void *fn = kernel_for(fmt, tps, trackg);
     if (!fn) return bfail(b, GF_EINVAL, "no batched kernel for this format / threads per site");
     int dev = 0, nsm = 0, per_sm = 0;
+    const size_t smem = fmt == DF64_18 ? 9 * sizeof(float4) * (size_t)block : 0;  // prefetched E
     BCK(cudaGetDevice(&dev));
     BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0));
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem));
     if (per_sm < 1) return bfail(b, GF_ECUDA, "batched kernel cannot be resident");
     int grid = nsm * per_sm;
     if (grid > 2 * b->ntiles) grid = 2 * b->ntiles;
@@ -498,9 +549,11 @@ static int issue_phase(gf_batch *b, int fmt, bool trackg, double omega, double t
     a.tile_cfg = b->dtile;
     a.ncfg = b->n;
     a.ntiles = b->ntiles;
-    a.fp64 = !(fmt == F32_12 || fmt == F32_18);
-    a.arena = a.fp64 ? b->a64 : b->a32;
+    const bool fp64 = !(fmt == F32_12 || fmt == F32_18);
+    a.kind = fmt == DF64_18 ? 2 : (fp64 ? 1 : 0);
+    a.arena = a.kind == 2 ? b->adf : (fp64 ? b->a64 : b->a32);
     a.garena = b->ag;
+    a.earena = b->ae;
     a.omega = omega;
     a.target = target;
     a.check_every = b->check_every;
@@ -514,13 +567,13 @@ static int issue_phase(gf_batch *b, int fmt, bool trackg, double omega, double t
     a.status = status_of(b);
     a.timeout_ns = (long long)(b->timeout_ms * 1e6);
     a.expected_blocks = (unsigned)(grid + b->extra_blocks);
-    a.reunit = a.fp64 ? 0 : 1;
+    a.reunit = fp64 ? 0 : 1;
 
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = b->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -529,7 +582,7 @@ static int issue_phase(gf_batch *b, int fmt, bool trackg, double omega, double t
     cfg.numAttrs = 1;
     void *args[] = { &a };
     BCK(cudaLaunchKernelExC(&cfg, fn, args));
-    b->stats[a.fp64 ? "grid_fp64" : "grid_fp32"] = grid;
+    b->stats[a.kind == 2 ? "grid_df64" : (fp64 ? "grid_fp64" : "grid_fp32")] = grid;
     b->stats["threads_per_site"] = tps;
     b->stats["block"] = block;
     return GF_OK;
@@ -545,7 +598,7 @@ static int issue_solve(gf_batch *b, double *const *U, double omega, double theta
     int nb = (b->n + 127) / 128;
     BCK(record_event(b, b->ev[0]));
     k_batch_first_phase<<<nb, 128, 0, b->stream>>>(b->n, max_iter, conv_of(b), sweeps_of(b), maxit_of(b),
-                                                  sweeps32_of(b), status_of(b), bar_of(b));
+                                                  sweeps32_of(b), sweepsdf_of(b), status_of(b), bar_of(b));
     BCK(cudaGetLastError());
     if (fp32_first) {
         for (int i = 0; i < b->n; ++i) {
@@ -571,6 +624,21 @@ static int issue_solve(gf_batch *b, double *const *U, double omega, double theta
                                                c.g, b->stream));
             else
                 BCK(launch_encode(f64, U[i], d64, c.g, b->stream));
+            if (b->fp64_arith)
+                BCK(launch_to_df(f64, d64, FieldRef{ b->adf + c.offdf, (size_t)c.g.plane * 16 }, c.g, b->stream));
+        }
+        if (b->fp64_arith) {
+            // double-float sweeps on the copies, E = g - 1 tracked; g applied to the FP64 fields in
+            // FP64; native FP64 sweeps then finish whatever lattice is not yet below the target
+            BCK(cudaMemsetAsync(b->ae, 0, b->ae_bytes, b->stream));
+            BRET(issue_phase(b, DF64_18, false, omega, theta_target));
+            for (int i = 0; i < b->n; ++i) {
+                const BatchConfig &c = b->cfg[i];
+                BCK(launch_apply_gauge_e(f64, FieldRef{ b->a64 + c.off64, (size_t)c.g.plane * 16 },
+                                         FieldRef{ b->ae + c.offe, (size_t)c.g.plane * 16 }, c.g, b->stream));
+            }
+            k_batch_after_df<<<nb, 128, 0, b->stream>>>(b->n, conv_of(b), sweeps_of(b), maxit_of(b), sweepsdf_of(b));
+            BCK(cudaGetLastError());
         }
         BRET(issue_phase(b, f64, false, omega, theta_target));
     }
@@ -582,7 +650,7 @@ static int issue_solve(gf_batch *b, double *const *U, double omega, double theta
         if (!fp64_phase) BCK(launch_reunitarize(f32, f, c.g, b->stream));
         BCK(launch_decode(fmt_out, f, c.g, U[i], b->stream));
     }
-    BCK(cudaMemcpyAsync(b->hint, b->dint, sizeof(int) * (4 * (size_t)b->n + 4), cudaMemcpyDeviceToHost,
+    BCK(cudaMemcpyAsync(b->hint, b->dint, sizeof(int) * dint_count(b), cudaMemcpyDeviceToHost,
                         b->stream));
     BCK(cudaMemcpyAsync(b->hdbl, b->ddbl, sizeof(double) * 2 * b->n, cudaMemcpyDeviceToHost, b->stream));
     return GF_OK;
@@ -597,9 +665,9 @@ static void drop_graph(gf_batch *b)
 
 static int ensure_small_buffers(gf_batch *b)
 {
-    if (!b->dint) BCK(cudaMalloc(&b->dint, sizeof(int) * (4 * (size_t)b->n + 4)));
+    if (!b->dint) BCK(cudaMalloc(&b->dint, sizeof(int) * dint_count(b)));
     if (!b->ddbl) BCK(cudaMalloc(&b->ddbl, sizeof(double) * 2 * (size_t)b->n));
-    if (!b->hint) BCK(cudaMallocHost(&b->hint, sizeof(int) * (4 * (size_t)b->n + 4)));
+    if (!b->hint) BCK(cudaMallocHost(&b->hint, sizeof(int) * dint_count(b)));
     if (!b->hdbl) BCK(cudaMallocHost(&b->hdbl, sizeof(double) * 2 * (size_t)b->n));
     for (int k = 0; k < 3; ++k)
         if (!b->ev[k]) BCK(cudaEventCreate(&b->ev[k]));
@@ -652,6 +720,8 @@ int gf_batch_destroy(gf_batch *b)
     cudaFree(b->a32);
     cudaFree(b->a64);
     cudaFree(b->ag);
+    cudaFree(b->adf);
+    cudaFree(b->ae);
     cudaFree(b->dcfg);
     cudaFree(b->dtile);
     cudaFree(b->partials);
@@ -708,6 +778,10 @@ int gf_batch_set_option(gf_batch *b, const char *key, double v)
         b->extra_blocks = iv;
     } else if (k == "use_graphs") {
         b->use_graphs = v != 0.0;
+    } else if (k == "fp64_arith") {
+        if (iv != 0 && iv != 1) return bfail(b, GF_EINVAL, "fp64_arith: 0 (native) or 1 (double-float)");
+        b->fp64_arith = iv;
+        b->tiles_spt = 0;  // the arenas of the double-float phase are sized with the tiles
     } else {
         return bfail(b, GF_EINVAL, "unknown option " + k);
     }
@@ -796,7 +870,8 @@ int gf_batch_overrelax(gf_batch *b, double *const *U, double omega, double theta
     for (int i = 0; i < b->n; ++i) {
         int s_last = b->hint[b->n + i];
         int s32 = b->precision == GF_MIXED ? b->hint[3 * b->n + i] : (fp32_first ? s_last : 0);
-        int it = b->precision == GF_MIXED ? s32 + s_last : s_last;
+        int sdf = fp64_phase && b->fp64_arith ? b->hint[4 * b->n + 4 + i] : 0;
+        int it = b->precision == GF_MIXED ? s32 + sdf + s_last : sdf + s_last;
         double th = b->hdbl[b->n + i];
         if (iters) iters[i] = it;
         if (F) F[i] = b->hdbl[i];
@@ -859,6 +934,20 @@ int gf_batch_autotune(gf_batch *b, double *const *U, int *threads_per_site, int 
     b->use_graphs = saved_graphs;
     b->tiles_spt = 0;
     drop_graph(b);
+    return rc;
+}
+
+// One call for the common case: a batch with the default options, used once.
+int gf_overrelax_batched(int n, const int (*dims)[4], double **U, double omega, double theta_target, int max_iter,
+                         int *iters, double *F, double *theta)
+{
+    if (n < 1 || !dims || !U) return GF_EINVAL;
+    gf_batch *b = nullptr;
+    int rc = gf_batch_create(n, &dims[0][0], GF_LANDAU, &b);
+    if (rc != GF_OK) return rc;
+    b->use_graphs = 0;  // used once: capturing a graph would not pay
+    rc = gf_batch_overrelax(b, U, omega, theta_target, max_iter, iters, F, theta);
+    gf_batch_destroy(b);
     return rc;
 }
 

@@ -534,13 +534,25 @@ __device__ __forceinline__ double u01(uint32_t w) { return ((double)w + 0.5) * (
 // sqrt(1 - s0^2) exp(alpha s0), alpha = |k|/T (Creutz 1980 below alpha = 2,
 // Kennedy-Pendleton 1985 above), direction of the imaginary part uniform on
 // the sphere, then r = s k/|k| (quaternion product).  FP64 throughout so that
-// accept/reject decisions follow the FP64 definition.  Returns 1 on success,
-// 0 when cap attempts were rejected, 2 when k = 0 (nothing to do).
-__device__ __forceinline__ int heatbath_quat(const double k[4], double T, uint32_t site, uint32_t sweep, int sg,
-                                             int cap, uint2 key, double r[4], uint32_t tag = GF_SA_TAG)
+// accept/reject decisions follow the FP64 definition.  st = 1 on success,
+// 0 when cap attempts were rejected, 2 when k = 0 (nothing to do; r unset).
+// Not inlined: a site update draws for three subgroups, and three inlined
+// copies of this FP64 code (log, exp, cos, sincos, sqrt) overflow the
+// instruction cache of the larger site-update kernels.
+struct HeatbathDraw {
+    double r0, r1, r2, r3;
+    int st;
+};
+
+static __device__ __noinline__ HeatbathDraw heatbath_draw(double k0, double k1, double k2, double k3, double T,
+                                                   uint32_t site, uint32_t sweep, int sg, int cap, uint2 key,
+                                                   uint32_t tag)
 {
-    double kn = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
-    if (kn == 0.0) return 2;
+    HeatbathDraw d;
+    d.r0 = d.r1 = d.r2 = d.r3 = 0.0;
+    d.st = 2;
+    double kn = sqrt(k0 * k0 + k1 * k1 + k2 * k2 + k3 * k3);
+    if (kn == 0.0) return d;
     double alpha = kn / T;
     double s0 = 0.0;
     bool ok = false;
@@ -566,7 +578,10 @@ __device__ __forceinline__ int heatbath_quat(const double k[4], double T, uint32
             }
         }
     }
-    if (!ok) return 0;
+    if (!ok) {
+        d.st = 0;
+        return d;
+    }
     uint4 w = philox4x32_10(make_uint4(site, sweep, (uint32_t)sg * 256u + GF_SA_DIRECTION, tag), key);
     double ct = 2.0 * u01(w.x) - 1.0;
     double phi = GF_TWO_PI * u01(w.y);
@@ -576,13 +591,28 @@ __device__ __forceinline__ int heatbath_quat(const double k[4], double T, uint32
     sincos(phi, &sp, &cp);
     double s[4] = { s0, rho * st * cp, rho * st * sp, rho * ct };
     const double ikn = 1.0 / kn;  // one FP64 division instead of four
-    double kh[4] = { k[0] * ikn, k[1] * ikn, k[2] * ikn, k[3] * ikn };
+    double kh[4] = { k0 * ikn, k1 * ikn, k2 * ikn, k3 * ikn };
     // r = s kh (product of the SU(2) matrices)
-    r[0] = s[0] * kh[0] - (s[1] * kh[1] + s[2] * kh[2] + s[3] * kh[3]);
-    r[1] = s[0] * kh[1] + kh[0] * s[1] - (s[2] * kh[3] - s[3] * kh[2]);
-    r[2] = s[0] * kh[2] + kh[0] * s[2] - (s[3] * kh[1] - s[1] * kh[3]);
-    r[3] = s[0] * kh[3] + kh[0] * s[3] - (s[1] * kh[2] - s[2] * kh[1]);
-    return 1;
+    d.r0 = s[0] * kh[0] - (s[1] * kh[1] + s[2] * kh[2] + s[3] * kh[3]);
+    d.r1 = s[0] * kh[1] + kh[0] * s[1] - (s[2] * kh[3] - s[3] * kh[2]);
+    d.r2 = s[0] * kh[2] + kh[0] * s[2] - (s[3] * kh[1] - s[1] * kh[3]);
+    d.r3 = s[0] * kh[3] + kh[0] * s[3] - (s[1] * kh[2] - s[2] * kh[1]);
+    d.st = 1;
+    return d;
+}
+
+// the draw above; r is written only on success (return value 1)
+__device__ __forceinline__ int heatbath_quat(const double k[4], double T, uint32_t site, uint32_t sweep, int sg,
+                                             int cap, uint2 key, double r[4], uint32_t tag = GF_SA_TAG)
+{
+    const HeatbathDraw d = heatbath_draw(k[0], k[1], k[2], k[3], T, site, sweep, sg, cap, key, tag);
+    if (d.st == 1) {
+        r[0] = d.r0;
+        r[1] = d.r1;
+        r[2] = d.r2;
+        r[3] = d.r3;
+    }
+    return d.st;
 }
 
 // Stochastic relaxation: the maximiser r* = k/|k|, replaced with probability

@@ -289,6 +289,15 @@ cudaError_t launch_narrow(int src_fmt, FieldRef src, int dst_fmt, FieldRef dst, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_to_df(int src_fmt, FieldRef src, FieldRef dst, const Geom &g, cudaStream_t s)
+{
+    int n = nblocks(8L * g.Vh, 256);
+    if (src_fmt == F64_18) k_transcode<F64_18, DF64_18><<<n, 256, 0, s>>>(src, dst, g);
+    else if (src_fmt == F64_12) k_transcode<F64_12, DF64_18><<<n, 256, 0, s>>>(src, dst, g);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gauge_identity(FieldRef gt, const Geom &g, cudaStream_t s)
 {
     k_gauge_identity<<<nblocks(2L * g.Vh, 256), 256, 0, s>>>(gt, g);

@@ -20,6 +20,7 @@ constexpr int GF_ACC = 0, GF_ACC_R168 = -1, GF_ACC_R128 = -2;
 struct SweepArgs {
     FieldRef f;       // resident field
     FieldRef gt;      // accumulated gauge transformation (F32_12 site field) or {0}
+    FieldRef ge;      // double-float sweeps: E = g - 1 of the applied transformation (DF64_18 site field) or {0}
     Geom g;
     int parity;
     double omega;     // overrelaxation exponent
@@ -144,5 +145,10 @@ cudaError_t launch_gauge_algebra(FieldRef gt, const Geom &g, double inv_scale, f
 cudaError_t launch_expmap_to_gauge(const float *c, double scale, FieldRef gt, const Geom &g, cudaStream_t s);
 cudaError_t launch_gauge_transform_resident(int fmt, FieldRef f, FieldRef gt, const Geom &g, cudaStream_t s);
 cudaError_t launch_decode_gauge(FieldRef gt, const Geom &g, double *out, cudaStream_t s);
+// FP64 field (F64_18 / F64_12) -> double-float working copy (DF64_18)
+cudaError_t launch_to_df(int src_fmt, FieldRef src, FieldRef dst, const Geom &g, cudaStream_t s);
+// FP64 field := g(x) U_mu(x) g(x+mu)^dagger with g = 1 + E (E a DF64_18 site
+// field), reunitarised in FP64
+cudaError_t launch_apply_gauge_e(int fmt, FieldRef f, FieldRef ge, const Geom &g, cudaStream_t s);
 
 }  // namespace gf

@@ -158,6 +158,32 @@ __global__ void k_gauge_transform_resident(FieldRef f, FieldRef gt, Geom g)
     store_d<FMT>(f, pm * Store<FMT>::NCHUNK, h, mul3(mul3(gx, u), dagger(gy)));
 }
 
+// U_mu(x) := g(x) U_mu(x) g(x+mu)^dagger in FP64 with g = 1 + E read from the
+// double-float site field ge (E = g - 1 as tracked by the double-float sweeps),
+// reunitarised in FP64: the FP64 field stays a gauge transform of its input to
+// FP64 rounding
+template <int FMT>
+__global__ void k_apply_gauge_e(FieldRef f, FieldRef ge, Geom g)
+{
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 8L * g.Vh) return;
+    int h = (int)(t % g.Vh), pm = (int)(t / g.Vh);
+    int p = pm >> 2, mu = pm & 3;
+    int c[4];
+    site_coords(g, p, h, c);
+    mat3<double> gx = load_d<DF64_18>(ge, p * 9, h);
+    mat3<double> gy = load_d<DF64_18>(ge, (p ^ 1) * 9, fwd_half(g, c, mu));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        gx.e[i][i].re += 1.0;
+        gy.e[i][i].re += 1.0;
+    }
+    reunitarize3(gx);
+    reunitarize3(gy);
+    mat3<double> u = load_d<FMT>(f, pm * Store<FMT>::NCHUNK, h);
+    store_d<FMT>(f, pm * Store<FMT>::NCHUNK, h, mul3(mul3(gx, u), dagger(gy)));
+}
+
 // tracked g as a canonical site field double g[V][3][3][2] (reunitarised)
 __global__ void k_decode_gauge(FieldRef gt, Geom g, double *__restrict__ out)
 {
@@ -200,6 +226,15 @@ cudaError_t launch_gauge_transform_resident(int fmt, FieldRef f, FieldRef gt, co
     if (fmt == F64_18) k_gauge_transform_resident<F64_18><<<n, 128, 0, s>>>(f, gt, g);
     else if (fmt == F64_12) k_gauge_transform_resident<F64_12><<<n, 128, 0, s>>>(f, gt, g);
     else if (fmt == DF64_18) k_gauge_transform_resident<DF64_18><<<n, 128, 0, s>>>(f, gt, g);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_gauge_e(int fmt, FieldRef f, FieldRef ge, const Geom &g, cudaStream_t s)
+{
+    int n = nb(8L * g.Vh, 128);
+    if (fmt == F64_18) k_apply_gauge_e<F64_18><<<n, 128, 0, s>>>(f, ge, g);
+    else if (fmt == F64_12) k_apply_gauge_e<F64_12><<<n, 128, 0, s>>>(f, ge, g);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

@@ -69,6 +69,7 @@ SIGNATURES = {
     "gf_reunitarize": (C.c_int, [_vp]),
     "gf_autotune": (C.c_int, [_vp, _ip, _ip]),
     "gf_measure_noalloc": (C.c_int, [_ip, C.c_int, _vp, _vp, _vp]),
+    "gf_fma_peak": (C.c_int, [C.c_int, C.c_int, _dp, _dp]),
     "gf_batch_create": (C.c_int, [C.c_int, _ip, C.c_int, C.POINTER(_vp)]),
     "gf_batch_destroy": (C.c_int, [_vp]),
     "gf_batch_last_error": (C.c_char_p, [_vp]),
@@ -78,6 +79,8 @@ SIGNATURES = {
     "gf_batch_overrelax": (C.c_int, [_vp, C.POINTER(_vp), C.c_double, C.c_double, C.c_int, _ip, _dp,
                                      _dp]),
     "gf_batch_autotune": (C.c_int, [_vp, C.POINTER(_vp), _ip, _ip]),
+    "gf_overrelax_batched": (C.c_int, [C.c_int, _ip, C.POINTER(_vp), C.c_double, C.c_double, C.c_int, _ip, _dp,
+                                       _dp]),
     "gf_net_param_count": (C.c_size_t, []),
     "gf_net_create": (C.c_int, [_ip, C.POINTER(_vp)]),
     "gf_net_destroy": (C.c_int, [_vp]),
@@ -356,6 +359,16 @@ def gf_measure_noalloc(dims, gauge: int, U, out, stream=None) -> int:
     return lib.gf_measure_noalloc(arr, int(gauge), _ptr(U), _ptr(out), s or None)
 
 
+def gf_fma_peak(fp64: bool, iters: int):
+    """Measured FMA rate of the current device: (TFLOP/s, ms per launch)."""
+    lib = load()
+    t, ms = C.c_double(), C.c_double()
+    rc = lib.gf_fma_peak(1 if fp64 else 0, int(iters), C.byref(t), C.byref(ms))
+    if rc != GF_OK:
+        raise GFError(rc, "gf_fma_peak")
+    return t.value, ms.value
+
+
 class Batch:
     """Owns a gf_batch handle (n lattices gauge-fixed in one persistent launch)."""
 
@@ -426,6 +439,26 @@ def gf_batch_overrelax(b: Batch, fields, omega: float, theta_target: float, max_
                                   it, F, th)
     if raise_on_error:
         b.check(rc, "gf_batch_overrelax", ok=(GF_OK, GF_ENOTCONVERGED))
+    return rc, list(it), list(F), list(th)
+
+
+def gf_overrelax_batched(dims_list, fields, omega: float, theta_target: float, max_iter: int):
+    """One-call batched solve (Landau gauge, default batch options).
+    Returns (rc, iters, F, theta) with per-lattice lists; fields fixed in place."""
+    lib = load()
+    n = len(dims_list)
+    if len(fields) != n:
+        raise ValueError("one field per lattice")
+    flat = [int(d) for dims in dims_list for d in dims]
+    if len(flat) != 4 * n:
+        raise ValueError("four extents per lattice")
+    it = (C.c_int * n)()
+    F = (C.c_double * n)()
+    th = (C.c_double * n)()
+    rc = lib.gf_overrelax_batched(n, (C.c_int * len(flat))(*flat), _ptr_array(fields), float(omega),
+                                  float(theta_target), int(max_iter), it, F, th)
+    if rc not in (GF_OK, GF_ENOTCONVERGED):
+        raise GFError(rc, "gf_overrelax_batched")
     return rc, list(it), list(F), list(th)
 
 

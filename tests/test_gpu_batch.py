@@ -121,3 +121,57 @@ def test_batch_rejects_host_fields():
     b = gf.gf_batch_create(DIMS[:1], gf.GF_LANDAU)
     rc, *_ = gf.gf_batch_overrelax(b, host, 1.7, 1e-12, 10, raise_on_error=False)
     assert rc == gf.GF_EINVAL
+
+
+def test_one_call_batched_entry_point():
+    """gf_overrelax_batched (the one-call form): the same per-lattice results,
+    bit for bit, as a batch object with the default options; every returned
+    field checked by the oracle: theta below the target, plaquette kept, and
+    F equal to the oracle's own FP64 solve from the same input (the same
+    maximum; Alg. 1 with the checks of Sec. 4.1)."""
+    host = fields(DIMS, seed0=300)
+    one = [torch.from_numpy(u).cuda() for u in host]
+    rc, iters, F, th = gf.gf_overrelax_batched(DIMS, one, 1.7, 1e-13, 20000)
+    assert rc == gf.GF_OK
+    obj = [torch.from_numpy(u).cuda() for u in host]
+    b = gf.gf_batch_create(DIMS, gf.GF_LANDAU)
+    gf.gf_batch_set_option(b, "use_graphs", 0)
+    rc2, iters2, F2, th2 = gf.gf_batch_overrelax(b, obj, 1.7, 1e-13, 20000)
+    assert rc2 == gf.GF_OK and iters2 == iters and F2 == F and th2 == th
+    for k, u in enumerate(host):
+        W = one[k].cpu().numpy()
+        assert np.array_equal(W, obj[k].cpu().numpy())
+        assert oracle.theta(W, 0) < 1e-13
+        assert oracle.plaquette(W) == pytest.approx(oracle.plaquette(u), abs=1e-13)
+        conv, oit, oF, oth = oracle.overrelax(u.copy(), 0, 1.7, 1e-13, 20000, 25)
+        assert conv and F[k] == pytest.approx(oF, abs=1e-12)
+    # argument errors come back as codes
+    with pytest.raises(gf.GFError):
+        gf.gf_overrelax_batched([(4, 4, 4, 5)], one[:1], 1.7, 1e-13, 10)
+
+
+@pytest.mark.parametrize("precision", [gf.GF_MIXED, gf.GF_FP64])
+def test_batch_double_float_phase_is_exact(precision):
+    """Batch option fp64_arith 1: the FP64 phase as double-float sweeps with
+    E = g - 1 tracked per lattice and applied in FP64.  Every lattice reaches
+    theta < 1e-14 (the oracle on the returned field), keeps its plaquette
+    (an exact FP64 gauge transform) and ends at the native batch's F."""
+    host = fields(DIMS, seed0=400)
+    res = {}
+    for arith in (0, 1):
+        dev = [torch.from_numpy(u).cuda() for u in host]
+        b = gf.gf_batch_create(DIMS, gf.GF_LANDAU)
+        gf.gf_batch_set_option(b, "precision", precision)
+        gf.gf_batch_set_option(b, "check_every", 10)
+        gf.gf_batch_set_option(b, "fp64_arith", arith)
+        rc, iters, F, th = gf.gf_batch_overrelax(b, dev, 1.7, 1e-14, 20000)
+        assert rc == gf.GF_OK
+        res[arith] = (iters, F, [d.cpu().numpy() for d in dev])
+        if arith:
+            assert gf.gf_batch_get_stat(b, "grid_df64") > 0
+    for k, u in enumerate(host):
+        W = res[1][2][k]
+        assert oracle.theta(W, 0) < 1e-14
+        assert oracle.plaquette(W) == pytest.approx(oracle.plaquette(u), abs=1e-13)
+        assert res[1][1][k] == pytest.approx(res[0][1][k], abs=1e-13)
+        assert abs(res[1][0][k] - res[0][0][k]) <= 20 + res[0][0][k] // 20

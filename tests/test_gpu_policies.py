@@ -124,3 +124,78 @@ def test_fp32_restarts_reach_the_fp64_result(dims, restarts):
     Uo = U.copy()
     conv_o, it_o, F_o, th_o = oracle.overrelax(Uo, 0, 1.7, 1e-14, 40000, 10)
     assert conv_o and abs(F - F_o) <= 1e-13
+
+
+@pytest.mark.parametrize("gauge", [gf.GF_LANDAU, gf.GF_COULOMB])
+@pytest.mark.parametrize("policy", ["fp64", "mixed", "mixed_restarts"])
+def test_double_float_finish_is_an_exact_fp64_gauge_transform(gauge, policy):
+    """fp64_arith 1: the double-float sweeps work on a copy and track E = g - 1;
+    g is applied to the FP64 field in FP64, so the returned field is a gauge
+    transform of the input to FP64 rounding: the plaquette to 1e-14, the same
+    F as the native FP64 solve to 1e-14 (|dF| was 1.3e-13 while the links
+    themselves were double-float), theta < 1e-14 by the oracle."""
+    dims = (8, 8, 8, 8) if gauge == gf.GF_LANDAU else (6, 4, 6, 10)
+    U = cpu_field(dims, 3, 4)
+    P0 = oracle.plaquette(U)
+    opts = {"precision": gf.GF_FP64 if policy == "fp64" else gf.GF_MIXED}
+    if policy == "mixed_restarts":
+        opts.update(fp32_restarts=2, theta_switch=1e-30)
+    res = {}
+    for arith in (0, 1):
+        c = gf.gf_create(dims, gauge)
+        gf.gf_set_option(c, "check_every", 10)
+        for k, v in opts.items():
+            gf.gf_set_option(c, k, v)
+        gf.gf_set_option(c, "fp64_arith", arith)
+        d = torch.from_numpy(U).cuda()
+        conv, it, F, th = gf.gf_overrelax(c, d, 1.7, 1e-14, 40000)
+        assert conv and th < 1e-14, (arith, th)
+        W = d.cpu().numpy()
+        res[arith] = (F, it, W)
+        if arith == 1:
+            assert gf.gf_get_stat(c, "sweeps_df64") > 0
+            assert oracle.plaquette(W) == pytest.approx(P0, abs=1e-14)
+            assert oracle.theta(W, gauge) < 1e-14
+            assert oracle.functional(W, gauge) == pytest.approx(F, abs=1e-14)  # summation order
+            assert unitarity(W)[0] < 1e-13
+    assert abs(res[1][0] - res[0][0]) <= 1e-14
+    # the same maximum, reached in about the same number of sweeps
+    assert abs(res[1][1] - res[0][1]) <= 20 + res[0][1] // 20
+
+
+def test_fma_peak_is_plausible():
+    """The measured FMA rates that the ALU rooflines divide by: positive, and
+    within a factor of a few of the nominal figures (FP64: 152 SMs x 4 flop
+    per clock x about 2 GHz = 1.26 TFLOP/s; FP32: 152 x 256 x 2 GHz = 80)."""
+    t64, ms64 = gf.gf_fma_peak(True, 2000)
+    t32, ms32 = gf.gf_fma_peak(False, 50000)
+    assert 0.3 < t64 < 3.0 and ms64 > 0
+    assert 20.0 < t32 < 200.0 and ms32 > 0
+    assert t32 > 10 * t64
+    with pytest.raises(gf.GFError):
+        gf.gf_fma_peak(True, 0)
+
+
+@pytest.mark.parametrize("gauge", [gf.GF_LANDAU, gf.GF_COULOMB])
+def test_double_float_annealing_is_an_exact_fp64_gauge_transform(gauge):
+    """gf_anneal with fp64_arith 1: heatbath sweeps on a double-float copy with
+    E = g - 1 tracked, g applied to the FP64 field in FP64.  A 12-sweep
+    schedule equals the oracle's (same Philox draws, Sec. 1 annealing) to
+    1e-10; after 300 sweeps the field is unitary to 1e-13 and its plaquette
+    is the input's to 1e-14."""
+    dims = (8, 8, 8, 16)
+    U = cpu_field(dims, 27, 28, plaq=0.58)
+    P0 = oracle.plaquette(U)
+    c = gf.gf_create(dims, gauge)
+    gf.gf_set_option(c, "fp64_arith", 1)
+    d = torch.from_numpy(U).cuda()
+    gf.gf_anneal(c, d, 1.45, 0.01, 12, 77)
+    W = U.copy()
+    assert oracle.anneal(W, gauge, 1.45, 0.01, 12, 77) == 0
+    got = d.cpu().numpy()
+    assert np.abs(got - W).max() / np.abs(W).max() < 1e-10
+    d = torch.from_numpy(U).cuda()
+    gf.gf_anneal(c, d, 1.45, 0.01, 300, 77)
+    got = d.cpu().numpy()
+    assert unitarity(got)[0] < 1e-13
+    assert oracle.plaquette(got) == pytest.approx(P0, abs=1e-14)
