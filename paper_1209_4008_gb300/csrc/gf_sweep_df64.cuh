@@ -112,12 +112,14 @@ __device__ __forceinline__ void subgroup_element_df(const SweepArgs &a, cdf xaa,
 }
 
 // U_mu(x) <- G U_mu(x) (one column of U at a time) and U_mu(x-mu) <- U_mu(x-mu)
-// G^dagger (one row at a time) for mu = 0..3; CROSS: rows 0, 1 multiplied out
-// and row 2 = conj(row0 x row1), else all three rows multiplied out
-template <bool CROSS>
-__device__ __forceinline__ void apply_links_df(const SweepArgs &a, int p, int h, const int hb[4], const mat3df &G)
+// G^dagger (one row at a time) for mu = 0..3.  Rows 0 and 1 are multiplied
+// out; row 2 is rebuilt as conj(row0 x row1) when cross is set, else
+// multiplied out as well.  cross is uniform in a warp, and both ways share one
+// loop body: two full copies of this loop overflow the instruction cache of the
+// double-float kernels (most of their stalls were instruction fetches).
+__device__ __forceinline__ void apply_links_df(const SweepArgs &a, int p, int h, const int hb[4], const mat3df &G,
+                                               bool cross)
 {
-    constexpr int NR = CROSS ? 2 : 3;
 #pragma unroll 1
     for (int mu = 0; mu < 4; ++mu) {
         const int pf = (p * 4 + mu) * 9, pb = ((p ^ 1) * 4 + mu) * 9;
@@ -128,26 +130,33 @@ __device__ __forceinline__ void apply_links_df(const SweepArgs &a, int p, int h,
 #pragma unroll
             for (int l = 0; l < 3; ++l) col[l] = reload_chunk_df(a.f, pf + 3 * l + j, h);
 #pragma unroll
-            for (int i = 0; i < NR; ++i) {
-                const cdf s = cdf_dot3<false>(G.e[i], col);
-                if (CROSS) v[i][j] = s;
-                store_chunk_df(a.f, pf + 3 * i + j, h, s);
+            for (int i = 0; i < 2; ++i) {
+                v[i][j] = cdf_dot3<false>(G.e[i], col);
+                store_chunk_df(a.f, pf + 3 * i + j, h, v[i][j]);
             }
+            if (!cross) store_chunk_df(a.f, pf + 6 + j, h, cdf_dot3<false>(G.e[2], col));
         }
-        if (CROSS) store_row2_df(a.f, pf, h, v);
+        if (cross) store_row2_df(a.f, pf, h, v);
 #pragma unroll
-        for (int i = 0; i < NR; ++i) {
+        for (int i = 0; i < 2; ++i) {
             cdf row[3];
 #pragma unroll
             for (int l = 0; l < 3; ++l) row[l] = reload_chunk_df(a.f, pb + 3 * i + l, hb[mu]);
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
-                const cdf s = cdf_dot3<true>(row, G.e[j]);
-                if (CROSS) v[i][j] = s;
-                store_chunk_df(a.f, pb + 3 * i + j, hb[mu], s);
+                v[i][j] = cdf_dot3<true>(row, G.e[j]);
+                store_chunk_df(a.f, pb + 3 * i + j, hb[mu], v[i][j]);
             }
         }
-        if (CROSS) store_row2_df(a.f, pb, hb[mu], v);
+        if (cross) {
+            store_row2_df(a.f, pb, hb[mu], v);
+        } else {
+            cdf row[3];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) row[l] = reload_chunk_df(a.f, pb + 6 + l, hb[mu]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) store_chunk_df(a.f, pb + 6 + j, hb[mu], cdf_dot3<true>(row, G.e[j]));
+        }
     }
 }
 
@@ -275,8 +284,7 @@ __device__ __forceinline__ void sweep_site_df(const SweepArgs &a, int h, const f
     // accumulate form, kCrossRow2), else multiplied out as well
     const float w = G.e[2][0].re.hi * G.e[2][0].re.hi + G.e[2][0].im.hi * G.e[2][0].im.hi +
                     G.e[2][1].re.hi * G.e[2][1].re.hi + G.e[2][1].im.hi * G.e[2][1].im.hi;
-    if (__all_sync(__activemask(), w < (float)kCrossRow2)) apply_links_df<true>(a, p, h, hb, G);  // per warp
-    else apply_links_df<false>(a, p, h, hb, G);
+    apply_links_df(a, p, h, hb, G, __all_sync(__activemask(), w < (float)kCrossRow2));  // per warp
     if (TRACKE) track_e_df(a, p, h, G, epre, t, nthreads);
     if (TRACKG) {
         mat3<float> gx, gy, Gf;
