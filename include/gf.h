@@ -157,6 +157,16 @@ int gf_set_stream(gf_ctx *ctx, void *stream);
  *                    report their time (default 0; creating the events may
  *                    fail with GF_ECUDA)
  *   "sa_cap"         heatbath rejection cap per draw (default 64, <= 255)
+ *   "sa_draw"        heatbath draw of gf_anneal / gf_sa_half_sweep: 0 = FP64
+ *                    throughout (default), 1 = the FP32 reading: alpha = |k|/T
+ *                    rounded once to FP32, uniforms ((w >> 9) + 1/2) / 2^23,
+ *                    the Creutz / Kennedy-Pendleton steps and the direction in
+ *                    FP32 operations as written, the drawn element widened to
+ *                    FP64 and normalised before the product with k/|k| (the
+ *                    rotation stays unitary to FP64 rounding).  The decisions
+ *                    follow the FP32 arithmetic; the library's FP32 exp, log,
+ *                    cos and sin may differ from another implementation by an
+ *                    ulp
  *   "sa_sweep_offset" Philox sweep counter of the first annealing sweep
  *   "stochastic_p"   > 0: gf_overrelax / gf_or_sweeps / gf_converge use
  *                    stochastic relaxation with this probability instead of

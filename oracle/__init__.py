@@ -66,6 +66,8 @@ def _declare(lib: C.CDLL) -> C.CDLL:
     d.oracle_block_quaternion.argtypes = [_dp, _dp]
     d.oracle_block_quaternion.restype = None
     d.oracle_overrelax_quaternion.argtypes = [_dp, C.c_double, _dp]
+    d.oracle_set_sa_draw.argtypes = [C.c_int]
+    d.oracle_set_sa_draw.restype = C.c_int
     d.oracle_set_or_variant.argtypes = [C.c_int]
     d.oracle_mag_half_sweep.argtypes = [_dp, _ip, C.c_int, C.c_double]
     d.oracle_mag_functional.argtypes = [_dp, _ip]
@@ -173,6 +175,12 @@ def set_or_variant(v: int) -> None:
         counting = _libs.get("liboracle_count.so")
     if counting is not None:
         _check(counting.oracle_set_or_variant(int(v)), "or variant")
+
+
+def set_sa_draw(fp32: int) -> None:
+    """Precision of the annealing heatbath draw for every later call: 0 the
+    FP64 definition (default), 1 the FP32 reading (see gf_oracle.c)."""
+    _check(lib().oracle_set_sa_draw(int(fp32)), "sa draw")
 
 
 def or_half_sweep(U, parity: int, omega: float, gauge: int = 0, counting: bool = False) -> None:

@@ -843,6 +843,61 @@ static int heatbath_s0(double alpha, uint32_t site, uint32_t sweep, int sg, int 
     return 0;
 }
 
+/*
+ * The FP32 reading of the same draw (oracle_set_sa_draw(1); annealing only,
+ * the Wilson-action generation keeps FP64).  A preconditioner does not need
+ * the draw's precision, and FP32 transcendental functions are far cheaper on
+ * the GPU than FP64 ones, so the reading is stated here as its own
+ * definition: alpha = |k|/T is computed in FP64 and rounded once to FP32;
+ * uniforms are ((w >> 9) + 1/2) / 2^23 (exact in FP32, open interval); every
+ * later operation -- expf, logf, cosf, sinf, sqrtf, products, sums, the
+ * divisions, the accept/reject comparisons -- is one FP32 operation in the
+ * order written; the four components of the drawn SU(2) element are then
+ * widened to FP64 and normalised in FP64 before the product with k/|k|, so
+ * that the rotation is unitary to FP64 rounding.
+ */
+static int g_sa_draw_fp32 = 0;
+
+int oracle_set_sa_draw(int fp32)
+{
+    if (fp32 != 0 && fp32 != 1) return -1;
+    g_sa_draw_fp32 = fp32;
+    return 0;
+}
+
+static float u01f(uint32_t w) { return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f); }
+
+#define ORACLE_TWO_PI_F 6.28318530717958647692f
+
+static int heatbath_s0_f32(float alpha, uint32_t site, uint32_t sweep, int sg, int cap,
+                           const uint32_t key[2], uint32_t tag, float *s0_out)
+{
+    for (int a = 0; a < cap && a < (int)SA_DIRECTION_DRAW; ++a) {
+        uint32_t ctr[4] = { site, sweep, (uint32_t)sg * 256u + (uint32_t)a, tag };
+        uint32_t w[4];
+        oracle_philox4x32_10(ctr, key, w);
+        if (alpha < (float)SA_ALPHA_SWITCH) {
+            float u = u01f(w[0]);
+            float e = expf(-2.0f * alpha);
+            float s0 = 1.0f + logf(e + u * (1.0f - e)) / alpha;
+            float v = u01f(w[1]);
+            if (v <= sqrtf(1.0f - s0 * s0)) {
+                *s0_out = s0;
+                return 1;
+            }
+        } else {
+            float c = cosf(ORACLE_TWO_PI_F * u01f(w[1]));
+            float lam2 = -(logf(u01f(w[0])) + c * c * logf(u01f(w[2]))) / (2.0f * alpha);
+            float v = u01f(w[3]);
+            if (v * v <= 1.0f - lam2) {
+                *s0_out = 1.0f - 2.0f * lam2;
+                return 1;
+            }
+        }
+    }
+    return 0;
+}
+
 /* quaternion product q = a b, the product of the SU(2) matrices */
 static void quat_mul(const double a[4], const double b[4], double q[4])
 {
@@ -867,6 +922,24 @@ static int heatbath_quaternion_tag(const double k[4], double T, uint32_t site, u
 {
     double kn = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
     if (kn == 0.0) return 2; /* nothing to do */
+    if (g_sa_draw_fp32 && tag == SA_TAG) {
+        float s0f;
+        if (!heatbath_s0_f32((float)(kn / T), site, sweep, sg, cap, key, tag, &s0f)) return 0;
+        uint32_t ctr[4] = { site, sweep, (uint32_t)sg * 256u + SA_DIRECTION_DRAW, tag };
+        uint32_t w[4];
+        oracle_philox4x32_10(ctr, key, w);
+        float ct = 2.0f * u01f(w[0]) - 1.0f;
+        float phi = ORACLE_TWO_PI_F * u01f(w[1]);
+        float st = sqrtf(1.0f - ct * ct);
+        float rho = sqrtf(1.0f - s0f * s0f);
+        double s[4] = { (double)s0f, (double)(rho * st * cosf(phi)), (double)(rho * st * sinf(phi)),
+                        (double)(rho * ct) };
+        double sn = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + s[3] * s[3]);
+        for (int c = 0; c < 4; ++c) s[c] /= sn;
+        double kh[4] = { k[0] / kn, k[1] / kn, k[2] / kn, k[3] / kn };
+        quat_mul(s, kh, r);
+        return 1;
+    }
     double s0;
     if (!heatbath_s0(kn / T, site, sweep, sg, cap, key, tag, &s0)) return 0;
     uint32_t ctr[4] = { site, sweep, (uint32_t)sg * 256u + SA_DIRECTION_DRAW, tag };

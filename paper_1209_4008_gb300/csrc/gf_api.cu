@@ -80,6 +80,7 @@ struct gf_ctx {
     long kn[2] = { 0, 0 };         // half-sweep launches those milliseconds cover
     int autotune = 0;
     int sa_cap = 64;
+    int sa_draw = 0;           // heatbath draw: 0 the FP64 definition, 1 its FP32 reading
     uint32_t sa_sweep_offset = 0;
     int track = 0;             // resident sweeps also rotate the tracked g
     double sr_p = 0.0;         // > 0: gf_overrelax uses stochastic relaxation with this probability
@@ -316,6 +317,7 @@ static SweepArgs sweep_args(gf_ctx *ctx, char *field, int parity, double omega)
     a.orv = ctx->or_variant;
     a.T = 1.0;
     a.cap = ctx->sa_cap;
+    a.sa_fp32 = ctx->sa_draw;
     a.status = ctx->dstatus;
     return a;
 }
@@ -802,6 +804,9 @@ int gf_set_option(gf_ctx *ctx, const char *key, double v)
         if (!(v >= 0.0) || v > 18446744073709551615.0) return fail(ctx, GF_EINVAL, "sr_seed");
         ctx->sr_seed = (uint64_t)v;
         ctx->sr_sweep = 0;
+    } else if (k == "sa_draw") {
+        if (iv != 0 && iv != 1) return fail(ctx, GF_EINVAL, "sa_draw: 0 (FP64 draw) or 1 (FP32 reading)");
+        ctx->sa_draw = iv;
     } else if (k == "sa_cap") {
         if (!integral || iv < 1 || iv > 255) return fail(ctx, GF_EINVAL, "sa_cap: 1..255");
         ctx->sa_cap = iv;
@@ -839,6 +844,7 @@ int gf_get_option(const gf_ctx *ctx, const char *key, double *v)
     else if (k == "kernel_timing") *v = ctx->kernel_timing;
     else if (k == "autotune") *v = ctx->autotune;
     else if (k == "sa_cap") *v = ctx->sa_cap;
+    else if (k == "sa_draw") *v = ctx->sa_draw;
     else if (k == "track") *v = ctx->track;
     else if (k == "stochastic_p") *v = ctx->sr_p;
     else if (k == "sr_seed") *v = (double)ctx->sr_seed;

@@ -601,11 +601,87 @@ static __device__ __noinline__ HeatbathDraw heatbath_draw(double k0, double k1, 
     return d;
 }
 
-// the draw above; r is written only on success (return value 1)
-__device__ __forceinline__ int heatbath_quat(const double k[4], double T, uint32_t site, uint32_t sweep, int sg,
-                                             int cap, uint2 key, double r[4], uint32_t tag = GF_SA_TAG)
+// open-interval uniform (0,1) in FP32 from the top 23 bits of a word: ((w >> 9) + 1/2) / 2^23, exact
+__device__ __forceinline__ float u01f(uint32_t w) { return __fmul_rn(__fadd_rn((float)(w >> 9), 0.5f), 1.0f / 8388608.0f); }
+
+#define GF_TWO_PI_F 6.28318530717958647692f
+
+// The FP32 reading of the same draw (option "sa_draw" 1, annealing only):
+// alpha = |k|/T in FP64 rounded once to FP32, uniforms u01f, every later
+// operation one FP32 operation in the order written (the _rn intrinsics keep
+// the compiler from contracting them into fused multiply-adds, so only the
+// library's expf, logf, cosf and sinf may differ from another correctly
+// written implementation, by an ulp); the drawn element is widened to FP64 and
+// normalised in FP64 before the product with k/|k|, so that the rotation stays
+// unitary to FP64 rounding.  The FP32 pipe and the special-function units do
+// the transcendental work that the FP64 reading leaves to the small FP64 unit.
+static __device__ __noinline__ HeatbathDraw heatbath_draw_f32(double k0, double k1, double k2, double k3, double T,
+                                                              uint32_t site, uint32_t sweep, int sg, int cap, uint2 key,
+                                                              uint32_t tag)
 {
-    const HeatbathDraw d = heatbath_draw(k[0], k[1], k[2], k[3], T, site, sweep, sg, cap, key, tag);
+    HeatbathDraw d;
+    d.r0 = d.r1 = d.r2 = d.r3 = 0.0;
+    d.st = 2;
+    double kn = sqrt(k0 * k0 + k1 * k1 + k2 * k2 + k3 * k3);
+    if (kn == 0.0) return d;
+    const float alpha = __double2float_rn(kn / T);
+    float s0 = 0.0f;
+    bool ok = false;
+    for (int a = 0; a < cap && a < (int)GF_SA_DIRECTION; ++a) {
+        uint4 w = philox4x32_10(make_uint4(site, sweep, (uint32_t)sg * 256u + (uint32_t)a, tag), key);
+        if (alpha < (float)GF_SA_ALPHA_SWITCH) {
+            const float u = u01f(w.x);
+            const float e = expf(__fmul_rn(-2.0f, alpha));
+            const float s = __fadd_rn(1.0f, __fdiv_rn(logf(__fadd_rn(e, __fmul_rn(u, __fsub_rn(1.0f, e)))), alpha));
+            if (u01f(w.y) <= __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(s, s)))) {
+                s0 = s;
+                ok = true;
+                break;
+            }
+        } else {
+            const float c = cosf(__fmul_rn(GF_TWO_PI_F, u01f(w.y)));
+            const float lam2 = -__fdiv_rn(__fadd_rn(logf(u01f(w.x)), __fmul_rn(__fmul_rn(c, c), logf(u01f(w.z)))),
+                                          __fmul_rn(2.0f, alpha));
+            const float v = u01f(w.w);
+            if (__fmul_rn(v, v) <= __fsub_rn(1.0f, lam2)) {
+                s0 = __fsub_rn(1.0f, __fmul_rn(2.0f, lam2));
+                ok = true;
+                break;
+            }
+        }
+    }
+    if (!ok) {
+        d.st = 0;
+        return d;
+    }
+    uint4 w = philox4x32_10(make_uint4(site, sweep, (uint32_t)sg * 256u + GF_SA_DIRECTION, tag), key);
+    const float ct = __fsub_rn(__fmul_rn(2.0f, u01f(w.x)), 1.0f);
+    const float phi = __fmul_rn(GF_TWO_PI_F, u01f(w.y));
+    const float st = __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(ct, ct)));
+    const float rho = __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(s0, s0)));
+    const float rs = __fmul_rn(rho, st);
+    double s[4] = { (double)s0, (double)__fmul_rn(rs, cosf(phi)), (double)__fmul_rn(rs, sinf(phi)),
+                    (double)__fmul_rn(rho, ct) };
+    const double sn = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + s[3] * s[3]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[c] /= sn;
+    const double ikn = 1.0 / kn;
+    double kh[4] = { k0 * ikn, k1 * ikn, k2 * ikn, k3 * ikn };
+    d.r0 = s[0] * kh[0] - (s[1] * kh[1] + s[2] * kh[2] + s[3] * kh[3]);
+    d.r1 = s[0] * kh[1] + kh[0] * s[1] - (s[2] * kh[3] - s[3] * kh[2]);
+    d.r2 = s[0] * kh[2] + kh[0] * s[2] - (s[3] * kh[1] - s[1] * kh[3]);
+    d.r3 = s[0] * kh[3] + kh[0] * s[3] - (s[1] * kh[2] - s[2] * kh[1]);
+    d.st = 1;
+    return d;
+}
+
+// the draw above (fp32: its FP32 reading); r is written only on success (return value 1)
+__device__ __forceinline__ int heatbath_quat(const double k[4], double T, uint32_t site, uint32_t sweep, int sg,
+                                             int cap, uint2 key, double r[4], uint32_t tag = GF_SA_TAG,
+                                             bool fp32 = false)
+{
+    const HeatbathDraw d = fp32 ? heatbath_draw_f32(k[0], k[1], k[2], k[3], T, site, sweep, sg, cap, key, tag)
+                                : heatbath_draw(k[0], k[1], k[2], k[3], T, site, sweep, sg, cap, key, tag);
     if (d.st == 1) {
         r[0] = d.r0;
         r[1] = d.r1;

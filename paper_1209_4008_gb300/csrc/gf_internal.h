@@ -29,6 +29,7 @@ struct SweepArgs {
     uint2 key;        // Philox key (seed)
     uint32_t sweep;   // Philox sweep counter
     int cap;          // heatbath rejection cap
+    int sa_fp32;      // heatbath: 1 = the FP32 reading of the draw
     double prob;      // stochastic relaxation: probability of the microcanonical step
     int *status;      // [0]: heatbath draws that hit the cap
 };

@@ -168,7 +168,7 @@ __device__ __forceinline__ void subgroup_element(const SweepArgs &a, quat<T> q, 
     } else {
         double kd[4] = { (double)q.k[0], (double)q.k[1], (double)q.k[2], (double)q.k[3] };
         double rd[4];
-        int st = heatbath_quat(kd, a.T, site, a.sweep, sg, a.cap, a.key, rd);
+        int st = heatbath_quat(kd, a.T, site, a.sweep, sg, a.cap, a.key, rd, GF_SA_TAG, a.sa_fp32 != 0);
         if (st == 0) atomicAdd(a.status, 1);
         ok = (st == 1);
 #pragma unroll
@@ -552,7 +552,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs &a, int h, int j, uns
         } else {
             double kd[4] = { (double)k[0], (double)k[1], (double)k[2], (double)k[3] };
             double rd[4];
-            int st = heatbath_quat(kd, a.T, site, a.sweep, sg, a.cap, a.key, rd);
+            int st = heatbath_quat(kd, a.T, site, a.sweep, sg, a.cap, a.key, rd, GF_SA_TAG, a.sa_fp32 != 0);
             if (st == 0 && j == 0) atomicAdd(a.status, 1);
             ok = (st == 1);
 #pragma unroll

@@ -97,7 +97,7 @@ __device__ __forceinline__ void subgroup_element_df(const SweepArgs &a, cdf xaa,
     } else if (MODE == MODE_SR) {
         ok = sr_quat(k, a.prob, site, a.sweep, sg, a.key, rd);
     } else {
-        int st = heatbath_quat(k, a.T, site, a.sweep, sg, a.cap, a.key, rd);
+        int st = heatbath_quat(k, a.T, site, a.sweep, sg, a.cap, a.key, rd, GF_SA_TAG, a.sa_fp32 != 0);
         if (st == 0) atomicAdd(a.status, 1);
         ok = (st == 1);
     }

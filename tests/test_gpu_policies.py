@@ -199,3 +199,62 @@ def test_double_float_annealing_is_an_exact_fp64_gauge_transform(gauge):
     got = d.cpu().numpy()
     assert unitarity(got)[0] < 1e-13
     assert oracle.plaquette(got) == pytest.approx(P0, abs=1e-14)
+
+
+@pytest.fixture
+def oracle_sa_draw():
+    yield oracle.set_sa_draw
+    oracle.set_sa_draw(0)
+
+
+SA_FORMS = {"acc": {"variant": 2}, "tps2": {"variant": 1, "threads_per_site": 2}, "df64": {"fp64_arith": 1}}
+
+
+@pytest.mark.parametrize("gauge", [gf.GF_LANDAU, gf.GF_COULOMB])
+@pytest.mark.parametrize("form", sorted(SA_FORMS))
+@pytest.mark.parametrize("T", [1.45, 0.3, 0.01])
+def test_fp32_heatbath_draw_half_sweep_parity(oracle_sa_draw, gauge, form, T):
+    """The FP32 reading of the heatbath draw (option sa_draw 1) against the
+    oracle's FP32 reading, same Philox draws.  Both decide accept/reject in FP32;
+    their FP32 exp/log/cos/sin (CUDA's, the C library's) may differ by an ulp,
+    which moves the drawn element by ~1e-7 relative: links agree to 1e-5 per
+    half-sweep, and no decision differs on these seeds (a differing decision
+    would change a whole site by O(1))."""
+    oracle_sa_draw(1)
+    dims = (6, 4, 6, 10)
+    U = cpu_field(dims, 35, 36)
+    c = gf.gf_create(dims, gauge)
+    for k, v in {**SA_FORMS[form], "sa_draw": 1}.items():
+        gf.gf_set_option(c, k, v)
+    d = torch.from_numpy(U).cuda()
+    gf.gf_upload(c, d, gf.GF_FP64)
+    for parity in (0, 1):
+        gf.gf_sa_half_sweep(c, parity, T, 99, 4)
+        assert oracle.sa_half_sweep(U, parity, T, gauge, 99, 4) == 0
+    gf.gf_download(c, d)
+    diff = np.abs(d.cpu().numpy() - U).reshape(-1, 18).max(axis=1)
+    assert diff.max() < 1e-5, (int((diff > 1e-5).sum()), diff.max())
+
+
+def test_fp32_draw_annealing_is_exact_and_matches_oracle(oracle_sa_draw):
+    """gf_anneal with the double-float sweeps (E tracked, g applied in FP64) and
+    the FP32 draw: a 6-sweep schedule 1.45 -> 0.01 equals the oracle's FP32
+    reading to 1e-4 (differences of ~1e-7 per draw grow along the chain), and
+    300 sweeps keep the plaquette to 1e-14 and unitarity to 1e-13."""
+    oracle_sa_draw(1)
+    dims = (8, 8, 8, 16)
+    U = cpu_field(dims, 27, 28, plaq=0.58)
+    P0 = oracle.plaquette(U)
+    c = gf.gf_create(dims, gf.GF_COULOMB)
+    gf.gf_set_option(c, "fp64_arith", 1)
+    gf.gf_set_option(c, "sa_draw", 1)
+    d = torch.from_numpy(U).cuda()
+    gf.gf_anneal(c, d, 1.45, 0.01, 6, 77)
+    W = U.copy()
+    assert oracle.anneal(W, gf.GF_COULOMB, 1.45, 0.01, 6, 77) == 0
+    assert np.abs(d.cpu().numpy() - W).max() < 1e-4
+    d = torch.from_numpy(U).cuda()
+    gf.gf_anneal(c, d, 1.45, 0.01, 300, 77)
+    got = d.cpu().numpy()
+    assert unitarity(got)[0] < 1e-13
+    assert oracle.plaquette(got) == pytest.approx(P0, abs=1e-14)

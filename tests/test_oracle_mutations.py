@@ -134,6 +134,17 @@ MUTATIONS = [
     ("convolution taps transposed", "conv_oracle.c",
      "int d[4] = { k % 3 - 1, (k / 3) % 3 - 1, (k / 9) % 3 - 1, (k / 27) % 3 - 1 };",
      "int d[4] = { (k / 3) % 3 - 1, k % 3 - 1, (k / 9) % 3 - 1, (k / 27) % 3 - 1 };"),
+    ("FP32 draw: Creutz support", "gf_oracle.c",
+     "float e = expf(-2.0f * alpha);", "float e = expf(-alpha);"),
+    ("FP32 draw: Kennedy-Pendleton uniforms swapped", "gf_oracle.c",
+     "float lam2 = -(logf(u01f(w[0])) + c * c * logf(u01f(w[2]))) / (2.0f * alpha);",
+     "float lam2 = -(logf(u01f(w[2])) + c * c * logf(u01f(w[0]))) / (2.0f * alpha);"),
+    ("FP32 draw: direction without the sphere factor", "gf_oracle.c",
+     "double s[4] = { (double)s0f, (double)(rho * st * cosf(phi)), (double)(rho * st * sinf(phi)),",
+     "double s[4] = { (double)s0f, (double)(rho * cosf(phi)), (double)(rho * st * sinf(phi)),"),
+    ("FP32 draw: uniform from the low bits", "gf_oracle.c",
+     "static float u01f(uint32_t w) { return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f); }",
+     "static float u01f(uint32_t w) { return ((float)(w & 0x7FFFFFu) + 0.5f) * (1.0f / 8388608.0f); }"),
     ("convolution backward data with the forward shift", "conv_oracle.c",
      "const double *dy = dY + shifted(&g, s, k, -1) * cout;", "const double *dy = dY + shifted(&g, s, k, +1) * cout;"),
 ]

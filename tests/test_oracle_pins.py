@@ -452,10 +452,23 @@ def s0_cdf(alpha):
     return x, c / c[-1]
 
 
+@pytest.fixture
+def sa_draw():
+    """Select the heatbath draw's reading (0 FP64, 1 FP32) for one test."""
+    def set_(v):
+        oracle.set_sa_draw(v)
+    yield set_
+    oracle.set_sa_draw(0)
+
+
 @pytest.mark.parametrize("alpha", [0.3, 1.9, 2.1, 8.0, 150.0])
-def test_heatbath_samples_weighted_haar(alpha):
+@pytest.mark.parametrize("draw", [0, 1])
+def test_heatbath_samples_weighted_haar(alpha, draw, sa_draw):
     """r . k/|k| must follow sqrt(1 - s^2) exp(alpha s) (weight exp(Re tr[gK]/T)
-    times the SU(2) Haar measure); the perpendicular part must be isotropic."""
+    times the SU(2) Haar measure); the perpendicular part must be isotropic.
+    Both readings of the draw (FP64, and FP32 with the element renormalised in
+    FP64) sample the same density."""
+    sa_draw(draw)
     rng = np.random.default_rng(int(alpha * 10))
     k = rng.standard_normal(4)
     kn = np.linalg.norm(k)
@@ -483,12 +496,49 @@ def test_heatbath_samples_weighted_haar(alpha):
     np.testing.assert_allclose(np.diag(perp.T @ perp / n), 1 / 3, atol=0.04)
 
 
-def test_heatbath_zero_temperature_is_relaxation():
+@pytest.mark.parametrize("draw", [0, 1])
+def test_heatbath_zero_temperature_is_relaxation(draw, sa_draw):
+    sa_draw(draw)
     rng = np.random.default_rng(3)
     for j in range(20):
         k = rng.standard_normal(4)
         st, r = oracle.heatbath_quaternion(k, 1e-9 * np.linalg.norm(k), j, 0, 0, 64, 9)
         np.testing.assert_allclose(r, k / np.linalg.norm(k), atol=1e-3)
+
+
+def test_heatbath_fp32_reading_follows_the_fp64_draw(sa_draw):
+    """The FP32 reading takes the same steps as the FP64 definition from the
+    same Philox words (23 of their 32 bits): draw by draw, the two elements
+    agree to FP32 rounding unless an accept/reject decision falls within that
+    rounding of its threshold, which is rare.  A dropped term, a wrong sign or
+    a swapped uniform in either reading moves most draws far apart."""
+    rng = np.random.default_rng(5)
+    far = 0
+    n = 3000
+    for j in range(n):
+        k = rng.standard_normal(4) * rng.choice([0.05, 0.5, 3.0])
+        T = np.linalg.norm(k) / rng.choice([0.2, 1.0, 1.99, 2.01, 5.0, 60.0])
+        sa_draw(0)
+        st0, r0 = oracle.heatbath_quaternion(k, T, j, 3, j % 3, 64, 77)
+        sa_draw(1)
+        st1, r1 = oracle.heatbath_quaternion(k, T, j, 3, j % 3, 64, 77)
+        assert st0 == 1 and st1 == 1
+        assert abs(np.linalg.norm(r1) - 1) < 1e-15
+        d = np.abs(r1 - r0).max()
+        if d > 2e-4:
+            far += 1
+    assert far <= n // 500, far
+
+
+def test_anneal_fp32_draw_is_gauge_transformation(sa_draw):
+    sa_draw(1)
+    dims = (4, 4, 4, 4)
+    for gauge in (0, 1):
+        U = field(dims, seed=93, gseed=94)
+        P = oracle.plaquette(U)
+        assert oracle.anneal(U, gauge, 1.45, 0.01, 30, 77) == 0
+        assert oracle.plaquette(U) == pytest.approx(P, abs=1e-13)
+        assert unitarity_error(U) < 1e-13
 
 
 def test_heatbath_rejection_cap_reported():
