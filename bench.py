@@ -749,6 +749,10 @@ def coulomb(args):
     gf.gf_set_option(ctx, "storage64", 18)
     gf.gf_set_option(ctx, "check_every", CHECK_EVERY)
     gf.gf_set_option(ctx, "autotune", 1)
+    # --fast: double-float sweeps (E tracked, applied in FP64: exact FP64 gauge transforms) and the
+    # FP32 reading of the heatbath draw
+    gf.gf_set_option(ctx, "fp64_arith", 1 if args.fast else 0)
+    gf.gf_set_option(ctx, "sa_draw", 1 if args.fast else 0)
     gf.gf_set_stream(ctx, torch.cuda.current_stream())
     V = int(np.prod(COULOMB_DIMS))
     rows = []
@@ -782,7 +786,8 @@ def coulomb(args):
     stat = lambda v: {"mean": float(np.mean(v)), "std": float(np.std(v)), "min": float(min(v)), "max": float(max(v))}
     print(json.dumps({
         "workload": f"coulomb 48^3x96 FP64, plaquette 0.58, {args.sa_sweeps} heatbath sweeps T 1.45->0.01, "
-                    f"then OR omega 1.7 to theta<1e-13; {args.seeds} seeds",
+                    f"then OR omega 1.7 to theta<1e-13; {args.seeds} seeds"
+                    + ("; double-float sweeps (exact FP64 result), FP32 heatbath draw" if args.fast else ""),
         "seeds": rows, "F_sa_or": stat(F_sa), "F_or": stat(F_or) if F_or else None,
         "sa_higher_F": int(sum(r["sa+or"]["F"] > r["or"]["F"] for r in rows if "or" in r)),
         "or_sweeps_saved_by_sa": [r["or"]["sweeps"] - r["sa+or"]["sweeps"] for r in rows if "or" in r],
@@ -1044,6 +1049,8 @@ def main():
     ap.add_argument("--sr-max-iter", type=int, default=40000)
     ap.add_argument("--therm", type=int, default=100, help="--thermal: compound sweeps of generation")
     ap.add_argument("--seeds", type=int, default=8)
+    ap.add_argument("--fast", action="store_true",
+                    help="--coulomb: double-float sweeps with the exact FP64 result and the FP32 heatbath draw")
     ap.add_argument("--sa-sweeps", type=int, default=3000)
     args = ap.parse_args()
     if args.learned:

@@ -428,37 +428,103 @@ cudaError_t conv_tc(const bf16 *X, int I, const bf16 *W, int O, const float *b, 
 
 // ---------------------------------------------------------------------------
 // halo-tile convolution on the tensor cores (net option "conv_halo"): a CTA
-// computes an 8 (x) x 16 (y) tile of one (z, t) plane, M = 128 rows with row
-// r = x + 8 y.  Per 16-channel chunk of the input it stages the tile's periodic
-// halo (10 x 18 x 3 x 3 sites) once in shared memory, K-major without swizzle:
-// the 8 consecutive x positions of a y line form one core matrix (8 rows x
-// 16 B), consecutive y lines are 160 B apart (SBO) and the two 8-channel core
-// columns HS * 16 B apart (LBO).  The A operand of tap d is then the same
-// array from a different start address, so nothing is gathered per tap; the
-// weights of one slab of 27 taps (fixed dt) are staged per phase.  Phases run
-// one after another (a CTA waits for its MMAs before restaging); two CTAs per
-// SM overlap one's staging with the other's MMAs.  Needs Lx % 8 == 0 and
-// Ly % 16 == 0; other lattices use k_conv_tc.
+// computes an 8 (x) x 16 (y) x 2 (z) tile of one t, two accumulators of
+// M = 128 rows (row r = x + 8 y, one per z plane).  Per 16-channel chunk of
+// the input it stages the tile's periodic halo (10 x 18 x 4 x 3 sites) once in
+// shared memory, K-major without swizzle: the 8 consecutive x positions of a y
+// line form one core matrix (8 rows x 16 B), consecutive y lines are 160 B
+// apart (SBO) and the two 8-channel core columns HS * 16 B apart (LBO).  The A
+// operand of tap d and plane z is then the same array from another start
+// address, so nothing is gathered per tap.  The weights of one slab of 27 taps
+// (fixed dt) are staged per phase (chunk, slab) and serve both planes.
+// Pipeline: halo and weights are double-buffered and filled with cp.async
+// (16-byte copies, zero-filled past the input channels and output rows), so
+// the copies of phase n + 1 are in flight while the MMAs of phase n run; a
+// buffer is refilled once the MMAs of the phase before (tcgen05.commit to the
+// buffer's mbarrier) have read it.  Every wait is bounded.  Needs Lx % 8 == 0,
+// Ly % 16 == 0 and Lz % 2 == 0; other lattices use k_conv_tc.
 // ---------------------------------------------------------------------------
 namespace halo {
-constexpr int TX = 8, TY = 16, HX = TX + 2, HY = TY + 2, HZ = 3, HT = 3;
-constexpr int HS = HX * HY * HZ * HT;  // 1620 halo sites
+constexpr int TX = 8, TY = 16, TZ = 2;
+constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HT = 3;
+constexpr int HS = HX * HY * HZ * HT;  // 2160 halo sites
 constexpr int LBO_A = HS * 16;         // between the two 8-channel core columns
 constexpr int SBO_A = HX * 16;         // between consecutive y lines (8-row groups)
-constexpr int A_BYTES = 2 * LBO_A;
+constexpr int A_BYTES = 2 * LBO_A;     // one 16-channel chunk of the halo
+constexpr int THREADS = 256;           // 8 warps: copies issued by all; warps w and w + 4 read one TMEM lane quarter
 }  // namespace halo
 
 template <int N>
 struct HaloLayout {
     static constexpr int W_BYTES = 27 * N * 32;  // 27 taps x N outputs x 16 BF16 channels
-    static constexpr int BAR_OFF = halo::A_BYTES + W_BYTES;
-    static constexpr int SMEM = BAR_OFF + 2 * 8 + 16;
+    static constexpr int B_OFF = 2 * halo::A_BYTES;
+    static constexpr int BAR_OFF = B_OFF + 2 * W_BYTES;  // bar[0], bar[1]: MMAs of even, odd phases; bar[2]: drain
+    static constexpr int TAB_OFF = BAR_OFF + 48;         // global site index of every halo site
+    static constexpr int SMEM = TAB_OFF + 4 * halo::HS;
+    static constexpr int TMEM_COLS = halo::TZ * N < 32 ? 32 : halo::TZ * N;
 };
 
-static bool halo_ok(const Lat &g) { return g.L[0] % halo::TX == 0 && g.L[1] % halo::TY == 0; }
+static bool halo_ok(const Lat &g)
+{
+    return g.L[0] % halo::TX == 0 && g.L[1] % halo::TY == 0 && g.L[2] % halo::TZ == 0;
+}
+
+// 16 bytes global -> shared, asynchronous; valid == false fills zeros (src not read)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(gf::tc::smem_u32(dst)), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+// global site index of every halo site of the tile (periodic wrap), once per CTA
+__device__ __forceinline__ void halo_sites(int *tab, const Lat &g, int x0, int y0, int z0, int t0)
+{
+    using namespace halo;
+    for (int hs = threadIdx.x; hs < HS; hs += blockDim.x) {
+        const int hx = hs % HX;
+        int l = hs / HX;
+        const int hy = l % HY;
+        l /= HY;
+        const int hz = l % HZ, ht = l / HZ;
+        const int x = wrap_coord(x0 - 1 + hx, g.L[0]);
+        const int y = wrap_coord(y0 - 1 + hy, g.L[1]);
+        const int z = wrap_coord(z0 - 1 + hz, g.L[2]);
+        const int t = wrap_coord(t0 - 1 + ht, g.L[3]);
+        tab[hs] = x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
+    }
+}
+
+// the tile's halo, input channels ch0 .. ch0 + 15, into one A buffer
+__device__ __forceinline__ void stage_halo(uint8_t *A, const bf16 *__restrict__ X, int I, const int *tab, int ch0)
+{
+    using namespace halo;
+    for (int w = threadIdx.x; w < 2 * HS; w += blockDim.x) {
+        const int kc = w & 1, hs = w >> 1;
+        const int ch = ch0 + 8 * kc;
+        const bool ok = ch < I;
+        cp_async16(A + kc * LBO_A + hs * 16, ok ? X + (long)tab[hs] * I + ch : X, ok);
+    }
+}
+
+// weights of the 27 taps of a slab (fixed dt), channels ch0 .. ch0 + 15: tap
+// j's B at j * N * 32, core (mr, kc) at (kc * (N/8) + mr) * 128 -> SBO 128, LBO N * 16
+template <int N>
+__device__ __forceinline__ void stage_slab_weights(uint8_t *B, const bf16 *__restrict__ W, int I, int O, int slab,
+                                                   int ch0)
+{
+    for (int w = threadIdx.x; w < 27 * N * 2; w += blockDim.x) {
+        const int kc = w & 1, r = w >> 1;
+        const int o = r % N, j = r / N;
+        const int ch = ch0 + 8 * kc;
+        const bool ok = o < O && ch < I;
+        cp_async16(B + j * N * 32 + (kc * (N / 8) + (o >> 3)) * 128 + (o & 7) * 16,
+                   ok ? W + ((long)(27 * slab + j) * O + o) * I + ch : W, ok);
+    }
+}
 
 template <int IP, int N>
-__global__ void __launch_bounds__(128) k_conv_halo_tc(const bf16 *__restrict__ X, int I, const bf16 *__restrict__ W,
+__global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const bf16 *__restrict__ X, int I, const bf16 *__restrict__ W,
                                                       int O, const float *__restrict__ bias, Lat g, int sign, int relu,
                                                       const bf16 *__restrict__ mask, bf16 *__restrict__ Yb,
                                                       float *__restrict__ Yf, int *__restrict__ err)
@@ -467,132 +533,127 @@ __global__ void __launch_bounds__(128) k_conv_halo_tc(const bf16 *__restrict__ X
     using namespace halo;
     typedef HaloLayout<N> LY;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t *A = smem;
-    uint8_t *B = smem + A_BYTES;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);  // [0] per phase, [1] final drain
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + 16);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + 24);
+    int *tab = reinterpret_cast<int *>(smem + LY::TAB_OFF);
     const int tid = threadIdx.x, warp = tid >> 5;
     constexpr uint32_t idesc = instr_desc(kM, N);
     constexpr int NPHASE = (IP / 16) * 3;  // (16-channel chunk, dt slab)
 
     int b = blockIdx.x;
-    const int nbx = g.L[0] / TX, nby = g.L[1] / TY;
+    const int nbx = g.L[0] / TX, nby = g.L[1] / TY, nbz = g.L[2] / TZ;
     const int x0 = (b % nbx) * TX;
     b /= nbx;
     const int y0 = (b % nby) * TY;
     b /= nby;
-    const int z0 = b % g.L[2];
-    const int t0 = b / g.L[2];
+    const int z0 = (b % nbz) * TZ;
+    const int t0 = b / nbz;
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int k = 0; k < 3; ++k) mbar_init(&bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tmem_slot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(LY::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    halo_sites(tab, g, x0, y0, z0, t0);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
+    // prologue: the copies of phase 0
+    stage_halo(smem, X, I, tab, 0);
+    stage_slab_weights<N>(smem + LY::B_OFF, W, I, O, 0, 0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+
     bool fail = false;
     for (int ph = 0; ph < NPHASE; ++ph) {
         const int cc = ph / 3, slab = ph % 3;
-        // the MMAs of the previous phase read A and B: wait for them before restaging
-        if (ph > 0 && !mbar_wait(&bar[0], (uint32_t)((ph - 1) & 1))) fail = true;
-        if (__syncthreads_or(fail)) {
-            fail = true;
-            break;
-        }
-        if (slab == 0) {
-            // halo of the tile, channels 16 cc .. 16 cc + 15; adjacent threads take the two
-            // 16-byte halves of one site's 32 bytes
-            for (int w = tid; w < 2 * HS; w += kThreads) {
-                const int kc = w & 1, hs = w >> 1;
-                const int hx = hs % HX;
-                int l = hs / HX;
-                const int hy = l % HY;
-                l /= HY;
-                const int hz = l % HZ, ht = l / HZ;
-                const long x = wrap_coord(x0 - 1 + hx, g.L[0]);
-                const long y = wrap_coord(y0 - 1 + hy, g.L[1]);
-                const long z = wrap_coord(z0 - 1 + hz, g.L[2]);
-                const long t = wrap_coord(t0 - 1 + ht, g.L[3]);
-                const long site = x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
-                const int ch = 16 * cc + 8 * kc;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (ch < I) v = *reinterpret_cast<const uint4 *>(X + site * I + ch);
-                *reinterpret_cast<uint4 *>(A + kc * LBO_A + hs * 16) = v;
+        const int nx = ph + 1;
+        if (nx < NPHASE) {
+            // the buffers of phase nx were last read by the MMAs of phase ph - 1 (weights) or of
+            // the chunk before (halo): wait for those, then start the copies of phase nx
+            if (ph > 0 && !mbar_wait(&bar[(ph - 1) & 1], (uint32_t)(((ph - 1) >> 1) & 1))) fail = true;
+            if (__syncthreads_or(fail)) {
+                fail = true;
+                break;
             }
+            if (nx % 3 == 0) stage_halo(smem + ((nx / 3) & 1) * A_BYTES, X, I, tab, 16 * (nx / 3));
+            stage_slab_weights<N>(smem + LY::B_OFF + (nx & 1) * LY::W_BYTES, W, I, O, nx % 3, 16 * (nx / 3));
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");  // this thread's copies of phase ph have landed
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
-        // weights of the 27 taps of this slab, the same 16 channels: tap j's B at
-        // j * N * 32, core (mr, kc) at (kc * (N/8) + mr) * 128 -> SBO 128, LBO N * 16
-        for (int w = tid; w < 27 * N * 2; w += kThreads) {
-            const int kc = w & 1, r = w >> 1;
-            const int o = r % N, j = r / N;
-            const int ch = 16 * cc + 8 * kc;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (o < O && ch < I) v = *reinterpret_cast<const uint4 *>(W + ((long)(27 * slab + j) * O + o) * I + ch);
-            *reinterpret_cast<uint4 *>(B + j * N * 32 + (kc * (N / 8) + (o >> 3)) * 128 + (o & 7) * 16) = v;
-        }
-        fence_proxy_async();
+        fence_proxy_async();  // the copies are read by the tensor cores (async proxy)
         __syncthreads();
         if (tid == 0) {
             fence_after_sync();
+            const uint8_t *A = smem + (cc & 1) * A_BYTES;
+            const uint8_t *B = smem + LY::B_OFF + (ph & 1) * LY::W_BYTES;
             const int dt = sign * (slab - 1);
             for (int j = 0; j < 27; ++j) {
                 const int dx = sign * (j % 3 - 1), dy = sign * ((j / 3) % 3 - 1), dz = sign * (j / 9 - 1);
-                // first halo line of the shifted tile; x offset dx + 1 within the line
-                const int l0 = (dy + 1) + HY * ((dz + 1) + HZ * (dt + 1));
-                const uint64_t ad = smem_desc(smem_u32(A + (l0 * HX + dx + 1) * 16), LBO_A, SBO_A);
                 const uint64_t bd = smem_desc(smem_u32(B + j * N * 32), (N / 8) * 128, 128);
-                mma_bf16(tmem, ad, bd, idesc, (ph | j) != 0);
+#pragma unroll
+                for (int zz = 0; zz < TZ; ++zz) {
+                    // first halo line of the shifted tile of plane zz; x offset dx + 1 within the line
+                    const int l0 = (dy + 1) + HY * ((zz + dz + 1) + HZ * (dt + 1));
+                    const uint64_t ad = smem_desc(smem_u32(A + (l0 * HX + dx + 1) * 16), LBO_A, SBO_A);
+                    mma_bf16(tmem + (uint32_t)(zz * N), ad, bd, idesc, (ph | j) != 0);
+                }
             }
-            mma_commit(&bar[0]);
+            mma_commit(&bar[ph & 1]);
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // nothing may land after the CTA is gone
     // all MMAs issued by thread 0 are complete once the final commit arrives
-    if (tid == 0) mma_commit(&bar[1]);
-    if (!mbar_wait(&bar[1], 0)) fail = true;
+    if (tid == 0) mma_commit(&bar[2]);
+    if (!mbar_wait(&bar[2], 0)) fail = true;
     fail = __syncthreads_or(fail);
     if (!fail) {
         fence_after_sync();
-        uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        if (N == 32) {
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(taddr));
-        } else {
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-                " [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(taddr));
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        // accumulator row tid = x + 8 y of the tile
-        const long site = (x0 + (tid & 7)) + (long)g.L[0] * ((y0 + (tid >> 3)) + (long)g.L[1] * (z0 + (long)g.L[2] * t0));
+        {
+            // warp w reads TMEM lanes 32 (w % 4) .. + 31 of plane w / 4
+            const int zz = warp >> 2, row = (warp & 3) * 32 + (tid & 31);
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(zz * N);
+            if (N == 32) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr));
+            } else {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+                    " [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(taddr));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            // accumulator row = x + 8 y of plane zz
+            const long site =
+                (x0 + (row & 7)) + (long)g.L[0] * ((y0 + (row >> 3)) + (long)g.L[1] * ((z0 + zz) + (long)g.L[2] * t0));
 #pragma unroll
-        for (int o = 0; o < N; ++o) {
-            if (o >= O) break;
-            float v = __uint_as_float(r[o]) + (bias ? bias[o] : 0.0f);
-            if (relu) v = v > 0.0f ? v : 0.0f;
-            if (mask && !(__bfloat162float(mask[site * O + o]) > 0.0f)) v = 0.0f;
-            if (Yb) Yb[site * O + o] = __float2bfloat16(v);
-            if (Yf) Yf[site * O + o] = v;
+            for (int o = 0; o < N; ++o) {
+                if (o >= O) break;
+                float v = __uint_as_float(r[o]) + (bias ? bias[o] : 0.0f);
+                if (relu) v = v > 0.0f ? v : 0.0f;
+                if (mask && !(__bfloat162float(mask[site * O + o]) > 0.0f)) v = 0.0f;
+                if (Yb) Yb[site * O + o] = __float2bfloat16(v);
+                if (Yf) Yf[site * O + o] = v;
+            }
         }
     } else if (tid == 0) {
         atomicExch(err, GF_ETIMEOUT);
@@ -601,7 +662,8 @@ __global__ void __launch_bounds__(128) k_conv_halo_tc(const bf16 *__restrict__ X
     __syncthreads();
     if (warp == 0) {
         fence_after_sync();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(LY::TMEM_COLS)
+                     : "memory");
     }
 }
 
@@ -617,8 +679,8 @@ cudaError_t conv_halo_tc(const bf16 *X, int I, const bf16 *W, int O, const float
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int blocks = (g.L[0] / halo::TX) * (g.L[1] / halo::TY) * g.L[2] * g.L[3];
-    k_conv_halo_tc<IP, N><<<blocks, gf::tc::kThreads, LY::SMEM, s>>>(X, I, W, O, b, g, sign, relu, mask, Yb, Yf, err);
+    const int blocks = (g.L[0] / halo::TX) * (g.L[1] / halo::TY) * (g.L[2] / halo::TZ) * g.L[3];
+    k_conv_halo_tc<IP, N><<<blocks, halo::THREADS, LY::SMEM, s>>>(X, I, W, O, b, g, sign, relu, mask, Yb, Yf, err);
     return cudaGetLastError();
 }
 
