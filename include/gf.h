@@ -358,10 +358,11 @@ int gf_net_gradient(gf_net *n, const void *features, const float *target, float 
 /* Options: "tensor_cores" (default 1): forward, backward-data and
  * weight-gradient convolutions as implicit GEMMs on the tcgen05 tensor cores
  * (BF16 in, FP32 accumulators in tensor memory); 0 = the CUDA-core kernels.
- * "conv_halo" (default 0): 1 = forward and backward-data convolutions stage
- * each 8 x 16 site tile's periodic halo once per 16 input channels and read
- * every tap's operand from it (lattices with Lx % 8 == 0 and Ly % 16 == 0;
- * others keep the per-tap gather kernel).  Forward, gradient and train
+ * "conv_halo" (default 1): forward and backward-data convolutions stage each
+ * 8 x 16 x 2 site tile's periodic halo once per 16 input channels and read
+ * every tap's operand from it (lattices with Lx % 8 == 0, Ly % 16 == 0 and
+ * Lz % 2 == 0; others use the per-tap gather kernel); 0 = the per-tap gather
+ * kernel everywhere.  Forward, gradient and train
  * calls synchronise the stream and return GF_ETIMEOUT if a bounded wait in a
  * tensor-core kernel expired. */
 int gf_net_set_option(gf_net *n, const char *key, double value);

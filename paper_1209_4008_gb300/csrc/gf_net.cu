@@ -6,8 +6,10 @@
 // Conventions (as in the oracle): activations X[site][C] with site = x +
 // Lx (y + Ly (z + Lz t)); tap k = (dx+1) + 3 (dy+1) + 9 (dz+1) + 27 (dt+1);
 // W[k][co][ci]; Y[s][co] = b[co] + sum_k sum_ci W[k][co][ci] X[s + d(k)][ci].
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is looked up at run time)
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -429,39 +431,48 @@ cudaError_t conv_tc(const bf16 *X, int I, const bf16 *W, int O, const float *b, 
 // ---------------------------------------------------------------------------
 // halo-tile convolution on the tensor cores (net option "conv_halo"): a CTA
 // computes an 8 (x) x 16 (y) x 2 (z) tile of one t, two accumulators of
-// M = 128 rows (row r = x + 8 y, one per z plane).  Per 16-channel chunk of
-// the input it stages the tile's periodic halo (10 x 18 x 4 x 3 sites) once in
-// shared memory, K-major without swizzle: the 8 consecutive x positions of a y
-// line form one core matrix (8 rows x 16 B), consecutive y lines are 160 B
-// apart (SBO) and the two 8-channel core columns HS * 16 B apart (LBO).  The A
-// operand of tap d and plane z is then the same array from another start
-// address, so nothing is gathered per tap.  The weights of one slab of 27 taps
-// (fixed dt) are staged per phase (chunk, slab) and serve both planes.
-// Pipeline: halo and weights are double-buffered and filled with cp.async
-// (16-byte copies, zero-filled past the input channels and output rows), so
-// the copies of phase n + 1 are in flight while the MMAs of phase n run; a
-// buffer is refilled once the MMAs of the phase before (tcgen05.commit to the
-// buffer's mbarrier) have read it.  Every wait is bounded.  Needs Lx % 8 == 0,
-// Ly % 16 == 0 and Lz % 2 == 0; other lattices use k_conv_tc.
+// M = 128 rows (row r = x + 8 y, one per z plane).  A phase is one 16-channel
+// chunk of the input and one slab of 27 taps (fixed dt); those taps read only
+// one t-plane of the tile's periodic halo, which the phase stages in shared
+// memory as three copies shifted in x by -1, 0, +1 (18 x 4 lines of 8 sites
+// each), K-major without swizzle: each line is one core matrix (8 rows x 16 B,
+// 128-byte aligned), consecutive y lines are 128 B apart (SBO) and the two
+// 8-channel core columns 3 x 72 x 128 B apart (LBO).  The A operand of tap d and
+// plane z is then the copy for dx from another aligned start address, so
+// nothing is gathered per tap; the slab's weights serve both planes.
+// Staging is TMA (cp.async.bulk.tensor): the input is first copied into a
+// buffer with one periodic ghost site on each side of every dimension
+// (k_pad_periodic), so every halo copy is one in-range 5D box {8 channels, 8 x,
+// 18 y, 4 z, 1 t} and the slab's weights one 3D box {8 channels, N outputs,
+// 27 taps} per 8-channel half; channels past the input's and rows past the
+// outputs' are filled with zeros by the TMA unit.  One thread drives the
+// pipeline: the boxes of phase n + 1 land in the other buffers (mbarrier with
+// expected bytes) while the MMAs of phase n run, and a buffer is refilled once
+// the MMAs that read it have completed (tcgen05.commit).  Every wait is
+// bounded.  Needs Lx % 8 == 0, Ly % 16 == 0 and Lz % 2 == 0; other lattices use
+// k_conv_tc.
 // ---------------------------------------------------------------------------
 namespace halo {
 constexpr int TX = 8, TY = 16, TZ = 2;
-constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HT = 3;
-constexpr int HS = HX * HY * HZ * HT;  // 2160 halo sites
-constexpr int LBO_A = HS * 16;         // between the two 8-channel core columns
-constexpr int SBO_A = HX * 16;         // between consecutive y lines (8-row groups)
-constexpr int A_BYTES = 2 * LBO_A;     // one 16-channel chunk of the halo
-constexpr int THREADS = 256;           // 8 warps: copies issued by all; warps w and w + 4 read one TMEM lane quarter
+constexpr int HY = TY + 2, HZ = TZ + 2;
+constexpr int NL = HY * HZ;            // lines (y, z) of one t-plane of the halo
+constexpr int COPY = NL * 128;         // one x-shifted copy of an 8-channel half (one TMA box)
+constexpr int LBO_A = 3 * COPY;        // between the two 8-channel core columns
+constexpr int SBO_A = 128;             // between consecutive y lines (8-row groups)
+constexpr int A_BYTES = 2 * LBO_A;     // one phase: a halo t-plane as three x-shifted copies
+constexpr int THREADS = 256;           // warps w and w + 4 read one TMEM lane quarter (two planes)
 }  // namespace halo
 
 template <int N>
 struct HaloLayout {
-    static constexpr int W_BYTES = 27 * N * 32;  // 27 taps x N outputs x 16 BF16 channels
+    static constexpr int W_HALF = 27 * N * 16;        // one 8-channel half of a slab: [tap][o][8 channels]
+    static constexpr int W_BYTES = 2 * W_HALF;
     static constexpr int B_OFF = 2 * halo::A_BYTES;
-    static constexpr int BAR_OFF = B_OFF + 2 * W_BYTES;  // bar[0], bar[1]: MMAs of even, odd phases; bar[2]: drain
-    static constexpr int TAB_OFF = BAR_OFF + 48;         // global site index of every halo site
-    static constexpr int SMEM = TAB_OFF + 4 * halo::HS;
+    // bar[0..1]: boxes of even / odd phases landed; bar[2..3]: MMAs of even / odd phases done; bar[4]: drain
+    static constexpr int BAR_OFF = B_OFF + 2 * W_BYTES;
+    static constexpr int SMEM = BAR_OFF + 5 * 8 + 8 + 16;
     static constexpr int TMEM_COLS = halo::TZ * N < 32 ? 32 : halo::TZ * N;
+    static constexpr uint32_t TX_BYTES = halo::A_BYTES + W_BYTES;  // bytes the boxes of one phase deliver
 };
 
 static bool halo_ok(const Lat &g)
@@ -469,73 +480,84 @@ static bool halo_ok(const Lat &g)
     return g.L[0] % halo::TX == 0 && g.L[1] % halo::TY == 0 && g.L[2] % halo::TZ == 0;
 }
 
-// 16 bytes global -> shared, asynchronous; valid == false fills zeros (src not read)
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid)
+// sites of the ghost-padded lattice: (Lx + 2)(Ly + 2)(Lz + 2)(Lt + 2)
+static long padded_sites(const Lat &g) { return (long)(g.L[0] + 2) * (g.L[1] + 2) * (g.L[2] + 2) * (g.L[3] + 2); }
+
+// Xp = X with one periodic ghost site on each side of every dimension:
+// padded site (px, py, pz, pt) holds site ((px - 1) mod Lx, ...); 16 bytes per thread
+__global__ void k_pad_periodic(const bf16 *__restrict__ X, int I, Lat g, bf16 *__restrict__ Xp)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(gf::tc::smem_u32(dst)), "l"(src),
-                 "r"(valid ? 16 : 0)
+    const int chunks = I / 8;
+    const int Px = g.L[0] + 2, Py = g.L[1] + 2, Pz = g.L[2] + 2;
+    const long n = (long)Px * Py * Pz * (g.L[3] + 2) * chunks;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const int ch = (int)(e % chunks);
+        long p = e / chunks;
+        const long ps = p;
+        const int px = (int)(p % Px);
+        p /= Px;
+        const int py = (int)(p % Py);
+        p /= Py;
+        const int pz = (int)(p % Pz);
+        const int pt = (int)(p / Pz);
+        const long s = wrap_coord(px - 1, g.L[0]) +
+                       (long)g.L[0] * (wrap_coord(py - 1, g.L[1]) +
+                                       (long)g.L[1] * (wrap_coord(pz - 1, g.L[2]) + (long)g.L[2] * wrap_coord(pt - 1, g.L[3])));
+        reinterpret_cast<uint4 *>(Xp + ps * I)[ch] = reinterpret_cast<const uint4 *>(X + s * I)[ch];
+    }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(gf::tc::smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
 
-// global site index of every halo site of the tile (periodic wrap), once per CTA
-__device__ __forceinline__ void halo_sites(int *tab, const Lat &g, int x0, int y0, int z0, int t0)
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t *bar)
 {
-    using namespace halo;
-    for (int hs = threadIdx.x; hs < HS; hs += blockDim.x) {
-        const int hx = hs % HX;
-        int l = hs / HX;
-        const int hy = l % HY;
-        l /= HY;
-        const int hz = l % HZ, ht = l / HZ;
-        const int x = wrap_coord(x0 - 1 + hx, g.L[0]);
-        const int y = wrap_coord(y0 - 1 + hy, g.L[1]);
-        const int z = wrap_coord(z0 - 1 + hz, g.L[2]);
-        const int t = wrap_coord(t0 - 1 + ht, g.L[3]);
-        tab[hs] = x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
-    }
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+        "[%7];" ::"r"(gf::tc::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(gf::tc::smem_u32(bar))
+        : "memory");
 }
 
-// the tile's halo, input channels ch0 .. ch0 + 15, into one A buffer
-__device__ __forceinline__ void stage_halo(uint8_t *A, const bf16 *__restrict__ X, int I, const int *tab, int ch0)
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar)
 {
-    using namespace halo;
-    for (int w = threadIdx.x; w < 2 * HS; w += blockDim.x) {
-        const int kc = w & 1, hs = w >> 1;
-        const int ch = ch0 + 8 * kc;
-        const bool ok = ch < I;
-        cp_async16(A + kc * LBO_A + hs * 16, ok ? X + (long)tab[hs] * I + ch : X, ok);
-    }
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            gf::tc::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(gf::tc::smem_u32(bar))
+        : "memory");
 }
 
-// weights of the 27 taps of a slab (fixed dt), channels ch0 .. ch0 + 15: tap
-// j's B at j * N * 32, core (mr, kc) at (kc * (N/8) + mr) * 128 -> SBO 128, LBO N * 16
-template <int N>
-__device__ __forceinline__ void stage_slab_weights(uint8_t *B, const bf16 *__restrict__ W, int I, int O, int slab,
-                                                   int ch0)
+// bounded wait for a barrier phase with a pause between polls (threads that
+// only wait for the end do not take issue slots from the one that works)
+__device__ __forceinline__ bool mbar_wait_idle(uint64_t *bar, uint32_t parity)
 {
-    for (int w = threadIdx.x; w < 27 * N * 2; w += blockDim.x) {
-        const int kc = w & 1, r = w >> 1;
-        const int o = r % N, j = r / N;
-        const int ch = ch0 + 8 * kc;
-        const bool ok = o < O && ch < I;
-        cp_async16(B + j * N * 32 + (kc * (N / 8) + (o >> 3)) * 128 + (o & 7) * 16,
-                   ok ? W + ((long)(27 * slab + j) * O + o) * I + ch : W, ok);
+    const long long t0 = gf::tc::now_ns();
+    while (!gf::tc::mbar_try_wait(bar, parity)) {
+        if (gf::tc::now_ns() - t0 > gf::tc::kWaitNs) return false;
+        __nanosleep(500);
     }
+    return true;
 }
 
 template <int IP, int N>
-__global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const bf16 *__restrict__ X, int I, const bf16 *__restrict__ W,
-                                                      int O, const float *__restrict__ bias, Lat g, int sign, int relu,
-                                                      const bf16 *__restrict__ mask, bf16 *__restrict__ Yb,
-                                                      float *__restrict__ Yf, int *__restrict__ err)
+__global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const __grid_constant__ CUtensorMap tx,
+                                                                const __grid_constant__ CUtensorMap tw, int O,
+                                                                const float *__restrict__ bias, Lat g, int sign,
+                                                                int relu, const bf16 *__restrict__ mask,
+                                                                bf16 *__restrict__ Yb, float *__restrict__ Yf,
+                                                                int *__restrict__ err)
 {
     using namespace gf::tc;
     using namespace halo;
     typedef HaloLayout<N> LY;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + 24);
-    int *tab = reinterpret_cast<int *>(smem + LY::TAB_OFF);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + 40);
     const int tid = threadIdx.x, warp = tid >> 5;
     constexpr uint32_t idesc = instr_desc(kM, N);
     constexpr int NPHASE = (IP / 16) * 3;  // (16-channel chunk, dt slab)
@@ -550,7 +572,7 @@ __global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const bf16 *__re
     const int t0 = b / nbz;
 
     if (tid == 0) {
-        for (int k = 0; k < 3; ++k) mbar_init(&bar[k], 1);
+        for (int k = 0; k < 5; ++k) mbar_init(&bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -559,62 +581,74 @@ __global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const bf16 *__re
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    halo_sites(tab, g, x0, y0, z0, t0);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    // prologue: the copies of phase 0
-    stage_halo(smem, X, I, tab, 0);
-    stage_slab_weights<N>(smem + LY::B_OFF, W, I, O, 0, 0);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-
     bool fail = false;
-    for (int ph = 0; ph < NPHASE; ++ph) {
-        const int cc = ph / 3, slab = ph % 3;
-        const int nx = ph + 1;
-        if (nx < NPHASE) {
-            // the buffers of phase nx were last read by the MMAs of phase ph - 1 (weights) or of
-            // the chunk before (halo): wait for those, then start the copies of phase nx
-            if (ph > 0 && !mbar_wait(&bar[(ph - 1) & 1], (uint32_t)(((ph - 1) >> 1) & 1))) fail = true;
-            if (__syncthreads_or(fail)) {
+    if (tid == 0) {
+        // the boxes of phase ph into buffer ph & 1: the halo t-plane read by the slab's taps
+        // (dt = sign (slab - 1)) in padded coordinates (halo x0 - 1 + c .. is padded x0 + c ..),
+        // three x-shifted copies per 8-channel half, then the slab's weights
+        auto issue = [&](int ph) {
+            const int buf = ph & 1, ch0 = 16 * (ph / 3), slab = ph % 3;
+            const int ht = sign > 0 ? slab : 2 - slab;
+            uint64_t *full = &bar[buf];
+            mbar_expect_tx(full, LY::TX_BYTES);
+            uint8_t *A = smem + buf * A_BYTES;
+#pragma unroll
+            for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    tma_load_5d(A + kc * LBO_A + c * COPY, &tx, ch0 + 8 * kc, x0 + c, y0, z0, t0 + ht, full);
+            uint8_t *B = smem + LY::B_OFF + buf * LY::W_BYTES;
+#pragma unroll
+            for (int kc = 0; kc < 2; ++kc) tma_load_3d(B + kc * LY::W_HALF, &tw, ch0 + 8 * kc, 0, 27 * slab, full);
+        };
+        int issued = 0, landed = 0;
+        issue(0);
+        issued = 1;
+        for (int ph = 0; ph < NPHASE; ++ph) {
+            const int nx = ph + 1;
+            if (nx < NPHASE) {
+                // the buffers of phase nx were last read by the MMAs of phase ph - 1
+                if (ph > 0 && !mbar_wait(&bar[2 + ((ph - 1) & 1)], (uint32_t)(((ph - 1) >> 1) & 1))) {
+                    fail = true;
+                    break;
+                }
+                issue(nx);
+                issued = nx + 1;
+            }
+            if (!mbar_wait(&bar[ph & 1], (uint32_t)((ph >> 1) & 1))) {  // the boxes of phase ph have landed
                 fail = true;
                 break;
             }
-            if (nx % 3 == 0) stage_halo(smem + ((nx / 3) & 1) * A_BYTES, X, I, tab, 16 * (nx / 3));
-            stage_slab_weights<N>(smem + LY::B_OFF + (nx & 1) * LY::W_BYTES, W, I, O, nx % 3, 16 * (nx / 3));
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            asm volatile("cp.async.wait_group 1;" ::: "memory");  // this thread's copies of phase ph have landed
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
-        fence_proxy_async();  // the copies are read by the tensor cores (async proxy)
-        __syncthreads();
-        if (tid == 0) {
+            landed = ph + 1;
             fence_after_sync();
-            const uint8_t *A = smem + (cc & 1) * A_BYTES;
+            const uint8_t *A = smem + (ph & 1) * A_BYTES;
             const uint8_t *B = smem + LY::B_OFF + (ph & 1) * LY::W_BYTES;
-            const int dt = sign * (slab - 1);
             for (int j = 0; j < 27; ++j) {
                 const int dx = sign * (j % 3 - 1), dy = sign * ((j / 3) % 3 - 1), dz = sign * (j / 9 - 1);
-                const uint64_t bd = smem_desc(smem_u32(B + j * N * 32), (N / 8) * 128, 128);
+                const uint64_t bd = smem_desc(smem_u32(B + j * N * 16), LY::W_HALF, 128);
 #pragma unroll
                 for (int zz = 0; zz < TZ; ++zz) {
-                    // first halo line of the shifted tile of plane zz; x offset dx + 1 within the line
-                    const int l0 = (dy + 1) + HY * ((zz + dz + 1) + HZ * (dt + 1));
-                    const uint64_t ad = smem_desc(smem_u32(A + (l0 * HX + dx + 1) * 16), LBO_A, SBO_A);
+                    // first line of the shifted tile of plane zz in the copy shifted by dx
+                    const int l0 = (dy + 1) + HY * (zz + dz + 1);
+                    const uint64_t ad = smem_desc(smem_u32(A + (dx + 1) * COPY + l0 * 128), LBO_A, SBO_A);
                     mma_bf16(tmem + (uint32_t)(zz * N), ad, bd, idesc, (ph | j) != 0);
                 }
             }
-            mma_commit(&bar[ph & 1]);
+            mma_commit(&bar[2 + (ph & 1)]);
         }
+        // boxes issued but not consumed must land before the CTA ends (bounded)
+        for (int q = landed; q < issued; ++q)
+            if (!mbar_wait(&bar[q & 1], (uint32_t)((q >> 1) & 1))) fail = true;
+        mma_commit(&bar[4]);  // arrives once every MMA issued above is complete
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");  // nothing may land after the CTA is gone
-    // all MMAs issued by thread 0 are complete once the final commit arrives
-    if (tid == 0) mma_commit(&bar[2]);
-    if (!mbar_wait(&bar[2], 0)) fail = true;
-    fail = __syncthreads_or(fail);
+    // everyone: all MMAs complete (bounded wait), then the epilogue
+    const bool drained = mbar_wait_idle(&bar[4], 0);
+    fail = __syncthreads_or(fail || !drained);
     if (!fail) {
         fence_after_sync();
         {
@@ -667,11 +701,35 @@ __global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const bf16 *__re
     }
 }
 
+// the tensor-map encoder of the driver, looked up once through the runtime (no link to the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
+{
+    static const EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// X [V][I] (I a multiple of 8) through the padded copy xpad (padded_sites x I) into the halo kernel
 template <int IP, int N>
 cudaError_t conv_halo_tc(const bf16 *X, int I, const bf16 *W, int O, const float *b, const Lat &g, int sign, int relu,
-                         const bf16 *mask, bf16 *Yb, float *Yf, int *err, cudaStream_t s)
+                         const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad, cudaStream_t s)
 {
     typedef HaloLayout<N> LY;
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc || !xpad) return cudaErrorNotSupported;
     static bool configured = false;
     if (!configured) {
         cudaError_t e =
@@ -679,8 +737,30 @@ cudaError_t conv_halo_tc(const bf16 *X, int I, const bf16 *W, int O, const float
         if (e != cudaSuccess) return e;
         configured = true;
     }
+    const long nchunks = padded_sites(g) * (I / 8);
+    const int pblocks = (int)std::min<long>((nchunks + 255) / 256, 152L * 32);
+    k_pad_periodic<<<pblocks, 256, 0, s>>>(X, I, g, xpad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const cuuint64_t es = sizeof(bf16);
+    const cuuint64_t Px = g.L[0] + 2, Py = g.L[1] + 2, Pz = g.L[2] + 2, Pt = g.L[3] + 2;
+    const cuuint64_t xdim[5] = { (cuuint64_t)I, Px, Py, Pz, Pt };
+    const cuuint64_t xstr[4] = { I * es, I * es * Px, I * es * Px * Py, I * es * Px * Py * Pz };
+    const cuuint32_t xbox[5] = { 8, halo::TX, halo::HY, halo::HZ, 1 };
+    const cuuint32_t ones[5] = { 1, 1, 1, 1, 1 };
+    const cuuint64_t wdim[3] = { (cuuint64_t)I, (cuuint64_t)O, 81 };
+    const cuuint64_t wstr[2] = { I * es, I * es * O };
+    const cuuint32_t wbox[3] = { 8, (cuuint32_t)N, 27 };
+    CUtensorMap tx, tw;
+    if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, xpad, xdim, xstr, xbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS ||
+        enc(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16 *>(W), wdim, wstr, wbox, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     const int blocks = (g.L[0] / halo::TX) * (g.L[1] / halo::TY) * (g.L[2] / halo::TZ) * g.L[3];
-    k_conv_halo_tc<IP, N><<<blocks, halo::THREADS, LY::SMEM, s>>>(X, I, W, O, b, g, sign, relu, mask, Yb, Yf, err);
+    k_conv_halo_tc<IP, N><<<blocks, halo::THREADS, LY::SMEM, s>>>(tx, tw, O, b, g, sign, relu, mask, Yb, Yf, err);
     return cudaGetLastError();
 }
 
@@ -904,10 +984,11 @@ struct gf_net {
     bf16 *act[4] = { nullptr };  // act[1..3] owned; act[0] = caller's features
     float *out = nullptr;
     bf16 *dA = nullptr, *dB = nullptr;  // [V][32] gradient scratch (ping-pong)
+    bf16 *xpad = nullptr;  // halo-tile convolutions: the input with periodic ghost sites, up to 80 channels
     double *partial = nullptr, *dloss = nullptr;
     int *derr = nullptr;  // tensor-core kernels: bounded-wait expiry
     int use_tc = 1;       // forward and backward-data on tcgen05 (else CUDA cores)
-    int use_halo = 0;     // ... with the halo-tile kernel where the extents allow it
+    int use_halo = 1;     // ... with the halo-tile kernel where the extents allow it
     int step = 0;
     std::string err;
 };
@@ -952,7 +1033,7 @@ static cudaError_t conv_tensor(const gf_net *n, const bf16 *X, int I, const bf16
                                int relu, const bf16 *mask, bf16 *Yb, float *Yf)
 {
     if (n->use_halo && halo_ok(n->g))
-        return conv_halo_tc<IP, N>(X, I, W, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->stream);
+        return conv_halo_tc<IP, N>(X, I, W, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->xpad, n->stream);
     return conv_tc<IP, N>(X, I, W, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->stream);
 }
 
@@ -1089,6 +1170,7 @@ static int ensure_buffers(gf_net *n)
     NCK(cudaMalloc(&n->out, sizeof(float) * V * 8));
     NCK(cudaMalloc(&n->dA, sizeof(bf16) * V * 32));
     NCK(cudaMalloc(&n->dB, sizeof(bf16) * V * 32));
+    if (halo_ok(n->g)) NCK(cudaMalloc(&n->xpad, sizeof(bf16) * padded_sites(n->g) * GF_NET_CIN));
     NCK(cudaMalloc(&n->partial, sizeof(double) * 1024));
     NCK(cudaMalloc(&n->dloss, sizeof(double)));
     NCK(cudaMalloc(&n->derr, sizeof(int)));
@@ -1111,6 +1193,7 @@ int gf_net_destroy(gf_net *n)
     cudaFree(n->out);
     cudaFree(n->dA);
     cudaFree(n->dB);
+    cudaFree(n->xpad);
     cudaFree(n->partial);
     cudaFree(n->dloss);
     cudaFree(n->derr);
