@@ -433,18 +433,20 @@ cudaError_t conv_tc(const bf16 *X, int I, const bf16 *W, int O, const float *b, 
 // computes an 8 (x) x 16 (y) x 2 (z) tile of one t, two accumulators of
 // M = 128 rows (row r = x + 8 y, one per z plane).  A phase is one 16-channel
 // chunk of the input and one slab of 27 taps (fixed dt); those taps read only
-// one t-plane of the tile's periodic halo, which the phase stages in shared
-// memory as three copies shifted in x by -1, 0, +1 (18 x 4 lines of 8 sites
-// each), K-major without swizzle: each line is one core matrix (8 rows x 16 B,
-// 128-byte aligned), consecutive y lines are 128 B apart (SBO) and the two
-// 8-channel core columns 3 x 72 x 128 B apart (LBO).  The A operand of tap d and
-// plane z is then the copy for dx from another aligned start address, so
-// nothing is gathered per tap; the slab's weights serve both planes.
+// one t-plane of the tile's periodic halo (18 x 4 lines of 10 sites), which the
+// phase stages in shared memory K-major without swizzle: the 8 consecutive x
+// positions of a y line form one core matrix (8 rows x 16 B), consecutive y
+// lines are 160 B apart (SBO) and the two 8-channel core columns one plane half
+// apart (LBO).  The A operand of tap d and plane z is then the same array from
+// another start address, so nothing is gathered per tap; the slab's weights
+// serve both planes.  (Aligned x-shifted copies double the MMA rate but triple
+// the halo bytes or need a copy pass; measured, both were slower than this
+// layout, which keeps shared memory small enough for two CTAs per SM.)
 // Staging is TMA (cp.async.bulk.tensor): the input is first copied into a
 // buffer with one periodic ghost site on each side of every dimension
-// (k_pad_periodic), so every halo copy is one in-range 5D box {8 channels, 8 x,
-// 18 y, 4 z, 1 t} and the slab's weights one 3D box {8 channels, N outputs,
-// 27 taps} per 8-channel half; channels past the input's and rows past the
+// (k_pad_periodic), so every halo plane is one in-range 5D box {8 channels,
+// 10 x, 18 y, 4 z, 1 t} and the slab's weights one 3D box {8 channels, N
+// outputs, 27 taps} per 8-channel half; channels past the input's and rows past the
 // outputs' are filled with zeros by the TMA unit.  One thread drives the
 // pipeline: the boxes of phase n + 1 land in the other buffers (mbarrier with
 // expected bytes) while the MMAs of phase n run, and a buffer is refilled once
@@ -455,11 +457,12 @@ cudaError_t conv_tc(const bf16 *X, int I, const bf16 *W, int O, const float *b, 
 namespace halo {
 constexpr int TX = 8, TY = 16, TZ = 2;
 constexpr int HY = TY + 2, HZ = TZ + 2;
+constexpr int HX = TX + 2;             // sites of one halo line
 constexpr int NL = HY * HZ;            // lines (y, z) of one t-plane of the halo
-constexpr int COPY = NL * 128;         // one x-shifted copy of an 8-channel half (one TMA box)
-constexpr int LBO_A = 3 * COPY;        // between the two 8-channel core columns
-constexpr int SBO_A = 128;             // between consecutive y lines (8-row groups)
-constexpr int A_BYTES = 2 * LBO_A;     // one phase: a halo t-plane as three x-shifted copies
+constexpr int RAW = NL * HX * 16;      // one 8-channel half of a halo t-plane (one TMA box)
+constexpr int LBO_A = RAW;             // between the two 8-channel core columns
+constexpr int SBO_A = HX * 16;         // between consecutive y lines (8-row groups)
+constexpr int A_BYTES = 2 * RAW;       // one phase: a halo t-plane
 constexpr int THREADS = 256;           // warps w and w + 4 read one TMEM lane quarter (two planes)
 }  // namespace halo
 
@@ -589,8 +592,8 @@ __global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const __grid_con
     bool fail = false;
     if (tid == 0) {
         // the boxes of phase ph into buffer ph & 1: the halo t-plane read by the slab's taps
-        // (dt = sign (slab - 1)) in padded coordinates (halo x0 - 1 + c .. is padded x0 + c ..),
-        // three x-shifted copies per 8-channel half, then the slab's weights
+        // (dt = sign (slab - 1)) in padded coordinates (halo x0 - 1 is padded x0), one box per
+        // 8-channel half, then the slab's weights
         auto issue = [&](int ph) {
             const int buf = ph & 1, ch0 = 16 * (ph / 3), slab = ph % 3;
             const int ht = sign > 0 ? slab : 2 - slab;
@@ -598,10 +601,7 @@ __global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const __grid_con
             mbar_expect_tx(full, LY::TX_BYTES);
             uint8_t *A = smem + buf * A_BYTES;
 #pragma unroll
-            for (int kc = 0; kc < 2; ++kc)
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    tma_load_5d(A + kc * LBO_A + c * COPY, &tx, ch0 + 8 * kc, x0 + c, y0, z0, t0 + ht, full);
+            for (int kc = 0; kc < 2; ++kc) tma_load_5d(A + kc * LBO_A, &tx, ch0 + 8 * kc, x0, y0, z0, t0 + ht, full);
             uint8_t *B = smem + LY::B_OFF + buf * LY::W_BYTES;
 #pragma unroll
             for (int kc = 0; kc < 2; ++kc) tma_load_3d(B + kc * LY::W_HALF, &tw, ch0 + 8 * kc, 0, 27 * slab, full);
@@ -633,9 +633,9 @@ __global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const __grid_con
                 const uint64_t bd = smem_desc(smem_u32(B + j * N * 16), LY::W_HALF, 128);
 #pragma unroll
                 for (int zz = 0; zz < TZ; ++zz) {
-                    // first line of the shifted tile of plane zz in the copy shifted by dx
+                    // first halo line of the shifted tile of plane zz; x offset dx + 1 within the line
                     const int l0 = (dy + 1) + HY * (zz + dz + 1);
-                    const uint64_t ad = smem_desc(smem_u32(A + (dx + 1) * COPY + l0 * 128), LBO_A, SBO_A);
+                    const uint64_t ad = smem_desc(smem_u32(A + (l0 * HX + dx + 1) * 16), LBO_A, SBO_A);
                     mma_bf16(tmem + (uint32_t)(zz * N), ad, bd, idesc, (ph | j) != 0);
                 }
             }
@@ -746,7 +746,7 @@ cudaError_t conv_halo_tc(const bf16 *X, int I, const bf16 *W, int O, const float
     const cuuint64_t Px = g.L[0] + 2, Py = g.L[1] + 2, Pz = g.L[2] + 2, Pt = g.L[3] + 2;
     const cuuint64_t xdim[5] = { (cuuint64_t)I, Px, Py, Pz, Pt };
     const cuuint64_t xstr[4] = { I * es, I * es * Px, I * es * Px * Py, I * es * Px * Py * Pz };
-    const cuuint32_t xbox[5] = { 8, halo::TX, halo::HY, halo::HZ, 1 };
+    const cuuint32_t xbox[5] = { 8, halo::HX, halo::HY, halo::HZ, 1 };
     const cuuint32_t ones[5] = { 1, 1, 1, 1, 1 };
     const cuuint64_t wdim[3] = { (cuuint64_t)I, (cuuint64_t)O, 81 };
     const cuuint64_t wstr[2] = { I * es, I * es * O };
