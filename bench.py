@@ -812,7 +812,7 @@ def net_kernels(args):
     net = gf.gf_net_create(dims)
     gf.gf_net_set_stream(net, torch.cuda.current_stream())
     gf.gf_net_set_params(net, L.init_params(0))
-    gf.gf_net_set_option(net, "conv_halo", 0 if args.conv_gather else 1)
+    gf.gf_net_set_option(net, "conv_halo", args.conv_halo)
     gen = torch.Generator(device="cuda").manual_seed(7)
     feats = torch.randn(V, ch[0], device="cuda", generator=gen).to(torch.bfloat16)
     target = 0.1 * torch.randn(V, ch[4], device="cuda", generator=gen)
@@ -837,8 +837,8 @@ def net_kernels(args):
     for r in res.values():
         r["frac_of_bf16_peak"] = r["tflops"] / bf16 if bf16 else None
     print(json.dumps({"workload": f"warm-start network {'x'.join(map(str, dims))}, channels {list(ch)}"
-                                  + (", per-tap gather convolutions" if args.conv_gather else
-                                     ", halo-tile convolutions"),
+                                  + {0: ", per-tap gather convolutions", 1: ", x-line convolutions",
+                                     2: ", halo-tile convolutions"}[args.conv_halo],
                       "sites": V, "flop_forward": fwd_flop, "flop_train_step": train_flop,
                       "bf16_peak_tflops": bf16, **res}), flush=True)
 
@@ -1035,8 +1035,8 @@ def main():
                     help="--learned: skip the pairs and training, evaluate these stored parameters")
     ap.add_argument("--coulomb", action="store_true", help="the 48^3x96 Coulomb workload with annealing")
     ap.add_argument("--net", action="store_true", help="time the warm-start network's kernels")
-    ap.add_argument("--conv-gather", action="store_true",
-                    help="--net: the per-tap gather convolutions instead of the halo-tile ones (the default)")
+    ap.add_argument("--conv-halo", type=int, default=1, choices=(0, 1, 2),
+                    help="--net: convolution kernel, 1 x-line (default), 2 halo-tile, 0 per-tap gather")
     ap.add_argument("--mag", action="store_true", help="the maximally Abelian gauge on the 32^4 field")
     ap.add_argument("--thermal", action="store_true", help="gauge fixing of a field thermalised at beta 6.1")
     ap.add_argument("--solve", action="store_true",

@@ -358,11 +358,14 @@ int gf_net_gradient(gf_net *n, const void *features, const float *target, float 
 /* Options: "tensor_cores" (default 1): forward, backward-data and
  * weight-gradient convolutions as implicit GEMMs on the tcgen05 tensor cores
  * (BF16 in, FP32 accumulators in tensor memory); 0 = the CUDA-core kernels.
- * "conv_halo" (default 1): forward and backward-data convolutions stage each
- * 8 x 16 x 2 site tile's periodic halo once per 16 input channels and read
- * every tap's operand from it (lattices with Lx % 8 == 0, Ly % 16 == 0 and
- * Lz % 2 == 0; others use the per-tap gather kernel); 0 = the per-tap gather
- * kernel everywhere.  Forward, gradient and train
+ * "conv_halo" (default 1): forward and backward-data convolutions stage a
+ * tile's periodic halo once per 16 input channels and read every tap's operand
+ * from it.  1 = x-line tiles (whole x lines, 128 / Lx lines of y, two z
+ * planes; lattices with Lx = 8, 16 or 32, Ly % (128 / Lx) == 0 and
+ * Lz % 2 == 0), else 8 x 16 x 2 site tiles (Lx % 8 == 0, Ly % 16 == 0,
+ * Lz % 2 == 0); 2 = the 8 x 16 x 2 tiles only; lattices that fit neither, and
+ * 0, use the per-tap gather kernel.  Other values: GF_EINVAL.  Forward,
+ * gradient and train
  * calls synchronise the stream and return GF_ETIMEOUT if a bounded wait in a
  * tensor-core kernel expired. */
 int gf_net_set_option(gf_net *n, const char *key, double value);

@@ -206,8 +206,10 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ gr, floa
     p[e] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
 }
 
+// ... and the same two blocked by 8 input channels for the halo kernels' TMA
+// boxes: Wh[i / 8][k][o][i % 8] and Wth[o / 8][k][i][o % 8] (I, O multiples of 8)
 __global__ void k_cast_weights(const float *__restrict__ W, int I, int O, bf16 *__restrict__ Wb,
-                               bf16 *__restrict__ Wt)
+                               bf16 *__restrict__ Wt, bf16 *__restrict__ Wh, bf16 *__restrict__ Wth)
 {
     long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long n = 81L * I * O;
@@ -218,6 +220,8 @@ __global__ void k_cast_weights(const float *__restrict__ W, int I, int O, bf16 *
     bf16 w = __float2bfloat16(W[e]);
     Wb[e] = w;
     Wt[((long)k * I + i) * O + o] = w;
+    Wh[(((long)(i >> 3) * 81 + k) * O + o) * 8 + (i & 7)] = w;
+    Wth[(((long)(o >> 3) * 81 + k) * I + i) * 8 + (o & 7)] = w;
 }
 
 
@@ -483,30 +487,37 @@ static bool halo_ok(const Lat &g)
     return g.L[0] % halo::TX == 0 && g.L[1] % halo::TY == 0 && g.L[2] % halo::TZ == 0;
 }
 
-// sites of the ghost-padded lattice: (Lx + 2)(Ly + 2)(Lz + 2)(Lt + 2)
-static long padded_sites(const Lat &g) { return (long)(g.L[0] + 2) * (g.L[1] + 2) * (g.L[2] + 2) * (g.L[3] + 2); }
-
-// Xp = X with one periodic ghost site on each side of every dimension:
-// padded site (px, py, pz, pt) holds site ((px - 1) mod Lx, ...); 16 bytes per thread
-__global__ void k_pad_periodic(const bf16 *__restrict__ X, int I, Lat g, bf16 *__restrict__ Xp)
+// sites of the ghost-padded lattice: (Lx + 2 gx)(Ly + 2)(Lz + 2)(Lt + 2), gx = 1
+// with ghosts in x, 0 without
+static long padded_sites(const Lat &g, int gx = 1)
 {
-    const int chunks = I / 8;
-    const int Px = g.L[0] + 2, Py = g.L[1] + 2, Pz = g.L[2] + 2;
-    const long n = (long)Px * Py * Pz * (g.L[3] + 2) * chunks;
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-        const int ch = (int)(e % chunks);
-        long p = e / chunks;
-        const long ps = p;
+    return (long)(g.L[0] + 2 * gx) * (g.L[1] + 2) * (g.L[2] + 2) * (g.L[3] + 2);
+}
+
+// Xp = X with one periodic ghost site on each side of y, z, t (and of x when
+// gx = 1), blocked by 8 channels so that a TMA box row is a contiguous run:
+// Xp[c][pt][pz][py][px][8] holds channels 8 c .. 8 c + 7 of site
+// ((px - gx) mod Lx, (py - 1) mod Ly, (pz - 1) mod Lz, (pt - 1) mod Lt).  One
+// thread per padded site: it reads the site's I channels (contiguous) and
+// writes one 16-byte piece per group, consecutive threads side by side.
+__global__ void k_pad_periodic(const bf16 *__restrict__ X, int I, Lat g, int gx, bf16 *__restrict__ Xp)
+{
+    const int G = I / 8;
+    const int Px = g.L[0] + 2 * gx, Py = g.L[1] + 2, Pz = g.L[2] + 2;
+    const long P = (long)Px * Py * Pz * (g.L[3] + 2);
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (long)gridDim.x * blockDim.x) {
+        long p = e;
         const int px = (int)(p % Px);
         p /= Px;
         const int py = (int)(p % Py);
         p /= Py;
         const int pz = (int)(p % Pz);
         const int pt = (int)(p / Pz);
-        const long s = wrap_coord(px - 1, g.L[0]) +
-                       (long)g.L[0] * (wrap_coord(py - 1, g.L[1]) +
-                                       (long)g.L[1] * (wrap_coord(pz - 1, g.L[2]) + (long)g.L[2] * wrap_coord(pt - 1, g.L[3])));
-        reinterpret_cast<uint4 *>(Xp + ps * I)[ch] = reinterpret_cast<const uint4 *>(X + s * I)[ch];
+        const long zt = wrap_coord(pz - 1, g.L[2]) + (long)g.L[2] * wrap_coord(pt - 1, g.L[3]);
+        const long s = wrap_coord(px - gx, g.L[0]) + (long)g.L[0] * (wrap_coord(py - 1, g.L[1]) + (long)g.L[1] * zt);
+        const uint4 *src = reinterpret_cast<const uint4 *>(X + s * I);
+        uint4 *dst = reinterpret_cast<uint4 *>(Xp) + e;
+        for (int c = 0; c < G; ++c) dst[(long)c * P] = src[c];
     }
 }
 
@@ -516,22 +527,22 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
-__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
-                                            uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
-        "[%7];" ::"r"(gf::tc::smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(gf::tc::smem_u32(bar))
-        : "memory");
-}
-
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar)
 {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
             gf::tc::smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(gf::tc::smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(gf::tc::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(gf::tc::smem_u32(bar))
         : "memory");
 }
 
@@ -545,6 +556,98 @@ __device__ __forceinline__ bool mbar_wait_idle(uint64_t *bar, uint32_t parity)
         __nanosleep(500);
     }
     return true;
+}
+
+// 32 (N = 32) or 16 (N = 16) accumulator columns of this warp's lane quarter, as floats
+template <int N>
+__device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float *v)
+{
+    uint32_t r[N];
+    if (N == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+            " [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int o = 0; o < N; ++o) v[o] = __uint_as_float(r[o]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// The epilogue of one warp's 32 accumulator rows (row r of the warp is the
+// site site_of(r); this thread holds row lane in acc): bias, ReLU, the mask,
+// then BF16 (Yb) or FP32 (Yf) rows of O channels.  Mask and output rows pass
+// through the warp's staging area in shared memory (32 rows of at most 128 B),
+// so global memory is read and written in 16-byte pieces at consecutive
+// addresses: one 2-byte access per channel made an L2 request per element.
+template <int N, typename SiteOf>
+__device__ __forceinline__ void epilogue_rows(float (&acc)[N], int O, const float *__restrict__ bias, int relu,
+                                              const bf16 *__restrict__ mask, bf16 *__restrict__ Yb,
+                                              float *__restrict__ Yf, uint4 *stage, int lane, SiteOf site_of)
+{
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+        float v = acc[o] + (bias && o < O ? bias[o] : 0.0f);
+        acc[o] = relu && !(v > 0.0f) ? 0.0f : v;
+    }
+    if (mask) {
+        const int cpr = O / 8;  // 16-byte pieces of a BF16 row
+        for (int c = lane; c < 32 * cpr; c += 32)
+            stage[c] = reinterpret_cast<const uint4 *>(mask + site_of(c / cpr) * O)[c % cpr];
+        __syncwarp();
+        const bf16 *m = reinterpret_cast<const bf16 *>(stage + lane * cpr);
+#pragma unroll
+        for (int o = 0; o < N; ++o)
+            if (o < O && !(__bfloat162float(m[o]) > 0.0f)) acc[o] = 0.0f;
+        __syncwarp();
+    }
+    if (Yb) {
+        const int cpr = O / 8;
+#pragma unroll
+        for (int c = 0; c < N / 8; ++c) {
+            if (c < cpr) {
+                uint4 u;
+                u.x = pack_bf16x2(acc[8 * c + 0], acc[8 * c + 1]);
+                u.y = pack_bf16x2(acc[8 * c + 2], acc[8 * c + 3]);
+                u.z = pack_bf16x2(acc[8 * c + 4], acc[8 * c + 5]);
+                u.w = pack_bf16x2(acc[8 * c + 6], acc[8 * c + 7]);
+                stage[lane * cpr + c] = u;
+            }
+        }
+        __syncwarp();
+        for (int c = lane; c < 32 * cpr; c += 32)
+            reinterpret_cast<uint4 *>(Yb + site_of(c / cpr) * O)[c % cpr] = stage[c];
+        __syncwarp();
+    }
+    if (Yf) {
+        const int cpr = O / 4;  // 16-byte pieces of an FP32 row
+#pragma unroll
+        for (int c = 0; c < N / 4; ++c)
+            if (c < cpr)
+                stage[lane * cpr + c] = make_uint4(__float_as_uint(acc[4 * c + 0]), __float_as_uint(acc[4 * c + 1]),
+                                                   __float_as_uint(acc[4 * c + 2]), __float_as_uint(acc[4 * c + 3]));
+        __syncwarp();
+        for (int c = lane; c < 32 * cpr; c += 32)
+            reinterpret_cast<uint4 *>(Yf + site_of(c / cpr) * O)[c % cpr] = stage[c];
+        __syncwarp();
+    }
 }
 
 template <int IP, int N>
@@ -592,8 +695,8 @@ __global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const __grid_con
     bool fail = false;
     if (tid == 0) {
         // the boxes of phase ph into buffer ph & 1: the halo t-plane read by the slab's taps
-        // (dt = sign (slab - 1)) in padded coordinates (halo x0 - 1 is padded x0), one box per
-        // 8-channel half, then the slab's weights
+        // (dt = sign (slab - 1)) in padded coordinates (halo x0 - 1 is padded x0; the plane of
+        // channel group c at t is c Pt + t), one box per 8-channel half, then the slab's weights
         auto issue = [&](int ph) {
             const int buf = ph & 1, ch0 = 16 * (ph / 3), slab = ph % 3;
             const int ht = sign > 0 ? slab : 2 - slab;
@@ -601,10 +704,11 @@ __global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const __grid_con
             mbar_expect_tx(full, LY::TX_BYTES);
             uint8_t *A = smem + buf * A_BYTES;
 #pragma unroll
-            for (int kc = 0; kc < 2; ++kc) tma_load_5d(A + kc * LBO_A, &tx, ch0 + 8 * kc, x0, y0, z0, t0 + ht, full);
+            for (int kc = 0; kc < 2; ++kc)
+                tma_load_4d(A + kc * LBO_A, &tx, 8 * x0, y0, z0, (ch0 / 8 + kc) * (g.L[3] + 2) + t0 + ht, full);
             uint8_t *B = smem + LY::B_OFF + buf * LY::W_BYTES;
 #pragma unroll
-            for (int kc = 0; kc < 2; ++kc) tma_load_3d(B + kc * LY::W_HALF, &tw, ch0 + 8 * kc, 0, 27 * slab, full);
+            for (int kc = 0; kc < 2; ++kc) tma_load_3d(B + kc * LY::W_HALF, &tw, 0, 27 * slab, ch0 / 8 + kc, full);
         };
         int issued = 0, landed = 0;
         issue(0);
@@ -651,44 +755,18 @@ __global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const __grid_con
     fail = __syncthreads_or(fail || !drained);
     if (!fail) {
         fence_after_sync();
-        {
-            // warp w reads TMEM lanes 32 (w % 4) .. + 31 of plane w / 4
-            const int zz = warp >> 2, row = (warp & 3) * 32 + (tid & 31);
-            uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(zz * N);
-            if (N == 32) {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(taddr));
-            } else {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-                    " [%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15])
-                    : "r"(taddr));
-            }
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            // accumulator row = x + 8 y of plane zz
-            const long site =
-                (x0 + (row & 7)) + (long)g.L[0] * ((y0 + (row >> 3)) + (long)g.L[1] * ((z0 + zz) + (long)g.L[2] * t0));
-#pragma unroll
-            for (int o = 0; o < N; ++o) {
-                if (o >= O) break;
-                float v = __uint_as_float(r[o]) + (bias ? bias[o] : 0.0f);
-                if (relu) v = v > 0.0f ? v : 0.0f;
-                if (mask && !(__bfloat162float(mask[site * O + o]) > 0.0f)) v = 0.0f;
-                if (Yb) Yb[site * O + o] = __float2bfloat16(v);
-                if (Yf) Yf[site * O + o] = v;
-            }
-        }
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 of plane w / 4; accumulator row = x + 8 y
+        const int zz = warp >> 2, q = warp & 3;
+        float acc[N];
+        tmem_load_cols<N>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(zz * N), acc);
+        const long plane = (long)g.L[1] * ((z0 + zz) + (long)g.L[2] * t0);
+        auto site_of = [&](int r) {
+            const int row = q * 32 + r;
+            return (long)(x0 + (row & 7)) + (long)g.L[0] * ((y0 + (row >> 3)) + plane);
+        };
+        // the A buffers are free once every MMA has completed
+        epilogue_rows<N>(acc, O, bias, relu, mask, Yb, Yf, reinterpret_cast<uint4 *>(smem) + warp * 256,
+                         tid & 31, site_of);
     } else if (tid == 0) {
         atomicExch(err, GF_ETIMEOUT);
     }
@@ -722,14 +800,50 @@ static EncodeTiledFn encode_tiled()
     return fn;
 }
 
-// X [V][I] (I a multiple of 8) through the padded copy xpad (padded_sites x I) into the halo kernel
-template <int IP, int N>
-cudaError_t conv_halo_tc(const bf16 *X, int I, const bf16 *W, int O, const float *b, const Lat &g, int sign, int relu,
-                         const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad, cudaStream_t s)
+// Pads X [V][I] (I a multiple of 8) into xpad (blocked by 8 channels, x ghosts
+// when gx = 1) and encodes the tensor maps of the halo kernels.  A line of x
+// and its 8 channels are contiguous in xpad, and so are the rows o of a tap and
+// their 8 channels in the blocked weights, so each is one inner dimension and
+// a box row is a contiguous run (a TMA request per 16-byte row would bind the
+// L2): tx over xpad as {8 Px, Py, Pz, (I / 8) Pt} with box {8 bx, by, bz, 1},
+// tw over Wblk[I / 8][81][O][8] as {8 O, 81, I / 8} with box {8 N, 27, 1}.
+// Channel groups past I / 8 and rows past O are outside the maps: the TMA unit
+// fills them with zeros.
+static cudaError_t halo_prepare(const bf16 *X, int I, const bf16 *Wblk, int O, int N, const Lat &g, int gx, int bx,
+                                int by, int bz, bf16 *xpad, cudaStream_t s, CUtensorMap *tx, CUtensorMap *tw)
 {
-    typedef HaloLayout<N> LY;
     const EncodeTiledFn enc = encode_tiled();
     if (!enc || !xpad) return cudaErrorNotSupported;
+    const long P = padded_sites(g, gx);
+    const int pblocks = (int)std::min<long>((P + 255) / 256, 152L * 32);
+    k_pad_periodic<<<pblocks, 256, 0, s>>>(X, I, g, gx, xpad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const cuuint64_t es = sizeof(bf16);
+    const cuuint64_t Px = g.L[0] + 2 * gx, Py = g.L[1] + 2, Pz = g.L[2] + 2, Pt = g.L[3] + 2;
+    const cuuint64_t xdim[4] = { 8 * Px, Py, Pz, (cuuint64_t)(I / 8) * Pt };
+    const cuuint64_t xstr[3] = { 8 * es * Px, 8 * es * Px * Py, 8 * es * Px * Py * Pz };
+    const cuuint32_t xbox[4] = { (cuuint32_t)(8 * bx), (cuuint32_t)by, (cuuint32_t)bz, 1 };
+    const cuuint32_t ones[4] = { 1, 1, 1, 1 };
+    const cuuint64_t wdim[3] = { 8 * (cuuint64_t)O, 81, (cuuint64_t)(I / 8) };
+    const cuuint64_t wstr[2] = { 8 * es * O, 8 * es * O * 81 };
+    const cuuint32_t wbox[3] = { (cuuint32_t)(8 * N), 27, 1 };
+    if (enc(tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, xpad, xdim, xstr, xbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS ||
+        enc(tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16 *>(Wblk), wdim, wstr, wbox, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+// X [V][I] through the padded copy into the halo-tile kernel; Wblk = the weights blocked by 8 input channels
+template <int IP, int N>
+cudaError_t conv_halo_tc(const bf16 *X, int I, const bf16 *Wblk, int O, const float *b, const Lat &g, int sign,
+                         int relu, const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad, cudaStream_t s)
+{
+    typedef HaloLayout<N> LY;
     static bool configured = false;
     if (!configured) {
         cudaError_t e =
@@ -737,30 +851,217 @@ cudaError_t conv_halo_tc(const bf16 *X, int I, const bf16 *W, int O, const float
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const long nchunks = padded_sites(g) * (I / 8);
-    const int pblocks = (int)std::min<long>((nchunks + 255) / 256, 152L * 32);
-    k_pad_periodic<<<pblocks, 256, 0, s>>>(X, I, g, xpad);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const cuuint64_t es = sizeof(bf16);
-    const cuuint64_t Px = g.L[0] + 2, Py = g.L[1] + 2, Pz = g.L[2] + 2, Pt = g.L[3] + 2;
-    const cuuint64_t xdim[5] = { (cuuint64_t)I, Px, Py, Pz, Pt };
-    const cuuint64_t xstr[4] = { I * es, I * es * Px, I * es * Px * Py, I * es * Px * Py * Pz };
-    const cuuint32_t xbox[5] = { 8, halo::HX, halo::HY, halo::HZ, 1 };
-    const cuuint32_t ones[5] = { 1, 1, 1, 1, 1 };
-    const cuuint64_t wdim[3] = { (cuuint64_t)I, (cuuint64_t)O, 81 };
-    const cuuint64_t wstr[2] = { I * es, I * es * O };
-    const cuuint32_t wbox[3] = { 8, (cuuint32_t)N, 27 };
     CUtensorMap tx, tw;
-    if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, xpad, xdim, xstr, xbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
-            CUDA_SUCCESS ||
-        enc(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16 *>(W), wdim, wstr, wbox, ones,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+    cudaError_t e = halo_prepare(X, I, Wblk, O, N, g, 1, halo::HX, halo::HY, halo::HZ, xpad, s, &tx, &tw);
+    if (e != cudaSuccess) return e;
     const int blocks = (g.L[0] / halo::TX) * (g.L[1] / halo::TY) * (g.L[2] / halo::TZ) * g.L[3];
     k_conv_halo_tc<IP, N><<<blocks, halo::THREADS, LY::SMEM, s>>>(tx, tw, O, b, g, sign, relu, mask, Yb, Yf, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// x-line convolution on the tensor cores (the default where Lx is 8, 16 or 32):
+// a CTA computes whole periodic x lines, 128 / Lx lines of y (M = 128 rows,
+// row r = x + Lx y) in each of two z planes, at one t.  The x shift of a tap is
+// taken out of the A operand and applied to the accumulator: for the lines of
+// one (dy, dz) a single MMA multiplies the unshifted rows by the weights of the
+// three taps dx = -1, 0, +1 side by side (N = 3 x 32 columns), and the epilogue
+// adds the three column blocks with their rows moved by -dx, a lane shuffle
+// within each line that wraps around the period.  So every A view starts on a
+// whole line (a multiple of 128 bytes, where the tensor core reads shared
+// memory at full rate), the halo has no x ghosts, and a phase issues 18 MMAs
+// instead of 54 (the x-shifted views of the tile kernel above read shared
+// memory at half rate).  A phase is one 16-channel chunk and one dt slab as
+// above; its halo t-plane, 4 z x (128 / Lx + 2) y lines of Lx sites, is one TMA
+// box per 8-channel half from the ghost-padded copy, and its weights the same
+// boxes as above.  Needs Lx in {8, 16, 32}, Ly % (128 / Lx) == 0, Lz % 2 == 0.
+// ---------------------------------------------------------------------------
+namespace xline {
+constexpr int TZ = 2, HZ = TZ + 2;
+constexpr int RAW_MAX = HZ * 16 * (128 + 2 * 32);  // one 8-channel half of a halo t-plane, Lx = 32
+constexpr int A_BYTES = 2 * RAW_MAX;
+constexpr int THREADS = 256;  // warps w and w + 4 read one TMEM lane quarter (two planes)
+}  // namespace xline
+
+template <int N>
+struct LineLayout {
+    static constexpr int W_HALF = 27 * N * 16;  // one 8-channel half of a slab: [tap][o][8 channels]
+    static constexpr int W_BYTES = 2 * W_HALF;
+    static constexpr int B_OFF = 2 * xline::A_BYTES;
+    // bar[0..1]: boxes of even / odd phases landed; bar[2..3]: MMAs of even / odd phases done; bar[4]: drain
+    static constexpr int BAR_OFF = B_OFF + 2 * W_BYTES;
+    static constexpr int SMEM = BAR_OFF + 5 * 8 + 8 + 16;
+    static constexpr int NM = 3 * N;                // columns of one plane's accumulator: taps dx = -1, 0, +1
+    static constexpr int PS = NM <= 64 ? 64 : 128;  // TMEM columns between the two planes
+    static constexpr int TMEM_COLS = 2 * PS;
+};
+
+static bool line_ok(const Lat &g)
+{
+    const int Lx = g.L[0];
+    return (Lx == 8 || Lx == 16 || Lx == 32) && g.L[1] % (128 / Lx) == 0 && g.L[2] % xline::TZ == 0;
+}
+
+template <int IP, int N>
+__global__ void __launch_bounds__(xline::THREADS) k_conv_line_tc(const __grid_constant__ CUtensorMap tx,
+                                                                 const __grid_constant__ CUtensorMap tw, int O,
+                                                                 const float *__restrict__ bias, Lat g, int sign,
+                                                                 int relu, const bf16 *__restrict__ mask,
+                                                                 bf16 *__restrict__ Yb, float *__restrict__ Yf,
+                                                                 int *__restrict__ err)
+{
+    using namespace gf::tc;
+    using namespace xline;
+    typedef LineLayout<N> LY;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + 40);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr uint32_t idesc = instr_desc(kM, LY::NM);
+    constexpr int NPHASE = (IP / 16) * 3;  // (16-channel chunk, dt slab)
+
+    const int Lx = g.L[0], TYL = 128 / Lx, HY = TYL + 2;
+    const uint32_t line = (uint32_t)Lx * 16;        // bytes of one halo line (8 channels)
+    const uint32_t raw = (uint32_t)(HZ * HY) * line;  // one 8-channel half of the halo t-plane
+    int b = blockIdx.x;
+    const int nby = g.L[1] / TYL, nbz = g.L[2] / TZ;
+    const int y0 = (b % nby) * TYL;
+    b /= nby;
+    const int z0 = (b % nbz) * TZ;
+    const int t0 = b / nbz;
+
+    if (tid == 0) {
+        for (int k = 0; k < 5; ++k) mbar_init(&bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(LY::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    bool fail = false;
+    if (tid == 0) {
+        // the boxes of phase ph into buffer ph & 1: the halo t-plane of the slab (dt = sign (slab - 1))
+        // in padded coordinates (no x ghosts; halo y0 - 1 is padded y0; the plane of channel group
+        // c at t is c Pt + t), one box per 8-channel half, then the slab's weights
+        auto issue = [&](int ph) {
+            const int buf = ph & 1, ch0 = 16 * (ph / 3), slab = ph % 3;
+            const int ht = sign > 0 ? slab : 2 - slab;
+            uint64_t *full = &bar[buf];
+            mbar_expect_tx(full, 2 * raw + (uint32_t)LY::W_BYTES);
+            uint8_t *A = smem + buf * A_BYTES;
+#pragma unroll
+            for (int kc = 0; kc < 2; ++kc)
+                tma_load_4d(A + kc * raw, &tx, 0, y0, z0, (ch0 / 8 + kc) * (g.L[3] + 2) + t0 + ht, full);
+            uint8_t *B = smem + LY::B_OFF + buf * LY::W_BYTES;
+#pragma unroll
+            for (int kc = 0; kc < 2; ++kc) tma_load_3d(B + kc * LY::W_HALF, &tw, 0, 27 * slab, ch0 / 8 + kc, full);
+        };
+        int issued = 0, landed = 0;
+        issue(0);
+        issued = 1;
+        for (int ph = 0; ph < NPHASE; ++ph) {
+            const int nx = ph + 1;
+            if (nx < NPHASE) {
+                // the buffers of phase nx were last read by the MMAs of phase ph - 1
+                if (ph > 0 && !mbar_wait(&bar[2 + ((ph - 1) & 1)], (uint32_t)(((ph - 1) >> 1) & 1))) {
+                    fail = true;
+                    break;
+                }
+                issue(nx);
+                issued = nx + 1;
+            }
+            if (!mbar_wait(&bar[ph & 1], (uint32_t)((ph >> 1) & 1))) {  // the boxes of phase ph have landed
+                fail = true;
+                break;
+            }
+            landed = ph + 1;
+            fence_after_sync();
+            const uint8_t *A = smem + (ph & 1) * A_BYTES;
+            const uint8_t *B = smem + LY::B_OFF + (ph & 1) * LY::W_BYTES;
+            for (int jz = 0; jz < 3; ++jz) {
+                for (int jy = 0; jy < 3; ++jy) {
+                    const int dy = sign * (jy - 1), dz = sign * (jz - 1);
+                    // the slab's taps (jx, jy, jz), jx = 0, 1, 2: 3 N consecutive weight rows
+                    const uint64_t bd = smem_desc(smem_u32(B + (3 * jy + 9 * jz) * N * 16), LY::W_HALF, 128);
+#pragma unroll
+                    for (int zz = 0; zz < TZ; ++zz) {
+                        // first halo line of the tile of plane zz moved by (dy, dz); no x shift
+                        const int l0 = (dy + 1) + HY * (zz + dz + 1);
+                        const uint64_t ad = smem_desc(smem_u32(A + l0 * line), raw, 128);
+                        mma_bf16(tmem + (uint32_t)(zz * LY::PS), ad, bd, idesc, (ph | jy | jz) != 0);
+                    }
+                }
+            }
+            mma_commit(&bar[2 + (ph & 1)]);
+        }
+        // boxes issued but not consumed must land before the CTA ends (bounded)
+        for (int q = landed; q < issued; ++q)
+            if (!mbar_wait(&bar[q & 1], (uint32_t)((q >> 1) & 1))) fail = true;
+        mma_commit(&bar[4]);  // arrives once every MMA issued above is complete
+    }
+    // everyone: all MMAs complete (bounded wait), then the epilogue
+    const bool drained = mbar_wait_idle(&bar[4], 0);
+    fail = __syncthreads_or(fail || !drained);
+    if (!fail) {
+        fence_after_sync();
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 of plane w / 4; row = x + Lx y, and
+        // a warp holds 32 / Lx whole lines
+        const int zz = warp >> 2, row = (warp & 3) * 32 + lane;
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(zz * LY::PS);
+        const int x = row & (Lx - 1), seg = lane & ~(Lx - 1);
+        const int from_left = seg | ((x + Lx - 1) & (Lx - 1)), from_right = seg | ((x + 1) & (Lx - 1));
+        // the column block of input x contributes to output x - dx: tap jx has dx = sign (jx - 1),
+        // so output x takes block 1 - sign from x - 1 and block 1 + sign from x + 1
+        float acc[N], v[N];
+        tmem_load_cols<N>(taddr + (uint32_t)N, acc);
+        tmem_load_cols<N>(taddr + (uint32_t)((1 - sign) * N), v);
+#pragma unroll
+        for (int o = 0; o < N; ++o) acc[o] += __shfl_sync(0xffffffffu, v[o], from_left);
+        tmem_load_cols<N>(taddr + (uint32_t)((1 + sign) * N), v);
+#pragma unroll
+        for (int o = 0; o < N; ++o) acc[o] += __shfl_sync(0xffffffffu, v[o], from_right);
+        // the warp's 32 rows are 32 consecutive sites; the A buffers are free once every MMA has completed
+        const long first = (long)Lx * (y0 + (long)g.L[1] * ((z0 + zz) + (long)g.L[2] * t0)) + (warp & 3) * 32;
+        epilogue_rows<N>(acc, O, bias, relu, mask, Yb, Yf, reinterpret_cast<uint4 *>(smem) + warp * 256, lane,
+                         [&](int r) { return first + r; });
+    } else if (tid == 0) {
+        atomicExch(err, GF_ETIMEOUT);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(LY::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// X [V][I] through the padded copy (no x ghosts) into the x-line kernel; Wblk = the weights blocked by 8 input channels
+template <int IP, int N>
+cudaError_t conv_line_tc(const bf16 *X, int I, const bf16 *Wblk, int O, const float *b, const Lat &g, int sign,
+                         int relu, const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad, cudaStream_t s)
+{
+    typedef LineLayout<N> LY;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_conv_line_tc<IP, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, LY::SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int TYL = 128 / g.L[0];
+    CUtensorMap tx, tw;
+    cudaError_t e = halo_prepare(X, I, Wblk, O, N, g, 0, g.L[0], TYL + 2, xline::HZ, xpad, s, &tx, &tw);
+    if (e != cudaSuccess) return e;
+    const int blocks = (g.L[1] / TYL) * (g.L[2] / xline::TZ) * g.L[3];
+    k_conv_line_tc<IP, N><<<blocks, xline::THREADS, LY::SMEM, s>>>(tx, tw, O, b, g, sign, relu, mask, Yb, Yf, err);
     return cudaGetLastError();
 }
 
@@ -981,6 +1282,7 @@ struct gf_net {
     long np = 0;
     long woff[4], boff[4];
     bf16 *Wb[4] = { nullptr }, *Wt[4] = { nullptr };
+    bf16 *Wh[4] = { nullptr }, *Wth[4] = { nullptr };  // the same, blocked by 8 input channels
     bf16 *act[4] = { nullptr };  // act[1..3] owned; act[0] = caller's features
     float *out = nullptr;
     bf16 *dA = nullptr, *dB = nullptr;  // [V][32] gradient scratch (ping-pong)
@@ -988,7 +1290,7 @@ struct gf_net {
     double *partial = nullptr, *dloss = nullptr;
     int *derr = nullptr;  // tensor-core kernels: bounded-wait expiry
     int use_tc = 1;       // forward and backward-data on tcgen05 (else CUDA cores)
-    int use_halo = 1;     // ... with the halo-tile kernel where the extents allow it
+    int use_halo = 1;     // ... staged by halo: 1 x-line kernel first, 2 halo-tile kernel only, 0 neither
     int step = 0;
     std::string err;
 };
@@ -1020,20 +1322,25 @@ static int refresh_weights(gf_net *n)
     for (int l = 0; l < 4; ++l) {
         long cnt = 81L * kC[l + 1] * kC[l];
         k_cast_weights<<<(int)((cnt + 255) / 256), 256, 0, n->stream>>>(n->params + n->woff[l], kC[l], kC[l + 1],
-                                                                          n->Wb[l], n->Wt[l]);
+                                                                          n->Wb[l], n->Wt[l], n->Wh[l],
+                                                                          n->Wth[l]);
         NCK(cudaGetLastError());
     }
     return GF_OK;
 }
 
-// forward / backward-data convolution on the tensor cores: the halo-tile kernel
-// when selected and the extents allow it, else the per-tap gather kernel
+// forward / backward-data convolution on the tensor cores: with conv_halo 1 the
+// x-line kernel, else (or with conv_halo 2) the halo-tile kernel, where the
+// extents allow them; otherwise the per-tap gather kernel
+// (W = weights [81][O][I], Wblk = the same blocked by 8 input channels)
 template <int IP, int N>
-static cudaError_t conv_tensor(const gf_net *n, const bf16 *X, int I, const bf16 *W, int O, const float *b, int sign,
-                               int relu, const bf16 *mask, bf16 *Yb, float *Yf)
+static cudaError_t conv_tensor(const gf_net *n, const bf16 *X, int I, const bf16 *W, const bf16 *Wblk, int O,
+                               const float *b, int sign, int relu, const bf16 *mask, bf16 *Yb, float *Yf)
 {
-    if (n->use_halo && halo_ok(n->g))
-        return conv_halo_tc<IP, N>(X, I, W, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->xpad, n->stream);
+    if (n->use_halo == 1 && line_ok(n->g))
+        return conv_line_tc<IP, N>(X, I, Wblk, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->xpad, n->stream);
+    if (n->use_halo != 0 && halo_ok(n->g))
+        return conv_halo_tc<IP, N>(X, I, Wblk, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->xpad, n->stream);
     return conv_tc<IP, N>(X, I, W, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->stream);
 }
 
@@ -1043,13 +1350,14 @@ static int forward(gf_net *n, const bf16 *f)
     cudaStream_t s = n->stream;
     n->act[0] = const_cast<bf16 *>(f);
     if (n->use_tc) {
-        NCK((conv_tensor<80, 32>(n, f, 80, n->Wb[0], 32, n->params + n->boff[0], 1, 1, nullptr, n->act[1], nullptr)));
-        NCK((conv_tensor<32, 32>(n, n->act[1], 32, n->Wb[1], 32, n->params + n->boff[1], 1, 1, nullptr, n->act[2],
+        NCK((conv_tensor<80, 32>(n, f, 80, n->Wb[0], n->Wh[0], 32, n->params + n->boff[0], 1, 1, nullptr, n->act[1],
                                  nullptr)));
-        NCK((conv_tensor<32, 32>(n, n->act[2], 32, n->Wb[2], 32, n->params + n->boff[2], 1, 1, nullptr, n->act[3],
-                                 nullptr)));
-        NCK((conv_tensor<32, 16>(n, n->act[3], 32, n->Wb[3], 8, n->params + n->boff[3], 1, 0, nullptr, nullptr,
-                                 n->out)));
+        NCK((conv_tensor<32, 32>(n, n->act[1], 32, n->Wb[1], n->Wh[1], 32, n->params + n->boff[1], 1, 1, nullptr,
+                                 n->act[2], nullptr)));
+        NCK((conv_tensor<32, 32>(n, n->act[2], 32, n->Wb[2], n->Wh[2], 32, n->params + n->boff[2], 1, 1, nullptr,
+                                 n->act[3], nullptr)));
+        NCK((conv_tensor<32, 16>(n, n->act[3], 32, n->Wb[3], n->Wh[3], 8, n->params + n->boff[3], 1, 0, nullptr,
+                                 nullptr, n->out)));
         return GF_OK;
     }
     NCK((conv_cc<80, 32>(f, n->Wb[0], n->params + n->boff[0], g, 1, 1, nullptr, n->act[1], nullptr, s)));
@@ -1065,10 +1373,12 @@ static int backward_data(gf_net *n, int l, const bf16 *dY, bf16 *dX)
     const Lat &g = n->g;
     cudaStream_t s = n->stream;
     if (l == 3) {
-        if (n->use_tc) NCK((conv_tensor<16, 32>(n, dY, 8, n->Wt[3], 32, nullptr, -1, 0, n->act[3], dX, nullptr)));
+        if (n->use_tc)
+            NCK((conv_tensor<16, 32>(n, dY, 8, n->Wt[3], n->Wth[3], 32, nullptr, -1, 0, n->act[3], dX, nullptr)));
         else NCK((conv_cc<8, 32>(dY, n->Wt[3], nullptr, g, -1, 0, n->act[3], dX, nullptr, s)));
     } else {
-        if (n->use_tc) NCK((conv_tensor<32, 32>(n, dY, 32, n->Wt[l], 32, nullptr, -1, 0, n->act[l], dX, nullptr)));
+        if (n->use_tc)
+            NCK((conv_tensor<32, 32>(n, dY, 32, n->Wt[l], n->Wth[l], 32, nullptr, -1, 0, n->act[l], dX, nullptr)));
         else NCK((conv_cc<32, 32>(dY, n->Wt[l], nullptr, g, -1, 0, n->act[l], dX, nullptr, s)));
     }
     return GF_OK;
@@ -1165,12 +1475,14 @@ static int ensure_buffers(gf_net *n)
         long cnt = 81L * kC[l + 1] * kC[l];
         NCK(cudaMalloc(&n->Wb[l], sizeof(bf16) * cnt));
         NCK(cudaMalloc(&n->Wt[l], sizeof(bf16) * cnt));
+        NCK(cudaMalloc(&n->Wh[l], sizeof(bf16) * cnt));
+        NCK(cudaMalloc(&n->Wth[l], sizeof(bf16) * cnt));
     }
     for (int l = 1; l < 4; ++l) NCK(cudaMalloc(&n->act[l], sizeof(bf16) * V * 32));
     NCK(cudaMalloc(&n->out, sizeof(float) * V * 8));
     NCK(cudaMalloc(&n->dA, sizeof(bf16) * V * 32));
     NCK(cudaMalloc(&n->dB, sizeof(bf16) * V * 32));
-    if (halo_ok(n->g)) NCK(cudaMalloc(&n->xpad, sizeof(bf16) * padded_sites(n->g) * GF_NET_CIN));
+    if (halo_ok(n->g) || line_ok(n->g)) NCK(cudaMalloc(&n->xpad, sizeof(bf16) * padded_sites(n->g) * GF_NET_CIN));
     NCK(cudaMalloc(&n->partial, sizeof(double) * 1024));
     NCK(cudaMalloc(&n->dloss, sizeof(double)));
     NCK(cudaMalloc(&n->derr, sizeof(int)));
@@ -1188,6 +1500,8 @@ int gf_net_destroy(gf_net *n)
     for (int l = 0; l < 4; ++l) {
         cudaFree(n->Wb[l]);
         cudaFree(n->Wt[l]);
+        cudaFree(n->Wh[l]);
+        cudaFree(n->Wth[l]);
     }
     for (int l = 1; l < 4; ++l) cudaFree(n->act[l]);
     cudaFree(n->out);
@@ -1253,7 +1567,8 @@ int gf_net_set_option(gf_net *n, const char *key, double value)
         return GF_OK;
     }
     if (std::string(key) == "conv_halo") {
-        n->use_halo = value != 0.0;
+        if (value != 0.0 && value != 1.0 && value != 2.0) return nfail(n, GF_EINVAL, "conv_halo is 0, 1 or 2");
+        n->use_halo = (int)value;
         return GF_OK;
     }
     return nfail(n, GF_EINVAL, std::string("unknown option ") + key);

@@ -188,8 +188,14 @@ def exact_network(dims, seed, nnz=(12, 6, 3, 6)):
     return np.concatenate(flat).astype(np.float32), X0, target, acts[4]
 
 
-@pytest.mark.parametrize("dims", [(8, 16, 4, 4), (16, 32, 4, 4), (6, 4, 6, 10)])
-@pytest.mark.parametrize("path", ["gather", "halo", "cuda_cores"])
+# net option conv_halo of each convolution path: 1 = x-line kernel where Lx is
+# 8, 16 or 32, 2 = halo-tile kernel (Lx % 8, Ly % 16, Lz % 2), both falling back
+# to the per-tap gather kernel (0) where the extents do not allow them
+CONV_HALO = {"gather": 0, "xline": 1, "halo_tile": 2, "cuda_cores": 0}
+
+
+@pytest.mark.parametrize("dims", [(8, 16, 4, 4), (16, 32, 4, 4), (32, 4, 4, 3), (6, 4, 6, 10)])
+@pytest.mark.parametrize("path", ["gather", "xline", "halo_tile", "cuda_cores"])
 def test_network_exact_arithmetic_matches_oracle_bit_for_bit(dims, path):
     params, X0, target, out_exact = exact_network(dims, seed=sum(dims))
     V = int(np.prod(dims))
@@ -198,7 +204,7 @@ def test_network_exact_arithmetic_matches_oracle_bit_for_bit(dims, path):
     assert np.array_equal(grad_o.astype(np.float32).astype(np.float64), grad_o)  # exact in FP32
     net = gf.gf_net_create(dims)
     gf.gf_net_set_option(net, "tensor_cores", 0 if path == "cuda_cores" else 1)
-    gf.gf_net_set_option(net, "conv_halo", 1 if path == "halo" else 0)
+    gf.gf_net_set_option(net, "conv_halo", CONV_HALO[path])
     gf.gf_net_set_params(net, params)
     fd = torch.from_numpy(X0.astype(np.float32)).to(torch.bfloat16).cuda()
     td = torch.from_numpy(target.astype(np.float32)).cuda()
@@ -232,8 +238,8 @@ def forward_error_sigma(X0, Ws, bs, dims):
         VarE = VarD * (Y > 0) + (2.0 ** -7 * X) ** 2 / 12.0
 
 
-@pytest.mark.parametrize("dims", [(8, 16, 4, 4), (6, 4, 6, 10)])
-@pytest.mark.parametrize("path", ["gather", "halo", "cuda_cores"])
+@pytest.mark.parametrize("dims", [(8, 16, 4, 4), (32, 4, 4, 3), (6, 4, 6, 10)])
+@pytest.mark.parametrize("path", ["gather", "xline", "halo_tile", "cuda_cores"])
 def test_network_forward_within_rounding_bound_elementwise(dims, path):
     V = int(np.prod(dims))
     rng = np.random.default_rng(7)
@@ -250,7 +256,7 @@ def test_network_forward_within_rounding_bound_elementwise(dims, path):
     D = 8.0 * sigma + 1e-7 * np.abs(Y)
     net = gf.gf_net_create(dims)
     gf.gf_net_set_option(net, "tensor_cores", 0 if path == "cuda_cores" else 1)
-    gf.gf_net_set_option(net, "conv_halo", 1 if path == "halo" else 0)
+    gf.gf_net_set_option(net, "conv_halo", CONV_HALO[path])
     gf.gf_net_set_params(net, params)
     out = torch.empty(V, 8, dtype=torch.float32, device="cuda")
     gf.gf_net_forward(net, torch.from_numpy(X0.astype(np.float32)).to(torch.bfloat16).cuda(), out)
