@@ -1237,6 +1237,275 @@ __global__ void k_bias_grad(const bf16 *__restrict__ dY, int O, int V, float *__
     if (threadIdx.x < O) atomicAdd(&db[threadIdx.x], acc[threadIdx.x]);
 }
 
+// ---------------------------------------------------------------------------
+// weight gradient on the tensor cores, x-line form (Lx in {8, 16, 32},
+// Ly % (128 / Lx) == 0).  With the x part of a tap moved onto dY,
+//
+//   dW[k][o][i] = sum_s X[s + (0, dy, dz, dt)][i] dY[s - (dx, 0, 0, 0)][o],
+//
+// the GEMM D[(dz, i)][(dx, o)] = sum_s A[(dz, i)][s] B[(dx, o)][s], one per
+// (dy, dt), gives the taps k = (dx+1) + 3 (dy+1) + 9 (dz+1) + 27 (dt+1).  The
+// site sum is the MMA's K dimension and both operands are MN-major: in the
+// ghost-padded copies, blocked by 8 channels, a run of sites along x with its
+// 8 channels is already a column of 8-site x 16-byte core matrices, so TMA
+// boxes land in shared memory as operands without a transpose.  A stage is
+// 128 sites, 128 / Lx whole x lines at one (z, t):
+// - A: one 5D box of the X copy per stage: channel groups g0 .. g0 + CH - 1,
+//   z - 1 .. z + 1, the lines y0 - 1 .. y0 + 128 / Lx at t + dt.  Slot
+//   3 (g - g0) + (dz + 1) of the box is one M column of 8 channels, the slots
+//   at a uniform stride, and the MMA of tap row dy reads each slot from its
+//   line dy + 1 on: a view that starts on a whole line.  So one box serves the
+//   3 dy x 3 dz taps of 3 CH M columns (CH = 4 of 4 groups, or 5 of 10).
+// - B: one box per dx, dY at x - dx from the copy with x ghosts, all output
+//   groups: N = 3 O columns (padded to a multiple of 32).
+// A stage issues 3 x 8 MMAs of K = 16 (dy, K step) into 3 accumulators.  Each
+// CTA takes one (dt, channel chunk) and every R-th stage from its first, so the
+// CTAs move through the lattice together and the planes they read stay in L2;
+// it adds its accumulators into dW (FP32 atomics) at the end.  Roles: warp 4
+// issues the boxes into a ring of STAGES buffers, warp 5 the MMAs, warps 0-3
+// read the accumulators (warp w: TMEM lanes 32 w .. 32 w + 31).  Every wait is
+// bounded.
+// ---------------------------------------------------------------------------
+namespace dwline {
+constexpr int STAGES = 3;
+constexpr int SLOT_MAX = 3072;            // one M column: 128 / Lx + 2 lines of Lx sites x 16 bytes (Lx = 32)
+constexpr int A_BYTES = 16 * SLOT_MAX;    // 16 M columns of an MMA (only 3 CH <= 15 are loaded)
+constexpr int B_BOX = 128 * 16;           // 128 sites x 8 channels
+constexpr int THREADS = 192;
+}  // namespace dwline
+
+template <int NP>  // accumulator columns per tap row: 3 x output channels, padded to a multiple of 32
+struct DwLineLayout {
+    static_assert(NP % 32 == 0 && NP <= 128, "accumulator read in blocks of 32 columns");
+    static constexpr int B_BYTES = (NP / 8) * dwline::B_BOX;
+    static constexpr int STAGE = dwline::A_BYTES + B_BYTES;
+    // bar[0..S-1] boxes landed, bar[S..2S-1] MMAs done with the buffer, bar[2S] accumulators final,
+    // bar[2S+1] drain
+    static constexpr int NBAR = 2 * dwline::STAGES + 2;
+    static constexpr int BAR_OFF = dwline::STAGES * STAGE;
+    static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16;
+    static constexpr int TMEM_COLS = 3 * NP <= 128 ? 128 : (3 * NP <= 256 ? 256 : 512);
+};
+
+static bool dw_line_ok(const Lat &g)
+{
+    const int Lx = g.L[0];
+    return (Lx == 8 || Lx == 16 || Lx == 32) && g.L[1] % (128 / Lx) == 0;
+}
+
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(gf::tc::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(gf::tc::smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory descriptor of an MN-major operand without swizzle: core
+// matrices of 8 K-rows x 16 bytes (8 MN elements), lbo = byte offset between
+// core matrices adjacent in K, sbo = between core matrices adjacent in M or N.
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr, uint32_t lbo_k, uint32_t sbo_mn)
+{
+    return gf::tc::smem_desc(addr, lbo_k, sbo_mn);
+}
+
+// grid = 3 * nchunk * R CTAs: CTA b has dt = b / (nchunk R) - 1, channel chunk (b / R) % nchunk, member b % R
+template <int NP>
+__global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __grid_constant__ CUtensorMap tx,
+                                                                     const __grid_constant__ CUtensorMap ty, int I,
+                                                                     int O, int CH, Lat g, float *__restrict__ dW,
+                                                                     int *__restrict__ err)
+{
+    using namespace gf::tc;
+    using dwline::B_BOX;
+    typedef DwLineLayout<NP> LY;
+    constexpr int S = dwline::STAGES;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);
+    uint64_t *acc_done = &bar[2 * S], *drain = &bar[2 * S + 1];
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + LY::NBAR * 8);
+    int *consumed_sh = reinterpret_cast<int *>(smem + LY::BAR_OFF + LY::NBAR * 8 + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // kind::f16, D = F32, A = B = BF16, both operands MN-major (bits 15, 16)
+    constexpr uint32_t idesc = instr_desc(kM, NP) | (1u << 15) | (1u << 16);
+    const int G = I / 8, OG = O / 8, Lx = g.L[0], TYL = 128 / Lx, nby = g.L[1] / TYL;
+    const uint32_t line = (uint32_t)Lx * 16, slot = (uint32_t)(TYL + 2) * line;
+    const int nchunk = (G + CH - 1) / CH, R = gridDim.x / (3 * nchunk);
+    const int type = blockIdx.x / R, member = blockIdx.x - type * R;
+    const int dti = type / nchunk, g0 = (type - dti * nchunk) * CH, nch = min(CH, G - g0);
+    const int NS = g.V / 128;
+    const int n = member < NS ? (NS - member + R - 1) / R : 0;  // stages member, member + R, ...
+
+    // M columns beyond 3 nch and the N padding stay zero
+    for (int e = tid; e < LY::BAR_OFF / 16; e += dwline::THREADS)
+        reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
+    fence_proxy_async();
+    if (tid == 0) {
+        for (int k = 0; k < LY::NBAR; ++k) mbar_init(&bar[k], 1);
+        *consumed_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(LY::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    bool fail = false;
+    int issued = 0;
+    if (warp == 4 && lane == 0) {
+        // producer: the boxes of stage p into buffer p % S once the MMAs of stage p - S are done
+        const uint32_t bytes = (uint32_t)(3 * nch) * slot + (uint32_t)(3 * OG) * B_BOX;
+        for (int p = 0; p < n; ++p) {
+            const int b = p % S;
+            if (p >= S && !mbar_wait(&bar[S + b], (uint32_t)((p / S - 1) & 1))) {
+                fail = true;
+                break;
+            }
+            const int st = member + p * R;
+            const int y0 = (st % nby) * TYL, zt = st / nby, z = zt % g.L[2], t = zt / g.L[2];
+            uint8_t *A = smem + b * LY::STAGE;
+            uint8_t *B = A + dwline::A_BYTES;
+            mbar_expect_tx(&bar[b], bytes);
+            // padded coordinates: lines y0 - 1 .. (padded y0), planes z - 1 .. z + 1 (padded z), t + dt
+            tma_load_5d(A, &tx, 0, y0, z, t + dti, g0, &bar[b]);
+            // dY at x - dx: padded x from 1 - dx, dx = dxi - 1
+            for (int dxi = 0; dxi < 3; ++dxi)
+                tma_load_5d(B + dxi * OG * B_BOX, &ty, 8 * (2 - dxi), y0 + 1, z + 1, t + 1, 0, &bar[b]);
+            issued = p + 1;
+        }
+    } else if (warp == 5 && lane == 0) {
+        // MMA issuer: accumulator dyi = tap row dy = dyi - 1, at columns dyi NP
+        int consumed = 0;
+        for (int p = 0; p < n; ++p) {
+            if (!mbar_wait(&bar[p % S], (uint32_t)((p / S) & 1))) {
+                fail = true;
+                break;
+            }
+            consumed = p + 1;
+            fence_after_sync();
+            const uint32_t A = smem_u32(smem + (p % S) * LY::STAGE);
+            const uint32_t B = A + dwline::A_BYTES;
+#pragma unroll
+            for (int dyi = 0; dyi < 3; ++dyi)
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk)
+                    mma_bf16(tmem + (uint32_t)(dyi * NP), smem_desc_mn(A + dyi * line + kk * 256, 128, slot),
+                             smem_desc_mn(B + kk * 256, 128, B_BOX), idesc, (p | kk) != 0);
+            mma_commit(&bar[S + p % S]);
+        }
+        *consumed_sh = consumed;
+        if (!fail && n > 0) mma_commit(acc_done);
+        mma_commit(drain);
+        if (!mbar_wait(drain, 0)) fail = true;
+    } else if (warp < 4 && n > 0) {
+        // row 32 w + lane = M column m = 3 (g - g0) + (dz + 1), channel i = 8 g + (row % 8)
+        const int row = 32 * warp + lane, m = row >> 3, gl = m / 3, dzi = m - 3 * gl;
+        const int i = 8 * (g0 + gl) + (row & 7);
+        if (!mbar_wait_idle(acc_done, 0)) {
+            fail = true;
+        } else {
+            fence_after_sync();
+#pragma unroll 1
+            for (int dyi = 0; dyi < 3; ++dyi) {
+                const int k0 = 3 * dyi + 9 * dzi + 27 * dti;  // tap of dx = -1
+#pragma unroll 1
+                for (int c0 = 0; c0 < NP; c0 += 32) {
+                    float v[32];
+                    tmem_load_cols<32>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(dyi * NP + c0), v);
+                    if (gl < nch) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const int col = c0 + c;  // (dx + 1) O + o
+                            if (col < 3 * O) {
+                                const int dxi = col / O, o = col - dxi * O;
+                                atomicAdd(&dW[((long)(k0 + dxi) * O + o) * I + i], v[c]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    fail = __syncthreads_or(fail);
+    if (fail) {
+        if (tid == 0) atomicExch(err, GF_ETIMEOUT);
+        // boxes issued but not consumed land before the buffers go away (bounded)
+        if (warp == 4 && lane == 0)
+            for (int p = *consumed_sh; p < issued; ++p) mbar_wait(&bar[p % S], (uint32_t)((p / S) & 1));
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(LY::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// dW and db of one layer through the x-line weight-gradient kernel: X [V][I] is
+// padded without x ghosts into xpad, dY [V][O] with them into ypad
+template <int NP>
+cudaError_t conv_dw_line_tc(const bf16 *dY, int O, const bf16 *X, int I, const Lat &g, float *dW, float *db,
+                            int *err, bf16 *xpad, bf16 *ypad, cudaStream_t s)
+{
+    typedef DwLineLayout<NP> LY;
+    static bool configured = false;
+    static int nsm = 0;
+    cudaError_t e;
+    if (!configured) {
+        e = cudaFuncSetAttribute(k_conv_dw_line_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, LY::SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        configured = true;
+    }
+    const EncodeTiledFn enc = encode_tiled();
+    const int G = I / 8, OG = O / 8;
+    if (!enc || !xpad || !ypad || I % 8 || O % 8 || 3 * O > NP) return cudaErrorNotSupported;
+    // channel groups per chunk: the largest divisor of G with 3 CH <= 15 M columns
+    int CH = 1;
+    for (int d = 1; d <= 5; ++d)
+        if (G % d == 0) CH = d;
+    const int Lx = g.L[0], TYL = 128 / Lx;
+    const long px = padded_sites(g, 0), py = padded_sites(g, 1);
+    k_pad_periodic<<<(int)std::min<long>((px + 255) / 256, 152L * 32), 256, 0, s>>>(X, I, g, 0, xpad);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_pad_periodic<<<(int)std::min<long>((py + 255) / 256, 152L * 32), 256, 0, s>>>(dY, O, g, 1, ypad);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const cuuint64_t es = sizeof(bf16);
+    const cuuint64_t Py = g.L[1] + 2, Pz = g.L[2] + 2, Pt = g.L[3] + 2;
+    const cuuint32_t ones[5] = { 1, 1, 1, 1, 1 };
+    CUtensorMap tmap[2];
+    for (int which = 0; which < 2; ++which) {  // 0: X (no x ghosts), 1: dY (x ghosts)
+        const cuuint64_t Px = Lx + 2 * which, groups = (cuuint64_t)(which ? OG : G);
+        const cuuint64_t dim[5] = { 8 * Px, Py, Pz, Pt, groups };
+        const cuuint64_t str[4] = { 8 * es * Px, 8 * es * Px * Py, 8 * es * Px * Py * Pz,
+                                    8 * es * Px * Py * Pz * Pt };
+        const cuuint32_t box[5] = { (cuuint32_t)(8 * Lx), (cuuint32_t)(which ? TYL : TYL + 2), which ? 1u : 3u, 1,
+                                    (cuuint32_t)(which ? OG : CH) };
+        if (enc(&tmap[which], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, which ? ypad : xpad, dim, str, box, ones,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    const int NT = 3 * ((G + CH - 1) / CH);
+    const int NS = g.V / 128;
+    const int R = std::max(1, std::min(nsm / NT, NS));
+    k_conv_dw_line_tc<NP><<<NT * R, dwline::THREADS, LY::SMEM, s>>>(tmap[0], tmap[1], I, O, CH, g, dW, err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_bias_grad<<<256, 256, 0, s>>>(dY, O, g.V, db);
+    return cudaGetLastError();
+}
+
 template <int IP, int N>
 cudaError_t conv_dw_tc(const bf16 *dY, int O, const bf16 *X, int I, const Lat &g, float *dW, float *db, int *err,
                        cudaStream_t s)
@@ -1287,6 +1556,7 @@ struct gf_net {
     float *out = nullptr;
     bf16 *dA = nullptr, *dB = nullptr;  // [V][32] gradient scratch (ping-pong)
     bf16 *xpad = nullptr;  // halo-tile convolutions: the input with periodic ghost sites, up to 80 channels
+    bf16 *ypad = nullptr;  // x-line weight gradients: dY with periodic ghost sites, up to 32 channels
     double *partial = nullptr, *dloss = nullptr;
     int *derr = nullptr;  // tensor-core kernels: bounded-wait expiry
     int use_tc = 1;       // forward and backward-data on tcgen05 (else CUDA cores)
@@ -1342,6 +1612,18 @@ static cudaError_t conv_tensor(const gf_net *n, const bf16 *X, int I, const bf16
     if (n->use_halo != 0 && halo_ok(n->g))
         return conv_halo_tc<IP, N>(X, I, Wblk, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->xpad, n->stream);
     return conv_tc<IP, N>(X, I, W, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->stream);
+}
+
+// weight and bias gradients of one layer on the tensor cores: with conv_halo 1
+// the x-line kernel where the extents allow it, otherwise the gather kernel
+template <int IP, int N>
+static cudaError_t dw_tensor(const gf_net *n, const bf16 *dY, int O, const bf16 *X, int I, float *dW, float *db)
+{
+    if (n->use_halo == 1 && n->ypad && dw_line_ok(n->g)) {
+        if (O <= 8) return conv_dw_line_tc<32>(dY, O, X, I, n->g, dW, db, n->derr, n->xpad, n->ypad, n->stream);
+        return conv_dw_line_tc<96>(dY, O, X, I, n->g, dW, db, n->derr, n->xpad, n->ypad, n->stream);
+    }
+    return conv_dw_tc<IP, N>(dY, O, X, I, n->g, dW, db, n->derr, n->stream);
 }
 
 static int forward(gf_net *n, const bf16 *f)
@@ -1411,22 +1693,22 @@ static int backward(gf_net *n, const bf16 *f, const float *target)
     NCK(cudaGetLastError());
     NCK(cudaMemsetAsync(n->grad, 0, sizeof(float) * n->np, s));
     // layer 4: dY = dA [V][8]
-    if (n->use_tc) NCK((conv_dw_tc<32, 16>(n->dA, 8, n->act[3], 32, g, n->grad + n->woff[3], n->grad + n->boff[3], n->derr, s)));
+    if (n->use_tc) NCK((dw_tensor<32, 16>(n, n->dA, 8, n->act[3], 32, n->grad + n->woff[3], n->grad + n->boff[3])));
     else NCK((conv_dw<32, 8>(n->dA, n->act[3], g, n->grad + n->woff[3], n->grad + n->boff[3], s)));
     r = backward_data(n, 3, n->dA, n->dB);
     if (r != GF_OK) return r;
     // layer 3
-    if (n->use_tc) NCK((conv_dw_tc<32, 32>(n->dB, 32, n->act[2], 32, g, n->grad + n->woff[2], n->grad + n->boff[2], n->derr, s)));
+    if (n->use_tc) NCK((dw_tensor<32, 32>(n, n->dB, 32, n->act[2], 32, n->grad + n->woff[2], n->grad + n->boff[2])));
     else NCK((conv_dw<32, 32>(n->dB, n->act[2], g, n->grad + n->woff[2], n->grad + n->boff[2], s)));
     r = backward_data(n, 2, n->dB, n->dA);
     if (r != GF_OK) return r;
     // layer 2
-    if (n->use_tc) NCK((conv_dw_tc<32, 32>(n->dA, 32, n->act[1], 32, g, n->grad + n->woff[1], n->grad + n->boff[1], n->derr, s)));
+    if (n->use_tc) NCK((dw_tensor<32, 32>(n, n->dA, 32, n->act[1], 32, n->grad + n->woff[1], n->grad + n->boff[1])));
     else NCK((conv_dw<32, 32>(n->dA, n->act[1], g, n->grad + n->woff[1], n->grad + n->boff[1], s)));
     r = backward_data(n, 1, n->dA, n->dB);
     if (r != GF_OK) return r;
     // layer 1 (no input gradient needed)
-    if (n->use_tc) NCK((conv_dw_tc<128, 32>(n->dB, 32, f, 80, g, n->grad + n->woff[0], n->grad + n->boff[0], n->derr, s)));
+    if (n->use_tc) NCK((dw_tensor<128, 32>(n, n->dB, 32, f, 80, n->grad + n->woff[0], n->grad + n->boff[0])));
     else NCK((conv_dw<80, 32>(n->dB, f, g, n->grad + n->woff[0], n->grad + n->boff[0], s)));
     return GF_OK;
 }
@@ -1482,7 +1764,9 @@ static int ensure_buffers(gf_net *n)
     NCK(cudaMalloc(&n->out, sizeof(float) * V * 8));
     NCK(cudaMalloc(&n->dA, sizeof(bf16) * V * 32));
     NCK(cudaMalloc(&n->dB, sizeof(bf16) * V * 32));
-    if (halo_ok(n->g) || line_ok(n->g)) NCK(cudaMalloc(&n->xpad, sizeof(bf16) * padded_sites(n->g) * GF_NET_CIN));
+    if (halo_ok(n->g) || line_ok(n->g) || dw_line_ok(n->g))
+        NCK(cudaMalloc(&n->xpad, sizeof(bf16) * padded_sites(n->g) * GF_NET_CIN));
+    if (dw_line_ok(n->g)) NCK(cudaMalloc(&n->ypad, sizeof(bf16) * padded_sites(n->g) * 32));
     NCK(cudaMalloc(&n->partial, sizeof(double) * 1024));
     NCK(cudaMalloc(&n->dloss, sizeof(double)));
     NCK(cudaMalloc(&n->derr, sizeof(int)));
@@ -1508,6 +1792,7 @@ int gf_net_destroy(gf_net *n)
     cudaFree(n->dA);
     cudaFree(n->dB);
     cudaFree(n->xpad);
+    cudaFree(n->ypad);
     cudaFree(n->partial);
     cudaFree(n->dloss);
     cudaFree(n->derr);

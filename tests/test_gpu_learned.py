@@ -11,10 +11,12 @@ compared with the FP64 oracle in two ways:
   steps are then all exact, so any wrong tap, channel, site, wrap or mask
   shows up as a difference.  The test asserts that precondition on the
   oracle's own intermediate values before it compares.  Lattices: 8x16x4x4
-  and 16x32x4x4 (periodic wrap inside one halo tile, several tiles), and the
-  ragged 6x4x6x10 (1440 sites, not a multiple of the 128-site tile), each
-  with the per-tap gather kernels, the halo-tile kernels and the CUDA-core
-  kernels;
+  and 16x32x4x4 (periodic wrap inside one halo tile, several tiles),
+  32x4x4x3, the ragged 6x4x6x10 (1440 sites, not a multiple of the 128-site
+  tile) and 16x16x8x8 (where each CTA of the x-line weight-gradient kernel
+  runs several stages through its buffer ring and crosses from one group of
+  taps to the next), each with the per-tap gather kernels, the x-line and
+  halo-tile kernels and the CUDA-core kernels;
 - element by element on random weights, within 8 standard deviations of
   the rounding error, which is propagated through the layers from the
   arithmetic: the BF16 rounding of every stored activation and the FP32
@@ -194,7 +196,7 @@ def exact_network(dims, seed, nnz=(12, 6, 3, 6)):
 CONV_HALO = {"gather": 0, "xline": 1, "halo_tile": 2, "cuda_cores": 0}
 
 
-@pytest.mark.parametrize("dims", [(8, 16, 4, 4), (16, 32, 4, 4), (32, 4, 4, 3), (6, 4, 6, 10)])
+@pytest.mark.parametrize("dims", [(8, 16, 4, 4), (16, 32, 4, 4), (32, 4, 4, 3), (6, 4, 6, 10), (16, 16, 8, 8)])
 @pytest.mark.parametrize("path", ["gather", "xline", "halo_tile", "cuda_cores"])
 def test_network_exact_arithmetic_matches_oracle_bit_for_bit(dims, path):
     params, X0, target, out_exact = exact_network(dims, seed=sum(dims))
