@@ -427,11 +427,12 @@ def gpu_arm(args, rank, world, local):
     e2e_ms = max_over_ranks(e2e_ms, world)
     e2e_value = world * V * e2e_sweeps / (e2e_ms / 1e3)
 
-    # DRAM bytes (read + write) per launch of the FP64 phase's half-sweep from one ncu capture
-    # (profiles/or_half_sweep_fp64_18_32x32x32x32.md): valid for the configuration captured there,
-    # the accumulate form with 128 registers per thread near convergence; null for any other
-    acc = gf.gf_get_stat(ctx, "accumulate_form") == 1 and gf.gf_get_stat(ctx, "acc_registers") == 128
-    traffic64 = 1554.9e6 if acc else None
+    # DRAM bytes (read + write) per launch of the FP64 phase's half-sweep from ncu captures
+    # (profiles/or_half_sweep_fp64_18_32x32x32x32.md): valid for the configurations captured there,
+    # the accumulate form near convergence with each register budget at block 128; null for any other
+    acc = gf.gf_get_stat(ctx, "accumulate_form") == 1
+    traffic64 = {255: 1169.9e6, 168: 1335.4e6, 128: 1495.8e6}.get(
+        int(gf.gf_get_stat(ctx, "acc_registers"))) if acc else None
     pk = peaks()
     hbm = pk.get("hbm_gbs")
     # dominant kernel of the step: the half-sweep of the phase whose kernels took longer; its

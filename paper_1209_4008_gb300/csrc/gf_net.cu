@@ -50,6 +50,13 @@ __device__ __forceinline__ int shift_site(const Lat &g, int s, int k, int sign)
     return c0 + g.L[0] * (c1 + g.L[1] * (c2 + g.L[2] * c3));
 }
 
+// two floats rounded to BF16, packed low | high
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
 // ---------------------------------------------------------------------------
 // convolution on CUDA cores: Y[s][o] = b[o] + sum_k sum_i Wk[k][o][i] X[s + sign d(k)][i]
 // 256 threads: SITES sites x (O / 8) output groups of 8 outputs each.
@@ -167,11 +174,20 @@ __global__ void __launch_bounds__(256) k_conv_dw(const bf16 *__restrict__ dY, co
 __global__ void k_mse(const float *__restrict__ out, const float *__restrict__ t, long n, float inv_n,
                       bf16 *__restrict__ dout, double *__restrict__ partial)
 {
+    // four elements per step (n is a multiple of 8: 8 outputs per site)
     double acc = 0.0;
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-        float d = out[e] - t[e];
-        acc += (double)d * d;
-        dout[e] = __float2bfloat16(2.0f * d * inv_n);
+    const long n4 = n / 4;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += (long)gridDim.x * blockDim.x) {
+        const float4 o = reinterpret_cast<const float4 *>(out)[e], y = reinterpret_cast<const float4 *>(t)[e];
+        const float d0 = o.x - y.x, d1 = o.y - y.y, d2 = o.z - y.z, d3 = o.w - y.w;
+        acc = fma((double)d0, (double)d0, acc);
+        acc = fma((double)d1, (double)d1, acc);
+        acc = fma((double)d2, (double)d2, acc);
+        acc = fma((double)d3, (double)d3, acc);
+        uint2 g;
+        g.x = pack_bf16x2(2.0f * d0 * inv_n, 2.0f * d1 * inv_n);
+        g.y = pack_bf16x2(2.0f * d2 * inv_n, 2.0f * d3 * inv_n);
+        reinterpret_cast<uint2 *>(dout)[e] = g;
     }
     __shared__ double red[256];
     red[threadIdx.x] = acc;
@@ -183,13 +199,13 @@ __global__ void k_mse(const float *__restrict__ out, const float *__restrict__ t
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
+// one warp, fixed order: lane l sums partials l, l + 32, ..., then a shuffle tree
 __global__ void k_sum_partials(const double *p, int n, double scale, double *out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += p[i];
-        *out = s * scale;
-    }
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) s += p[i];
+    for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+    if (threadIdx.x == 0) *out = s * scale;
 }
 
 // Adam on the FP32 master parameters, then BF16 copies W[k][o][i] and Wt[k][i][o]
@@ -583,12 +599,6 @@ __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float *v)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int o = 0; o < N; ++o) v[o] = __uint_as_float(r[o]);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
-{
-    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&h);
 }
 
 // The epilogue of one warp's 32 accumulator rows (row r of the warp is the
@@ -1261,7 +1271,9 @@ __global__ void k_bias_grad(const bf16 *__restrict__ dY, int O, int V, float *__
 // A stage issues 3 x 8 MMAs of K = 16 (dy, K step) into 3 accumulators.  Each
 // CTA takes one (dt, channel chunk) and every R-th stage from its first, so the
 // CTAs move through the lattice together and the planes they read stay in L2;
-// it adds its accumulators into dW (FP32 atomics) at the end.  Roles: warp 4
+// it adds its accumulators into dW (FP32 atomics) at the end.  The bias
+// gradient db[o] = sum_s dY[s][o] comes out of the same MMAs: the CTAs of
+// dt = 0 and the first chunk hold ones in the unused M column 3 CH.  Roles: warp 4
 // issues the boxes into a ring of STAGES buffers, warp 5 the MMAs, warps 0-3
 // read the accumulators (warp w: TMEM lanes 32 w .. 32 w + 31).  Every wait is
 // bounded.
@@ -1316,7 +1328,7 @@ template <int NP>
 __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __grid_constant__ CUtensorMap tx,
                                                                      const __grid_constant__ CUtensorMap ty, int I,
                                                                      int O, int CH, Lat g, float *__restrict__ dW,
-                                                                     int *__restrict__ err)
+                                                                     float *__restrict__ db, int *__restrict__ err)
 {
     using namespace gf::tc;
     using dwline::B_BOX;
@@ -1338,9 +1350,17 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
     const int NS = g.V / 128;
     const int n = member < NS ? (NS - member + R - 1) / R : 0;  // stages member, member + R, ...
 
-    // M columns beyond 3 nch and the N padding stay zero
-    for (int e = tid; e < LY::BAR_OFF / 16; e += dwline::THREADS)
-        reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
+    // M columns beyond 3 nch and the N padding stay zero, except that the CTAs of dt = 0 and
+    // the first chunk fill M column 3 CH (never loaded) with ones in every buffer: its first
+    // row of the dy = -1 accumulator is then sum_s dY[s - dx][o], the bias gradient at dx = 0
+    const bool bias = dti == 1 && g0 == 0 && 3 * CH < 16;
+    const uint32_t ones_lo = bias ? (uint32_t)(3 * CH) * slot : 0u, ones_hi = bias ? ones_lo + slot : 0u;
+    for (int e = tid; e < LY::BAR_OFF / 16; e += dwline::THREADS) {
+        const uint32_t off = (uint32_t)(e * 16) % (uint32_t)LY::STAGE;
+        const uint32_t one = 0x3F803F80u;  // two BF16 ones
+        reinterpret_cast<uint4 *>(smem)[e] =
+            off >= ones_lo && off < ones_hi ? make_uint4(one, one, one, one) : make_uint4(0, 0, 0, 0);
+    }
     fence_proxy_async();
     if (tid == 0) {
         for (int k = 0; k < LY::NBAR; ++k) mbar_init(&bar[k], 1);
@@ -1406,9 +1426,11 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
         mma_commit(drain);
         if (!mbar_wait(drain, 0)) fail = true;
     } else if (warp < 4 && n > 0) {
-        // row 32 w + lane = M column m = 3 (g - g0) + (dz + 1), channel i = 8 g + (row % 8)
+        // row 32 w + lane = M column m = 3 (g - g0) + (dz + 1), channel i = 8 g + (row % 8);
+        // row 8 (3 CH) of the dy = -1 accumulator is the bias gradient where ones fill column 3 CH
         const int row = 32 * warp + lane, m = row >> 3, gl = m / 3, dzi = m - 3 * gl;
         const int i = 8 * (g0 + gl) + (row & 7);
+        const bool bias_row = bias && row == 8 * 3 * CH;
         if (!mbar_wait_idle(acc_done, 0)) {
             fail = true;
         } else {
@@ -1420,6 +1442,13 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
                 for (int c0 = 0; c0 < NP; c0 += 32) {
                     float v[32];
                     tmem_load_cols<32>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(dyi * NP + c0), v);
+                    if (bias_row && dyi == 0) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const int col = c0 + c;
+                            if (col >= O && col < 2 * O) atomicAdd(&db[col - O], v[c]);
+                        }
+                    }
                     if (gl < nch) {
 #pragma unroll
                         for (int c = 0; c < 32; ++c) {
@@ -1500,10 +1529,13 @@ cudaError_t conv_dw_line_tc(const bf16 *dY, int O, const bf16 *X, int I, const L
     const int NT = 3 * ((G + CH - 1) / CH);
     const int NS = g.V / 128;
     const int R = std::max(1, std::min(nsm / NT, NS));
-    k_conv_dw_line_tc<NP><<<NT * R, dwline::THREADS, LY::SMEM, s>>>(tmap[0], tmap[1], I, O, CH, g, dW, err);
+    k_conv_dw_line_tc<NP><<<NT * R, dwline::THREADS, LY::SMEM, s>>>(tmap[0], tmap[1], I, O, CH, g, dW, db, err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_bias_grad<<<256, 256, 0, s>>>(dY, O, g.V, db);
-    return cudaGetLastError();
+    if (3 * CH >= 16) {  // no free M column for the ones: the bias gradient on its own
+        k_bias_grad<<<256, 256, 0, s>>>(dY, O, g.V, db);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
 }
 
 template <int IP, int N>
