@@ -325,8 +325,8 @@ def gpu_arm(args, rank, world, local):
                                         ("fp64_12", gf.GF_FP64, "storage64", 12, 1536),
                                         ("fp64_18", gf.GF_FP64, "storage64", 18, 2304),
                                         ("df64_18", gf.GF_FP64, "fp64_arith", 1, 2304)):
-        n = 200 if prec == gf.GF_FP32 else 40
-        t_half, tps, block = sweep_throughput(gf, ctx64, pristine, prec, key, st, nsweeps=n, warm=10)
+        # 200 timed sweeps after 20 warm-up sweeps, for every storage format
+        t_half, tps, block = sweep_throughput(gf, ctx64, pristine, prec, key, st, nsweeps=200, warm=20)
         thr[name] = {"ms_per_half_sweep": t_half, "gsu_per_s": Vh / (t_half * 1e-3) / 1e9,
                      "algorithmic_gbs": Vh * nbytes / (t_half * 1e-3) / 1e9,
                      "bytes_per_site_update": nbytes,
@@ -459,6 +459,7 @@ def gpu_arm(args, rank, world, local):
                      "fp32_fma_peak": fp32_peak,
                      "hbm_gbs": gbs, "hbm_frac": gbs / hbm if hbm else None,
                      "traffic": traffic64, "traffic_unit": "bytes per launch (ncu dram read + write)",
+                     "registers_per_thread": int(gf.gf_get_stat(ctx, "acc_registers")) if acc else None,
                      "algorithmic_bytes": Vh * thr[dom]["bytes_per_site_update"]})
 
     cpu = None

@@ -527,6 +527,8 @@ static int autotune_format(gf_ctx *ctx, int fmt, char *field, int *tps_out, int 
     for (int i = 0; i < ntps && e == cudaSuccess; ++i)
         for (int b = 0; b < 3 && e == cudaSuccess; ++b) {
             if (tps_c[i] == GF_ACC_R168 && blk_c[b] > 128) continue;
+            // the double-float overrelaxation kernel runs blocks of at most 128 threads
+            if (fmt == DF64_18 && tps_c[i] == GF_ACC && mode == 0 && blk_c[b] > 128) continue;
             if (ctx->gauge == GF_MAG && tps_c[i] <= 0) continue;  // the MAG step uses the per-subgroup form
             std::pair<int, int> cfg{ tps_c[i], blk_c[b] };
             e = mode == 1 ? issue_sa_sweeps(ctx, fmt, scratch, 1, cfg, ctx->stream)

@@ -811,7 +811,8 @@ static EncodeTiledFn encode_tiled()
 }
 
 // Pads X [V][I] (I a multiple of 8) into xpad (blocked by 8 channels, x ghosts
-// when gx = 1) and encodes the tensor maps of the halo kernels.  A line of x
+// when gx = 1; skipped when padded is set because xpad already holds it) and
+// encodes the tensor maps of the halo kernels.  A line of x
 // and its 8 channels are contiguous in xpad, and so are the rows o of a tap and
 // their 8 channels in the blocked weights, so each is one inner dimension and
 // a box row is a contiguous run (a TMA request per 16-byte row would bind the
@@ -820,15 +821,18 @@ static EncodeTiledFn encode_tiled()
 // Channel groups past I / 8 and rows past O are outside the maps: the TMA unit
 // fills them with zeros.
 static cudaError_t halo_prepare(const bf16 *X, int I, const bf16 *Wblk, int O, int N, const Lat &g, int gx, int bx,
-                                int by, int bz, bf16 *xpad, cudaStream_t s, CUtensorMap *tx, CUtensorMap *tw)
+                                int by, int bz, bf16 *xpad, cudaStream_t s, CUtensorMap *tx, CUtensorMap *tw,
+                                bool padded = false)
 {
     const EncodeTiledFn enc = encode_tiled();
     if (!enc || !xpad) return cudaErrorNotSupported;
-    const long P = padded_sites(g, gx);
-    const int pblocks = (int)std::min<long>((P + 255) / 256, 152L * 32);
-    k_pad_periodic<<<pblocks, 256, 0, s>>>(X, I, g, gx, xpad);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (!padded) {  // padded: xpad already holds X so padded
+        const long P = padded_sites(g, gx);
+        const int pblocks = (int)std::min<long>((P + 255) / 256, 152L * 32);
+        k_pad_periodic<<<pblocks, 256, 0, s>>>(X, I, g, gx, xpad);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     const cuuint64_t es = sizeof(bf16);
     const cuuint64_t Px = g.L[0] + 2 * gx, Py = g.L[1] + 2, Pz = g.L[2] + 2, Pt = g.L[3] + 2;
     const cuuint64_t xdim[4] = { 8 * Px, Py, Pz, (cuuint64_t)(I / 8) * Pt };
@@ -918,7 +922,7 @@ __global__ void __launch_bounds__(xline::THREADS) k_conv_line_tc(const __grid_co
                                                                  const float *__restrict__ bias, Lat g, int sign,
                                                                  int relu, const bf16 *__restrict__ mask,
                                                                  bf16 *__restrict__ Yb, float *__restrict__ Yf,
-                                                                 int *__restrict__ err)
+                                                                 int *__restrict__ err, int x0)
 {
     using namespace gf::tc;
     using namespace xline;
@@ -958,8 +962,9 @@ __global__ void __launch_bounds__(xline::THREADS) k_conv_line_tc(const __grid_co
     bool fail = false;
     if (tid == 0) {
         // the boxes of phase ph into buffer ph & 1: the halo t-plane of the slab (dt = sign (slab - 1))
-        // in padded coordinates (no x ghosts; halo y0 - 1 is padded y0; the plane of channel group
-        // c at t is c Pt + t), one box per 8-channel half, then the slab's weights
+        // in padded coordinates (x from element x0: 0 in a copy without x ghosts, 8 with them;
+        // halo y0 - 1 is padded y0; the plane of channel group c at t is c Pt + t), one box per
+        // 8-channel half, then the slab's weights
         auto issue = [&](int ph) {
             const int buf = ph & 1, ch0 = 16 * (ph / 3), slab = ph % 3;
             const int ht = sign > 0 ? slab : 2 - slab;
@@ -968,7 +973,7 @@ __global__ void __launch_bounds__(xline::THREADS) k_conv_line_tc(const __grid_co
             uint8_t *A = smem + buf * A_BYTES;
 #pragma unroll
             for (int kc = 0; kc < 2; ++kc)
-                tma_load_4d(A + kc * raw, &tx, 0, y0, z0, (ch0 / 8 + kc) * (g.L[3] + 2) + t0 + ht, full);
+                tma_load_4d(A + kc * raw, &tx, x0, y0, z0, (ch0 / 8 + kc) * (g.L[3] + 2) + t0 + ht, full);
             uint8_t *B = smem + LY::B_OFF + buf * LY::W_BYTES;
 #pragma unroll
             for (int kc = 0; kc < 2; ++kc) tma_load_3d(B + kc * LY::W_HALF, &tw, 0, 27 * slab, ch0 / 8 + kc, full);
@@ -1053,10 +1058,12 @@ __global__ void __launch_bounds__(xline::THREADS) k_conv_line_tc(const __grid_co
     }
 }
 
-// X [V][I] through the padded copy (no x ghosts) into the x-line kernel; Wblk = the weights blocked by 8 input channels
+// X [V][I] through the padded copy into the x-line kernel (gx: x ghosts in the copy; padded: xpad
+// already holds it); Wblk = the weights blocked by 8 input channels
 template <int IP, int N>
 cudaError_t conv_line_tc(const bf16 *X, int I, const bf16 *Wblk, int O, const float *b, const Lat &g, int sign,
-                         int relu, const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad, cudaStream_t s)
+                         int relu, const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad, cudaStream_t s,
+                         int gx = 0, bool padded = false)
 {
     typedef LineLayout<N> LY;
     static bool configured = false;
@@ -1068,10 +1075,11 @@ cudaError_t conv_line_tc(const bf16 *X, int I, const bf16 *Wblk, int O, const fl
     }
     const int TYL = 128 / g.L[0];
     CUtensorMap tx, tw;
-    cudaError_t e = halo_prepare(X, I, Wblk, O, N, g, 0, g.L[0], TYL + 2, xline::HZ, xpad, s, &tx, &tw);
+    cudaError_t e = halo_prepare(X, I, Wblk, O, N, g, gx, g.L[0], TYL + 2, xline::HZ, xpad, s, &tx, &tw, padded);
     if (e != cudaSuccess) return e;
     const int blocks = (g.L[1] / TYL) * (g.L[2] / xline::TZ) * g.L[3];
-    k_conv_line_tc<IP, N><<<blocks, xline::THREADS, LY::SMEM, s>>>(tx, tw, O, b, g, sign, relu, mask, Yb, Yf, err);
+    k_conv_line_tc<IP, N><<<blocks, xline::THREADS, LY::SMEM, s>>>(tx, tw, O, b, g, sign, relu, mask, Yb, Yf, err,
+                                                                   8 * gx);
     return cudaGetLastError();
 }
 
@@ -1480,10 +1488,11 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
 }
 
 // dW and db of one layer through the x-line weight-gradient kernel: X [V][I] is
-// padded without x ghosts into xpad, dY [V][O] with them into ypad
+// padded without x ghosts into xpad (unless x_padded: xpad holds it already),
+// dY [V][O] with them into ypad
 template <int NP>
 cudaError_t conv_dw_line_tc(const bf16 *dY, int O, const bf16 *X, int I, const Lat &g, float *dW, float *db,
-                            int *err, bf16 *xpad, bf16 *ypad, cudaStream_t s)
+                            int *err, bf16 *xpad, bf16 *ypad, cudaStream_t s, bool x_padded = false)
 {
     typedef DwLineLayout<NP> LY;
     static bool configured = false;
@@ -1506,8 +1515,10 @@ cudaError_t conv_dw_line_tc(const bf16 *dY, int O, const bf16 *X, int I, const L
         if (G % d == 0) CH = d;
     const int Lx = g.L[0], TYL = 128 / Lx;
     const long px = padded_sites(g, 0), py = padded_sites(g, 1);
-    k_pad_periodic<<<(int)std::min<long>((px + 255) / 256, 152L * 32), 256, 0, s>>>(X, I, g, 0, xpad);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!x_padded) {
+        k_pad_periodic<<<(int)std::min<long>((px + 255) / 256, 152L * 32), 256, 0, s>>>(X, I, g, 0, xpad);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     k_pad_periodic<<<(int)std::min<long>((py + 255) / 256, 152L * 32), 256, 0, s>>>(dY, O, g, 1, ypad);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const cuuint64_t es = sizeof(bf16);
@@ -1589,6 +1600,10 @@ struct gf_net {
     bf16 *dA = nullptr, *dB = nullptr;  // [V][32] gradient scratch (ping-pong)
     bf16 *xpad = nullptr;  // halo-tile convolutions: the input with periodic ghost sites, up to 80 channels
     bf16 *ypad = nullptr;  // x-line weight gradients: dY with periodic ghost sites, up to 32 channels
+    // training on the x-line path: each layer's input as the forward pass padded it (no x
+    // ghosts), kept for the weight gradients; keep is set while backward() runs
+    bf16 *xin[4] = { nullptr };
+    int keep = 0;
     double *partial = nullptr, *dloss = nullptr;
     int *derr = nullptr;  // tensor-core kernels: bounded-wait expiry
     int use_tc = 1;       // forward and backward-data on tcgen05 (else CUDA cores)
@@ -1635,12 +1650,16 @@ static int refresh_weights(gf_net *n)
 // x-line kernel, else (or with conv_halo 2) the halo-tile kernel, where the
 // extents allow them; otherwise the per-tap gather kernel
 // (W = weights [81][O][I], Wblk = the same blocked by 8 input channels)
+// (pad, gx, padded: on the x-line path, the padded copy to use instead of n->xpad, its x
+// ghosts, and whether it holds X already)
 template <int IP, int N>
 static cudaError_t conv_tensor(const gf_net *n, const bf16 *X, int I, const bf16 *W, const bf16 *Wblk, int O,
-                               const float *b, int sign, int relu, const bf16 *mask, bf16 *Yb, float *Yf)
+                               const float *b, int sign, int relu, const bf16 *mask, bf16 *Yb, float *Yf,
+                               bf16 *pad = nullptr, int gx = 0, bool padded = false)
 {
     if (n->use_halo == 1 && line_ok(n->g))
-        return conv_line_tc<IP, N>(X, I, Wblk, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->xpad, n->stream);
+        return conv_line_tc<IP, N>(X, I, Wblk, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, pad ? pad : n->xpad,
+                                   n->stream, gx, padded);
     if (n->use_halo != 0 && halo_ok(n->g))
         return conv_halo_tc<IP, N>(X, I, Wblk, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->xpad, n->stream);
     return conv_tc<IP, N>(X, I, W, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->stream);
@@ -1648,12 +1667,15 @@ static cudaError_t conv_tensor(const gf_net *n, const bf16 *X, int I, const bf16
 
 // weight and bias gradients of one layer on the tensor cores: with conv_halo 1
 // the x-line kernel where the extents allow it, otherwise the gather kernel
+// (xin: X as the forward pass padded it, or nullptr)
 template <int IP, int N>
-static cudaError_t dw_tensor(const gf_net *n, const bf16 *dY, int O, const bf16 *X, int I, float *dW, float *db)
+static cudaError_t dw_tensor(const gf_net *n, const bf16 *dY, int O, const bf16 *X, int I, float *dW, float *db,
+                             bf16 *xin = nullptr)
 {
     if (n->use_halo == 1 && n->ypad && dw_line_ok(n->g)) {
-        if (O <= 8) return conv_dw_line_tc<32>(dY, O, X, I, n->g, dW, db, n->derr, n->xpad, n->ypad, n->stream);
-        return conv_dw_line_tc<96>(dY, O, X, I, n->g, dW, db, n->derr, n->xpad, n->ypad, n->stream);
+        bf16 *xp = xin ? xin : n->xpad;
+        if (O <= 8) return conv_dw_line_tc<32>(dY, O, X, I, n->g, dW, db, n->derr, xp, n->ypad, n->stream, xin);
+        return conv_dw_line_tc<96>(dY, O, X, I, n->g, dW, db, n->derr, xp, n->ypad, n->stream, xin);
     }
     return conv_dw_tc<IP, N>(dY, O, X, I, n->g, dW, db, n->derr, n->stream);
 }
@@ -1664,14 +1686,16 @@ static int forward(gf_net *n, const bf16 *f)
     cudaStream_t s = n->stream;
     n->act[0] = const_cast<bf16 *>(f);
     if (n->use_tc) {
+        // while training on the x-line path each layer's padded input is kept (xin) for its weight gradient
+        bf16 *const *kp = n->keep ? n->xin : nullptr;
         NCK((conv_tensor<80, 32>(n, f, 80, n->Wb[0], n->Wh[0], 32, n->params + n->boff[0], 1, 1, nullptr, n->act[1],
-                                 nullptr)));
+                                 nullptr, kp ? kp[0] : nullptr)));
         NCK((conv_tensor<32, 32>(n, n->act[1], 32, n->Wb[1], n->Wh[1], 32, n->params + n->boff[1], 1, 1, nullptr,
-                                 n->act[2], nullptr)));
+                                 n->act[2], nullptr, kp ? kp[1] : nullptr)));
         NCK((conv_tensor<32, 32>(n, n->act[2], 32, n->Wb[2], n->Wh[2], 32, n->params + n->boff[2], 1, 1, nullptr,
-                                 n->act[3], nullptr)));
+                                 n->act[3], nullptr, kp ? kp[2] : nullptr)));
         NCK((conv_tensor<32, 16>(n, n->act[3], 32, n->Wb[3], n->Wh[3], 8, n->params + n->boff[3], 1, 0, nullptr,
-                                 nullptr, n->out)));
+                                 nullptr, n->out, kp ? kp[3] : nullptr)));
         return GF_OK;
     }
     NCK((conv_cc<80, 32>(f, n->Wb[0], n->params + n->boff[0], g, 1, 1, nullptr, n->act[1], nullptr, s)));
@@ -1686,13 +1710,18 @@ static int backward_data(gf_net *n, int l, const bf16 *dY, bf16 *dX)
 {
     const Lat &g = n->g;
     cudaStream_t s = n->stream;
+    // while training on the x-line path, the weight gradient of this layer has just padded dY
+    // with x ghosts into ypad: read it from there
+    bf16 *yp = n->keep ? n->ypad : nullptr;
     if (l == 3) {
         if (n->use_tc)
-            NCK((conv_tensor<16, 32>(n, dY, 8, n->Wt[3], n->Wth[3], 32, nullptr, -1, 0, n->act[3], dX, nullptr)));
+            NCK((conv_tensor<16, 32>(n, dY, 8, n->Wt[3], n->Wth[3], 32, nullptr, -1, 0, n->act[3], dX, nullptr, yp,
+                                     yp ? 1 : 0, yp != nullptr)));
         else NCK((conv_cc<8, 32>(dY, n->Wt[3], nullptr, g, -1, 0, n->act[3], dX, nullptr, s)));
     } else {
         if (n->use_tc)
-            NCK((conv_tensor<32, 32>(n, dY, 32, n->Wt[l], n->Wth[l], 32, nullptr, -1, 0, n->act[l], dX, nullptr)));
+            NCK((conv_tensor<32, 32>(n, dY, 32, n->Wt[l], n->Wth[l], 32, nullptr, -1, 0, n->act[l], dX, nullptr, yp,
+                                     yp ? 1 : 0, yp != nullptr)));
         else NCK((conv_cc<32, 32>(dY, n->Wt[l], nullptr, g, -1, 0, n->act[l], dX, nullptr, s)));
     }
     return GF_OK;
@@ -1711,12 +1740,40 @@ static int check_status(gf_net *n)
 }
 
 // forward + loss + backward into n->grad; loss left in n->dloss (device)
+// the padded layer inputs kept by a training forward pass on the x-line path
+static int ensure_train_buffers(gf_net *n)
+{
+    if (n->xin[0] || !(n->use_tc && n->use_halo == 1 && line_ok(n->g))) return GF_OK;
+    const long P = padded_sites(n->g, 0);
+    for (int l = 0; l < 4; ++l) {
+        const cudaError_t e = cudaMalloc(&n->xin[l], sizeof(bf16) * P * kC[l]);
+        if (e != cudaSuccess) {
+            for (int k = 0; k < 4; ++k) {
+                cudaFree(n->xin[k]);
+                n->xin[k] = nullptr;
+            }
+            return nfail(n, e == cudaErrorMemoryAllocation ? GF_ENOMEM : GF_ECUDA,
+                         std::string("padded layer inputs: ") + cudaGetErrorString(e));
+        }
+    }
+    return GF_OK;
+}
+
+
 static int backward(gf_net *n, const bf16 *f, const float *target)
 {
     const Lat &g = n->g;
     cudaStream_t s = n->stream;
-    int r = forward(n, f);
+    int r = ensure_train_buffers(n);
     if (r != GF_OK) return r;
+    // x-line path: the forward pass keeps its padded layer inputs for the weight gradients, and the
+    // data gradients read dY from the copy the weight gradients padded (line_ok implies dw_line_ok)
+    n->keep = n->use_tc && n->use_halo == 1 && line_ok(g) && n->xin[0] && n->ypad;
+    r = forward(n, f);
+    if (r != GF_OK) {
+        n->keep = 0;
+        return r;
+    }
     long nout = (long)g.V * 8;
     int nblk = 512;
     k_mse<<<nblk, 256, 0, s>>>(n->out, target, nout, 1.0f / (float)nout, n->dA, n->partial);
@@ -1725,23 +1782,33 @@ static int backward(gf_net *n, const bf16 *f, const float *target)
     NCK(cudaGetLastError());
     NCK(cudaMemsetAsync(n->grad, 0, sizeof(float) * n->np, s));
     // layer 4: dY = dA [V][8]
-    if (n->use_tc) NCK((dw_tensor<32, 16>(n, n->dA, 8, n->act[3], 32, n->grad + n->woff[3], n->grad + n->boff[3])));
+    bf16 *const *kx = n->keep ? n->xin : nullptr;
+    if (n->use_tc)
+        NCK((dw_tensor<32, 16>(n, n->dA, 8, n->act[3], 32, n->grad + n->woff[3], n->grad + n->boff[3],
+                               kx ? kx[3] : nullptr)));
     else NCK((conv_dw<32, 8>(n->dA, n->act[3], g, n->grad + n->woff[3], n->grad + n->boff[3], s)));
     r = backward_data(n, 3, n->dA, n->dB);
     if (r != GF_OK) return r;
     // layer 3
-    if (n->use_tc) NCK((dw_tensor<32, 32>(n, n->dB, 32, n->act[2], 32, n->grad + n->woff[2], n->grad + n->boff[2])));
+    if (n->use_tc)
+        NCK((dw_tensor<32, 32>(n, n->dB, 32, n->act[2], 32, n->grad + n->woff[2], n->grad + n->boff[2],
+                               kx ? kx[2] : nullptr)));
     else NCK((conv_dw<32, 32>(n->dB, n->act[2], g, n->grad + n->woff[2], n->grad + n->boff[2], s)));
     r = backward_data(n, 2, n->dB, n->dA);
     if (r != GF_OK) return r;
     // layer 2
-    if (n->use_tc) NCK((dw_tensor<32, 32>(n, n->dA, 32, n->act[1], 32, n->grad + n->woff[1], n->grad + n->boff[1])));
+    if (n->use_tc)
+        NCK((dw_tensor<32, 32>(n, n->dA, 32, n->act[1], 32, n->grad + n->woff[1], n->grad + n->boff[1],
+                               kx ? kx[1] : nullptr)));
     else NCK((conv_dw<32, 32>(n->dA, n->act[1], g, n->grad + n->woff[1], n->grad + n->boff[1], s)));
     r = backward_data(n, 1, n->dA, n->dB);
     if (r != GF_OK) return r;
     // layer 1 (no input gradient needed)
-    if (n->use_tc) NCK((dw_tensor<128, 32>(n, n->dB, 32, f, 80, n->grad + n->woff[0], n->grad + n->boff[0])));
+    if (n->use_tc)
+        NCK((dw_tensor<128, 32>(n, n->dB, 32, f, 80, n->grad + n->woff[0], n->grad + n->boff[0],
+                                kx ? kx[0] : nullptr)));
     else NCK((conv_dw<80, 32>(n->dB, f, g, n->grad + n->woff[0], n->grad + n->boff[0], s)));
+    n->keep = 0;
     return GF_OK;
 }
 
@@ -1825,6 +1892,7 @@ int gf_net_destroy(gf_net *n)
     cudaFree(n->dB);
     cudaFree(n->xpad);
     cudaFree(n->ypad);
+    for (int l = 0; l < 4; ++l) cudaFree(n->xin[l]);
     cudaFree(n->partial);
     cudaFree(n->dloss);
     cudaFree(n->derr);

@@ -11,10 +11,15 @@
 
 namespace gf {
 
-// at most 128 registers: occupancy matters more than registers here (long
-// dependent chains of double-float operations)
+// Occupancy matters more than registers here (long dependent chains of
+// double-float operations): at most 96 registers for overrelaxation and
+// stochastic relaxation (five blocks of at most 128 threads per SM; the
+// E-tracked half-sweep ran 6 % faster than with 128 registers), 128 for the
+// heatbath, which spills around its draw at 96.
+constexpr int kDfBlockMax = 128;
 template <bool COULOMB, int MODE, bool TRACKG, bool TRACKE = false>
-__global__ void __launch_bounds__(256, 2) k_sweep_df(SweepArgs a)
+__global__ void __launch_bounds__(MODE == MODE_SA ? 256 : kDfBlockMax, MODE == MODE_SA ? 2 : 5)
+    k_sweep_df(SweepArgs a)
 {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= a.g.Vh) return;
@@ -30,6 +35,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_df(SweepArgs a)
 // overrelaxation or heatbath with E = g - 1 tracked in double-float (a.ge)
 static cudaError_t launch_df_e(const SweepArgs &a, int coulomb, int mode, int block, cudaStream_t s)
 {
+    if (mode != MODE_SA && block > kDfBlockMax) block = kDfBlockMax;
     int grid = (a.g.Vh + block - 1) / block;
     const size_t smem = 9 * sizeof(float4) * (size_t)block;  // prefetched E, at most 36 KiB
     if (mode == MODE_OR) {
@@ -47,6 +53,7 @@ static cudaError_t launch_df_e(const SweepArgs &a, int coulomb, int mode, int bl
 template <bool TRACKG>
 static cudaError_t launch_df(const SweepArgs &a, int coulomb, int mode, int block, cudaStream_t s)
 {
+    if (mode != MODE_SA && block > kDfBlockMax) block = kDfBlockMax;
     int grid = (a.g.Vh + block - 1) / block;
     if (mode == MODE_OR) {
         if (coulomb) k_sweep_df<true, MODE_OR, TRACKG><<<grid, block, 0, s>>>(a);
