@@ -1439,7 +1439,9 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
         const int row = 32 * warp + lane, m = row >> 3, gl = m / 3, dzi = m - 3 * gl;
         const int i = 8 * (g0 + gl) + (row & 7);
         const bool bias_row = bias && row == 8 * 3 * CH;
-        if (!mbar_wait_idle(acc_done, 0)) {
+        // one decision per warp (and the warp converged) before the warp-wide accumulator loads
+        const bool landed = mbar_wait_idle(acc_done, 0);
+        if (!__all_sync(0xffffffffu, landed)) {
             fail = true;
         } else {
             fence_after_sync();
