@@ -364,10 +364,15 @@ int gf_net_gradient(gf_net *n, const void *features, const float *target, float 
  * planes; lattices with Lx = 8, 16 or 32, Ly % (128 / Lx) == 0 and
  * Lz % 2 == 0), else 8 x 16 x 2 site tiles (Lx % 8 == 0, Ly % 16 == 0,
  * Lz % 2 == 0); 2 = the 8 x 16 x 2 tiles only; lattices that fit neither, and
- * 0, use the per-tap gather kernel.  Other values: GF_EINVAL.  Forward,
- * gradient and train
- * calls synchronise the stream and return GF_ETIMEOUT if a bounded wait in a
- * tensor-core kernel expired. */
+ * 0, use the per-tap gather kernel.  Other values: GF_EINVAL.  With 1 and
+ * Lx = 8, 16 or 32, Ly % (128 / Lx) == 0, the weight and bias gradients are
+ * GEMMs over the site sum with both operands staged by TMA from ghost-padded
+ * copies (otherwise a gather kernel); where the x-line tiles apply, gradient
+ * and train calls also keep each layer's padded input of the forward pass
+ * for its weight gradient (extra device memory: Lx (Ly+2) (Lz+2) (Lt+2)
+ * x 176 BF16 values, allocated on the first such call).  Forward, gradient
+ * and train calls synchronise the stream and return GF_ETIMEOUT if a bounded
+ * wait in a tensor-core kernel expired. */
 int gf_net_set_option(gf_net *n, const char *key, double value);
 /* One Adam step on (features, target); loss before the step in *loss. */
 int gf_net_train_step(gf_net *n, const void *features, const float *target, float lr, double *loss);
