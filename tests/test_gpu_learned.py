@@ -14,9 +14,8 @@ compared with the FP64 oracle in two ways:
   and 16x32x4x4 (periodic wrap inside one halo tile, several tiles),
   32x4x4x3, the ragged 6x4x6x10 (1440 sites, not a multiple of the 128-site
   tile) and 16x16x8x8 (where each CTA of the x-line weight-gradient kernel
-  runs several stages through its buffer ring and crosses from one group of
-  taps to the next), each with the per-tap gather kernels, the x-line and
-  halo-tile kernels and the CUDA-core kernels;
+  runs several stages through its buffer ring), each with the per-tap gather
+  kernels, the x-line and halo-tile kernels and the CUDA-core kernels;
 - element by element on random weights, within 8 standard deviations of
   the rounding error, which is propagated through the layers from the
   arithmetic: the BF16 rounding of every stored activation and the FP32
