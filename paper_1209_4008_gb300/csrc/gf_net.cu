@@ -543,6 +543,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(gf::tc::smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar)
 {
     asm volatile(
@@ -875,7 +880,7 @@ cudaError_t conv_halo_tc(const bf16 *X, int I, const bf16 *Wblk, int O, const fl
 
 // ---------------------------------------------------------------------------
 // x-line convolution on the tensor cores (the default where Lx is 8, 16 or 32):
-// a CTA computes whole periodic x lines, 128 / Lx lines of y (M = 128 rows,
+// a tile is whole periodic x lines, 128 / Lx lines of y (M = 128 rows,
 // row r = x + Lx y) in each of two z planes, at one t.  The x shift of a tap is
 // taken out of the A operand and applied to the accumulator: for the lines of
 // one (dy, dz) a single MMA multiplies the unshifted rows by the weights of the
@@ -894,21 +899,7 @@ namespace xline {
 constexpr int TZ = 2, HZ = TZ + 2;
 constexpr int RAW_MAX = HZ * 16 * (128 + 2 * 32);  // one 8-channel half of a halo t-plane, Lx = 32
 constexpr int A_BYTES = 2 * RAW_MAX;
-constexpr int THREADS = 256;  // warps w and w + 4 read one TMEM lane quarter (two planes)
 }  // namespace xline
-
-template <int N>
-struct LineLayout {
-    static constexpr int W_HALF = 27 * N * 16;  // one 8-channel half of a slab: [tap][o][8 channels]
-    static constexpr int W_BYTES = 2 * W_HALF;
-    static constexpr int B_OFF = 2 * xline::A_BYTES;
-    // bar[0..1]: boxes of even / odd phases landed; bar[2..3]: MMAs of even / odd phases done; bar[4]: drain
-    static constexpr int BAR_OFF = B_OFF + 2 * W_BYTES;
-    static constexpr int SMEM = BAR_OFF + 5 * 8 + 8 + 16;
-    static constexpr int NM = 3 * N;                // columns of one plane's accumulator: taps dx = -1, 0, +1
-    static constexpr int PS = NM <= 64 ? 64 : 128;  // TMEM columns between the two planes
-    static constexpr int TMEM_COLS = 2 * PS;
-};
 
 static bool line_ok(const Lat &g)
 {
@@ -916,36 +907,83 @@ static bool line_ok(const Lat &g)
     return (Lx == 8 || Lx == 16 || Lx == 32) && g.L[1] % (128 / Lx) == 0 && g.L[2] % xline::TZ == 0;
 }
 
+// ---------------------------------------------------------------------------
+// The kernel is persistent: one CTA per SM walks the tiles b, b + gridDim.x,
+// ...  Warp 8 issues the boxes of every (tile, phase) into a ring of STAGES
+// buffers; warp 9 issues the MMAs into one of two accumulator sets in tensor
+// memory (tile parity); warps 0-7 read the other set and run the epilogue
+// (warps w and w + 4 read one TMEM lane quarter of the two planes), so a
+// tile's epilogue overlaps the next tile's MMAs.  (One CTA per tile, two per
+// SM, left the tensor pipe idle during each tile's epilogue: 156 against 135
+// us for a 32 -> 32 layer at 32^4.)  Every wait is bounded.
+// ---------------------------------------------------------------------------
+namespace xlp {
+constexpr int EPI_WARPS = 8;                    // two planes x four TMEM lane quarters
+constexpr int THREADS = (EPI_WARPS + 2) * 32;   // + a TMA warp and an MMA warp
+constexpr int EPI_STAGE = 2048;                 // per epilogue warp: 32 rows of at most 64 bytes
+constexpr int SMEM_MAX = 232448;                // opt-in shared memory per block
+}  // namespace xlp
+
+template <int N>
+struct LinePLayout {
+    static constexpr int W_HALF = 27 * N * 16;
+    static constexpr int W_BYTES = 2 * W_HALF;
+    static constexpr int STAGE = xline::A_BYTES + W_BYTES;
+    static constexpr int EPI_BYTES = xlp::EPI_WARPS * xlp::EPI_STAGE;
+    static constexpr int FIXED = EPI_BYTES + 1024;  // staging, barriers and slack
+    static constexpr int STAGES = (xlp::SMEM_MAX - FIXED) / STAGE < 4 ? (xlp::SMEM_MAX - FIXED) / STAGE : 4;
+    static_assert(STAGES >= 2, "two buffers at least");
+    static constexpr int EPI_OFF = STAGES * STAGE;
+    static constexpr int BAR_OFF = EPI_OFF + EPI_BYTES;
+    // bar[0..S-1] boxes landed, bar[S..2S-1] buffer free, bar[2S..2S+1] accumulator set full,
+    // bar[2S+2..2S+3] accumulator set read, bar[2S+4] drain
+    static constexpr int NBAR = 2 * STAGES + 5;
+    static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16;
+    static constexpr int NM = 3 * N;
+    static constexpr int PS = NM <= 64 ? 64 : 128;  // TMEM columns between the two planes
+    static constexpr int ACC_COLS = 2 * PS;         // one tile's accumulators
+    static constexpr int TMEM_COLS = 2 * ACC_COLS;  // two tiles in flight
+};
+
 template <int IP, int N>
-__global__ void __launch_bounds__(xline::THREADS) k_conv_line_tc(const __grid_constant__ CUtensorMap tx,
-                                                                 const __grid_constant__ CUtensorMap tw, int O,
-                                                                 const float *__restrict__ bias, Lat g, int sign,
-                                                                 int relu, const bf16 *__restrict__ mask,
-                                                                 bf16 *__restrict__ Yb, float *__restrict__ Yf,
-                                                                 int *__restrict__ err, int x0)
+__global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_constant__ CUtensorMap tx,
+                                                                   const __grid_constant__ CUtensorMap tw, int O,
+                                                                   const float *__restrict__ bias, Lat g, int sign,
+                                                                   int relu, const bf16 *__restrict__ mask,
+                                                                   bf16 *__restrict__ Yb, float *__restrict__ Yf,
+                                                                   int *__restrict__ err, int x0)
 {
     using namespace gf::tc;
     using namespace xline;
-    typedef LineLayout<N> LY;
+    typedef LinePLayout<N> LY;
+    constexpr int S = LY::STAGES;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + 40);
+    uint64_t *full = bar, *empty = bar + S, *acc_full = bar + 2 * S, *acc_empty = bar + 2 * S + 2;
+    uint64_t *drain = bar + 2 * S + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + LY::NBAR * 8);
+    int *consumed_sh = reinterpret_cast<int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr uint32_t idesc = instr_desc(kM, LY::NM);
     constexpr int NPHASE = (IP / 16) * 3;  // (16-channel chunk, dt slab)
 
     const int Lx = g.L[0], TYL = 128 / Lx, HY = TYL + 2;
-    const uint32_t line = (uint32_t)Lx * 16;        // bytes of one halo line (8 channels)
-    const uint32_t raw = (uint32_t)(HZ * HY) * line;  // one 8-channel half of the halo t-plane
-    int b = blockIdx.x;
+    const uint32_t line = (uint32_t)Lx * 16;
+    const uint32_t raw = (uint32_t)(HZ * HY) * line;
     const int nby = g.L[1] / TYL, nbz = g.L[2] / TZ;
-    const int y0 = (b % nby) * TYL;
-    b /= nby;
-    const int z0 = (b % nbz) * TZ;
-    const int t0 = b / nbz;
+    const int ntiles = nby * nbz * g.L[3];
+    const int nt = (int)blockIdx.x < ntiles ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    auto tile_of = [&](int k, int &y0, int &z0, int &t0) {
+        int b = (int)blockIdx.x + k * (int)gridDim.x;
+        y0 = (b % nby) * TYL;
+        b /= nby;
+        z0 = (b % nbz) * TZ;
+        t0 = b / nbz;
+    };
 
     if (tid == 0) {
-        for (int k = 0; k < 5; ++k) mbar_init(&bar[k], 1);
+        for (int k = 0; k < LY::NBAR; ++k) mbar_init(&bar[k], (k == 2 * S + 2 || k == 2 * S + 3) ? xlp::EPI_WARPS : 1);
+        *consumed_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -960,94 +998,119 @@ __global__ void __launch_bounds__(xline::THREADS) k_conv_line_tc(const __grid_co
     const uint32_t tmem = *tmem_slot;
 
     bool fail = false;
-    if (tid == 0) {
-        // the boxes of phase ph into buffer ph & 1: the halo t-plane of the slab (dt = sign (slab - 1))
-        // in padded coordinates (x from element x0: 0 in a copy without x ghosts, 8 with them;
-        // halo y0 - 1 is padded y0; the plane of channel group c at t is c Pt + t), one box per
-        // 8-channel half, then the slab's weights
-        auto issue = [&](int ph) {
-            const int buf = ph & 1, ch0 = 16 * (ph / 3), slab = ph % 3;
-            const int ht = sign > 0 ? slab : 2 - slab;
-            uint64_t *full = &bar[buf];
-            mbar_expect_tx(full, 2 * raw + (uint32_t)LY::W_BYTES);
-            uint8_t *A = smem + buf * A_BYTES;
-#pragma unroll
-            for (int kc = 0; kc < 2; ++kc)
-                tma_load_4d(A + kc * raw, &tx, x0, y0, z0, (ch0 / 8 + kc) * (g.L[3] + 2) + t0 + ht, full);
-            uint8_t *B = smem + LY::B_OFF + buf * LY::W_BYTES;
-#pragma unroll
-            for (int kc = 0; kc < 2; ++kc) tma_load_3d(B + kc * LY::W_HALF, &tw, 0, 27 * slab, ch0 / 8 + kc, full);
-        };
-        int issued = 0, landed = 0;
-        issue(0);
-        issued = 1;
-        for (int ph = 0; ph < NPHASE; ++ph) {
-            const int nx = ph + 1;
-            if (nx < NPHASE) {
-                // the buffers of phase nx were last read by the MMAs of phase ph - 1
-                if (ph > 0 && !mbar_wait(&bar[2 + ((ph - 1) & 1)], (uint32_t)(((ph - 1) >> 1) & 1))) {
+    int issued = 0;
+    if (warp == xlp::EPI_WARPS) {
+        if (lane == 0) {
+            // the boxes of (tile k, phase ph) into buffer q % S, q = k NPHASE + ph: the halo t-plane of
+            // the slab (dt = sign (slab - 1)) in padded coordinates, one box per 8-channel half, then
+            // the slab's weights
+            for (int q = 0; q < nt * NPHASE; ++q) {
+                const int slot = q % S;
+                if (q >= S && !mbar_wait(&empty[slot], (uint32_t)((q / S - 1) & 1))) {
                     fail = true;
                     break;
                 }
-                issue(nx);
-                issued = nx + 1;
+                const int k = q / NPHASE, ph = q - k * NPHASE;
+                int y0, z0, t0;
+                tile_of(k, y0, z0, t0);
+                const int ch0 = 16 * (ph / 3), slab = ph % 3;
+                const int ht = sign > 0 ? slab : 2 - slab;
+                mbar_expect_tx(&full[slot], 2 * raw + (uint32_t)LY::W_BYTES);
+                uint8_t *A = smem + slot * LY::STAGE;
+#pragma unroll
+                for (int kc = 0; kc < 2; ++kc)
+                    tma_load_4d(A + kc * raw, &tx, x0, y0, z0, (ch0 / 8 + kc) * (g.L[3] + 2) + t0 + ht, &full[slot]);
+                uint8_t *B = A + A_BYTES;
+#pragma unroll
+                for (int kc = 0; kc < 2; ++kc)
+                    tma_load_3d(B + kc * LY::W_HALF, &tw, 0, 27 * slab, ch0 / 8 + kc, &full[slot]);
+                issued = q + 1;
             }
-            if (!mbar_wait(&bar[ph & 1], (uint32_t)((ph >> 1) & 1))) {  // the boxes of phase ph have landed
+        }
+    } else if (warp == xlp::EPI_WARPS + 1) {
+        if (lane == 0) {
+            int consumed = 0;
+            for (int k = 0; k < nt && !fail; ++k) {
+                const int buf = k & 1;
+                // the epilogue has read this accumulator set (tile k - 2)
+                if (k >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)((k / 2 - 1) & 1))) {
+                    fail = true;
+                    break;
+                }
+                fence_after_sync();
+                for (int ph = 0; ph < NPHASE; ++ph) {
+                    const int q = k * NPHASE + ph, slot = q % S;
+                    if (!mbar_wait(&full[slot], (uint32_t)((q / S) & 1))) {
+                        fail = true;
+                        break;
+                    }
+                    consumed = q + 1;
+                    fence_after_sync();
+                    const uint8_t *A = smem + slot * LY::STAGE;
+                    const uint8_t *B = A + A_BYTES;
+                    for (int jz = 0; jz < 3; ++jz) {
+                        for (int jy = 0; jy < 3; ++jy) {
+                            const int dy = sign * (jy - 1), dz = sign * (jz - 1);
+                            const uint64_t bd = smem_desc(smem_u32(B + (3 * jy + 9 * jz) * N * 16), LY::W_HALF, 128);
+#pragma unroll
+                            for (int zz = 0; zz < TZ; ++zz) {
+                                const int l0 = (dy + 1) + HY * (zz + dz + 1);
+                                const uint64_t ad = smem_desc(smem_u32(A + l0 * line), raw, 128);
+                                mma_bf16(tmem + (uint32_t)(buf * LY::ACC_COLS + zz * LY::PS), ad, bd, idesc,
+                                         (ph | jy | jz) != 0);
+                            }
+                        }
+                    }
+                    mma_commit(&empty[slot]);
+                }
+                if (!fail) mma_commit(&acc_full[buf]);
+            }
+            *consumed_sh = consumed;
+            mma_commit(drain);
+            if (!mbar_wait(drain, 0)) fail = true;
+        }
+    } else {
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 of plane w / 4; row = x + Lx y, a warp holds
+        // 32 / Lx whole lines; the column block of input x contributes to output x - dx: tap jx has
+        // dx = sign (jx - 1), so output x takes block 1 - sign from x - 1 and block 1 + sign from x + 1
+        const int zz = warp >> 2, qd = warp & 3, row = qd * 32 + lane;
+        const int x = row & (Lx - 1), seg = lane & ~(Lx - 1);
+        const int from_left = seg | ((x + Lx - 1) & (Lx - 1)), from_right = seg | ((x + 1) & (Lx - 1));
+        uint4 *stage = reinterpret_cast<uint4 *>(smem + LY::EPI_OFF + warp * xlp::EPI_STAGE);
+        for (int k = 0; k < nt; ++k) {
+            const int buf = k & 1;
+            const bool landed = mbar_wait_idle(&acc_full[buf], (uint32_t)((k / 2) & 1));
+            if (!__all_sync(0xffffffffu, landed)) {  // one decision per warp, the warp converged
                 fail = true;
                 break;
             }
-            landed = ph + 1;
             fence_after_sync();
-            const uint8_t *A = smem + (ph & 1) * A_BYTES;
-            const uint8_t *B = smem + LY::B_OFF + (ph & 1) * LY::W_BYTES;
-            for (int jz = 0; jz < 3; ++jz) {
-                for (int jy = 0; jy < 3; ++jy) {
-                    const int dy = sign * (jy - 1), dz = sign * (jz - 1);
-                    // the slab's taps (jx, jy, jz), jx = 0, 1, 2: 3 N consecutive weight rows
-                    const uint64_t bd = smem_desc(smem_u32(B + (3 * jy + 9 * jz) * N * 16), LY::W_HALF, 128);
+            const uint32_t taddr =
+                tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * LY::ACC_COLS + zz * LY::PS);
+            float acc[N], v[N];
+            tmem_load_cols<N>(taddr + (uint32_t)N, acc);
+            tmem_load_cols<N>(taddr + (uint32_t)((1 - sign) * N), v);
 #pragma unroll
-                    for (int zz = 0; zz < TZ; ++zz) {
-                        // first halo line of the tile of plane zz moved by (dy, dz); no x shift
-                        const int l0 = (dy + 1) + HY * (zz + dz + 1);
-                        const uint64_t ad = smem_desc(smem_u32(A + l0 * line), raw, 128);
-                        mma_bf16(tmem + (uint32_t)(zz * LY::PS), ad, bd, idesc, (ph | jy | jz) != 0);
-                    }
-                }
-            }
-            mma_commit(&bar[2 + (ph & 1)]);
+            for (int o = 0; o < N; ++o) acc[o] += __shfl_sync(0xffffffffu, v[o], from_left);
+            tmem_load_cols<N>(taddr + (uint32_t)((1 + sign) * N), v);
+#pragma unroll
+            for (int o = 0; o < N; ++o) acc[o] += __shfl_sync(0xffffffffu, v[o], from_right);
+            // the accumulator set is free for tile k + 2 once every lane of the warp has read it
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            int y0, z0, t0;
+            tile_of(k, y0, z0, t0);
+            const long first = (long)Lx * (y0 + (long)g.L[1] * ((z0 + zz) + (long)g.L[2] * t0)) + qd * 32;
+            epilogue_rows<N>(acc, O, bias, relu, mask, Yb, Yf, stage, lane, [&](int r) { return first + r; });
         }
-        // boxes issued but not consumed must land before the CTA ends (bounded)
-        for (int q = landed; q < issued; ++q)
-            if (!mbar_wait(&bar[q & 1], (uint32_t)((q >> 1) & 1))) fail = true;
-        mma_commit(&bar[4]);  // arrives once every MMA issued above is complete
     }
-    // everyone: all MMAs complete (bounded wait), then the epilogue
-    const bool drained = mbar_wait_idle(&bar[4], 0);
-    fail = __syncthreads_or(fail || !drained);
-    if (!fail) {
-        fence_after_sync();
-        // warp w reads TMEM lanes 32 (w % 4) .. + 31 of plane w / 4; row = x + Lx y, and
-        // a warp holds 32 / Lx whole lines
-        const int zz = warp >> 2, row = (warp & 3) * 32 + lane;
-        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(zz * LY::PS);
-        const int x = row & (Lx - 1), seg = lane & ~(Lx - 1);
-        const int from_left = seg | ((x + Lx - 1) & (Lx - 1)), from_right = seg | ((x + 1) & (Lx - 1));
-        // the column block of input x contributes to output x - dx: tap jx has dx = sign (jx - 1),
-        // so output x takes block 1 - sign from x - 1 and block 1 + sign from x + 1
-        float acc[N], v[N];
-        tmem_load_cols<N>(taddr + (uint32_t)N, acc);
-        tmem_load_cols<N>(taddr + (uint32_t)((1 - sign) * N), v);
-#pragma unroll
-        for (int o = 0; o < N; ++o) acc[o] += __shfl_sync(0xffffffffu, v[o], from_left);
-        tmem_load_cols<N>(taddr + (uint32_t)((1 + sign) * N), v);
-#pragma unroll
-        for (int o = 0; o < N; ++o) acc[o] += __shfl_sync(0xffffffffu, v[o], from_right);
-        // the warp's 32 rows are 32 consecutive sites; the A buffers are free once every MMA has completed
-        const long first = (long)Lx * (y0 + (long)g.L[1] * ((z0 + zz) + (long)g.L[2] * t0)) + (warp & 3) * 32;
-        epilogue_rows<N>(acc, O, bias, relu, mask, Yb, Yf, reinterpret_cast<uint4 *>(smem) + warp * 256, lane,
-                         [&](int r) { return first + r; });
-    } else if (tid == 0) {
-        atomicExch(err, GF_ETIMEOUT);
+    fail = __syncthreads_or(fail);
+    if (fail) {
+        if (tid == 0) atomicExch(err, GF_ETIMEOUT);
+        // boxes issued but not consumed land before the buffers go away (bounded)
+        if (warp == xlp::EPI_WARPS && lane == 0)
+            for (int q = *consumed_sh; q < issued; ++q) mbar_wait(&full[q % S], (uint32_t)((q / S) & 1));
     }
     fence_before_sync();
     __syncthreads();
@@ -1058,28 +1121,34 @@ __global__ void __launch_bounds__(xline::THREADS) k_conv_line_tc(const __grid_co
     }
 }
 
-// X [V][I] through the padded copy into the x-line kernel (gx: x ghosts in the copy; padded: xpad
-// already holds it); Wblk = the weights blocked by 8 input channels
+// X [V][I] through the padded copy into the persistent x-line kernel (gx: x ghosts in the copy;
+// padded: xpad already holds it); Wblk = the weights blocked by 8 input channels
 template <int IP, int N>
-cudaError_t conv_line_tc(const bf16 *X, int I, const bf16 *Wblk, int O, const float *b, const Lat &g, int sign,
-                         int relu, const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad, cudaStream_t s,
-                         int gx = 0, bool padded = false)
+cudaError_t conv_line_ptc(const bf16 *X, int I, const bf16 *Wblk, int O, const float *b, const Lat &g, int sign,
+                          int relu, const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad, cudaStream_t s,
+                          int gx = 0, bool padded = false)
 {
-    typedef LineLayout<N> LY;
+    typedef LinePLayout<N> LY;
     static bool configured = false;
+    static int nsm = 0;
+    cudaError_t e;
     if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_conv_line_tc<IP, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, LY::SMEM);
+        e = cudaFuncSetAttribute(k_conv_line_ptc<IP, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, LY::SMEM);
         if (e != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         configured = true;
     }
+    // the epilogue stages 32 rows of at most 64 bytes per warp
+    if (O > 32 || (Yf && O > 16)) return cudaErrorInvalidValue;
     const int TYL = 128 / g.L[0];
     CUtensorMap tx, tw;
-    cudaError_t e = halo_prepare(X, I, Wblk, O, N, g, gx, g.L[0], TYL + 2, xline::HZ, xpad, s, &tx, &tw, padded);
+    e = halo_prepare(X, I, Wblk, O, N, g, gx, g.L[0], TYL + 2, xline::HZ, xpad, s, &tx, &tw, padded);
     if (e != cudaSuccess) return e;
-    const int blocks = (g.L[1] / TYL) * (g.L[2] / xline::TZ) * g.L[3];
-    k_conv_line_tc<IP, N><<<blocks, xline::THREADS, LY::SMEM, s>>>(tx, tw, O, b, g, sign, relu, mask, Yb, Yf, err,
-                                                                   8 * gx);
+    const int tiles = (g.L[1] / TYL) * (g.L[2] / xline::TZ) * g.L[3];
+    k_conv_line_ptc<IP, N><<<std::min(tiles, nsm), xlp::THREADS, LY::SMEM, s>>>(tx, tw, O, b, g, sign, relu, mask,
+                                                                                Yb, Yf, err, 8 * gx);
     return cudaGetLastError();
 }
 
@@ -1660,8 +1729,8 @@ static cudaError_t conv_tensor(const gf_net *n, const bf16 *X, int I, const bf16
                                bf16 *pad = nullptr, int gx = 0, bool padded = false)
 {
     if (n->use_halo == 1 && line_ok(n->g))
-        return conv_line_tc<IP, N>(X, I, Wblk, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, pad ? pad : n->xpad,
-                                   n->stream, gx, padded);
+        return conv_line_ptc<IP, N>(X, I, Wblk, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, pad ? pad : n->xpad,
+                                    n->stream, gx, padded);
     if (n->use_halo != 0 && halo_ok(n->g))
         return conv_halo_tc<IP, N>(X, I, Wblk, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->xpad, n->stream);
     return conv_tc<IP, N>(X, I, W, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->stream);
