@@ -9,7 +9,8 @@ reduction scratch in a fixed device array instead.  This file checks, on two
 calls in a row (different lattices and gauges, so stale scratch contents from
 the first call would show up in the second), that it gives the oracle's F and
 theta (Sec. 2, eqs. F_g and theta) and the same values as the context-based
-gf_functional / gf_theta, and that it refuses what it cannot hold: volumes
+gf_functional / gf_theta, that repeated calls leave the device's free memory
+unchanged, and that it refuses what it cannot hold: volumes
 beyond its fixed scratch, host memory (pageable or pinned), odd extents, and
 tensors of the wrong type or size.
 
@@ -47,6 +48,26 @@ def test_noalloc_measure_matches_oracle_and_context_entry_points():
         gf.gf_destroy(ctx)
         assert F_na == pytest.approx(F, rel=1e-13, abs=1e-15)
         assert th_na == pytest.approx(th, rel=1e-12)
+
+
+def test_noalloc_measure_leaves_free_device_memory_unchanged():
+    """The first call on a device looks up the scratch array's address and
+    loads the kernels; after it, calls move no device memory at all: the
+    free memory the driver reports is the same before and after three calls
+    (an allocation would take at least its 2 MiB granule)."""
+    dims = (8, 8, 8, 8)
+    Ud = synth.make_field(dims, 0.60, 1, 2).to("cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    assert gf.gf_measure_noalloc(dims, gf.GF_LANDAU, Ud, out) == gf.GF_OK
+    torch.cuda.synchronize()
+    first = out.cpu().numpy().copy()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert gf.gf_measure_noalloc(dims, gf.GF_LANDAU, Ud, out) == gf.GF_OK
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+    np.testing.assert_array_equal(out.cpu().numpy(), first)
 
 
 def test_noalloc_measure_rejects_what_it_cannot_hold():
