@@ -1046,17 +1046,21 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
                     }
                     consumed = q + 1;
                     fence_after_sync();
-                    const uint8_t *A = smem + slot * LY::STAGE;
-                    const uint8_t *B = A + A_BYTES;
+                    // the descriptors of this buffer once; each MMA adds its view's offset to the start
+                    // address field (16-byte units; shared memory stays below 256 KiB, so no carry)
+                    const uint32_t A = smem_u32(smem + slot * LY::STAGE);
+                    const uint64_t a0 = smem_desc(A, raw, 128), b0 = smem_desc(A + A_BYTES, LY::W_HALF, 128);
+                    const uint32_t d0 = tmem + (uint32_t)(buf * LY::ACC_COLS);
+#pragma unroll
                     for (int jz = 0; jz < 3; ++jz) {
+#pragma unroll
                         for (int jy = 0; jy < 3; ++jy) {
                             const int dy = sign * (jy - 1), dz = sign * (jz - 1);
-                            const uint64_t bd = smem_desc(smem_u32(B + (3 * jy + 9 * jz) * N * 16), LY::W_HALF, 128);
+                            const uint64_t bd = b0 + (uint64_t)((3 * jy + 9 * jz) * N);
 #pragma unroll
                             for (int zz = 0; zz < TZ; ++zz) {
-                                const int l0 = (dy + 1) + HY * (zz + dz + 1);
-                                const uint64_t ad = smem_desc(smem_u32(A + l0 * line), raw, 128);
-                                mma_bf16(tmem + (uint32_t)(buf * LY::ACC_COLS + zz * LY::PS), ad, bd, idesc,
+                                const int l0 = (dy + 1) + HY * (zz + dz + 1);  // first halo line of the view
+                                mma_bf16(d0 + (uint32_t)(zz * LY::PS), a0 + (uint64_t)(l0 * Lx), bd, idesc,
                                          (ph | jy | jz) != 0);
                             }
                         }
@@ -1488,14 +1492,16 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
             }
             consumed = p + 1;
             fence_after_sync();
+            // the descriptors of this buffer once; each MMA adds its view's offset to the start address
+            // field (16-byte units; shared memory stays below 256 KiB, so no carry)
             const uint32_t A = smem_u32(smem + (p % S) * LY::STAGE);
-            const uint32_t B = A + dwline::A_BYTES;
+            const uint64_t a0 = smem_desc_mn(A, 128, slot), b0 = smem_desc_mn(A + dwline::A_BYTES, 128, B_BOX);
 #pragma unroll
             for (int dyi = 0; dyi < 3; ++dyi)
 #pragma unroll
                 for (int kk = 0; kk < 8; ++kk)
-                    mma_bf16(tmem + (uint32_t)(dyi * NP), smem_desc_mn(A + dyi * line + kk * 256, 128, slot),
-                             smem_desc_mn(B + kk * 256, 128, B_BOX), idesc, (p | kk) != 0);
+                    mma_bf16(tmem + (uint32_t)(dyi * NP), a0 + (uint64_t)(dyi * Lx + kk * 16), b0 + (uint64_t)(kk * 16),
+                             idesc, (p | kk) != 0);
             mma_commit(&bar[S + p % S]);
         }
         *consumed_sh = consumed;
