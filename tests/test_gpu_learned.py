@@ -219,6 +219,31 @@ def test_network_exact_arithmetic_matches_oracle_bit_for_bit(dims, path):
     assert bad.size == 0, (bad[:10], grad[bad[:10]], grad_o[bad[:10]])
 
 
+def test_network_exact_arithmetic_persistent_tiles_bit_for_bit():
+    """The persistent x-line convolution walks 512 tiles with 152 CTAs or
+    fewer, so every CTA runs three or four tiles: both accumulator sets are
+    reused and the buffer ring wraps across tiles.  Forward output and all
+    gradients bit for bit against the oracle, as above, on 32x32x16x8."""
+    dims = (32, 32, 16, 8)
+    params, X0, target, out_exact = exact_network(dims, seed=sum(dims))
+    V = int(np.prod(dims))
+    loss_o, grad_o, out_o = oracle.net_loss(X0, target, params.astype(np.float64), dims, CHANNELS)
+    assert np.array_equal(out_o, out_exact)
+    assert np.array_equal(grad_o.astype(np.float32).astype(np.float64), grad_o)
+    net = gf.gf_net_create(dims)
+    gf.gf_net_set_params(net, params)
+    fd = torch.from_numpy(X0.astype(np.float32)).to(torch.bfloat16).cuda()
+    td = torch.from_numpy(target.astype(np.float32)).cuda()
+    out = torch.empty(V, 8, dtype=torch.float32, device="cuda")
+    gf.gf_net_forward(net, fd, out)
+    np.testing.assert_array_equal(out.cpu().numpy().astype(np.float64), out_o)
+    grad = np.zeros(gf.gf_net_param_count(), dtype=np.float32)
+    loss = gf.gf_net_gradient(net, fd, td, grad)
+    assert loss == pytest.approx(loss_o, rel=1e-14)
+    bad = np.flatnonzero(grad.astype(np.float64) != grad_o)
+    assert bad.size == 0, (bad[:10], grad[bad[:10]], grad_o[bad[:10]])
+
+
 def forward_error_sigma(X0, Ws, bs, dims):
     """Element-wise standard deviation of GPU output - FP64 output, from the
     arithmetic: every stored activation is rounded to BF16 (an error uniform
