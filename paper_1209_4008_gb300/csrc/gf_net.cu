@@ -224,6 +224,15 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ gr, floa
 
 // ... and the same two blocked by 8 input channels for the halo kernels' TMA
 // boxes: Wh[i / 8][k][o][i % 8] and Wth[o / 8][k][i][o % 8] (I, O multiples of 8)
+// Row block of tap k = jx + 3 jy + 9 jz + 27 jt in the blocked weight copies used with the
+// given sign of the shift: within each dt slab (27 rows) the order is (jy, z block, jx) with z
+// block 2 - jz for sign +1 and jz for sign -1.  Then, for one jy, the rows that two adjacent z
+// planes of the x-line kernel need from one halo view are adjacent (see k_conv_line_ptc).
+__host__ __device__ constexpr int slab_row(int k, int sign)
+{
+    return 27 * (k / 27) + (k % 3) + 3 * (sign > 0 ? 2 - (k / 9) % 3 : (k / 9) % 3) + 9 * ((k / 3) % 3);
+}
+
 __global__ void k_cast_weights(const float *__restrict__ W, int I, int O, bf16 *__restrict__ Wb,
                                bf16 *__restrict__ Wt, bf16 *__restrict__ Wh, bf16 *__restrict__ Wth)
 {
@@ -236,8 +245,8 @@ __global__ void k_cast_weights(const float *__restrict__ W, int I, int O, bf16 *
     bf16 w = __float2bfloat16(W[e]);
     Wb[e] = w;
     Wt[((long)k * I + i) * O + o] = w;
-    Wh[(((long)(i >> 3) * 81 + k) * O + o) * 8 + (i & 7)] = w;
-    Wth[(((long)(o >> 3) * 81 + k) * I + i) * 8 + (o & 7)] = w;
+    Wh[(((long)(i >> 3) * 81 + slab_row(k, 1)) * O + o) * 8 + (i & 7)] = w;
+    Wth[(((long)(o >> 3) * 81 + slab_row(k, -1)) * I + i) * 8 + (o & 7)] = w;
 }
 
 
@@ -615,7 +624,8 @@ __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float *v)
 template <int N, typename SiteOf>
 __device__ __forceinline__ void epilogue_rows(float (&acc)[N], int O, const float *__restrict__ bias, int relu,
                                               const bf16 *__restrict__ mask, bf16 *__restrict__ Yb,
-                                              float *__restrict__ Yf, uint4 *stage, int lane, SiteOf site_of)
+                                              float *__restrict__ Yf, uint4 *stage, int lane, SiteOf site_of,
+                                              bool mask_staged = false)
 {
 #pragma unroll
     for (int o = 0; o < N; ++o) {
@@ -624,8 +634,9 @@ __device__ __forceinline__ void epilogue_rows(float (&acc)[N], int O, const floa
     }
     if (mask) {
         const int cpr = O / 8;  // 16-byte pieces of a BF16 row
-        for (int c = lane; c < 32 * cpr; c += 32)
-            stage[c] = reinterpret_cast<const uint4 *>(mask + site_of(c / cpr) * O)[c % cpr];
+        if (!mask_staged)       // (else the caller has copied the mask rows into stage already)
+            for (int c = lane; c < 32 * cpr; c += 32)
+                stage[c] = reinterpret_cast<const uint4 *>(mask + site_of(c / cpr) * O)[c % cpr];
         __syncwarp();
         const bf16 *m = reinterpret_cast<const bf16 *>(stage + lane * cpr);
 #pragma unroll
@@ -749,7 +760,7 @@ __global__ void __launch_bounds__(halo::THREADS) k_conv_halo_tc(const __grid_con
             const uint8_t *B = smem + LY::B_OFF + (ph & 1) * LY::W_BYTES;
             for (int j = 0; j < 27; ++j) {
                 const int dx = sign * (j % 3 - 1), dy = sign * ((j / 3) % 3 - 1), dz = sign * (j / 9 - 1);
-                const uint64_t bd = smem_desc(smem_u32(B + j * N * 16), LY::W_HALF, 128);
+                const uint64_t bd = smem_desc(smem_u32(B + slab_row(j, sign) * N * 16), LY::W_HALF, 128);
 #pragma unroll
                 for (int zz = 0; zz < TZ; ++zz) {
                     // first halo line of the shifted tile of plane zz; x offset dx + 1 within the line
@@ -940,9 +951,9 @@ struct LinePLayout {
     static constexpr int NBAR = 2 * STAGES + 5;
     static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16;
     static constexpr int NM = 3 * N;
-    static constexpr int PS = NM <= 64 ? 64 : 128;  // TMEM columns between the two planes
+    static constexpr int PS = NM;                   // TMEM columns between the two planes (adjacent)
     static constexpr int ACC_COLS = 2 * PS;         // one tile's accumulators
-    static constexpr int TMEM_COLS = 2 * ACC_COLS;  // two tiles in flight
+    static constexpr int TMEM_COLS = 2 * ACC_COLS <= 256 ? 256 : 512;  // two tiles in flight
 };
 
 template <int IP, int N>
@@ -964,7 +975,8 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + LY::NBAR * 8);
     int *consumed_sh = reinterpret_cast<int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr uint32_t idesc = instr_desc(kM, LY::NM);
+    constexpr uint32_t idesc1 = instr_desc(kM, LY::NM);      // one plane: taps dx = -1, 0, +1
+    constexpr uint32_t idesc2 = instr_desc(kM, 2 * LY::NM);  // both planes from one halo view
     constexpr int NPHASE = (IP / 16) * 3;  // (16-channel chunk, dt slab)
 
     const int Lx = g.L[0], TYL = 128 / Lx, HY = TYL + 2;
@@ -1051,19 +1063,21 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
                     const uint32_t A = smem_u32(smem + slot * LY::STAGE);
                     const uint64_t a0 = smem_desc(A, raw, 128), b0 = smem_desc(A + A_BYTES, LY::W_HALF, 128);
                     const uint32_t d0 = tmem + (uint32_t)(buf * LY::ACC_COLS);
+                    // Halo z plane zp (0..3) of the view serves plane zz = 0 with one dz tap and plane 1
+                    // with the next: the weight rows of one jy are ordered by z block Zb (slab_row), and
+                    // plane 0 at zp takes block 2 - zp, plane 1 block 3 - zp.  So zp = 1, 2 are one MMA
+                    // each with N = 2 NM (both planes, adjacent in TMEM), zp = 0 and 3 one plane each.
 #pragma unroll
-                    for (int jz = 0; jz < 3; ++jz) {
-#pragma unroll
-                        for (int jy = 0; jy < 3; ++jy) {
-                            const int dy = sign * (jy - 1), dz = sign * (jz - 1);
-                            const uint64_t bd = b0 + (uint64_t)((3 * jy + 9 * jz) * N);
-#pragma unroll
-                            for (int zz = 0; zz < TZ; ++zz) {
-                                const int l0 = (dy + 1) + HY * (zz + dz + 1);  // first halo line of the view
-                                mma_bf16(d0 + (uint32_t)(zz * LY::PS), a0 + (uint64_t)(l0 * Lx), bd, idesc,
-                                         (ph | jy | jz) != 0);
-                            }
-                        }
+                    for (int jy = 0; jy < 3; ++jy) {
+                        const int dy = sign * (jy - 1);
+                        const uint64_t av = a0 + (uint64_t)((dy + 1) * Lx);    // view of halo plane 0
+                        const uint64_t bj = b0 + (uint64_t)(9 * jy * N);       // rows of this jy, block 0
+                        const uint64_t zpl = (uint64_t)(HY * Lx);              // one halo z plane further
+                        const uint32_t first = (ph | jy) != 0;
+                        mma_bf16(d0, av, bj + (uint64_t)(6 * N), idesc1, first);                  // zp 0: plane 0
+                        mma_bf16(d0 + (uint32_t)LY::PS, av + 3 * zpl, bj, idesc1, first);       // zp 3: plane 1
+                        mma_bf16(d0, av + zpl, bj + (uint64_t)(3 * N), idesc2, 1u);              // zp 1: both
+                        mma_bf16(d0, av + 2 * zpl, bj, idesc2, 1u);                             // zp 2: both
                     }
                     mma_commit(&empty[slot]);
                 }
@@ -1083,8 +1097,22 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
         uint4 *stage = reinterpret_cast<uint4 *>(smem + LY::EPI_OFF + warp * xlp::EPI_STAGE);
         for (int k = 0; k < nt; ++k) {
             const int buf = k & 1;
+            int y0, z0, t0;
+            tile_of(k, y0, z0, t0);
+            const long first = (long)Lx * (y0 + (long)g.L[1] * ((z0 + zz) + (long)g.L[2] * t0)) + qd * 32;
+            // the tile's mask rows start on their way into the staging area while the MMAs run
+            if (mask) {
+                const int cpr = O / 8;
+                for (int c = lane; c < 32 * cpr; c += 32) {
+                    const uint32_t dst = smem_u32(stage + c);
+                    const uint4 *src = reinterpret_cast<const uint4 *>(mask + (first + c / cpr) * O) + c % cpr;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            }
             const bool landed = mbar_wait_idle(&acc_full[buf], (uint32_t)((k / 2) & 1));
             if (!__all_sync(0xffffffffu, landed)) {  // one decision per warp, the warp converged
+                if (mask) asm volatile("cp.async.wait_all;" ::: "memory");  // nothing lands after the CTA ends
                 fail = true;
                 break;
             }
@@ -1103,10 +1131,8 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[buf]);
-            int y0, z0, t0;
-            tile_of(k, y0, z0, t0);
-            const long first = (long)Lx * (y0 + (long)g.L[1] * ((z0 + zz) + (long)g.L[2] * t0)) + qd * 32;
-            epilogue_rows<N>(acc, O, bias, relu, mask, Yb, Yf, stage, lane, [&](int r) { return first + r; });
+            if (mask) asm volatile("cp.async.wait_all;" ::: "memory");
+            epilogue_rows<N>(acc, O, bias, relu, mask, Yb, Yf, stage, lane, [&](int r) { return first + r; }, true);
         }
     }
     fail = __syncthreads_or(fail);
