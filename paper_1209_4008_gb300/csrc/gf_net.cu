@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -48,6 +49,21 @@ __device__ __forceinline__ int shift_site(const Lat &g, int s, int k, int sign)
     c2 = c2 < 0 ? c2 + g.L[2] : (c2 >= g.L[2] ? c2 - g.L[2] : c2);
     c3 = c3 < 0 ? c3 + g.L[3] : (c3 >= g.L[3] ? c3 - g.L[3] : c3);
     return c0 + g.L[0] * (c1 + g.L[1] * (c2 + g.L[2] * c3));
+}
+
+// Set-up of a kernel that needs more than 48 KiB of dynamic shared memory: the attribute is set
+// once on each device (bit dev of done), and *nsm gets that device's SM count when asked for.
+static cudaError_t kernel_setup(const void *fn, int smem, std::atomic<unsigned long long> &done, int *nsm = nullptr)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!((done.load() >> dev) & 1ull)) {
+        if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+        done.fetch_or(1ull << dev);
+    }
+    return nsm ? cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, dev) : cudaSuccess;
 }
 
 // two floats rounded to BF16, packed low | high
@@ -445,12 +461,9 @@ cudaError_t conv_tc(const bf16 *X, int I, const bf16 *W, int O, const float *b, 
                     const bf16 *mask, bf16 *Yb, float *Yf, int *err, cudaStream_t s)
 {
     typedef TcLayout<IP, N> LY;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<IP, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, LY::SMEM);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{ 0 };
+    cudaError_t e = kernel_setup((const void *)k_conv_tc<IP, N>, LY::SMEM, configured);
+    if (e != cudaSuccess) return e;
     k_conv_tc<IP, N><<<(g.V + gf::tc::kM - 1) / gf::tc::kM, gf::tc::kThreads, LY::SMEM, s>>>(X, I, W, O, b, g, sign,
                                                                                           relu, mask, Yb, Yf, err);
     return cudaGetLastError();
@@ -874,15 +887,11 @@ cudaError_t conv_halo_tc(const bf16 *X, int I, const bf16 *Wblk, int O, const fl
                          int relu, const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad, cudaStream_t s)
 {
     typedef HaloLayout<N> LY;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_conv_halo_tc<IP, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, LY::SMEM);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{ 0 };
+    cudaError_t e = kernel_setup((const void *)k_conv_halo_tc<IP, N>, LY::SMEM, configured);
+    if (e != cudaSuccess) return e;
     CUtensorMap tx, tw;
-    cudaError_t e = halo_prepare(X, I, Wblk, O, N, g, 1, halo::HX, halo::HY, halo::HZ, xpad, s, &tx, &tw);
+    e = halo_prepare(X, I, Wblk, O, N, g, 1, halo::HX, halo::HY, halo::HZ, xpad, s, &tx, &tw);
     if (e != cudaSuccess) return e;
     const int blocks = (g.L[0] / halo::TX) * (g.L[1] / halo::TY) * (g.L[2] / halo::TZ) * g.L[3];
     k_conv_halo_tc<IP, N><<<blocks, halo::THREADS, LY::SMEM, s>>>(tx, tw, O, b, g, sign, relu, mask, Yb, Yf, err);
@@ -1159,17 +1168,10 @@ cudaError_t conv_line_ptc(const bf16 *X, int I, const bf16 *Wblk, int O, const f
                           int gx = 0, bool padded = false)
 {
     typedef LinePLayout<N> LY;
-    static bool configured = false;
-    static int nsm = 0;
-    cudaError_t e;
-    if (!configured) {
-        e = cudaFuncSetAttribute(k_conv_line_ptc<IP, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, LY::SMEM);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{ 0 };
+    int nsm = 0;
+    cudaError_t e = kernel_setup((const void *)k_conv_line_ptc<IP, N>, LY::SMEM, configured, &nsm);
+    if (e != cudaSuccess) return e;
     // the epilogue stages 32 rows of at most 64 bytes per warp
     if (O > 32 || (Yf && O > 16)) return cudaErrorInvalidValue;
     const int TYL = 128 / g.L[0];
@@ -1598,17 +1600,10 @@ cudaError_t conv_dw_line_tc(const bf16 *dY, int O, const bf16 *X, int I, const L
                             int *err, bf16 *xpad, bf16 *ypad, cudaStream_t s, bool x_padded = false)
 {
     typedef DwLineLayout<NP> LY;
-    static bool configured = false;
-    static int nsm = 0;
-    cudaError_t e;
-    if (!configured) {
-        e = cudaFuncSetAttribute(k_conv_dw_line_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, LY::SMEM);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{ 0 };
+    int nsm = 0;
+    cudaError_t e = kernel_setup((const void *)k_conv_dw_line_tc<NP>, LY::SMEM, configured, &nsm);
+    if (e != cudaSuccess) return e;
     const EncodeTiledFn enc = encode_tiled();
     const int G = I / 8, OG = O / 8;
     if (!enc || !xpad || !ypad || I % 8 || O % 8 || 3 * O > NP) return cudaErrorNotSupported;
@@ -1657,15 +1652,12 @@ cudaError_t conv_dw_tc(const bf16 *dY, int O, const bf16 *X, int I, const Lat &g
                        cudaStream_t s)
 {
     typedef DwLayout<IP, N> LY;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_dw_tc<IP, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, LY::SMEM);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{ 0 };
+    cudaError_t e = kernel_setup((const void *)k_conv_dw_tc<IP, N>, LY::SMEM, configured);
+    if (e != cudaSuccess) return e;
     dim3 grid((g.V + kDwChunk - 1) / kDwChunk, (81 + LY::TG - 1) / LY::TG);
     k_conv_dw_tc<IP, N><<<grid, gf::tc::kThreads, LY::SMEM, s>>>(dY, O, X, I, g, dW, err);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_bias_grad<<<256, 256, 0, s>>>(dY, O, g.V, db);
     return cudaGetLastError();
