@@ -190,23 +190,24 @@ __global__ void __launch_bounds__(256) k_conv_dw(const bf16 *__restrict__ dY, co
 __global__ void k_mse(const float *__restrict__ out, const float *__restrict__ t, long n, float inv_n,
                       bf16 *__restrict__ dout, double *__restrict__ partial)
 {
-    // four elements per step (n is a multiple of 8: 8 outputs per site)
-    double acc = 0.0;
+    // four elements per step (n is a multiple of 8: 8 outputs per site), one FP64 accumulator per
+    // lane of the float4 so that the four FMA chains run side by side
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     const long n4 = n / 4;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += (long)gridDim.x * blockDim.x) {
         const float4 o = reinterpret_cast<const float4 *>(out)[e], y = reinterpret_cast<const float4 *>(t)[e];
         const float d0 = o.x - y.x, d1 = o.y - y.y, d2 = o.z - y.z, d3 = o.w - y.w;
-        acc = fma((double)d0, (double)d0, acc);
-        acc = fma((double)d1, (double)d1, acc);
-        acc = fma((double)d2, (double)d2, acc);
-        acc = fma((double)d3, (double)d3, acc);
+        a0 = fma((double)d0, (double)d0, a0);
+        a1 = fma((double)d1, (double)d1, a1);
+        a2 = fma((double)d2, (double)d2, a2);
+        a3 = fma((double)d3, (double)d3, a3);
         uint2 g;
         g.x = pack_bf16x2(2.0f * d0 * inv_n, 2.0f * d1 * inv_n);
         g.y = pack_bf16x2(2.0f * d2 * inv_n, 2.0f * d3 * inv_n);
         reinterpret_cast<uint2 *>(dout)[e] = g;
     }
     __shared__ double red[256];
-    red[threadIdx.x] = acc;
+    red[threadIdx.x] = (a0 + a1) + (a2 + a3);
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
         if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
@@ -1870,7 +1871,7 @@ static int backward(gf_net *n, const bf16 *f, const float *target)
         return r;
     }
     long nout = (long)g.V * 8;
-    int nblk = 512;
+    int nblk = 1024;  // (n->partial holds 1024 block sums)
     k_mse<<<nblk, 256, 0, s>>>(n->out, target, nout, 1.0f / (float)nout, n->dA, n->partial);
     NCK(cudaGetLastError());
     k_sum_partials<<<1, 32, 0, s>>>(n->partial, nblk, 1.0 / (double)nout, n->dloss);
