@@ -908,13 +908,14 @@ cudaError_t conv_halo_tc(const bf16 *X, int I, const bf16 *Wblk, int O, const fl
 // three taps dx = -1, 0, +1 side by side (N = 3 x 32 columns), and the epilogue
 // adds the three column blocks with their rows moved by -dx, a lane shuffle
 // within each line that wraps around the period.  So every A view starts on a
-// whole line (a multiple of 128 bytes, where the tensor core reads shared
-// memory at full rate), the halo has no x ghosts, and a phase issues 18 MMAs
-// instead of 54 (the x-shifted views of the tile kernel above read shared
-// memory at half rate).  A phase is one 16-channel chunk and one dt slab as
-// above; its halo t-plane, 4 z x (128 / Lx + 2) y lines of Lx sites, is one TMA
-// box per 8-channel half from the ghost-padded copy, and its weights the same
-// boxes as above.  Needs Lx in {8, 16, 32}, Ly % (128 / Lx) == 0, Lz % 2 == 0.
+// whole line (a multiple of 128 bytes), the halo has no x ghosts, and a phase
+// issues 18 (dy, dz, plane) products instead of the tile kernel's 54 x-shifted
+// ones; adjacent z planes share their halo views, so those 18 products are 12
+// MMAs (k_conv_line_ptc below).  A phase is one 16-channel chunk and one dt
+// slab as above; its halo t-plane, 4 z x (128 / Lx + 2) y lines of Lx sites,
+// is one TMA box per 8-channel half from the ghost-padded copy, and its
+// weights the same boxes as above.  Needs Lx in {8, 16, 32},
+// Ly % (128 / Lx) == 0, Lz % 2 == 0.
 // ---------------------------------------------------------------------------
 namespace xline {
 constexpr int TZ = 2, HZ = TZ + 2;
