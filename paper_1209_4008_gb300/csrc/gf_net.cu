@@ -571,6 +571,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(gf::tc::smem_u32(bar)) : "memory");
 }
 
+// untiled bulk copy of bytes (a multiple of 16) from global to shared memory, completing on bar
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     gf::tc::smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(gf::tc::smem_u32(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar)
 {
     asm volatile(
@@ -639,7 +648,7 @@ template <int N, typename SiteOf>
 __device__ __forceinline__ void epilogue_rows(float (&acc)[N], int O, const float *__restrict__ bias, int relu,
                                               const bf16 *__restrict__ mask, bf16 *__restrict__ Yb,
                                               float *__restrict__ Yf, uint4 *stage, int lane, SiteOf site_of,
-                                              bool mask_staged = false)
+                                              const uint4 *mrows = nullptr)
 {
 #pragma unroll
     for (int o = 0; o < N; ++o) {
@@ -648,11 +657,13 @@ __device__ __forceinline__ void epilogue_rows(float (&acc)[N], int O, const floa
     }
     if (mask) {
         const int cpr = O / 8;  // 16-byte pieces of a BF16 row
-        if (!mask_staged)       // (else the caller has copied the mask rows into stage already)
+        if (!mrows) {           // (else the warp's 32 mask rows are in shared memory at mrows)
             for (int c = lane; c < 32 * cpr; c += 32)
                 stage[c] = reinterpret_cast<const uint4 *>(mask + site_of(c / cpr) * O)[c % cpr];
+            mrows = stage;
+        }
         __syncwarp();
-        const bf16 *m = reinterpret_cast<const bf16 *>(stage + lane * cpr);
+        const bf16 *m = reinterpret_cast<const bf16 *>(mrows + lane * cpr);
 #pragma unroll
         for (int o = 0; o < N; ++o)
             if (o < O && !(__bfloat162float(m[o]) > 0.0f)) acc[o] = 0.0f;
@@ -946,20 +957,25 @@ constexpr int EPI_STAGE = 2048;                 // per epilogue warp: 32 rows of
 constexpr int SMEM_MAX = 232448;                // opt-in shared memory per block
 }  // namespace xlp
 
-template <int N>
+template <int N, bool MASKED>
 struct LinePLayout {
     static constexpr int W_HALF = 27 * N * 16;
     static constexpr int W_BYTES = 2 * W_HALF;
     static constexpr int STAGE = xline::A_BYTES + W_BYTES;
     static constexpr int EPI_BYTES = xlp::EPI_WARPS * xlp::EPI_STAGE;
-    static constexpr int FIXED = EPI_BYTES + 1024;  // staging, barriers and slack
+    // MASKED: the ReLU mask rows of two tiles (two planes x 128 rows of at most 64 bytes each)
+    static constexpr int MASK_PLANE = 128 * 64;
+    static constexpr int MASK_BYTES = MASKED ? 2 * 2 * MASK_PLANE : 0;
+    static constexpr int FIXED = EPI_BYTES + MASK_BYTES + 1024;  // staging, masks, barriers and slack
     static constexpr int STAGES = (xlp::SMEM_MAX - FIXED) / STAGE < 4 ? (xlp::SMEM_MAX - FIXED) / STAGE : 4;
     static_assert(STAGES >= 2, "two buffers at least");
-    static constexpr int EPI_OFF = STAGES * STAGE;
+    static constexpr int MASK_OFF = STAGES * STAGE;
+    static constexpr int EPI_OFF = MASK_OFF + MASK_BYTES;
     static constexpr int BAR_OFF = EPI_OFF + EPI_BYTES;
     // bar[0..S-1] boxes landed, bar[S..2S-1] buffer free, bar[2S..2S+1] accumulator set full,
-    // bar[2S+2..2S+3] accumulator set read, bar[2S+4] drain
-    static constexpr int NBAR = 2 * STAGES + 5;
+    // bar[2S+2..2S+3] accumulator set read, bar[2S+4] drain; MASKED: bar[2S+5..2S+6] mask rows
+    // landed, bar[2S+7..2S+8] mask rows read
+    static constexpr int NBAR = 2 * STAGES + 5 + (MASKED ? 4 : 0);
     static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16;
     static constexpr int NM = 3 * N;
     static constexpr int PS = NM;                   // TMEM columns between the two planes (adjacent)
@@ -967,7 +983,7 @@ struct LinePLayout {
     static constexpr int TMEM_COLS = 2 * ACC_COLS <= 256 ? 256 : 512;  // two tiles in flight
 };
 
-template <int IP, int N>
+template <int IP, int N, bool MASKED>
 __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_constant__ CUtensorMap tx,
                                                                    const __grid_constant__ CUtensorMap tw, int O,
                                                                    const float *__restrict__ bias, Lat g, int sign,
@@ -977,12 +993,12 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
 {
     using namespace gf::tc;
     using namespace xline;
-    typedef LinePLayout<N> LY;
+    typedef LinePLayout<N, MASKED> LY;
     constexpr int S = LY::STAGES;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);
     uint64_t *full = bar, *empty = bar + S, *acc_full = bar + 2 * S, *acc_empty = bar + 2 * S + 2;
-    uint64_t *drain = bar + 2 * S + 4;
+    uint64_t *drain = bar + 2 * S + 4, *mask_full = bar + 2 * S + 5, *mask_empty = bar + 2 * S + 7;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + LY::NBAR * 8);
     int *consumed_sh = reinterpret_cast<int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1005,7 +1021,8 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
     };
 
     if (tid == 0) {
-        for (int k = 0; k < LY::NBAR; ++k) mbar_init(&bar[k], (k == 2 * S + 2 || k == 2 * S + 3) ? xlp::EPI_WARPS : 1);
+        for (int k = 0; k < LY::NBAR; ++k)
+            mbar_init(&bar[k], (k == 2 * S + 2 || k == 2 * S + 3 || k >= 2 * S + 7) ? xlp::EPI_WARPS : 1);
         *consumed_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1021,7 +1038,7 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
     const uint32_t tmem = *tmem_slot;
 
     bool fail = false;
-    int issued = 0;
+    int issued = 0, masks_issued = 0;
     if (warp == xlp::EPI_WARPS) {
         if (lane == 0) {
             // the boxes of (tile k, phase ph) into buffer q % S, q = k NPHASE + ph: the halo t-plane of
@@ -1036,6 +1053,24 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
                 const int k = q / NPHASE, ph = q - k * NPHASE;
                 int y0, z0, t0;
                 tile_of(k, y0, z0, t0);
+                if (MASKED && ph == NPHASE - 1) {
+                    // the tile's mask rows, one contiguous run of 128 sites per plane, into mask buffer
+                    // k & 1 once the epilogue has read tile k - 2's; issued with the tile's last boxes, so
+                    // that wait comes after the tile's first MMAs have been fed
+                    const int mb = k & 1;
+                    if (k >= 2 && !mbar_wait(&mask_empty[mb], (uint32_t)((k / 2 - 1) & 1))) {
+                        fail = true;
+                        break;
+                    }
+                    const uint32_t rows = 128u * (uint32_t)O * 2u;
+                    mbar_expect_tx(&mask_full[mb], 2 * rows);
+                    for (int zz = 0; zz < TZ; ++zz) {
+                        const long first = (long)Lx * (y0 + (long)g.L[1] * ((z0 + zz) + (long)g.L[2] * t0));
+                        bulk_load(smem + LY::MASK_OFF + (mb * 2 + zz) * LY::MASK_PLANE, mask + first * O, rows,
+                                  &mask_full[mb]);
+                    }
+                    masks_issued = k + 1;
+                }
                 const int ch0 = 16 * (ph / 3), slab = ph % 3;
                 const int ht = sign > 0 ? slab : 2 - slab;
                 mbar_expect_tx(&full[slot], 2 * raw + (uint32_t)LY::W_BYTES);
@@ -1111,19 +1146,9 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
             int y0, z0, t0;
             tile_of(k, y0, z0, t0);
             const long first = (long)Lx * (y0 + (long)g.L[1] * ((z0 + zz) + (long)g.L[2] * t0)) + qd * 32;
-            // the tile's mask rows start on their way into the staging area while the MMAs run
-            if (mask) {
-                const int cpr = O / 8;
-                for (int c = lane; c < 32 * cpr; c += 32) {
-                    const uint32_t dst = smem_u32(stage + c);
-                    const uint4 *src = reinterpret_cast<const uint4 *>(mask + (first + c / cpr) * O) + c % cpr;
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-                }
-                asm volatile("cp.async.commit_group;" ::: "memory");
-            }
-            const bool landed = mbar_wait_idle(&acc_full[buf], (uint32_t)((k / 2) & 1));
+            bool landed = mbar_wait_idle(&acc_full[buf], (uint32_t)((k / 2) & 1));
+            if (MASKED) landed = landed && mbar_wait_idle(&mask_full[buf], (uint32_t)((k / 2) & 1));
             if (!__all_sync(0xffffffffu, landed)) {  // one decision per warp, the warp converged
-                if (mask) asm volatile("cp.async.wait_all;" ::: "memory");  // nothing lands after the CTA ends
                 fail = true;
                 break;
             }
@@ -1142,16 +1167,31 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[buf]);
-            if (mask) asm volatile("cp.async.wait_all;" ::: "memory");
-            epilogue_rows<N>(acc, O, bias, relu, mask, Yb, Yf, stage, lane, [&](int r) { return first + r; }, true);
+            // MASKED: this warp's 32 mask rows, as the TMA warp copied them
+            const uint4 *mrows = MASKED ? reinterpret_cast<const uint4 *>(smem + LY::MASK_OFF +
+                                                                           (buf * 2 + zz) * LY::MASK_PLANE +
+                                                                           qd * 32 * O * 2)
+                                        : nullptr;
+            epilogue_rows<N>(acc, O, bias, relu, MASKED ? mask : nullptr, Yb, Yf, stage, lane,
+                             [&](int r) { return first + r; }, mrows);
+            if (MASKED) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&mask_empty[buf]);
+            }
         }
     }
     fail = __syncthreads_or(fail);
     if (fail) {
         if (tid == 0) atomicExch(err, GF_ETIMEOUT);
         // boxes issued but not consumed land before the buffers go away (bounded)
-        if (warp == xlp::EPI_WARPS && lane == 0)
+        if (warp == xlp::EPI_WARPS && lane == 0) {
             for (int q = *consumed_sh; q < issued; ++q) mbar_wait(&full[q % S], (uint32_t)((q / S) & 1));
+            // the last mask copy into each buffer (an earlier one was read before it was issued)
+            for (int mb = 0; mb < 2; ++mb) {
+                const int uses = (masks_issued + 1 - mb) / 2;  // tiles k < masks_issued with k & 1 == mb
+                if (MASKED && uses > 0) mbar_wait(&mask_full[mb], (uint32_t)((uses - 1) & 1));
+            }
+        }
     }
     fence_before_sync();
     __syncthreads();
@@ -1164,15 +1204,15 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
 
 // X [V][I] through the padded copy into the persistent x-line kernel (gx: x ghosts in the copy;
 // padded: xpad already holds it); Wblk = the weights blocked by 8 input channels
-template <int IP, int N>
-cudaError_t conv_line_ptc(const bf16 *X, int I, const bf16 *Wblk, int O, const float *b, const Lat &g, int sign,
-                          int relu, const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad, cudaStream_t s,
-                          int gx = 0, bool padded = false)
+template <int IP, int N, bool MASKED>
+cudaError_t conv_line_ptc_launch(const bf16 *X, int I, const bf16 *Wblk, int O, const float *b, const Lat &g,
+                                 int sign, int relu, const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad,
+                                 cudaStream_t s, int gx, bool padded)
 {
-    typedef LinePLayout<N> LY;
+    typedef LinePLayout<N, MASKED> LY;
     static std::atomic<unsigned long long> configured{ 0 };
     int nsm = 0;
-    cudaError_t e = kernel_setup((const void *)k_conv_line_ptc<IP, N>, LY::SMEM, configured, &nsm);
+    cudaError_t e = kernel_setup((const void *)k_conv_line_ptc<IP, N, MASKED>, LY::SMEM, configured, &nsm);
     if (e != cudaSuccess) return e;
     // the epilogue stages 32 rows of at most 64 bytes per warp
     if (O > 32 || (Yf && O > 16)) return cudaErrorInvalidValue;
@@ -1181,9 +1221,22 @@ cudaError_t conv_line_ptc(const bf16 *X, int I, const bf16 *Wblk, int O, const f
     e = halo_prepare(X, I, Wblk, O, N, g, gx, g.L[0], TYL + 2, xline::HZ, xpad, s, &tx, &tw, padded);
     if (e != cudaSuccess) return e;
     const int tiles = (g.L[1] / TYL) * (g.L[2] / xline::TZ) * g.L[3];
-    k_conv_line_ptc<IP, N><<<std::min(tiles, nsm), xlp::THREADS, LY::SMEM, s>>>(tx, tw, O, b, g, sign, relu, mask,
-                                                                                Yb, Yf, err, 8 * gx);
+    k_conv_line_ptc<IP, N, MASKED><<<std::min(tiles, nsm), xlp::THREADS, LY::SMEM, s>>>(tx, tw, O, b, g, sign, relu,
+                                                                                        mask, Yb, Yf, err, 8 * gx);
     return cudaGetLastError();
+}
+
+// (a ReLU mask selects the variant that stages the mask rows with the boxes)
+template <int IP, int N>
+cudaError_t conv_line_ptc(const bf16 *X, int I, const bf16 *Wblk, int O, const float *b, const Lat &g, int sign,
+                          int relu, const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad, cudaStream_t s,
+                          int gx = 0, bool padded = false)
+{
+    if (mask)
+        return conv_line_ptc_launch<IP, N, true>(X, I, Wblk, O, b, g, sign, relu, mask, Yb, Yf, err, xpad, s, gx,
+                                                 padded);
+    return conv_line_ptc_launch<IP, N, false>(X, I, Wblk, O, b, g, sign, relu, mask, Yb, Yf, err, xpad, s, gx,
+                                              padded);
 }
 
 // ---------------------------------------------------------------------------
