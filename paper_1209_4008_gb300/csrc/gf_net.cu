@@ -638,6 +638,62 @@ __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float *v)
     for (int o = 0; o < N; ++o) v[o] = __uint_as_float(r[o]);
 }
 
+// coordinate c on an axis of extent L >= 3 with gh ghost sites on each side (padded index p
+// holds (p - gh) mod L) sits at padded index c + gh and, when gh = 1 and c is on a face, at
+// the ghost on the far side: image 1 is that ghost's index, or -1
+__device__ __forceinline__ int padded_image(int i, int c, int L, int gh)
+{
+    if (i == 0) return c + gh;
+    return !gh ? -1 : c == L - 1 ? 0 : c == 0 ? L + 1 : -1;
+}
+
+// One row of a convolution's output (site (x, y, z, t), O channels in acc) into
+// the ghost-padded copy that the next convolution reads, blocked by 8
+// channels: Yp[c][pt][pz][py][px][8] with gx ghost sites in x and one in y, z
+// and t (the layout k_pad_periodic writes).  The row goes to every padded
+// position holding the site, so no copy pass is needed.  Lanes with
+// consecutive x write consecutive 16-byte pieces.
+template <int N>
+__device__ __forceinline__ void store_padded_row(const float (&acc)[N], int O, bf16 *__restrict__ Yp, int gx,
+                                                 const Lat &g, int x, int y, int z, int t)
+{
+    const int Px = g.L[0] + 2 * gx, Py = g.L[1] + 2, Pz = g.L[2] + 2;
+    const long P = (long)Px * Py * Pz * (g.L[3] + 2);
+    uint4 u[N / 8];
+#pragma unroll
+    for (int c = 0; c < N / 8; ++c) {
+        u[c].x = pack_bf16x2(acc[8 * c + 0], acc[8 * c + 1]);
+        u[c].y = pack_bf16x2(acc[8 * c + 2], acc[8 * c + 3]);
+        u[c].z = pack_bf16x2(acc[8 * c + 4], acc[8 * c + 5]);
+        u[c].w = pack_bf16x2(acc[8 * c + 6], acc[8 * c + 7]);
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(Yp);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int pt = padded_image(it, t, g.L[3], 1);
+        if (pt < 0) continue;
+#pragma unroll
+        for (int iz = 0; iz < 2; ++iz) {
+            const int pz = padded_image(iz, z, g.L[2], 1);
+            if (pz < 0) continue;
+#pragma unroll
+            for (int iy = 0; iy < 2; ++iy) {
+                const int py = padded_image(iy, y, g.L[1], 1);
+                if (py < 0) continue;
+                const long line = (((long)pt * Pz + pz) * Py + py) * Px;
+#pragma unroll
+                for (int ix = 0; ix < 2; ++ix) {
+                    const int px = padded_image(ix, x, g.L[0], gx);
+                    if (px < 0) continue;
+#pragma unroll
+                    for (int c = 0; c < N / 8; ++c)
+                        if (c < O / 8) dst[(long)c * P + line + px] = u[c];
+                }
+            }
+        }
+    }
+}
+
 // The epilogue of one warp's 32 accumulator rows (row r of the warp is the
 // site site_of(r); this thread holds row lane in acc): bias, ReLU, the mask,
 // then BF16 (Yb) or FP32 (Yf) rows of O channels.  Mask and output rows pass
@@ -963,8 +1019,9 @@ struct LinePLayout {
     static constexpr int W_BYTES = 2 * W_HALF;
     static constexpr int STAGE = xline::A_BYTES + W_BYTES;
     static constexpr int EPI_BYTES = xlp::EPI_WARPS * xlp::EPI_STAGE;
-    // MASKED: the ReLU mask rows of two tiles (two planes x 128 rows of at most 64 bytes each)
-    static constexpr int MASK_PLANE = 128 * 64;
+    // MASKED: the ReLU mask of two tiles (two planes x up to 4 channel groups x 128 sites x 16 bytes)
+    static constexpr int MASK_GROUP = 128 * 16;
+    static constexpr int MASK_PLANE = 4 * MASK_GROUP;
     static constexpr int MASK_BYTES = MASKED ? 2 * 2 * MASK_PLANE : 0;
     static constexpr int FIXED = EPI_BYTES + MASK_BYTES + 1024;  // staging, masks, barriers and slack
     static constexpr int STAGES = (xlp::SMEM_MAX - FIXED) / STAGE < 4 ? (xlp::SMEM_MAX - FIXED) / STAGE : 4;
@@ -989,6 +1046,7 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
                                                                    const float *__restrict__ bias, Lat g, int sign,
                                                                    int relu, const bf16 *__restrict__ mask,
                                                                    bf16 *__restrict__ Yb, float *__restrict__ Yf,
+                                                                   bf16 *__restrict__ Yp, int ygx,
                                                                    int *__restrict__ err, int x0)
 {
     using namespace gf::tc;
@@ -1054,21 +1112,24 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
                 int y0, z0, t0;
                 tile_of(k, y0, z0, t0);
                 if (MASKED && ph == NPHASE - 1) {
-                    // the tile's mask rows, one contiguous run of 128 sites per plane, into mask buffer
-                    // k & 1 once the epilogue has read tile k - 2's; issued with the tile's last boxes, so
-                    // that wait comes after the tile's first MMAs have been fed
+                    // the tile's mask: in the padded copy without x ghosts, one channel group of a plane's
+                    // 128 sites is one contiguous run of 2 KB; the O / 8 groups of both planes go into mask
+                    // buffer k & 1 once the epilogue has read tile k - 2's (issued with the tile's last
+                    // boxes, so that wait comes after the tile's first MMAs have been fed)
                     const int mb = k & 1;
                     if (k >= 2 && !mbar_wait(&mask_empty[mb], (uint32_t)((k / 2 - 1) & 1))) {
                         fail = true;
                         break;
                     }
-                    const uint32_t rows = 128u * (uint32_t)O * 2u;
-                    mbar_expect_tx(&mask_full[mb], 2 * rows);
-                    for (int zz = 0; zz < TZ; ++zz) {
-                        const long first = (long)Lx * (y0 + (long)g.L[1] * ((z0 + zz) + (long)g.L[2] * t0));
-                        bulk_load(smem + LY::MASK_OFF + (mb * 2 + zz) * LY::MASK_PLANE, mask + first * O, rows,
-                                  &mask_full[mb]);
-                    }
+                    const int MG = O / 8;
+                    const long Py = g.L[1] + 2, Pz = g.L[2] + 2, Pt = g.L[3] + 2;
+                    mbar_expect_tx(&mask_full[mb], (uint32_t)(TZ * MG * LY::MASK_GROUP));
+                    for (int zz = 0; zz < TZ; ++zz)
+                        for (int c = 0; c < MG; ++c) {
+                            const long run = ((((long)c * Pt + t0 + 1) * Pz + z0 + zz + 1) * Py + y0 + 1) * Lx;
+                            bulk_load(smem + LY::MASK_OFF + (mb * TZ + zz) * LY::MASK_PLANE + c * LY::MASK_GROUP,
+                                      mask + 8 * run, LY::MASK_GROUP, &mask_full[mb]);
+                        }
                     masks_issued = k + 1;
                 }
                 const int ch0 = 16 * (ph / 3), slab = ph % 3;
@@ -1167,16 +1228,33 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[buf]);
-            // MASKED: this warp's 32 mask rows, as the TMA warp copied them
-            const uint4 *mrows = MASKED ? reinterpret_cast<const uint4 *>(smem + LY::MASK_OFF +
-                                                                           (buf * 2 + zz) * LY::MASK_PLANE +
-                                                                           qd * 32 * O * 2)
-                                        : nullptr;
-            epilogue_rows<N>(acc, O, bias, relu, MASKED ? mask : nullptr, Yb, Yf, stage, lane,
-                             [&](int r) { return first + r; }, mrows);
-            if (MASKED) {
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&mask_empty[buf]);
+            if (Yp) {
+                // bias, ReLU and the mask (MASKED: this row's channel groups as the TMA warp copied them),
+                // then the row straight into the padded copy Yp
+#pragma unroll
+                for (int o = 0; o < N; ++o) {
+                    const float v = acc[o] + (bias && o < O ? bias[o] : 0.0f);
+                    acc[o] = relu && !(v > 0.0f) ? 0.0f : v;
+                }
+                if (MASKED) {
+                    const uint8_t *mrow = smem + LY::MASK_OFF + (buf * TZ + zz) * LY::MASK_PLANE + row * 16;
+#pragma unroll
+                    for (int c = 0; c < N / 8; ++c)
+                        if (c < O / 8) {
+                            const uint4 u = *reinterpret_cast<const uint4 *>(mrow + c * LY::MASK_GROUP);
+                            const uint32_t w[4] = { u.x, u.y, u.z, u.w };
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const uint16_t h = (uint16_t)(w[j / 2] >> (16 * (j % 2)));
+                                if (!(__bfloat162float(__ushort_as_bfloat16(h)) > 0.0f)) acc[8 * c + j] = 0.0f;
+                            }
+                        }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&mask_empty[buf]);
+                }
+                store_padded_row<N>(acc, O, Yp, ygx, g, x, y0 + row / Lx, z0 + zz, t0);
+            } else {
+                epilogue_rows<N>(acc, O, bias, relu, nullptr, Yb, Yf, stage, lane, [&](int r) { return first + r; });
             }
         }
     }
@@ -1206,37 +1284,41 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
 // padded: xpad already holds it); Wblk = the weights blocked by 8 input channels
 template <int IP, int N, bool MASKED>
 cudaError_t conv_line_ptc_launch(const bf16 *X, int I, const bf16 *Wblk, int O, const float *b, const Lat &g,
-                                 int sign, int relu, const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad,
-                                 cudaStream_t s, int gx, bool padded)
+                                 int sign, int relu, const bf16 *mask, bf16 *Yb, float *Yf, bf16 *Yp, int ygx,
+                                 int *err, bf16 *xpad, cudaStream_t s, int gx, bool padded)
 {
     typedef LinePLayout<N, MASKED> LY;
     static std::atomic<unsigned long long> configured{ 0 };
     int nsm = 0;
     cudaError_t e = kernel_setup((const void *)k_conv_line_ptc<IP, N, MASKED>, LY::SMEM, configured, &nsm);
     if (e != cudaSuccess) return e;
-    // the epilogue stages 32 rows of at most 64 bytes per warp
-    if (O > 32 || (Yf && O > 16)) return cudaErrorInvalidValue;
+    // the epilogue stages 32 rows of at most 64 bytes per warp; one output; the mask is read from a
+    // padded copy, so it goes with a padded output
+    if (O > 32 || O % 8 || (Yf && O > 16) || (Yb != nullptr) + (Yf != nullptr) + (Yp != nullptr) != 1 ||
+        (MASKED && !Yp) || ygx < 0 || ygx > 1)
+        return cudaErrorInvalidValue;
     const int TYL = 128 / g.L[0];
     CUtensorMap tx, tw;
     e = halo_prepare(X, I, Wblk, O, N, g, gx, g.L[0], TYL + 2, xline::HZ, xpad, s, &tx, &tw, padded);
     if (e != cudaSuccess) return e;
     const int tiles = (g.L[1] / TYL) * (g.L[2] / xline::TZ) * g.L[3];
-    k_conv_line_ptc<IP, N, MASKED><<<std::min(tiles, nsm), xlp::THREADS, LY::SMEM, s>>>(tx, tw, O, b, g, sign, relu,
-                                                                                        mask, Yb, Yf, err, 8 * gx);
+    k_conv_line_ptc<IP, N, MASKED><<<std::min(tiles, nsm), xlp::THREADS, LY::SMEM, s>>>(
+        tx, tw, O, b, g, sign, relu, mask, Yb, Yf, Yp, ygx, err, 8 * gx);
     return cudaGetLastError();
 }
 
-// (a ReLU mask selects the variant that stages the mask rows with the boxes)
+// (a ReLU mask, itself a padded copy without x ghosts, selects the variant that stages it with
+// the boxes; Yp, ygx: the output as a padded copy with ygx x ghosts instead of rows Yb or Yf)
 template <int IP, int N>
 cudaError_t conv_line_ptc(const bf16 *X, int I, const bf16 *Wblk, int O, const float *b, const Lat &g, int sign,
-                          int relu, const bf16 *mask, bf16 *Yb, float *Yf, int *err, bf16 *xpad, cudaStream_t s,
-                          int gx = 0, bool padded = false)
+                          int relu, const bf16 *mask, bf16 *Yb, float *Yf, bf16 *Yp, int ygx, int *err, bf16 *xpad,
+                          cudaStream_t s, int gx, bool padded)
 {
     if (mask)
-        return conv_line_ptc_launch<IP, N, true>(X, I, Wblk, O, b, g, sign, relu, mask, Yb, Yf, err, xpad, s, gx,
-                                                 padded);
-    return conv_line_ptc_launch<IP, N, false>(X, I, Wblk, O, b, g, sign, relu, mask, Yb, Yf, err, xpad, s, gx,
-                                              padded);
+        return conv_line_ptc_launch<IP, N, true>(X, I, Wblk, O, b, g, sign, relu, mask, Yb, Yf, Yp, ygx, err, xpad,
+                                                 s, gx, padded);
+    return conv_line_ptc_launch<IP, N, false>(X, I, Wblk, O, b, g, sign, relu, mask, Yb, Yf, Yp, ygx, err, xpad, s,
+                                              gx, padded);
 }
 
 // ---------------------------------------------------------------------------
@@ -1649,10 +1731,11 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
 
 // dW and db of one layer through the x-line weight-gradient kernel: X [V][I] is
 // padded without x ghosts into xpad (unless x_padded: xpad holds it already),
-// dY [V][O] with them into ypad
+// dY [V][O] with them into ypad (unless y_padded)
 template <int NP>
 cudaError_t conv_dw_line_tc(const bf16 *dY, int O, const bf16 *X, int I, const Lat &g, float *dW, float *db,
-                            int *err, bf16 *xpad, bf16 *ypad, cudaStream_t s, bool x_padded = false)
+                            int *err, bf16 *xpad, bf16 *ypad, cudaStream_t s, bool x_padded = false,
+                            bool y_padded = false)
 {
     typedef DwLineLayout<NP> LY;
     static std::atomic<unsigned long long> configured{ 0 };
@@ -1672,8 +1755,10 @@ cudaError_t conv_dw_line_tc(const bf16 *dY, int O, const bf16 *X, int I, const L
         k_pad_periodic<<<(int)std::min<long>((px + 255) / 256, 152L * 32), 256, 0, s>>>(X, I, g, 0, xpad);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_pad_periodic<<<(int)std::min<long>((py + 255) / 256, 152L * 32), 256, 0, s>>>(dY, O, g, 1, ypad);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!y_padded) {
+        k_pad_periodic<<<(int)std::min<long>((py + 255) / 256, 152L * 32), 256, 0, s>>>(dY, O, g, 1, ypad);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const cuuint64_t es = sizeof(bf16);
     const cuuint64_t Py = g.L[1] + 2, Pz = g.L[2] + 2, Pt = g.L[3] + 2;
     const cuuint32_t ones[5] = { 1, 1, 1, 1, 1 };
@@ -1696,6 +1781,7 @@ cudaError_t conv_dw_line_tc(const bf16 *dY, int O, const bf16 *X, int I, const L
     k_conv_dw_line_tc<NP><<<NT * R, dwline::THREADS, LY::SMEM, s>>>(tmap[0], tmap[1], I, O, CH, g, dW, db, err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (3 * CH >= 16) {  // no free M column for the ones: the bias gradient on its own
+        if (!dY) return cudaErrorInvalidValue;
         k_bias_grad<<<256, 256, 0, s>>>(dY, O, g.V, db);
         return cudaGetLastError();
     }
@@ -1749,11 +1835,12 @@ struct gf_net {
     float *out = nullptr;
     bf16 *dA = nullptr, *dB = nullptr;  // [V][32] gradient scratch (ping-pong)
     bf16 *xpad = nullptr;  // halo-tile convolutions: the input with periodic ghost sites, up to 80 channels
-    bf16 *ypad = nullptr;  // x-line weight gradients: dY with periodic ghost sites, up to 32 channels
-    // training on the x-line path: each layer's input as the forward pass padded it (no x
-    // ghosts), kept for the weight gradients; keep is set while backward() runs
+    // x-line weight gradients: dY with periodic ghost sites (x included), up to 32 channels; on the
+    // x-line path the data gradients write their output into the other one of the two
+    bf16 *ypad = nullptr, *ypad2 = nullptr;
+    // x-line path: each layer's input as a padded copy without x ghosts; layer 1's is padded from
+    // the features, the others are written by the previous layer's epilogue (act[] is unused there)
     bf16 *xin[4] = { nullptr };
-    int keep = 0;
     double *partial = nullptr, *dloss = nullptr;
     int *derr = nullptr;  // tensor-core kernels: bounded-wait expiry
     int use_tc = 1;       // forward and backward-data on tcgen05 (else CUDA cores)
@@ -1796,38 +1883,100 @@ static int refresh_weights(gf_net *n)
     return GF_OK;
 }
 
-// forward / backward-data convolution on the tensor cores: with conv_halo 1 the
-// x-line kernel, else (or with conv_halo 2) the halo-tile kernel, where the
-// extents allow them; otherwise the per-tap gather kernel
-// (W = weights [81][O][I], Wblk = the same blocked by 8 input channels)
-// (pad, gx, padded: on the x-line path, the padded copy to use instead of n->xpad, its x
-// ghosts, and whether it holds X already)
+// the x-line path (forward_line, backward_line): conv_halo 1 on a lattice the x-line kernels take
+static bool line_path(const gf_net *n) { return n->use_tc && n->use_halo == 1 && line_ok(n->g) && n->ypad2; }
+
+// forward / backward-data convolution on the tensor cores off the x-line path: the
+// halo-tile kernel where the extents allow it and conv_halo is not 0, otherwise
+// the per-tap gather kernel (W = weights [81][O][I], Wblk = the same blocked by 8
+// input channels)
 template <int IP, int N>
 static cudaError_t conv_tensor(const gf_net *n, const bf16 *X, int I, const bf16 *W, const bf16 *Wblk, int O,
-                               const float *b, int sign, int relu, const bf16 *mask, bf16 *Yb, float *Yf,
-                               bf16 *pad = nullptr, int gx = 0, bool padded = false)
+                               const float *b, int sign, int relu, const bf16 *mask, bf16 *Yb, float *Yf)
 {
-    if (n->use_halo == 1 && line_ok(n->g))
-        return conv_line_ptc<IP, N>(X, I, Wblk, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, pad ? pad : n->xpad,
-                                    n->stream, gx, padded);
     if (n->use_halo != 0 && halo_ok(n->g))
         return conv_halo_tc<IP, N>(X, I, Wblk, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->xpad, n->stream);
     return conv_tc<IP, N>(X, I, W, O, b, n->g, sign, relu, mask, Yb, Yf, n->derr, n->stream);
 }
 
-// weight and bias gradients of one layer on the tensor cores: with conv_halo 1
-// the x-line kernel where the extents allow it, otherwise the gather kernel
-// (xin: X as the forward pass padded it, or nullptr)
+// weight and bias gradients of one layer on the tensor cores off the x-line path:
+// with conv_halo 1 the x-line weight-gradient kernel where the extents allow it
+// (Lz odd, say), otherwise the gather kernel
 template <int IP, int N>
-static cudaError_t dw_tensor(const gf_net *n, const bf16 *dY, int O, const bf16 *X, int I, float *dW, float *db,
-                             bf16 *xin = nullptr)
+static cudaError_t dw_tensor(const gf_net *n, const bf16 *dY, int O, const bf16 *X, int I, float *dW, float *db)
 {
     if (n->use_halo == 1 && n->ypad && dw_line_ok(n->g)) {
-        bf16 *xp = xin ? xin : n->xpad;
-        if (O <= 8) return conv_dw_line_tc<32>(dY, O, X, I, n->g, dW, db, n->derr, xp, n->ypad, n->stream, xin);
-        return conv_dw_line_tc<96>(dY, O, X, I, n->g, dW, db, n->derr, xp, n->ypad, n->stream, xin);
+        if (O <= 8) return conv_dw_line_tc<32>(dY, O, X, I, n->g, dW, db, n->derr, n->xpad, n->ypad, n->stream);
+        return conv_dw_line_tc<96>(dY, O, X, I, n->g, dW, db, n->derr, n->xpad, n->ypad, n->stream);
     }
     return conv_dw_tc<IP, N>(dY, O, X, I, n->g, dW, db, n->derr, n->stream);
+}
+
+// the padded layer inputs of the x-line path
+static int ensure_line_buffers(gf_net *n)
+{
+    if (n->xin[0]) return GF_OK;
+    const long P = padded_sites(n->g, 0);
+    for (int l = 0; l < 4; ++l) {
+        const cudaError_t e = cudaMalloc(&n->xin[l], sizeof(bf16) * P * kC[l]);
+        if (e != cudaSuccess) {
+            for (int k = 0; k < 4; ++k) {
+                cudaFree(n->xin[k]);
+                n->xin[k] = nullptr;
+            }
+            return nfail(n, e == cudaErrorMemoryAllocation ? GF_ENOMEM : GF_ECUDA,
+                         std::string("padded layer inputs: ") + cudaGetErrorString(e));
+        }
+    }
+    return GF_OK;
+}
+
+// forward pass on the x-line path: the features are padded into xin[0]; each
+// layer's epilogue writes the next layer's padded input xin[l + 1] itself
+static int forward_line(gf_net *n, const bf16 *f)
+{
+    const int r = ensure_line_buffers(n);
+    if (r != GF_OK) return r;
+    const Lat &g = n->g;
+    cudaStream_t s = n->stream;
+    bf16 *const *xi = n->xin;
+    NCK((conv_line_ptc<80, 32>(f, 80, n->Wh[0], 32, n->params + n->boff[0], g, 1, 1, nullptr, nullptr, nullptr,
+                               xi[1], 0, n->derr, xi[0], s, 0, false)));
+    NCK((conv_line_ptc<32, 32>(nullptr, 32, n->Wh[1], 32, n->params + n->boff[1], g, 1, 1, nullptr, nullptr,
+                               nullptr, xi[2], 0, n->derr, xi[1], s, 0, true)));
+    NCK((conv_line_ptc<32, 32>(nullptr, 32, n->Wh[2], 32, n->params + n->boff[2], g, 1, 1, nullptr, nullptr,
+                               nullptr, xi[3], 0, n->derr, xi[2], s, 0, true)));
+    NCK((conv_line_ptc<32, 16>(nullptr, 32, n->Wh[3], 8, n->params + n->boff[3], g, 1, 0, nullptr, nullptr, n->out,
+                               nullptr, 0, n->derr, xi[3], s, 0, true)));
+    return GF_OK;
+}
+
+// backward pass on the x-line path after forward_line, from dY of layer 4 (n->dA):
+// the weight gradient of layer 4 pads dY into ypad (x ghosts included); from there
+// each data gradient reads dY from one padded copy, masks by the layer's padded
+// input and writes its output into the other copy, which the weight gradient of
+// the layer below and the next data gradient read as they are
+static int backward_line(gf_net *n, const bf16 *f)
+{
+    const Lat &g = n->g;
+    cudaStream_t s = n->stream;
+    bf16 *const *xi = n->xin;
+    bf16 *yp[2] = { n->ypad, n->ypad2 };
+    NCK((conv_dw_line_tc<32>(n->dA, 8, nullptr, 32, g, n->grad + n->woff[3], n->grad + n->boff[3], n->derr, xi[3],
+                             yp[0], s, true, false)));
+    NCK((conv_line_ptc<16, 32>(nullptr, 8, n->Wth[3], 32, nullptr, g, -1, 0, xi[3], nullptr, nullptr, yp[1], 1,
+                               n->derr, yp[0], s, 1, true)));
+    int cur = 1;  // yp[cur] holds dY of layer l
+    for (int l = 2; l >= 1; --l) {
+        NCK((conv_dw_line_tc<96>(nullptr, 32, nullptr, 32, g, n->grad + n->woff[l], n->grad + n->boff[l], n->derr,
+                                 xi[l], yp[cur], s, true, true)));
+        NCK((conv_line_ptc<32, 32>(nullptr, 32, n->Wth[l], 32, nullptr, g, -1, 0, xi[l], nullptr, nullptr,
+                                   yp[1 - cur], 1, n->derr, yp[cur], s, 1, true)));
+        cur = 1 - cur;
+    }
+    NCK((conv_dw_line_tc<96>(nullptr, 32, f, 80, g, n->grad + n->woff[0], n->grad + n->boff[0], n->derr, xi[0],
+                             yp[cur], s, true, true)));
+    return GF_OK;
 }
 
 static int forward(gf_net *n, const bf16 *f)
@@ -1835,17 +1984,16 @@ static int forward(gf_net *n, const bf16 *f)
     const Lat &g = n->g;
     cudaStream_t s = n->stream;
     n->act[0] = const_cast<bf16 *>(f);
+    if (line_path(n)) return forward_line(n, f);
     if (n->use_tc) {
-        // while training on the x-line path each layer's padded input is kept (xin) for its weight gradient
-        bf16 *const *kp = n->keep ? n->xin : nullptr;
         NCK((conv_tensor<80, 32>(n, f, 80, n->Wb[0], n->Wh[0], 32, n->params + n->boff[0], 1, 1, nullptr, n->act[1],
-                                 nullptr, kp ? kp[0] : nullptr)));
+                                 nullptr)));
         NCK((conv_tensor<32, 32>(n, n->act[1], 32, n->Wb[1], n->Wh[1], 32, n->params + n->boff[1], 1, 1, nullptr,
-                                 n->act[2], nullptr, kp ? kp[1] : nullptr)));
+                                 n->act[2], nullptr)));
         NCK((conv_tensor<32, 32>(n, n->act[2], 32, n->Wb[2], n->Wh[2], 32, n->params + n->boff[2], 1, 1, nullptr,
-                                 n->act[3], nullptr, kp ? kp[2] : nullptr)));
+                                 n->act[3], nullptr)));
         NCK((conv_tensor<32, 16>(n, n->act[3], 32, n->Wb[3], n->Wh[3], 8, n->params + n->boff[3], 1, 0, nullptr,
-                                 nullptr, n->out, kp ? kp[3] : nullptr)));
+                                 nullptr, n->out)));
         return GF_OK;
     }
     NCK((conv_cc<80, 32>(f, n->Wb[0], n->params + n->boff[0], g, 1, 1, nullptr, n->act[1], nullptr, s)));
@@ -1855,23 +2003,16 @@ static int forward(gf_net *n, const bf16 *f)
     return GF_OK;
 }
 
-// backward data of layer l (l = 3, 2, 1): dX = conv^T(dY) masked by act[l] > 0
+// backward data of layer l (l = 3, 2, 1) off the x-line path: dX = conv^T(dY) masked by act[l] > 0
 static int backward_data(gf_net *n, int l, const bf16 *dY, bf16 *dX)
 {
     const Lat &g = n->g;
     cudaStream_t s = n->stream;
-    // while training on the x-line path, the weight gradient of this layer has just padded dY
-    // with x ghosts into ypad: read it from there
-    bf16 *yp = n->keep ? n->ypad : nullptr;
     if (l == 3) {
-        if (n->use_tc)
-            NCK((conv_tensor<16, 32>(n, dY, 8, n->Wt[3], n->Wth[3], 32, nullptr, -1, 0, n->act[3], dX, nullptr, yp,
-                                     yp ? 1 : 0, yp != nullptr)));
+        if (n->use_tc) NCK((conv_tensor<16, 32>(n, dY, 8, n->Wt[3], n->Wth[3], 32, nullptr, -1, 0, n->act[3], dX, nullptr)));
         else NCK((conv_cc<8, 32>(dY, n->Wt[3], nullptr, g, -1, 0, n->act[3], dX, nullptr, s)));
     } else {
-        if (n->use_tc)
-            NCK((conv_tensor<32, 32>(n, dY, 32, n->Wt[l], n->Wth[l], 32, nullptr, -1, 0, n->act[l], dX, nullptr, yp,
-                                     yp ? 1 : 0, yp != nullptr)));
+        if (n->use_tc) NCK((conv_tensor<32, 32>(n, dY, 32, n->Wt[l], n->Wth[l], 32, nullptr, -1, 0, n->act[l], dX, nullptr)));
         else NCK((conv_cc<32, 32>(dY, n->Wt[l], nullptr, g, -1, 0, n->act[l], dX, nullptr, s)));
     }
     return GF_OK;
@@ -1890,40 +2031,12 @@ static int check_status(gf_net *n)
 }
 
 // forward + loss + backward into n->grad; loss left in n->dloss (device)
-// the padded layer inputs kept by a training forward pass on the x-line path
-static int ensure_train_buffers(gf_net *n)
-{
-    if (n->xin[0] || !(n->use_tc && n->use_halo == 1 && line_ok(n->g))) return GF_OK;
-    const long P = padded_sites(n->g, 0);
-    for (int l = 0; l < 4; ++l) {
-        const cudaError_t e = cudaMalloc(&n->xin[l], sizeof(bf16) * P * kC[l]);
-        if (e != cudaSuccess) {
-            for (int k = 0; k < 4; ++k) {
-                cudaFree(n->xin[k]);
-                n->xin[k] = nullptr;
-            }
-            return nfail(n, e == cudaErrorMemoryAllocation ? GF_ENOMEM : GF_ECUDA,
-                         std::string("padded layer inputs: ") + cudaGetErrorString(e));
-        }
-    }
-    return GF_OK;
-}
-
-
 static int backward(gf_net *n, const bf16 *f, const float *target)
 {
     const Lat &g = n->g;
     cudaStream_t s = n->stream;
-    int r = ensure_train_buffers(n);
+    int r = forward(n, f);
     if (r != GF_OK) return r;
-    // x-line path: the forward pass keeps its padded layer inputs for the weight gradients, and the
-    // data gradients read dY from the copy the weight gradients padded (line_ok implies dw_line_ok)
-    n->keep = n->use_tc && n->use_halo == 1 && line_ok(g) && n->xin[0] && n->ypad;
-    r = forward(n, f);
-    if (r != GF_OK) {
-        n->keep = 0;
-        return r;
-    }
     long nout = (long)g.V * 8;
     int nblk = 1024;  // (n->partial holds 1024 block sums)
     k_mse<<<nblk, 256, 0, s>>>(n->out, target, nout, 1.0f / (float)nout, n->dA, n->partial);
@@ -1931,34 +2044,29 @@ static int backward(gf_net *n, const bf16 *f, const float *target)
     k_sum_partials<<<1, 32, 0, s>>>(n->partial, nblk, 1.0 / (double)nout, n->dloss);
     NCK(cudaGetLastError());
     NCK(cudaMemsetAsync(n->grad, 0, sizeof(float) * n->np, s));
+    if (line_path(n)) return backward_line(n, f);
     // layer 4: dY = dA [V][8]
-    bf16 *const *kx = n->keep ? n->xin : nullptr;
     if (n->use_tc)
-        NCK((dw_tensor<32, 16>(n, n->dA, 8, n->act[3], 32, n->grad + n->woff[3], n->grad + n->boff[3],
-                               kx ? kx[3] : nullptr)));
+        NCK((dw_tensor<32, 16>(n, n->dA, 8, n->act[3], 32, n->grad + n->woff[3], n->grad + n->boff[3])));
     else NCK((conv_dw<32, 8>(n->dA, n->act[3], g, n->grad + n->woff[3], n->grad + n->boff[3], s)));
     r = backward_data(n, 3, n->dA, n->dB);
     if (r != GF_OK) return r;
     // layer 3
     if (n->use_tc)
-        NCK((dw_tensor<32, 32>(n, n->dB, 32, n->act[2], 32, n->grad + n->woff[2], n->grad + n->boff[2],
-                               kx ? kx[2] : nullptr)));
+        NCK((dw_tensor<32, 32>(n, n->dB, 32, n->act[2], 32, n->grad + n->woff[2], n->grad + n->boff[2])));
     else NCK((conv_dw<32, 32>(n->dB, n->act[2], g, n->grad + n->woff[2], n->grad + n->boff[2], s)));
     r = backward_data(n, 2, n->dB, n->dA);
     if (r != GF_OK) return r;
     // layer 2
     if (n->use_tc)
-        NCK((dw_tensor<32, 32>(n, n->dA, 32, n->act[1], 32, n->grad + n->woff[1], n->grad + n->boff[1],
-                               kx ? kx[1] : nullptr)));
+        NCK((dw_tensor<32, 32>(n, n->dA, 32, n->act[1], 32, n->grad + n->woff[1], n->grad + n->boff[1])));
     else NCK((conv_dw<32, 32>(n->dA, n->act[1], g, n->grad + n->woff[1], n->grad + n->boff[1], s)));
     r = backward_data(n, 1, n->dA, n->dB);
     if (r != GF_OK) return r;
     // layer 1 (no input gradient needed)
     if (n->use_tc)
-        NCK((dw_tensor<128, 32>(n, n->dB, 32, f, 80, n->grad + n->woff[0], n->grad + n->boff[0],
-                                kx ? kx[0] : nullptr)));
+        NCK((dw_tensor<128, 32>(n, n->dB, 32, f, 80, n->grad + n->woff[0], n->grad + n->boff[0])));
     else NCK((conv_dw<80, 32>(n->dB, f, g, n->grad + n->woff[0], n->grad + n->boff[0], s)));
-    n->keep = 0;
     return GF_OK;
 }
 
@@ -2016,6 +2124,7 @@ static int ensure_buffers(gf_net *n)
     if (halo_ok(n->g) || line_ok(n->g) || dw_line_ok(n->g))
         NCK(cudaMalloc(&n->xpad, sizeof(bf16) * padded_sites(n->g) * GF_NET_CIN));
     if (dw_line_ok(n->g)) NCK(cudaMalloc(&n->ypad, sizeof(bf16) * padded_sites(n->g) * 32));
+    if (line_ok(n->g)) NCK(cudaMalloc(&n->ypad2, sizeof(bf16) * padded_sites(n->g) * 32));
     NCK(cudaMalloc(&n->partial, sizeof(double) * 1024));
     NCK(cudaMalloc(&n->dloss, sizeof(double)));
     NCK(cudaMalloc(&n->derr, sizeof(int)));
@@ -2042,6 +2151,7 @@ int gf_net_destroy(gf_net *n)
     cudaFree(n->dB);
     cudaFree(n->xpad);
     cudaFree(n->ypad);
+    cudaFree(n->ypad2);
     for (int l = 0; l < 4; ++l) cudaFree(n->xin[l]);
     cudaFree(n->partial);
     cudaFree(n->dloss);

@@ -191,11 +191,16 @@ def exact_network(dims, seed, nnz=(12, 6, 3, 6)):
 
 # net option conv_halo of each convolution path: 1 = x-line kernel where Lx is
 # 8, 16 or 32, 2 = halo-tile kernel (Lx % 8, Ly % 16, Lz % 2), both falling back
-# to the per-tap gather kernel (0) where the extents do not allow them
+# to the per-tap gather kernel (0) where the extents do not allow them.  On the
+# x-line path every layer writes the next one's ghost-padded input itself; with
+# Lz odd, (16, 8, 3, 4), conv_halo 1 runs the x-line weight-gradient kernel
+# beside the gather convolutions instead.
 CONV_HALO = {"gather": 0, "xline": 1, "halo_tile": 2, "cuda_cores": 0}
 
 
-@pytest.mark.parametrize("dims", [(8, 16, 4, 4), (16, 32, 4, 4), (32, 4, 4, 3), (6, 4, 6, 10), (16, 16, 8, 8)])
+@pytest.mark.parametrize(
+    "dims", [(8, 16, 4, 4), (16, 32, 4, 4), (32, 4, 4, 3), (6, 4, 6, 10), (16, 16, 8, 8), (16, 8, 3, 4)]
+)
 @pytest.mark.parametrize("path", ["gather", "xline", "halo_tile", "cuda_cores"])
 def test_network_exact_arithmetic_matches_oracle_bit_for_bit(dims, path):
     params, X0, target, out_exact = exact_network(dims, seed=sum(dims))
