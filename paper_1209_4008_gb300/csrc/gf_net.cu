@@ -186,36 +186,6 @@ __global__ void __launch_bounds__(256) k_conv_dw(const bf16 *__restrict__ dY, co
     }
 }
 
-// loss partials and the output gradient dOut = 2 (out - t) / n (BF16)
-__global__ void k_mse(const float *__restrict__ out, const float *__restrict__ t, long n, float inv_n,
-                      bf16 *__restrict__ dout, double *__restrict__ partial)
-{
-    // four elements per step (n is a multiple of 8: 8 outputs per site), one FP64 accumulator per
-    // lane of the float4 so that the four FMA chains run side by side
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    const long n4 = n / 4;
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += (long)gridDim.x * blockDim.x) {
-        const float4 o = reinterpret_cast<const float4 *>(out)[e], y = reinterpret_cast<const float4 *>(t)[e];
-        const float d0 = o.x - y.x, d1 = o.y - y.y, d2 = o.z - y.z, d3 = o.w - y.w;
-        a0 = fma((double)d0, (double)d0, a0);
-        a1 = fma((double)d1, (double)d1, a1);
-        a2 = fma((double)d2, (double)d2, a2);
-        a3 = fma((double)d3, (double)d3, a3);
-        uint2 g;
-        g.x = pack_bf16x2(2.0f * d0 * inv_n, 2.0f * d1 * inv_n);
-        g.y = pack_bf16x2(2.0f * d2 * inv_n, 2.0f * d3 * inv_n);
-        reinterpret_cast<uint2 *>(dout)[e] = g;
-    }
-    __shared__ double red[256];
-    red[threadIdx.x] = (a0 + a1) + (a2 + a3);
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
-}
-
 // one warp, fixed order: lane l sums partials l, l + 32, ..., then a shuffle tree
 __global__ void k_sum_partials(const double *p, int n, double scale, double *out)
 {
@@ -692,6 +662,73 @@ __device__ __forceinline__ void store_padded_row(const float (&acc)[N], int O, b
             }
         }
     }
+}
+
+// Knuth's two-sum: s + e == a + b exactly (round to nearest, no reassociation)
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// The loss partials and dY of the last layer, one site (8 outputs) per step:
+// d = out - target in FP32, dY = 2 d / n in BF16, and sum d^2 into partial[block].
+// Each square is an exact pair p + e (p = d d rounded, e = fma(d, d, -p)); a
+// site's 8 pairs are summed in FP32 with two-sum (the rounding errors collected
+// in a second word), and the two words enter the thread's FP64 accumulator:
+// four operations of the slow FP64 pipe per site instead of 16.  Exact where the
+// sums fit in the two words; else the site sum is off by a few units of 2^-48 of it.
+// PADDED: dY goes into the ghost-padded copy with x ghosts, one channel group
+// (the layout k_pad_periodic writes), at every padded position of the site.
+template <bool PADDED>
+__global__ void k_mse(const float *__restrict__ out, const float *__restrict__ t, Lat g, float inv_n,
+                      bf16 *__restrict__ dout, double *__restrict__ partial)
+{
+    double acc = 0.0;
+    for (long s = (long)blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += (long)gridDim.x * blockDim.x) {
+        const float4 *o4 = reinterpret_cast<const float4 *>(out) + 2 * s;
+        const float4 *y4 = reinterpret_cast<const float4 *>(t) + 2 * s;
+        const float4 oa = o4[0], ob = o4[1], ya = y4[0], yb = y4[1];
+        float d[8] = { oa.x - ya.x, oa.y - ya.y, oa.z - ya.z, oa.w - ya.w,
+                       ob.x - yb.x, ob.y - yb.y, ob.z - yb.z, ob.w - yb.w };
+        float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float p = __fmul_rn(d[j], d[j]);
+            const float e = __fmaf_rn(d[j], d[j], -p);
+            float r;
+            two_sum_f(hi, p, hi, r);
+            lo = __fadd_rn(lo, __fadd_rn(r, e));
+        }
+        acc += (double)hi;
+        acc += (double)lo;
+        float gr[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) gr[j] = 2.0f * d[j] * inv_n;
+        if (PADDED) {
+            const int x = (int)(s % g.L[0]);
+            long r = s / g.L[0];
+            const int y = (int)(r % g.L[1]);
+            r /= g.L[1];
+            store_padded_row<8>(gr, 8, dout, 1, g, x, y, (int)(r % g.L[2]), (int)(r / g.L[2]));
+        } else {
+            uint4 u;
+            u.x = pack_bf16x2(gr[0], gr[1]);
+            u.y = pack_bf16x2(gr[2], gr[3]);
+            u.z = pack_bf16x2(gr[4], gr[5]);
+            u.w = pack_bf16x2(gr[6], gr[7]);
+            reinterpret_cast<uint4 *>(dout)[s] = u;
+        }
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
 // The epilogue of one warp's 32 accumulator rows (row r of the warp is the
@@ -1525,7 +1562,6 @@ __global__ void k_bias_grad(const bf16 *__restrict__ dY, int O, int V, float *__
 // bounded.
 // ---------------------------------------------------------------------------
 namespace dwline {
-constexpr int STAGES = 3;
 constexpr int SLOT_MAX = 3072;            // one M column: 128 / Lx + 2 lines of Lx sites x 16 bytes (Lx = 32)
 constexpr int A_BYTES = 16 * SLOT_MAX;    // 16 M columns of an MMA (only 3 CH <= 15 are loaded)
 constexpr int B_BOX = 128 * 16;           // 128 sites x 8 channels
@@ -1537,10 +1573,13 @@ struct DwLineLayout {
     static_assert(NP % 32 == 0 && NP <= 128, "accumulator read in blocks of 32 columns");
     static constexpr int B_BYTES = (NP / 8) * dwline::B_BOX;
     static constexpr int STAGE = dwline::A_BYTES + B_BYTES;
+    // as many stages as fit, up to four (NP = 32: 4 of 56 KB, NP = 96: 3 of 72 KB)
+    static constexpr int STAGES = (xlp::SMEM_MAX - 256) / STAGE < 4 ? (xlp::SMEM_MAX - 256) / STAGE : 4;
+    static_assert(STAGES >= 2, "two buffers at least");
     // bar[0..S-1] boxes landed, bar[S..2S-1] MMAs done with the buffer, bar[2S] accumulators final,
     // bar[2S+1] drain
-    static constexpr int NBAR = 2 * dwline::STAGES + 2;
-    static constexpr int BAR_OFF = dwline::STAGES * STAGE;
+    static constexpr int NBAR = 2 * STAGES + 2;
+    static constexpr int BAR_OFF = STAGES * STAGE;
     static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16;
     static constexpr int TMEM_COLS = 3 * NP <= 128 ? 128 : (3 * NP <= 256 ? 256 : 512);
 };
@@ -1579,7 +1618,7 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
     using namespace gf::tc;
     using dwline::B_BOX;
     typedef DwLineLayout<NP> LY;
-    constexpr int S = dwline::STAGES;
+    constexpr int S = LY::STAGES;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);
     uint64_t *acc_done = &bar[2 * S], *drain = &bar[2 * S + 1];
@@ -1951,19 +1990,19 @@ static int forward_line(gf_net *n, const bf16 *f)
     return GF_OK;
 }
 
-// backward pass on the x-line path after forward_line, from dY of layer 4 (n->dA):
-// the weight gradient of layer 4 pads dY into ypad (x ghosts included); from there
-// each data gradient reads dY from one padded copy, masks by the layer's padded
-// input and writes its output into the other copy, which the weight gradient of
-// the layer below and the next data gradient read as they are
+// backward pass on the x-line path after forward_line, from dY of layer 4 as the
+// loss kernel wrote it into ypad (ghost-padded, x ghosts included): each data
+// gradient reads dY from one padded copy, masks by the layer's padded input and
+// writes its output into the other copy, which the weight gradient of the layer
+// below and the next data gradient read as they are
 static int backward_line(gf_net *n, const bf16 *f)
 {
     const Lat &g = n->g;
     cudaStream_t s = n->stream;
     bf16 *const *xi = n->xin;
     bf16 *yp[2] = { n->ypad, n->ypad2 };
-    NCK((conv_dw_line_tc<32>(n->dA, 8, nullptr, 32, g, n->grad + n->woff[3], n->grad + n->boff[3], n->derr, xi[3],
-                             yp[0], s, true, false)));
+    NCK((conv_dw_line_tc<32>(nullptr, 8, nullptr, 32, g, n->grad + n->woff[3], n->grad + n->boff[3], n->derr,
+                             xi[3], yp[0], s, true, true)));
     NCK((conv_line_ptc<16, 32>(nullptr, 8, n->Wth[3], 32, nullptr, g, -1, 0, xi[3], nullptr, nullptr, yp[1], 1,
                                n->derr, yp[0], s, 1, true)));
     int cur = 1;  // yp[cur] holds dY of layer l
@@ -2039,7 +2078,9 @@ static int backward(gf_net *n, const bf16 *f, const float *target)
     if (r != GF_OK) return r;
     long nout = (long)g.V * 8;
     int nblk = 1024;  // (n->partial holds 1024 block sums)
-    k_mse<<<nblk, 256, 0, s>>>(n->out, target, nout, 1.0f / (float)nout, n->dA, n->partial);
+    // x-line path: dY of layer 4 straight into the padded copy its weight gradient reads
+    if (line_path(n)) k_mse<true><<<nblk, 256, 0, s>>>(n->out, target, g, 1.0f / (float)nout, n->ypad, n->partial);
+    else k_mse<false><<<nblk, 256, 0, s>>>(n->out, target, g, 1.0f / (float)nout, n->dA, n->partial);
     NCK(cudaGetLastError());
     k_sum_partials<<<1, 32, 0, s>>>(n->partial, nblk, 1.0 / (double)nout, n->dloss);
     NCK(cudaGetLastError());
