@@ -367,10 +367,13 @@ int gf_net_gradient(gf_net *n, const void *features, const float *target, float 
  * 0, use the per-tap gather kernel.  Other values: GF_EINVAL.  With 1 and
  * Lx = 8, 16 or 32, Ly % (128 / Lx) == 0, the weight and bias gradients are
  * GEMMs over the site sum with both operands staged by TMA from ghost-padded
- * copies (otherwise a gather kernel); where the x-line tiles apply, gradient
- * and train calls also keep each layer's padded input of the forward pass
- * for its weight gradient (extra device memory: Lx (Ly+2) (Lz+2) (Lt+2)
- * x 176 BF16 values, allocated on the first such call).  Forward, gradient
+ * copies (otherwise a gather kernel); where the x-line tiles apply, each
+ * layer's input exists only as such a copy, written by the previous layer's
+ * epilogue (the features are copied into theirs), and so does the output
+ * gradient of each layer in the backward pass (extra device memory:
+ * Lx (Ly+2) (Lz+2) (Lt+2) x 176 BF16 values, allocated on the first forward,
+ * gradient or train call, beside two dY copies of (Lx+2) (Ly+2) (Lz+2) (Lt+2)
+ * x 32 BF16 values allocated at creation).  Forward, gradient
  * and train calls synchronise the stream and return GF_ETIMEOUT if a bounded
  * wait in a tensor-core kernel expired. */
 int gf_net_set_option(gf_net *n, const char *key, double value);
