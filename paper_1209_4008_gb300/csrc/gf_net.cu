@@ -1050,16 +1050,20 @@ constexpr int EPI_STAGE = 2048;                 // per epilogue warp: 32 rows of
 constexpr int SMEM_MAX = 232448;                // opt-in shared memory per block
 }  // namespace xlp
 
-template <int N, bool MASKED>
+// MB: mask buffers (0 = no ReLU mask)
+template <int N, int MB>
 struct LinePLayout {
+    static constexpr bool MASKED = MB > 0;
     static constexpr int W_HALF = 27 * N * 16;
     static constexpr int W_BYTES = 2 * W_HALF;
     static constexpr int STAGE = xline::A_BYTES + W_BYTES;
-    static constexpr int EPI_BYTES = xlp::EPI_WARPS * xlp::EPI_STAGE;
-    // MASKED: the ReLU mask of two tiles (two planes x up to 4 channel groups x 128 sites x 16 bytes)
+    // MASKED: the output goes into a padded copy (no staging area) and MB buffers hold the ReLU
+    // mask of a tile each (two planes x up to 4 channel groups x 128 sites x 16 bytes)
+    static constexpr int EPI_BYTES = MASKED ? 0 : xlp::EPI_WARPS * xlp::EPI_STAGE;
     static constexpr int MASK_GROUP = 128 * 16;
     static constexpr int MASK_PLANE = 4 * MASK_GROUP;
-    static constexpr int MASK_BYTES = MASKED ? 2 * 2 * MASK_PLANE : 0;
+    static constexpr int MASK_TILE = 2 * MASK_PLANE;
+    static constexpr int MASK_BYTES = MB * MASK_TILE;
     static constexpr int FIXED = EPI_BYTES + MASK_BYTES + 1024;  // staging, masks, barriers and slack
     static constexpr int STAGES = (xlp::SMEM_MAX - FIXED) / STAGE < 4 ? (xlp::SMEM_MAX - FIXED) / STAGE : 4;
     static_assert(STAGES >= 2, "two buffers at least");
@@ -1067,15 +1071,23 @@ struct LinePLayout {
     static constexpr int EPI_OFF = MASK_OFF + MASK_BYTES;
     static constexpr int BAR_OFF = EPI_OFF + EPI_BYTES;
     // bar[0..S-1] boxes landed, bar[S..2S-1] buffer free, bar[2S..2S+1] accumulator set full,
-    // bar[2S+2..2S+3] accumulator set read, bar[2S+4] drain; MASKED: bar[2S+5..2S+6] mask rows
-    // landed, bar[2S+7..2S+8] mask rows read
-    static constexpr int NBAR = 2 * STAGES + 5 + (MASKED ? 4 : 0);
+    // bar[2S+2..2S+3] accumulator set read, bar[2S+4] drain; MASKED: bar[2S+5..2S+4+MB] mask
+    // landed, bar[2S+5+MB..2S+4+2MB] mask read
+    static constexpr int NBAR = 2 * STAGES + 5 + 2 * MB;
     static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16;
     static constexpr int NM = 3 * N;
     static constexpr int PS = NM;                   // TMEM columns between the two planes (adjacent)
     static constexpr int ACC_COLS = 2 * PS;         // one tile's accumulators
     static constexpr int TMEM_COLS = 2 * ACC_COLS <= 256 ? 256 : 512;  // two tiles in flight
 };
+
+// (mask buffers of the masked variant: two where a tile has only three phases (IP = 16), so the
+// TMA warp can run a tile ahead; one elsewhere, which leaves room for four stages)
+template <int IP, bool MASKED>
+constexpr int line_mask_bufs()
+{
+    return MASKED ? (IP <= 16 ? 2 : 1) : 0;
+}
 
 template <int IP, int N, bool MASKED>
 __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_constant__ CUtensorMap tx,
@@ -1088,12 +1100,14 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
 {
     using namespace gf::tc;
     using namespace xline;
-    typedef LinePLayout<N, MASKED> LY;
+    constexpr int MB = line_mask_bufs<IP, MASKED>();
+    constexpr int MBD = MB > 0 ? MB : 1;  // (divisor in code that runs only when MASKED)
+    typedef LinePLayout<N, MB> LY;
     constexpr int S = LY::STAGES;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + LY::BAR_OFF);
     uint64_t *full = bar, *empty = bar + S, *acc_full = bar + 2 * S, *acc_empty = bar + 2 * S + 2;
-    uint64_t *drain = bar + 2 * S + 4, *mask_full = bar + 2 * S + 5, *mask_empty = bar + 2 * S + 7;
+    uint64_t *drain = bar + 2 * S + 4, *mask_full = bar + 2 * S + 5, *mask_empty = bar + 2 * S + 5 + MB;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + LY::BAR_OFF + LY::NBAR * 8);
     int *consumed_sh = reinterpret_cast<int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1117,7 +1131,7 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
 
     if (tid == 0) {
         for (int k = 0; k < LY::NBAR; ++k)
-            mbar_init(&bar[k], (k == 2 * S + 2 || k == 2 * S + 3 || k >= 2 * S + 7) ? xlp::EPI_WARPS : 1);
+            mbar_init(&bar[k], (k == 2 * S + 2 || k == 2 * S + 3 || k >= 2 * S + 5 + MB) ? xlp::EPI_WARPS : 1);
         *consumed_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1150,11 +1164,11 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
                 tile_of(k, y0, z0, t0);
                 if (MASKED && ph == NPHASE - 1) {
                     // the tile's mask: in the padded copy without x ghosts, one channel group of a plane's
-                    // 128 sites is one contiguous run of 2 KB; the O / 8 groups of both planes go into mask
-                    // buffer k & 1 once the epilogue has read tile k - 2's (issued with the tile's last
-                    // boxes, so that wait comes after the tile's first MMAs have been fed)
-                    const int mb = k & 1;
-                    if (k >= 2 && !mbar_wait(&mask_empty[mb], (uint32_t)((k / 2 - 1) & 1))) {
+                    // 128 sites is one contiguous run of 2 KB; the O / 8 groups of both planes go into
+                    // mask buffer k % MB once the epilogue has read tile k - MB's (issued with the tile's
+                    // last boxes: that epilogue has begun before the tile's first MMAs)
+                    const int mb = k % MBD;
+                    if (k >= MB && !mbar_wait(&mask_empty[mb], (uint32_t)((k / MBD - 1) & 1))) {
                         fail = true;
                         break;
                     }
@@ -1164,7 +1178,8 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
                     for (int zz = 0; zz < TZ; ++zz)
                         for (int c = 0; c < MG; ++c) {
                             const long run = ((((long)c * Pt + t0 + 1) * Pz + z0 + zz + 1) * Py + y0 + 1) * Lx;
-                            bulk_load(smem + LY::MASK_OFF + (mb * TZ + zz) * LY::MASK_PLANE + c * LY::MASK_GROUP,
+                            bulk_load(smem + LY::MASK_OFF + mb * LY::MASK_TILE + zz * LY::MASK_PLANE +
+                                          c * LY::MASK_GROUP,
                                       mask + 8 * run, LY::MASK_GROUP, &mask_full[mb]);
                         }
                     masks_issued = k + 1;
@@ -1238,14 +1253,16 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
         const int zz = warp >> 2, qd = warp & 3, row = qd * 32 + lane;
         const int x = row & (Lx - 1), seg = lane & ~(Lx - 1);
         const int from_left = seg | ((x + Lx - 1) & (Lx - 1)), from_right = seg | ((x + 1) & (Lx - 1));
-        uint4 *stage = reinterpret_cast<uint4 *>(smem + LY::EPI_OFF + warp * xlp::EPI_STAGE);
+        // (MASKED writes a padded copy and has no staging area)
+        uint4 *stage = MASKED ? nullptr : reinterpret_cast<uint4 *>(smem + LY::EPI_OFF + warp * xlp::EPI_STAGE);
         for (int k = 0; k < nt; ++k) {
             const int buf = k & 1;
             int y0, z0, t0;
             tile_of(k, y0, z0, t0);
             const long first = (long)Lx * (y0 + (long)g.L[1] * ((z0 + zz) + (long)g.L[2] * t0)) + qd * 32;
             bool landed = mbar_wait_idle(&acc_full[buf], (uint32_t)((k / 2) & 1));
-            if (MASKED) landed = landed && mbar_wait_idle(&mask_full[buf], (uint32_t)((k / 2) & 1));
+            const int mb = k % MBD;
+            if (MASKED) landed = landed && mbar_wait_idle(&mask_full[mb], (uint32_t)((k / MBD) & 1));
             if (!__all_sync(0xffffffffu, landed)) {  // one decision per warp, the warp converged
                 fail = true;
                 break;
@@ -1265,7 +1282,7 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[buf]);
-            if (Yp) {
+            if (MASKED || Yp) {
                 // bias, ReLU and the mask (MASKED: this row's channel groups as the TMA warp copied them),
                 // then the row straight into the padded copy Yp
 #pragma unroll
@@ -1274,7 +1291,7 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
                     acc[o] = relu && !(v > 0.0f) ? 0.0f : v;
                 }
                 if (MASKED) {
-                    const uint8_t *mrow = smem + LY::MASK_OFF + (buf * TZ + zz) * LY::MASK_PLANE + row * 16;
+                    const uint8_t *mrow = smem + LY::MASK_OFF + mb * LY::MASK_TILE + zz * LY::MASK_PLANE + row * 16;
 #pragma unroll
                     for (int c = 0; c < N / 8; ++c)
                         if (c < O / 8) {
@@ -1287,7 +1304,7 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
                             }
                         }
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&mask_empty[buf]);
+                    if (lane == 0) mbar_arrive(&mask_empty[mb]);
                 }
                 store_padded_row<N>(acc, O, Yp, ygx, g, x, y0 + row / Lx, z0 + zz, t0);
             } else {
@@ -1301,10 +1318,10 @@ __global__ void __launch_bounds__(xlp::THREADS, 1) k_conv_line_ptc(const __grid_
         // boxes issued but not consumed land before the buffers go away (bounded)
         if (warp == xlp::EPI_WARPS && lane == 0) {
             for (int q = *consumed_sh; q < issued; ++q) mbar_wait(&full[q % S], (uint32_t)((q / S) & 1));
-            // the last mask copy into each buffer (an earlier one was read before it was issued)
-            for (int mb = 0; mb < 2; ++mb) {
-                const int uses = (masks_issued + 1 - mb) / 2;  // tiles k < masks_issued with k & 1 == mb
-                if (MASKED && uses > 0) mbar_wait(&mask_full[mb], (uint32_t)((uses - 1) & 1));
+            // the last mask copy into each buffer (an earlier one was read before the next was issued)
+            for (int b = 0; b < MB; ++b) {
+                const int uses = (masks_issued - b + MB - 1) / MBD;  // tiles k < masks_issued with k % MB == b
+                if (uses > 0) mbar_wait(&mask_full[b], (uint32_t)((uses - 1) & 1));
             }
         }
     }
@@ -1324,7 +1341,7 @@ cudaError_t conv_line_ptc_launch(const bf16 *X, int I, const bf16 *Wblk, int O, 
                                  int sign, int relu, const bf16 *mask, bf16 *Yb, float *Yf, bf16 *Yp, int ygx,
                                  int *err, bf16 *xpad, cudaStream_t s, int gx, bool padded)
 {
-    typedef LinePLayout<N, MASKED> LY;
+    typedef LinePLayout<N, line_mask_bufs<IP, MASKED>()> LY;
     static std::atomic<unsigned long long> configured{ 0 };
     int nsm = 0;
     cudaError_t e = kernel_setup((const void *)k_conv_line_ptc<IP, N, MASKED>, LY::SMEM, configured, &nsm);
