@@ -740,8 +740,7 @@ __global__ void k_mse(const float *__restrict__ out, const float *__restrict__ t
 template <int N, typename SiteOf>
 __device__ __forceinline__ void epilogue_rows(float (&acc)[N], int O, const float *__restrict__ bias, int relu,
                                               const bf16 *__restrict__ mask, bf16 *__restrict__ Yb,
-                                              float *__restrict__ Yf, uint4 *stage, int lane, SiteOf site_of,
-                                              const uint4 *mrows = nullptr)
+                                              float *__restrict__ Yf, uint4 *stage, int lane, SiteOf site_of)
 {
 #pragma unroll
     for (int o = 0; o < N; ++o) {
@@ -750,13 +749,10 @@ __device__ __forceinline__ void epilogue_rows(float (&acc)[N], int O, const floa
     }
     if (mask) {
         const int cpr = O / 8;  // 16-byte pieces of a BF16 row
-        if (!mrows) {           // (else the warp's 32 mask rows are in shared memory at mrows)
-            for (int c = lane; c < 32 * cpr; c += 32)
-                stage[c] = reinterpret_cast<const uint4 *>(mask + site_of(c / cpr) * O)[c % cpr];
-            mrows = stage;
-        }
+        for (int c = lane; c < 32 * cpr; c += 32)
+            stage[c] = reinterpret_cast<const uint4 *>(mask + site_of(c / cpr) * O)[c % cpr];
         __syncwarp();
-        const bf16 *m = reinterpret_cast<const bf16 *>(mrows + lane * cpr);
+        const bf16 *m = reinterpret_cast<const bf16 *>(stage + lane * cpr);
 #pragma unroll
         for (int o = 0; o < N; ++o)
             if (o < O && !(__bfloat162float(m[o]) > 0.0f)) acc[o] = 0.0f;
