@@ -1622,7 +1622,7 @@ __device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr, uint32_t lbo_k, 
 }
 
 // grid = 3 * nchunk * R CTAs: CTA b has dt = b / (nchunk R) - 1, channel chunk (b / R) % nchunk, member b % R
-template <int NP>
+template <int NP, int TD>
 __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __grid_constant__ CUtensorMap tx,
                                                                      const __grid_constant__ CUtensorMap ty, int I,
                                                                      int O, int CH, Lat g, float *__restrict__ dW,
@@ -1642,15 +1642,19 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
     constexpr uint32_t idesc = instr_desc(kM, NP) | (1u << 15) | (1u << 16);
     const int G = I / 8, OG = O / 8, Lx = g.L[0], TYL = 128 / Lx, nby = g.L[1] / TYL;
     const uint32_t line = (uint32_t)Lx * 16, slot = (uint32_t)(TYL + 2) * line;
-    const int nchunk = (G + CH - 1) / CH, R = gridDim.x / (3 * nchunk);
+    // TD = 1: a CTA type per (dt, chunk); TD = 3: dt rides on dY as dx does, a type per chunk
+    const int nchunk = (G + CH - 1) / CH, R = gridDim.x / ((3 / TD) * nchunk);
     const int type = blockIdx.x / R, member = blockIdx.x - type * R;
-    const int dti = type / nchunk, g0 = (type - dti * nchunk) * CH, nch = min(CH, G - g0);
+    const int dti = TD == 3 ? 1 : type / nchunk, g0 = (type - (TD == 3 ? 0 : dti) * nchunk) * CH;
+    const int nch = min(CH, G - g0);
+    constexpr int BIAS_BLK = TD == 3 ? 4 : 1;  // column block of dt = 0, dx = 0
     const int NS = g.V / 128;
     const int n = member < NS ? (NS - member + R - 1) / R : 0;  // stages member, member + R, ...
 
-    // M columns beyond 3 nch and the N padding stay zero, except that the CTAs of dt = 0 and
-    // the first chunk fill M column 3 CH (never loaded) with ones in every buffer: its first
-    // row of the dy = -1 accumulator is then sum_s dY[s - dx][o], the bias gradient at dx = 0
+    // M columns beyond 3 nch and the N padding stay zero, except that the CTAs of dt = 0 (all,
+    // TD = 3) and the first chunk fill M column 3 CH (never loaded) with ones in every buffer:
+    // its first row of the dy = -1 accumulator is then sum_s dY[s - (dx, 0, 0, dt)][o], the
+    // bias gradient in the column block of dx = dt = 0
     const bool bias = dti == 1 && g0 == 0 && 3 * CH < 16;
     const uint32_t ones_lo = bias ? (uint32_t)(3 * CH) * slot : 0u, ones_hi = bias ? ones_lo + slot : 0u;
     for (int e = tid; e < LY::BAR_OFF / 16; e += dwline::THREADS) {
@@ -1680,7 +1684,7 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
     int issued = 0;
     if (warp == 4 && lane == 0) {
         // producer: the boxes of stage p into buffer p % S once the MMAs of stage p - S are done
-        const uint32_t bytes = (uint32_t)(3 * nch) * slot + (uint32_t)(3 * OG) * B_BOX;
+        const uint32_t bytes = (uint32_t)(3 * nch) * slot + (uint32_t)(3 * TD * OG) * B_BOX;
         for (int p = 0; p < n; ++p) {
             const int b = p % S;
             if (p >= S && !mbar_wait(&bar[S + b], (uint32_t)((p / S - 1) & 1))) {
@@ -1694,9 +1698,12 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
             mbar_expect_tx(&bar[b], bytes);
             // padded coordinates: lines y0 - 1 .. (padded y0), planes z - 1 .. z + 1 (padded z), t + dt
             tma_load_5d(A, &tx, 0, y0, z, t + dti, g0, &bar[b]);
-            // dY at x - dx: padded x from 1 - dx, dx = dxi - 1
-            for (int dxi = 0; dxi < 3; ++dxi)
-                tma_load_5d(B + dxi * OG * B_BOX, &ty, 8 * (2 - dxi), y0 + 1, z + 1, t + 1, 0, &bar[b]);
+            // dY at x - dx: padded x from 1 - dx, dx = dxi - 1; TD = 3: and at t - dt, padded t
+            // 2 + t - dtc, dt = dtc - 1 (the X box above is then at dt = 0), column block 3 dtc + dxi
+            for (int dtc = 0; dtc < TD; ++dtc)
+                for (int dxi = 0; dxi < 3; ++dxi)
+                    tma_load_5d(B + (3 * dtc + dxi) * OG * B_BOX, &ty, 8 * (2 - dxi), y0 + 1, z + 1,
+                                TD == 3 ? t + 2 - dtc : t + 1, 0, &bar[b]);
             issued = p + 1;
         }
     } else if (warp == 5 && lane == 0) {
@@ -1739,7 +1746,7 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
             fence_after_sync();
 #pragma unroll 1
             for (int dyi = 0; dyi < 3; ++dyi) {
-                const int k0 = 3 * dyi + 9 * dzi + 27 * dti;  // tap of dx = -1
+                const int k0 = 3 * dyi + 9 * dzi;  // tap of dx = -1, dt = -1
 #pragma unroll 1
                 for (int c0 = 0; c0 < NP; c0 += 32) {
                     float v[32];
@@ -1748,16 +1755,17 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
 #pragma unroll
                         for (int c = 0; c < 32; ++c) {
                             const int col = c0 + c;
-                            if (col >= O && col < 2 * O) atomicAdd(&db[col - O], v[c]);
+                            if (col >= BIAS_BLK * O && col < (BIAS_BLK + 1) * O) atomicAdd(&db[col - BIAS_BLK * O], v[c]);
                         }
                     }
                     if (gl < nch) {
 #pragma unroll
                         for (int c = 0; c < 32; ++c) {
-                            const int col = c0 + c;  // (dx + 1) O + o
-                            if (col < 3 * O) {
-                                const int dxi = col / O, o = col - dxi * O;
-                                atomicAdd(&dW[((long)(k0 + dxi) * O + o) * I + i], v[c]);
+                            const int col = c0 + c;  // (3 dtc + dx + 1) O + o (TD = 1: dtc = 0, dt from the type)
+                            if (col < 3 * TD * O) {
+                                const int blk = col / O, o = col - blk * O;
+                                const int dtk = TD == 3 ? blk / 3 : dti, dxi = blk % 3;
+                                atomicAdd(&dW[((long)(k0 + 27 * dtk + dxi) * O + o) * I + i], v[c]);
                             }
                         }
                     }
@@ -1784,19 +1792,22 @@ __global__ void __launch_bounds__(dwline::THREADS) k_conv_dw_line_tc(const __gri
 // dW and db of one layer through the x-line weight-gradient kernel: X [V][I] is
 // padded without x ghosts into xpad (unless x_padded: xpad holds it already),
 // dY [V][O] with them into ypad (unless y_padded)
-template <int NP>
+// (TD = 3: the three dt columns of each tap ride on dY in N as the dx ones do, for
+// 3 TD O <= NP; one CTA type per channel chunk instead of three)
+template <int NP, int TD>
 cudaError_t conv_dw_line_tc(const bf16 *dY, int O, const bf16 *X, int I, const Lat &g, float *dW, float *db,
                             int *err, bf16 *xpad, bf16 *ypad, cudaStream_t s, bool x_padded = false,
                             bool y_padded = false)
 {
+    static_assert(TD == 1 || TD == 3, "dt per CTA type or all three in N");
     typedef DwLineLayout<NP> LY;
     static std::atomic<unsigned long long> configured{ 0 };
     int nsm = 0;
-    cudaError_t e = kernel_setup((const void *)k_conv_dw_line_tc<NP>, LY::SMEM, configured, &nsm);
+    cudaError_t e = kernel_setup((const void *)k_conv_dw_line_tc<NP, TD>, LY::SMEM, configured, &nsm);
     if (e != cudaSuccess) return e;
     const EncodeTiledFn enc = encode_tiled();
     const int G = I / 8, OG = O / 8;
-    if (!enc || !xpad || !ypad || I % 8 || O % 8 || 3 * O > NP) return cudaErrorNotSupported;
+    if (!enc || !xpad || !ypad || I % 8 || O % 8 || 3 * TD * O > NP) return cudaErrorNotSupported;
     // channel groups per chunk: the largest divisor of G with 3 CH <= 15 M columns
     int CH = 1;
     for (int d = 1; d <= 5; ++d)
@@ -1827,10 +1838,10 @@ cudaError_t conv_dw_line_tc(const bf16 *dY, int O, const bf16 *X, int I, const L
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
-    const int NT = 3 * ((G + CH - 1) / CH);
+    const int NT = (3 / TD) * ((G + CH - 1) / CH);
     const int NS = g.V / 128;
     const int R = std::max(1, std::min(nsm / NT, NS));
-    k_conv_dw_line_tc<NP><<<NT * R, dwline::THREADS, LY::SMEM, s>>>(tmap[0], tmap[1], I, O, CH, g, dW, db, err);
+    k_conv_dw_line_tc<NP, TD><<<NT * R, dwline::THREADS, LY::SMEM, s>>>(tmap[0], tmap[1], I, O, CH, g, dW, db, err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (3 * CH >= 16) {  // no free M column for the ones: the bias gradient on its own
         if (!dY) return cudaErrorInvalidValue;
@@ -1958,8 +1969,8 @@ template <int IP, int N>
 static cudaError_t dw_tensor(const gf_net *n, const bf16 *dY, int O, const bf16 *X, int I, float *dW, float *db)
 {
     if (n->use_halo == 1 && n->ypad && dw_line_ok(n->g)) {
-        if (O <= 8) return conv_dw_line_tc<32>(dY, O, X, I, n->g, dW, db, n->derr, n->xpad, n->ypad, n->stream);
-        return conv_dw_line_tc<96>(dY, O, X, I, n->g, dW, db, n->derr, n->xpad, n->ypad, n->stream);
+        if (O <= 8) return conv_dw_line_tc<96, 3>(dY, O, X, I, n->g, dW, db, n->derr, n->xpad, n->ypad, n->stream);
+        return conv_dw_line_tc<96, 1>(dY, O, X, I, n->g, dW, db, n->derr, n->xpad, n->ypad, n->stream);
     }
     return conv_dw_tc<IP, N>(dY, O, X, I, n->g, dW, db, n->derr, n->stream);
 }
@@ -2014,19 +2025,19 @@ static int backward_line(gf_net *n, const bf16 *f)
     cudaStream_t s = n->stream;
     bf16 *const *xi = n->xin;
     bf16 *yp[2] = { n->ypad, n->ypad2 };
-    NCK((conv_dw_line_tc<32>(nullptr, 8, nullptr, 32, g, n->grad + n->woff[3], n->grad + n->boff[3], n->derr,
+    NCK((conv_dw_line_tc<96, 3>(nullptr, 8, nullptr, 32, g, n->grad + n->woff[3], n->grad + n->boff[3], n->derr,
                              xi[3], yp[0], s, true, true)));
     NCK((conv_line_ptc<16, 32>(nullptr, 8, n->Wth[3], 32, nullptr, g, -1, 0, xi[3], nullptr, nullptr, yp[1], 1,
                                n->derr, yp[0], s, 1, true)));
     int cur = 1;  // yp[cur] holds dY of layer l
     for (int l = 2; l >= 1; --l) {
-        NCK((conv_dw_line_tc<96>(nullptr, 32, nullptr, 32, g, n->grad + n->woff[l], n->grad + n->boff[l], n->derr,
+        NCK((conv_dw_line_tc<96, 1>(nullptr, 32, nullptr, 32, g, n->grad + n->woff[l], n->grad + n->boff[l], n->derr,
                                  xi[l], yp[cur], s, true, true)));
         NCK((conv_line_ptc<32, 32>(nullptr, 32, n->Wth[l], 32, nullptr, g, -1, 0, xi[l], nullptr, nullptr,
                                    yp[1 - cur], 1, n->derr, yp[cur], s, 1, true)));
         cur = 1 - cur;
     }
-    NCK((conv_dw_line_tc<96>(nullptr, 32, f, 80, g, n->grad + n->woff[0], n->grad + n->boff[0], n->derr, xi[0],
+    NCK((conv_dw_line_tc<96, 1>(nullptr, 32, f, 80, g, n->grad + n->woff[0], n->grad + n->boff[0], n->derr, xi[0],
                              yp[cur], s, true, true)));
     return GF_OK;
 }
