@@ -195,21 +195,8 @@ __global__ void k_sum_partials(const double *p, int n, double scale, double *out
     if (threadIdx.x == 0) *out = s * scale;
 }
 
-// Adam on the FP32 master parameters, then BF16 copies W[k][o][i] and Wt[k][i][o]
-__global__ void k_adam(float *__restrict__ p, const float *__restrict__ gr, float *__restrict__ m,
-                       float *__restrict__ v, long n, float lr, float b1, float b2, float eps, float c1, float c2)
-{
-    long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    float gi = gr[e];
-    float mi = b1 * m[e] + (1.0f - b1) * gi;
-    float vi = b2 * v[e] + (1.0f - b2) * gi * gi;
-    m[e] = mi;
-    v[e] = vi;
-    p[e] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
-}
-
-// ... and the same two blocked by 8 input channels for the halo kernels' TMA
+// BF16 copies of the weights W [81][O][I]: W[k][o][i] and Wt[k][i][o] for the
+// gather kernels, and the same two blocked by 8 input channels for the halo kernels' TMA
 // boxes: Wh[i / 8][k][o][i % 8] and Wth[o / 8][k][i][o % 8] (I, O multiples of 8)
 // Row block of tap k = jx + 3 jy + 9 jz + 27 jt in the blocked weight copies used with the
 // given sign of the shift: within each dt slab (27 rows) the order is (jy, z block, jx) with z
@@ -220,20 +207,57 @@ __host__ __device__ constexpr int slab_row(int k, int sign)
     return 27 * (k / 27) + (k % 3) + 3 * (sign > 0 ? 2 - (k / 9) % 3 : (k / 9) % 3) + 9 * ((k / 3) % 3);
 }
 
+// weight e of W [81][O][I] (FP32 value w) into its four BF16 copies
+__device__ __forceinline__ void cast_weight(long e, float wf, int I, int O, bf16 *__restrict__ Wb,
+                                            bf16 *__restrict__ Wt, bf16 *__restrict__ Wh, bf16 *__restrict__ Wth)
+{
+    int k = (int)(e / ((long)I * O));
+    int r = (int)(e - (long)k * I * O);
+    int o = r / I, i = r - o * I;
+    bf16 w = __float2bfloat16(wf);
+    Wb[e] = w;
+    Wt[((long)k * I + i) * O + o] = w;
+    Wh[(((long)(i >> 3) * 81 + slab_row(k, 1)) * O + o) * 8 + (i & 7)] = w;
+    Wth[(((long)(o >> 3) * 81 + slab_row(k, -1)) * I + i) * 8 + (o & 7)] = w;
+}
+
 __global__ void k_cast_weights(const float *__restrict__ W, int I, int O, bf16 *__restrict__ Wb,
                                bf16 *__restrict__ Wt, bf16 *__restrict__ Wh, bf16 *__restrict__ Wth)
 {
     long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long n = 81L * I * O;
     if (e >= n) return;
-    int k = (int)(e / ((long)I * O));
-    int r = (int)(e - (long)k * I * O);
-    int o = r / I, i = r - o * I;
-    bf16 w = __float2bfloat16(W[e]);
-    Wb[e] = w;
-    Wt[((long)k * I + i) * O + o] = w;
-    Wh[(((long)(i >> 3) * 81 + slab_row(k, 1)) * O + o) * 8 + (i & 7)] = w;
-    Wth[(((long)(o >> 3) * 81 + slab_row(k, -1)) * I + i) * 8 + (o & 7)] = w;
+    cast_weight(e, W[e], I, O, Wb, Wt, Wh, Wth);
+}
+
+// the four layers' weight copies, for the Adam kernel
+struct WeightCopies {
+    long woff[4];
+    int I[4], O[4];
+    bf16 *Wb[4], *Wt[4], *Wh[4], *Wth[4];
+};
+
+// Adam on the FP32 master parameters; an updated weight goes into its BF16 copies at once
+// (W[k][o][i], Wt[k][i][o] and the blocked Wh, Wth), as k_cast_weights would write them
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ gr, float *__restrict__ m,
+                       float *__restrict__ v, long n, float lr, float b1, float b2, float eps, float c1, float c2,
+                       WeightCopies wc)
+{
+    long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    float gi = gr[e];
+    float mi = b1 * m[e] + (1.0f - b1) * gi;
+    float vi = b2 * v[e] + (1.0f - b2) * gi * gi;
+    m[e] = mi;
+    v[e] = vi;
+    const float pi = p[e] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    p[e] = pi;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const int I = wc.I[l], O = wc.O[l];
+        const long r = e - wc.woff[l];
+        if (r >= 0 && r < 81L * I * O) cast_weight(r, pi, I, O, wc.Wb[l], wc.Wt[l], wc.Wh[l], wc.Wth[l]);
+    }
 }
 
 
@@ -2306,11 +2330,19 @@ int gf_net_train_step(gf_net *n, const void *features, const float *target, floa
     const float b1 = 0.9f, b2 = 0.999f;
     float c1 = 1.0f / (1.0f - powf(b1, (float)n->step));
     float c2 = 1.0f / (1.0f - powf(b2, (float)n->step));
+    WeightCopies wc;
+    for (int l = 0; l < 4; ++l) {
+        wc.woff[l] = n->woff[l];
+        wc.I[l] = kC[l];
+        wc.O[l] = kC[l + 1];
+        wc.Wb[l] = n->Wb[l];
+        wc.Wt[l] = n->Wt[l];
+        wc.Wh[l] = n->Wh[l];
+        wc.Wth[l] = n->Wth[l];
+    }
     k_adam<<<(int)((n->np + 255) / 256), 256, 0, n->stream>>>(n->params, n->grad, n->m, n->v, n->np, lr, b1, b2,
-                                                              1e-8f, c1, c2);
+                                                              1e-8f, c1, c2, wc);
     NCK(cudaGetLastError());
-    r = refresh_weights(n);
-    if (r != GF_OK) return r;
     if (loss) NCK(cudaMemcpyAsync(loss, n->dloss, sizeof(double), cudaMemcpyDefault, n->stream));
     return check_status(n);
 }

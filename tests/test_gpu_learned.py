@@ -317,6 +317,31 @@ def test_training_reduces_loss():
     assert gf.gf_net_gradient(net, feats, target) < 0.5 * l0
 
 
+@pytest.mark.parametrize("dims", [(32, 4, 4, 3), (6, 4, 6, 10)])
+def test_train_step_weight_copies_match_a_fresh_cast(dims):
+    """The Adam kernel writes each updated weight into the four BF16 copies the
+    convolutions read; setting the same FP32 parameters again casts them anew.
+    Both must give the same network, bit for bit (x-line and gather paths)."""
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(7)
+    feats = torch.from_numpy(bf16_round(rng.standard_normal((V, 80)))).to(torch.bfloat16).cuda()
+    target = torch.from_numpy(rng.standard_normal((V, 8)).astype(np.float32)).cuda()
+    net = gf.gf_net_create(dims)
+    gf.gf_net_set_params(net, learned.init_params(5))
+    for _ in range(3):
+        gf.gf_net_train_step(net, feats, target, 1e-2)
+    out_step = torch.empty(V, 8, dtype=torch.float32, device="cuda")
+    gf.gf_net_forward(net, feats, out_step)
+    params = np.zeros(gf.gf_net_param_count(), dtype=np.float32)
+    gf.gf_net_get_params(net, params)
+    fresh = gf.gf_net_create(dims)
+    gf.gf_net_set_params(fresh, params)
+    out_fresh = torch.empty(V, 8, dtype=torch.float32, device="cuda")
+    gf.gf_net_forward(fresh, feats, out_fresh)
+    assert torch.equal(out_step, out_fresh)
+    assert out_step.abs().max().item() > 0
+
+
 def test_tensor_core_and_cuda_core_convolutions_agree():
     dims = (4, 6, 4, 8)
     V = int(np.prod(dims))
